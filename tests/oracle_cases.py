@@ -1,0 +1,78 @@
+"""Tiny hand-built systems with closed-form answers (shared by the oracle pin
+tests and the GPU parity tests).  Pure input construction: no CD arithmetic.
+"""
+import math
+
+import numpy as np
+
+from paper_1104_3516_gb300.workloads import Workload, masses
+
+G = 1.0
+DT = 1e-3
+
+
+def _wl(name, dim, x, r, v=None, w=None, inv_I=None, **kw):
+    x = np.asarray(x, dtype=np.float64).reshape(-1, dim)
+    r = np.asarray(r, dtype=np.float64)
+    n = r.shape[0]
+    inv_m, iI = masses(dim, r)
+    if inv_I is not None:
+        iI = np.asarray(inv_I, dtype=np.float64)
+    v = np.zeros((n, dim)) if v is None else np.asarray(v, dtype=np.float64).reshape(n, dim)
+    if w is None:
+        w = np.zeros(n) if dim == 2 else np.zeros((n, 3))
+    return Workload(name=name, dim=dim, x=x, v=v, w=np.asarray(w, dtype=np.float64), r=r, inv_m=inv_m,
+                    inv_I=iI, **kw)
+
+
+def resting_disc(dim=2, radius=1.0, mu=0.3):
+    """One particle touching the floor (gap 0), at rest, gravity 1."""
+    if dim == 2:
+        return _wl("resting_disc", 2, [[0.0, radius]], [radius], dt=DT, mu=mu, gravity=(0.0, -G, 0.0),
+                   box_lo=(-10.0, 0.0, 0.0), box_hi=(10.0, 10.0, 1.0), wall_mask=0b0100)
+    return _wl("resting_sphere", 3, [[0.0, 0.0, radius]], [radius], dt=DT, mu=mu, gravity=(0.0, 0.0, -G),
+               box_lo=(-10.0, -10.0, 0.0), box_hi=(10.0, 10.0, 10.0), wall_mask=0b010000)
+
+
+def column(n=6, radius=1.0, mu=0.3):
+    """n equal discs stacked vertically on the floor, all gaps exactly 0."""
+    y = radius + 2.0 * radius * np.arange(n)
+    x = np.stack([np.zeros(n), y], axis=1)
+    return _wl("column", 2, x, np.full(n, radius), dt=DT, mu=mu, gravity=(0.0, -G, 0.0),
+               box_lo=(-5.0, 0.0, 0.0), box_hi=(5.0, 2.0 * radius * n + 5.0, 1.0), wall_mask=0b0100)
+
+
+def chain(n=8, radius=1.0, force=1.0):
+    """n equal discs in a row along x touching each other, the first touching
+    the fixed wall x = 0; a force `force` pushes the last one towards the wall.
+    No gravity.  Returns (workload, f_ext)."""
+    xs = radius + 2.0 * radius * np.arange(n)
+    x = np.stack([xs, np.zeros(n)], axis=1)
+    wl = _wl("chain", 2, x, np.full(n, radius), dt=DT, mu=0.3, gravity=(0.0, 0.0, 0.0),
+             box_lo=(0.0, -5.0, 0.0), box_hi=(2.0 * radius * n + 5.0, 5.0, 1.0), wall_mask=0b0001)
+    f = np.zeros((n, 2))
+    f[-1, 0] = -force
+    return wl, f
+
+
+def incline(theta, mu, dim=2, frozen=True, radius=1.0):
+    """One particle resting on the floor with gravity tilted by theta:
+    g = (sin theta, -cos theta) (2D) or (sin theta, 0, -cos theta) (3D)."""
+    if dim == 2:
+        inv_I = np.zeros(1) if frozen else None
+        return _wl("incline", 2, [[0.0, radius]], [radius], inv_I=inv_I, dt=DT, mu=mu,
+                   gravity=(G * math.sin(theta), -G * math.cos(theta), 0.0), box_lo=(-10.0, 0.0, 0.0),
+                   box_hi=(10.0, 10.0, 1.0), wall_mask=0b0100)
+    inv_I = np.zeros(1) if frozen else None
+    return _wl("incline3", 3, [[0.0, 0.0, radius]], [radius], inv_I=inv_I, dt=DT, mu=mu,
+               gravity=(G * math.sin(theta), 0.0, -G * math.cos(theta)), box_lo=(-10.0, -10.0, 0.0),
+               box_hi=(10.0, 10.0, 10.0), wall_mask=0b010000)
+
+
+def head_on(v1, v2, r1=1.0, r2=1.0, gap=None):
+    """Two discs on the x axis approaching each other; no gravity, no walls."""
+    if gap is None:
+        gap = 0.5 * (v1 - v2) * DT
+    x = [[0.0, 0.0], [r1 + r2 + gap, 0.0]]
+    return _wl("head_on", 2, x, [r1, r2], v=[[v1, 0.0], [v2, 0.0]], dt=DT, mu=0.3, gravity=(0.0, 0.0, 0.0),
+               box_lo=(-20.0, -20.0, 0.0), box_hi=(20.0, 20.0, 1.0))

@@ -1,0 +1,305 @@
+"""Pins of the FP64 oracle against what the paper and mechanics fix.
+
+Each test checks a closed form, a threshold, an invariant or a special case
+that a plausible slip in the oracle (dropped term, wrong sign, transposed
+operand, wrong update order) would break.  No GPU needed.
+"""
+import math
+
+import numpy as np
+import pytest
+
+import oracle as O
+from oracle_adapter import params, system
+import oracle_cases as cases
+
+G, DT = cases.G, cases.DT
+
+
+def _one_step(wl, **over):
+    s = system(wl, **over)
+    st = s.step()
+    return s, st
+
+
+# --- single contact (Fig. 2, Eqs. 3-5) -------------------------------------
+
+@pytest.mark.parametrize("dim", [2, 3])
+def test_resting_particle_normal_impulse_is_weight(dim):
+    """A particle at rest on the floor: P_n = m g dt after the solve, P_t = 0,
+    and the new velocity is zero (Sec. 2.1, Eqs. 1, 3, 5)."""
+    wl = cases.resting_disc(dim=dim)
+    s, st = _one_step(wl, criterion=O.CRIT_GLOBAL_REL, alpha=1e-14)
+    m = 1.0 / wl.inv_m[0]
+    P = s.impulses
+    assert s.nc == 1 and st["converged"]
+    assert P[0, 0] == pytest.approx(m * G * DT, rel=1e-15, abs=0)
+    assert np.all(np.abs(P[0, 1:]) < 1e-18)
+    assert np.all(np.abs(s.v) < 1e-18)
+    # wall force reported by the solve: the weight m g
+    assert st["wall_force"][2 if dim == 2 else 4] == pytest.approx(m * G, rel=1e-14)
+
+
+def test_open_contact_keeps_zero_force():
+    """Eq. 3: a contact whose gap stays positive with R = 0 gets no force."""
+    wl = cases.resting_disc()
+    wl.x[0, 1] = 1.1          # gap 0.1 < delta: detected, but stays open
+    s, st = _one_step(wl)
+    assert s.nc == 1
+    assert np.all(s.impulses == 0.0)
+    assert s.v[1] == pytest.approx(-G * DT, rel=1e-15)
+    assert st["sweeps"] == 1 and st["converged"]
+
+
+# --- the iterated network (Sec. 2.1) -----------------------------------------
+
+@pytest.mark.parametrize("order", [O.ORDER_RANDOM, O.ORDER_COLOUR])
+def test_vertical_column_static_force_chain(order):
+    """Column of n equal discs on the floor: contact k from the top carries
+    k m g dt, no tangential force; same in random sequential and colour order."""
+    n = 6
+    wl = cases.column(n=n)
+    s, st = _one_step(wl, order=order, criterion=O.CRIT_GLOBAL_REL, alpha=1e-15, max_sweeps=20000)
+    m = 1.0 / wl.inv_m[0]
+    pairs, P = s.contacts, s.impulses
+    assert st["converged"]
+    assert len(pairs) == n     # n-1 disc pairs + floor
+    for (a, b), (pn, pt) in zip(pairs, P):
+        k = n - a if b == n + 2 else n - 1 - a   # discs above this contact
+        assert pn == pytest.approx(k * m * G * DT, rel=1e-9)
+        assert abs(pt) < 1e-15
+    assert np.max(np.abs(s.v)) < 1e-9
+
+
+def test_column_local_criterion_reaches_the_chain():
+    """Convergence test (I) stops with every contact close to k m g dt."""
+    n = 6
+    wl = cases.column(n=n)
+    s, st = _one_step(wl, order=O.ORDER_RANDOM, criterion=O.CRIT_LOCAL, alpha=1e-12, max_sweeps=20000)
+    assert st["converged"]
+    m = 1.0 / wl.inv_m[0]
+    for (a, b), (pn, _) in zip(s.contacts, s.impulses):
+        k = n - a if b == n + 2 else n - 1 - a
+        assert pn == pytest.approx(k * m * G * DT, rel=1e-4)
+
+
+def test_compressed_chain_carries_the_force_everywhere():
+    """Fig. 13(a): a chain of touching discs pressed by F against a fixed
+    wall carries F dt on every contact once converged."""
+    F = 2.5
+    wl, f = cases.chain(n=8, force=F)
+    s, st = _one_step(wl, f_ext=f, order=O.ORDER_RANDOM, criterion=O.CRIT_GLOBAL_REL, alpha=1e-15,
+                      max_sweeps=50000)
+    assert st["converged"]
+    assert s.nc == 8
+    assert np.allclose(s.impulses[:, 0], F * DT, rtol=1e-9, atol=0)
+
+
+def test_chain_iterations_grow_diffusively():
+    """Sec. 4.3: forces relax diffusively, so the sweeps needed grow ~ n^2
+    (loose check: doubling the chain needs well over twice the sweeps)."""
+    sweeps = []
+    for n in (8, 16):
+        wl, f = cases.chain(n=n, force=1.0)
+        s, st = _one_step(wl, f_ext=f, order=O.ORDER_RANDOM, criterion=O.CRIT_LOCAL, alpha=1e-10,
+                          max_sweeps=200000)
+        assert st["converged"]
+        sweeps.append(st["sweeps"])
+    assert sweeps[1] > 2.5 * sweeps[0]
+
+
+# --- Coulomb friction (Eqs. 6-11) --------------------------------------------
+
+@pytest.mark.parametrize("dim", [2, 3])
+def test_incline_frozen_rotation_stick_below_tan_mu(dim):
+    mu = 0.4
+    th = math.atan(0.9 * mu)
+    wl = cases.incline(th, mu, dim=dim, frozen=True)
+    s, st = _one_step(wl, alpha=1e-15, max_sweeps=100)
+    m = 1.0 / wl.inv_m[0]
+    P = s.impulses[0]
+    assert P[0] == pytest.approx(m * G * math.cos(th) * DT, rel=1e-13)
+    pt = abs(P[1]) if dim == 2 else float(np.linalg.norm(P[1:]))
+    assert pt == pytest.approx(m * G * math.sin(th) * DT, rel=1e-13)
+    assert np.max(np.abs(s.v)) < 1e-15      # stuck
+
+
+@pytest.mark.parametrize("dim", [2, 3])
+def test_incline_frozen_rotation_slides_above_tan_mu(dim):
+    mu = 0.4
+    th = math.atan(1.1 * mu)
+    wl = cases.incline(th, mu, dim=dim, frozen=True)
+    s, st = _one_step(wl, alpha=1e-15, max_sweeps=100)
+    P = s.impulses[0]
+    pt = abs(P[1]) if dim == 2 else float(np.linalg.norm(P[1:]))
+    assert pt == pytest.approx(mu * P[0], rel=1e-14)
+    # sliding: a = g (sin th - mu cos th) along the slope, friction opposing
+    assert s.v[0] == pytest.approx(G * (math.sin(th) - mu * math.cos(th)) * DT, rel=1e-12)
+    # the tangential impulse opposes the motion: on the particle it points to -x
+    force_on_particle_x = -(P[1] if dim == 2 else P[1])
+    assert force_on_particle_x < 0
+
+
+@pytest.mark.parametrize("dim,factor,roll_frac", [(2, 3.0, 2.0 / 3.0), (3, 3.5, 5.0 / 7.0)])
+def test_incline_free_rotation_rolls_until_threshold(dim, factor, roll_frac):
+    """A free disc rolls without slipping while tan(theta) <= 3 mu (sphere:
+    7 mu / 2): then v = (2/3) g sin(theta) dt (sphere 5/7) and the contact
+    point is at rest; beyond the threshold it slips."""
+    mu = 0.2
+    th = math.atan(0.9 * factor * mu)
+    wl = cases.incline(th, mu, dim=dim, frozen=False)
+    s, st = _one_step(wl, alpha=1e-15, max_sweeps=100)
+    r = wl.r[0]
+    assert s.v[0] == pytest.approx(roll_frac * G * math.sin(th) * DT, rel=1e-12)
+    if dim == 2:
+        # contact point (below the centre, arm -r e_y): v_x + w r = 0
+        assert abs(s.v[0] + s.w[0] * r) < 1e-15
+    else:
+        # arm -r e_z: v + w x (-r e_z) -> x component v_x - w_y r
+        assert abs(s.v[0] - s.w[1] * r) < 1e-15
+    P = s.impulses[0]
+    pt = abs(P[1]) if dim == 2 else float(np.linalg.norm(P[1:]))
+    assert pt < mu * P[0]
+    th2 = math.atan(1.1 * factor * mu)
+    wl2 = cases.incline(th2, mu, dim=dim, frozen=False)
+    s2, _ = _one_step(wl2, alpha=1e-15, max_sweeps=100)
+    P2 = s2.impulses[0]
+    pt2 = abs(P2[1]) if dim == 2 else float(np.linalg.norm(P2[1:]))
+    assert pt2 == pytest.approx(mu * P2[0], rel=1e-14)
+    slip = (s2.v[0] + s2.w[0] * r) if dim == 2 else (s2.v[0] - s2.w[1] * r)
+    assert slip > 1e-9
+
+
+# --- perfectly inelastic collision (Sec. 2.1, Eq. 4) -------------------------
+
+@pytest.mark.parametrize("r1,r2,v1,v2", [(1.0, 1.0, 2.0, -2.0), (1.2, 0.8, 3.0, -0.5)])
+def test_head_on_collision_closes_gap_then_moves_together(r1, r2, v1, v2):
+    wl = cases.head_on(v1, v2, r1=r1, r2=r2)
+    m1, m2 = 1.0 / wl.inv_m[0], 1.0 / wl.inv_m[1]
+    p0 = m1 * v1 + m2 * v2
+    s = system(wl, alpha=1e-15, max_sweeps=100)
+    s.step()
+    vx = s.v.reshape(2, 2)[:, 0]
+    x = s.x.reshape(2, 2)
+    gap = (x[1, 0] - x[0, 0]) - (r1 + r2)
+    assert abs(gap) < 1e-13                          # Eq. 4: the new gap is zero
+    assert m1 * vx[0] + m2 * vx[1] == pytest.approx(p0, rel=1e-14)
+    s.step()                                         # touching now: no rebound
+    vx = s.v.reshape(2, 2)[:, 0]
+    vc = p0 / (m1 + m2)
+    assert vx[0] == pytest.approx(vc, rel=1e-12, abs=1e-14)
+    assert vx[1] == pytest.approx(vc, rel=1e-12, abs=1e-14)
+
+
+# --- invariants ----------------------------------------------------------------
+
+def _gas(n=300, L=60.0, seed=3, dim=2):
+    from paper_1104_3516_gb300 import workloads as W
+    r = W.uniform(seed, n, 0.8, 1.2)
+    x = W.rsa(dim, n, r, (0.0,) * dim, (L,) * dim, (1,) * dim, seed)
+    v = W.normal(seed, n * dim, 1.0).reshape(n, dim)
+    inv_m, inv_I = W.masses(dim, r)
+    w = np.zeros(n) if dim == 2 else np.zeros((n, 3))
+    return W.Workload(name="gas", dim=dim, x=x, v=v, w=w, r=r, inv_m=inv_m, inv_I=inv_I, dt=2e-2,
+                      gravity=(0.0, 0.0, 0.0), box_lo=(0.0, 0.0, 0.0), box_hi=(L, L, L), periodic=(1, 1, 1))
+
+
+@pytest.mark.parametrize("dim", [2, 3])
+def test_momentum_conserved_without_walls(dim):
+    """Each contact applies +P and -P, so total momentum is conserved and the
+    perfectly inelastic contacts never add kinetic energy."""
+    wl = _gas(dim=dim)
+    m = 1.0 / wl.inv_m
+    s = system(wl, alpha=1e-10, max_sweeps=500)
+    p0 = (m[:, None] * s.v.reshape(-1, dim)).sum(axis=0)
+    scale = float((m[:, None] * np.abs(s.v.reshape(-1, dim))).sum())
+
+    def ke():
+        v = s.v.reshape(-1, dim)
+        I = 1.0 / wl.inv_I
+        wr = s.w.reshape(len(m), -1)
+        return 0.5 * float((m[:, None] * v * v).sum()) + 0.5 * float((I[:, None] * wr * wr).sum())
+
+    e_prev = ke()
+    touched = 0
+    for _ in range(15):
+        st = s.step()
+        touched += int(np.count_nonzero(s.impulses[:, 0]))
+        e = ke()
+        assert e <= e_prev * (1 + 1e-12)
+        e_prev = e
+    p1 = (m[:, None] * s.v.reshape(-1, dim)).sum(axis=0)
+    assert touched > 0
+    assert np.all(np.abs(p1 - p0) <= 1e-13 * scale)
+
+
+def test_free_fall_is_semi_implicit_euler():
+    """Eqs. 1-2: v(t+dt) = v + g dt, then r(t+dt) = r + v(t+dt) dt, so after k
+    steps y = y0 - g dt^2 k (k + 1) / 2 (an explicit update would give k(k-1)/2)."""
+    wl = cases.resting_disc()
+    wl.x[0, 1] = 5.0
+    s = system(wl)
+    k = 7
+    for _ in range(k):
+        s.step()
+    assert s.v[1] == pytest.approx(-G * DT * k, rel=1e-14)
+    assert s.x[1] == pytest.approx(5.0 - G * DT * DT * k * (k + 1) / 2, rel=1e-14)
+
+
+# --- convergence tests (Sec. 2.1) ----------------------------------------------
+
+def test_squared_global_test_matches_plain_test_at_sqrt_alpha():
+    """Test (II) compares the squared ratio with alpha: equivalent to the
+    plain ratio against sqrt(alpha)."""
+    wl = cases.column(n=5)
+    _, st_sq = _one_step(wl, order=O.ORDER_COLOUR, criterion=O.CRIT_GLOBAL_SQ, alpha=1e-12, max_sweeps=10000)
+    _, st_pl = _one_step(wl, order=O.ORDER_COLOUR, criterion=O.CRIT_GLOBAL_REL, alpha=1e-6, max_sweeps=10000)
+    assert st_sq["sweeps"] == st_pl["sweeps"] and st_sq["converged"] and st_pl["converged"]
+    _, st_tight = _one_step(wl, order=O.ORDER_COLOUR, criterion=O.CRIT_GLOBAL_REL, alpha=1e-12, max_sweeps=10000)
+    assert st_tight["sweeps"] > st_pl["sweeps"]
+
+
+def test_zero_alpha_never_converges_and_hits_the_cap():
+    wl = cases.column(n=4)
+    _, st = _one_step(wl, alpha=0.0, max_sweeps=37)
+    assert st["sweeps"] == 37 and not st["converged"]
+
+
+def test_warm_start_reuses_the_previous_forces():
+    """A static column stepped twice: with the forces carried over the second
+    solve needs only a few sweeps; from zero forces it needs as many again."""
+    wl = cases.column(n=5)
+    s = system(wl, alpha=1e-13, max_sweeps=20000, order=O.ORDER_RANDOM)
+    st1 = s.step()
+    st2 = s.step()
+    assert st1["sweeps"] > 10
+    assert 4 * st2["sweeps"] < st1["sweeps"]
+    s_cold = system(wl, alpha=1e-13, max_sweeps=20000, order=O.ORDER_RANDOM, warm_start=0)
+    s_cold.step()
+    st_cold = s_cold.step()
+    assert st_cold["sweeps"] > 4 * st2["sweeps"]
+
+
+# --- mixed parallel / sequential update (Sec. 2.3) -----------------------------
+
+def test_parallel_fraction_zero_is_the_sequential_scheme():
+    wl = cases.column(n=5)
+    a, st_a = _one_step(wl, order=O.ORDER_COLOUR, alpha=1e-13, max_sweeps=5000)
+    b, st_b = _one_step(wl, order=O.ORDER_COLOUR, alpha=1e-13, max_sweeps=5000, parallel_p=0.0)
+    assert st_a["sweeps"] == st_b["sweeps"]
+    assert np.array_equal(a.impulses, b.impulses)
+
+
+def test_jacobi_update_needs_more_sweeps_than_gauss_seidel():
+    """Sec. 4.3: the parallel (Jacobi) update diffuses information more slowly
+    (D_s / D_p ~ 1.5), so the chain needs more sweeps; both reach F dt."""
+    F = 1.0
+    out = {}
+    for p in (0.0, 1.0):
+        wl, f = cases.chain(n=12, force=F)
+        s, st = _one_step(wl, f_ext=f, order=O.ORDER_RANDOM, criterion=O.CRIT_LOCAL, alpha=1e-16,
+                          max_sweeps=200000, parallel_p=p)
+        assert st["converged"]
+        assert np.allclose(s.impulses[:, 0], F * DT, rtol=1e-5)
+        out[p] = st["sweeps"]
+    assert out[1.0] > 1.2 * out[0.0]
