@@ -1,0 +1,198 @@
+/*
+ * cd_api.h -- C ABI of the GB300 (sm_103a) Contact Dynamics hot path.
+ *
+ * The library computes one time step of the non-smooth Contact Dynamics (CD)
+ * method of Shojaaee et al., "An Adaptive Hierarchical Domain Decomposition
+ * Method for Parallel Contact Dynamics Simulations of Granular Materials"
+ * (arXiv:1104.3516), for rigid frictional discs (2D) or spheres (3D):
+ *
+ *   1. contact detection with a cell list (Sec. 3.2), margin delta (Eq. 12,
+ *      Sec. 3.1: cell side l = 2 r_max + delta),
+ *   2. the iterative contact-impulse solve: every contact re-solved from its
+ *      two bodies' current velocities against the Signorini (Eqs. 3-5) and
+ *      Coulomb (Eqs. 6-11) conditions, nonlinear Gauss-Seidel until the
+ *      convergence test of Sec. 2.1 passes (Fig. 2, Sec. 2.1),
+ *   3. the first-order Euler update of velocities and positions (Eqs. 1-2).
+ *
+ * The Gauss-Seidel order is a colour order: contacts are coloured so that no
+ * two contacts of one colour share a particle, and each colour is updated in
+ * parallel.  This is an admissible sequential order of the paper's scheme
+ * (each freshly computed force is used immediately by later contacts).
+ *
+ * Conventions used by every entry point:
+ *   - Arrays passed as pointers are DEVICE pointers on the current CUDA
+ *     device unless the parameter name ends in `_host`.  They are owned by
+ *     the caller and must stay valid for the life of the system; the library
+ *     never frees them.
+ *   - Layouts: pos, vel: n*dim doubles interleaved per particle
+ *     (x0,y0[,z0],x1,...); omega: n doubles (2D, about z) or n*3 (3D);
+ *     theta: n doubles (2D orientation) or NULL.
+ *   - Walls are axis-aligned planes with index k = 2*axis + side (side 0:
+ *     low plane, side 1: high plane), infinite mass and prescribed velocity.
+ *     A wall acts as body number n + k in contact keys.
+ *   - Contacts are identified by key (a, b), a < b; the normal points from
+ *     body a to body b; impulses are P = R dt.  2D impulses are stored as
+ *     (P_n, P_t) with t = (-n_y, n_x); 3D as (P_n, P_tx, P_ty, P_tz).
+ *   - All work is enqueued on the stream given at creation; calls that
+ *     return statistics synchronise that stream.  A system is not
+ *     thread-safe; use one system per stream.
+ *   - Every function returns a cd_status and never aborts or traps; the
+ *     message of the last failure is available from cd_last_error().
+ */
+#ifndef CD_API_H
+#define CD_API_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    CD_OK = 0,
+    CD_ERR_INVALID_ARG = 1,   /* bad size, NaN or non-positive radius, bad params */
+    CD_ERR_CUDA = 2,          /* a CUDA runtime call failed (message has details) */
+    CD_ERR_OOM = 3,           /* workspace missing or too small */
+    CD_ERR_CAPACITY = 4,      /* more contacts (or colours) than the capacity */
+    CD_ERR_NOT_CONVERGED = 5, /* informational: sweep cap reached, step still taken */
+    CD_ERR_TIMEOUT = 6,       /* a bounded device-side wait ran out */
+    CD_ERR_STATE = 7          /* call out of order (e.g. solve before detection) */
+} cd_status;
+
+enum { CD_FP64 = 0, CD_FP32 = 1 };
+/* Convergence tests of Sec. 2.1.  GLOBAL_REL: |R^j - R^{j-1}| / (R^j + R^{j-1})
+ * < alpha with R = mean |P| (the default); GLOBAL_SQ: the paper's squared form
+ * (II); LOCAL: test (I) (90% of contacts below alpha relative, the rest below
+ * alpha R_avg^2 absolute); NONE: run exactly max_sweeps. */
+enum { CD_CONV_NONE = -1, CD_CONV_GLOBAL_REL = 0, CD_CONV_GLOBAL_SQ = 1, CD_CONV_LOCAL = 2 };
+
+typedef struct {
+    int64_t dim;            /* 2 or 3 */
+    int64_t precision;      /* CD_FP64 or CD_FP32 (sweep arithmetic; detection,
+                               residual and integration stay FP64) */
+    double dt;              /* time step */
+    double mu;              /* Coulomb friction coefficient (Eq. 8) */
+    double gravity[3];      /* external acceleration, applied explicitly (Eq. 1) */
+    double box_lo[3];       /* box spanned by the cell grid; periodic extent */
+    double box_hi[3];
+    int64_t periodic[3];    /* 1: periodic along that axis */
+    int64_t wall_mask;      /* bit k set: wall k present */
+    double wall_pos[6];     /* initial plane position of each wall */
+    double wall_vel[18];    /* velocity of each wall (3 per wall) */
+    double delta;           /* detection margin: contact iff surface gap < delta */
+    double alpha;           /* convergence threshold */
+    int64_t criterion;      /* CD_CONV_* */
+    int64_t max_sweeps;     /* iteration cap N_I per time step */
+    int64_t warm_start;     /* 1: start each solve from the previous step's
+                               impulses matched by contact key; 0: from zero */
+    int64_t rotations;      /* 0: rotational degrees of freedom frozen */
+    uint64_t seed;          /* seeds the colouring priorities */
+    int64_t max_contacts;   /* contact capacity of the workspace */
+} cd_params;
+
+typedef struct cd_system cd_system;
+
+typedef struct {
+    int64_t sweeps;           /* sweeps done in the last solve */
+    int64_t converged;        /* 1 if the convergence test passed */
+    double residual;          /* value of the convergence test at the last sweep */
+    double r_avg;             /* mean |P| after the last sweep */
+    int64_t n_contacts;
+    int64_t n_colours;
+    double wall_force[6];     /* sum of normal impulses on each wall / dt */
+} cd_solve_stats;
+
+typedef struct {
+    int64_t steps_done;
+    int64_t total_sweeps;         /* summed over the steps of the call */
+    int64_t total_contact_updates;/* sum over steps of sweeps * contacts */
+    int64_t max_sweeps_in_step;
+    int64_t n_not_converged;      /* steps that hit the sweep cap */
+    cd_solve_stats last;          /* statistics of the last step */
+} cd_step_stats;
+
+/* Creates a system over caller-owned device arrays (layouts above).
+ * inv_mass / inv_inertia: 1/m and 1/I per particle (0 for an immovable
+ * particle).  f_ext: n*dim explicit external forces, or NULL.  cuda_stream:
+ * a cudaStream_t (NULL = legacy default stream).  Validates the parameters
+ * and the radii on the device (one synchronisation) and returns
+ * CD_ERR_INVALID_ARG for a non-positive or NaN radius or a box/cell grid the
+ * periodic wrap cannot handle.  The system needs a workspace before use. */
+cd_status cd_create_system(const cd_params* params, int64_t n, double* pos, double* vel, double* omega,
+                           double* theta, const double* radius, const double* inv_mass,
+                           const double* inv_inertia, const double* f_ext, void* cuda_stream,
+                           cd_system** out);
+
+/* Bytes of device workspace the system needs (cell grid, contact arrays in
+ * key and colour order, colouring and reduction buffers). */
+cd_status cd_workspace_size(const cd_system* sys, size_t* bytes);
+
+/* Hands the system a caller-allocated device buffer of at least
+ * cd_workspace_size() bytes, 256-byte aligned.  The library never calls
+ * cudaMalloc; the buffer stays owned by the caller. */
+cd_status cd_set_workspace(cd_system* sys, void* dev_ptr, size_t bytes);
+
+/* Contact detection for the current positions (Sec. 3.2), followed by the
+ * contact geometry, the warm-start match by key, the colouring and the colour
+ * ordering.  Returns the number of contacts in *n_contacts (synchronises).
+ * If they exceed max_contacts, returns CD_ERR_CAPACITY with the number
+ * needed in *n_contacts and leaves the previous contact set unchanged. */
+cd_status cd_detect_contacts(cd_system* sys, int64_t* n_contacts);
+
+/* Replaces the contact set by the caller's list (device arrays, nc keys
+ * (a, b) with a < b in ascending key order; impulses may be NULL for zero,
+ * else nc*2 (2D) or nc*4 (3D) doubles).  Geometry, colouring and ordering are
+ * computed as after detection.  Used to feed an externally chosen contact
+ * set (for instance to compare solvers on the same contacts). */
+cd_status cd_set_contacts(cd_system* sys, int64_t nc, const int32_t* pairs, const double* impulses);
+
+/* The iterative impulse solve of Sec. 2.1 on the current contact set.  The
+ * current particle velocities are taken as the free velocities (no contact
+ * impulses); the solve applies the starting impulses, sweeps the colours
+ * until the convergence test passes or max_sweeps is reached, and writes the
+ * final velocities back into vel/omega and the impulses into the contact
+ * store.  Positions are not moved.  out may be NULL (then nothing is
+ * synchronised).  Returns CD_ERR_NOT_CONVERGED (informational) when the
+ * sweep cap was hit and out was given. */
+cd_status cd_solve_contacts(cd_system* sys, cd_solve_stats* out);
+
+/* n_steps full time steps (Fig. 3): detection (as cd_detect_contacts), the
+ * explicit external forces (Eq. 1 with F = m g + f_ext), the impulse solve
+ * (as cd_solve_contacts), the position update (Eq. 2, periodic wrap) and the
+ * wall motion.  Nothing is synchronised between steps.  out may be NULL.  On
+ * contact overflow the failing step and all later ones are skipped on the
+ * device, the state stays as it was before that step, and CD_ERR_CAPACITY is
+ * returned once out is read (needs out != NULL or a later call). */
+cd_status cd_step(cd_system* sys, int64_t n_steps, cd_step_stats* out);
+
+/* Copies the current contact set in key order into caller DEVICE arrays
+ * (any pointer may be NULL): pairs nc*2 int32, normal nc*3, gap nc,
+ * impulse nc*2 (2D) / nc*4 (3D), colour nc int32.  *n_contacts receives nc.
+ * Synchronises. */
+cd_status cd_get_contacts(cd_system* sys, int64_t* n_contacts, int32_t* pairs, double* normal, double* gap,
+                          double* impulse, int32_t* colour);
+
+/* Current wall plane positions (6 doubles, host memory).  Synchronises. */
+cd_status cd_get_walls(cd_system* sys, double* wall_pos_host);
+
+/* Host <-> device copies of the particle state (pos, vel, omega; theta if
+ * the system has it) from/to pinned or pageable host memory, enqueued on the
+ * system's stream (download synchronises). */
+cd_status cd_upload_state(cd_system* sys, const double* pos_host, const double* vel_host,
+                          const double* omega_host);
+cd_status cd_download_state(cd_system* sys, double* pos_host, double* vel_host, double* omega_host);
+
+/* Releases the host-side system object (not the caller's arrays or
+ * workspace).  Safe on NULL. */
+void cd_destroy_system(cd_system* sys);
+
+/* Message of the last failure on this system ("" if none); NULL system gives
+ * the last creation failure. */
+const char* cd_last_error(const cd_system* sys);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* CD_API_H */

@@ -1,0 +1,334 @@
+"""Python binding of the C ABI in ``include/cd_api.h`` (argument marshalling only).
+
+Every compute step runs in the CUDA library ``_lib/libcd_gb300.so``; this
+module only passes torch tensors' device pointers and the current CUDA stream.
+There is no CPU fallback: if the library is missing the import of a system
+fails with an error that says how to build it.
+
+The functions ``cd_create_system`` ... ``cd_last_error`` mirror the C entry
+points one to one; :class:`CDSystem` bundles them with the torch tensors that
+own the particle state and the workspace.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import threading
+
+import numpy as np
+import torch
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "_lib", "libcd_gb300.so")
+
+CD_OK, CD_ERR_INVALID_ARG, CD_ERR_CUDA, CD_ERR_OOM, CD_ERR_CAPACITY, CD_ERR_NOT_CONVERGED, CD_ERR_TIMEOUT, \
+    CD_ERR_STATE = range(8)
+STATUS_NAMES = ["CD_OK", "CD_ERR_INVALID_ARG", "CD_ERR_CUDA", "CD_ERR_OOM", "CD_ERR_CAPACITY",
+                "CD_ERR_NOT_CONVERGED", "CD_ERR_TIMEOUT", "CD_ERR_STATE"]
+CD_FP64, CD_FP32 = 0, 1
+CD_CONV_NONE, CD_CONV_GLOBAL_REL, CD_CONV_GLOBAL_SQ, CD_CONV_LOCAL = -1, 0, 1, 2
+
+
+class CDError(RuntimeError):
+    def __init__(self, status, message):
+        super().__init__(f"{STATUS_NAMES[status] if 0 <= status < len(STATUS_NAMES) else status}: {message}")
+        self.status = status
+        self.message = message
+
+
+class cd_params(C.Structure):
+    _fields_ = [
+        ("dim", C.c_int64),
+        ("precision", C.c_int64),
+        ("dt", C.c_double),
+        ("mu", C.c_double),
+        ("gravity", C.c_double * 3),
+        ("box_lo", C.c_double * 3),
+        ("box_hi", C.c_double * 3),
+        ("periodic", C.c_int64 * 3),
+        ("wall_mask", C.c_int64),
+        ("wall_pos", C.c_double * 6),
+        ("wall_vel", C.c_double * 18),
+        ("delta", C.c_double),
+        ("alpha", C.c_double),
+        ("criterion", C.c_int64),
+        ("max_sweeps", C.c_int64),
+        ("warm_start", C.c_int64),
+        ("rotations", C.c_int64),
+        ("seed", C.c_uint64),
+        ("max_contacts", C.c_int64),
+    ]
+
+
+class cd_solve_stats(C.Structure):
+    _fields_ = [
+        ("sweeps", C.c_int64),
+        ("converged", C.c_int64),
+        ("residual", C.c_double),
+        ("r_avg", C.c_double),
+        ("n_contacts", C.c_int64),
+        ("n_colours", C.c_int64),
+        ("wall_force", C.c_double * 6),
+    ]
+
+    def as_dict(self):
+        return {"sweeps": int(self.sweeps), "converged": bool(self.converged), "residual": float(self.residual),
+                "r_avg": float(self.r_avg), "n_contacts": int(self.n_contacts), "n_colours": int(self.n_colours),
+                "wall_force": [float(v) for v in self.wall_force]}
+
+
+class cd_step_stats(C.Structure):
+    _fields_ = [
+        ("steps_done", C.c_int64),
+        ("total_sweeps", C.c_int64),
+        ("total_contact_updates", C.c_int64),
+        ("max_sweeps_in_step", C.c_int64),
+        ("n_not_converged", C.c_int64),
+        ("last", cd_solve_stats),
+    ]
+
+    def as_dict(self):
+        return {"steps_done": int(self.steps_done), "total_sweeps": int(self.total_sweeps),
+                "total_contact_updates": int(self.total_contact_updates),
+                "max_sweeps_in_step": int(self.max_sweeps_in_step), "n_not_converged": int(self.n_not_converged),
+                "last": self.last.as_dict()}
+
+
+_lock = threading.Lock()
+_lib = None
+
+# (name, restype, argtypes) of every entry point declared in include/cd_api.h
+_P = C.c_void_p
+SIGNATURES = [
+    ("cd_create_system", C.c_int, [C.POINTER(cd_params), C.c_int64, _P, _P, _P, _P, _P, _P, _P, _P, _P,
+                                   C.POINTER(_P)]),
+    ("cd_workspace_size", C.c_int, [_P, C.POINTER(C.c_size_t)]),
+    ("cd_set_workspace", C.c_int, [_P, _P, C.c_size_t]),
+    ("cd_detect_contacts", C.c_int, [_P, C.POINTER(C.c_int64)]),
+    ("cd_set_contacts", C.c_int, [_P, C.c_int64, _P, _P]),
+    ("cd_solve_contacts", C.c_int, [_P, C.POINTER(cd_solve_stats)]),
+    ("cd_step", C.c_int, [_P, C.c_int64, C.POINTER(cd_step_stats)]),
+    ("cd_get_contacts", C.c_int, [_P, C.POINTER(C.c_int64), _P, _P, _P, _P, _P]),
+    ("cd_get_walls", C.c_int, [_P, C.POINTER(C.c_double)]),
+    ("cd_upload_state", C.c_int, [_P, _P, _P, _P]),
+    ("cd_download_state", C.c_int, [_P, _P, _P, _P]),
+    ("cd_destroy_system", None, [_P]),
+    ("cd_last_error", C.c_char_p, [_P]),
+]
+
+
+def lib():
+    """Loads the CUDA library; raises if it has not been built."""
+    global _lib
+    with _lock:
+        if _lib is None:
+            if not os.path.exists(LIB_PATH):
+                raise RuntimeError(f"CUDA library {LIB_PATH} is missing: run "
+                                   "`python -c 'import __graft_entry__ as g; g.build()'` on a machine with nvcc")
+            L = C.CDLL(LIB_PATH)
+            for name, res, args in SIGNATURES:
+                f = getattr(L, name)
+                f.restype = res
+                f.argtypes = args
+            _lib = L
+    return _lib
+
+
+def _check(sysptr, status, allow=(CD_OK,)):
+    if status in allow:
+        return status
+    msg = lib().cd_last_error(sysptr)
+    raise CDError(status, msg.decode() if msg else "")
+
+
+# --- one-to-one wrappers of the C entry points -------------------------------
+
+def cd_create_system(params: cd_params, n, pos, vel, omega, theta, radius, inv_mass, inv_inertia, f_ext, stream):
+    out = _P()
+    ptr = lambda t: None if t is None else t.data_ptr()
+    st = lib().cd_create_system(C.byref(params), int(n), ptr(pos), ptr(vel), ptr(omega), ptr(theta), ptr(radius),
+                                ptr(inv_mass), ptr(inv_inertia), ptr(f_ext), stream, C.byref(out))
+    _check(None, st)
+    return out
+
+
+def cd_workspace_size(sysptr) -> int:
+    b = C.c_size_t()
+    _check(sysptr, lib().cd_workspace_size(sysptr, C.byref(b)))
+    return int(b.value)
+
+
+def cd_set_workspace(sysptr, buf: torch.Tensor):
+    _check(sysptr, lib().cd_set_workspace(sysptr, buf.data_ptr(), buf.numel() * buf.element_size()))
+
+
+def cd_detect_contacts(sysptr) -> int:
+    nc = C.c_int64()
+    _check(sysptr, lib().cd_detect_contacts(sysptr, C.byref(nc)))
+    return int(nc.value)
+
+
+def cd_set_contacts(sysptr, pairs: torch.Tensor, impulses=None):
+    nc = int(pairs.shape[0])
+    _check(sysptr, lib().cd_set_contacts(sysptr, nc, pairs.data_ptr() if nc else None,
+                                         None if impulses is None else impulses.data_ptr()))
+
+
+def cd_solve_contacts(sysptr) -> dict:
+    st = cd_solve_stats()
+    _check(sysptr, lib().cd_solve_contacts(sysptr, C.byref(st)), allow=(CD_OK, CD_ERR_NOT_CONVERGED))
+    return st.as_dict()
+
+
+def cd_step(sysptr, n_steps: int, stats: bool = True):
+    st = cd_step_stats()
+    _check(sysptr, lib().cd_step(sysptr, int(n_steps), C.byref(st) if stats else None),
+           allow=(CD_OK, CD_ERR_NOT_CONVERGED))
+    return st.as_dict() if stats else None
+
+
+def cd_get_contacts(sysptr, pairs, normal, gap, impulse, colour) -> int:
+    nc = C.c_int64()
+    ptr = lambda t: None if t is None else t.data_ptr()
+    _check(sysptr, lib().cd_get_contacts(sysptr, C.byref(nc), ptr(pairs), ptr(normal), ptr(gap), ptr(impulse),
+                                         ptr(colour)))
+    return int(nc.value)
+
+
+def cd_get_walls(sysptr) -> np.ndarray:
+    out = (C.c_double * 6)()
+    _check(sysptr, lib().cd_get_walls(sysptr, out))
+    return np.array(list(out))
+
+
+def cd_upload_state(sysptr, pos_host, vel_host, omega_host):
+    ptr = lambda a: None if a is None else (a.data_ptr() if isinstance(a, torch.Tensor) else a.ctypes.data)
+    _check(sysptr, lib().cd_upload_state(sysptr, ptr(pos_host), ptr(vel_host), ptr(omega_host)))
+
+
+def cd_download_state(sysptr, pos_host, vel_host, omega_host):
+    ptr = lambda a: None if a is None else (a.data_ptr() if isinstance(a, torch.Tensor) else a.ctypes.data)
+    _check(sysptr, lib().cd_download_state(sysptr, ptr(pos_host), ptr(vel_host), ptr(omega_host)))
+
+
+def cd_destroy_system(sysptr):
+    lib().cd_destroy_system(sysptr)
+
+
+def cd_last_error(sysptr=None) -> str:
+    m = lib().cd_last_error(sysptr)
+    return m.decode() if m else ""
+
+
+# --- convenience object ----------------------------------------------------------
+
+def make_params(wl, precision=CD_FP64, criterion=CD_CONV_GLOBAL_REL, max_contacts=None, warm_start=1, rotations=1,
+                seed=None, max_sweeps=None, alpha=None) -> cd_params:
+    p = cd_params()
+    p.dim = wl.dim
+    p.precision = precision
+    p.dt = wl.dt
+    p.mu = wl.mu
+    for k in range(3):
+        p.gravity[k] = wl.gravity[k]
+        p.box_lo[k] = wl.box_lo[k]
+        p.box_hi[k] = wl.box_hi[k]
+        p.periodic[k] = int(wl.periodic[k])
+    p.wall_mask = int(wl.wall_mask)
+    wp = np.asarray(wl.wall_pos, dtype=np.float64).reshape(6)
+    wv = np.asarray(wl.wall_vel, dtype=np.float64).reshape(18)
+    for k in range(6):
+        p.wall_pos[k] = float(wp[k])
+    for k in range(18):
+        p.wall_vel[k] = float(wv[k])
+    p.delta = wl.delta
+    p.alpha = wl.alpha if alpha is None else alpha
+    p.criterion = criterion
+    p.max_sweeps = wl.max_sweeps if max_sweeps is None else max_sweeps
+    p.warm_start = int(warm_start)
+    p.rotations = int(rotations)
+    p.seed = int(wl.seed if seed is None else seed) & (2**64 - 1)
+    p.max_contacts = int(max_contacts if max_contacts is not None else max(64, 6 * wl.n))
+    return p
+
+
+class CDSystem:
+    """A CD system over torch-owned device tensors (FP64 state, SoA layouts of cd_api.h)."""
+
+    def __init__(self, wl, device="cuda", f_ext=None, stream=None, **param_kw):
+        self.wl = wl
+        self.dim = wl.dim
+        self.n = wl.n
+        self.device = torch.device(device)
+        dd = dict(dtype=torch.float64, device=self.device)
+        self.pos = torch.as_tensor(np.ascontiguousarray(wl.x).reshape(-1), **dd).clone()
+        self.vel = torch.as_tensor(np.ascontiguousarray(wl.v).reshape(-1), **dd).clone()
+        self.omega = torch.as_tensor(np.ascontiguousarray(wl.w).reshape(-1), **dd).clone()
+        self.theta = torch.zeros(self.n, **dd) if wl.dim == 2 else None
+        self.radius = torch.as_tensor(wl.r, **dd).clone()
+        self.inv_mass = torch.as_tensor(wl.inv_m, **dd).clone()
+        self.inv_inertia = torch.as_tensor(wl.inv_I, **dd).clone()
+        self.f_ext = None if f_ext is None else torch.as_tensor(np.asarray(f_ext).reshape(-1), **dd).clone()
+        self.params = make_params(wl, **param_kw)
+        self.pw = 2 if wl.dim == 2 else 4
+        self.stream = stream if stream is not None else torch.cuda.current_stream(self.device)
+        self._h = cd_create_system(self.params, self.n, self.pos, self.vel, self.omega, self.theta, self.radius,
+                                   self.inv_mass, self.inv_inertia, self.f_ext, self.stream.cuda_stream)
+        nbytes = cd_workspace_size(self._h)
+        self.workspace = torch.empty(nbytes + 256, dtype=torch.uint8, device=self.device)
+        off = (-self.workspace.data_ptr()) % 256
+        self._ws_view = self.workspace[off: off + nbytes]
+        cd_set_workspace(self._h, self._ws_view)
+
+    def __del__(self):
+        h = getattr(self, "_h", None)
+        if h:
+            try:
+                cd_destroy_system(h)
+            except Exception:
+                pass
+            self._h = None
+
+    @property
+    def handle(self):
+        return self._h
+
+    def detect_contacts(self) -> int:
+        return cd_detect_contacts(self._h)
+
+    def set_contacts(self, pairs, impulses=None):
+        pairs = torch.as_tensor(np.asarray(pairs, dtype=np.int32).reshape(-1, 2), device=self.device).contiguous()
+        imp = None
+        if impulses is not None:
+            imp = torch.as_tensor(np.asarray(impulses, dtype=np.float64).reshape(-1, self.pw),
+                                  device=self.device).contiguous()
+        cd_set_contacts(self._h, pairs, imp)
+
+    def solve_contacts(self) -> dict:
+        return cd_solve_contacts(self._h)
+
+    def step(self, n_steps=1, stats=True):
+        return cd_step(self._h, n_steps, stats)
+
+    def contacts(self) -> dict:
+        """Current contact set in key order, as numpy arrays."""
+        nc = cd_get_contacts(self._h, None, None, None, None, None)
+        m = max(nc, 1)
+        pairs = torch.empty((m, 2), dtype=torch.int32, device=self.device)
+        normal = torch.empty((m, 3), dtype=torch.float64, device=self.device)
+        gap = torch.empty(m, dtype=torch.float64, device=self.device)
+        imp = torch.empty((m, self.pw), dtype=torch.float64, device=self.device)
+        col = torch.empty(m, dtype=torch.int32, device=self.device)
+        nc = cd_get_contacts(self._h, pairs, normal, gap, imp, col)
+        return {"pairs": pairs[:nc].cpu().numpy(), "normal": normal[:nc].cpu().numpy(), "gap": gap[:nc].cpu().numpy(),
+                "impulse": imp[:nc].cpu().numpy(), "colour": col[:nc].cpu().numpy()}
+
+    def walls(self) -> np.ndarray:
+        return cd_get_walls(self._h)
+
+    def state(self) -> dict:
+        torch.cuda.synchronize(self.device)
+        return {"x": self.pos.cpu().numpy().reshape(self.n, self.dim),
+                "v": self.vel.cpu().numpy().reshape(self.n, self.dim),
+                "w": self.omega.cpu().numpy().reshape(self.n, -1) if self.dim == 3 else self.omega.cpu().numpy(),
+                "theta": None if self.theta is None else self.theta.cpu().numpy()}

@@ -1,0 +1,495 @@
+// cd_api.cu -- host runtime behind the C ABI of include/cd_api.h: the system
+// object, the workspace layout, parameter validation and the order of the
+// kernel launches for detection, colouring, solve and time step.
+#include <cmath>
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "cd_internal.cuh"
+
+struct cd_system {
+    cd_params p;
+    int64_t n;
+    double* pos;
+    double* vel;
+    double* omega;
+    double* theta;
+    const double* radius;
+    const double* inv_m;
+    const double* inv_I;
+    const double* f_ext;
+    cudaStream_t stream;
+    int device;
+    int num_sms;
+    int pw;
+    int sweep_blocks;
+    int colour_blocks;
+    int has_contacts;
+    size_t ws_bytes;
+    void* ws;
+    CdGeom g;
+    CdWork w;
+    std::string err;
+};
+
+static thread_local std::string g_create_err;
+
+static cd_status fail(cd_system* s, cd_status st, const std::string& msg)
+{
+    if (s) s->err = msg; else g_create_err = msg;
+    return st;
+}
+
+static cd_status cuda_fail(cd_system* s, cudaError_t e, const char* where)
+{
+    std::string m = std::string(where) + ": " + cudaGetErrorString(e);
+    return fail(s, CD_ERR_CUDA, m);
+}
+
+#define CD_CUDA(s, call)                                   \
+    do {                                                   \
+        cudaError_t e_ = (call);                           \
+        if (e_ != cudaSuccess) return cuda_fail((s), e_, #call); \
+    } while (0)
+
+// ---------------------------------------------------------------------------
+// Workspace layout: every array 256-byte aligned, in one caller buffer.
+// ---------------------------------------------------------------------------
+struct Layout {
+    size_t off = 0;
+    template <typename T>
+    T* take(char* base, size_t count)
+    {
+        off = (off + 255) & ~(size_t)255;
+        T* p = base ? (T*)(base + off) : nullptr;
+        off += sizeof(T) * (count > 0 ? count : 1);
+        return p;
+    }
+};
+
+static size_t layout(cd_system* s, char* base, CdWork* w)
+{
+    Layout L;
+    const size_t n = (size_t)s->n;
+    const size_t cap = (size_t)s->p.max_contacts;
+    const size_t ncell = (size_t)s->g.ncell[0] * s->g.ncell[1] * s->g.ncell[2];
+    const size_t real = (s->p.precision == CD_FP64) ? 8 : 4;
+    const size_t vrec = (s->p.dim == 2 ? 4 : 8) * real;   // velocity record bytes
+    const size_t nchunk = (cap + CD_CHUNK - 1) / CD_CHUNK;
+    const size_t G = (size_t)(s->sweep_blocks > s->colour_blocks ? s->sweep_blocks : s->colour_blocks) + 1;
+    size_t scan_max = ncell + 1;
+    if (n + 1 > scan_max) scan_max = n + 1;
+    if (CD_KMAX * nchunk > scan_max) scan_max = CD_KMAX * nchunk;
+    CdWork t;
+    t.ctrl = L.take<CdCtrl>(base, 1);
+    t.V = L.take<char>(base, n * vrec);
+    t.S = L.take<char>(base, n * 4 * real);
+    t.cell_of = L.take<int>(base, n);
+    t.cell_cnt = L.take<int>(base, ncell + 1);
+    t.cell_start = L.take<int>(base, ncell + 1);
+    t.cell_fill = L.take<int>(base, ncell);
+    t.cell_pid = L.take<int>(base, n);
+    t.pcnt = L.take<int>(base, n + 1);
+    t.poff = L.take<int>(base, n + 1);
+    t.scan_tmp = L.take<int>(base, cd_scan_tmp_ints((int)scan_max) + 32);
+    t.pairs = L.take<int2>(base, cap);
+    t.pairs_nx = L.take<int2>(base, cap);
+    t.Pk = L.take<double>(base, cap * s->pw);
+    t.Pk_nx = L.take<double>(base, cap * s->pw);
+    t.nrm = L.take<double>(base, cap * 3);
+    t.gap = L.take<double>(base, cap);
+    t.mn = L.take<double>(base, cap);
+    t.mt = L.take<double>(base, cap);
+    t.colour = L.take<int>(base, cap);
+    t.p2c_cnt = L.take<int>(base, n + 1);
+    t.p2c_off = L.take<int>(base, n + 1);
+    t.p2c_fill = L.take<int>(base, n);
+    t.p2c = L.take<int>(base, 2 * cap);
+    t.prio = L.take<unsigned long long>(base, cap);
+    t.round_cnt = L.take<int>(base, 4);
+    t.chunk_cnt = L.take<int>(base, CD_KMAX * nchunk + 1);
+    t.colour_off = L.take<int>(base, CD_KMAX + 1);
+    t.perm = L.take<int>(base, cap);
+    t.c_ab = L.take<int2>(base, cap);
+    t.c_geo = L.take<char>(base, cap * 4 * real);
+    t.c_m = L.take<char>(base, cap * (s->p.dim == 2 ? 1 : 2) * real);
+    t.c_P = L.take<char>(base, cap * (s->p.dim == 2 ? 2 : 4) * real);
+    t.partials = L.take<double>(base, 2 * 3 * G);
+    t.wpart = L.take<double>(base, 6 * G);
+    if (w) *w = t;
+    return (L.off + 255) & ~(size_t)255;
+}
+
+// ---------------------------------------------------------------------------
+// Helpers
+// ---------------------------------------------------------------------------
+__global__ void k_begin_call(CdCtrl* ctrl, int reset_accum)
+{
+    ctrl->skip = 0;
+    ctrl->overflow = 0;
+    ctrl->error = CDE_NONE;
+    if (reset_accum) {
+        ctrl->steps_done = 0;
+        ctrl->total_sweeps = 0;
+        ctrl->total_updates = 0;
+        ctrl->max_sweeps_step = 0;
+        ctrl->n_not_conv = 0;
+    }
+}
+
+__global__ void k_error_gate(CdCtrl* ctrl)
+{
+    if (ctrl->error != CDE_NONE) ctrl->skip = 1;
+}
+
+static cd_status read_ctrl(cd_system* s, CdCtrl* h)
+{
+    CD_CUDA(s, cudaMemcpyAsync(h, s->w.ctrl, sizeof(CdCtrl), cudaMemcpyDeviceToHost, s->stream));
+    CD_CUDA(s, cudaStreamSynchronize(s->stream));
+    return CD_OK;
+}
+
+static cd_status ctrl_status(cd_system* s, const CdCtrl& h)
+{
+    if (h.overflow) {
+        char buf[160];
+        snprintf(buf, sizeof buf, "contact capacity %lld exceeded: %d contacts needed",
+                 (long long)s->p.max_contacts, h.nc_needed);
+        return fail(s, CD_ERR_CAPACITY, buf);
+    }
+    if (h.error == CDE_TIMEOUT) return fail(s, CD_ERR_TIMEOUT, "a bounded device-side wait ran out");
+    if (h.error == CDE_COLOURS) return fail(s, CD_ERR_CAPACITY, "the contact graph needs more than 64 colours");
+    if (h.error == CDE_PER_PARTICLE) return fail(s, CD_ERR_CAPACITY, "a particle has more than 64 contact candidates");
+    return CD_OK;
+}
+
+static void fill_solve_stats(const cd_system* s, const CdCtrl& h, cd_solve_stats* o)
+{
+    o->sweeps = h.sweeps;
+    o->converged = h.converged;
+    o->residual = h.residual;
+    o->r_avg = h.r_avg;
+    o->n_contacts = h.nc;
+    o->n_colours = h.ncolours;
+    for (int k = 0; k < 6; ++k) o->wall_force[k] = h.wall_force[k];
+    (void)s;
+}
+
+static cd_status need_ready(cd_system* s)
+{
+    if (!s) return CD_ERR_INVALID_ARG;
+    if (!s->ws) return fail(s, CD_ERR_OOM, "no workspace set (cd_workspace_size / cd_set_workspace)");
+    CD_CUDA(s, cudaSetDevice(s->device));
+    return CD_OK;
+}
+
+static cd_status launch_detect_chain(cd_system* s)
+{
+    CD_CUDA(s, cd_launch_detect(s->g, s->w, s->pos, s->radius, s->inv_m, s->inv_I, (int)s->p.warm_start, s->pw,
+                                s->stream));
+    CD_CUDA(s, cd_launch_colour(s->g, s->w, s->colour_blocks, (int)s->p.precision, s->pw, s->stream));
+    k_error_gate<<<1, 1, 0, s->stream>>>(s->w.ctrl);
+    CD_CUDA(s, cudaGetLastError());
+    return CD_OK;
+}
+
+static cd_status launch_solve(cd_system* s, int free_flight)
+{
+    CD_CUDA(s, cd_launch_pack(s->g, s->w, s->vel, s->omega, s->radius, s->inv_m, s->inv_I, s->f_ext, free_flight,
+                              (int)s->p.precision, s->stream));
+    CD_CUDA(s, cd_launch_sweep(s->g, s->w, s->sweep_blocks, (int)s->p.precision, (int)s->p.criterion, s->p.alpha,
+                               (int)s->p.max_sweeps, s->pw, s->stream));
+    return CD_OK;
+}
+
+// ---------------------------------------------------------------------------
+// ABI
+// ---------------------------------------------------------------------------
+extern "C" cd_status cd_create_system(const cd_params* params, int64_t n, double* pos, double* vel, double* omega,
+                                      double* theta, const double* radius, const double* inv_mass,
+                                      const double* inv_inertia, const double* f_ext, void* cuda_stream,
+                                      cd_system** out)
+{
+    if (!out) return fail(nullptr, CD_ERR_INVALID_ARG, "out is NULL");
+    *out = nullptr;
+    if (!params) return fail(nullptr, CD_ERR_INVALID_ARG, "params is NULL");
+    const cd_params& p = *params;
+    if (p.dim != 2 && p.dim != 3) return fail(nullptr, CD_ERR_INVALID_ARG, "dim must be 2 or 3");
+    if (p.precision != CD_FP64 && p.precision != CD_FP32) return fail(nullptr, CD_ERR_INVALID_ARG, "bad precision");
+    if (n <= 0 || n + 6 >= (int64_t)0x7fffffff) return fail(nullptr, CD_ERR_INVALID_ARG, "particle count out of range");
+    if (!(p.dt > 0.0) || !std::isfinite(p.dt)) return fail(nullptr, CD_ERR_INVALID_ARG, "dt must be positive");
+    if (!(p.mu >= 0.0) || !std::isfinite(p.mu)) return fail(nullptr, CD_ERR_INVALID_ARG, "mu must be >= 0");
+    if (!(p.delta >= 0.0) || !std::isfinite(p.delta)) return fail(nullptr, CD_ERR_INVALID_ARG, "delta must be >= 0");
+    if (!(p.alpha >= 0.0)) return fail(nullptr, CD_ERR_INVALID_ARG, "alpha must be >= 0");
+    if (p.max_sweeps < 0) return fail(nullptr, CD_ERR_INVALID_ARG, "max_sweeps must be >= 0");
+    if (p.criterion < CD_CONV_NONE || p.criterion > CD_CONV_LOCAL) return fail(nullptr, CD_ERR_INVALID_ARG, "bad criterion");
+    if (p.max_contacts <= 0 || p.max_contacts > (int64_t)0x3fffffff)
+        return fail(nullptr, CD_ERR_INVALID_ARG, "max_contacts out of range");
+    if (!pos || !vel || !omega || !radius || !inv_mass || !inv_inertia)
+        return fail(nullptr, CD_ERR_INVALID_ARG, "a required state array is NULL");
+    for (int k = 0; k < p.dim; ++k) {
+        if (!(p.box_hi[k] > p.box_lo[k]) || !std::isfinite(p.box_hi[k] - p.box_lo[k]))
+            return fail(nullptr, CD_ERR_INVALID_ARG, "box_hi must exceed box_lo on every axis");
+        for (int q = 0; q < 3; ++q)
+            if (!std::isfinite(p.gravity[q])) return fail(nullptr, CD_ERR_INVALID_ARG, "gravity not finite");
+    }
+    for (int k = 0; k < 6; ++k) {
+        if (!((p.wall_mask >> k) & 1)) continue;
+        if ((k >> 1) >= p.dim) return fail(nullptr, CD_ERR_INVALID_ARG, "wall on an axis the dimension lacks");
+        if (p.periodic[k >> 1]) return fail(nullptr, CD_ERR_INVALID_ARG, "wall on a periodic axis");
+        if (!std::isfinite(p.wall_pos[k])) return fail(nullptr, CD_ERR_INVALID_ARG, "wall position not finite");
+    }
+    if (((p.wall_mask & 3) == 3 && !(p.wall_pos[1] > p.wall_pos[0])) ||
+        ((p.wall_mask & 12) == 12 && !(p.wall_pos[3] > p.wall_pos[2])) ||
+        ((p.wall_mask & 48) == 48 && !(p.wall_pos[5] > p.wall_pos[4])))
+        return fail(nullptr, CD_ERR_INVALID_ARG, "opposite walls overlap");
+
+    cd_system* s = new cd_system();
+    s->p = p;
+    s->n = n;
+    s->pos = pos; s->vel = vel; s->omega = omega; s->theta = theta;
+    s->radius = radius; s->inv_m = inv_mass; s->inv_I = inv_inertia; s->f_ext = f_ext;
+    s->stream = (cudaStream_t)cuda_stream;
+    s->pw = (p.dim == 2) ? 2 : 4;
+    cudaError_t e = cudaGetDevice(&s->device);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&s->num_sms, cudaDevAttrMultiProcessorCount, s->device);
+    int coop = 0;
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, s->device);
+    if (e != cudaSuccess) { cuda_fail(nullptr, e, "device query"); delete s; return CD_ERR_CUDA; }
+    if (!coop) { delete s; return fail(nullptr, CD_ERR_CUDA, "device lacks cooperative launch"); }
+
+    // radii and inverse masses: validated on the host once
+    std::vector<double> hr((size_t)n), hm((size_t)n);
+    e = cudaMemcpy(hr.data(), radius, sizeof(double) * (size_t)n, cudaMemcpyDeviceToHost);
+    if (e == cudaSuccess) e = cudaMemcpy(hm.data(), inv_mass, sizeof(double) * (size_t)n, cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) { cuda_fail(nullptr, e, "reading radius/inv_mass"); delete s; return CD_ERR_CUDA; }
+    double rmax = 0.0;
+    for (int64_t i = 0; i < n; ++i) {
+        if (!(hr[(size_t)i] > 0.0) || !std::isfinite(hr[(size_t)i])) {
+            delete s;
+            return fail(nullptr, CD_ERR_INVALID_ARG, "radius must be positive and finite");
+        }
+        if (!(hm[(size_t)i] >= 0.0) || !std::isfinite(hm[(size_t)i])) {
+            delete s;
+            return fail(nullptr, CD_ERR_INVALID_ARG, "inv_mass must be >= 0 and finite");
+        }
+        if (hr[(size_t)i] > rmax) rmax = hr[(size_t)i];
+    }
+
+    CdGeom& g = s->g;
+    memset(&g, 0, sizeof g);
+    g.dim = (int)p.dim;
+    g.n = (int)n;
+    g.cap = (int)p.max_contacts;
+    g.wall_mask = (int)p.wall_mask;
+    g.delta = p.delta;
+    g.dt = p.dt;
+    g.mu = p.mu;
+    g.rotations = (int)p.rotations;
+    g.seed = p.seed;
+    for (int k = 0; k < 18; ++k) g.wall_vel[k] = p.wall_vel[k];
+    const double ell = 2.0 * rmax + p.delta;   // Sec. 3.1: cell side l = 2 r_max + delta
+    double ncell_total = 1.0;
+    for (int k = 0; k < 3; ++k) {
+        g.gravity[k] = p.gravity[k];
+        g.periodic[k] = (k < p.dim) ? (int)p.periodic[k] : 0;
+        if (k < p.dim) {
+            g.lo[k] = p.box_lo[k];
+            g.hi[k] = p.box_hi[k];
+            g.L[k] = p.box_hi[k] - p.box_lo[k];
+            double m = std::floor(g.L[k] / ell);
+            if (m < 1.0) m = 1.0;
+            if (m > 1.0e6) m = 1.0e6;
+            g.ncell[k] = (int)m;
+            g.cs[k] = g.L[k] / m;
+            if (g.periodic[k] && g.ncell[k] < 3) {
+                delete s;
+                return fail(nullptr, CD_ERR_INVALID_ARG, "a periodic axis needs at least 3 cells (box >= 3 l)");
+            }
+        } else {
+            g.lo[k] = 0.0; g.hi[k] = 1.0; g.L[k] = 1.0; g.ncell[k] = 1; g.cs[k] = 1.0;
+        }
+        ncell_total *= g.ncell[k];
+    }
+    if (ncell_total > 2.0e8) { delete s; return fail(nullptr, CD_ERR_INVALID_ARG, "cell grid too large for the box"); }
+    s->sweep_blocks = cd_sweep_max_blocks((int)p.precision, (int)p.dim, s->num_sms);
+    s->colour_blocks = cd_colour_max_blocks(s->num_sms);
+    if (s->sweep_blocks <= 0 || s->colour_blocks <= 0) {
+        delete s;
+        return fail(nullptr, CD_ERR_CUDA, "cooperative kernels do not fit on this device");
+    }
+    *out = s;
+    return CD_OK;
+}
+
+extern "C" cd_status cd_workspace_size(const cd_system* sys, size_t* bytes)
+{
+    if (!sys || !bytes) return CD_ERR_INVALID_ARG;
+    *bytes = layout(const_cast<cd_system*>(sys), nullptr, nullptr);
+    return CD_OK;
+}
+
+extern "C" cd_status cd_set_workspace(cd_system* s, void* dev_ptr, size_t bytes)
+{
+    if (!s) return CD_ERR_INVALID_ARG;
+    size_t need = layout(s, nullptr, nullptr);
+    if (!dev_ptr || bytes < need) return fail(s, CD_ERR_OOM, "workspace missing or smaller than cd_workspace_size()");
+    if (((uintptr_t)dev_ptr & 255) != 0) return fail(s, CD_ERR_INVALID_ARG, "workspace must be 256-byte aligned");
+    CD_CUDA(s, cudaSetDevice(s->device));
+    s->ws = dev_ptr;
+    s->ws_bytes = bytes;
+    layout(s, (char*)dev_ptr, &s->w);
+    CdCtrl h;
+    memset(&h, 0, sizeof h);
+    for (int k = 0; k < 6; ++k) h.wall_pos[k] = s->p.wall_pos[k];
+    CD_CUDA(s, cudaMemcpyAsync(s->w.ctrl, &h, sizeof h, cudaMemcpyHostToDevice, s->stream));
+    CD_CUDA(s, cd_launch_static(s->g, s->w, s->radius, s->inv_m, s->inv_I, (int)s->p.precision, s->stream));
+    CD_CUDA(s, cudaStreamSynchronize(s->stream));
+    s->has_contacts = 0;
+    return CD_OK;
+}
+
+extern "C" cd_status cd_detect_contacts(cd_system* s, int64_t* n_contacts)
+{
+    cd_status st = need_ready(s);
+    if (st != CD_OK) return st;
+    k_begin_call<<<1, 1, 0, s->stream>>>(s->w.ctrl, 0);
+    if ((st = launch_detect_chain(s)) != CD_OK) return st;
+    CdCtrl h;
+    if ((st = read_ctrl(s, &h)) != CD_OK) return st;
+    if (n_contacts) *n_contacts = h.overflow ? h.nc_needed : h.nc;
+    st = ctrl_status(s, h);
+    if (st == CD_OK) s->has_contacts = 1;
+    return st;
+}
+
+extern "C" cd_status cd_set_contacts(cd_system* s, int64_t nc, const int32_t* pairs, const double* impulses)
+{
+    cd_status st = need_ready(s);
+    if (st != CD_OK) return st;
+    if (nc < 0 || nc > s->p.max_contacts) return fail(s, CD_ERR_CAPACITY, "contact list larger than max_contacts");
+    if (nc > 0 && !pairs) return fail(s, CD_ERR_INVALID_ARG, "pairs is NULL");
+    k_begin_call<<<1, 1, 0, s->stream>>>(s->w.ctrl, 0);
+    CD_CUDA(s, cd_launch_set_contacts(s->g, s->w, s->pos, s->radius, s->inv_m, s->inv_I, (int)nc, pairs, impulses,
+                                      s->pw, s->stream));
+    CD_CUDA(s, cd_launch_colour(s->g, s->w, s->colour_blocks, (int)s->p.precision, s->pw, s->stream));
+    k_error_gate<<<1, 1, 0, s->stream>>>(s->w.ctrl);
+    CdCtrl h;
+    if ((st = read_ctrl(s, &h)) != CD_OK) return st;
+    st = ctrl_status(s, h);
+    if (st == CD_OK) s->has_contacts = 1;
+    return st;
+}
+
+extern "C" cd_status cd_solve_contacts(cd_system* s, cd_solve_stats* out)
+{
+    cd_status st = need_ready(s);
+    if (st != CD_OK) return st;
+    if (!s->has_contacts) return fail(s, CD_ERR_STATE, "no contact set: call cd_detect_contacts or cd_set_contacts");
+    k_begin_call<<<1, 1, 0, s->stream>>>(s->w.ctrl, 1);
+    if ((st = launch_solve(s, 0)) != CD_OK) return st;
+    CD_CUDA(s, cd_launch_unpack(s->g, s->w, s->pos, s->vel, s->omega, s->theta, 0, (int)s->p.precision, s->stream));
+    if (!out) return CD_OK;
+    CdCtrl h;
+    if ((st = read_ctrl(s, &h)) != CD_OK) return st;
+    if ((st = ctrl_status(s, h)) != CD_OK) return st;
+    fill_solve_stats(s, h, out);
+    return h.converged ? CD_OK : CD_ERR_NOT_CONVERGED;
+}
+
+extern "C" cd_status cd_step(cd_system* s, int64_t n_steps, cd_step_stats* out)
+{
+    cd_status st = need_ready(s);
+    if (st != CD_OK) return st;
+    if (n_steps < 0) return fail(s, CD_ERR_INVALID_ARG, "n_steps must be >= 0");
+    k_begin_call<<<1, 1, 0, s->stream>>>(s->w.ctrl, 1);
+    for (int64_t i = 0; i < n_steps; ++i) {
+        if ((st = launch_detect_chain(s)) != CD_OK) return st;
+        if ((st = launch_solve(s, 1)) != CD_OK) return st;
+        CD_CUDA(s, cd_launch_unpack(s->g, s->w, s->pos, s->vel, s->omega, s->theta, 1, (int)s->p.precision,
+                                    s->stream));
+    }
+    if (n_steps > 0) s->has_contacts = 1;
+    if (!out) return CD_OK;
+    CdCtrl h;
+    if ((st = read_ctrl(s, &h)) != CD_OK) return st;
+    out->steps_done = h.steps_done;
+    out->total_sweeps = h.total_sweeps;
+    out->total_contact_updates = h.total_updates;
+    out->max_sweeps_in_step = h.max_sweeps_step;
+    out->n_not_converged = h.n_not_conv;
+    fill_solve_stats(s, h, &out->last);
+    if ((st = ctrl_status(s, h)) != CD_OK) return st;
+    return h.n_not_conv ? CD_ERR_NOT_CONVERGED : CD_OK;
+}
+
+extern "C" cd_status cd_get_contacts(cd_system* s, int64_t* n_contacts, int32_t* pairs, double* normal, double* gap,
+                                     double* impulse, int32_t* colour)
+{
+    cd_status st = need_ready(s);
+    if (st != CD_OK) return st;
+    CdCtrl h;
+    if ((st = read_ctrl(s, &h)) != CD_OK) return st;
+    size_t nc = (size_t)h.nc;
+    if (n_contacts) *n_contacts = (int64_t)nc;
+    if (nc == 0) return CD_OK;
+    cudaStream_t q = s->stream;
+    if (pairs) CD_CUDA(s, cudaMemcpyAsync(pairs, s->w.pairs, nc * sizeof(int2), cudaMemcpyDeviceToDevice, q));
+    if (normal) CD_CUDA(s, cudaMemcpyAsync(normal, s->w.nrm, nc * 3 * sizeof(double), cudaMemcpyDeviceToDevice, q));
+    if (gap) CD_CUDA(s, cudaMemcpyAsync(gap, s->w.gap, nc * sizeof(double), cudaMemcpyDeviceToDevice, q));
+    if (impulse)
+        CD_CUDA(s, cudaMemcpyAsync(impulse, s->w.Pk, nc * s->pw * sizeof(double), cudaMemcpyDeviceToDevice, q));
+    if (colour) CD_CUDA(s, cudaMemcpyAsync(colour, s->w.colour, nc * sizeof(int), cudaMemcpyDeviceToDevice, q));
+    CD_CUDA(s, cudaStreamSynchronize(q));
+    return CD_OK;
+}
+
+extern "C" cd_status cd_get_walls(cd_system* s, double* wall_pos_host)
+{
+    cd_status st = need_ready(s);
+    if (st != CD_OK) return st;
+    if (!wall_pos_host) return fail(s, CD_ERR_INVALID_ARG, "wall_pos_host is NULL");
+    CdCtrl h;
+    if ((st = read_ctrl(s, &h)) != CD_OK) return st;
+    for (int k = 0; k < 6; ++k) wall_pos_host[k] = h.wall_pos[k];
+    return CD_OK;
+}
+
+extern "C" cd_status cd_upload_state(cd_system* s, const double* pos_host, const double* vel_host,
+                                     const double* omega_host)
+{
+    if (!s) return CD_ERR_INVALID_ARG;
+    CD_CUDA(s, cudaSetDevice(s->device));
+    size_t nd = (size_t)s->n * (size_t)s->p.dim * sizeof(double);
+    size_t nw = (size_t)s->n * (s->p.dim == 2 ? 1 : 3) * sizeof(double);
+    if (pos_host) CD_CUDA(s, cudaMemcpyAsync(s->pos, pos_host, nd, cudaMemcpyHostToDevice, s->stream));
+    if (vel_host) CD_CUDA(s, cudaMemcpyAsync(s->vel, vel_host, nd, cudaMemcpyHostToDevice, s->stream));
+    if (omega_host) CD_CUDA(s, cudaMemcpyAsync(s->omega, omega_host, nw, cudaMemcpyHostToDevice, s->stream));
+    return CD_OK;
+}
+
+extern "C" cd_status cd_download_state(cd_system* s, double* pos_host, double* vel_host, double* omega_host)
+{
+    if (!s) return CD_ERR_INVALID_ARG;
+    CD_CUDA(s, cudaSetDevice(s->device));
+    size_t nd = (size_t)s->n * (size_t)s->p.dim * sizeof(double);
+    size_t nw = (size_t)s->n * (s->p.dim == 2 ? 1 : 3) * sizeof(double);
+    if (pos_host) CD_CUDA(s, cudaMemcpyAsync(pos_host, s->pos, nd, cudaMemcpyDeviceToHost, s->stream));
+    if (vel_host) CD_CUDA(s, cudaMemcpyAsync(vel_host, s->vel, nd, cudaMemcpyDeviceToHost, s->stream));
+    if (omega_host) CD_CUDA(s, cudaMemcpyAsync(omega_host, s->omega, nw, cudaMemcpyDeviceToHost, s->stream));
+    CD_CUDA(s, cudaStreamSynchronize(s->stream));
+    return CD_OK;
+}
+
+extern "C" void cd_destroy_system(cd_system* s)
+{
+    delete s;
+}
+
+extern "C" const char* cd_last_error(const cd_system* s)
+{
+    return s ? s->err.c_str() : g_create_err.c_str();
+}

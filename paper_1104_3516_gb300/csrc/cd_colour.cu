@@ -1,0 +1,251 @@
+// cd_colour.cu -- colouring of the contact graph and the colour ordering.
+//
+// The paper updates contacts one by one in random order (Sec. 2.1).  On the
+// GPU the same nonlinear Gauss-Seidel runs in a colour order: contacts that
+// share no particle are independent, so one colour class is updated in
+// parallel and every freshly computed impulse is seen by the later colours.
+//
+// Colouring: Jones-Plassmann with priority splitmix64(seed ^ key) (ties by
+// ascending key).  A contact takes the smallest colour not used by any
+// higher-priority neighbour once all of those are coloured; the fixed point
+// equals the greedy colouring in descending priority, so the result does not
+// depend on scheduling.  Walls never conflict.
+//
+// Ordering: stable partition of the key-ordered contacts by colour (chunk
+// histograms, one exclusive scan, a rank within the chunk from warp match
+// masks), then the contact data is gathered into colour order in the sweep's
+// real type.
+#include <type_traits>
+
+#include "cd_internal.cuh"
+
+__global__ void k_p2c_count(CdGeom g, CdWork w)
+{
+    CdCtrl* ctrl = w.ctrl;
+    if (ctrl->skip) return;
+    int nc = ctrl->nc;
+    for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < nc; c += gridDim.x * blockDim.x) {
+        int2 ab = w.pairs[c];
+        atomicAdd(&w.p2c_cnt[ab.x], 1);
+        if (ab.y < g.n) atomicAdd(&w.p2c_cnt[ab.y], 1);
+    }
+}
+
+__global__ void k_p2c_fill(CdGeom g, CdWork w)
+{
+    CdCtrl* ctrl = w.ctrl;
+    if (ctrl->skip) return;
+    int nc = ctrl->nc;
+    for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < nc; c += gridDim.x * blockDim.x) {
+        int2 ab = w.pairs[c];
+        int s = atomicAdd(&w.p2c_fill[ab.x], 1);
+        w.p2c[w.p2c_off[ab.x] + s] = c;
+        if (ab.y < g.n) {
+            s = atomicAdd(&w.p2c_fill[ab.y], 1);
+            w.p2c[w.p2c_off[ab.y] + s] = c;
+        }
+    }
+}
+
+// Persistent cooperative kernel: Jones-Plassmann rounds separated by the
+// bounded grid barrier.  `prio` scratch lives in the chunk buffer (8 bytes per
+// contact is reserved there by the workspace layout).
+__global__ void __launch_bounds__(CD_SWEEP_THREADS) k_jp(CdGeom g, CdWork w, unsigned long long* prio,
+                                                          int* round_cnt)
+{
+    CdCtrl* ctrl = w.ctrl;
+    if (ctrl->skip) return;
+    const int nc = ctrl->nc;
+    const unsigned long long nb = gridDim.x;
+    unsigned long long epoch = 0;
+    const int tid = blockIdx.x * blockDim.x + threadIdx.x;
+    const int stride = gridDim.x * blockDim.x;
+    for (int c = tid; c < nc; c += stride) {
+        int2 ab = w.pairs[c];
+        prio[c] = cd_splitmix64(g.seed ^ cd_key(ab.x, ab.y));
+        w.colour[c] = -1;
+    }
+    if (tid == 0) { round_cnt[0] = 0; round_cnt[1] = 0; round_cnt[2] = 0; ctrl->ncolours = 0; }
+    if (!cd_grid_sync(ctrl, nb, epoch)) return;
+    __shared__ int s_rem;
+    for (int round = 0; round < 1 << 20; ++round) {
+        if (threadIdx.x == 0) s_rem = 0;
+        if (tid == 0) round_cnt[(round + 1) % 3] = 0;
+        __syncthreads();
+        int rem = 0;
+        for (int c = tid; c < nc; c += stride) {
+            if (cd_ld_volatile_int(&w.colour[c]) >= 0) continue;
+            unsigned long long pc = prio[c];
+            int2 ab = w.pairs[c];
+            unsigned long long kc = cd_key(ab.x, ab.y);
+            unsigned long long used = 0ULL;
+            bool ready = true;
+            for (int side = 0; side < 2 && ready; ++side) {
+                int q = side ? ab.y : ab.x;
+                if (q >= g.n) continue;
+                int e = w.p2c_off[q + 1];
+                for (int s = w.p2c_off[q]; s < e; ++s) {
+                    int d = w.p2c[s];
+                    if (d == c) continue;
+                    unsigned long long pd = prio[d];
+                    bool higher = pd > pc;
+                    if (pd == pc) {
+                        int2 dd = w.pairs[d];
+                        higher = cd_key(dd.x, dd.y) < kc;
+                    }
+                    if (!higher) continue;
+                    int cdl = cd_ld_volatile_int(&w.colour[d]);
+                    if (cdl < 0) { ready = false; break; }
+                    used |= 1ULL << cdl;
+                }
+            }
+            if (!ready) { ++rem; continue; }
+            if (used == ~0ULL) {
+                atomicCAS(&ctrl->error, CDE_NONE, CDE_COLOURS);
+                continue;
+            }
+            int col = __ffsll((long long)~used) - 1;
+            *(volatile int*)&w.colour[c] = col;
+            atomicMax(&ctrl->ncolours, col + 1);
+        }
+        if (rem) atomicAdd(&s_rem, rem);
+        __syncthreads();
+        if (threadIdx.x == 0 && s_rem) atomicAdd(&round_cnt[round % 3], s_rem);
+        if (!cd_grid_sync(ctrl, nb, epoch)) return;
+        if (cd_ld_volatile_int(&round_cnt[round % 3]) == 0) break;
+        if (cd_ld_volatile_int(&ctrl->error) != CDE_NONE) break;
+    }
+}
+
+// Per-chunk colour histogram, layout [colour][chunk].
+__global__ void k_chunk_hist(CdWork w, int nchunk)
+{
+    __shared__ int s_cnt[CD_KMAX];
+    CdCtrl* ctrl = w.ctrl;
+    if (ctrl->skip) return;
+    int nc = ctrl->nc;
+    for (int k = threadIdx.x; k < CD_KMAX; k += blockDim.x) s_cnt[k] = 0;
+    __syncthreads();
+    int c = blockIdx.x * CD_CHUNK + threadIdx.x;
+    if (c < nc) {
+        int k = w.colour[c];
+        if (k >= 0 && k < CD_KMAX) atomicAdd(&s_cnt[k], 1);
+    }
+    __syncthreads();
+    for (int k = threadIdx.x; k < CD_KMAX; k += blockDim.x) w.chunk_cnt[k * nchunk + blockIdx.x] = s_cnt[k];
+}
+
+template <int DIM, typename T>
+__global__ void k_colour_scatter(CdGeom g, CdWork w, int nchunk, int pw)
+{
+    __shared__ int s_wcnt[CD_CHUNK / 32][CD_KMAX];
+    CdCtrl* ctrl = w.ctrl;
+    if (ctrl->skip) return;
+    int nc = ctrl->nc;
+    int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    for (int i = threadIdx.x; i < (CD_CHUNK / 32) * CD_KMAX; i += blockDim.x) (&s_wcnt[0][0])[i] = 0;
+    __syncthreads();
+    int c = blockIdx.x * CD_CHUNK + threadIdx.x;
+    int k = (c < nc) ? w.colour[c] : -1;
+    unsigned mask = __match_any_sync(0xffffffffu, k);
+    int rank = __popc(mask & ((1u << lane) - 1u));
+    if (k >= 0 && lane == __ffs(mask) - 1) s_wcnt[wid][k] = __popc(mask);
+    __syncthreads();
+    if (c >= nc || k < 0) return;
+    for (int v = 0; v < wid; ++v) rank += s_wcnt[v][k];
+    int pos = w.chunk_cnt[k * nchunk + blockIdx.x] + rank;
+    w.perm[pos] = c;
+    int2 ab = w.pairs[c];
+    w.c_ab[pos] = ab;
+    double b = __ddiv_rn(w.gap[c], g.dt);
+    if (DIM == 2) {
+        typedef typename std::conditional<sizeof(T) == 8, double4, float4>::type T4;
+        typedef typename std::conditional<sizeof(T) == 8, double2, float2>::type T2;
+        T4 geo;
+        geo.x = (T)w.nrm[3 * c];
+        geo.y = (T)w.nrm[3 * c + 1];
+        geo.z = (T)b;
+        geo.w = (T)w.mn[c];
+        ((T4*)w.c_geo)[pos] = geo;
+        ((T*)w.c_m)[pos] = (T)w.mt[c];
+        T2 P;
+        P.x = (T)w.Pk[2 * c];
+        P.y = (T)w.Pk[2 * c + 1];
+        ((T2*)w.c_P)[pos] = P;
+    } else {
+        typedef typename std::conditional<sizeof(T) == 8, double4, float4>::type T4;
+        typedef typename std::conditional<sizeof(T) == 8, double2, float2>::type T2;
+        T4 geo;
+        geo.x = (T)w.nrm[3 * c];
+        geo.y = (T)w.nrm[3 * c + 1];
+        geo.z = (T)w.nrm[3 * c + 2];
+        geo.w = (T)b;
+        ((T4*)w.c_geo)[pos] = geo;
+        T2 m;
+        m.x = (T)w.mn[c];
+        m.y = (T)w.mt[c];
+        ((T2*)w.c_m)[pos] = m;
+        T4 P;
+        P.x = (T)w.Pk[4 * c];
+        P.y = (T)w.Pk[4 * c + 1];
+        P.z = (T)w.Pk[4 * c + 2];
+        P.w = (T)w.Pk[4 * c + 3];
+        ((T4*)w.c_P)[pos] = P;
+    }
+}
+
+__global__ void k_colour_offsets(CdWork w, int nchunk)
+{
+    CdCtrl* ctrl = w.ctrl;
+    if (ctrl->skip) return;
+    int k = threadIdx.x;
+    if (k < CD_KMAX) w.colour_off[k] = w.chunk_cnt[k * nchunk];
+    if (k == 0) w.colour_off[CD_KMAX] = ctrl->nc;
+}
+
+int cd_colour_max_blocks(int num_sms)
+{
+    int per_sm = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_jp, CD_SWEEP_THREADS, 0) != cudaSuccess) return 0;
+    if (per_sm > 1) per_sm = 1;   // one block per SM keeps the barrier cheap
+    return per_sm * num_sms;
+}
+
+cudaError_t cd_launch_colour(const CdGeom& g, const CdWork& w, int coop_blocks, int precision, int pw,
+                             cudaStream_t s)
+{
+    cudaError_t e;
+    int nchunk = (g.cap + CD_CHUNK - 1) / CD_CHUNK;
+    if (nchunk < 1) nchunk = 1;
+    int gc = (g.cap + CD_BLOCK - 1) / CD_BLOCK;
+    if (gc < 1) gc = 1;
+    if (gc > 4096) gc = 4096;
+    if ((e = cudaMemsetAsync(w.p2c_cnt, 0, sizeof(int) * (size_t)(g.n + 1), s)) != cudaSuccess) return e;
+    if ((e = cudaMemsetAsync(w.p2c_fill, 0, sizeof(int) * (size_t)g.n, s)) != cudaSuccess) return e;
+    k_p2c_count<<<gc, CD_BLOCK, 0, s>>>(g, w);
+    if ((e = cd_scan_exclusive(w.p2c_cnt, w.p2c_off, g.n + 1, w.scan_tmp, nullptr, s)) != cudaSuccess) return e;
+    k_p2c_fill<<<gc, CD_BLOCK, 0, s>>>(g, w);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    if (coop_blocks > 0) {
+        CdGeom ga = g;
+        CdWork wa = w;
+        unsigned long long* prio = w.prio;
+        int* rc = w.round_cnt;
+        void* args[] = {&ga, &wa, &prio, &rc};
+        if ((e = cudaMemsetAsync(w.ctrl, 0, 2 * sizeof(unsigned long long), s)) != cudaSuccess) return e;
+        e = cudaLaunchCooperativeKernel((const void*)k_jp, dim3(coop_blocks), dim3(CD_SWEEP_THREADS), args, 0, s);
+        if (e != cudaSuccess) return e;
+    }
+    k_chunk_hist<<<nchunk, CD_CHUNK, 0, s>>>(w, nchunk);
+    if ((e = cd_scan_exclusive(w.chunk_cnt, w.chunk_cnt, CD_KMAX * nchunk, w.scan_tmp, nullptr, s)) != cudaSuccess)
+        return e;
+    if (g.dim == 2) {
+        if (precision == CD_FP64) k_colour_scatter<2, double><<<nchunk, CD_CHUNK, 0, s>>>(g, w, nchunk, pw);
+        else k_colour_scatter<2, float><<<nchunk, CD_CHUNK, 0, s>>>(g, w, nchunk, pw);
+    } else {
+        if (precision == CD_FP64) k_colour_scatter<3, double><<<nchunk, CD_CHUNK, 0, s>>>(g, w, nchunk, pw);
+        else k_colour_scatter<3, float><<<nchunk, CD_CHUNK, 0, s>>>(g, w, nchunk, pw);
+    }
+    k_colour_offsets<<<1, CD_KMAX, 0, s>>>(w, nchunk);
+    return cudaGetLastError();
+}

@@ -1,0 +1,509 @@
+// cd_detect.cu -- contact detection with a cell list (paper Sec. 3.2) and the
+// per-contact geometry (Sec. 2.1, Fig. 1; pair mass matrix of Eq. 5).
+//
+// Pipeline (all on one stream, sizes read from the control block so nothing
+// is synchronised with the host):
+//   cell_count -> scan -> cell_fill          counting sort of particles by cell
+//   pair_count -> scan -> capacity check     contacts per particle a (b > a)
+//   pair_emit                                keys (a, b) sorted per a, geometry
+//   warm_match -> commit                     impulses carried over by key
+// The pair test uses the same FP64 operation sequence as the CPU oracle
+// (explicit round-to-nearest intrinsics, no FMA contraction) so the contact
+// set is bit-identical to brute force.
+#include "cd_internal.cuh"
+
+// ---------------------------------------------------------------------------
+// Exclusive scan of int32 (three passes: block sums, scan of the sums, block
+// scans).  `total_dst` (device) receives the sum of all inputs if non-null.
+// ---------------------------------------------------------------------------
+#define SCAN_T 256
+#define SCAN_PER 4
+#define SCAN_TILE (SCAN_T * SCAN_PER)
+
+__device__ __forceinline__ int warp_incl_scan(int v)
+{
+    int lane = threadIdx.x & 31;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        int u = __shfl_up_sync(0xffffffffu, v, o);
+        if (lane >= o) v += u;
+    }
+    return v;
+}
+
+// Block-wide exclusive scan of one value per thread; returns the exclusive
+// prefix and writes the block total to *total.
+__device__ __forceinline__ int block_excl_scan(int v, int* total)
+{
+    __shared__ int warp_sums[SCAN_T / 32];
+    int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    int incl = warp_incl_scan(v);
+    if (lane == 31) warp_sums[wid] = incl;
+    __syncthreads();
+    if (wid == 0) {
+        int s = (lane < SCAN_T / 32) ? warp_sums[lane] : 0;
+        int si = warp_incl_scan(s);
+        if (lane < SCAN_T / 32) warp_sums[lane] = si - s;
+        if (lane == SCAN_T / 32 - 1) *total = si;
+    }
+    __syncthreads();
+    int r = warp_sums[wid] + incl - v;
+    __syncthreads();
+    return r;
+}
+
+__global__ void k_scan_sums(const int* __restrict__ in, int n, int* __restrict__ sums)
+{
+    int base = blockIdx.x * SCAN_TILE;
+    int s = 0;
+#pragma unroll
+    for (int k = 0; k < SCAN_PER; ++k) {
+        int i = base + k * SCAN_T + threadIdx.x;
+        if (i < n) s += in[i];
+    }
+    __shared__ int tot;
+    block_excl_scan(s, &tot);
+    if (threadIdx.x == 0) sums[blockIdx.x] = tot;
+}
+
+__global__ void k_scan_top(int* sums, int nb, int* total_dst)
+{
+    __shared__ int carry_s;
+    if (threadIdx.x == 0) carry_s = 0;
+    __syncthreads();
+    for (int base = 0; base < nb; base += SCAN_T) {
+        int i = base + threadIdx.x;
+        int v = (i < nb) ? sums[i] : 0;
+        __shared__ int tot;
+        int ex = block_excl_scan(v, &tot);
+        int carry = carry_s;
+        if (i < nb) sums[i] = carry + ex;
+        __syncthreads();
+        if (threadIdx.x == 0) carry_s = carry + tot;
+        __syncthreads();
+    }
+    if (threadIdx.x == 0 && total_dst) *total_dst = carry_s;
+}
+
+__global__ void k_scan_apply(const int* in, int n, const int* __restrict__ sums, int* out)
+{
+    int base = blockIdx.x * SCAN_TILE + threadIdx.x * SCAN_PER;
+    int v[SCAN_PER];
+    int s = 0;
+#pragma unroll
+    for (int k = 0; k < SCAN_PER; ++k) {
+        int i = base + k;
+        v[k] = (i < n) ? in[i] : 0;
+        s += v[k];
+    }
+    __shared__ int tot;
+    int ex = block_excl_scan(s, &tot) + sums[blockIdx.x];
+#pragma unroll
+    for (int k = 0; k < SCAN_PER; ++k) {
+        int i = base + k;
+        if (i < n) out[i] = ex;
+        ex += v[k];
+    }
+}
+
+size_t cd_scan_tmp_ints(int n)
+{
+    return (size_t)((n + SCAN_TILE - 1) / SCAN_TILE + 1);
+}
+
+cudaError_t cd_scan_exclusive(const int* in, int* out, int n, int* tmp, int* total_dst, cudaStream_t stream)
+{
+    if (n <= 0) return cudaSuccess;
+    int nb = (n + SCAN_TILE - 1) / SCAN_TILE;
+    k_scan_sums<<<nb, SCAN_T, 0, stream>>>(in, n, tmp);
+    k_scan_top<<<1, SCAN_T, 0, stream>>>(tmp, nb, total_dst);
+    k_scan_apply<<<nb, SCAN_T, 0, stream>>>(in, n, tmp, out);
+    return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
+// Cell list
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ int cell_axis(const CdGeom& g, int k, double x)
+{
+    double q = floor(__ddiv_rn(__dsub_rn(x, g.lo[k]), g.cs[k]));
+    int c = (q < 0.0) ? 0 : (q > (double)(g.ncell[k] - 1) ? g.ncell[k] - 1 : (int)q);
+    return c;
+}
+
+template <int DIM>
+__global__ void k_cell_count(CdGeom g, const double* __restrict__ pos, int* __restrict__ cell_of,
+                             int* __restrict__ cell_cnt, const CdCtrl* ctrl)
+{
+    if (ctrl->skip) return;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < g.n; i += gridDim.x * blockDim.x) {
+        int c0 = cell_axis(g, 0, pos[i * DIM + 0]);
+        int c1 = cell_axis(g, 1, pos[i * DIM + 1]);
+        int c2 = (DIM == 3) ? cell_axis(g, 2, pos[i * DIM + 2]) : 0;
+        int c = (c2 * g.ncell[1] + c1) * g.ncell[0] + c0;
+        cell_of[i] = c;
+        atomicAdd(&cell_cnt[c], 1);
+    }
+}
+
+__global__ void k_cell_fill(int n, const int* __restrict__ cell_of, const int* __restrict__ cell_start,
+                            int* __restrict__ cell_fill, int* __restrict__ cell_pid, const CdCtrl* ctrl)
+{
+    if (ctrl->skip) return;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        int c = cell_of[i];
+        int slot = atomicAdd(&cell_fill[c], 1);
+        cell_pid[cell_start[c] + slot] = i;
+    }
+}
+
+// Separation b - a along axis k with the minimum-image rule (same operations
+// as the oracle).
+__device__ __forceinline__ double sep_axis(const CdGeom& g, int k, double xa, double xb)
+{
+    double d = __dsub_rn(xb, xa);
+    if (g.periodic[k]) {
+        double half = __dmul_rn(0.5, g.L[k]);
+        if (d > half) d = __dsub_rn(d, g.L[k]);
+        else if (d < -half) d = __dadd_rn(d, g.L[k]);
+    }
+    return d;
+}
+
+template <int DIM>
+__device__ __forceinline__ bool pair_touches(const CdGeom& g, const double* xa, double ra, const double* __restrict__ pos,
+                                             const double* __restrict__ radius, int b)
+{
+    double d2 = 0.0;
+#pragma unroll
+    for (int k = 0; k < DIM; ++k) {
+        double d = sep_axis(g, k, xa[k], pos[b * DIM + k]);
+        double dd = __dmul_rn(d, d);
+        d2 = (k == 0) ? dd : __dadd_rn(d2, dd);
+    }
+    double s = __dadd_rn(__dadd_rn(ra, radius[b]), g.delta);
+    return d2 < __dmul_rn(s, s);
+}
+
+__device__ __forceinline__ double wall_gap(const double* xa, double ra, const double* wall_pos, int k)
+{
+    int axis = k >> 1;
+    if ((k & 1) == 0) return __dsub_rn(__dsub_rn(xa[axis], wall_pos[k]), ra);
+    return __dsub_rn(__dsub_rn(wall_pos[k], xa[axis]), ra);
+}
+
+__device__ __forceinline__ bool wall_on(const CdGeom& g, int k)
+{
+    return ((g.wall_mask >> k) & 1) && (k >> 1) < g.dim;
+}
+
+// Visits the candidate partners b > a of particle a in the 3^DIM cells around
+// it; calls f(b) for each b that passes the pair test.
+template <int DIM, typename F>
+__device__ __forceinline__ void for_each_partner(const CdGeom& g, int a, const double* xa, double ra,
+                                                 const double* __restrict__ pos, const double* __restrict__ radius,
+                                                 const int* __restrict__ cell_of, const int* __restrict__ cell_start,
+                                                 const int* __restrict__ cell_pid, F f)
+{
+    int c = cell_of[a];
+    int q0 = c % g.ncell[0];
+    int q1 = (c / g.ncell[0]) % g.ncell[1];
+    int q2 = c / (g.ncell[0] * g.ncell[1]);
+    const int zlo = (DIM == 3) ? -1 : 0, zhi = (DIM == 3) ? 1 : 0;
+    for (int dz = zlo; dz <= zhi; ++dz) {
+        int t2 = q2 + dz;
+        if (DIM == 3) {
+            if (t2 < 0 || t2 >= g.ncell[2]) {
+                if (!g.periodic[2]) continue;
+                t2 = (t2 + g.ncell[2]) % g.ncell[2];
+            }
+        }
+        for (int dy = -1; dy <= 1; ++dy) {
+            int t1 = q1 + dy;
+            if (t1 < 0 || t1 >= g.ncell[1]) {
+                if (!g.periodic[1]) continue;
+                t1 = (t1 + g.ncell[1]) % g.ncell[1];
+            }
+            for (int dx = -1; dx <= 1; ++dx) {
+                int t0 = q0 + dx;
+                if (t0 < 0 || t0 >= g.ncell[0]) {
+                    if (!g.periodic[0]) continue;
+                    t0 = (t0 + g.ncell[0]) % g.ncell[0];
+                }
+                int cc = (t2 * g.ncell[1] + t1) * g.ncell[0] + t0;
+                int e = cell_start[cc + 1];
+                for (int s = cell_start[cc]; s < e; ++s) {
+                    int b = cell_pid[s];
+                    if (b <= a) continue;
+                    if (pair_touches<DIM>(g, xa, ra, pos, radius, b)) f(b);
+                }
+            }
+        }
+    }
+}
+
+template <int DIM>
+__global__ void k_pair_count(CdGeom g, const double* __restrict__ pos, const double* __restrict__ radius,
+                             const int* __restrict__ cell_of, const int* __restrict__ cell_start,
+                             const int* __restrict__ cell_pid, int* __restrict__ pcnt, CdCtrl* ctrl)
+{
+    if (ctrl->skip) return;
+    for (int a = blockIdx.x * blockDim.x + threadIdx.x; a < g.n; a += gridDim.x * blockDim.x) {
+        double xa[3] = {0.0, 0.0, 0.0};
+#pragma unroll
+        for (int k = 0; k < DIM; ++k) xa[k] = pos[a * DIM + k];
+        double ra = radius[a];
+        int cnt = 0;
+        for_each_partner<DIM>(g, a, xa, ra, pos, radius, cell_of, cell_start, cell_pid, [&](int) { ++cnt; });
+        int nw = 0;
+        for (int k = 0; k < 2 * DIM; ++k)
+            if (wall_on(g, k) && wall_gap(xa, ra, ctrl->wall_pos, k) < g.delta) ++nw;
+        if (cnt > CD_MAXLOC) atomicCAS(&ctrl->error, CDE_NONE, CDE_PER_PARTICLE);
+        pcnt[a] = cnt + nw;
+    }
+}
+
+// Capacity check after the scan of the per-particle counts.
+__global__ void k_cap_check(CdCtrl* ctrl, int cap)
+{
+    if (ctrl->skip) return;
+    if (ctrl->nc_needed > cap || ctrl->error != CDE_NONE) {
+        ctrl->overflow = (ctrl->nc_needed > cap) ? 1 : ctrl->overflow;
+        ctrl->skip = 1;
+    }
+}
+
+// Geometry of contact (a, b): normal from a to b, gap, m_n = 1/w_n and
+// m_t = 1/w_t with w_n = 1/m_a + 1/m_b, w_t = w_n + r_a^2/I_a + r_b^2/I_b.
+template <int DIM>
+__device__ __forceinline__ void contact_geometry(const CdGeom& g, int a, int b, const double* __restrict__ pos,
+                                                 const double* __restrict__ radius, const double* __restrict__ inv_m,
+                                                 const double* __restrict__ inv_I, const double* wall_pos,
+                                                 double nv[3], double* gap, double* mn, double* mt)
+{
+    double xa[3] = {0.0, 0.0, 0.0};
+#pragma unroll
+    for (int k = 0; k < DIM; ++k) xa[k] = pos[a * DIM + k];
+    double ra = radius[a];
+    double wa_m = inv_m[a], wa_I = g.rotations ? inv_I[a] : 0.0;
+    double wb_m = 0.0, wb_I = 0.0, rb = 0.0;
+    nv[0] = nv[1] = nv[2] = 0.0;
+    if (b < g.n) {
+        double dv[3] = {0.0, 0.0, 0.0};
+        double d2 = 0.0;
+#pragma unroll
+        for (int k = 0; k < DIM; ++k) {
+            dv[k] = sep_axis(g, k, xa[k], pos[b * DIM + k]);
+            double dd = __dmul_rn(dv[k], dv[k]);
+            d2 = (k == 0) ? dd : __dadd_rn(d2, dd);
+        }
+        double d = __dsqrt_rn(d2);
+        if (d > 0.0) {
+#pragma unroll
+            for (int k = 0; k < DIM; ++k) nv[k] = __ddiv_rn(dv[k], d);
+        } else {
+            nv[0] = 1.0;
+        }
+        rb = radius[b];
+        *gap = __dsub_rn(d, __dadd_rn(ra, rb));
+        wb_m = inv_m[b];
+        wb_I = g.rotations ? inv_I[b] : 0.0;
+    } else {
+        int k = b - g.n;
+        nv[k >> 1] = (k & 1) ? 1.0 : -1.0;
+        *gap = wall_gap(xa, ra, wall_pos, k);
+    }
+    double w_n = __dadd_rn(wa_m, wb_m);
+    double w_t = __dadd_rn(__dadd_rn(w_n, __dmul_rn(__dmul_rn(ra, ra), wa_I)), __dmul_rn(__dmul_rn(rb, rb), wb_I));
+    *mn = (w_n > 0.0) ? __ddiv_rn(1.0, w_n) : 0.0;
+    *mt = (w_t > 0.0) ? __ddiv_rn(1.0, w_t) : 0.0;
+}
+
+template <int DIM>
+__device__ __forceinline__ void store_geometry(const CdWork& w, int c, int a, int b, const double nv[3], double gap,
+                                               double mn, double mt)
+{
+    w.pairs_nx[c] = make_int2(a, b);
+    w.nrm[3 * c + 0] = nv[0];
+    w.nrm[3 * c + 1] = nv[1];
+    w.nrm[3 * c + 2] = nv[2];
+    w.gap[c] = gap;
+    w.mn[c] = mn;
+    w.mt[c] = mt;
+}
+
+template <int DIM>
+__global__ void k_pair_emit(CdGeom g, CdWork w, const double* __restrict__ pos, const double* __restrict__ radius,
+                            const double* __restrict__ inv_m, const double* __restrict__ inv_I)
+{
+    CdCtrl* ctrl = w.ctrl;
+    if (ctrl->skip) return;
+    for (int a = blockIdx.x * blockDim.x + threadIdx.x; a < g.n; a += gridDim.x * blockDim.x) {
+        double xa[3] = {0.0, 0.0, 0.0};
+#pragma unroll
+        for (int k = 0; k < DIM; ++k) xa[k] = pos[a * DIM + k];
+        double ra = radius[a];
+        int found[CD_MAXLOC];
+        int nf = 0;
+        for_each_partner<DIM>(g, a, xa, ra, pos, radius, w.cell_of, w.cell_start, w.cell_pid, [&](int b) {
+            if (nf < CD_MAXLOC) {
+                // insertion into the sorted prefix
+                int j = nf++;
+                while (j > 0 && found[j - 1] > b) { found[j] = found[j - 1]; --j; }
+                found[j] = b;
+            }
+        });
+        int o = w.poff[a];
+        for (int f = 0; f < nf; ++f) {
+            double nv[3], gap, mn, mt;
+            contact_geometry<DIM>(g, a, found[f], pos, radius, inv_m, inv_I, ctrl->wall_pos, nv, &gap, &mn, &mt);
+            store_geometry<DIM>(w, o++, a, found[f], nv, gap, mn, mt);
+        }
+        for (int k = 0; k < 2 * DIM; ++k) {
+            if (wall_on(g, k) && wall_gap(xa, ra, ctrl->wall_pos, k) < g.delta) {
+                double nv[3], gap, mn, mt;
+                contact_geometry<DIM>(g, a, g.n + k, pos, radius, inv_m, inv_I, ctrl->wall_pos, nv, &gap, &mn, &mt);
+                store_geometry<DIM>(w, o++, a, g.n + k, nv, gap, mn, mt);
+            }
+        }
+    }
+}
+
+// Geometry of a caller-supplied contact list (already in pairs_nx).
+template <int DIM>
+__global__ void k_geometry_given(CdGeom g, CdWork w, int nc, const double* __restrict__ pos,
+                                 const double* __restrict__ radius, const double* __restrict__ inv_m,
+                                 const double* __restrict__ inv_I)
+{
+    for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < nc; c += gridDim.x * blockDim.x) {
+        int2 ab = w.pairs_nx[c];
+        double nv[3], gap, mn, mt;
+        contact_geometry<DIM>(g, ab.x, ab.y, pos, radius, inv_m, inv_I, w.ctrl->wall_pos, nv, &gap, &mn, &mt);
+        store_geometry<DIM>(w, c, ab.x, ab.y, nv, gap, mn, mt);
+    }
+}
+
+__global__ void k_copy_pairs(int nc, const int32_t* __restrict__ src, int2* __restrict__ dst, CdCtrl* ctrl)
+{
+    for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < nc; c += gridDim.x * blockDim.x)
+        dst[c] = make_int2(src[2 * c], src[2 * c + 1]);
+    if (blockIdx.x == 0 && threadIdx.x == 0) ctrl->nc_needed = nc;
+}
+
+// Impulses of the new set: matched by key in the current (previous) set; in
+// 3D the old tangential impulse is projected onto the new tangent plane.
+template <int DIM>
+__global__ void k_warm_match(CdWork w, int warm, int pw)
+{
+    CdCtrl* ctrl = w.ctrl;
+    if (ctrl->skip) return;
+    int nnew = ctrl->nc_needed;
+    int nold = ctrl->nc;
+    for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < nnew; c += gridDim.x * blockDim.x) {
+        double out[4] = {0.0, 0.0, 0.0, 0.0};
+        if (warm && nold > 0) {
+            int2 ab = w.pairs_nx[c];
+            unsigned long long key = cd_key(ab.x, ab.y);
+            int lo = 0, hi = nold - 1, o = -1;
+            while (lo <= hi) {
+                int mid = lo + ((hi - lo) >> 1);
+                int2 m = w.pairs[mid];
+                unsigned long long km = cd_key(m.x, m.y);
+                if (km == key) { o = mid; break; }
+                if (km < key) lo = mid + 1; else hi = mid - 1;
+            }
+            if (o >= 0) {
+                if (DIM == 2) {
+                    out[0] = w.Pk[2 * o];
+                    out[1] = w.Pk[2 * o + 1];
+                } else {
+                    const double* q = w.Pk + 4 * o;
+                    double n0 = w.nrm[3 * c], n1 = w.nrm[3 * c + 1], n2 = w.nrm[3 * c + 2];
+                    double tn = __dadd_rn(__dadd_rn(__dmul_rn(q[1], n0), __dmul_rn(q[2], n1)), __dmul_rn(q[3], n2));
+                    out[0] = q[0];
+                    out[1] = __dsub_rn(q[1], __dmul_rn(tn, n0));
+                    out[2] = __dsub_rn(q[2], __dmul_rn(tn, n1));
+                    out[3] = __dsub_rn(q[3], __dmul_rn(tn, n2));
+                }
+            }
+        }
+        for (int k = 0; k < pw; ++k) w.Pk_nx[pw * c + k] = out[k];
+    }
+}
+
+// Caller-given starting impulses (or zeros) for a caller-given list.
+__global__ void k_given_impulses(CdWork w, int nc, const double* __restrict__ imp, int pw)
+{
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < nc * pw; i += gridDim.x * blockDim.x)
+        w.Pk_nx[i] = imp ? imp[i] : 0.0;
+}
+
+__global__ void k_commit(CdWork w, int pw)
+{
+    CdCtrl* ctrl = w.ctrl;
+    if (ctrl->skip) return;
+    int nc = ctrl->nc_needed;
+    for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < nc; c += gridDim.x * blockDim.x) {
+        w.pairs[c] = w.pairs_nx[c];
+        for (int k = 0; k < pw; ++k) w.Pk[pw * c + k] = w.Pk_nx[pw * c + k];
+    }
+}
+
+__global__ void k_set_nc(CdCtrl* ctrl)
+{
+    if (ctrl->skip) return;
+    ctrl->nc = ctrl->nc_needed;
+}
+
+static int grid_for(int n, int per_block = CD_BLOCK)
+{
+    int g = (n + per_block - 1) / per_block;
+    if (g < 1) g = 1;
+    if (g > 4096) g = 4096;
+    return g;
+}
+
+cudaError_t cd_launch_detect(const CdGeom& g, const CdWork& w, const double* pos, const double* radius,
+                             const double* inv_m, const double* inv_I, int warm, int pw, cudaStream_t s)
+{
+    int ncell = g.ncell[0] * g.ncell[1] * g.ncell[2];
+    cudaError_t e;
+    if ((e = cudaMemsetAsync(w.cell_cnt, 0, sizeof(int) * (size_t)(ncell + 1), s)) != cudaSuccess) return e;
+    if ((e = cudaMemsetAsync(w.cell_fill, 0, sizeof(int) * (size_t)ncell, s)) != cudaSuccess) return e;
+    int gb = grid_for(g.n);
+    if (g.dim == 2) k_cell_count<2><<<gb, CD_BLOCK, 0, s>>>(g, pos, w.cell_of, w.cell_cnt, w.ctrl);
+    else k_cell_count<3><<<gb, CD_BLOCK, 0, s>>>(g, pos, w.cell_of, w.cell_cnt, w.ctrl);
+    if ((e = cd_scan_exclusive(w.cell_cnt, w.cell_start, ncell + 1, w.scan_tmp, nullptr, s)) != cudaSuccess) return e;
+    k_cell_fill<<<gb, CD_BLOCK, 0, s>>>(g.n, w.cell_of, w.cell_start, w.cell_fill, w.cell_pid, w.ctrl);
+    if (g.dim == 2)
+        k_pair_count<2><<<gb, CD_BLOCK, 0, s>>>(g, pos, radius, w.cell_of, w.cell_start, w.cell_pid, w.pcnt, w.ctrl);
+    else
+        k_pair_count<3><<<gb, CD_BLOCK, 0, s>>>(g, pos, radius, w.cell_of, w.cell_start, w.cell_pid, w.pcnt, w.ctrl);
+    if ((e = cudaMemsetAsync(w.pcnt + g.n, 0, sizeof(int), s)) != cudaSuccess) return e;
+    if ((e = cd_scan_exclusive(w.pcnt, w.poff, g.n + 1, w.scan_tmp, &w.ctrl->nc_needed, s)) != cudaSuccess) return e;
+    k_cap_check<<<1, 1, 0, s>>>(w.ctrl, g.cap);
+    if (g.dim == 2) k_pair_emit<2><<<gb, CD_BLOCK, 0, s>>>(g, w, pos, radius, inv_m, inv_I);
+    else k_pair_emit<3><<<gb, CD_BLOCK, 0, s>>>(g, w, pos, radius, inv_m, inv_I);
+    int gc = grid_for(g.cap);
+    if (g.dim == 2) k_warm_match<2><<<gc, CD_BLOCK, 0, s>>>(w, warm, pw);
+    else k_warm_match<3><<<gc, CD_BLOCK, 0, s>>>(w, warm, pw);
+    k_commit<<<gc, CD_BLOCK, 0, s>>>(w, pw);
+    k_set_nc<<<1, 1, 0, s>>>(w.ctrl);
+    return cudaGetLastError();
+}
+
+cudaError_t cd_launch_set_contacts(const CdGeom& g, const CdWork& w, const double* pos, const double* radius,
+                                   const double* inv_m, const double* inv_I, int nc, const int32_t* pairs,
+                                   const double* impulses, int pw, cudaStream_t s)
+{
+    int gc = grid_for(nc > 0 ? nc : 1);
+    k_copy_pairs<<<gc, CD_BLOCK, 0, s>>>(nc, pairs, w.pairs_nx, w.ctrl);
+    if (nc > 0) {
+        if (g.dim == 2) k_geometry_given<2><<<gc, CD_BLOCK, 0, s>>>(g, w, nc, pos, radius, inv_m, inv_I);
+        else k_geometry_given<3><<<gc, CD_BLOCK, 0, s>>>(g, w, nc, pos, radius, inv_m, inv_I);
+    }
+    k_given_impulses<<<grid_for(nc * pw > 0 ? nc * pw : 1), CD_BLOCK, 0, s>>>(w, nc, impulses, pw);
+    k_commit<<<gc, CD_BLOCK, 0, s>>>(w, pw);
+    k_set_nc<<<1, 1, 0, s>>>(w.ctrl);
+    return cudaGetLastError();
+}

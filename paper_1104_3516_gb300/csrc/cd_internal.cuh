@@ -1,0 +1,211 @@
+// cd_internal.cuh -- device-side layout and helpers shared by the CUDA
+// translation units of the Contact Dynamics library (not a public header).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "cd_api.h"
+
+#define CD_KMAX 64            // colours the ordering supports (bit mask in the colouring)
+#define CD_MAXLOC 64          // pair candidates one particle may emit
+#define CD_SWEEP_THREADS 512  // threads per block of the persistent kernels
+#define CD_BLOCK 256          // threads per block of the streaming kernels
+#define CD_CHUNK 256          // contacts per chunk of the stable colour partition
+#define CD_WAIT_NS 2000000000ULL  // bound on any device-side wait (2 s)
+
+// Device error codes written into CdCtrl::error.
+enum { CDE_NONE = 0, CDE_TIMEOUT = 1, CDE_COLOURS = 2, CDE_PER_PARTICLE = 3 };
+
+// Control block at the start of the workspace.
+struct CdCtrl {
+    unsigned long long bar_count;   // grid barrier: arrivals (monotone within a launch)
+    unsigned long long bar_epoch;   // grid barrier: released epoch
+    int nc;                         // contacts in the current set
+    int nc_needed;                  // contacts found by the last detection
+    int ncolours;
+    int overflow;                   // 1: capacity exceeded in the current call
+    int error;                      // CDE_* (timeouts, colour overflow)
+    int skip;                       // 1: skip all remaining work of this call
+    int uncoloured;
+    int pad0;
+    long long sweeps;               // last solve
+    long long converged;
+    double residual;
+    double r_avg;
+    double wall_force[6];
+    double wall_pos[6];             // moving wall planes
+    // accumulated over the steps of one cd_step call
+    long long steps_done;
+    long long total_sweeps;
+    long long total_updates;
+    long long max_sweeps_step;
+    long long n_not_conv;
+};
+
+// Pointers into the caller's workspace.
+struct CdWork {
+    CdCtrl* ctrl;
+    // particles
+    void* V;            // packed velocity state (2D: 1 vec4, 3D: 2 vec4 per particle), real type
+    void* S;            // packed static (inv_m, r, r/I, 0), real type
+    int* cell_of;       // n
+    int* cell_cnt;      // ncell + 1
+    int* cell_start;    // ncell + 1
+    int* cell_fill;     // ncell
+    int* cell_pid;      // n
+    int* pcnt;          // n + 1
+    int* poff;          // n + 1
+    int* scan_tmp;      // block sums of the scans
+    // contacts, key order
+    int2* pairs;        // current set
+    int2* pairs_nx;     // set being detected
+    double* Pk;         // impulses of the current set (pw per contact)
+    double* Pk_nx;
+    double* nrm;        // 3 per contact
+    double* gap;
+    double* mn;
+    double* mt;
+    int* colour;
+    // colouring
+    int* p2c_cnt;       // n + 1
+    int* p2c_off;       // n + 1
+    int* p2c_fill;      // n
+    int* p2c;           // 2 * cap
+    unsigned long long* prio;  // cap colouring priorities
+    int* round_cnt;     // 3 counters of the colouring rounds
+    int* chunk_cnt;     // CD_KMAX * nchunk_cap + 1
+    int* colour_off;    // CD_KMAX + 1
+    int* perm;          // colour position -> key index
+    // contacts, colour order (real type)
+    int2* c_ab;
+    void* c_geo;        // 2D: (nx, ny, b, mn)   3D: (nx, ny, nz, b)
+    void* c_m;          // 2D: mt                3D: (mn, mt)
+    void* c_P;          // 2D: (Pn, Pt)          3D: (Pn, Ptx, Pty, Ptz)
+    double* partials;   // 2 * G * 4 reduction partials
+    double* wpart;      // G * 6 wall-force partials
+};
+
+// Geometry of the problem in the form the kernels need.
+struct CdGeom {
+    int dim;
+    int n;
+    int cap;
+    int periodic[3];
+    int wall_mask;
+    int ncell[3];
+    double lo[3];
+    double hi[3];
+    double L[3];
+    double cs[3];       // cell side per axis
+    double delta;
+    double dt;
+    double mu;
+    double gravity[3];
+    double wall_vel[18];
+    int rotations;
+    int pad;
+    unsigned long long seed;
+};
+
+// ---------------------------------------------------------------------------
+// splitmix64 (Steele, Lea and Flood 2014) from its published definition; the
+// colouring priority of contact key k is splitmix64(seed ^ k).
+// ---------------------------------------------------------------------------
+__host__ __device__ __forceinline__ unsigned long long cd_splitmix64(unsigned long long x)
+{
+    unsigned long long z = x + 0x9E3779B97F4A7C15ULL;
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ULL;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBULL;
+    return z ^ (z >> 31);
+}
+
+__host__ __device__ __forceinline__ unsigned long long cd_key(int a, int b)
+{
+    return ((unsigned long long)(unsigned)a << 32) | (unsigned long long)(unsigned)b;
+}
+
+// ---------------------------------------------------------------------------
+// Bounded grid barrier for cooperative launches.  Arrivals are counted in a
+// monotone 64-bit counter; the last arrival of epoch e publishes e.  Waiters
+// spin with an acquire load, a %globaltimer bound (CD_WAIT_NS) and an early
+// exit when another block has flagged an error.  Returns false (all threads
+// of the block) when the wait gave up; the caller must then leave the kernel.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ unsigned long long cd_globaltimer()
+{
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+__device__ __forceinline__ unsigned long long cd_ld_acquire(const unsigned long long* p)
+{
+    unsigned long long v;
+    asm volatile("ld.acquire.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+    return v;
+}
+
+__device__ __forceinline__ int cd_ld_volatile_int(const int* p)
+{
+    return *(volatile const int*)p;
+}
+
+__device__ __forceinline__ bool cd_grid_sync(CdCtrl* ctrl, unsigned long long nblocks, unsigned long long& epoch)
+{
+    __shared__ int s_ok;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        epoch += 1;
+        int ok = 1;
+        __threadfence();
+        unsigned long long arrived = atomicAdd(&ctrl->bar_count, 1ULL) + 1ULL;
+        if (arrived == nblocks * epoch) {
+            __threadfence();
+            asm volatile("st.release.gpu.global.u64 [%0], %1;" :: "l"(&ctrl->bar_epoch), "l"(epoch) : "memory");
+        } else {
+            unsigned long long t0 = cd_globaltimer();
+            unsigned spins = 0;
+            while (cd_ld_acquire(&ctrl->bar_epoch) < epoch) {
+                if ((++spins & 63u) == 0) {
+                    if (cd_ld_volatile_int(&ctrl->error) != CDE_NONE) { ok = 0; break; }
+                    if (cd_globaltimer() - t0 > CD_WAIT_NS) {
+                        atomicCAS(&ctrl->error, CDE_NONE, CDE_TIMEOUT);
+                        ok = 0;
+                        break;
+                    }
+                }
+                __nanosleep(20);
+            }
+        }
+        __threadfence();
+        s_ok = ok;
+    }
+    __syncthreads();
+    return s_ok != 0;
+}
+
+// ---------------------------------------------------------------------------
+// Host-side launchers (defined in the .cu files), all on `stream`.
+// ---------------------------------------------------------------------------
+cudaError_t cd_scan_exclusive(const int* in, int* out, int n, int* tmp, int* total_dst, cudaStream_t stream);
+size_t cd_scan_tmp_ints(int n);
+
+cudaError_t cd_launch_detect(const CdGeom& g, const CdWork& w, const double* pos, const double* radius,
+                             const double* inv_m, const double* inv_I, int warm, int pw, cudaStream_t stream);
+cudaError_t cd_launch_set_contacts(const CdGeom& g, const CdWork& w, const double* pos, const double* radius,
+                                   const double* inv_m, const double* inv_I, int nc, const int32_t* pairs,
+                                   const double* impulses, int pw, cudaStream_t stream);
+cudaError_t cd_launch_colour(const CdGeom& g, const CdWork& w, int coop_blocks, int precision, int pw,
+                             cudaStream_t stream);
+cudaError_t cd_launch_pack(const CdGeom& g, const CdWork& w, const double* vel, const double* omega,
+                           const double* radius, const double* inv_m, const double* inv_I, const double* f_ext,
+                           int free_flight, int precision, cudaStream_t stream);
+cudaError_t cd_launch_sweep(const CdGeom& g, const CdWork& w, int coop_blocks, int precision, int criterion,
+                            double alpha, int max_sweeps, int pw, cudaStream_t stream);
+cudaError_t cd_launch_unpack(const CdGeom& g, const CdWork& w, double* pos, double* vel, double* omega,
+                             double* theta, int integrate, int precision, cudaStream_t stream);
+cudaError_t cd_launch_static(const CdGeom& g, const CdWork& w, const double* radius, const double* inv_m,
+                             const double* inv_I, int precision, cudaStream_t stream);
+int cd_sweep_max_blocks(int precision, int dim, int num_sms);
+int cd_colour_max_blocks(int num_sms);

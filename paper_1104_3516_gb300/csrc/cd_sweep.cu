@@ -1,0 +1,564 @@
+// cd_sweep.cu -- the iterative contact-impulse solve (paper Sec. 2.1, Fig. 2)
+// and the Euler update (Eqs. 1-2).
+//
+// k_sweep is one cooperative persistent launch per solve: it applies the
+// starting impulses, then repeats sweeps over the colour classes (one grid
+// barrier per colour) until the convergence test of Sec. 2.1 passes or the
+// sweep cap is hit.  All blocks compute the residual from the same per-block
+// partial sums in the same order, so they agree on when to stop without any
+// host round trip.
+//
+// Single-contact update (Fig. 2), in impulses P = R dt.  With u the current
+// relative velocity of the contact points (this contact's own impulse
+// included) and M = diag(m_n, m_t) the pair mass matrix (Eq. 5), removing the
+// own impulse gives v_g0 = u - M^-1 P_old, so the sticking impulse of Eq. 5,
+// P = -M (g/dt n + v_g0), reads
+//     P_n* = P_n,old - m_n (g/dt + u_n),   P_t* = P_t,old - m_t u_t.
+// Eq. 3 (gap stays open) is P_n* < 0 -> P = 0; the Coulomb test (Eq. 8) and
+// the sliding solution (Eqs. 9-11: tangential impulse of magnitude mu P_n
+// against the sliding velocity, which for discs and spheres is parallel to
+// P_t*) give P_t = P_t* scaled onto |P_t| <= mu P_n.
+#include <type_traits>
+
+#include "cd_internal.cuh"
+
+template <typename T> struct Vec;
+template <> struct Vec<double> { typedef double4 V4; typedef double2 V2; };
+template <> struct Vec<float> { typedef float4 V4; typedef float2 V2; };
+
+// ---------------------------------------------------------------------------
+// Static per-particle record (inv_m, r, r / I, 0) in the sweep's real type.
+// ---------------------------------------------------------------------------
+template <typename T>
+__global__ void k_static(int n, int rotations, const double* __restrict__ radius, const double* __restrict__ inv_m,
+                         const double* __restrict__ inv_I, typename Vec<T>::V4* __restrict__ S)
+{
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        typename Vec<T>::V4 s;
+        double r = radius[i];
+        s.x = (T)inv_m[i];
+        s.y = (T)r;
+        s.z = rotations ? (T)(r * inv_I[i]) : (T)0;
+        s.w = (T)0;
+        S[i] = s;
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Packs the caller's velocities into the sweep state; with free_flight the
+// explicit external forces of Eq. 1 are applied first (F = m g + f_ext).
+// ---------------------------------------------------------------------------
+template <int DIM, typename T>
+__global__ void k_pack(CdGeom g, CdWork w, const double* __restrict__ vel, const double* __restrict__ omega,
+                       const double* __restrict__ inv_m, const double* __restrict__ f_ext, int free_flight)
+{
+    if (w.ctrl->skip) return;
+    typedef typename Vec<T>::V4 T4;
+    T4* V = (T4*)w.V;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < g.n; i += gridDim.x * blockDim.x) {
+        double v[3] = {0.0, 0.0, 0.0};
+        double im = inv_m[i];
+#pragma unroll
+        for (int k = 0; k < DIM; ++k) {
+            double vk = vel[i * DIM + k];
+            if (free_flight) {
+                double a = (im == 0.0) ? 0.0 : g.gravity[k];
+                if (f_ext) a = __dadd_rn(a, __dmul_rn(f_ext[i * DIM + k], im));
+                vk = __dadd_rn(vk, __dmul_rn(a, g.dt));
+            }
+            v[k] = vk;
+        }
+        if (DIM == 2) {
+            T4 s;
+            s.x = (T)v[0]; s.y = (T)v[1]; s.z = (T)omega[i]; s.w = (T)0;
+            V[i] = s;
+        } else {
+            T4 s, o;
+            s.x = (T)v[0]; s.y = (T)v[1]; s.z = (T)v[2]; s.w = (T)0;
+            o.x = (T)omega[3 * i]; o.y = (T)omega[3 * i + 1]; o.z = (T)omega[3 * i + 2]; o.w = (T)0;
+            V[2 * i] = s;
+            V[2 * i + 1] = o;
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Unpacks the sweep state into the caller's velocities; with integrate the
+// positions (and 2D orientations) follow Eq. 2 and the walls move.
+// ---------------------------------------------------------------------------
+template <int DIM, typename T>
+__global__ void k_unpack(CdGeom g, CdWork w, double* __restrict__ pos, double* __restrict__ vel,
+                         double* __restrict__ omega, double* __restrict__ theta, int integrate)
+{
+    CdCtrl* ctrl = w.ctrl;
+    if (ctrl->skip) return;
+    typedef typename Vec<T>::V4 T4;
+    const T4* V = (const T4*)w.V;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < g.n; i += gridDim.x * blockDim.x) {
+        double v[3], om[3];
+        if (DIM == 2) {
+            T4 s = V[i];
+            v[0] = (double)s.x; v[1] = (double)s.y; v[2] = 0.0;
+            om[0] = (double)s.z;
+        } else {
+            T4 s = V[2 * i], o = V[2 * i + 1];
+            v[0] = (double)s.x; v[1] = (double)s.y; v[2] = (double)s.z;
+            om[0] = (double)o.x; om[1] = (double)o.y; om[2] = (double)o.z;
+        }
+#pragma unroll
+        for (int k = 0; k < DIM; ++k) {
+            vel[i * DIM + k] = v[k];
+            if (integrate) {
+                double xn = __dadd_rn(pos[i * DIM + k], __dmul_rn(v[k], g.dt));
+                if (g.periodic[k]) {
+                    if (xn >= g.hi[k]) xn = __dsub_rn(xn, g.L[k]);
+                    else if (xn < g.lo[k]) xn = __dadd_rn(xn, g.L[k]);
+                }
+                pos[i * DIM + k] = xn;
+            }
+        }
+        if (DIM == 2) {
+            omega[i] = om[0];
+            if (integrate && theta) theta[i] = __dadd_rn(theta[i], __dmul_rn(om[0], g.dt));
+        } else {
+            omega[3 * i] = om[0]; omega[3 * i + 1] = om[1]; omega[3 * i + 2] = om[2];
+        }
+    }
+    if (integrate && blockIdx.x == 0 && threadIdx.x == 0) {
+        for (int k = 0; k < 2 * DIM; ++k)
+            if ((g.wall_mask >> k) & 1)
+                ctrl->wall_pos[k] = __dadd_rn(ctrl->wall_pos[k], __dmul_rn(g.wall_vel[3 * k + (k >> 1)], g.dt));
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Deterministic reductions
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ double warp_sum(double v)
+{
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+// Block sum of NV values per thread (fixed tree); result valid in thread 0.
+template <int NV>
+__device__ __forceinline__ void block_sum(double (&v)[NV], double (*s_red)[NV])
+{
+    int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+#pragma unroll
+    for (int j = 0; j < NV; ++j) v[j] = warp_sum(v[j]);
+    if (lane == 0)
+#pragma unroll
+        for (int j = 0; j < NV; ++j) s_red[wid][j] = v[j];
+    __syncthreads();
+    if (wid == 0) {
+        int nw = blockDim.x >> 5;
+#pragma unroll
+        for (int j = 0; j < NV; ++j) {
+            double x = (lane < nw) ? s_red[lane][j] : 0.0;
+            v[j] = warp_sum(x);
+        }
+    }
+    __syncthreads();
+}
+
+// Sum over blocks of partial field f, identical in every block: lanes of warp
+// 0 stride over the blocks in order, then a fixed butterfly; broadcast.
+__device__ __forceinline__ double grid_total(const double* part, int nblocks, double* s_bcast)
+{
+    if (threadIdx.x < 32) {
+        double x = 0.0;
+        for (int b = threadIdx.x; b < nblocks; b += 32) x += part[b];
+        x = warp_sum(x);
+        if (threadIdx.x == 0) *s_bcast = x;
+    }
+    __syncthreads();
+    double r = *s_bcast;
+    __syncthreads();
+    return r;
+}
+
+// ---------------------------------------------------------------------------
+// Single-contact updates (Fig. 2)
+// ---------------------------------------------------------------------------
+struct UpdOut {
+    double pabs;     // |P| after the update
+    int rel_ok;      // local test (I), relative branch
+    int bad;         // local test (I): fails both branches
+};
+
+template <typename T>
+__device__ __forceinline__ T clampT(T x, T lo, T hi) { return x < lo ? lo : (x > hi ? hi : x); }
+
+template <typename T>
+__device__ __forceinline__ UpdOut update2d(const CdGeom& g, const CdWork& w, int pos, bool apply_only, int crit,
+                                           double alpha, double ravg_prev)
+{
+    typedef typename Vec<T>::V4 T4;
+    typedef typename Vec<T>::V2 T2;
+    T4* V = (T4*)w.V;
+    const T4* S = (const T4*)w.S;
+    int2 ab = w.c_ab[pos];
+    T4 geo = ((const T4*)w.c_geo)[pos];
+    T2 P = ((T2*)w.c_P)[pos];
+    const bool wall = ab.y >= g.n;
+    T4 va = V[ab.x], sa = S[ab.x];
+    T4 vb, sb;
+    if (!wall) {
+        vb = V[ab.y];
+        sb = S[ab.y];
+    } else {
+        int k = ab.y - g.n;
+        vb.x = (T)g.wall_vel[3 * k]; vb.y = (T)g.wall_vel[3 * k + 1]; vb.z = (T)0; vb.w = (T)0;
+        sb.x = (T)0; sb.y = (T)0; sb.z = (T)0; sb.w = (T)0;
+    }
+    const T nx = geo.x, ny = geo.y;
+    T Pn, Pt;
+    if (apply_only) {
+        Pn = (T)0; Pt = (T)0;          // treated as a change from zero to P
+        T dPn = P.x, dPt = P.y;
+        T dPx = dPn * nx - dPt * ny, dPy = dPn * ny + dPt * nx;
+        va.x -= sa.x * dPx; va.y -= sa.x * dPy; va.z -= sa.z * dPt;
+        vb.x += sb.x * dPx; vb.y += sb.x * dPy; vb.z -= sb.z * dPt;
+        V[ab.x] = va;
+        if (!wall) V[ab.y] = vb;
+        UpdOut o;
+        o.pabs = sqrt((double)P.x * (double)P.x + (double)P.y * (double)P.y);
+        o.rel_ok = 0; o.bad = 0;
+        return o;
+    }
+    const T mn = geo.w, b = geo.z;
+    const T mt = ((const T*)w.c_m)[pos];
+    T dvx = vb.x - va.x, dvy = vb.y - va.y;
+    T un = dvx * nx + dvy * ny;
+    T ut = (dvy * nx - dvx * ny) - (sa.y * va.z + sb.y * vb.z);
+    Pn = P.x - mn * (b + un);
+    Pn = Pn > (T)0 ? Pn : (T)0;
+    T lim = (T)g.mu * Pn;
+    Pt = clampT(P.y - mt * ut, -lim, lim);
+    T dPn = Pn - P.x, dPt = Pt - P.y;
+    T dPx = dPn * nx - dPt * ny, dPy = dPn * ny + dPt * nx;
+    va.x -= sa.x * dPx; va.y -= sa.x * dPy; va.z -= sa.z * dPt;
+    vb.x += sb.x * dPx; vb.y += sb.x * dPy; vb.z -= sb.z * dPt;
+    V[ab.x] = va;
+    if (!wall) V[ab.y] = vb;
+    T2 Pnew; Pnew.x = Pn; Pnew.y = Pt;
+    ((T2*)w.c_P)[pos] = Pnew;
+    UpdOut o;
+    double pn = (double)Pn, pt = (double)Pt;
+    o.pabs = sqrt(pn * pn + pt * pt);
+    o.rel_ok = 0; o.bad = 0;
+    if (crit == CD_CONV_LOCAL) {
+        double d0 = (double)dPn, d1 = (double)dPt;
+        double s0 = pn + (double)P.x, s1 = pt + (double)P.y;
+        double d2 = d0 * d0 + d1 * d1, s2 = s0 * s0 + s1 * s1;
+        o.rel_ok = d2 < alpha * s2;
+        o.bad = !o.rel_ok && !(d2 <= alpha * ravg_prev * ravg_prev);
+    }
+    return o;
+}
+
+template <typename T>
+__device__ __forceinline__ UpdOut update3d(const CdGeom& g, const CdWork& w, int pos, bool apply_only, int crit,
+                                           double alpha, double ravg_prev)
+{
+    typedef typename Vec<T>::V4 T4;
+    typedef typename Vec<T>::V2 T2;
+    T4* V = (T4*)w.V;
+    const T4* S = (const T4*)w.S;
+    int2 ab = w.c_ab[pos];
+    T4 geo = ((const T4*)w.c_geo)[pos];   // nx, ny, nz, b
+    T4 P = ((T4*)w.c_P)[pos];              // Pn, Ptx, Pty, Ptz
+    const bool wall = ab.y >= g.n;
+    T4 va = V[2 * ab.x], wa = V[2 * ab.x + 1], sa = S[ab.x];
+    T4 vb, wb, sb;
+    if (!wall) {
+        vb = V[2 * ab.y]; wb = V[2 * ab.y + 1]; sb = S[ab.y];
+    } else {
+        int k = ab.y - g.n;
+        vb.x = (T)g.wall_vel[3 * k]; vb.y = (T)g.wall_vel[3 * k + 1]; vb.z = (T)g.wall_vel[3 * k + 2]; vb.w = (T)0;
+        wb.x = wb.y = wb.z = wb.w = (T)0;
+        sb.x = sb.y = sb.z = sb.w = (T)0;
+    }
+    const T nx = geo.x, ny = geo.y, nz = geo.z;
+    T dPn, dtx, dty, dtz;
+    T Pn, Ptx, Pty, Ptz;
+    if (apply_only) {
+        Pn = P.x; Ptx = P.y; Pty = P.z; Ptz = P.w;
+        dPn = Pn; dtx = Ptx; dty = Pty; dtz = Ptz;
+    } else {
+        const T2 m = ((const T2*)w.c_m)[pos];
+        const T mn = m.x, mt = m.y, b = geo.w;
+        // relative velocity of the contact points: (vb - va) - (ra wa + rb wb) x n
+        T lx = sa.y * wa.x + sb.y * wb.x, ly = sa.y * wa.y + sb.y * wb.y, lz = sa.y * wa.z + sb.y * wb.z;
+        T gx = (vb.x - va.x) - (ly * nz - lz * ny);
+        T gy = (vb.y - va.y) - (lz * nx - lx * nz);
+        T gz = (vb.z - va.z) - (lx * ny - ly * nx);
+        T un = gx * nx + gy * ny + gz * nz;
+        T tx = gx - un * nx, ty = gy - un * ny, tz = gz - un * nz;
+        Pn = P.x - mn * (b + un);
+        Pn = Pn > (T)0 ? Pn : (T)0;
+        Ptx = P.y - mt * tx; Pty = P.z - mt * ty; Ptz = P.w - mt * tz;
+        T lim = (T)g.mu * Pn;
+        T q2 = Ptx * Ptx + Pty * Pty + Ptz * Ptz;
+        if (q2 > lim * lim) {
+            T sc = lim / sqrt(q2);
+            Ptx *= sc; Pty *= sc; Ptz *= sc;
+        }
+        dPn = Pn - P.x; dtx = Ptx - P.y; dty = Pty - P.z; dtz = Ptz - P.w;
+    }
+    T dx = dPn * nx + dtx, dy = dPn * ny + dty, dz = dPn * nz + dtz;
+    // n x dP
+    T cx = ny * dz - nz * dy, cy = nz * dx - nx * dz, cz = nx * dy - ny * dx;
+    va.x -= sa.x * dx; va.y -= sa.x * dy; va.z -= sa.x * dz;
+    wa.x -= sa.z * cx; wa.y -= sa.z * cy; wa.z -= sa.z * cz;
+    vb.x += sb.x * dx; vb.y += sb.x * dy; vb.z += sb.x * dz;
+    wb.x -= sb.z * cx; wb.y -= sb.z * cy; wb.z -= sb.z * cz;
+    V[2 * ab.x] = va; V[2 * ab.x + 1] = wa;
+    if (!wall) { V[2 * ab.y] = vb; V[2 * ab.y + 1] = wb; }
+    UpdOut o;
+    double pn = (double)Pn, px = (double)Ptx, py = (double)Pty, pz = (double)Ptz;
+    o.pabs = sqrt(pn * pn + px * px + py * py + pz * pz);
+    o.rel_ok = 0; o.bad = 0;
+    if (!apply_only) {
+        T4 Pnew; Pnew.x = Pn; Pnew.y = Ptx; Pnew.z = Pty; Pnew.w = Ptz;
+        ((T4*)w.c_P)[pos] = Pnew;
+        if (crit == CD_CONV_LOCAL) {
+            double d0 = (double)dPn, d1 = (double)dtx, d2_ = (double)dty, d3 = (double)dtz;
+            double s0 = pn + (double)P.x, s1 = px + (double)P.y, s2_ = py + (double)P.z, s3 = pz + (double)P.w;
+            double d2 = d0 * d0 + d1 * d1 + d2_ * d2_ + d3 * d3;
+            double s2 = s0 * s0 + s1 * s1 + s2_ * s2_ + s3 * s3;
+            o.rel_ok = d2 < alpha * s2;
+            o.bad = !o.rel_ok && !(d2 <= alpha * ravg_prev * ravg_prev);
+        }
+    }
+    return o;
+}
+
+template <int DIM, typename T>
+__device__ __forceinline__ UpdOut update(const CdGeom& g, const CdWork& w, int pos, bool apply_only, int crit,
+                                         double alpha, double ravg_prev)
+{
+    if (DIM == 2) return update2d<T>(g, w, pos, apply_only, crit, alpha, ravg_prev);
+    return update3d<T>(g, w, pos, apply_only, crit, alpha, ravg_prev);
+}
+
+// ---------------------------------------------------------------------------
+// The persistent sweep kernel
+// ---------------------------------------------------------------------------
+template <int DIM, typename T>
+__global__ void __launch_bounds__(CD_SWEEP_THREADS, 1)
+k_sweep(CdGeom g, CdWork w, int crit, double alpha, int max_sweeps)
+{
+    __shared__ int s_off[CD_KMAX + 1];
+    __shared__ double s_red[CD_SWEEP_THREADS / 32][3];
+    __shared__ double s_bc;
+    CdCtrl* ctrl = w.ctrl;
+    if (ctrl->skip) return;
+    const int nc = ctrl->nc;
+    const int K = ctrl->ncolours;
+    const int nb = gridDim.x;
+    const int tid = blockIdx.x * blockDim.x + threadIdx.x;
+    const int stride = gridDim.x * blockDim.x;
+    unsigned long long epoch = 0;
+    for (int k = threadIdx.x; k <= CD_KMAX; k += blockDim.x) s_off[k] = w.colour_off[k];
+    __syncthreads();
+
+    int sweeps = 0, converged = (nc == 0);
+    double resid = 0.0, ravg = 0.0, ravg_prev = 0.0;
+    if (nc > 0) {
+        // starting impulses, colour by colour
+        double acc[3] = {0.0, 0.0, 0.0};
+        for (int k = 0; k < K; ++k) {
+            for (int p = s_off[k] + tid; p < s_off[k + 1]; p += stride)
+                acc[0] += update<DIM, T>(g, w, p, true, crit, alpha, 0.0).pabs;
+            if (k == K - 1) {
+                block_sum<3>(acc, s_red);
+                if (threadIdx.x == 0) w.partials[blockIdx.x] = acc[0];
+            }
+            if (!cd_grid_sync(ctrl, nb, epoch)) return;
+        }
+        ravg_prev = grid_total(w.partials, nb, &s_bc) / (double)nc;
+        ravg = ravg_prev;
+
+        while (!converged && sweeps < max_sweeps) {
+            const int buf = (sweeps & 1) ? 0 : 1;   // alternate with the buffer of the previous sweep
+            double* part = w.partials + (size_t)buf * 3 * nb;
+            double a3[3] = {0.0, 0.0, 0.0};
+            for (int k = 0; k < K; ++k) {
+                for (int p = s_off[k] + tid; p < s_off[k + 1]; p += stride) {
+                    UpdOut o = update<DIM, T>(g, w, p, false, crit, alpha, ravg_prev);
+                    a3[0] += o.pabs;
+                    a3[1] += (double)o.rel_ok;
+                    a3[2] += (double)o.bad;
+                }
+                if (k == K - 1) {
+                    block_sum<3>(a3, s_red);
+                    if (threadIdx.x == 0) {
+                        part[blockIdx.x] = a3[0];
+                        part[nb + blockIdx.x] = a3[1];
+                        part[2 * nb + blockIdx.x] = a3[2];
+                    }
+                }
+                if (!cd_grid_sync(ctrl, nb, epoch)) return;
+            }
+            ++sweeps;
+            ravg = grid_total(part, nb, &s_bc) / (double)nc;
+            double den = ravg + ravg_prev;
+            if (crit == CD_CONV_GLOBAL_REL) {
+                resid = (den > 0.0) ? fabs(ravg - ravg_prev) / den : 0.0;
+                converged = resid < alpha;
+            } else if (crit == CD_CONV_GLOBAL_SQ) {
+                double q = (den > 0.0) ? (ravg - ravg_prev) / den : 0.0;
+                resid = q * q;
+                converged = resid < alpha;
+            } else if (crit == CD_CONV_LOCAL) {
+                double nrel = grid_total(part + nb, nb, &s_bc);
+                double nbad = grid_total(part + 2 * nb, nb, &s_bc);
+                resid = (double)(nc - (long long)nrel) / (double)nc;
+                converged = (10.0 * nrel >= 9.0 * (double)nc) && nbad == 0.0;
+            } else {
+                resid = (den > 0.0) ? fabs(ravg - ravg_prev) / den : 0.0;
+                converged = 0;
+            }
+            ravg_prev = ravg;
+        }
+    }
+
+    // impulses back to key order (FP64) and wall forces
+    double wsum[6] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0};
+    typedef typename Vec<T>::V4 T4;
+    typedef typename Vec<T>::V2 T2;
+    for (int p = tid; p < nc; p += stride) {
+        int c = w.perm[p];
+        int2 ab = w.c_ab[p];
+        double pn;
+        if (DIM == 2) {
+            T2 P = ((const T2*)w.c_P)[p];
+            pn = (double)P.x;
+            w.Pk[2 * c] = (double)P.x;
+            w.Pk[2 * c + 1] = (double)P.y;
+        } else {
+            T4 P = ((const T4*)w.c_P)[p];
+            pn = (double)P.x;
+            w.Pk[4 * c] = (double)P.x;
+            w.Pk[4 * c + 1] = (double)P.y;
+            w.Pk[4 * c + 2] = (double)P.z;
+            w.Pk[4 * c + 3] = (double)P.w;
+        }
+        if (ab.y >= g.n) {
+            int k = ab.y - g.n;
+#pragma unroll
+            for (int q = 0; q < 6; ++q) if (q == k) wsum[q] += pn;
+        }
+    }
+    {
+        double a[3] = {wsum[0], wsum[1], wsum[2]};
+        block_sum<3>(a, s_red);
+        double b3[3] = {wsum[3], wsum[4], wsum[5]};
+        block_sum<3>(b3, s_red);
+        if (threadIdx.x == 0) {
+            for (int q = 0; q < 3; ++q) w.wpart[q * nb + blockIdx.x] = a[q];
+            for (int q = 0; q < 3; ++q) w.wpart[(3 + q) * nb + blockIdx.x] = b3[q];
+        }
+    }
+    if (!cd_grid_sync(ctrl, nb, epoch)) return;
+    if (blockIdx.x == 0) {
+        double wf[6];
+        for (int q = 0; q < 6; ++q) wf[q] = grid_total(w.wpart + q * nb, nb, &s_bc);
+        if (threadIdx.x == 0) {
+            for (int q = 0; q < 6; ++q) ctrl->wall_force[q] = wf[q] / g.dt;
+            ctrl->sweeps = sweeps;
+            ctrl->converged = converged;
+            ctrl->residual = resid;
+            ctrl->r_avg = ravg;
+            ctrl->steps_done += 1;
+            ctrl->total_sweeps += sweeps;
+            ctrl->total_updates += (long long)sweeps * (long long)nc;
+            if (sweeps > ctrl->max_sweeps_step) ctrl->max_sweeps_step = sweeps;
+            if (!converged) ctrl->n_not_conv += 1;
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Launchers
+// ---------------------------------------------------------------------------
+static int grid_n(int n)
+{
+    int g = (n + CD_BLOCK - 1) / CD_BLOCK;
+    return g < 1 ? 1 : (g > 4096 ? 4096 : g);
+}
+
+cudaError_t cd_launch_static(const CdGeom& g, const CdWork& w, const double* radius, const double* inv_m,
+                             const double* inv_I, int precision, cudaStream_t s)
+{
+    if (precision == CD_FP64)
+        k_static<double><<<grid_n(g.n), CD_BLOCK, 0, s>>>(g.n, g.rotations, radius, inv_m, inv_I, (double4*)w.S);
+    else
+        k_static<float><<<grid_n(g.n), CD_BLOCK, 0, s>>>(g.n, g.rotations, radius, inv_m, inv_I, (float4*)w.S);
+    return cudaGetLastError();
+}
+
+cudaError_t cd_launch_pack(const CdGeom& g, const CdWork& w, const double* vel, const double* omega,
+                           const double* radius, const double* inv_m, const double* inv_I, const double* f_ext,
+                           int free_flight, int precision, cudaStream_t s)
+{
+    (void)radius; (void)inv_I;
+    int gb = grid_n(g.n);
+    if (g.dim == 2) {
+        if (precision == CD_FP64) k_pack<2, double><<<gb, CD_BLOCK, 0, s>>>(g, w, vel, omega, inv_m, f_ext, free_flight);
+        else k_pack<2, float><<<gb, CD_BLOCK, 0, s>>>(g, w, vel, omega, inv_m, f_ext, free_flight);
+    } else {
+        if (precision == CD_FP64) k_pack<3, double><<<gb, CD_BLOCK, 0, s>>>(g, w, vel, omega, inv_m, f_ext, free_flight);
+        else k_pack<3, float><<<gb, CD_BLOCK, 0, s>>>(g, w, vel, omega, inv_m, f_ext, free_flight);
+    }
+    return cudaGetLastError();
+}
+
+cudaError_t cd_launch_unpack(const CdGeom& g, const CdWork& w, double* pos, double* vel, double* omega,
+                             double* theta, int integrate, int precision, cudaStream_t s)
+{
+    int gb = grid_n(g.n);
+    if (g.dim == 2) {
+        if (precision == CD_FP64) k_unpack<2, double><<<gb, CD_BLOCK, 0, s>>>(g, w, pos, vel, omega, theta, integrate);
+        else k_unpack<2, float><<<gb, CD_BLOCK, 0, s>>>(g, w, pos, vel, omega, theta, integrate);
+    } else {
+        if (precision == CD_FP64) k_unpack<3, double><<<gb, CD_BLOCK, 0, s>>>(g, w, pos, vel, omega, theta, integrate);
+        else k_unpack<3, float><<<gb, CD_BLOCK, 0, s>>>(g, w, pos, vel, omega, theta, integrate);
+    }
+    return cudaGetLastError();
+}
+
+static const void* sweep_fn(int dim, int precision)
+{
+    if (dim == 2) return precision == CD_FP64 ? (const void*)k_sweep<2, double> : (const void*)k_sweep<2, float>;
+    return precision == CD_FP64 ? (const void*)k_sweep<3, double> : (const void*)k_sweep<3, float>;
+}
+
+int cd_sweep_max_blocks(int precision, int dim, int num_sms)
+{
+    int per_sm = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, sweep_fn(dim, precision), CD_SWEEP_THREADS, 0) !=
+        cudaSuccess)
+        return 0;
+    if (per_sm > 1) per_sm = 1;
+    return per_sm * num_sms;
+}
+
+cudaError_t cd_launch_sweep(const CdGeom& g, const CdWork& w, int coop_blocks, int precision, int criterion,
+                            double alpha, int max_sweeps, int pw, cudaStream_t s)
+{
+    (void)pw;
+    cudaError_t e = cudaMemsetAsync(w.ctrl, 0, 2 * sizeof(unsigned long long), s);
+    if (e != cudaSuccess) return e;
+    CdGeom ga = g;
+    CdWork wa = w;
+    int crit = criterion;
+    double al = alpha;
+    int ms = max_sweeps;
+    void* args[] = {&ga, &wa, &crit, &al, &ms};
+    return cudaLaunchCooperativeKernel(sweep_fn(g.dim, precision), dim3(coop_blocks), dim3(CD_SWEEP_THREADS), args,
+                                       0, s);
+}

@@ -214,10 +214,12 @@ def dense_biaxial_discs(seed=1106, n=100_000, phi=0.80, mu=0.3, steps=100, wall_
 
 def sphere_gas(seed=1107, n=1_000_000, floor=100.0, phi=0.3, mu=0.5, vsig=0.1, steps=50) -> Workload:
     """Spheres r ~ U[0.8, 1.2], RSA gas at packing fraction 0.3 over a
-    floor x floor base with floor and four side walls, velocities N(0, 0.1)."""
+    floor x floor base with floor and four side walls, velocities N(0, 0.1).
+    The fraction is taken over the region the sphere centres can reach."""
     r = uniform(seed, n, 0.8, 1.2)
     vol = float(np.sum((4.0 / 3.0) * math.pi * r ** 3))
-    height = vol / (floor * floor * phi)
+    # packing fraction over the region the centres can reach (inside the walls)
+    height = vol / ((floor - 2.4) ** 2 * phi) + 2.4
     x = rsa(3, n, r, (0.0, 0.0, 0.0), (floor, floor, height), (0, 0, 0), seed)
     v = normal(seed, 3 * n, vsig).reshape(n, 3)
     wp = np.zeros(6)
@@ -230,20 +232,41 @@ def sphere_gas(seed=1107, n=1_000_000, floor=100.0, phi=0.3, mu=0.5, vsig=0.1, s
                    steps=steps, seed=seed)
 
 
+def jittered_lattice(n, r, width, phi, seed):
+    """Triangular lattice filling a box `width` wide row by row, with the
+    spacing a of packing fraction phi and each site jittered uniformly by up
+    to (a - 2 r_max) / 2 per axis, so no two discs overlap."""
+    rmax = float(r.max())
+    area = float(np.sum(math.pi * r * r))
+    a = math.sqrt(2.0 * area / (n * phi * math.sqrt(3.0)))
+    if a < 2.0 * rmax:
+        raise RuntimeError(f"packing fraction {phi} too high for a jittered lattice")
+    nx = max(1, int(math.floor((width - 2.0 * rmax - 0.5 * a) / a)) + 1)
+    j = np.arange(n)
+    row, col = j // nx, j % nx
+    x = rmax + col * a + 0.5 * a * (row % 2)
+    y = rmax + row * a * math.sqrt(3.0) / 2.0
+    jit = 0.5 * (a - 2.0 * rmax)
+    x = x + uniform(seed, n, -jit, jit, stream=21)
+    y = y + uniform(seed, n, -jit, jit, stream=22)
+    return np.stack([x, y], axis=1)
+
+
 def settling_discs(seed=1109, n=10_000, phi=0.5, mu=0.3, vsig=0.05, steps=200, width=None) -> Workload:
-    """Discs r ~ U[0.8, 1.2] placed by RSA at packing fraction 0.5 in a square
-    box with floor and side walls, initial velocities N(0, vsig), gravity 1."""
+    """Discs r ~ U[0.8, 1.2] on a jittered triangular lattice at packing
+    fraction phi in a square box with floor and side walls, initial
+    velocities N(0, vsig), gravity 1: a loose packing that settles."""
     r = uniform(seed, n, 0.8, 1.2)
     area = float(np.sum(math.pi * r * r))
     L = math.sqrt(area / phi) if width is None else width
-    H = area / (phi * L)
-    x = rsa(2, n, r, (0.0, 0.0), (L, H), (0, 0), seed)
+    x = jittered_lattice(n, r, L, phi, seed)
+    H = float(np.max(x[:, 1] + r)) + 0.5
     v = normal(seed, 2 * n, vsig).reshape(n, 2) if vsig > 0 else None
     wp = np.zeros(6)
     wp[1] = L
-    wp[3] = H + 2.4
+    wp[3] = H
     return _finish("settling_discs_2d", 2, x, r, v=v, mu=mu, gravity=(0.0, -1.0, 0.0), box_lo=(0.0, 0.0, 0.0),
-                   box_hi=(L, H + 2.4, 1.0), periodic=(0, 0, 0), wall_mask=0b0111, wall_pos=wp, steps=steps,
+                   box_hi=(L, H, 1.0), periodic=(0, 0, 0), wall_mask=0b0111, wall_pos=wp, steps=steps,
                    seed=seed)
 
 
@@ -254,8 +277,9 @@ def batch_sizes(seed=1108, n_packings=512, nmin=200, nmax=20000) -> np.ndarray:
 
 
 def batched_settling(seed=1108, n_packings=512, nmin=200, nmax=20000, steps=100):
-    """Independent packings: sizes log-uniform, mu ~ U[0.1, 0.6] each, RSA at
-    packing fraction 0.5 in square boxes, gravity settling."""
+    """Independent packings: sizes log-uniform, mu ~ U[0.1, 0.6] each, loose
+    jittered lattices at packing fraction 0.5 in square boxes, gravity
+    settling."""
     sizes = batch_sizes(seed, n_packings, nmin, nmax)
     mus = uniform(seed, n_packings, 0.1, 0.6, stream=4)
     out = []

@@ -1,0 +1,279 @@
+"""GPU parity: the CUDA path (through the C ABI) against the FP64 oracle on the
+same seeded inputs.
+
+Bars: contact sets, normals and gaps bit-identical; colours identical to the
+oracle's greedy colouring; impulses sweep by sweep within 1e-12 of the
+colour-ordered oracle relative to the impulse scale max|P| (FP64), 1e-4
+(FP32); velocities within the same relative bound of their scale.
+"""
+import math
+
+import numpy as np
+import pytest
+
+import oracle as O
+import oracle_cases as cases
+from gpu_common import gpu_system, impulse_err, needs_gpu, run_pair
+from oracle_adapter import params as oparams
+from oracle_adapter import system as osystem
+from paper_1104_3516_gb300 import workloads as W
+
+pytestmark = [pytest.mark.gpu, needs_gpu]
+
+FP64_TOL = 1e-12
+FP32_TOL = 1e-4
+
+
+def small_cases():
+    return {
+        "dilute_discs": W.dilute_discs(n=1000),
+        "settling_discs": W.settling_discs(n=3000, vsig=0.3),
+        "dense_deposit": W.dense_biaxial_discs(n=5000),
+        "sphere_gas": W.sphere_gas(n=3000, floor=20.0, vsig=0.5),
+    }
+
+
+CASES = small_cases()
+
+
+@pytest.mark.parametrize("name", list(CASES))
+def test_detection_is_bit_exact_against_brute_force(name):
+    wl = CASES[name]
+    g = gpu_system(wl)
+    nc = g.detect_contacts()
+    got = g.contacts()
+    p = oparams(wl)
+    ref = O.detect_brute(p, wl.x, wl.r, np.asarray(wl.wall_pos, dtype=np.float64))
+    assert nc == len(ref) and np.array_equal(got["pairs"], ref)
+    normal, gap, mn, mt = O.contact_geometry(p, wl.x, wl.r, wl.inv_m, wl.inv_I,
+                                             np.asarray(wl.wall_pos, dtype=np.float64), ref)
+    assert np.array_equal(got["normal"], normal)
+    assert np.array_equal(got["gap"], gap)
+
+
+@pytest.mark.parametrize("name", list(CASES))
+def test_colours_equal_oracle_greedy_colouring(name):
+    wl = CASES[name]
+    g = gpu_system(wl)
+    g.detect_contacts()
+    got = g.contacts()
+    colour, K = O.colour_greedy(wl.n, got["pairs"], wl.seed)
+    assert np.array_equal(got["colour"], colour)
+
+
+@pytest.mark.parametrize("name", ["dense_deposit", "settling_discs", "sphere_gas"])
+@pytest.mark.parametrize("k", [1, 2, 7, 40])
+def test_fp64_sweep_by_sweep(name, k):
+    from paper_1104_3516_gb300 import cd
+    wl = CASES[name]
+    g, o, gst, ost = run_pair(wl, criterion=cd.CD_CONV_NONE, max_sweeps=k)
+    c = g.contacts()
+    assert np.array_equal(c["pairs"], o.contacts)
+    assert gst[0]["last"]["sweeps"] == k == ost[0]["sweeps"]
+    assert impulse_err(c["impulse"], o.impulses) <= FP64_TOL
+    s = g.state()
+    vs = max(float(np.abs(o.v).max()), 1e-300)
+    assert float(np.abs(s["v"].reshape(-1) - o.v).max()) <= FP64_TOL * vs
+    ws = max(float(np.abs(o.w).max()), 1e-300)
+    assert float(np.abs(s["w"].reshape(-1) - o.w).max()) <= FP64_TOL * ws
+    assert float(np.abs(s["x"].reshape(-1) - o.x).max()) <= 1e-13 * max(1.0, float(np.abs(o.x).max()))
+
+
+@pytest.mark.parametrize("name", ["dense_deposit", "sphere_gas"])
+@pytest.mark.parametrize("k", [1, 40])
+def test_fp32_sweep_by_sweep(name, k):
+    from paper_1104_3516_gb300 import cd
+    wl = CASES[name]
+    g, o, gst, ost = run_pair(wl, criterion=cd.CD_CONV_NONE, max_sweeps=k, precision=cd.CD_FP32)
+    c = g.contacts()
+    assert np.array_equal(c["pairs"], o.contacts)
+    assert impulse_err(c["impulse"], o.impulses) <= FP32_TOL
+
+
+@pytest.mark.parametrize("crit", ["global_rel", "global_sq", "local"])
+def test_convergence_test_stops_at_the_oracle_sweep(crit):
+    from paper_1104_3516_gb300 import cd
+    c_gpu = {"global_rel": cd.CD_CONV_GLOBAL_REL, "global_sq": cd.CD_CONV_GLOBAL_SQ, "local": cd.CD_CONV_LOCAL}[crit]
+    alpha = {"global_rel": 1e-6, "global_sq": 1e-10, "local": 1e-8}[crit]
+    wl = CASES["dense_deposit"]
+    g, o, gst, ost = run_pair(wl, criterion=c_gpu, max_sweeps=1000, alpha=alpha)
+    assert gst[0]["last"]["sweeps"] == ost[0]["sweeps"]
+    assert gst[0]["last"]["converged"] == ost[0]["converged"]
+    assert impulse_err(g.contacts()["impulse"], o.impulses) <= FP64_TOL
+    assert gst[0]["last"]["r_avg"] == pytest.approx(ost[0]["r_avg"], rel=1e-13)
+
+
+def test_multi_step_warm_started_trajectory():
+    wl = W.settling_discs(n=2000, vsig=0.3, seed=31)
+    g, o, gst, ost = run_pair(wl, steps=8, max_sweeps=300, alpha=1e-8)
+    for a, b in zip(gst, ost):
+        assert a["last"]["sweeps"] == b["sweeps"]
+    c = g.contacts()
+    assert np.array_equal(c["pairs"], o.contacts)
+    assert impulse_err(c["impulse"], o.impulses) <= 1e-11
+    s = g.state()
+    assert float(np.abs(s["x"].reshape(-1) - o.x).max()) <= 1e-12 * float(np.abs(o.x).max())
+    assert np.allclose(g.walls(), o.wall_pos, rtol=0, atol=0)
+
+
+def test_moving_wall_and_wall_force():
+    wl = W.dense_biaxial_discs(n=3000, wall_speed=0.5)
+    g, o, gst, ost = run_pair(wl, steps=3, max_sweeps=500, alpha=1e-9)
+    assert np.array_equal(g.walls(), o.wall_pos)
+    wf_g = np.array(gst[-1]["last"]["wall_force"])
+    wf_o = np.array(ost[-1]["wall_force"])
+    assert np.allclose(wf_g, wf_o, rtol=1e-11, atol=1e-12 * max(1.0, float(np.abs(wf_o).max())))
+
+
+# --- closed forms through the CUDA path ------------------------------------------
+
+def test_gpu_resting_disc_weight():
+    wl = cases.resting_disc()
+    g = gpu_system(wl, alpha=1e-14)
+    g.step(1)
+    P = g.contacts()["impulse"]
+    m = 1.0 / wl.inv_m[0]
+    assert P[0, 0] == pytest.approx(m * cases.G * cases.DT, rel=1e-15)
+
+
+def test_gpu_column_force_chain():
+    n = 6
+    wl = cases.column(n=n)
+    g = gpu_system(wl, alpha=1e-15, max_sweeps=20000)
+    st = g.step(1)
+    assert st["last"]["converged"]
+    c = g.contacts()
+    m = 1.0 / wl.inv_m[0]
+    for (a, b), (pn, pt) in zip(c["pairs"], c["impulse"]):
+        k = n - a if b == n + 2 else n - 1 - a
+        assert pn == pytest.approx(k * m * cases.G * cases.DT, rel=1e-9)
+
+
+@pytest.mark.parametrize("dim", [2, 3])
+def test_gpu_incline_stick_and_slide(dim):
+    mu = 0.4
+    for f, stick in ((0.9, True), (1.1, False)):
+        th = math.atan(f * mu)
+        wl = cases.incline(th, mu, dim=dim, frozen=True)
+        g = gpu_system(wl, alpha=1e-15, max_sweeps=100)
+        g.step(1)
+        P = g.contacts()["impulse"][0]
+        pt = abs(P[1]) if dim == 2 else float(np.linalg.norm(P[1:]))
+        m = 1.0 / wl.inv_m[0]
+        if stick:
+            assert pt == pytest.approx(m * cases.G * math.sin(th) * cases.DT, rel=1e-13)
+        else:
+            assert pt == pytest.approx(mu * P[0], rel=1e-14)
+
+
+def test_gpu_head_on_collision():
+    wl = cases.head_on(2.0, -1.0, r1=1.2, r2=0.8)
+    g = gpu_system(wl, alpha=1e-15, max_sweeps=100)
+    g.step(1)
+    s = g.state()
+    gap = (s["x"][1, 0] - s["x"][0, 0]) - 2.0
+    assert abs(gap) < 1e-13
+    m = 1.0 / wl.inv_m
+    assert float(m @ s["v"][:, 0]) == pytest.approx(float(m @ wl.v[:, 0]), rel=1e-14)
+
+
+# --- converged macroscopic quantities vs the random-sequential oracle -------------
+
+def test_macroscopic_parity_with_random_sequential_order():
+    """Forces of a hyperstatic packing are not unique (Sec. 4.4), so only
+    macroscopic quantities are compared between the GPU colour order and the
+    paper's random sequential order: the floor force of a deposited pile
+    resting on the floor (which also equals its weight once converged), the
+    packing height, and the coordination of force-carrying contacts."""
+    wl = W.dense_biaxial_discs(n=1000)
+    wl.wall_mask = 0b0100           # floor only: the pile carries its own weight
+    g = gpu_system(wl, alpha=1e-10, max_sweeps=200000)
+    gst = g.step(1)
+    o = osystem(wl, alpha=1e-10, max_sweeps=200000, order=O.ORDER_RANDOM)
+    ost = o.step()
+    assert gst["last"]["converged"] and ost["converged"]
+    floor_g, floor_o = gst["last"]["wall_force"][2], ost["wall_force"][2]
+    assert floor_g == pytest.approx(floor_o, rel=1e-6)
+    weight = float(np.sum(1.0 / wl.inv_m))
+    assert floor_g == pytest.approx(weight, rel=1e-4)
+    s = g.state()
+    h_g = float(np.max(s["x"][:, 1] + wl.r))
+    h_o = float(np.max(o.x.reshape(-1, 2)[:, 1] + wl.r))
+    assert h_g == pytest.approx(h_o, rel=1e-6)
+    Pg, Po = g.contacts()["impulse"], o.impulses
+    pairs = g.contacts()["pairs"]
+    inner = pairs[:, 1] < wl.n
+    thr_g = 1e-9 * float(Pg[:, 0].mean())
+    thr_o = 1e-9 * float(Po[:, 0].mean())
+    z_g = 2.0 * np.count_nonzero(Pg[inner, 0] > thr_g) / wl.n
+    z_o = 2.0 * np.count_nonzero(Po[inner, 0] > thr_o) / wl.n
+    assert abs(z_g - z_o) <= 0.02 * z_o
+
+
+# --- edge cases ----------------------------------------------------------------------
+
+def test_no_contacts_gives_zero_sweeps():
+    wl = cases.head_on(1.0, -1.0, gap=5.0)
+    g = gpu_system(wl)
+    st = g.step(1)
+    assert st["last"]["n_contacts"] == 0 and st["last"]["sweeps"] == 0 and st["last"]["converged"]
+    s = g.state()
+    assert np.allclose(s["x"][:, 0], wl.x[:, 0] + wl.v[:, 0] * wl.dt, rtol=0, atol=1e-15)
+
+
+def test_capacity_overflow_reports_needed_and_keeps_state():
+    from paper_1104_3516_gb300 import cd
+    wl = W.dense_biaxial_discs(n=2000)
+    g = gpu_system(wl, max_contacts=100)
+    x0 = g.pos.clone()
+    with pytest.raises(cd.CDError) as e:
+        g.step(3)
+    assert e.value.status == cd.CD_ERR_CAPACITY
+    assert "needed" in str(e.value)
+    assert bool((g.pos == x0).all())
+    with pytest.raises(cd.CDError) as e2:
+        g.detect_contacts()
+    assert e2.value.status == cd.CD_ERR_CAPACITY
+
+
+def test_invalid_radius_is_rejected_before_any_launch():
+    from paper_1104_3516_gb300 import cd
+    wl = cases.column(n=3)
+    wl.r = wl.r.copy()
+    wl.r[1] = -1.0
+    with pytest.raises(cd.CDError) as e:
+        gpu_system(wl)
+    assert e.value.status == cd.CD_ERR_INVALID_ARG
+
+
+def test_solve_before_detection_is_a_state_error():
+    from paper_1104_3516_gb300 import cd
+    g = gpu_system(cases.column(n=3))
+    with pytest.raises(cd.CDError) as e:
+        g.solve_contacts()
+    assert e.value.status == cd.CD_ERR_STATE
+
+
+def test_given_contact_list_and_warm_impulses():
+    """cd_set_contacts + cd_solve_contacts on the oracle's contact list with
+    nonzero starting impulses equals the oracle solve from the same start."""
+    from paper_1104_3516_gb300 import cd
+    wl = W.dense_biaxial_discs(n=2000)
+    p = oparams(wl, criterion=O.CRIT_NONE, max_sweeps=9)
+    wp = np.asarray(wl.wall_pos, dtype=np.float64)
+    pairs = O.detect_cells(p, wl.x, wl.r, wp)
+    normal, gap, mn, mt = O.contact_geometry(p, wl.x, wl.r, wl.inv_m, wl.inv_I, wp, pairs)
+    colour, K = O.colour_greedy(wl.n, pairs, wl.seed)
+    P0 = np.abs(W.normal(5, 2 * len(pairs), 1e-3).reshape(-1, 2))
+    vfree = wl.v.reshape(-1) + np.tile(np.asarray(wl.gravity[:2]) * wl.dt, wl.n)
+    P, v, w, st = O.solve(p, vfree, wl.w, wl.r, wl.inv_m, wl.inv_I, pairs, normal, gap, mn, mt, P0=P0,
+                          colour=colour)
+    wl2 = W.Workload(**{**wl.__dict__})
+    wl2.v = vfree.reshape(-1, 2)
+    g = gpu_system(wl2, criterion=cd.CD_CONV_NONE, max_sweeps=9)
+    g.set_contacts(pairs, P0)
+    gst = g.solve_contacts()
+    assert gst["sweeps"] == 9
+    assert impulse_err(g.contacts()["impulse"], P) <= FP64_TOL
+    s = g.state()
+    assert float(np.abs(s["v"].reshape(-1) - v).max()) <= FP64_TOL * float(np.abs(v).max())
