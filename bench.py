@@ -1,0 +1,345 @@
+#!/usr/bin/env python
+"""Benchmark of the Contact Dynamics hot path on GB300.
+
+A step is one full CD time step (detection, colouring and ordering, free
+flight, persistent colour-sweep impulse solve to the convergence test, Euler
+update) of the dense 2D workload: 100,000 frictional discs, radii U[0.8, 1.2],
+mu = 0.3, a gravity-deposited pile in a periodic-x box of width
+sqrt(sum pi r^2 / 0.80), top wall pushed down at 1e-3, dt = 1e-3, Gauss-Seidel
+until the relative change of the mean impulse is below 1e-6 or 1000 sweeps.
+
+Prints one JSON line.  ``value`` is contact updates per second (sum over the
+timed steps of sweeps x contacts, divided by the device time of those steps,
+measured with CUDA events recorded on the library's stream), aggregated over
+all ranks.  ``--impl reference`` times the FP64 CPU oracle on a bounded
+sample of the same workload instead.
+
+Multi-GPU (torchrun, one rank per GPU): every rank steps its own packing
+(seed offset by rank); no data-path collective; weak scaling.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import platform
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "contact updates/s and CD steps/s at residual 1e-6 (plain vs batched/adjoint)"
+UNIT = "contact updates/s"
+WORKLOAD = "dense_biaxial_discs_2d"
+# algorithmic bytes of one colour sweep: per contact record (ids 8, normal 16,
+# g/dt 8, m_n 8, m_t 8, impulse read 16 + write 16) and per particle (v, w
+# read + write 2 x 24, inv_m, r, r/I 24); FP32 halves the real-valued parts
+BYTES_PER_CONTACT = {"f64": 80, "f32": 44}
+BYTES_PER_PARTICLE = {"f64": 72, "f32": 36}
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--precision", choices=["f64", "f32"], default="f64")
+    ap.add_argument("--n", type=int, default=100_000)
+    ap.add_argument("--max-sweeps", type=int, default=1000)
+    ap.add_argument("--alpha", type=float, default=1e-6)
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-sweeps", type=int, default=30,
+                    help="sweep cap of the oracle's bounded sample step")
+    return ap.parse_args()
+
+
+def workload(args, rank):
+    from paper_1104_3516_gb300 import workloads as W
+    wl = W.dense_biaxial_discs(seed=1106 + rank, n=args.n)
+    wl.max_sweeps = args.max_sweeps
+    wl.alpha = args.alpha
+    return wl
+
+
+def config(args, wl, extra=None):
+    c = {"workload": WORKLOAD, "n_discs": wl.n, "packing_fraction_box": 0.80, "mu": wl.mu, "dt": wl.dt,
+         "gravity": 1.0, "top_wall_speed": 1e-3, "periodic": "x", "criterion": "global |dR_avg|/(R^j+R^j-1)",
+         "alpha": args.alpha, "max_sweeps": args.max_sweeps, "warm_start": True, "order": "colour (JP greedy)",
+         "l2": "flushed (512 MiB write) before every timed step"}
+    if extra:
+        c.update(extra)
+    return c
+
+
+def peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi samples of SM clock and throttle reasons during the timed region."""
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        q = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
+             "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+             "clocks_event_reasons.sw_power_cap")
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), f"--query-gpu={q}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except Exception:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if not self.proc:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.t.join(timeout=2)
+        sm, smax, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 8:
+                continue
+            try:
+                sm.append(float(f[0]))
+                smax = float(f[1])
+            except ValueError:
+                continue
+            for name, val in zip(names, f[4:8]):
+                if val.lower() == "active":
+                    reasons.add(name)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": smax, "samples": len(sm), "reasons": sorted(reasons)}
+
+
+def dist_init(args):
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    if ws > 1:
+        import torch.distributed as dist
+        backend = "nccl" if args.impl == "ours" else "gloo"
+        dist.init_process_group(backend=backend)
+        return dist.get_rank(), ws, int(os.environ.get("LOCAL_RANK", "0"))
+    return 0, 1, 0
+
+
+def reduce_max_sum(vals_max, vals_sum, ws, device):
+    if ws == 1:
+        return vals_max, vals_sum
+    import torch
+    import torch.distributed as dist
+    a = torch.tensor(vals_max, dtype=torch.float64, device=device)
+    b = torch.tensor(vals_sum, dtype=torch.float64, device=device)
+    dist.all_reduce(a, op=dist.ReduceOp.MAX)
+    dist.all_reduce(b, op=dist.ReduceOp.SUM)
+    return a.tolist(), b.tolist()
+
+
+def barrier(ws):
+    if ws > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+# ---------------------------------------------------------------------------
+# CPU oracle timing (reference arm and the cpu_baseline leg)
+# ---------------------------------------------------------------------------
+
+def oracle_steps(wl, steps, sweep_cap):
+    """Times `steps` oracle time steps (random sequential order, the paper's
+    scheme) of the workload with the sweep cap lowered to `sweep_cap`;
+    returns (contact updates, seconds, sweeps, contacts)."""
+    import oracle as O
+    p = O.make_params(dim=wl.dim, dt=wl.dt, mu=wl.mu, gravity=wl.gravity, box_lo=wl.box_lo, box_hi=wl.box_hi,
+                      periodic=wl.periodic, wall_mask=wl.wall_mask, wall_vel=np.asarray(wl.wall_vel).reshape(18),
+                      delta=wl.delta, alpha=wl.alpha, criterion=O.CRIT_GLOBAL_REL, max_sweeps=sweep_cap,
+                      order=O.ORDER_RANDOM, seed=wl.seed)
+    s = O.OracleSystem(p, wl.x, wl.v, wl.w, wl.r, wl.inv_m, wl.inv_I, np.asarray(wl.wall_pos, dtype=np.float64),
+                       cap=6 * wl.n)
+    upd, sweeps = 0, 0
+    t0 = time.perf_counter()
+    for _ in range(steps):
+        st = s.step()
+        upd += st["sweeps"] * s.nc
+        sweeps += st["sweeps"]
+    return upd, time.perf_counter() - t0, sweeps, s.nc
+
+
+def run_reference(args):
+    rank, ws, _ = dist_init(args)
+    if rank != 0:
+        return
+    wl = workload(args, 0)
+    oracle_steps(wl, args.warmup, args.cpu_sweeps) if args.warmup > 0 else None
+    upd, sec, sweeps, nc = oracle_steps(wl, args.steps, args.cpu_sweeps)
+    value = upd / sec
+    sample = (f"{args.steps} oracle time steps of the {wl.n}-disc workload, random sequential order, sweep cap "
+              f"lowered to {args.cpu_sweeps} ({sweeps} sweeps over {nc} contacts)")
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * sec / max(args.steps, 1),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": config(args, wl),
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample,
+                             "cpu": platform.processor() or platform.machine()},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+# ---------------------------------------------------------------------------
+# The CUDA path
+# ---------------------------------------------------------------------------
+
+def run_ours(args):
+    import torch
+    rank, ws, local = dist_init(args)
+    torch.cuda.set_device(local)
+    device = torch.device("cuda", local)
+    from paper_1104_3516_gb300 import cd
+    wl = workload(args, rank)
+    prec = cd.CD_FP64 if args.precision == "f64" else cd.CD_FP32
+    stream = torch.cuda.current_stream(device)
+    sysg = cd.CDSystem(wl, device=device, precision=prec, criterion=cd.CD_CONV_GLOBAL_REL, max_contacts=4 * wl.n,
+                       timing=1, stream=stream)
+    flush = torch.empty(512 << 20, dtype=torch.uint8, device=device)
+
+    for _ in range(args.warmup):
+        flush.zero_()
+        sysg.step(1)
+
+    barrier(ws)
+    torch.cuda.synchronize(device)
+    clocks = ClockSampler(local)
+    clocks.start()
+    wall0 = time.perf_counter()
+    upd = sweeps = launches = not_conv = 0
+    ph = {"detect": 0.0, "colour_order_pack": 0.0, "sweep": 0.0, "integrate": 0.0}
+    sweep_bytes = 0.0
+    ncs, colours = [], []
+    bpc, bpp = BYTES_PER_CONTACT[args.precision], BYTES_PER_PARTICLE[args.precision]
+    for _ in range(args.steps):
+        flush.zero_()
+        st = sysg.step(1)
+        upd += st["total_contact_updates"]
+        sweeps += st["total_sweeps"]
+        launches += st["kernel_launches"]
+        not_conv += st["n_not_converged"]
+        nc = st["last"]["n_contacts"]
+        ncs.append(nc)
+        colours.append(st["last"]["n_colours"])
+        sweep_bytes += st["total_sweeps"] * (nc * bpc + wl.n * bpp)
+        for k in ph:
+            ph[k] += st["phase_ms"][k]
+    torch.cuda.synchronize(device)
+    barrier(ws)
+    wall = time.perf_counter() - wall0
+    clk = clocks.stop()
+
+    dev_ms = sum(ph.values())
+    (dev_ms_max, wall_max), (upd_sum, steps_sum) = reduce_max_sum([dev_ms, wall], [float(upd), float(args.steps)],
+                                                                  ws, device)
+    value = upd_sum / (dev_ms_max / 1e3)
+    steps_per_s = steps_sum / (dev_ms_max / 1e3)
+
+    peak, peak_kind = peaks()
+    achieved = sweep_bytes / (ph["sweep"] / 1e3) / 1e9 if ph["sweep"] > 0 else 0.0
+    roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+                "traffic": None, "kernel": f"k_sweep<2,{'double' if args.precision == 'f64' else 'float'}>",
+                "peak_source": f"{peak_kind} HBM copy bandwidth",
+                "bytes_model": f"per sweep {bpc} B x contacts + {bpp} B x particles",
+                "avg_launch_ms": ph["sweep"] / max(args.steps, 1)}
+
+    e2e = None
+    if not args.no_e2e:
+        e2e = run_e2e(args, sysg, wl, device, ws)
+
+    cpu = None
+    if rank == 0 and not args.no_cpu_baseline:
+        o_upd, o_sec, o_sweeps, o_nc = oracle_steps(wl, 1, args.cpu_sweeps)
+        cpu = {"value": o_upd / o_sec, "unit": UNIT, "cores": 1, "kind": "oracle",
+               "sample": f"1 oracle time step of the same {wl.n}-disc packing, random sequential order, sweep cap "
+                         f"{args.cpu_sweeps} ({o_sweeps} sweeps over {o_nc} contacts, {o_sec:.1f} s)",
+               "cpu": platform.processor() or platform.machine()}
+
+    if rank != 0:
+        return
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": dev_ms_max / max(args.steps, 1), "steps_per_s": steps_per_s,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": args.precision,
+            "data": "synthetic (seeded gravity deposition)",
+            "config": config(args, wl, {"mean_contacts": float(np.mean(ncs)), "mean_colours": float(np.mean(colours)),
+                                        "sweeps_per_step": sweeps / max(args.steps, 1),
+                                        "steps_not_converged": not_conv, "parallelism": f"replicas x{ws}"}),
+            "phase_ms_per_step": {k: v / max(args.steps, 1) for k, v in ph.items()},
+            "wall_s": wall_max, "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
+            "gpu_launches": launches, "clocks": clk}
+    print(json.dumps(line), flush=True)
+
+
+def run_e2e(args, sysg, wl, device, ws):
+    """Same metric through the public API with host buffers: every step
+    uploads (pos, vel, omega) from pinned host memory, steps, and downloads
+    the new state."""
+    import torch
+    from paper_1104_3516_gb300 import cd
+    n, D = wl.n, wl.dim
+    pos_h = torch.empty(n * D, dtype=torch.float64, pin_memory=True)
+    vel_h = torch.empty(n * D, dtype=torch.float64, pin_memory=True)
+    om_h = torch.empty(n, dtype=torch.float64, pin_memory=True)
+    cd.cd_download_state(sysg.handle, pos_h, vel_h, om_h)
+    h2d = d2h = (2 * n * D + n) * 8
+    barrier(ws)
+    torch.cuda.synchronize(device)
+    t0 = time.perf_counter()
+    upd = 0
+    for _ in range(args.steps):
+        cd.cd_upload_state(sysg.handle, pos_h, vel_h, om_h)
+        st = sysg.step(1)
+        upd += st["total_contact_updates"]
+        cd.cd_download_state(sysg.handle, pos_h, vel_h, om_h)
+    sec = time.perf_counter() - t0
+    (sec_max,), (upd_sum,) = reduce_max_sum([sec], [float(upd)], ws, device)
+    return {"value": upd_sum / sec_max, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
+            "steps": args.steps, "api": "cd_upload_state + cd_step + cd_download_state"}
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

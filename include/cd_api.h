@@ -89,6 +89,8 @@ typedef struct {
     int64_t rotations;      /* 0: rotational degrees of freedom frozen */
     uint64_t seed;          /* seeds the colouring priorities */
     int64_t max_contacts;   /* contact capacity of the workspace */
+    int64_t timing;         /* 1: record CUDA events around the phases of each
+                               step on the system's stream (see cd_step_stats) */
 } cd_params;
 
 typedef struct cd_system cd_system;
@@ -109,6 +111,13 @@ typedef struct {
     int64_t total_contact_updates;/* sum over steps of sweeps * contacts */
     int64_t max_sweeps_in_step;
     int64_t n_not_converged;      /* steps that hit the sweep cap */
+    int64_t kernel_launches;      /* kernels this library launched in the call */
+    double phase_ms[4];           /* with params.timing: device time of [0]
+                                     detection, [1] colouring, ordering and the
+                                     free-flight velocities, [2] the persistent
+                                     sweep kernel (the impulse solve), [3] the
+                                     integration, summed over the steps of the
+                                     call (CUDA events on the system's stream) */
     cd_solve_stats last;          /* statistics of the last step */
 } cd_step_stats;
 

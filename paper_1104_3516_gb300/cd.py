@@ -57,6 +57,7 @@ class cd_params(C.Structure):
         ("rotations", C.c_int64),
         ("seed", C.c_uint64),
         ("max_contacts", C.c_int64),
+        ("timing", C.c_int64),
     ]
 
 
@@ -84,6 +85,8 @@ class cd_step_stats(C.Structure):
         ("total_contact_updates", C.c_int64),
         ("max_sweeps_in_step", C.c_int64),
         ("n_not_converged", C.c_int64),
+        ("kernel_launches", C.c_int64),
+        ("phase_ms", C.c_double * 4),
         ("last", cd_solve_stats),
     ]
 
@@ -91,6 +94,9 @@ class cd_step_stats(C.Structure):
         return {"steps_done": int(self.steps_done), "total_sweeps": int(self.total_sweeps),
                 "total_contact_updates": int(self.total_contact_updates),
                 "max_sweeps_in_step": int(self.max_sweeps_in_step), "n_not_converged": int(self.n_not_converged),
+                "kernel_launches": int(self.kernel_launches),
+                "phase_ms": {"detect": float(self.phase_ms[0]), "colour_order_pack": float(self.phase_ms[1]),
+                             "sweep": float(self.phase_ms[2]), "integrate": float(self.phase_ms[3])},
                 "last": self.last.as_dict()}
 
 
@@ -223,7 +229,7 @@ def cd_last_error(sysptr=None) -> str:
 # --- convenience object ----------------------------------------------------------
 
 def make_params(wl, precision=CD_FP64, criterion=CD_CONV_GLOBAL_REL, max_contacts=None, warm_start=1, rotations=1,
-                seed=None, max_sweeps=None, alpha=None) -> cd_params:
+                seed=None, max_sweeps=None, alpha=None, timing=0) -> cd_params:
     p = cd_params()
     p.dim = wl.dim
     p.precision = precision
@@ -249,6 +255,7 @@ def make_params(wl, precision=CD_FP64, criterion=CD_CONV_GLOBAL_REL, max_contact
     p.rotations = int(rotations)
     p.seed = int(wl.seed if seed is None else seed) & (2**64 - 1)
     p.max_contacts = int(max_contacts if max_contacts is not None else max(64, 6 * wl.n))
+    p.timing = int(timing)
     return p
 
 

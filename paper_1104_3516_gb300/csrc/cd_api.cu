@@ -32,6 +32,9 @@ struct cd_system {
     void* ws;
     CdGeom g;
     CdWork w;
+    int launches;                      // kernels launched since the call began
+    std::vector<cudaEvent_t> events;   // phase events (params.timing)
+    size_t ev_used;
     std::string err;
 };
 
@@ -145,6 +148,37 @@ __global__ void k_error_gate(CdCtrl* ctrl)
     if (ctrl->error != CDE_NONE) ctrl->skip = 1;
 }
 
+// Records the next phase event on the system's stream (params.timing).
+static cd_status mark(cd_system* s)
+{
+    if (!s->p.timing) return CD_OK;
+    if (s->ev_used == s->events.size()) {
+        cudaEvent_t e;
+        CD_CUDA(s, cudaEventCreate(&e));
+        s->events.push_back(e);
+    }
+    CD_CUDA(s, cudaEventRecord(s->events[s->ev_used++], s->stream));
+    return CD_OK;
+}
+
+// Sums the recorded phase intervals (5 events per step: before detection,
+// after detection, after colouring + ordering + free flight, after the
+// persistent sweep kernel, after integration).
+static cd_status collect_phases(cd_system* s, double* phase_ms)
+{
+    for (int k = 0; k < 4; ++k) phase_ms[k] = 0.0;
+    if (!s->p.timing) return CD_OK;
+    for (size_t b = 0; b + 5 <= s->ev_used; b += 5) {
+        for (int k = 0; k < 4; ++k) {
+            float ms = 0.0f;
+            CD_CUDA(s, cudaEventElapsedTime(&ms, s->events[b + k], s->events[b + k + 1]));
+            phase_ms[k] += (double)ms;
+        }
+    }
+    s->ev_used = 0;
+    return CD_OK;
+}
+
 static cd_status read_ctrl(cd_system* s, CdCtrl* h)
 {
     CD_CUDA(s, cudaMemcpyAsync(h, s->w.ctrl, sizeof(CdCtrl), cudaMemcpyDeviceToHost, s->stream));
@@ -186,22 +220,27 @@ static cd_status need_ready(cd_system* s)
     return CD_OK;
 }
 
-static cd_status launch_detect_chain(cd_system* s)
+static cd_status launch_detect_chain(cd_system* s, int timed)
 {
+    cd_status st;
     CD_CUDA(s, cd_launch_detect(s->g, s->w, s->pos, s->radius, s->inv_m, s->inv_I, (int)s->p.warm_start, s->pw,
-                                s->stream));
-    CD_CUDA(s, cd_launch_colour(s->g, s->w, s->colour_blocks, (int)s->p.precision, s->pw, s->stream));
+                                s->stream, &s->launches));
+    if (timed && (st = mark(s)) != CD_OK) return st;
+    CD_CUDA(s, cd_launch_colour(s->g, s->w, s->colour_blocks, (int)s->p.precision, s->pw, s->stream, &s->launches));
     k_error_gate<<<1, 1, 0, s->stream>>>(s->w.ctrl);
+    ++s->launches;
     CD_CUDA(s, cudaGetLastError());
     return CD_OK;
 }
 
-static cd_status launch_solve(cd_system* s, int free_flight)
+static cd_status launch_solve(cd_system* s, int free_flight, int timed)
 {
+    cd_status st;
     CD_CUDA(s, cd_launch_pack(s->g, s->w, s->vel, s->omega, s->radius, s->inv_m, s->inv_I, s->f_ext, free_flight,
-                              (int)s->p.precision, s->stream));
+                              (int)s->p.precision, s->stream, &s->launches));
+    if (timed && (st = mark(s)) != CD_OK) return st;
     CD_CUDA(s, cd_launch_sweep(s->g, s->w, s->sweep_blocks, (int)s->p.precision, (int)s->p.criterion, s->p.alpha,
-                               (int)s->p.max_sweeps, s->pw, s->stream));
+                               (int)s->p.max_sweeps, s->pw, s->stream, &s->launches));
     return CD_OK;
 }
 
@@ -346,7 +385,8 @@ extern "C" cd_status cd_set_workspace(cd_system* s, void* dev_ptr, size_t bytes)
     memset(&h, 0, sizeof h);
     for (int k = 0; k < 6; ++k) h.wall_pos[k] = s->p.wall_pos[k];
     CD_CUDA(s, cudaMemcpyAsync(s->w.ctrl, &h, sizeof h, cudaMemcpyHostToDevice, s->stream));
-    CD_CUDA(s, cd_launch_static(s->g, s->w, s->radius, s->inv_m, s->inv_I, (int)s->p.precision, s->stream));
+    CD_CUDA(s, cd_launch_static(s->g, s->w, s->radius, s->inv_m, s->inv_I, (int)s->p.precision, s->stream,
+                                &s->launches));
     CD_CUDA(s, cudaStreamSynchronize(s->stream));
     s->has_contacts = 0;
     return CD_OK;
@@ -357,7 +397,7 @@ extern "C" cd_status cd_detect_contacts(cd_system* s, int64_t* n_contacts)
     cd_status st = need_ready(s);
     if (st != CD_OK) return st;
     k_begin_call<<<1, 1, 0, s->stream>>>(s->w.ctrl, 0);
-    if ((st = launch_detect_chain(s)) != CD_OK) return st;
+    if ((st = launch_detect_chain(s, 0)) != CD_OK) return st;
     CdCtrl h;
     if ((st = read_ctrl(s, &h)) != CD_OK) return st;
     if (n_contacts) *n_contacts = h.overflow ? h.nc_needed : h.nc;
@@ -374,8 +414,8 @@ extern "C" cd_status cd_set_contacts(cd_system* s, int64_t nc, const int32_t* pa
     if (nc > 0 && !pairs) return fail(s, CD_ERR_INVALID_ARG, "pairs is NULL");
     k_begin_call<<<1, 1, 0, s->stream>>>(s->w.ctrl, 0);
     CD_CUDA(s, cd_launch_set_contacts(s->g, s->w, s->pos, s->radius, s->inv_m, s->inv_I, (int)nc, pairs, impulses,
-                                      s->pw, s->stream));
-    CD_CUDA(s, cd_launch_colour(s->g, s->w, s->colour_blocks, (int)s->p.precision, s->pw, s->stream));
+                                      s->pw, s->stream, &s->launches));
+    CD_CUDA(s, cd_launch_colour(s->g, s->w, s->colour_blocks, (int)s->p.precision, s->pw, s->stream, &s->launches));
     k_error_gate<<<1, 1, 0, s->stream>>>(s->w.ctrl);
     CdCtrl h;
     if ((st = read_ctrl(s, &h)) != CD_OK) return st;
@@ -390,8 +430,9 @@ extern "C" cd_status cd_solve_contacts(cd_system* s, cd_solve_stats* out)
     if (st != CD_OK) return st;
     if (!s->has_contacts) return fail(s, CD_ERR_STATE, "no contact set: call cd_detect_contacts or cd_set_contacts");
     k_begin_call<<<1, 1, 0, s->stream>>>(s->w.ctrl, 1);
-    if ((st = launch_solve(s, 0)) != CD_OK) return st;
-    CD_CUDA(s, cd_launch_unpack(s->g, s->w, s->pos, s->vel, s->omega, s->theta, 0, (int)s->p.precision, s->stream));
+    if ((st = launch_solve(s, 0, 0)) != CD_OK) return st;
+    CD_CUDA(s, cd_launch_unpack(s->g, s->w, s->pos, s->vel, s->omega, s->theta, 0, (int)s->p.precision, s->stream,
+                                &s->launches));
     if (!out) return CD_OK;
     CdCtrl h;
     if ((st = read_ctrl(s, &h)) != CD_OK) return st;
@@ -405,12 +446,17 @@ extern "C" cd_status cd_step(cd_system* s, int64_t n_steps, cd_step_stats* out)
     cd_status st = need_ready(s);
     if (st != CD_OK) return st;
     if (n_steps < 0) return fail(s, CD_ERR_INVALID_ARG, "n_steps must be >= 0");
+    s->launches = 0;
     k_begin_call<<<1, 1, 0, s->stream>>>(s->w.ctrl, 1);
+    ++s->launches;
     for (int64_t i = 0; i < n_steps; ++i) {
-        if ((st = launch_detect_chain(s)) != CD_OK) return st;
-        if ((st = launch_solve(s, 1)) != CD_OK) return st;
+        if ((st = mark(s)) != CD_OK) return st;
+        if ((st = launch_detect_chain(s, 1)) != CD_OK) return st;
+        if ((st = launch_solve(s, 1, 1)) != CD_OK) return st;
+        if ((st = mark(s)) != CD_OK) return st;
         CD_CUDA(s, cd_launch_unpack(s->g, s->w, s->pos, s->vel, s->omega, s->theta, 1, (int)s->p.precision,
-                                    s->stream));
+                                    s->stream, &s->launches));
+        if ((st = mark(s)) != CD_OK) return st;
     }
     if (n_steps > 0) s->has_contacts = 1;
     if (!out) return CD_OK;
@@ -421,6 +467,8 @@ extern "C" cd_status cd_step(cd_system* s, int64_t n_steps, cd_step_stats* out)
     out->total_contact_updates = h.total_updates;
     out->max_sweeps_in_step = h.max_sweeps_step;
     out->n_not_converged = h.n_not_conv;
+    out->kernel_launches = s->launches;
+    if ((st = collect_phases(s, out->phase_ms)) != CD_OK) return st;
     fill_solve_stats(s, h, &out->last);
     if ((st = ctrl_status(s, h)) != CD_OK) return st;
     return h.n_not_conv ? CD_ERR_NOT_CONVERGED : CD_OK;
@@ -486,6 +534,8 @@ extern "C" cd_status cd_download_state(cd_system* s, double* pos_host, double* v
 
 extern "C" void cd_destroy_system(cd_system* s)
 {
+    if (!s) return;
+    for (cudaEvent_t e : s->events) cudaEventDestroy(e);
     delete s;
 }
 

@@ -212,7 +212,7 @@ int cd_colour_max_blocks(int num_sms)
 }
 
 cudaError_t cd_launch_colour(const CdGeom& g, const CdWork& w, int coop_blocks, int precision, int pw,
-                             cudaStream_t s)
+                             cudaStream_t s, int* nl)
 {
     cudaError_t e;
     int nchunk = (g.cap + CD_CHUNK - 1) / CD_CHUNK;
@@ -222,9 +222,9 @@ cudaError_t cd_launch_colour(const CdGeom& g, const CdWork& w, int coop_blocks, 
     if (gc > 4096) gc = 4096;
     if ((e = cudaMemsetAsync(w.p2c_cnt, 0, sizeof(int) * (size_t)(g.n + 1), s)) != cudaSuccess) return e;
     if ((e = cudaMemsetAsync(w.p2c_fill, 0, sizeof(int) * (size_t)g.n, s)) != cudaSuccess) return e;
-    k_p2c_count<<<gc, CD_BLOCK, 0, s>>>(g, w);
-    if ((e = cd_scan_exclusive(w.p2c_cnt, w.p2c_off, g.n + 1, w.scan_tmp, nullptr, s)) != cudaSuccess) return e;
-    k_p2c_fill<<<gc, CD_BLOCK, 0, s>>>(g, w);
+    k_p2c_count<<<gc, CD_BLOCK, 0, s>>>(g, w); ++*nl;
+    if ((e = cd_scan_exclusive(w.p2c_cnt, w.p2c_off, g.n + 1, w.scan_tmp, nullptr, s, nl)) != cudaSuccess) return e;
+    k_p2c_fill<<<gc, CD_BLOCK, 0, s>>>(g, w); ++*nl;
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     if (coop_blocks > 0) {
         CdGeom ga = g;
@@ -235,17 +235,20 @@ cudaError_t cd_launch_colour(const CdGeom& g, const CdWork& w, int coop_blocks, 
         if ((e = cudaMemsetAsync(w.ctrl, 0, 2 * sizeof(unsigned long long), s)) != cudaSuccess) return e;
         e = cudaLaunchCooperativeKernel((const void*)k_jp, dim3(coop_blocks), dim3(CD_SWEEP_THREADS), args, 0, s);
         if (e != cudaSuccess) return e;
+        ++*nl;
     }
-    k_chunk_hist<<<nchunk, CD_CHUNK, 0, s>>>(w, nchunk);
-    if ((e = cd_scan_exclusive(w.chunk_cnt, w.chunk_cnt, CD_KMAX * nchunk, w.scan_tmp, nullptr, s)) != cudaSuccess)
+    k_chunk_hist<<<nchunk, CD_CHUNK, 0, s>>>(w, nchunk); ++*nl;
+    if ((e = cd_scan_exclusive(w.chunk_cnt, w.chunk_cnt, CD_KMAX * nchunk, w.scan_tmp, nullptr, s, nl)) != cudaSuccess)
         return e;
     if (g.dim == 2) {
         if (precision == CD_FP64) k_colour_scatter<2, double><<<nchunk, CD_CHUNK, 0, s>>>(g, w, nchunk, pw);
         else k_colour_scatter<2, float><<<nchunk, CD_CHUNK, 0, s>>>(g, w, nchunk, pw);
+        ++*nl;
     } else {
         if (precision == CD_FP64) k_colour_scatter<3, double><<<nchunk, CD_CHUNK, 0, s>>>(g, w, nchunk, pw);
         else k_colour_scatter<3, float><<<nchunk, CD_CHUNK, 0, s>>>(g, w, nchunk, pw);
+        ++*nl;
     }
-    k_colour_offsets<<<1, CD_KMAX, 0, s>>>(w, nchunk);
+    k_colour_offsets<<<1, CD_KMAX, 0, s>>>(w, nchunk); ++*nl;
     return cudaGetLastError();
 }

@@ -111,13 +111,15 @@ size_t cd_scan_tmp_ints(int n)
     return (size_t)((n + SCAN_TILE - 1) / SCAN_TILE + 1);
 }
 
-cudaError_t cd_scan_exclusive(const int* in, int* out, int n, int* tmp, int* total_dst, cudaStream_t stream)
+cudaError_t cd_scan_exclusive(const int* in, int* out, int n, int* tmp, int* total_dst, cudaStream_t stream,
+                              int* nl)
 {
     if (n <= 0) return cudaSuccess;
     int nb = (n + SCAN_TILE - 1) / SCAN_TILE;
     k_scan_sums<<<nb, SCAN_T, 0, stream>>>(in, n, tmp);
     k_scan_top<<<1, SCAN_T, 0, stream>>>(tmp, nb, total_dst);
     k_scan_apply<<<nb, SCAN_T, 0, stream>>>(in, n, tmp, out);
+    *nl += 3;
     return cudaGetLastError();
 }
 
@@ -464,7 +466,7 @@ static int grid_for(int n, int per_block = CD_BLOCK)
 }
 
 cudaError_t cd_launch_detect(const CdGeom& g, const CdWork& w, const double* pos, const double* radius,
-                             const double* inv_m, const double* inv_I, int warm, int pw, cudaStream_t s)
+                             const double* inv_m, const double* inv_I, int warm, int pw, cudaStream_t s, int* nl)
 {
     int ncell = g.ncell[0] * g.ncell[1] * g.ncell[2];
     cudaError_t e;
@@ -473,37 +475,42 @@ cudaError_t cd_launch_detect(const CdGeom& g, const CdWork& w, const double* pos
     int gb = grid_for(g.n);
     if (g.dim == 2) k_cell_count<2><<<gb, CD_BLOCK, 0, s>>>(g, pos, w.cell_of, w.cell_cnt, w.ctrl);
     else k_cell_count<3><<<gb, CD_BLOCK, 0, s>>>(g, pos, w.cell_of, w.cell_cnt, w.ctrl);
-    if ((e = cd_scan_exclusive(w.cell_cnt, w.cell_start, ncell + 1, w.scan_tmp, nullptr, s)) != cudaSuccess) return e;
-    k_cell_fill<<<gb, CD_BLOCK, 0, s>>>(g.n, w.cell_of, w.cell_start, w.cell_fill, w.cell_pid, w.ctrl);
+    ++*nl;
+    if ((e = cd_scan_exclusive(w.cell_cnt, w.cell_start, ncell + 1, w.scan_tmp, nullptr, s, nl)) != cudaSuccess) return e;
+    k_cell_fill<<<gb, CD_BLOCK, 0, s>>>(g.n, w.cell_of, w.cell_start, w.cell_fill, w.cell_pid, w.ctrl); ++*nl;
     if (g.dim == 2)
         k_pair_count<2><<<gb, CD_BLOCK, 0, s>>>(g, pos, radius, w.cell_of, w.cell_start, w.cell_pid, w.pcnt, w.ctrl);
     else
         k_pair_count<3><<<gb, CD_BLOCK, 0, s>>>(g, pos, radius, w.cell_of, w.cell_start, w.cell_pid, w.pcnt, w.ctrl);
+    ++*nl;
     if ((e = cudaMemsetAsync(w.pcnt + g.n, 0, sizeof(int), s)) != cudaSuccess) return e;
-    if ((e = cd_scan_exclusive(w.pcnt, w.poff, g.n + 1, w.scan_tmp, &w.ctrl->nc_needed, s)) != cudaSuccess) return e;
-    k_cap_check<<<1, 1, 0, s>>>(w.ctrl, g.cap);
+    if ((e = cd_scan_exclusive(w.pcnt, w.poff, g.n + 1, w.scan_tmp, &w.ctrl->nc_needed, s, nl)) != cudaSuccess) return e;
+    k_cap_check<<<1, 1, 0, s>>>(w.ctrl, g.cap); ++*nl;
     if (g.dim == 2) k_pair_emit<2><<<gb, CD_BLOCK, 0, s>>>(g, w, pos, radius, inv_m, inv_I);
     else k_pair_emit<3><<<gb, CD_BLOCK, 0, s>>>(g, w, pos, radius, inv_m, inv_I);
+    ++*nl;
     int gc = grid_for(g.cap);
     if (g.dim == 2) k_warm_match<2><<<gc, CD_BLOCK, 0, s>>>(w, warm, pw);
     else k_warm_match<3><<<gc, CD_BLOCK, 0, s>>>(w, warm, pw);
-    k_commit<<<gc, CD_BLOCK, 0, s>>>(w, pw);
-    k_set_nc<<<1, 1, 0, s>>>(w.ctrl);
+    ++*nl;
+    k_commit<<<gc, CD_BLOCK, 0, s>>>(w, pw); ++*nl;
+    k_set_nc<<<1, 1, 0, s>>>(w.ctrl); ++*nl;
     return cudaGetLastError();
 }
 
 cudaError_t cd_launch_set_contacts(const CdGeom& g, const CdWork& w, const double* pos, const double* radius,
                                    const double* inv_m, const double* inv_I, int nc, const int32_t* pairs,
-                                   const double* impulses, int pw, cudaStream_t s)
+                                   const double* impulses, int pw, cudaStream_t s, int* nl)
 {
     int gc = grid_for(nc > 0 ? nc : 1);
-    k_copy_pairs<<<gc, CD_BLOCK, 0, s>>>(nc, pairs, w.pairs_nx, w.ctrl);
+    k_copy_pairs<<<gc, CD_BLOCK, 0, s>>>(nc, pairs, w.pairs_nx, w.ctrl); ++*nl;
     if (nc > 0) {
         if (g.dim == 2) k_geometry_given<2><<<gc, CD_BLOCK, 0, s>>>(g, w, nc, pos, radius, inv_m, inv_I);
         else k_geometry_given<3><<<gc, CD_BLOCK, 0, s>>>(g, w, nc, pos, radius, inv_m, inv_I);
+        ++*nl;
     }
-    k_given_impulses<<<grid_for(nc * pw > 0 ? nc * pw : 1), CD_BLOCK, 0, s>>>(w, nc, impulses, pw);
-    k_commit<<<gc, CD_BLOCK, 0, s>>>(w, pw);
-    k_set_nc<<<1, 1, 0, s>>>(w.ctrl);
+    k_given_impulses<<<grid_for(nc * pw > 0 ? nc * pw : 1), CD_BLOCK, 0, s>>>(w, nc, impulses, pw); ++*nl;
+    k_commit<<<gc, CD_BLOCK, 0, s>>>(w, pw); ++*nl;
+    k_set_nc<<<1, 1, 0, s>>>(w.ctrl); ++*nl;
     return cudaGetLastError();
 }

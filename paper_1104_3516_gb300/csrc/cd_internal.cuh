@@ -126,11 +126,16 @@ __host__ __device__ __forceinline__ unsigned long long cd_key(int a, int b)
 }
 
 // ---------------------------------------------------------------------------
-// Bounded grid barrier for cooperative launches.  Arrivals are counted in a
-// monotone 64-bit counter; the last arrival of epoch e publishes e.  Waiters
-// spin with an acquire load, a %globaltimer bound (CD_WAIT_NS) and an early
-// exit when another block has flagged an error.  Returns false (all threads
-// of the block) when the wait gave up; the caller must then leave the kernel.
+// Bounded grid barrier for cooperative launches (sense-reversing counter).
+// Thread 0 of every block adds to one 32-bit word: block 0 adds
+// 2^31 - (nblocks - 1), every other block adds 1, so the word's top bit flips
+// exactly when the last block of the round arrives (all partial sums stay
+// below 2^31 within a round) and the low bits return to their old value.
+// Waiters compare the top bit with the value their own add returned.  The
+// spin is bounded by %globaltimer (CD_WAIT_NS) and also stops early when
+// another block has flagged an error; then it returns false (all threads of
+// the block) and the caller must leave the kernel.  The word must be zero at
+// launch (the launchers clear it).
 // ---------------------------------------------------------------------------
 __device__ __forceinline__ unsigned long long cd_globaltimer()
 {
@@ -139,10 +144,10 @@ __device__ __forceinline__ unsigned long long cd_globaltimer()
     return t;
 }
 
-__device__ __forceinline__ unsigned long long cd_ld_acquire(const unsigned long long* p)
+__device__ __forceinline__ unsigned cd_ld_acquire_u32(const unsigned* p)
 {
-    unsigned long long v;
-    asm volatile("ld.acquire.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+    unsigned v;
+    asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
     return v;
 }
 
@@ -156,30 +161,27 @@ __device__ __forceinline__ bool cd_grid_sync(CdCtrl* ctrl, unsigned long long nb
     __shared__ int s_ok;
     __syncthreads();
     if (threadIdx.x == 0) {
-        epoch += 1;
+        unsigned* word = reinterpret_cast<unsigned*>(&ctrl->bar_count);
+        const unsigned add = (blockIdx.x == 0) ? (0x80000000u - (unsigned)(nblocks - 1)) : 1u;
         int ok = 1;
         __threadfence();
-        unsigned long long arrived = atomicAdd(&ctrl->bar_count, 1ULL) + 1ULL;
-        if (arrived == nblocks * epoch) {
-            __threadfence();
-            asm volatile("st.release.gpu.global.u64 [%0], %1;" :: "l"(&ctrl->bar_epoch), "l"(epoch) : "memory");
-        } else {
-            unsigned long long t0 = cd_globaltimer();
-            unsigned spins = 0;
-            while (cd_ld_acquire(&ctrl->bar_epoch) < epoch) {
-                if ((++spins & 63u) == 0) {
-                    if (cd_ld_volatile_int(&ctrl->error) != CDE_NONE) { ok = 0; break; }
-                    if (cd_globaltimer() - t0 > CD_WAIT_NS) {
-                        atomicCAS(&ctrl->error, CDE_NONE, CDE_TIMEOUT);
-                        ok = 0;
-                        break;
-                    }
+        const unsigned old = atomicAdd(word, add);
+        unsigned long long t0 = 0;
+        unsigned spins = 0;
+        while (((cd_ld_acquire_u32(word) ^ old) & 0x80000000u) == 0u) {
+            if ((++spins & 255u) == 0u) {
+                if (t0 == 0) t0 = cd_globaltimer();
+                else if (cd_globaltimer() - t0 > CD_WAIT_NS) {
+                    atomicCAS(&ctrl->error, CDE_NONE, CDE_TIMEOUT);
+                    ok = 0;
+                    break;
                 }
-                __nanosleep(20);
+                if (cd_ld_volatile_int(&ctrl->error) != CDE_NONE) { ok = 0; break; }
             }
         }
         __threadfence();
         s_ok = ok;
+        ++epoch;
     }
     __syncthreads();
     return s_ok != 0;
@@ -188,24 +190,25 @@ __device__ __forceinline__ bool cd_grid_sync(CdCtrl* ctrl, unsigned long long nb
 // ---------------------------------------------------------------------------
 // Host-side launchers (defined in the .cu files), all on `stream`.
 // ---------------------------------------------------------------------------
-cudaError_t cd_scan_exclusive(const int* in, int* out, int n, int* tmp, int* total_dst, cudaStream_t stream);
+cudaError_t cd_scan_exclusive(const int* in, int* out, int n, int* tmp, int* total_dst, cudaStream_t stream,
+                              int* nl);
 size_t cd_scan_tmp_ints(int n);
 
 cudaError_t cd_launch_detect(const CdGeom& g, const CdWork& w, const double* pos, const double* radius,
-                             const double* inv_m, const double* inv_I, int warm, int pw, cudaStream_t stream);
+                             const double* inv_m, const double* inv_I, int warm, int pw, cudaStream_t stream, int* nl);
 cudaError_t cd_launch_set_contacts(const CdGeom& g, const CdWork& w, const double* pos, const double* radius,
                                    const double* inv_m, const double* inv_I, int nc, const int32_t* pairs,
-                                   const double* impulses, int pw, cudaStream_t stream);
+                                   const double* impulses, int pw, cudaStream_t stream, int* nl);
 cudaError_t cd_launch_colour(const CdGeom& g, const CdWork& w, int coop_blocks, int precision, int pw,
-                             cudaStream_t stream);
+                             cudaStream_t stream, int* nl);
 cudaError_t cd_launch_pack(const CdGeom& g, const CdWork& w, const double* vel, const double* omega,
                            const double* radius, const double* inv_m, const double* inv_I, const double* f_ext,
-                           int free_flight, int precision, cudaStream_t stream);
+                           int free_flight, int precision, cudaStream_t stream, int* nl);
 cudaError_t cd_launch_sweep(const CdGeom& g, const CdWork& w, int coop_blocks, int precision, int criterion,
-                            double alpha, int max_sweeps, int pw, cudaStream_t stream);
+                            double alpha, int max_sweeps, int pw, cudaStream_t stream, int* nl);
 cudaError_t cd_launch_unpack(const CdGeom& g, const CdWork& w, double* pos, double* vel, double* omega,
-                             double* theta, int integrate, int precision, cudaStream_t stream);
+                             double* theta, int integrate, int precision, cudaStream_t stream, int* nl);
 cudaError_t cd_launch_static(const CdGeom& g, const CdWork& w, const double* radius, const double* inv_m,
-                             const double* inv_I, int precision, cudaStream_t stream);
+                             const double* inv_I, int precision, cudaStream_t stream, int* nl);
 int cd_sweep_max_blocks(int precision, int dim, int num_sms);
 int cd_colour_max_blocks(int num_sms);

@@ -180,7 +180,10 @@ __device__ __forceinline__ double grid_total(const double* part, int nblocks, do
 }
 
 // ---------------------------------------------------------------------------
-// Single-contact updates (Fig. 2)
+// Single-contact updates (Fig. 2).  A contact record holds everything of the
+// update except the two bodies' velocities: it is read-only within a colour
+// phase, so a thread loads its next record before the grid barrier and only
+// the velocity loads sit on the critical path after it.
 // ---------------------------------------------------------------------------
 struct UpdOut {
     double pabs;     // |P| after the update
@@ -188,135 +191,163 @@ struct UpdOut {
     int bad;         // local test (I): fails both branches
 };
 
+template <int DIM, typename T> struct Rec;
+template <typename T> struct Rec<2, T> {
+    typedef typename Vec<T>::V4 T4;
+    typedef typename Vec<T>::V2 T2;
+    int2 ab;
+    T4 geo;      // nx, ny, b = g/dt, m_n
+    T mt;
+    T2 P;        // P_n, P_t before the update
+    T4 sa, sb;   // inv_m, r, r/I, 0 (sb = 0 for a wall)
+};
+template <typename T> struct Rec<3, T> {
+    typedef typename Vec<T>::V4 T4;
+    typedef typename Vec<T>::V2 T2;
+    int2 ab;
+    T4 geo;      // nx, ny, nz, b = g/dt
+    T2 m;        // m_n, m_t
+    T4 P;        // P_n, P_tx, P_ty, P_tz before the update
+    T4 sa, sb;
+};
+
+template <int DIM, typename T>
+__device__ __forceinline__ void load_rec(const CdGeom& g, const CdWork& w, int pos, Rec<DIM, T>& r)
+{
+    typedef typename Vec<T>::V4 T4;
+    typedef typename Vec<T>::V2 T2;
+    const T4* S = (const T4*)w.S;
+    r.ab = w.c_ab[pos];
+    r.geo = ((const T4*)w.c_geo)[pos];
+    if constexpr (DIM == 2) {
+        r.mt = ((const T*)w.c_m)[pos];
+        r.P = ((const T2*)w.c_P)[pos];
+    } else {
+        r.m = ((const T2*)w.c_m)[pos];
+        r.P = ((const T4*)w.c_P)[pos];
+    }
+    r.sa = S[r.ab.x];
+    if (r.ab.y < g.n) {
+        r.sb = S[r.ab.y];
+    } else {
+        r.sb.x = (T)0; r.sb.y = (T)0; r.sb.z = (T)0; r.sb.w = (T)0;
+    }
+}
+
 template <typename T>
 __device__ __forceinline__ T clampT(T x, T lo, T hi) { return x < lo ? lo : (x > hi ? hi : x); }
 
+// 2D: P_n = max(0, P_n,old - m_n (b + u_n)); P_t = clamp(P_t,old - m_t u_t, +-mu P_n)
 template <typename T>
-__device__ __forceinline__ UpdOut update2d(const CdGeom& g, const CdWork& w, int pos, bool apply_only, int crit,
-                                           double alpha, double ravg_prev)
+__device__ __forceinline__ UpdOut apply2d(const CdGeom& g, const CdWork& w, int pos, const Rec<2, T>& r,
+                                          bool apply_only, int crit, double alpha, double ravg_prev)
 {
     typedef typename Vec<T>::V4 T4;
     typedef typename Vec<T>::V2 T2;
     T4* V = (T4*)w.V;
-    const T4* S = (const T4*)w.S;
-    int2 ab = w.c_ab[pos];
-    T4 geo = ((const T4*)w.c_geo)[pos];
-    T2 P = ((T2*)w.c_P)[pos];
-    const bool wall = ab.y >= g.n;
-    T4 va = V[ab.x], sa = S[ab.x];
-    T4 vb, sb;
+    const bool wall = r.ab.y >= g.n;
+    T4 va = V[r.ab.x];
+    T4 vb;
     if (!wall) {
-        vb = V[ab.y];
-        sb = S[ab.y];
+        vb = V[r.ab.y];
     } else {
-        int k = ab.y - g.n;
+        int k = r.ab.y - g.n;
         vb.x = (T)g.wall_vel[3 * k]; vb.y = (T)g.wall_vel[3 * k + 1]; vb.z = (T)0; vb.w = (T)0;
-        sb.x = (T)0; sb.y = (T)0; sb.z = (T)0; sb.w = (T)0;
     }
-    const T nx = geo.x, ny = geo.y;
-    T Pn, Pt;
+    const T nx = r.geo.x, ny = r.geo.y;
+    T Pn, Pt, dPn, dPt;
     if (apply_only) {
-        Pn = (T)0; Pt = (T)0;          // treated as a change from zero to P
-        T dPn = P.x, dPt = P.y;
-        T dPx = dPn * nx - dPt * ny, dPy = dPn * ny + dPt * nx;
-        va.x -= sa.x * dPx; va.y -= sa.x * dPy; va.z -= sa.z * dPt;
-        vb.x += sb.x * dPx; vb.y += sb.x * dPy; vb.z -= sb.z * dPt;
-        V[ab.x] = va;
-        if (!wall) V[ab.y] = vb;
-        UpdOut o;
-        o.pabs = sqrt((double)P.x * (double)P.x + (double)P.y * (double)P.y);
-        o.rel_ok = 0; o.bad = 0;
-        return o;
+        Pn = r.P.x; Pt = r.P.y;
+        dPn = Pn; dPt = Pt;
+    } else {
+        const T b = r.geo.z, mn = r.geo.w;
+        T dvx = vb.x - va.x, dvy = vb.y - va.y;
+        T un = dvx * nx + dvy * ny;
+        T ut = (dvy * nx - dvx * ny) - (r.sa.y * va.z + r.sb.y * vb.z);
+        Pn = r.P.x - mn * (b + un);
+        Pn = Pn > (T)0 ? Pn : (T)0;
+        T lim = (T)g.mu * Pn;
+        Pt = clampT(r.P.y - r.mt * ut, -lim, lim);
+        dPn = Pn - r.P.x; dPt = Pt - r.P.y;
     }
-    const T mn = geo.w, b = geo.z;
-    const T mt = ((const T*)w.c_m)[pos];
-    T dvx = vb.x - va.x, dvy = vb.y - va.y;
-    T un = dvx * nx + dvy * ny;
-    T ut = (dvy * nx - dvx * ny) - (sa.y * va.z + sb.y * vb.z);
-    Pn = P.x - mn * (b + un);
-    Pn = Pn > (T)0 ? Pn : (T)0;
-    T lim = (T)g.mu * Pn;
-    Pt = clampT(P.y - mt * ut, -lim, lim);
-    T dPn = Pn - P.x, dPt = Pt - P.y;
     T dPx = dPn * nx - dPt * ny, dPy = dPn * ny + dPt * nx;
-    va.x -= sa.x * dPx; va.y -= sa.x * dPy; va.z -= sa.z * dPt;
-    vb.x += sb.x * dPx; vb.y += sb.x * dPy; vb.z -= sb.z * dPt;
-    V[ab.x] = va;
-    if (!wall) V[ab.y] = vb;
-    T2 Pnew; Pnew.x = Pn; Pnew.y = Pt;
-    ((T2*)w.c_P)[pos] = Pnew;
+    va.x -= r.sa.x * dPx; va.y -= r.sa.x * dPy; va.z -= r.sa.z * dPt;
+    V[r.ab.x] = va;
+    if (!wall) {
+        vb.x += r.sb.x * dPx; vb.y += r.sb.x * dPy; vb.z -= r.sb.z * dPt;
+        V[r.ab.y] = vb;
+    }
     UpdOut o;
     double pn = (double)Pn, pt = (double)Pt;
     o.pabs = sqrt(pn * pn + pt * pt);
     o.rel_ok = 0; o.bad = 0;
-    if (crit == CD_CONV_LOCAL) {
-        double d0 = (double)dPn, d1 = (double)dPt;
-        double s0 = pn + (double)P.x, s1 = pt + (double)P.y;
-        double d2 = d0 * d0 + d1 * d1, s2 = s0 * s0 + s1 * s1;
-        o.rel_ok = d2 < alpha * s2;
-        o.bad = !o.rel_ok && !(d2 <= alpha * ravg_prev * ravg_prev);
+    if (!apply_only) {
+        T2 Pnew; Pnew.x = Pn; Pnew.y = Pt;
+        ((T2*)w.c_P)[pos] = Pnew;
+        if (crit == CD_CONV_LOCAL) {
+            double d0 = (double)dPn, d1 = (double)dPt;
+            double s0 = pn + (double)r.P.x, s1 = pt + (double)r.P.y;
+            double d2 = d0 * d0 + d1 * d1, s2 = s0 * s0 + s1 * s1;
+            o.rel_ok = d2 < alpha * s2;
+            o.bad = !o.rel_ok && !(d2 <= alpha * ravg_prev * ravg_prev);
+        }
     }
     return o;
 }
 
+// 3D: the same with the tangential impulse a vector, scaled onto the cone.
 template <typename T>
-__device__ __forceinline__ UpdOut update3d(const CdGeom& g, const CdWork& w, int pos, bool apply_only, int crit,
-                                           double alpha, double ravg_prev)
+__device__ __forceinline__ UpdOut apply3d(const CdGeom& g, const CdWork& w, int pos, const Rec<3, T>& r,
+                                          bool apply_only, int crit, double alpha, double ravg_prev)
 {
     typedef typename Vec<T>::V4 T4;
-    typedef typename Vec<T>::V2 T2;
     T4* V = (T4*)w.V;
-    const T4* S = (const T4*)w.S;
-    int2 ab = w.c_ab[pos];
-    T4 geo = ((const T4*)w.c_geo)[pos];   // nx, ny, nz, b
-    T4 P = ((T4*)w.c_P)[pos];              // Pn, Ptx, Pty, Ptz
-    const bool wall = ab.y >= g.n;
-    T4 va = V[2 * ab.x], wa = V[2 * ab.x + 1], sa = S[ab.x];
-    T4 vb, wb, sb;
+    const bool wall = r.ab.y >= g.n;
+    T4 va = V[2 * r.ab.x], wa = V[2 * r.ab.x + 1];
+    T4 vb, wb;
     if (!wall) {
-        vb = V[2 * ab.y]; wb = V[2 * ab.y + 1]; sb = S[ab.y];
+        vb = V[2 * r.ab.y]; wb = V[2 * r.ab.y + 1];
     } else {
-        int k = ab.y - g.n;
+        int k = r.ab.y - g.n;
         vb.x = (T)g.wall_vel[3 * k]; vb.y = (T)g.wall_vel[3 * k + 1]; vb.z = (T)g.wall_vel[3 * k + 2]; vb.w = (T)0;
         wb.x = wb.y = wb.z = wb.w = (T)0;
-        sb.x = sb.y = sb.z = sb.w = (T)0;
     }
-    const T nx = geo.x, ny = geo.y, nz = geo.z;
-    T dPn, dtx, dty, dtz;
-    T Pn, Ptx, Pty, Ptz;
+    const T nx = r.geo.x, ny = r.geo.y, nz = r.geo.z;
+    T Pn, Ptx, Pty, Ptz, dPn, dtx, dty, dtz;
     if (apply_only) {
-        Pn = P.x; Ptx = P.y; Pty = P.z; Ptz = P.w;
+        Pn = r.P.x; Ptx = r.P.y; Pty = r.P.z; Ptz = r.P.w;
         dPn = Pn; dtx = Ptx; dty = Pty; dtz = Ptz;
     } else {
-        const T2 m = ((const T2*)w.c_m)[pos];
-        const T mn = m.x, mt = m.y, b = geo.w;
+        const T mn = r.m.x, mt = r.m.y, b = r.geo.w;
         // relative velocity of the contact points: (vb - va) - (ra wa + rb wb) x n
-        T lx = sa.y * wa.x + sb.y * wb.x, ly = sa.y * wa.y + sb.y * wb.y, lz = sa.y * wa.z + sb.y * wb.z;
+        T lx = r.sa.y * wa.x + r.sb.y * wb.x, ly = r.sa.y * wa.y + r.sb.y * wb.y, lz = r.sa.y * wa.z + r.sb.y * wb.z;
         T gx = (vb.x - va.x) - (ly * nz - lz * ny);
         T gy = (vb.y - va.y) - (lz * nx - lx * nz);
         T gz = (vb.z - va.z) - (lx * ny - ly * nx);
         T un = gx * nx + gy * ny + gz * nz;
         T tx = gx - un * nx, ty = gy - un * ny, tz = gz - un * nz;
-        Pn = P.x - mn * (b + un);
+        Pn = r.P.x - mn * (b + un);
         Pn = Pn > (T)0 ? Pn : (T)0;
-        Ptx = P.y - mt * tx; Pty = P.z - mt * ty; Ptz = P.w - mt * tz;
+        Ptx = r.P.y - mt * tx; Pty = r.P.z - mt * ty; Ptz = r.P.w - mt * tz;
         T lim = (T)g.mu * Pn;
         T q2 = Ptx * Ptx + Pty * Pty + Ptz * Ptz;
         if (q2 > lim * lim) {
             T sc = lim / sqrt(q2);
             Ptx *= sc; Pty *= sc; Ptz *= sc;
         }
-        dPn = Pn - P.x; dtx = Ptx - P.y; dty = Pty - P.z; dtz = Ptz - P.w;
+        dPn = Pn - r.P.x; dtx = Ptx - r.P.y; dty = Pty - r.P.z; dtz = Ptz - r.P.w;
     }
     T dx = dPn * nx + dtx, dy = dPn * ny + dty, dz = dPn * nz + dtz;
     // n x dP
     T cx = ny * dz - nz * dy, cy = nz * dx - nx * dz, cz = nx * dy - ny * dx;
-    va.x -= sa.x * dx; va.y -= sa.x * dy; va.z -= sa.x * dz;
-    wa.x -= sa.z * cx; wa.y -= sa.z * cy; wa.z -= sa.z * cz;
-    vb.x += sb.x * dx; vb.y += sb.x * dy; vb.z += sb.x * dz;
-    wb.x -= sb.z * cx; wb.y -= sb.z * cy; wb.z -= sb.z * cz;
-    V[2 * ab.x] = va; V[2 * ab.x + 1] = wa;
-    if (!wall) { V[2 * ab.y] = vb; V[2 * ab.y + 1] = wb; }
+    va.x -= r.sa.x * dx; va.y -= r.sa.x * dy; va.z -= r.sa.x * dz;
+    wa.x -= r.sa.z * cx; wa.y -= r.sa.z * cy; wa.z -= r.sa.z * cz;
+    V[2 * r.ab.x] = va; V[2 * r.ab.x + 1] = wa;
+    if (!wall) {
+        vb.x += r.sb.x * dx; vb.y += r.sb.x * dy; vb.z += r.sb.x * dz;
+        wb.x -= r.sb.z * cx; wb.y -= r.sb.z * cy; wb.z -= r.sb.z * cz;
+        V[2 * r.ab.y] = vb; V[2 * r.ab.y + 1] = wb;
+    }
     UpdOut o;
     double pn = (double)Pn, px = (double)Ptx, py = (double)Pty, pz = (double)Ptz;
     o.pabs = sqrt(pn * pn + px * px + py * py + pz * pz);
@@ -326,7 +357,7 @@ __device__ __forceinline__ UpdOut update3d(const CdGeom& g, const CdWork& w, int
         ((T4*)w.c_P)[pos] = Pnew;
         if (crit == CD_CONV_LOCAL) {
             double d0 = (double)dPn, d1 = (double)dtx, d2_ = (double)dty, d3 = (double)dtz;
-            double s0 = pn + (double)P.x, s1 = px + (double)P.y, s2_ = py + (double)P.z, s3 = pz + (double)P.w;
+            double s0 = pn + (double)r.P.x, s1 = px + (double)r.P.y, s2_ = py + (double)r.P.z, s3 = pz + (double)r.P.w;
             double d2 = d0 * d0 + d1 * d1 + d2_ * d2_ + d3 * d3;
             double s2 = s0 * s0 + s1 * s1 + s2_ * s2_ + s3 * s3;
             o.rel_ok = d2 < alpha * s2;
@@ -337,11 +368,37 @@ __device__ __forceinline__ UpdOut update3d(const CdGeom& g, const CdWork& w, int
 }
 
 template <int DIM, typename T>
-__device__ __forceinline__ UpdOut update(const CdGeom& g, const CdWork& w, int pos, bool apply_only, int crit,
-                                         double alpha, double ravg_prev)
+__device__ __forceinline__ UpdOut apply_rec(const CdGeom& g, const CdWork& w, int pos, const Rec<DIM, T>& r,
+                                            bool apply_only, int crit, double alpha, double ravg_prev)
 {
-    if (DIM == 2) return update2d<T>(g, w, pos, apply_only, crit, alpha, ravg_prev);
-    return update3d<T>(g, w, pos, apply_only, crit, alpha, ravg_prev);
+    if constexpr (DIM == 2) return apply2d<T>(g, w, pos, r, apply_only, crit, alpha, ravg_prev);
+    else return apply3d<T>(g, w, pos, r, apply_only, crit, alpha, ravg_prev);
+}
+
+// One colour phase for this thread: its first contact's record was loaded
+// into `nxt` before the barrier (if it has one); the rest are loaded inline.
+// Afterwards `nxt` holds the first record of colour `knext` (prefetch).
+template <int DIM, typename T>
+__device__ __forceinline__ void colour_phase(const CdGeom& g, const CdWork& w, const int* s_off, int k, int knext,
+                                             int tid, int stride, Rec<DIM, T>& nxt, bool apply_only, int crit,
+                                             double alpha, double ravg_prev, double (&acc)[3])
+{
+    const int end = s_off[k + 1];
+    int p = s_off[k] + tid;
+    if (p < end) {
+        UpdOut o = apply_rec<DIM, T>(g, w, p, nxt, apply_only, crit, alpha, ravg_prev);
+        acc[0] += o.pabs; acc[1] += (double)o.rel_ok; acc[2] += (double)o.bad;
+        for (p += stride; p < end; p += stride) {
+            Rec<DIM, T> r;
+            load_rec<DIM, T>(g, w, p, r);
+            o = apply_rec<DIM, T>(g, w, p, r, apply_only, crit, alpha, ravg_prev);
+            acc[0] += o.pabs; acc[1] += (double)o.rel_ok; acc[2] += (double)o.bad;
+        }
+    }
+    if (knext >= 0) {
+        int q = s_off[knext] + tid;
+        if (q < s_off[knext + 1]) load_rec<DIM, T>(g, w, q, nxt);
+    }
 }
 
 // ---------------------------------------------------------------------------
@@ -368,11 +425,13 @@ k_sweep(CdGeom g, CdWork w, int crit, double alpha, int max_sweeps)
     int sweeps = 0, converged = (nc == 0);
     double resid = 0.0, ravg = 0.0, ravg_prev = 0.0;
     if (nc > 0) {
+        Rec<DIM, T> nxt;
+        if (s_off[0] + tid < s_off[1]) load_rec<DIM, T>(g, w, s_off[0] + tid, nxt);
         // starting impulses, colour by colour
         double acc[3] = {0.0, 0.0, 0.0};
         for (int k = 0; k < K; ++k) {
-            for (int p = s_off[k] + tid; p < s_off[k + 1]; p += stride)
-                acc[0] += update<DIM, T>(g, w, p, true, crit, alpha, 0.0).pabs;
+            colour_phase<DIM, T>(g, w, s_off, k, (k + 1 < K) ? k + 1 : 0, tid, stride, nxt, true, crit, alpha, 0.0,
+                                 acc);
             if (k == K - 1) {
                 block_sum<3>(acc, s_red);
                 if (threadIdx.x == 0) w.partials[blockIdx.x] = acc[0];
@@ -387,12 +446,8 @@ k_sweep(CdGeom g, CdWork w, int crit, double alpha, int max_sweeps)
             double* part = w.partials + (size_t)buf * 3 * nb;
             double a3[3] = {0.0, 0.0, 0.0};
             for (int k = 0; k < K; ++k) {
-                for (int p = s_off[k] + tid; p < s_off[k + 1]; p += stride) {
-                    UpdOut o = update<DIM, T>(g, w, p, false, crit, alpha, ravg_prev);
-                    a3[0] += o.pabs;
-                    a3[1] += (double)o.rel_ok;
-                    a3[2] += (double)o.bad;
-                }
+                colour_phase<DIM, T>(g, w, s_off, k, (k + 1 < K) ? k + 1 : 0, tid, stride, nxt, false, crit, alpha,
+                                     ravg_prev, a3);
                 if (k == K - 1) {
                     block_sum<3>(a3, s_red);
                     if (threadIdx.x == 0) {
@@ -492,41 +547,46 @@ static int grid_n(int n)
 }
 
 cudaError_t cd_launch_static(const CdGeom& g, const CdWork& w, const double* radius, const double* inv_m,
-                             const double* inv_I, int precision, cudaStream_t s)
+                             const double* inv_I, int precision, cudaStream_t s, int* nl)
 {
     if (precision == CD_FP64)
         k_static<double><<<grid_n(g.n), CD_BLOCK, 0, s>>>(g.n, g.rotations, radius, inv_m, inv_I, (double4*)w.S);
     else
         k_static<float><<<grid_n(g.n), CD_BLOCK, 0, s>>>(g.n, g.rotations, radius, inv_m, inv_I, (float4*)w.S);
+    ++*nl;
     return cudaGetLastError();
 }
 
 cudaError_t cd_launch_pack(const CdGeom& g, const CdWork& w, const double* vel, const double* omega,
                            const double* radius, const double* inv_m, const double* inv_I, const double* f_ext,
-                           int free_flight, int precision, cudaStream_t s)
+                           int free_flight, int precision, cudaStream_t s, int* nl)
 {
     (void)radius; (void)inv_I;
     int gb = grid_n(g.n);
     if (g.dim == 2) {
         if (precision == CD_FP64) k_pack<2, double><<<gb, CD_BLOCK, 0, s>>>(g, w, vel, omega, inv_m, f_ext, free_flight);
         else k_pack<2, float><<<gb, CD_BLOCK, 0, s>>>(g, w, vel, omega, inv_m, f_ext, free_flight);
+        ++*nl;
     } else {
         if (precision == CD_FP64) k_pack<3, double><<<gb, CD_BLOCK, 0, s>>>(g, w, vel, omega, inv_m, f_ext, free_flight);
         else k_pack<3, float><<<gb, CD_BLOCK, 0, s>>>(g, w, vel, omega, inv_m, f_ext, free_flight);
+        ++*nl;
     }
     return cudaGetLastError();
 }
 
 cudaError_t cd_launch_unpack(const CdGeom& g, const CdWork& w, double* pos, double* vel, double* omega,
-                             double* theta, int integrate, int precision, cudaStream_t s)
+                             double* theta, int integrate, int precision, cudaStream_t s, int* nl)
 {
     int gb = grid_n(g.n);
     if (g.dim == 2) {
         if (precision == CD_FP64) k_unpack<2, double><<<gb, CD_BLOCK, 0, s>>>(g, w, pos, vel, omega, theta, integrate);
         else k_unpack<2, float><<<gb, CD_BLOCK, 0, s>>>(g, w, pos, vel, omega, theta, integrate);
+        ++*nl;
     } else {
         if (precision == CD_FP64) k_unpack<3, double><<<gb, CD_BLOCK, 0, s>>>(g, w, pos, vel, omega, theta, integrate);
         else k_unpack<3, float><<<gb, CD_BLOCK, 0, s>>>(g, w, pos, vel, omega, theta, integrate);
+        ++*nl;
     }
     return cudaGetLastError();
 }
@@ -548,7 +608,7 @@ int cd_sweep_max_blocks(int precision, int dim, int num_sms)
 }
 
 cudaError_t cd_launch_sweep(const CdGeom& g, const CdWork& w, int coop_blocks, int precision, int criterion,
-                            double alpha, int max_sweeps, int pw, cudaStream_t s)
+                            double alpha, int max_sweeps, int pw, cudaStream_t s, int* nl)
 {
     (void)pw;
     cudaError_t e = cudaMemsetAsync(w.ctrl, 0, 2 * sizeof(unsigned long long), s);
@@ -559,6 +619,7 @@ cudaError_t cd_launch_sweep(const CdGeom& g, const CdWork& w, int coop_blocks, i
     double al = alpha;
     int ms = max_sweeps;
     void* args[] = {&ga, &wa, &crit, &al, &ms};
+    ++*nl;
     return cudaLaunchCooperativeKernel(sweep_fn(g.dim, precision), dim3(coop_blocks), dim3(CD_SWEEP_THREADS), args,
                                        0, s);
 }
