@@ -192,12 +192,42 @@ cd_status cd_upload_state(cd_system* sys, const double* pos_host, const double* 
                           const double* omega_host);
 cd_status cd_download_state(cd_system* sys, double* pos_host, double* vel_host, double* omega_host);
 
+/* Contact detection that allocates nothing, for callers that cannot call
+ * cudaMalloc (code running inside a framework that owns all device memory, a
+ * plug-in that may only use buffers it is given, a run with a frozen memory
+ * budget).  There is no counterpart in the paper: it is the detection of
+ * cd_detect_contacts (same contact set, normals and gaps, key order, walls
+ * as bodies n + k) without a system object or a workspace.
+ *
+ * Inputs (device): pos, radius, inv_mass, inv_inertia as in
+ * cd_create_system; params as there (wall planes from params->wall_pos).
+ * Outputs (device, caller-owned): pairs max_contacts*2 int32, normal
+ * max_contacts*3 doubles, gap max_contacts doubles; *n_contacts (host) the
+ * number found.  Work is enqueued on cuda_stream and the call synchronises it.
+ *
+ * Scratch lives in a fixed device array of about 4.1 MB inside the library,
+ * held by every GPU that loads it until the process exits; limits: n <= 16384
+ * particles, at most 65536 cells of side 2 r_max + delta, max_contacts <=
+ * 65536.  Larger sizes return CD_ERR_INVALID_ARG (message via
+ * cd_last_error(NULL)); more contacts than max_contacts return
+ * CD_ERR_CAPACITY with the number needed in *n_contacts and nothing written
+ * past max_contacts.  The first call on each device looks up the array's
+ * device address (cudaGetSymbolAddress) with that device current, so make
+ * that first call before any stream capture.  All calls share the array:
+ * each call clears what must start at zero, and calls that overlap on the
+ * GPU (different streams or threads) race with each other. */
+cd_status cd_detect_contacts_noalloc(const cd_params* params, int64_t n, const double* pos, const double* radius,
+                                     const double* inv_mass, const double* inv_inertia, int64_t max_contacts,
+                                     int32_t* pairs, double* normal, double* gap, int64_t* n_contacts,
+                                     void* cuda_stream);
+
 /* Releases the host-side system object (not the caller's arrays or
  * workspace).  Safe on NULL. */
 void cd_destroy_system(cd_system* sys);
 
 /* Message of the last failure on this system ("" if none); NULL system gives
- * the last creation failure. */
+ * the last failure of cd_create_system or cd_detect_contacts_noalloc on this
+ * thread. */
 const char* cd_last_error(const cd_system* sys);
 
 #ifdef __cplusplus

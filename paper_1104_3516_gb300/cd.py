@@ -118,6 +118,8 @@ SIGNATURES = [
     ("cd_get_walls", C.c_int, [_P, C.POINTER(C.c_double)]),
     ("cd_upload_state", C.c_int, [_P, _P, _P, _P]),
     ("cd_download_state", C.c_int, [_P, _P, _P, _P]),
+    ("cd_detect_contacts_noalloc", C.c_int, [C.POINTER(cd_params), C.c_int64, _P, _P, _P, _P, C.c_int64, _P, _P,
+                                             _P, C.POINTER(C.c_int64), _P]),
     ("cd_destroy_system", None, [_P]),
     ("cd_last_error", C.c_char_p, [_P]),
 ]
@@ -215,6 +217,18 @@ def cd_upload_state(sysptr, pos_host, vel_host, omega_host):
 def cd_download_state(sysptr, pos_host, vel_host, omega_host):
     ptr = lambda a: None if a is None else (a.data_ptr() if isinstance(a, torch.Tensor) else a.ctypes.data)
     _check(sysptr, lib().cd_download_state(sysptr, ptr(pos_host), ptr(vel_host), ptr(omega_host)))
+
+
+def cd_detect_contacts_noalloc(params: cd_params, n, pos, radius, inv_mass, inv_inertia, max_contacts, pairs,
+                               normal, gap, stream) -> int:
+    """Detection without a system or workspace (library-held scratch; see cd_api.h)."""
+    nc = C.c_int64()
+    ptr = lambda t: None if t is None else t.data_ptr()
+    st = lib().cd_detect_contacts_noalloc(C.byref(params), int(n), ptr(pos), ptr(radius), ptr(inv_mass),
+                                          ptr(inv_inertia), int(max_contacts), ptr(pairs), ptr(normal), ptr(gap),
+                                          C.byref(nc), stream)
+    _check(None, st)
+    return int(nc.value)
 
 
 def cd_destroy_system(sysptr):

@@ -40,6 +40,13 @@ struct cd_system {
 
 static thread_local std::string g_create_err;
 
+// Sets the message cd_last_error(NULL) returns (used by entry points that
+// have no system object).
+__attribute__((visibility("hidden"))) void cd_set_global_error(const char* msg)
+{
+    g_create_err = msg ? msg : "";
+}
+
 static cd_status fail(cd_system* s, cd_status st, const std::string& msg)
 {
     if (s) s->err = msg; else g_create_err = msg;
