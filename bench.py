@@ -58,6 +58,10 @@ def parse():
     ap.add_argument("--alpha", type=float, default=1e-6)
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--tile-cells", type=int, default=0,
+                    help="0: global colour order; >= 2: tiled colour order with tiles of this many cells")
+    ap.add_argument("--dataflow", type=int, default=0,
+                    help="1: per-particle update counts instead of a grid barrier per colour")
     ap.add_argument("--cpu-sweeps", type=int, default=30,
                     help="sweep cap of the oracle's bounded sample step")
     return ap.parse_args()
@@ -74,7 +78,9 @@ def workload(args, rank):
 def config(args, wl, extra=None):
     c = {"workload": WORKLOAD, "n_discs": wl.n, "packing_fraction_box": 0.80, "mu": wl.mu, "dt": wl.dt,
          "gravity": 1.0, "top_wall_speed": 1e-3, "periodic": "x", "criterion": "global |dR_avg|/(R^j+R^j-1)",
-         "alpha": args.alpha, "max_sweeps": args.max_sweeps, "warm_start": True, "order": "colour (JP greedy)",
+         "alpha": args.alpha, "max_sweeps": args.max_sweeps, "warm_start": True,
+         "order": ("colour (JP greedy)" if args.tile_cells == 0 else
+                   f"tiled colour order, {args.tile_cells}-cell tiles"),
          "l2": "flushed (512 MiB write) before every timed step"}
     if extra:
         c.update(extra)
@@ -230,7 +236,7 @@ def run_ours(args):
     prec = cd.CD_FP64 if args.precision == "f64" else cd.CD_FP32
     stream = torch.cuda.current_stream(device)
     sysg = cd.CDSystem(wl, device=device, precision=prec, criterion=cd.CD_CONV_GLOBAL_REL, max_contacts=4 * wl.n,
-                       timing=1, stream=stream)
+                       timing=1, stream=stream, tile_cells=args.tile_cells, dataflow=args.dataflow)
     flush = torch.empty(512 << 20, dtype=torch.uint8, device=device)
 
     for _ in range(args.warmup):
@@ -274,7 +280,8 @@ def run_ours(args):
     peak, peak_kind = peaks()
     achieved = sweep_bytes / (ph["sweep"] / 1e3) / 1e9 if ph["sweep"] > 0 else 0.0
     roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
-                "traffic": None, "kernel": f"k_sweep<2,{'double' if args.precision == 'f64' else 'float'}>",
+                "traffic": None, "kernel": ("k_sweep" if args.tile_cells == 0 else "k_sweep_tiled")
+                + f"<2,{'double' if args.precision == 'f64' else 'float'}>",
                 "peak_source": f"{peak_kind} HBM copy bandwidth",
                 "bytes_model": f"per sweep {bpc} B x contacts + {bpp} B x particles",
                 "avg_launch_ms": ph["sweep"] / max(args.steps, 1)}

@@ -91,6 +91,27 @@ typedef struct {
     int64_t max_contacts;   /* contact capacity of the workspace */
     int64_t timing;         /* 1: record CUDA events around the phases of each
                                step on the system's stream (see cd_step_stats) */
+    int64_t tile_cells;     /* 0: global colour order (every colour class spread
+                               over the whole GPU, one grid barrier per colour).
+                               >= 2: tiled colour order: the cell grid is cut
+                               into tiles of tile_cells cells per axis
+                               (nt = cells / tile_cells per axis, even on a
+                               periodic axis); a contact belongs to the tile of
+                               its body a; tiles are coloured by coordinate
+                               parity (4 tile colours in 2D, 8 in 3D) and the
+                               contacts of a tile by greedy colouring inside
+                               the tile; the sweep order is (tile colour,
+                               tile, colour, key), one grid barrier per tile
+                               colour, a tile's particle state staged in
+                               shared memory */
+    int64_t dataflow;       /* with tile_cells = 0: 1 replaces the grid barrier
+                               after every colour by per-particle update
+                               counts: a contact waits until both particles
+                               have received every update that precedes it in
+                               the colour order (acquire/release through L2,
+                               bounded waits), so colours overlap; one grid
+                               barrier per sweep remains for the residual.
+                               Same update order, bit-identical results. */
 } cd_params;
 
 typedef struct cd_system cd_system;

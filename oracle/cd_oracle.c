@@ -70,6 +70,7 @@ typedef struct {
     uint64_t seed;          /* seeds the random order and the colouring */
     double parallel_p;      /* fraction of contacts updated in parallel */
     int64_t rotations;      /* 0: rotational degrees of freedom frozen */
+    int64_t tile_cells;     /* >= 2: tiled colour order (see ora_tile_colour) */
 } ora_params;
 
 typedef struct {
@@ -324,7 +325,18 @@ static int cmp_prio(const void* u, const void* v)
     return 0;
 }
 
+static int colour_greedy_in(long long n, long long nc, const int32_t* pairs, uint64_t seed,
+                            const int64_t* tile, int32_t* colour);
+
 int ora_colour_greedy(long long n, long long nc, const int32_t* pairs, uint64_t seed, int32_t* colour)
+{
+    return colour_greedy_in(n, nc, pairs, seed, NULL, colour);
+}
+
+/* Greedy colouring as above; with `tile` non-NULL two contacts conflict only
+ * when they share a particle and lie in the same tile. */
+static int colour_greedy_in(long long n, long long nc, const int32_t* pairs, uint64_t seed,
+                            const int64_t* tile, int32_t* colour)
 {
     if (nc == 0) return 0;
     long long* deg = (long long*)calloc((size_t)n + 1, sizeof(long long));
@@ -364,6 +376,7 @@ int ora_colour_greedy(long long n, long long nc, const int32_t* pairs, uint64_t 
             for (long long e = deg[q]; e < deg[q + 1]; ++e) {
                 long long d = adj[e];
                 if (d == c || colour[d] < 0) continue;
+                if (tile && tile[d] != tile[c]) continue;
                 if (colour[d] >= cap) {
                     int ncap = cap * 2;
                     while (ncap <= colour[d]) ncap *= 2;
@@ -385,6 +398,59 @@ int ora_colour_greedy(long long n, long long nc, const int32_t* pairs, uint64_t 
     }
     free(used); free(it); free(adj); free(fill); free(deg);
     return kmax;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Tiled colour order.  The cell grid of the detection (side >= l) is cut   */
+/* into tiles of tile_cells cells per axis (nt_k = m_k / tile_cells tiles,  */
+/* made even on a periodic axis, at least 1); cell q lies in tile           */
+/* floor(q nt / m).  A contact belongs to the tile of its body a.  Tiles are */
+/* coloured by the parity of their coordinates (2^dim tile colours): two    */
+/* tiles of one colour are at least one whole tile (>= 2 cells) apart, so   */
+/* their contacts share no particle.  Inside a tile, contacts are coloured  */
+/* greedily as in ora_colour_greedy, with conflicts only inside the tile.   */
+/* The sweep order is (tile colour, tile, colour, key).                     */
+/* group[c] = tile_colour * ntiles + tile; returns the number of colours.   */
+/* ------------------------------------------------------------------------ */
+int ora_tile_colour(const ora_params* p, long long n, const double* x, const double* r, long long nc,
+                    const int32_t* pairs, int32_t* colour, int64_t* group)
+{
+    int D = (int)p->dim;
+    double rmax = 0.0;
+    for (long long i = 0; i < n; ++i) if (r[i] > rmax) rmax = r[i];
+    double ell = 2.0 * rmax + p->delta;
+    long long m[3] = {1, 1, 1}, nt[3] = {1, 1, 1};
+    double cs[3] = {1.0, 1.0, 1.0};
+    for (int k = 0; k < D; ++k) {
+        double L = p->box_hi[k] - p->box_lo[k];
+        long long mk = (long long)floor(L / ell);
+        if (mk < 1) mk = 1;
+        m[k] = mk;
+        cs[k] = L / (double)mk;
+        long long t = (p->tile_cells > 0) ? mk / p->tile_cells : 1;
+        if (t < 1) t = 1;
+        if (p->periodic[k] && t > 1 && (t & 1)) t -= 1;
+        nt[k] = t;
+    }
+    long long ntiles = nt[0] * nt[1] * nt[2];
+    int64_t* tile = (int64_t*)malloc(sizeof(int64_t) * (size_t)(nc > 0 ? nc : 1));
+    for (long long c = 0; c < nc; ++c) {
+        long long a = pairs[2 * c];
+        long long tq[3] = {0, 0, 0};
+        for (int k = 0; k < D; ++k) {
+            long long q = (long long)floor((x[a * D + k] - p->box_lo[k]) / cs[k]);
+            if (q < 0) q = 0;
+            if (q > m[k] - 1) q = m[k] - 1;
+            tq[k] = (q * nt[k]) / m[k];
+        }
+        long long t = (tq[2] * nt[1] + tq[1]) * nt[0] + tq[0];
+        long long tc = (tq[0] & 1) | ((tq[1] & 1) << 1) | ((tq[2] & 1) << 2);
+        tile[c] = t;
+        group[c] = tc * ntiles + t;
+    }
+    int K = colour_greedy_in(n, nc, pairs, p->seed, tile, colour);
+    free(tile);
+    return K;
 }
 
 /* ------------------------------------------------------------------------ */
@@ -595,11 +661,24 @@ static int is_parallel(const ora_params* p, uint64_t key)
     return u < p->parallel_p;
 }
 
+static const int64_t* g_sort_group;
+static const int32_t* g_sort_colour;
+
+static int cmp_group_colour(const void* u, const void* v)
+{
+    long long a = *(const long long*)u, b = *(const long long*)v;
+    int64_t ga = g_sort_group ? g_sort_group[a] : 0, gb = g_sort_group ? g_sort_group[b] : 0;
+    if (ga != gb) return (ga < gb) ? -1 : 1;
+    if (g_sort_colour[a] != g_sort_colour[b]) return (g_sort_colour[a] < g_sort_colour[b]) ? -1 : 1;
+    return (a > b) - (a < b);
+}
+
 /* Solve the contact impulses of one time step.
  *   v, w     in: free velocities (external forces applied, no contact
  *                impulses); out: velocities with the final impulses applied.
  *   P        in: starting impulses (warm start or zeros); out: solution.
  *   colour   colour per contact (ORA_ORDER_COLOUR), may be NULL otherwise.
+ *   group    colour-order group per contact (tiled order), or NULL.
  *   fixed    the order for ORA_ORDER_FIXED, may be NULL otherwise.
  *   ravg_hist  if non-NULL, R_avg after sweep j is stored at [j]
  *              ([0] = starting impulses); room for max_sweeps + 1.
@@ -607,8 +686,8 @@ static int is_parallel(const ora_params* p, uint64_t key)
 int ora_solve(const ora_params* p, long long n, double* v, double* w,
               const double* r, const double* inv_m, const double* inv_I,
               long long nc, const int32_t* pairs, const double* normal, const double* gap,
-              const double* mn, const double* mt, const int32_t* colour, const int32_t* fixed,
-              long long step_index, double* P, double* ravg_hist, ora_solve_stats* st)
+              const double* mn, const double* mt, const int32_t* colour, const int64_t* group,
+              const int32_t* fixed, long long step_index, double* P, double* ravg_hist, ora_solve_stats* st)
 {
     int D = (int)p->dim;
     int pw = pw_of(D);
@@ -627,13 +706,14 @@ int ora_solve(const ora_params* p, long long n, double* v, double* w,
 
     long long* order = (long long*)malloc(sizeof(long long) * (size_t)(nc > 0 ? nc : 1));
     if (p->order == ORA_ORDER_COLOUR) {
+        /* (group, colour, key): a stable sort of the key-ordered contacts */
         int K = 0;
         for (long long c = 0; c < nc; ++c) if (colour[c] + 1 > K) K = colour[c] + 1;
         st->n_colours = K;
-        long long o = 0;
-        for (int k = 0; k < K; ++k)
-            for (long long c = 0; c < nc; ++c)
-                if (colour[c] == k) order[o++] = c;
+        for (long long c = 0; c < nc; ++c) order[c] = c;
+        g_sort_group = group;
+        g_sort_colour = colour;
+        qsort(order, (size_t)nc, sizeof(long long), cmp_group_colour);
     } else {
         for (long long c = 0; c < nc; ++c) order[c] = (p->order == ORA_ORDER_FIXED && fixed) ? fixed[c] : c;
     }
@@ -808,14 +888,19 @@ int ora_step(const ora_params* p, long long n, double* x, double* v, double* w, 
     }
 
     ora_params q = *p;
-    if (p->order == ORA_ORDER_COLOUR) {
+    int64_t* group = NULL;
+    if (p->order == ORA_ORDER_COLOUR && p->tile_cells >= 2) {
+        group = (int64_t*)malloc(sizeof(int64_t) * ncz);
+        ora_tile_colour(p, n, x, r, nc, pairs, colour, group);
+    } else if (p->order == ORA_ORDER_COLOUR) {
         int K = ora_colour_greedy(n, nc, pairs, p->seed, colour);
         (void)K;
     } else {
         for (long long c = 0; c < nc; ++c) colour[c] = 0;
     }
-    ora_solve(&q, n, v, w, r, inv_m, inv_I, nc, pairs, normal, gap, mn, mt, colour, NULL,
+    ora_solve(&q, n, v, w, r, inv_m, inv_I, nc, pairs, normal, gap, mn, mt, colour, group, NULL,
               step_index, P, NULL, st);
+    free(group);
 
     /* Eq. 2: positions with the new velocities; orientation likewise */
     for (long long i = 0; i < n; ++i) {

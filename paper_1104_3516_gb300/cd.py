@@ -58,6 +58,8 @@ class cd_params(C.Structure):
         ("seed", C.c_uint64),
         ("max_contacts", C.c_int64),
         ("timing", C.c_int64),
+        ("tile_cells", C.c_int64),
+        ("dataflow", C.c_int64),
     ]
 
 
@@ -243,7 +245,7 @@ def cd_last_error(sysptr=None) -> str:
 # --- convenience object ----------------------------------------------------------
 
 def make_params(wl, precision=CD_FP64, criterion=CD_CONV_GLOBAL_REL, max_contacts=None, warm_start=1, rotations=1,
-                seed=None, max_sweeps=None, alpha=None, timing=0) -> cd_params:
+                seed=None, max_sweeps=None, alpha=None, timing=0, tile_cells=0, dataflow=0) -> cd_params:
     p = cd_params()
     p.dim = wl.dim
     p.precision = precision
@@ -270,6 +272,8 @@ def make_params(wl, precision=CD_FP64, criterion=CD_CONV_GLOBAL_REL, max_contact
     p.seed = int(wl.seed if seed is None else seed) & (2**64 - 1)
     p.max_contacts = int(max_contacts if max_contacts is not None else max(64, 6 * wl.n))
     p.timing = int(timing)
+    p.tile_cells = int(tile_cells)
+    p.dataflow = int(dataflow)
     return p
 
 

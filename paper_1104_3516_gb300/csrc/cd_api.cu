@@ -93,6 +93,7 @@ static size_t layout(cd_system* s, char* base, CdWork* w)
     size_t scan_max = ncell + 1;
     if (n + 1 > scan_max) scan_max = n + 1;
     if (CD_KMAX * nchunk > scan_max) scan_max = CD_KMAX * nchunk;
+    if ((size_t)s->g.ntiles * CD_KLOCAL + 1 > scan_max) scan_max = (size_t)s->g.ntiles * CD_KLOCAL + 1;
     CdWork t;
     t.ctrl = L.take<CdCtrl>(base, 1);
     t.V = L.take<char>(base, n * vrec);
@@ -129,6 +130,15 @@ static size_t layout(cd_system* s, char* base, CdWork* w)
     t.c_P = L.take<char>(base, cap * (s->p.dim == 2 ? 2 : 4) * real);
     t.partials = L.take<double>(base, 2 * 3 * G);
     t.wpart = L.take<double>(base, 6 * G);
+    const size_t nseg = (size_t)s->g.ntiles * CD_KLOCAL;
+    t.c_tile = L.take<int>(base, cap);
+    t.tile_rank = L.take<int>(base, (size_t)s->g.ntiles);
+    t.tc_off = L.take<int>(base, 9);
+    t.seg_cnt = L.take<int>(base, nseg + 1);
+    t.seg_off = L.take<int>(base, nseg + 1);
+    t.seg_fill = L.take<int>(base, nseg);
+    t.c_need = L.take<int2>(base, cap);
+    t.deg = L.take<int>(base, n);
     if (w) *w = t;
     return (L.off + 255) & ~(size_t)255;
 }
@@ -233,10 +243,12 @@ static cd_status launch_detect_chain(cd_system* s, int timed)
     CD_CUDA(s, cd_launch_detect(s->g, s->w, s->pos, s->radius, s->inv_m, s->inv_I, (int)s->p.warm_start, s->pw,
                                 s->stream, &s->launches));
     if (timed && (st = mark(s)) != CD_OK) return st;
-    CD_CUDA(s, cd_launch_colour(s->g, s->w, s->colour_blocks, (int)s->p.precision, s->pw, s->stream, &s->launches));
+    CD_CUDA(s, cd_launch_colour(s->g, s->w, s->colour_blocks, (int)s->p.precision, s->pw, s->stream, &s->launches,
+                                s->pos));
     k_error_gate<<<1, 1, 0, s->stream>>>(s->w.ctrl);
     ++s->launches;
     CD_CUDA(s, cudaGetLastError());
+    if (s->g.dataflow) CD_CUDA(s, cd_launch_need(s->g, s->w, s->stream, &s->launches));
     return CD_OK;
 }
 
@@ -361,6 +373,29 @@ extern "C" cd_status cd_create_system(const cd_params* params, int64_t n, double
         ncell_total *= g.ncell[k];
     }
     if (ncell_total > 2.0e8) { delete s; return fail(nullptr, CD_ERR_INVALID_ARG, "cell grid too large for the box"); }
+    // tiled order: nt = cells / tile_cells per axis (>= 1, even on a periodic axis)
+    if (p.tile_cells < 0 || p.tile_cells == 1) {
+        delete s;
+        return fail(nullptr, CD_ERR_INVALID_ARG, "tile_cells must be 0 or >= 2");
+    }
+    g.tile_cells = (int)p.tile_cells;
+    g.ntiles = 1;
+    for (int k = 0; k < 3; ++k) {
+        int t = 1;
+        if (k < p.dim && g.tile_cells >= 2) {
+            t = g.ncell[k] / g.tile_cells;
+            if (t < 1) t = 1;
+            if (g.periodic[k] && t > 1 && (t & 1)) t -= 1;
+        }
+        g.ntile[k] = t;
+        g.ntiles *= t;
+    }
+    g.ntc = (g.tile_cells >= 2) ? (1 << p.dim) : 1;
+    g.dataflow = (p.dataflow && g.tile_cells == 0) ? 1 : 0;
+    if (g.tile_cells >= 2 && (double)g.ntiles * CD_KLOCAL > 1.0e8) {
+        delete s;
+        return fail(nullptr, CD_ERR_INVALID_ARG, "too many tiles: raise tile_cells");
+    }
     s->sweep_blocks = cd_sweep_max_blocks((int)p.precision, (int)p.dim, s->num_sms);
     s->colour_blocks = cd_colour_max_blocks(s->num_sms);
     if (s->sweep_blocks <= 0 || s->colour_blocks <= 0) {
@@ -392,6 +427,28 @@ extern "C" cd_status cd_set_workspace(cd_system* s, void* dev_ptr, size_t bytes)
     memset(&h, 0, sizeof h);
     for (int k = 0; k < 6; ++k) h.wall_pos[k] = s->p.wall_pos[k];
     CD_CUDA(s, cudaMemcpyAsync(s->w.ctrl, &h, sizeof h, cudaMemcpyHostToDevice, s->stream));
+    {
+        // tiles in (tile colour, tile) order; colour = parity of the tile coordinates
+        const CdGeom& g = s->g;
+        std::vector<int> rank((size_t)g.ntiles), off(9, 0);
+        std::vector<int> cnt(9, 0);
+        auto colour_of = [&](int t) {
+            int t0 = t % g.ntile[0], t1 = (t / g.ntile[0]) % g.ntile[1], t2 = t / (g.ntile[0] * g.ntile[1]);
+            return (g.ntc > 1) ? ((t0 & 1) | ((t1 & 1) << 1) | ((t2 & 1) << 2)) : 0;
+        };
+        for (int t = 0; t < g.ntiles; ++t) cnt[colour_of(t) + 1]++;
+        for (int c = 0; c < 8; ++c) cnt[c + 1] += cnt[c];
+        for (int c = 0; c <= 8; ++c) off[c] = cnt[c];
+        std::vector<int> fill(9, 0);
+        for (int t = 0; t < g.ntiles; ++t) {
+            int c = colour_of(t);
+            rank[(size_t)t] = off[c] + fill[c]++;
+        }
+        CD_CUDA(s, cudaMemcpyAsync(s->w.tile_rank, rank.data(), sizeof(int) * rank.size(), cudaMemcpyHostToDevice,
+                                   s->stream));
+        CD_CUDA(s, cudaMemcpyAsync(s->w.tc_off, off.data(), sizeof(int) * 9, cudaMemcpyHostToDevice, s->stream));
+        CD_CUDA(s, cudaStreamSynchronize(s->stream));
+    }
     CD_CUDA(s, cd_launch_static(s->g, s->w, s->radius, s->inv_m, s->inv_I, (int)s->p.precision, s->stream,
                                 &s->launches));
     CD_CUDA(s, cudaStreamSynchronize(s->stream));
@@ -422,8 +479,10 @@ extern "C" cd_status cd_set_contacts(cd_system* s, int64_t nc, const int32_t* pa
     k_begin_call<<<1, 1, 0, s->stream>>>(s->w.ctrl, 0);
     CD_CUDA(s, cd_launch_set_contacts(s->g, s->w, s->pos, s->radius, s->inv_m, s->inv_I, (int)nc, pairs, impulses,
                                       s->pw, s->stream, &s->launches));
-    CD_CUDA(s, cd_launch_colour(s->g, s->w, s->colour_blocks, (int)s->p.precision, s->pw, s->stream, &s->launches));
+    CD_CUDA(s, cd_launch_colour(s->g, s->w, s->colour_blocks, (int)s->p.precision, s->pw, s->stream, &s->launches,
+                                s->pos));
     k_error_gate<<<1, 1, 0, s->stream>>>(s->w.ctrl);
+    if (s->g.dataflow) CD_CUDA(s, cd_launch_need(s->g, s->w, s->stream, &s->launches));
     CdCtrl h;
     if ((st = read_ctrl(s, &h)) != CD_OK) return st;
     st = ctrl_status(s, h);

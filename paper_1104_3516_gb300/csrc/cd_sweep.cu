@@ -234,26 +234,34 @@ __device__ __forceinline__ void load_rec(const CdGeom& g, const CdWork& w, int p
     }
 }
 
-template <typename T>
-__device__ __forceinline__ T clampT(T x, T lo, T hi) { return x < lo ? lo : (x > hi ? hi : x); }
-
-// 2D: P_n = max(0, P_n,old - m_n (b + u_n)); P_t = clamp(P_t,old - m_t u_t, +-mu P_n)
-template <typename T>
-__device__ __forceinline__ UpdOut apply2d(const CdGeom& g, const CdWork& w, int pos, const Rec<2, T>& r,
-                                          bool apply_only, int crit, double alpha, double ravg_prev)
+// max(x, 0) and the projection of x onto [-lim, lim] (lim >= 0).  For FP64
+// they are done on the bit patterns with integer instructions (non-negative
+// doubles order like their 64-bit integer images), which keeps them off the
+// narrow FP64 pipe; the results are exactly those of the comparisons.
+__device__ __forceinline__ double pos_part(double x)
 {
-    typedef typename Vec<T>::V4 T4;
-    typedef typename Vec<T>::V2 T2;
-    T4* V = (T4*)w.V;
-    const bool wall = r.ab.y >= g.n;
-    T4 va = V[r.ab.x];
-    T4 vb;
-    if (!wall) {
-        vb = V[r.ab.y];
-    } else {
-        int k = r.ab.y - g.n;
-        vb.x = (T)g.wall_vel[3 * k]; vb.y = (T)g.wall_vel[3 * k + 1]; vb.z = (T)0; vb.w = (T)0;
-    }
+    long long b = __double_as_longlong(x);
+    return b < 0 ? 0.0 : x;
+}
+__device__ __forceinline__ float pos_part(float x) { return x > 0.0f ? x : 0.0f; }
+
+__device__ __forceinline__ double clamp_sym(double x, double lim)
+{
+    unsigned long long bx = (unsigned long long)__double_as_longlong(x);
+    unsigned long long bl = (unsigned long long)__double_as_longlong(lim);
+    unsigned long long ax = bx & 0x7FFFFFFFFFFFFFFFULL;
+    return ax > bl ? __longlong_as_double((long long)(bl | (bx & 0x8000000000000000ULL))) : x;
+}
+__device__ __forceinline__ float clamp_sym(float x, float lim) { return x < -lim ? -lim : (x > lim ? lim : x); }
+
+// 2D: P_n = max(0, P_n,old - m_n (b + u_n)); P_t = clamp(P_t,old - m_t u_t, +-mu P_n).
+// The core works on the two bodies' velocity records wherever they live
+// (global memory or a tile's shared-memory table).
+template <typename T>
+__device__ __forceinline__ UpdOut core2d(const CdGeom& g, const Rec<2, T>& r, typename Vec<T>::V4& va,
+                                         typename Vec<T>::V4& vb, bool wall, bool apply_only, int crit,
+                                         double alpha, double ravg_prev, typename Vec<T>::V2& Pnew)
+{
     const T nx = r.geo.x, ny = r.geo.y;
     T Pn, Pt, dPn, dPt;
     if (apply_only) {
@@ -264,54 +272,64 @@ __device__ __forceinline__ UpdOut apply2d(const CdGeom& g, const CdWork& w, int 
         T dvx = vb.x - va.x, dvy = vb.y - va.y;
         T un = dvx * nx + dvy * ny;
         T ut = (dvy * nx - dvx * ny) - (r.sa.y * va.z + r.sb.y * vb.z);
-        Pn = r.P.x - mn * (b + un);
-        Pn = Pn > (T)0 ? Pn : (T)0;
+        Pn = pos_part(r.P.x - mn * (b + un));
         T lim = (T)g.mu * Pn;
-        Pt = clampT(r.P.y - r.mt * ut, -lim, lim);
+        Pt = clamp_sym(r.P.y - r.mt * ut, lim);
         dPn = Pn - r.P.x; dPt = Pt - r.P.y;
     }
     T dPx = dPn * nx - dPt * ny, dPy = dPn * ny + dPt * nx;
     va.x -= r.sa.x * dPx; va.y -= r.sa.x * dPy; va.z -= r.sa.z * dPt;
-    V[r.ab.x] = va;
     if (!wall) {
         vb.x += r.sb.x * dPx; vb.y += r.sb.x * dPy; vb.z -= r.sb.z * dPt;
-        V[r.ab.y] = vb;
     }
+    Pnew.x = Pn; Pnew.y = Pt;
     UpdOut o;
     double pn = (double)Pn, pt = (double)Pt;
     o.pabs = sqrt(pn * pn + pt * pt);
     o.rel_ok = 0; o.bad = 0;
-    if (!apply_only) {
-        T2 Pnew; Pnew.x = Pn; Pnew.y = Pt;
-        ((T2*)w.c_P)[pos] = Pnew;
-        if (crit == CD_CONV_LOCAL) {
-            double d0 = (double)dPn, d1 = (double)dPt;
-            double s0 = pn + (double)r.P.x, s1 = pt + (double)r.P.y;
-            double d2 = d0 * d0 + d1 * d1, s2 = s0 * s0 + s1 * s1;
-            o.rel_ok = d2 < alpha * s2;
-            o.bad = !o.rel_ok && !(d2 <= alpha * ravg_prev * ravg_prev);
-        }
+    if (!apply_only && crit == CD_CONV_LOCAL) {
+        double d0 = (double)dPn, d1 = (double)dPt;
+        double s0 = pn + (double)r.P.x, s1 = pt + (double)r.P.y;
+        double d2 = d0 * d0 + d1 * d1, s2 = s0 * s0 + s1 * s1;
+        o.rel_ok = d2 < alpha * s2;
+        o.bad = !o.rel_ok && !(d2 <= alpha * ravg_prev * ravg_prev);
     }
+    return o;
+}
+
+template <typename T>
+__device__ __forceinline__ void wall_vel2(const CdGeom& g, int k, typename Vec<T>::V4& vb)
+{
+    vb.x = (T)g.wall_vel[3 * k]; vb.y = (T)g.wall_vel[3 * k + 1]; vb.z = (T)0; vb.w = (T)0;
+}
+
+template <typename T>
+__device__ __forceinline__ UpdOut apply2d(const CdGeom& g, const CdWork& w, int pos, const Rec<2, T>& r,
+                                          bool apply_only, int crit, double alpha, double ravg_prev)
+{
+    typedef typename Vec<T>::V4 T4;
+    typedef typename Vec<T>::V2 T2;
+    T4* V = (T4*)w.V;
+    const bool wall = r.ab.y >= g.n;
+    T4 va = V[r.ab.x];
+    T4 vb;
+    if (!wall) vb = V[r.ab.y];
+    else wall_vel2<T>(g, r.ab.y - g.n, vb);
+    T2 Pnew;
+    UpdOut o = core2d<T>(g, r, va, vb, wall, apply_only, crit, alpha, ravg_prev, Pnew);
+    V[r.ab.x] = va;
+    if (!wall) V[r.ab.y] = vb;
+    if (!apply_only) ((T2*)w.c_P)[pos] = Pnew;
     return o;
 }
 
 // 3D: the same with the tangential impulse a vector, scaled onto the cone.
 template <typename T>
-__device__ __forceinline__ UpdOut apply3d(const CdGeom& g, const CdWork& w, int pos, const Rec<3, T>& r,
-                                          bool apply_only, int crit, double alpha, double ravg_prev)
+__device__ __forceinline__ UpdOut core3d(const CdGeom& g, const Rec<3, T>& r, typename Vec<T>::V4& va,
+                                         typename Vec<T>::V4& wa, typename Vec<T>::V4& vb, typename Vec<T>::V4& wb,
+                                         bool wall, bool apply_only, int crit, double alpha, double ravg_prev,
+                                         typename Vec<T>::V4& Pnew)
 {
-    typedef typename Vec<T>::V4 T4;
-    T4* V = (T4*)w.V;
-    const bool wall = r.ab.y >= g.n;
-    T4 va = V[2 * r.ab.x], wa = V[2 * r.ab.x + 1];
-    T4 vb, wb;
-    if (!wall) {
-        vb = V[2 * r.ab.y]; wb = V[2 * r.ab.y + 1];
-    } else {
-        int k = r.ab.y - g.n;
-        vb.x = (T)g.wall_vel[3 * k]; vb.y = (T)g.wall_vel[3 * k + 1]; vb.z = (T)g.wall_vel[3 * k + 2]; vb.w = (T)0;
-        wb.x = wb.y = wb.z = wb.w = (T)0;
-    }
     const T nx = r.geo.x, ny = r.geo.y, nz = r.geo.z;
     T Pn, Ptx, Pty, Ptz, dPn, dtx, dty, dtz;
     if (apply_only) {
@@ -326,8 +344,7 @@ __device__ __forceinline__ UpdOut apply3d(const CdGeom& g, const CdWork& w, int 
         T gz = (vb.z - va.z) - (lx * ny - ly * nx);
         T un = gx * nx + gy * ny + gz * nz;
         T tx = gx - un * nx, ty = gy - un * ny, tz = gz - un * nz;
-        Pn = r.P.x - mn * (b + un);
-        Pn = Pn > (T)0 ? Pn : (T)0;
+        Pn = pos_part(r.P.x - mn * (b + un));
         Ptx = r.P.y - mt * tx; Pty = r.P.z - mt * ty; Ptz = r.P.w - mt * tz;
         T lim = (T)g.mu * Pn;
         T q2 = Ptx * Ptx + Pty * Pty + Ptz * Ptz;
@@ -342,28 +359,49 @@ __device__ __forceinline__ UpdOut apply3d(const CdGeom& g, const CdWork& w, int 
     T cx = ny * dz - nz * dy, cy = nz * dx - nx * dz, cz = nx * dy - ny * dx;
     va.x -= r.sa.x * dx; va.y -= r.sa.x * dy; va.z -= r.sa.x * dz;
     wa.x -= r.sa.z * cx; wa.y -= r.sa.z * cy; wa.z -= r.sa.z * cz;
-    V[2 * r.ab.x] = va; V[2 * r.ab.x + 1] = wa;
     if (!wall) {
         vb.x += r.sb.x * dx; vb.y += r.sb.x * dy; vb.z += r.sb.x * dz;
         wb.x -= r.sb.z * cx; wb.y -= r.sb.z * cy; wb.z -= r.sb.z * cz;
-        V[2 * r.ab.y] = vb; V[2 * r.ab.y + 1] = wb;
     }
+    Pnew.x = Pn; Pnew.y = Ptx; Pnew.z = Pty; Pnew.w = Ptz;
     UpdOut o;
     double pn = (double)Pn, px = (double)Ptx, py = (double)Pty, pz = (double)Ptz;
     o.pabs = sqrt(pn * pn + px * px + py * py + pz * pz);
     o.rel_ok = 0; o.bad = 0;
-    if (!apply_only) {
-        T4 Pnew; Pnew.x = Pn; Pnew.y = Ptx; Pnew.z = Pty; Pnew.w = Ptz;
-        ((T4*)w.c_P)[pos] = Pnew;
-        if (crit == CD_CONV_LOCAL) {
-            double d0 = (double)dPn, d1 = (double)dtx, d2_ = (double)dty, d3 = (double)dtz;
-            double s0 = pn + (double)r.P.x, s1 = px + (double)r.P.y, s2_ = py + (double)r.P.z, s3 = pz + (double)r.P.w;
-            double d2 = d0 * d0 + d1 * d1 + d2_ * d2_ + d3 * d3;
-            double s2 = s0 * s0 + s1 * s1 + s2_ * s2_ + s3 * s3;
-            o.rel_ok = d2 < alpha * s2;
-            o.bad = !o.rel_ok && !(d2 <= alpha * ravg_prev * ravg_prev);
-        }
+    if (!apply_only && crit == CD_CONV_LOCAL) {
+        double d0 = (double)dPn, d1 = (double)dtx, d2_ = (double)dty, d3 = (double)dtz;
+        double s0 = pn + (double)r.P.x, s1 = px + (double)r.P.y, s2_ = py + (double)r.P.z, s3 = pz + (double)r.P.w;
+        double d2 = d0 * d0 + d1 * d1 + d2_ * d2_ + d3 * d3;
+        double s2 = s0 * s0 + s1 * s1 + s2_ * s2_ + s3 * s3;
+        o.rel_ok = d2 < alpha * s2;
+        o.bad = !o.rel_ok && !(d2 <= alpha * ravg_prev * ravg_prev);
     }
+    return o;
+}
+
+template <typename T>
+__device__ __forceinline__ void wall_vel3(const CdGeom& g, int k, typename Vec<T>::V4& vb, typename Vec<T>::V4& wb)
+{
+    vb.x = (T)g.wall_vel[3 * k]; vb.y = (T)g.wall_vel[3 * k + 1]; vb.z = (T)g.wall_vel[3 * k + 2]; vb.w = (T)0;
+    wb.x = wb.y = wb.z = wb.w = (T)0;
+}
+
+template <typename T>
+__device__ __forceinline__ UpdOut apply3d(const CdGeom& g, const CdWork& w, int pos, const Rec<3, T>& r,
+                                          bool apply_only, int crit, double alpha, double ravg_prev)
+{
+    typedef typename Vec<T>::V4 T4;
+    T4* V = (T4*)w.V;
+    const bool wall = r.ab.y >= g.n;
+    T4 va = V[2 * r.ab.x], wa = V[2 * r.ab.x + 1];
+    T4 vb, wb;
+    if (!wall) { vb = V[2 * r.ab.y]; wb = V[2 * r.ab.y + 1]; }
+    else wall_vel3<T>(g, r.ab.y - g.n, vb, wb);
+    T4 Pnew;
+    UpdOut o = core3d<T>(g, r, va, wa, vb, wb, wall, apply_only, crit, alpha, ravg_prev, Pnew);
+    V[2 * r.ab.x] = va; V[2 * r.ab.x + 1] = wa;
+    if (!wall) { V[2 * r.ab.y] = vb; V[2 * r.ab.y + 1] = wb; }
+    if (!apply_only) ((T4*)w.c_P)[pos] = Pnew;
     return o;
 }
 
@@ -398,6 +436,69 @@ __device__ __forceinline__ void colour_phase(const CdGeom& g, const CdWork& w, c
     if (knext >= 0) {
         int q = s_off[knext] + tid;
         if (q < s_off[knext + 1]) load_rec<DIM, T>(g, w, q, nxt);
+    }
+}
+
+// Epilogue shared by both sweep kernels: impulses back to key order (FP64),
+// wall forces and the solve statistics.
+template <int DIM, typename T>
+__device__ __forceinline__ void finish_solve(const CdGeom& g, const CdWork& w, int nc, int nb, int tid, int stride,
+                                             unsigned long long& epoch, int sweeps, int converged, double resid,
+                                             double ravg, double (*s_red)[3], double& s_bc)
+{
+    CdCtrl* ctrl = w.ctrl;
+    double wsum[6] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0};
+    typedef typename Vec<T>::V4 T4;
+    typedef typename Vec<T>::V2 T2;
+    for (int p = tid; p < nc; p += stride) {
+        int c = w.perm[p];
+        int2 ab = w.c_ab[p];
+        double pn;
+        if (DIM == 2) {
+            T2 P = ((const T2*)w.c_P)[p];
+            pn = (double)P.x;
+            w.Pk[2 * c] = (double)P.x;
+            w.Pk[2 * c + 1] = (double)P.y;
+        } else {
+            T4 P = ((const T4*)w.c_P)[p];
+            pn = (double)P.x;
+            w.Pk[4 * c] = (double)P.x;
+            w.Pk[4 * c + 1] = (double)P.y;
+            w.Pk[4 * c + 2] = (double)P.z;
+            w.Pk[4 * c + 3] = (double)P.w;
+        }
+        if (ab.y >= g.n) {
+            int k = ab.y - g.n;
+#pragma unroll
+            for (int q = 0; q < 6; ++q) if (q == k) wsum[q] += pn;
+        }
+    }
+    {
+        double a[3] = {wsum[0], wsum[1], wsum[2]};
+        block_sum<3>(a, s_red);
+        double b3[3] = {wsum[3], wsum[4], wsum[5]};
+        block_sum<3>(b3, s_red);
+        if (threadIdx.x == 0) {
+            for (int q = 0; q < 3; ++q) w.wpart[q * nb + blockIdx.x] = a[q];
+            for (int q = 0; q < 3; ++q) w.wpart[(3 + q) * nb + blockIdx.x] = b3[q];
+        }
+    }
+    if (!cd_grid_sync(ctrl, nb, epoch)) return;
+    if (blockIdx.x == 0) {
+        double wf[6];
+        for (int q = 0; q < 6; ++q) wf[q] = grid_total(w.wpart + q * nb, nb, &s_bc);
+        if (threadIdx.x == 0) {
+            for (int q = 0; q < 6; ++q) ctrl->wall_force[q] = wf[q] / g.dt;
+            ctrl->sweeps = sweeps;
+            ctrl->converged = converged;
+            ctrl->residual = resid;
+            ctrl->r_avg = ravg;
+            ctrl->steps_done += 1;
+            ctrl->total_sweeps += sweeps;
+            ctrl->total_updates += (long long)sweeps * (long long)nc;
+            if (sweeps > ctrl->max_sweeps_step) ctrl->max_sweeps_step = sweeps;
+            if (!converged) ctrl->n_not_conv += 1;
+        }
     }
 }
 
@@ -481,60 +582,428 @@ k_sweep(CdGeom g, CdWork w, int crit, double alpha, int max_sweeps)
         }
     }
 
-    // impulses back to key order (FP64) and wall forces
-    double wsum[6] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0};
+    finish_solve<DIM, T>(g, w, nc, nb, tid, stride, epoch, sweeps, converged, resid, ravg, s_red, s_bc);
+}
+
+// ---------------------------------------------------------------------------
+// Dataflow schedule.  Every particle's first velocity record carries, in its
+// pad word, the number of contact updates applied to it so far in this solve.
+// In phase s (0 = starting impulses, then one per sweep) the contact at
+// colour position p may update body q once q has received need_q(p) +
+// s * deg(q) updates: exactly those that precede p in the colour order (the
+// particle's contacts of lower colour in this phase and all of its updates in
+// earlier phases).  The thread waits with acquire loads (bounded by
+// %globaltimer), updates, stores the velocities and publishes the count + 1
+// with a release store.  No two threads ever hold the same particle at once,
+// the update order equals the barrier schedule's, and the results are
+// bit-identical to it; colours overlap instead of waiting for the whole grid.
+// Progress: the earliest unfinished contact of the phase always has its
+// counts ready, and each thread walks its contacts in colour order.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ int ld_acquire_s32(const int* p)
+{
+    int v;
+    asm volatile("ld.acquire.gpu.global.s32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+
+__device__ __forceinline__ void st_release_s32(int* p, int v)
+{
+    asm volatile("st.release.gpu.global.s32 [%0], %1;" :: "l"(p), "r"(v) : "memory");
+}
+
+template <int DIM, typename T>
+__device__ __forceinline__ int* count_ptr(void* V, int i)
+{
+    typedef typename Vec<T>::V4 T4;
+    return reinterpret_cast<int*>(reinterpret_cast<char*>((T4*)V + (DIM == 2 ? i : 2 * i)) + 3 * sizeof(T));
+}
+
+// Waits until *cp >= need; false if the wait ran out or another block failed.
+__device__ __forceinline__ bool wait_count(const int* cp, int need, CdCtrl* ctrl)
+{
+    if (ld_acquire_s32(cp) >= need) return true;
+    unsigned long long t0 = cd_globaltimer();
+    unsigned spins = 0;
+    while (ld_acquire_s32(cp) < need) {
+        if ((++spins & 63u) == 0u) {
+            if (cd_ld_volatile_int(&ctrl->error) != CDE_NONE) return false;
+            if (cd_globaltimer() - t0 > CD_WAIT_NS) {
+                atomicCAS(&ctrl->error, CDE_NONE, CDE_TIMEOUT);
+                return false;
+            }
+        }
+        __nanosleep(32);
+    }
+    return true;
+}
+
+// Stores the first three components of a velocity record, leaving the count.
+template <typename T>
+__device__ __forceinline__ void store_xyz(typename Vec<T>::V4* dst, const typename Vec<T>::V4& v)
+{
+    typedef typename Vec<T>::V2 T2;
+    T2 xy;
+    xy.x = v.x; xy.y = v.y;
+    *reinterpret_cast<T2*>(dst) = xy;
+    reinterpret_cast<T*>(dst)[2] = v.z;
+}
+
+template <int DIM, typename T>
+__device__ __forceinline__ bool flow_update(const CdGeom& g, const CdWork& w, int p, int phase, bool apply_only,
+                                            int crit, double alpha, double ravg_prev, const Rec<DIM, T>& r,
+                                            double (&acc)[3])
+{
     typedef typename Vec<T>::V4 T4;
     typedef typename Vec<T>::V2 T2;
-    for (int p = tid; p < nc; p += stride) {
-        int c = w.perm[p];
-        int2 ab = w.c_ab[p];
-        double pn;
-        if (DIM == 2) {
-            T2 P = ((const T2*)w.c_P)[p];
-            pn = (double)P.x;
-            w.Pk[2 * c] = (double)P.x;
-            w.Pk[2 * c + 1] = (double)P.y;
-        } else {
-            T4 P = ((const T4*)w.c_P)[p];
-            pn = (double)P.x;
-            w.Pk[4 * c] = (double)P.x;
-            w.Pk[4 * c + 1] = (double)P.y;
-            w.Pk[4 * c + 2] = (double)P.z;
-            w.Pk[4 * c + 3] = (double)P.w;
-        }
-        if (ab.y >= g.n) {
-            int k = ab.y - g.n;
-#pragma unroll
-            for (int q = 0; q < 6; ++q) if (q == k) wsum[q] += pn;
+    CdCtrl* ctrl = w.ctrl;
+    T4* V = (T4*)w.V;
+    const bool wall = r.ab.y >= g.n;
+    const int2 nd = w.c_need[p];
+    const int ea = nd.x + phase * w.deg[r.ab.x];
+    const int eb = wall ? 0 : nd.y + phase * w.deg[r.ab.y];
+    int* ca = count_ptr<DIM, T>(w.V, r.ab.x);
+    int* cb = wall ? nullptr : count_ptr<DIM, T>(w.V, r.ab.y);
+    if (!wait_count(ca, ea, ctrl)) return false;
+    if (!wall && !wait_count(cb, eb, ctrl)) return false;
+    UpdOut o;
+    if constexpr (DIM == 2) {
+        T4 va = V[r.ab.x], vb;
+        if (!wall) vb = V[r.ab.y];
+        else wall_vel2<T>(g, r.ab.y - g.n, vb);
+        T2 Pnew;
+        o = core2d<T>(g, r, va, vb, wall, apply_only, crit, alpha, ravg_prev, Pnew);
+        store_xyz<T>(V + r.ab.x, va);
+        if (!wall) store_xyz<T>(V + r.ab.y, vb);
+        if (!apply_only) ((T2*)w.c_P)[p] = Pnew;
+    } else {
+        T4 va = V[2 * r.ab.x], wa = V[2 * r.ab.x + 1], vb, wb;
+        if (!wall) { vb = V[2 * r.ab.y]; wb = V[2 * r.ab.y + 1]; }
+        else wall_vel3<T>(g, r.ab.y - g.n, vb, wb);
+        T4 Pnew;
+        o = core3d<T>(g, r, va, wa, vb, wb, wall, apply_only, crit, alpha, ravg_prev, Pnew);
+        store_xyz<T>(V + 2 * r.ab.x, va);
+        V[2 * r.ab.x + 1] = wa;
+        if (!wall) { store_xyz<T>(V + 2 * r.ab.y, vb); V[2 * r.ab.y + 1] = wb; }
+        if (!apply_only) ((T4*)w.c_P)[p] = Pnew;
+    }
+    st_release_s32(ca, ea + 1);
+    if (!wall) st_release_s32(cb, eb + 1);
+    acc[0] += o.pabs; acc[1] += (double)o.rel_ok; acc[2] += (double)o.bad;
+    return true;
+}
+
+template <int DIM, typename T>
+__global__ void __launch_bounds__(CD_SWEEP_THREADS, 1)
+k_sweep_flow(CdGeom g, CdWork w, int crit, double alpha, int max_sweeps)
+{
+    __shared__ double s_red[CD_SWEEP_THREADS / 32][3];
+    __shared__ double s_bc;
+    __shared__ int s_fail;
+    CdCtrl* ctrl = w.ctrl;
+    if (ctrl->skip) return;
+    const int nc = ctrl->nc;
+    const int nb = gridDim.x;
+    const int tid = blockIdx.x * blockDim.x + threadIdx.x;
+    const int stride = gridDim.x * blockDim.x;
+    unsigned long long epoch = 0;
+    if (threadIdx.x == 0) s_fail = 0;
+    __syncthreads();
+
+    int sweeps = 0, converged = (nc == 0);
+    double resid = 0.0, ravg = 0.0, ravg_prev = 0.0;
+    if (nc > 0) {
+        for (int phase = 0; phase <= max_sweeps && !converged; ++phase) {
+            const bool apply_only = (phase == 0);
+            double a3[3] = {0.0, 0.0, 0.0};
+            bool ok = true;
+            for (int p = tid; p < nc && ok; p += stride) {
+                Rec<DIM, T> r;
+                load_rec<DIM, T>(g, w, p, r);
+                ok = flow_update<DIM, T>(g, w, p, phase, apply_only, crit, alpha, ravg_prev, r, a3);
+            }
+            if (!ok) s_fail = 1;
+            const int buf = (phase & 1);
+            double* part = w.partials + (size_t)buf * 3 * nb;
+            block_sum<3>(a3, s_red);
+            if (threadIdx.x == 0) {
+                part[blockIdx.x] = a3[0];
+                part[nb + blockIdx.x] = a3[1];
+                part[2 * nb + blockIdx.x] = a3[2];
+            }
+            if (s_fail) return;
+            if (!cd_grid_sync(ctrl, nb, epoch)) return;
+            ravg = grid_total(part, nb, &s_bc) / (double)nc;
+            if (apply_only) {
+                ravg_prev = ravg;
+                continue;
+            }
+            ++sweeps;
+            double den = ravg + ravg_prev;
+            if (crit == CD_CONV_GLOBAL_REL) {
+                resid = (den > 0.0) ? fabs(ravg - ravg_prev) / den : 0.0;
+                converged = resid < alpha;
+            } else if (crit == CD_CONV_GLOBAL_SQ) {
+                double q = (den > 0.0) ? (ravg - ravg_prev) / den : 0.0;
+                resid = q * q;
+                converged = resid < alpha;
+            } else if (crit == CD_CONV_LOCAL) {
+                double nrel = grid_total(part + nb, nb, &s_bc);
+                double nbad = grid_total(part + 2 * nb, nb, &s_bc);
+                resid = (double)(nc - (long long)nrel) / (double)nc;
+                converged = (10.0 * nrel >= 9.0 * (double)nc) && nbad == 0.0;
+            } else {
+                resid = (den > 0.0) ? fabs(ravg - ravg_prev) / den : 0.0;
+                converged = 0;
+            }
+            ravg_prev = ravg;
         }
     }
-    {
-        double a[3] = {wsum[0], wsum[1], wsum[2]};
-        block_sum<3>(a, s_red);
-        double b3[3] = {wsum[3], wsum[4], wsum[5]};
-        block_sum<3>(b3, s_red);
-        if (threadIdx.x == 0) {
-            for (int q = 0; q < 3; ++q) w.wpart[q * nb + blockIdx.x] = a[q];
-            for (int q = 0; q < 3; ++q) w.wpart[(3 + q) * nb + blockIdx.x] = b3[q];
+    finish_solve<DIM, T>(g, w, nc, nb, tid, stride, epoch, sweeps, converged, resid, ravg, s_red, s_bc);
+}
+
+// ---------------------------------------------------------------------------
+// Tiled order: one block per tile at a time.  The particles the tile's
+// contacts touch (its own and a one-cell halo) are gathered into a
+// shared-memory table (particle id -> slot, bounded linear probing) and the
+// tile's contact records are staged in shared memory, the tile's colours run
+// with block barriers only, and the table is written back.
+// Tiles of one tile colour share no particle, so blocks never race; a grid
+// barrier separates the tile colours.  A tile whose particles overflow the
+// table is processed through global memory instead (same order, same result).
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ unsigned ht_hash(int id)
+{
+    return ((unsigned)id * 2654435761u) >> (32 - 10);   // CD_HT = 1024 slots
+}
+
+__device__ __forceinline__ int ht_insert(int* keys, int id)
+{
+    unsigned h = ht_hash(id);
+    for (int probe = 0; probe < CD_HT; ++probe) {
+        int old = atomicCAS(&keys[h], -1, id);
+        if (old == -1 || old == id) return (int)h;
+        h = (h + 1) & (CD_HT - 1);
+    }
+    return -1;
+}
+
+#define CD_TREC 1024   // contact records of one tile staged in shared memory
+
+template <int DIM, typename T>
+struct TileSmem {
+    typedef typename Vec<T>::V4 T4;
+    typedef typename Vec<T>::V2 T2;
+    typedef typename std::conditional<DIM == 2, T, T2>::type TM;   // m_t (2D) or (m_n, m_t)
+    typedef typename std::conditional<DIM == 2, T2, T4>::type TP;  // impulse
+    int keys[CD_HT];
+    T4 V[CD_HT * (DIM == 2 ? 1 : 2)];
+    T4 S[CD_HT];
+    int2 ab[CD_TREC];
+    int2 slot[CD_TREC];
+    T4 geo[CD_TREC];
+    TM m[CD_TREC];
+    TP P[CD_TREC];
+    int off[CD_KLOCAL + 1];
+    int ovf;
+};
+
+template <int DIM, typename T>
+__device__ __forceinline__ UpdOut apply_staged(const CdGeom& g, const CdWork& w, int p, int i, TileSmem<DIM, T>& sm,
+                                               bool apply_only, int crit, double alpha, double ravg_prev)
+{
+    typedef typename Vec<T>::V4 T4;
+    typedef typename Vec<T>::V2 T2;
+    Rec<DIM, T> r;
+    r.ab = sm.ab[i];
+    r.geo = sm.geo[i];
+    const bool wall = r.ab.y >= g.n;
+    const int ia = sm.slot[i].x;
+    const int ib = sm.slot[i].y;
+    r.sa = sm.S[ia];
+    if (!wall) r.sb = sm.S[ib];
+    else { r.sb.x = (T)0; r.sb.y = (T)0; r.sb.z = (T)0; r.sb.w = (T)0; }
+    UpdOut o;
+    if constexpr (DIM == 2) {
+        r.mt = sm.m[i];
+        r.P = sm.P[i];
+        T4 va = sm.V[ia], vb;
+        if (!wall) vb = sm.V[ib];
+        else wall_vel2<T>(g, r.ab.y - g.n, vb);
+        T2 Pnew;
+        o = core2d<T>(g, r, va, vb, wall, apply_only, crit, alpha, ravg_prev, Pnew);
+        sm.V[ia] = va;
+        if (!wall) sm.V[ib] = vb;
+        if (!apply_only) ((T2*)w.c_P)[p] = Pnew;
+    } else {
+        r.m = sm.m[i];
+        r.P = sm.P[i];
+        T4 va = sm.V[2 * ia], wa = sm.V[2 * ia + 1], vb, wb;
+        if (!wall) { vb = sm.V[2 * ib]; wb = sm.V[2 * ib + 1]; }
+        else wall_vel3<T>(g, r.ab.y - g.n, vb, wb);
+        T4 Pnew;
+        o = core3d<T>(g, r, va, wa, vb, wb, wall, apply_only, crit, alpha, ravg_prev, Pnew);
+        sm.V[2 * ia] = va; sm.V[2 * ia + 1] = wa;
+        if (!wall) { sm.V[2 * ib] = vb; sm.V[2 * ib + 1] = wb; }
+        if (!apply_only) ((T4*)w.c_P)[p] = Pnew;
+    }
+    return o;
+}
+
+template <int DIM, typename T>
+__device__ __forceinline__ void process_tile(const CdGeom& g, const CdWork& w, int rank, TileSmem<DIM, T>& sm,
+                                             bool apply_only, int crit, double alpha, double ravg_prev,
+                                             double (&acc)[3])
+{
+    typedef typename Vec<T>::V4 T4;
+    typedef typename TileSmem<DIM, T>::TM TM;
+    typedef typename TileSmem<DIM, T>::TP TP;
+    const int base = rank * CD_KLOCAL;
+    const int bd = blockDim.x;
+    for (int k = threadIdx.x; k <= CD_KLOCAL; k += bd) sm.off[k] = w.seg_off[base + k];
+    for (int i = threadIdx.x; i < CD_HT; i += bd) sm.keys[i] = -1;
+    if (threadIdx.x == 0) sm.ovf = 0;
+    __syncthreads();
+    const int c0 = sm.off[0], c1 = sm.off[CD_KLOCAL];
+    if (c0 == c1) {
+        __syncthreads();
+        return;
+    }
+    if (c1 - c0 > CD_TREC) {
+        if (threadIdx.x == 0) sm.ovf = 1;
+    } else {
+        // contact records of the tile and their particles' table slots
+        for (int p = c0 + threadIdx.x; p < c1; p += bd) {
+            const int i = p - c0;
+            int2 ab = w.c_ab[p];
+            sm.ab[i] = ab;
+            sm.geo[i] = ((const T4*)w.c_geo)[p];
+            sm.m[i] = ((const TM*)w.c_m)[p];
+            sm.P[i] = ((const TP*)w.c_P)[p];
+            int ia = ht_insert(sm.keys, ab.x);
+            int ib = (ab.y < g.n) ? ht_insert(sm.keys, ab.y) : 0;
+            if (ia < 0 || ib < 0) sm.ovf = 1;
+            sm.slot[i] = make_int2(ia, ib);
         }
     }
-    if (!cd_grid_sync(ctrl, nb, epoch)) return;
-    if (blockIdx.x == 0) {
-        double wf[6];
-        for (int q = 0; q < 6; ++q) wf[q] = grid_total(w.wpart + q * nb, nb, &s_bc);
-        if (threadIdx.x == 0) {
-            for (int q = 0; q < 6; ++q) ctrl->wall_force[q] = wf[q] / g.dt;
-            ctrl->sweeps = sweeps;
-            ctrl->converged = converged;
-            ctrl->residual = resid;
-            ctrl->r_avg = ravg;
-            ctrl->steps_done += 1;
-            ctrl->total_sweeps += sweeps;
-            ctrl->total_updates += (long long)sweeps * (long long)nc;
-            if (sweeps > ctrl->max_sweeps_step) ctrl->max_sweeps_step = sweeps;
-            if (!converged) ctrl->n_not_conv += 1;
+    __syncthreads();
+    const bool staged = (sm.ovf == 0);
+    const T4* Vg = (const T4*)w.V;
+    const T4* Sg = (const T4*)w.S;
+    if (staged) {
+        for (int i = threadIdx.x; i < CD_HT; i += bd) {
+            int id = sm.keys[i];
+            if (id >= 0) {
+                if (DIM == 2) sm.V[i] = Vg[id];
+                else { sm.V[2 * i] = Vg[2 * id]; sm.V[2 * i + 1] = Vg[2 * id + 1]; }
+                sm.S[i] = Sg[id];
+            }
+        }
+        __syncthreads();
+    }
+    for (int lc = 0; lc < CD_KLOCAL; ++lc) {
+        const int s0 = sm.off[lc], s1 = sm.off[lc + 1];
+        if (s0 == s1) continue;
+        for (int p = s0 + threadIdx.x; p < s1; p += bd) {
+            UpdOut o;
+            if (staged) {
+                o = apply_staged<DIM, T>(g, w, p, p - c0, sm, apply_only, crit, alpha, ravg_prev);
+            } else {
+                Rec<DIM, T> r;
+                load_rec<DIM, T>(g, w, p, r);
+                o = apply_rec<DIM, T>(g, w, p, r, apply_only, crit, alpha, ravg_prev);
+            }
+            acc[0] += o.pabs; acc[1] += (double)o.rel_ok; acc[2] += (double)o.bad;
+        }
+        __syncthreads();
+    }
+    if (staged) {
+        T4* Vw = (T4*)w.V;
+        for (int i = threadIdx.x; i < CD_HT; i += bd) {
+            int id = sm.keys[i];
+            if (id >= 0) {
+                if (DIM == 2) Vw[id] = sm.V[i];
+                else { Vw[2 * id] = sm.V[2 * i]; Vw[2 * id + 1] = sm.V[2 * i + 1]; }
+            }
         }
     }
+    __syncthreads();
+}
+
+template <int DIM, typename T>
+__global__ void __launch_bounds__(CD_SWEEP_THREADS, 1)
+k_sweep_tiled(CdGeom g, CdWork w, int crit, double alpha, int max_sweeps)
+{
+    extern __shared__ __align__(16) unsigned char smraw[];
+    TileSmem<DIM, T>& sm = *reinterpret_cast<TileSmem<DIM, T>*>(smraw);
+    __shared__ int s_tc[9];
+    __shared__ double s_red[CD_SWEEP_THREADS / 32][3];
+    __shared__ double s_bc;
+    CdCtrl* ctrl = w.ctrl;
+    if (ctrl->skip) return;
+    const int nc = ctrl->nc;
+    const int nb = gridDim.x;
+    const int tid = blockIdx.x * blockDim.x + threadIdx.x;
+    const int stride = gridDim.x * blockDim.x;
+    unsigned long long epoch = 0;
+    if (threadIdx.x < 9) s_tc[threadIdx.x] = w.tc_off[threadIdx.x];
+    __syncthreads();
+
+    int sweeps = 0, converged = (nc == 0);
+    double resid = 0.0, ravg = 0.0, ravg_prev = 0.0;
+    if (nc > 0) {
+        double acc[3] = {0.0, 0.0, 0.0};
+        for (int tc = 0; tc < g.ntc; ++tc) {
+            for (int rk = s_tc[tc] + blockIdx.x; rk < s_tc[tc + 1]; rk += nb)
+                process_tile<DIM, T>(g, w, rk, sm, true, crit, alpha, 0.0, acc);
+            if (tc == g.ntc - 1) {
+                block_sum<3>(acc, s_red);
+                if (threadIdx.x == 0) w.partials[blockIdx.x] = acc[0];
+            }
+            if (!cd_grid_sync(ctrl, nb, epoch)) return;
+        }
+        ravg_prev = grid_total(w.partials, nb, &s_bc) / (double)nc;
+        ravg = ravg_prev;
+        while (!converged && sweeps < max_sweeps) {
+            const int buf = (sweeps & 1) ? 0 : 1;
+            double* part = w.partials + (size_t)buf * 3 * nb;
+            double a3[3] = {0.0, 0.0, 0.0};
+            for (int tc = 0; tc < g.ntc; ++tc) {
+                for (int rk = s_tc[tc] + blockIdx.x; rk < s_tc[tc + 1]; rk += nb)
+                    process_tile<DIM, T>(g, w, rk, sm, false, crit, alpha, ravg_prev, a3);
+                if (tc == g.ntc - 1) {
+                    block_sum<3>(a3, s_red);
+                    if (threadIdx.x == 0) {
+                        part[blockIdx.x] = a3[0];
+                        part[nb + blockIdx.x] = a3[1];
+                        part[2 * nb + blockIdx.x] = a3[2];
+                    }
+                }
+                if (!cd_grid_sync(ctrl, nb, epoch)) return;
+            }
+            ++sweeps;
+            ravg = grid_total(part, nb, &s_bc) / (double)nc;
+            double den = ravg + ravg_prev;
+            if (crit == CD_CONV_GLOBAL_REL) {
+                resid = (den > 0.0) ? fabs(ravg - ravg_prev) / den : 0.0;
+                converged = resid < alpha;
+            } else if (crit == CD_CONV_GLOBAL_SQ) {
+                double q = (den > 0.0) ? (ravg - ravg_prev) / den : 0.0;
+                resid = q * q;
+                converged = resid < alpha;
+            } else if (crit == CD_CONV_LOCAL) {
+                double nrel = grid_total(part + nb, nb, &s_bc);
+                double nbad = grid_total(part + 2 * nb, nb, &s_bc);
+                resid = (double)(nc - (long long)nrel) / (double)nc;
+                converged = (10.0 * nrel >= 9.0 * (double)nc) && nbad == 0.0;
+            } else {
+                resid = (den > 0.0) ? fabs(ravg - ravg_prev) / den : 0.0;
+                converged = 0;
+            }
+            ravg_prev = ravg;
+        }
+    }
+    finish_solve<DIM, T>(g, w, nc, nb, tid, stride, epoch, sweeps, converged, resid, ravg, s_red, s_bc);
 }
 
 // ---------------------------------------------------------------------------
@@ -591,19 +1060,43 @@ cudaError_t cd_launch_unpack(const CdGeom& g, const CdWork& w, double* pos, doub
     return cudaGetLastError();
 }
 
-static const void* sweep_fn(int dim, int precision)
+static const void* sweep_fn(int dim, int precision, int tiled)
 {
+    if (tiled == 2) {
+        if (dim == 2)
+            return precision == CD_FP64 ? (const void*)k_sweep_flow<2, double> : (const void*)k_sweep_flow<2, float>;
+        return precision == CD_FP64 ? (const void*)k_sweep_flow<3, double> : (const void*)k_sweep_flow<3, float>;
+    }
+    if (tiled) {
+        if (dim == 2)
+            return precision == CD_FP64 ? (const void*)k_sweep_tiled<2, double> : (const void*)k_sweep_tiled<2, float>;
+        return precision == CD_FP64 ? (const void*)k_sweep_tiled<3, double> : (const void*)k_sweep_tiled<3, float>;
+    }
     if (dim == 2) return precision == CD_FP64 ? (const void*)k_sweep<2, double> : (const void*)k_sweep<2, float>;
     return precision == CD_FP64 ? (const void*)k_sweep<3, double> : (const void*)k_sweep<3, float>;
 }
 
+static size_t tile_smem(int dim, int precision)
+{
+    if (dim == 2) return precision == CD_FP64 ? sizeof(TileSmem<2, double>) : sizeof(TileSmem<2, float>);
+    return precision == CD_FP64 ? sizeof(TileSmem<3, double>) : sizeof(TileSmem<3, float>);
+}
+
+// Blocks of the cooperative sweep grid: one per SM (keeps the grid barrier
+// cheap), for whichever of the two kernels the system uses.
 int cd_sweep_max_blocks(int precision, int dim, int num_sms)
 {
     int per_sm = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, sweep_fn(dim, precision), CD_SWEEP_THREADS, 0) !=
-        cudaSuccess)
-        return 0;
-    if (per_sm > 1) per_sm = 1;
+    for (int tiled = 0; tiled < 3; ++tiled) {
+        const void* fn = sweep_fn(dim, precision, tiled);
+        size_t dyn = (tiled == 1) ? tile_smem(dim, precision) : 0;
+        if (tiled && cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn) != cudaSuccess)
+            return 0;
+        int b = 0;
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, fn, CD_SWEEP_THREADS, dyn) != cudaSuccess) return 0;
+        if (b < 1) return 0;
+        per_sm = 1;
+    }
     return per_sm * num_sms;
 }
 
@@ -619,7 +1112,8 @@ cudaError_t cd_launch_sweep(const CdGeom& g, const CdWork& w, int coop_blocks, i
     double al = alpha;
     int ms = max_sweeps;
     void* args[] = {&ga, &wa, &crit, &al, &ms};
+    const int kind = (g.tile_cells >= 2) ? 1 : (g.dataflow ? 2 : 0);
     ++*nl;
-    return cudaLaunchCooperativeKernel(sweep_fn(g.dim, precision), dim3(coop_blocks), dim3(CD_SWEEP_THREADS), args,
-                                       0, s);
+    return cudaLaunchCooperativeKernel(sweep_fn(g.dim, precision, kind), dim3(coop_blocks), dim3(CD_SWEEP_THREADS),
+                                       args, kind == 1 ? tile_smem(g.dim, precision) : 0, s);
 }
