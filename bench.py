@@ -44,6 +44,13 @@ WORKLOAD = "dense_biaxial_discs_2d"
 # read + write 2 x 24, inv_m, r, r/I 24); FP32 halves the real-valued parts
 BYTES_PER_CONTACT = {"f64": 80, "f32": 44}
 BYTES_PER_PARTICLE = {"f64": 72, "f32": 36}
+# algorithmic FP64 flops of one 2D contact update as the sweep kernel writes
+# it: relative velocity 2 + 2 (u_n) + 7 (u_t), P_n 3, mu P_n 1, P_t 2,
+# impulse change 2, its vector 6, both bodies' velocities 12, |P| 4 (3 + sqrt)
+FLOPS_PER_UPDATE_2D = 42
+# FP64 peak of GB300 from unit counts and clock: 152 SMs x 2 FP64 FMA/clk x 2
+# flops x 2.07 GHz (nominal 1.25 TFLOP/s)
+FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12
 
 
 def parse():
@@ -85,6 +92,25 @@ def config(args, wl, extra=None):
     if extra:
         c.update(extra)
     return c
+
+
+def profiled_traffic(kernel, precision, n):
+    """DRAM bytes per launch from the committed ncu summary, or None if the
+    sweep kernel's source changed since the counters were taken."""
+    import hashlib
+    try:
+        src = open(os.path.join(ROOT, "paper_1104_3516_gb300", "csrc", "cd_sweep.cu"), "rb").read()
+        sha = hashlib.sha256(src).hexdigest()[:16]
+        for line in open(os.path.join(ROOT, "profiles", "k_sweep_traffic.txt")):
+            if line.startswith("#") or not line.strip():
+                continue
+            f = dict(kv.split("=", 1) for kv in line.split())
+            if (f.get("kernel") == kernel and f.get("precision") == precision and int(f.get("n", -1)) == n
+                    and f.get("src_sha256") == sha):
+                return float(f["traffic_bytes_per_launch"])
+    except Exception:
+        return None
+    return None
 
 
 def peaks():
@@ -278,13 +304,24 @@ def run_ours(args):
     steps_per_s = steps_sum / (dev_ms_max / 1e3)
 
     peak, peak_kind = peaks()
-    achieved = sweep_bytes / (ph["sweep"] / 1e3) / 1e9 if ph["sweep"] > 0 else 0.0
-    roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
-                "traffic": None, "kernel": ("k_sweep" if args.tile_cells == 0 else "k_sweep_tiled")
-                + f"<2,{'double' if args.precision == 'f64' else 'float'}>",
+    kname = ("k_sweep" if args.tile_cells == 0 and args.dataflow == 0 else
+             ("k_sweep_tiled" if args.tile_cells else "k_sweep_flow"))
+    kname += f"<2,{'double' if args.precision == 'f64' else 'float'}>"
+    sweep_s = ph["sweep"] / 1e3
+    gbs = sweep_bytes / sweep_s / 1e9 if sweep_s > 0 else 0.0
+    hbm_view = {"bound": "hbm", "achieved": gbs, "peak": peak, "unit": "GB/s", "frac": gbs / peak,
                 "peak_source": f"{peak_kind} HBM copy bandwidth",
-                "bytes_model": f"per sweep {bpc} B x contacts + {bpp} B x particles",
-                "avg_launch_ms": ph["sweep"] / max(args.steps, 1)}
+                "bytes_model": f"per sweep {bpc} B x contacts + {bpp} B x particles"}
+    traffic = profiled_traffic(kname, args.precision, wl.n)
+    if args.precision == "f64":
+        tf = FLOPS_PER_UPDATE_2D * upd / sweep_s / 1e12 if sweep_s > 0 else 0.0
+        roofline = {"bound": "alu", "achieved": tf, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
+                    "frac": tf / FP64_PEAK_TFLOPS, "traffic": traffic, "kernel": kname,
+                    "peak_source": "FP64 unit count x clock (152 SMs x 2 FMA/clk x 2 x 2.07 GHz)",
+                    "flops_model": f"{FLOPS_PER_UPDATE_2D} FP64 flops per contact update",
+                    "avg_launch_ms": ph["sweep"] / max(args.steps, 1), "hbm_view": hbm_view}
+    else:
+        roofline = dict(hbm_view, traffic=traffic, kernel=kname, avg_launch_ms=ph["sweep"] / max(args.steps, 1))
 
     e2e = None
     if not args.no_e2e:
