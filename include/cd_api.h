@@ -154,6 +154,26 @@ cd_status cd_create_system(const cd_params* params, int64_t n, double* pos, doub
                            const double* inv_inertia, const double* f_ext, void* cuda_stream,
                            cd_system** out);
 
+/* A batch of independent packings stepped together (hundreds of packings of
+ * uneven size).  Particles of all packings are concatenated: packing b owns
+ * particles offsets_host[b] .. offsets_host[b+1]-1 (offsets_host[0] = 0,
+ * offsets_host[n_packings] = n; host array of n_packings + 1).  params is a
+ * host array of n_packings cd_params: per packing mu, gravity, box, periodic
+ * axes, walls (mask, positions, velocities) are taken from its own entry;
+ * dim, precision, dt, delta, alpha, criterion, max_sweeps, warm_start,
+ * rotations, seed, timing and max_contacts (total over the batch) from
+ * entry 0; tile_cells must be 0.  State arrays as in cd_create_system over
+ * all n particles.  Each packing keeps its own cell grid and walls (wall k of
+ * packing b is body n + 6 b + k), contacts never join two packings, and each
+ * packing has its own convergence test (Sec. 2.1): the colour phases are
+ * shared, and a packing whose test passed is not updated in later sweeps, so
+ * every packing gets exactly the result of solving it alone.  cd_step,
+ * cd_detect_contacts, cd_solve_contacts, cd_get_contacts work on the whole
+ * batch; per-packing results come from cd_get_packing_stats. */
+cd_status cd_create_batch(const cd_params* params, int64_t n_packings, const int64_t* offsets_host, double* pos,
+                          double* vel, double* omega, double* theta, const double* radius, const double* inv_mass,
+                          const double* inv_inertia, const double* f_ext, void* cuda_stream, cd_system** out);
+
 /* Bytes of device workspace the system needs (cell grid, contact arrays in
  * key and colour order, colouring and reduction buffers). */
 cd_status cd_workspace_size(const cd_system* sys, size_t* bytes);
@@ -203,7 +223,22 @@ cd_status cd_step(cd_system* sys, int64_t n_steps, cd_step_stats* out);
 cd_status cd_get_contacts(cd_system* sys, int64_t* n_contacts, int32_t* pairs, double* normal, double* gap,
                           double* impulse, int32_t* colour);
 
-/* Current wall plane positions (6 doubles, host memory).  Synchronises. */
+typedef struct {
+    int64_t sweeps;          /* sweeps of the last solve of this packing */
+    int64_t converged;
+    double residual;
+    double r_avg;
+    int64_t n_contacts;
+    double wall_force[6];    /* normal impulses on each wall / dt, last solve */
+    double wall_pos[6];      /* current wall planes */
+} cd_packing_stats;
+
+/* Statistics of packings first .. first+count-1 of a batch (a plain system is
+ * packing 0) into a host array of count entries.  Synchronises. */
+cd_status cd_get_packing_stats(cd_system* sys, int64_t first, int64_t count, cd_packing_stats* out_host);
+
+/* Current wall plane positions (6 doubles, host memory; packing 0 of a
+ * batch).  Synchronises. */
 cd_status cd_get_walls(cd_system* sys, double* wall_pos_host);
 
 /* Host <-> device copies of the particle state (pos, vel, omega; theta if

@@ -102,6 +102,23 @@ class cd_step_stats(C.Structure):
                 "last": self.last.as_dict()}
 
 
+class cd_packing_stats(C.Structure):
+    _fields_ = [
+        ("sweeps", C.c_int64),
+        ("converged", C.c_int64),
+        ("residual", C.c_double),
+        ("r_avg", C.c_double),
+        ("n_contacts", C.c_int64),
+        ("wall_force", C.c_double * 6),
+        ("wall_pos", C.c_double * 6),
+    ]
+
+    def as_dict(self):
+        return {"sweeps": int(self.sweeps), "converged": bool(self.converged), "residual": float(self.residual),
+                "r_avg": float(self.r_avg), "n_contacts": int(self.n_contacts),
+                "wall_force": [float(v) for v in self.wall_force], "wall_pos": [float(v) for v in self.wall_pos]}
+
+
 _lock = threading.Lock()
 _lib = None
 
@@ -110,6 +127,8 @@ _P = C.c_void_p
 SIGNATURES = [
     ("cd_create_system", C.c_int, [C.POINTER(cd_params), C.c_int64, _P, _P, _P, _P, _P, _P, _P, _P, _P,
                                    C.POINTER(_P)]),
+    ("cd_create_batch", C.c_int, [C.POINTER(cd_params), C.c_int64, C.POINTER(C.c_int64), _P, _P, _P, _P, _P, _P, _P,
+                                  _P, _P, C.POINTER(_P)]),
     ("cd_workspace_size", C.c_int, [_P, C.POINTER(C.c_size_t)]),
     ("cd_set_workspace", C.c_int, [_P, _P, C.c_size_t]),
     ("cd_detect_contacts", C.c_int, [_P, C.POINTER(C.c_int64)]),
@@ -118,6 +137,7 @@ SIGNATURES = [
     ("cd_step", C.c_int, [_P, C.c_int64, C.POINTER(cd_step_stats)]),
     ("cd_get_contacts", C.c_int, [_P, C.POINTER(C.c_int64), _P, _P, _P, _P, _P]),
     ("cd_get_walls", C.c_int, [_P, C.POINTER(C.c_double)]),
+    ("cd_get_packing_stats", C.c_int, [_P, C.c_int64, C.c_int64, C.POINTER(cd_packing_stats)]),
     ("cd_upload_state", C.c_int, [_P, _P, _P, _P]),
     ("cd_download_state", C.c_int, [_P, _P, _P, _P]),
     ("cd_detect_contacts_noalloc", C.c_int, [C.POINTER(cd_params), C.c_int64, _P, _P, _P, _P, C.c_int64, _P, _P,
@@ -160,6 +180,23 @@ def cd_create_system(params: cd_params, n, pos, vel, omega, theta, radius, inv_m
                                 ptr(inv_mass), ptr(inv_inertia), ptr(f_ext), stream, C.byref(out))
     _check(None, st)
     return out
+
+
+def cd_create_batch(params_list, offsets, pos, vel, omega, theta, radius, inv_mass, inv_inertia, f_ext, stream):
+    out = _P()
+    ptr = lambda t: None if t is None else t.data_ptr()
+    arr = (cd_params * len(params_list))(*params_list)
+    offs = (C.c_int64 * len(offsets))(*[int(o) for o in offsets])
+    st = lib().cd_create_batch(arr, len(params_list), offs, ptr(pos), ptr(vel), ptr(omega), ptr(theta), ptr(radius),
+                               ptr(inv_mass), ptr(inv_inertia), ptr(f_ext), stream, C.byref(out))
+    _check(None, st)
+    return out
+
+
+def cd_get_packing_stats(sysptr, first, count):
+    arr = (cd_packing_stats * max(count, 1))()
+    _check(sysptr, lib().cd_get_packing_stats(sysptr, int(first), int(count), arr))
+    return [arr[i].as_dict() for i in range(count)]
 
 
 def cd_workspace_size(sysptr) -> int:
@@ -277,10 +314,26 @@ def make_params(wl, precision=CD_FP64, criterion=CD_CONV_GLOBAL_REL, max_contact
     return p
 
 
+def concat_workloads(batch):
+    """One Workload holding the particles of all packings (parameters of the
+    first); the packings' own parameters go to cd_create_batch separately."""
+    import dataclasses
+    w0 = batch[0]
+    cat = lambda name: np.concatenate([np.asarray(getattr(b, name)) for b in batch], axis=0)
+    return dataclasses.replace(w0, x=cat("x"), v=cat("v"), w=cat("w"), r=cat("r"), inv_m=cat("inv_m"),
+                               inv_I=cat("inv_I"))
+
+
 class CDSystem:
     """A CD system over torch-owned device tensors (FP64 state, SoA layouts of cd_api.h)."""
 
-    def __init__(self, wl, device="cuda", f_ext=None, stream=None, **param_kw):
+    def __init__(self, wl, device="cuda", f_ext=None, stream=None, batch=None, **param_kw):
+        """wl: one Workload, or with batch=[Workload, ...] the list of packings
+        (wl is then ignored and the packings are concatenated)."""
+        if batch is not None:
+            wl = concat_workloads(batch)
+            self.packings = batch
+            self.n_packings = len(batch)
         self.wl = wl
         self.dim = wl.dim
         self.n = wl.n
@@ -294,11 +347,21 @@ class CDSystem:
         self.inv_mass = torch.as_tensor(wl.inv_m, **dd).clone()
         self.inv_inertia = torch.as_tensor(wl.inv_I, **dd).clone()
         self.f_ext = None if f_ext is None else torch.as_tensor(np.asarray(f_ext).reshape(-1), **dd).clone()
-        self.params = make_params(wl, **param_kw)
         self.pw = 2 if wl.dim == 2 else 4
         self.stream = stream if stream is not None else torch.cuda.current_stream(self.device)
-        self._h = cd_create_system(self.params, self.n, self.pos, self.vel, self.omega, self.theta, self.radius,
-                                   self.inv_mass, self.inv_inertia, self.f_ext, self.stream.cuda_stream)
+        if batch is None:
+            self.params = make_params(wl, **param_kw)
+            self._h = cd_create_system(self.params, self.n, self.pos, self.vel, self.omega, self.theta, self.radius,
+                                       self.inv_mass, self.inv_inertia, self.f_ext, self.stream.cuda_stream)
+        else:
+            total = sum(b.n for b in batch)
+            kw = dict(param_kw)
+            kw.setdefault("max_contacts", max(64, 6 * total))
+            self.params = [make_params(b, **kw) for b in batch]
+            self.offsets = np.concatenate([[0], np.cumsum([b.n for b in batch])]).astype(np.int64)
+            self._h = cd_create_batch(self.params, self.offsets, self.pos, self.vel, self.omega, self.theta,
+                                      self.radius, self.inv_mass, self.inv_inertia, self.f_ext,
+                                      self.stream.cuda_stream)
         nbytes = cd_workspace_size(self._h)
         self.workspace = torch.empty(nbytes + 256, dtype=torch.uint8, device=self.device)
         off = (-self.workspace.data_ptr()) % 256
@@ -350,6 +413,9 @@ class CDSystem:
 
     def walls(self) -> np.ndarray:
         return cd_get_walls(self._h)
+
+    def packing_stats(self):
+        return cd_get_packing_stats(self._h, 0, getattr(self, "n_packings", 1))
 
     def state(self) -> dict:
         torch.cuda.synchronize(self.device)

@@ -33,6 +33,9 @@ struct cd_system {
     CdGeom g;
     CdWork w;
     int launches;                      // kernels launched since the call began
+    std::vector<CdPack> pk_host;       // packing table (one entry for a plain system)
+    std::vector<int> pack_of_host;     // packing of each particle (batched systems)
+    std::vector<double> pk_wall0;      // initial wall planes, 6 per packing
     std::vector<cudaEvent_t> events;   // phase events (params.timing)
     size_t ev_used;
     std::string err;
@@ -85,7 +88,7 @@ static size_t layout(cd_system* s, char* base, CdWork* w)
     Layout L;
     const size_t n = (size_t)s->n;
     const size_t cap = (size_t)s->p.max_contacts;
-    const size_t ncell = (size_t)s->g.ncell[0] * s->g.ncell[1] * s->g.ncell[2];
+    const size_t ncell = (size_t)s->g.ncell_total;
     const size_t real = (s->p.precision == CD_FP64) ? 8 : 4;
     const size_t vrec = (s->p.dim == 2 ? 4 : 8) * real;   // velocity record bytes
     const size_t nchunk = (cap + CD_CHUNK - 1) / CD_CHUNK;
@@ -139,6 +142,17 @@ static size_t layout(cd_system* s, char* base, CdWork* w)
     t.seg_fill = L.take<int>(base, nseg);
     t.c_need = L.take<int2>(base, cap);
     t.deg = L.take<int>(base, n);
+    const size_t npk = (size_t)s->g.npk;
+    t.pk = L.take<CdPack>(base, npk);
+    t.pack_of = L.take<int>(base, npk > 1 ? n : 1);
+    t.pk_wall_pos = L.take<double>(base, 6 * npk);
+    if (npk == 1 && base) t.pk_wall_pos = t.ctrl->wall_pos;   // the plain system's walls live in the control block
+    t.pk_coff = L.take<int>(base, npk + 1);
+    t.pk_done = L.take<int>(base, npk);
+    t.pk_stats = L.take<double>(base, CD_PKSTATS * npk);
+    t.c_abs = L.take<double>(base, cap);
+    t.c_flag = L.take<int>(base, cap);
+    t.act_cnt = L.take<int>(base, 4);
     if (w) *w = t;
     return (L.off + 255) & ~(size_t)255;
 }
@@ -242,6 +256,7 @@ static cd_status launch_detect_chain(cd_system* s, int timed)
     cd_status st;
     CD_CUDA(s, cd_launch_detect(s->g, s->w, s->pos, s->radius, s->inv_m, s->inv_I, (int)s->p.warm_start, s->pw,
                                 s->stream, &s->launches));
+    if (s->g.npk > 1) CD_CUDA(s, cd_launch_pk_ranges(s->g, s->w, s->stream, &s->launches));
     if (timed && (st = mark(s)) != CD_OK) return st;
     CD_CUDA(s, cd_launch_colour(s->g, s->w, s->colour_blocks, (int)s->p.precision, s->pw, s->stream, &s->launches,
                                 s->pos));
@@ -266,20 +281,42 @@ static cd_status launch_solve(cd_system* s, int free_flight, int timed)
 // ---------------------------------------------------------------------------
 // ABI
 // ---------------------------------------------------------------------------
-extern "C" cd_status cd_create_system(const cd_params* params, int64_t n, double* pos, double* vel, double* omega,
-                                      double* theta, const double* radius, const double* inv_mass,
-                                      const double* inv_inertia, const double* f_ext, void* cuda_stream,
-                                      cd_system** out)
+static cd_status check_packing(const cd_params& p, int dim)
+{
+    if (!(p.mu >= 0.0) || !std::isfinite(p.mu)) return fail(nullptr, CD_ERR_INVALID_ARG, "mu must be >= 0");
+    for (int k = 0; k < dim; ++k) {
+        if (!(p.box_hi[k] > p.box_lo[k]) || !std::isfinite(p.box_hi[k] - p.box_lo[k]))
+            return fail(nullptr, CD_ERR_INVALID_ARG, "box_hi must exceed box_lo on every axis");
+    }
+    for (int q = 0; q < 3; ++q)
+        if (!std::isfinite(p.gravity[q])) return fail(nullptr, CD_ERR_INVALID_ARG, "gravity not finite");
+    for (int k = 0; k < 6; ++k) {
+        if (!((p.wall_mask >> k) & 1)) continue;
+        if ((k >> 1) >= dim) return fail(nullptr, CD_ERR_INVALID_ARG, "wall on an axis the dimension lacks");
+        if (p.periodic[k >> 1]) return fail(nullptr, CD_ERR_INVALID_ARG, "wall on a periodic axis");
+        if (!std::isfinite(p.wall_pos[k])) return fail(nullptr, CD_ERR_INVALID_ARG, "wall position not finite");
+    }
+    if (((p.wall_mask & 3) == 3 && !(p.wall_pos[1] > p.wall_pos[0])) ||
+        ((p.wall_mask & 12) == 12 && !(p.wall_pos[3] > p.wall_pos[2])) ||
+        ((p.wall_mask & 48) == 48 && !(p.wall_pos[5] > p.wall_pos[4])))
+        return fail(nullptr, CD_ERR_INVALID_ARG, "opposite walls overlap");
+    return CD_OK;
+}
+
+// Shared by cd_create_system (one packing) and cd_create_batch.
+static cd_status create_impl(const cd_params* params, int64_t npk, const int64_t* offsets, int64_t n, double* pos,
+                             double* vel, double* omega, double* theta, const double* radius,
+                             const double* inv_mass, const double* inv_inertia, const double* f_ext,
+                             void* cuda_stream, cd_system** out)
 {
     if (!out) return fail(nullptr, CD_ERR_INVALID_ARG, "out is NULL");
     *out = nullptr;
     if (!params) return fail(nullptr, CD_ERR_INVALID_ARG, "params is NULL");
-    const cd_params& p = *params;
+    const cd_params& p = params[0];
     if (p.dim != 2 && p.dim != 3) return fail(nullptr, CD_ERR_INVALID_ARG, "dim must be 2 or 3");
     if (p.precision != CD_FP64 && p.precision != CD_FP32) return fail(nullptr, CD_ERR_INVALID_ARG, "bad precision");
-    if (n <= 0 || n + 6 >= (int64_t)0x7fffffff) return fail(nullptr, CD_ERR_INVALID_ARG, "particle count out of range");
+    if (n <= 0 || n + 6 * npk >= (int64_t)0x7fffffff) return fail(nullptr, CD_ERR_INVALID_ARG, "particle count out of range");
     if (!(p.dt > 0.0) || !std::isfinite(p.dt)) return fail(nullptr, CD_ERR_INVALID_ARG, "dt must be positive");
-    if (!(p.mu >= 0.0) || !std::isfinite(p.mu)) return fail(nullptr, CD_ERR_INVALID_ARG, "mu must be >= 0");
     if (!(p.delta >= 0.0) || !std::isfinite(p.delta)) return fail(nullptr, CD_ERR_INVALID_ARG, "delta must be >= 0");
     if (!(p.alpha >= 0.0)) return fail(nullptr, CD_ERR_INVALID_ARG, "alpha must be >= 0");
     if (p.max_sweeps < 0) return fail(nullptr, CD_ERR_INVALID_ARG, "max_sweeps must be >= 0");
@@ -288,22 +325,14 @@ extern "C" cd_status cd_create_system(const cd_params* params, int64_t n, double
         return fail(nullptr, CD_ERR_INVALID_ARG, "max_contacts out of range");
     if (!pos || !vel || !omega || !radius || !inv_mass || !inv_inertia)
         return fail(nullptr, CD_ERR_INVALID_ARG, "a required state array is NULL");
-    for (int k = 0; k < p.dim; ++k) {
-        if (!(p.box_hi[k] > p.box_lo[k]) || !std::isfinite(p.box_hi[k] - p.box_lo[k]))
-            return fail(nullptr, CD_ERR_INVALID_ARG, "box_hi must exceed box_lo on every axis");
-        for (int q = 0; q < 3; ++q)
-            if (!std::isfinite(p.gravity[q])) return fail(nullptr, CD_ERR_INVALID_ARG, "gravity not finite");
+    if (npk < 1 || npk > (1 << 20)) return fail(nullptr, CD_ERR_INVALID_ARG, "packing count out of range");
+    if (offsets[0] != 0 || offsets[npk] != n) return fail(nullptr, CD_ERR_INVALID_ARG, "offsets must run from 0 to n");
+    for (int64_t b = 0; b < npk; ++b) {
+        if (offsets[b + 1] < offsets[b]) return fail(nullptr, CD_ERR_INVALID_ARG, "offsets must not decrease");
+        cd_status st = check_packing(params[b], (int)p.dim);
+        if (st != CD_OK) return st;
     }
-    for (int k = 0; k < 6; ++k) {
-        if (!((p.wall_mask >> k) & 1)) continue;
-        if ((k >> 1) >= p.dim) return fail(nullptr, CD_ERR_INVALID_ARG, "wall on an axis the dimension lacks");
-        if (p.periodic[k >> 1]) return fail(nullptr, CD_ERR_INVALID_ARG, "wall on a periodic axis");
-        if (!std::isfinite(p.wall_pos[k])) return fail(nullptr, CD_ERR_INVALID_ARG, "wall position not finite");
-    }
-    if (((p.wall_mask & 3) == 3 && !(p.wall_pos[1] > p.wall_pos[0])) ||
-        ((p.wall_mask & 12) == 12 && !(p.wall_pos[3] > p.wall_pos[2])) ||
-        ((p.wall_mask & 48) == 48 && !(p.wall_pos[5] > p.wall_pos[4])))
-        return fail(nullptr, CD_ERR_INVALID_ARG, "opposite walls overlap");
+    if (npk > 1 && p.tile_cells != 0) return fail(nullptr, CD_ERR_INVALID_ARG, "a batch uses the colour order (tile_cells 0)");
 
     cd_system* s = new cd_system();
     s->p = p;
@@ -348,31 +377,64 @@ extern "C" cd_status cd_create_system(const cd_params* params, int64_t n, double
     g.mu = p.mu;
     g.rotations = (int)p.rotations;
     g.seed = p.seed;
+    g.npk = (int)npk;
     for (int k = 0; k < 18; ++k) g.wall_vel[k] = p.wall_vel[k];
     const double ell = 2.0 * rmax + p.delta;   // Sec. 3.1: cell side l = 2 r_max + delta
-    double ncell_total = 1.0;
-    for (int k = 0; k < 3; ++k) {
-        g.gravity[k] = p.gravity[k];
-        g.periodic[k] = (k < p.dim) ? (int)p.periodic[k] : 0;
-        if (k < p.dim) {
-            g.lo[k] = p.box_lo[k];
-            g.hi[k] = p.box_hi[k];
-            g.L[k] = p.box_hi[k] - p.box_lo[k];
-            double m = std::floor(g.L[k] / ell);
-            if (m < 1.0) m = 1.0;
-            if (m > 1.0e6) m = 1.0e6;
-            g.ncell[k] = (int)m;
-            g.cs[k] = g.L[k] / m;
-            if (g.periodic[k] && g.ncell[k] < 3) {
-                delete s;
-                return fail(nullptr, CD_ERR_INVALID_ARG, "a periodic axis needs at least 3 cells (box >= 3 l)");
+    double ncell_total = 0.0;
+    s->pk_host.resize((size_t)npk);
+    s->pk_wall0.resize((size_t)(6 * npk));
+    for (int64_t b = 0; b < npk; ++b) {
+        const cd_params& q = params[b];
+        CdPack& pk = s->pk_host[(size_t)b];
+        memset(&pk, 0, sizeof pk);
+        double cells = 1.0;
+        for (int k = 0; k < 3; ++k) {
+            pk.periodic[k] = (k < p.dim) ? (int)q.periodic[k] : 0;
+            pk.gravity[k] = q.gravity[k];
+            if (k < p.dim) {
+                pk.lo[k] = q.box_lo[k];
+                pk.hi[k] = q.box_hi[k];
+                pk.L[k] = q.box_hi[k] - q.box_lo[k];
+                double m = std::floor(pk.L[k] / ell);
+                if (m < 1.0) m = 1.0;
+                if (m > 1.0e6) m = 1.0e6;
+                pk.ncell[k] = (int)m;
+                pk.cs[k] = pk.L[k] / m;
+                if (pk.periodic[k] && pk.ncell[k] < 3) {
+                    delete s;
+                    return fail(nullptr, CD_ERR_INVALID_ARG, "a periodic axis needs at least 3 cells (box >= 3 l)");
+                }
+            } else {
+                pk.lo[k] = 0.0; pk.hi[k] = 1.0; pk.L[k] = 1.0; pk.ncell[k] = 1; pk.cs[k] = 1.0;
             }
-        } else {
-            g.lo[k] = 0.0; g.hi[k] = 1.0; g.L[k] = 1.0; g.ncell[k] = 1; g.cs[k] = 1.0;
+            cells *= pk.ncell[k];
         }
-        ncell_total *= g.ncell[k];
+        pk.cell_base = (int)ncell_total;
+        ncell_total += cells;
+        pk.wall_mask = (int)q.wall_mask;
+        pk.mu = q.mu;
+        for (int k = 0; k < 18; ++k) pk.wall_vel[k] = q.wall_vel[k];
+        for (int k = 0; k < 6; ++k) s->pk_wall0[(size_t)(6 * b + k)] = q.wall_pos[k];
+        pk.first = (int)offsets[b];
+        pk.count = (int)(offsets[b + 1] - offsets[b]);
+        pk.seed = q.seed;
     }
     if (ncell_total > 2.0e8) { delete s; return fail(nullptr, CD_ERR_INVALID_ARG, "cell grid too large for the box"); }
+    g.ncell_total = (int)ncell_total;
+    {
+        const CdPack& p0 = s->pk_host[0];
+        for (int k = 0; k < 3; ++k) {
+            g.gravity[k] = p.gravity[k];
+            g.periodic[k] = p0.periodic[k];
+            g.lo[k] = p0.lo[k]; g.hi[k] = p0.hi[k]; g.L[k] = p0.L[k];
+            g.ncell[k] = p0.ncell[k]; g.cs[k] = p0.cs[k];
+        }
+    }
+    if (npk > 1) {
+        s->pack_of_host.resize((size_t)n);
+        for (int64_t b = 0; b < npk; ++b)
+            for (int64_t i = offsets[b]; i < offsets[b + 1]; ++i) s->pack_of_host[(size_t)i] = (int)b;
+    }
     // tiled order: nt = cells / tile_cells per axis (>= 1, even on a periodic axis)
     if (p.tile_cells < 0 || p.tile_cells == 1) {
         delete s;
@@ -391,7 +453,7 @@ extern "C" cd_status cd_create_system(const cd_params* params, int64_t n, double
         g.ntiles *= t;
     }
     g.ntc = (g.tile_cells >= 2) ? (1 << p.dim) : 1;
-    g.dataflow = (p.dataflow && g.tile_cells == 0) ? 1 : 0;
+    g.dataflow = (p.dataflow && g.tile_cells == 0 && npk == 1) ? 1 : 0;
     if (g.tile_cells >= 2 && (double)g.ntiles * CD_KLOCAL > 1.0e8) {
         delete s;
         return fail(nullptr, CD_ERR_INVALID_ARG, "too many tiles: raise tile_cells");
@@ -404,6 +466,26 @@ extern "C" cd_status cd_create_system(const cd_params* params, int64_t n, double
     }
     *out = s;
     return CD_OK;
+}
+
+extern "C" cd_status cd_create_system(const cd_params* params, int64_t n, double* pos, double* vel, double* omega,
+                                      double* theta, const double* radius, const double* inv_mass,
+                                      const double* inv_inertia, const double* f_ext, void* cuda_stream,
+                                      cd_system** out)
+{
+    const int64_t offsets[2] = {0, n};
+    return create_impl(params, 1, offsets, n, pos, vel, omega, theta, radius, inv_mass, inv_inertia, f_ext,
+                       cuda_stream, out);
+}
+
+extern "C" cd_status cd_create_batch(const cd_params* params, int64_t n_packings, const int64_t* offsets_host,
+                                     double* pos, double* vel, double* omega, double* theta, const double* radius,
+                                     const double* inv_mass, const double* inv_inertia, const double* f_ext,
+                                     void* cuda_stream, cd_system** out)
+{
+    if (!offsets_host || n_packings < 1) return fail(nullptr, CD_ERR_INVALID_ARG, "offsets or packing count missing");
+    return create_impl(params, n_packings, offsets_host, offsets_host[n_packings], pos, vel, omega, theta, radius,
+                       inv_mass, inv_inertia, f_ext, cuda_stream, out);
 }
 
 extern "C" cd_status cd_workspace_size(const cd_system* sys, size_t* bytes)
@@ -425,8 +507,16 @@ extern "C" cd_status cd_set_workspace(cd_system* s, void* dev_ptr, size_t bytes)
     layout(s, (char*)dev_ptr, &s->w);
     CdCtrl h;
     memset(&h, 0, sizeof h);
-    for (int k = 0; k < 6; ++k) h.wall_pos[k] = s->p.wall_pos[k];
+    for (int k = 0; k < 6; ++k) h.wall_pos[k] = s->pk_wall0[(size_t)k];
     CD_CUDA(s, cudaMemcpyAsync(s->w.ctrl, &h, sizeof h, cudaMemcpyHostToDevice, s->stream));
+    CD_CUDA(s, cudaMemcpyAsync(s->w.pk, s->pk_host.data(), sizeof(CdPack) * s->pk_host.size(), cudaMemcpyHostToDevice,
+                               s->stream));
+    if (s->g.npk > 1) {
+        CD_CUDA(s, cudaMemcpyAsync(s->w.pack_of, s->pack_of_host.data(), sizeof(int) * s->pack_of_host.size(),
+                                   cudaMemcpyHostToDevice, s->stream));
+        CD_CUDA(s, cudaMemcpyAsync(s->w.pk_wall_pos, s->pk_wall0.data(), sizeof(double) * s->pk_wall0.size(),
+                                   cudaMemcpyHostToDevice, s->stream));
+    }
     {
         // tiles in (tile colour, tile) order; colour = parity of the tile coordinates
         const CdGeom& g = s->g;
@@ -479,6 +569,7 @@ extern "C" cd_status cd_set_contacts(cd_system* s, int64_t nc, const int32_t* pa
     k_begin_call<<<1, 1, 0, s->stream>>>(s->w.ctrl, 0);
     CD_CUDA(s, cd_launch_set_contacts(s->g, s->w, s->pos, s->radius, s->inv_m, s->inv_I, (int)nc, pairs, impulses,
                                       s->pw, s->stream, &s->launches));
+    if (s->g.npk > 1) CD_CUDA(s, cd_launch_pk_ranges(s->g, s->w, s->stream, &s->launches));
     CD_CUDA(s, cd_launch_colour(s->g, s->w, s->colour_blocks, (int)s->p.precision, s->pw, s->stream, &s->launches,
                                 s->pos));
     k_error_gate<<<1, 1, 0, s->stream>>>(s->w.ctrl);
@@ -566,9 +657,8 @@ extern "C" cd_status cd_get_walls(cd_system* s, double* wall_pos_host)
     cd_status st = need_ready(s);
     if (st != CD_OK) return st;
     if (!wall_pos_host) return fail(s, CD_ERR_INVALID_ARG, "wall_pos_host is NULL");
-    CdCtrl h;
-    if ((st = read_ctrl(s, &h)) != CD_OK) return st;
-    for (int k = 0; k < 6; ++k) wall_pos_host[k] = h.wall_pos[k];
+    CD_CUDA(s, cudaMemcpyAsync(wall_pos_host, s->w.pk_wall_pos, 6 * sizeof(double), cudaMemcpyDeviceToHost, s->stream));
+    CD_CUDA(s, cudaStreamSynchronize(s->stream));
     return CD_OK;
 }
 
@@ -595,6 +685,38 @@ extern "C" cd_status cd_download_state(cd_system* s, double* pos_host, double* v
     if (vel_host) CD_CUDA(s, cudaMemcpyAsync(vel_host, s->vel, nd, cudaMemcpyDeviceToHost, s->stream));
     if (omega_host) CD_CUDA(s, cudaMemcpyAsync(omega_host, s->omega, nw, cudaMemcpyDeviceToHost, s->stream));
     CD_CUDA(s, cudaStreamSynchronize(s->stream));
+    return CD_OK;
+}
+
+extern "C" cd_status cd_get_packing_stats(cd_system* s, int64_t first, int64_t count, cd_packing_stats* out_host)
+{
+    cd_status st = need_ready(s);
+    if (st != CD_OK) return st;
+    if (!out_host || first < 0 || count < 0 || first + count > s->g.npk)
+        return fail(s, CD_ERR_INVALID_ARG, "packing range out of bounds");
+    if (count == 0) return CD_OK;
+    std::vector<double> hs((size_t)(CD_PKSTATS * count)), hw((size_t)(6 * count));
+    std::vector<int> hc((size_t)count + 1);
+    CD_CUDA(s, cudaMemcpyAsync(hs.data(), s->w.pk_stats + CD_PKSTATS * first, sizeof(double) * hs.size(),
+                               cudaMemcpyDeviceToHost, s->stream));
+    CD_CUDA(s, cudaMemcpyAsync(hw.data(), s->w.pk_wall_pos + 6 * first, sizeof(double) * hw.size(),
+                               cudaMemcpyDeviceToHost, s->stream));
+    CD_CUDA(s, cudaMemcpyAsync(hc.data(), s->w.pk_coff + first, sizeof(int) * hc.size(), cudaMemcpyDeviceToHost,
+                               s->stream));
+    CD_CUDA(s, cudaStreamSynchronize(s->stream));
+    for (int64_t i = 0; i < count; ++i) {
+        const double* q = hs.data() + CD_PKSTATS * i;
+        cd_packing_stats& o = out_host[i];
+        o.sweeps = (int64_t)q[PKS_SWEEPS];
+        o.converged = (int64_t)q[PKS_CONV];
+        o.residual = q[PKS_RESID];
+        o.r_avg = q[PKS_RAVG];
+        o.n_contacts = (s->g.npk > 1) ? (int64_t)(hc[(size_t)i + 1] - hc[(size_t)i]) : (int64_t)q[PKS_NC];
+        for (int k = 0; k < 6; ++k) {
+            o.wall_force[k] = q[PKS_WF0 + k];
+            o.wall_pos[k] = hw[(size_t)(6 * i + k)];
+        }
+    }
     return CD_OK;
 }
 

@@ -62,7 +62,16 @@ __global__ void __launch_bounds__(CD_SWEEP_THREADS) k_jp(CdGeom g, CdWork w, uns
     const int stride = gridDim.x * blockDim.x;
     for (int c = tid; c < nc; c += stride) {
         int2 ab = w.pairs[c];
-        prio[c] = cd_splitmix64(g.seed ^ cd_key(ab.x, ab.y));
+        if (g.npk > 1) {
+            // a packing of a batch is coloured with its own seed and local
+            // ids (walls n_b + k), exactly as if it were a system alone
+            const CdPack& P = w.pk[w.pack_of[ab.x]];
+            const int al = ab.x - P.first;
+            const int bl = (ab.y < g.n) ? ab.y - P.first : P.count + (ab.y - g.n) % 6;
+            prio[c] = cd_splitmix64(P.seed ^ cd_key(al, bl));
+        } else {
+            prio[c] = cd_splitmix64(g.seed ^ cd_key(ab.x, ab.y));
+        }
         w.colour[c] = -1;
     }
     if (tid == 0) { round_cnt[0] = 0; round_cnt[1] = 0; round_cnt[2] = 0; ctrl->ncolours = 0; }
@@ -331,6 +340,34 @@ __global__ void k_need(CdGeom g, CdWork w)
     }
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < g.n; i += gridDim.x * blockDim.x)
         w.deg[i] = w.p2c_off[i + 1] - w.p2c_off[i];
+}
+
+// Key-order contact range of each packing: contacts are sorted by body a and
+// the packings' particles are consecutive, so packing b's contacts start at
+// the first key whose a >= the packing's first particle.
+__global__ void k_pk_ranges(CdGeom g, CdWork w)
+{
+    CdCtrl* ctrl = w.ctrl;
+    if (ctrl->skip) return;
+    const int nc = ctrl->nc;
+    for (int b = blockIdx.x * blockDim.x + threadIdx.x; b <= g.npk; b += gridDim.x * blockDim.x) {
+        if (b == g.npk) { w.pk_coff[b] = nc; continue; }
+        const int first = w.pk[b].first;
+        int lo = 0, hi = nc;
+        while (lo < hi) {
+            int mid = lo + ((hi - lo) >> 1);
+            if (w.pairs[mid].x < first) lo = mid + 1; else hi = mid;
+        }
+        w.pk_coff[b] = lo;
+    }
+}
+
+cudaError_t cd_launch_pk_ranges(const CdGeom& g, const CdWork& w, cudaStream_t s, int* nl)
+{
+    int gb = (g.npk + 1 + CD_BLOCK - 1) / CD_BLOCK;
+    k_pk_ranges<<<gb, CD_BLOCK, 0, s>>>(g, w);
+    ++*nl;
+    return cudaGetLastError();
 }
 
 cudaError_t cd_launch_need(const CdGeom& g, const CdWork& w, cudaStream_t s, int* nl)

@@ -124,25 +124,56 @@ cudaError_t cd_scan_exclusive(const int* in, int* out, int n, int* tmp, int* tot
 }
 
 // ---------------------------------------------------------------------------
-// Cell list
+// Cell list.  Every packing of a batched system has its own grid (a plain
+// system is one packing); global cell id = the packing's cell_base + local id,
+// so particles of different packings are never in neighbouring cells.
 // ---------------------------------------------------------------------------
-__device__ __forceinline__ int cell_axis(const CdGeom& g, int k, double x)
+struct GridV {
+    double lo[3], cs[3], L[3];
+    int ncell[3], periodic[3];
+    int base, wall_mask, pkid;
+};
+
+__device__ __forceinline__ void grid_of(const CdGeom& g, const CdWork& w, int i, GridV& v)
 {
-    double q = floor(__ddiv_rn(__dsub_rn(x, g.lo[k]), g.cs[k]));
-    int c = (q < 0.0) ? 0 : (q > (double)(g.ncell[k] - 1) ? g.ncell[k] - 1 : (int)q);
+    if (g.npk > 1) {
+        const int b = w.pack_of[i];
+        const CdPack& p = w.pk[b];
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+            v.lo[k] = p.lo[k]; v.cs[k] = p.cs[k]; v.L[k] = p.L[k];
+            v.ncell[k] = p.ncell[k]; v.periodic[k] = p.periodic[k];
+        }
+        v.base = p.cell_base; v.wall_mask = p.wall_mask; v.pkid = b;
+    } else {
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+            v.lo[k] = g.lo[k]; v.cs[k] = g.cs[k]; v.L[k] = g.L[k];
+            v.ncell[k] = g.ncell[k]; v.periodic[k] = g.periodic[k];
+        }
+        v.base = 0; v.wall_mask = g.wall_mask; v.pkid = 0;
+    }
+}
+
+__device__ __forceinline__ int cell_axis(const GridV& v, int k, double x)
+{
+    double q = floor(__ddiv_rn(__dsub_rn(x, v.lo[k]), v.cs[k]));
+    int c = (q < 0.0) ? 0 : (q > (double)(v.ncell[k] - 1) ? v.ncell[k] - 1 : (int)q);
     return c;
 }
 
 template <int DIM>
-__global__ void k_cell_count(CdGeom g, const double* __restrict__ pos, int* __restrict__ cell_of,
+__global__ void k_cell_count(CdGeom g, CdWork w, const double* __restrict__ pos, int* __restrict__ cell_of,
                              int* __restrict__ cell_cnt, const CdCtrl* ctrl)
 {
     if (ctrl->skip) return;
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < g.n; i += gridDim.x * blockDim.x) {
-        int c0 = cell_axis(g, 0, pos[i * DIM + 0]);
-        int c1 = cell_axis(g, 1, pos[i * DIM + 1]);
-        int c2 = (DIM == 3) ? cell_axis(g, 2, pos[i * DIM + 2]) : 0;
-        int c = (c2 * g.ncell[1] + c1) * g.ncell[0] + c0;
+        GridV v;
+        grid_of(g, w, i, v);
+        int c0 = cell_axis(v, 0, pos[i * DIM + 0]);
+        int c1 = cell_axis(v, 1, pos[i * DIM + 1]);
+        int c2 = (DIM == 3) ? cell_axis(v, 2, pos[i * DIM + 2]) : 0;
+        int c = v.base + (c2 * v.ncell[1] + c1) * v.ncell[0] + c0;
         cell_of[i] = c;
         atomicAdd(&cell_cnt[c], 1);
     }
@@ -161,29 +192,29 @@ __global__ void k_cell_fill(int n, const int* __restrict__ cell_of, const int* _
 
 // Separation b - a along axis k with the minimum-image rule (same operations
 // as the oracle).
-__device__ __forceinline__ double sep_axis(const CdGeom& g, int k, double xa, double xb)
+__device__ __forceinline__ double sep_axis(const GridV& v, int k, double xa, double xb)
 {
     double d = __dsub_rn(xb, xa);
-    if (g.periodic[k]) {
-        double half = __dmul_rn(0.5, g.L[k]);
-        if (d > half) d = __dsub_rn(d, g.L[k]);
-        else if (d < -half) d = __dadd_rn(d, g.L[k]);
+    if (v.periodic[k]) {
+        double half = __dmul_rn(0.5, v.L[k]);
+        if (d > half) d = __dsub_rn(d, v.L[k]);
+        else if (d < -half) d = __dadd_rn(d, v.L[k]);
     }
     return d;
 }
 
 template <int DIM>
-__device__ __forceinline__ bool pair_touches(const CdGeom& g, const double* xa, double ra, const double* __restrict__ pos,
-                                             const double* __restrict__ radius, int b)
+__device__ __forceinline__ bool pair_touches(const GridV& v, double delta, const double* xa, double ra,
+                                             const double* __restrict__ pos, const double* __restrict__ radius, int b)
 {
     double d2 = 0.0;
 #pragma unroll
     for (int k = 0; k < DIM; ++k) {
-        double d = sep_axis(g, k, xa[k], pos[b * DIM + k]);
+        double d = sep_axis(v, k, xa[k], pos[b * DIM + k]);
         double dd = __dmul_rn(d, d);
         d2 = (k == 0) ? dd : __dadd_rn(d2, dd);
     }
-    double s = __dadd_rn(__dadd_rn(ra, radius[b]), g.delta);
+    double s = __dadd_rn(__dadd_rn(ra, radius[b]), delta);
     return d2 < __dmul_rn(s, s);
 }
 
@@ -194,50 +225,50 @@ __device__ __forceinline__ double wall_gap(const double* xa, double ra, const do
     return __dsub_rn(__dsub_rn(wall_pos[k], xa[axis]), ra);
 }
 
-__device__ __forceinline__ bool wall_on(const CdGeom& g, int k)
+__device__ __forceinline__ bool wall_on(const GridV& v, int dim, int k)
 {
-    return ((g.wall_mask >> k) & 1) && (k >> 1) < g.dim;
+    return ((v.wall_mask >> k) & 1) && (k >> 1) < dim;
 }
 
 // Visits the candidate partners b > a of particle a in the 3^DIM cells around
-// it; calls f(b) for each b that passes the pair test.
+// it (in a's packing grid); calls f(b) for each b that passes the pair test.
 template <int DIM, typename F>
-__device__ __forceinline__ void for_each_partner(const CdGeom& g, int a, const double* xa, double ra,
+__device__ __forceinline__ void for_each_partner(const CdGeom& g, const GridV& v, int a, const double* xa, double ra,
                                                  const double* __restrict__ pos, const double* __restrict__ radius,
                                                  const int* __restrict__ cell_of, const int* __restrict__ cell_start,
                                                  const int* __restrict__ cell_pid, F f)
 {
-    int c = cell_of[a];
-    int q0 = c % g.ncell[0];
-    int q1 = (c / g.ncell[0]) % g.ncell[1];
-    int q2 = c / (g.ncell[0] * g.ncell[1]);
+    int c = cell_of[a] - v.base;
+    int q0 = c % v.ncell[0];
+    int q1 = (c / v.ncell[0]) % v.ncell[1];
+    int q2 = c / (v.ncell[0] * v.ncell[1]);
     const int zlo = (DIM == 3) ? -1 : 0, zhi = (DIM == 3) ? 1 : 0;
     for (int dz = zlo; dz <= zhi; ++dz) {
         int t2 = q2 + dz;
         if (DIM == 3) {
-            if (t2 < 0 || t2 >= g.ncell[2]) {
-                if (!g.periodic[2]) continue;
-                t2 = (t2 + g.ncell[2]) % g.ncell[2];
+            if (t2 < 0 || t2 >= v.ncell[2]) {
+                if (!v.periodic[2]) continue;
+                t2 = (t2 + v.ncell[2]) % v.ncell[2];
             }
         }
         for (int dy = -1; dy <= 1; ++dy) {
             int t1 = q1 + dy;
-            if (t1 < 0 || t1 >= g.ncell[1]) {
-                if (!g.periodic[1]) continue;
-                t1 = (t1 + g.ncell[1]) % g.ncell[1];
+            if (t1 < 0 || t1 >= v.ncell[1]) {
+                if (!v.periodic[1]) continue;
+                t1 = (t1 + v.ncell[1]) % v.ncell[1];
             }
             for (int dx = -1; dx <= 1; ++dx) {
                 int t0 = q0 + dx;
-                if (t0 < 0 || t0 >= g.ncell[0]) {
-                    if (!g.periodic[0]) continue;
-                    t0 = (t0 + g.ncell[0]) % g.ncell[0];
+                if (t0 < 0 || t0 >= v.ncell[0]) {
+                    if (!v.periodic[0]) continue;
+                    t0 = (t0 + v.ncell[0]) % v.ncell[0];
                 }
-                int cc = (t2 * g.ncell[1] + t1) * g.ncell[0] + t0;
+                int cc = v.base + (t2 * v.ncell[1] + t1) * v.ncell[0] + t0;
                 int e = cell_start[cc + 1];
                 for (int s = cell_start[cc]; s < e; ++s) {
                     int b = cell_pid[s];
                     if (b <= a) continue;
-                    if (pair_touches<DIM>(g, xa, ra, pos, radius, b)) f(b);
+                    if (pair_touches<DIM>(v, g.delta, xa, ra, pos, radius, b)) f(b);
                 }
             }
         }
@@ -245,21 +276,24 @@ __device__ __forceinline__ void for_each_partner(const CdGeom& g, int a, const d
 }
 
 template <int DIM>
-__global__ void k_pair_count(CdGeom g, const double* __restrict__ pos, const double* __restrict__ radius,
+__global__ void k_pair_count(CdGeom g, CdWork w, const double* __restrict__ pos, const double* __restrict__ radius,
                              const int* __restrict__ cell_of, const int* __restrict__ cell_start,
                              const int* __restrict__ cell_pid, int* __restrict__ pcnt, CdCtrl* ctrl)
 {
     if (ctrl->skip) return;
     for (int a = blockIdx.x * blockDim.x + threadIdx.x; a < g.n; a += gridDim.x * blockDim.x) {
+        GridV v;
+        grid_of(g, w, a, v);
+        const double* wp = w.pk_wall_pos + 6 * v.pkid;
         double xa[3] = {0.0, 0.0, 0.0};
 #pragma unroll
         for (int k = 0; k < DIM; ++k) xa[k] = pos[a * DIM + k];
         double ra = radius[a];
         int cnt = 0;
-        for_each_partner<DIM>(g, a, xa, ra, pos, radius, cell_of, cell_start, cell_pid, [&](int) { ++cnt; });
+        for_each_partner<DIM>(g, v, a, xa, ra, pos, radius, cell_of, cell_start, cell_pid, [&](int) { ++cnt; });
         int nw = 0;
         for (int k = 0; k < 2 * DIM; ++k)
-            if (wall_on(g, k) && wall_gap(xa, ra, ctrl->wall_pos, k) < g.delta) ++nw;
+            if (wall_on(v, DIM, k) && wall_gap(xa, ra, wp, k) < g.delta) ++nw;
         if (cnt > CD_MAXLOC) atomicCAS(&ctrl->error, CDE_NONE, CDE_PER_PARTICLE);
         pcnt[a] = cnt + nw;
     }
@@ -277,12 +311,15 @@ __global__ void k_cap_check(CdCtrl* ctrl, int cap)
 
 // Geometry of contact (a, b): normal from a to b, gap, m_n = 1/w_n and
 // m_t = 1/w_t with w_n = 1/m_a + 1/m_b, w_t = w_n + r_a^2/I_a + r_b^2/I_b.
+// A wall is body n + 6 * packing + k.
 template <int DIM>
-__device__ __forceinline__ void contact_geometry(const CdGeom& g, int a, int b, const double* __restrict__ pos,
-                                                 const double* __restrict__ radius, const double* __restrict__ inv_m,
-                                                 const double* __restrict__ inv_I, const double* wall_pos,
+__device__ __forceinline__ void contact_geometry(const CdGeom& g, const CdWork& w, int a, int b,
+                                                 const double* __restrict__ pos, const double* __restrict__ radius,
+                                                 const double* __restrict__ inv_m, const double* __restrict__ inv_I,
                                                  double nv[3], double* gap, double* mn, double* mt)
 {
+    GridV v;
+    grid_of(g, w, a, v);
     double xa[3] = {0.0, 0.0, 0.0};
 #pragma unroll
     for (int k = 0; k < DIM; ++k) xa[k] = pos[a * DIM + k];
@@ -295,7 +332,7 @@ __device__ __forceinline__ void contact_geometry(const CdGeom& g, int a, int b, 
         double d2 = 0.0;
 #pragma unroll
         for (int k = 0; k < DIM; ++k) {
-            dv[k] = sep_axis(g, k, xa[k], pos[b * DIM + k]);
+            dv[k] = sep_axis(v, k, xa[k], pos[b * DIM + k]);
             double dd = __dmul_rn(dv[k], dv[k]);
             d2 = (k == 0) ? dd : __dadd_rn(d2, dd);
         }
@@ -311,9 +348,10 @@ __device__ __forceinline__ void contact_geometry(const CdGeom& g, int a, int b, 
         wb_m = inv_m[b];
         wb_I = g.rotations ? inv_I[b] : 0.0;
     } else {
-        int k = b - g.n;
+        int t = b - g.n;
+        int k = t % 6;
         nv[k >> 1] = (k & 1) ? 1.0 : -1.0;
-        *gap = wall_gap(xa, ra, wall_pos, k);
+        *gap = wall_gap(xa, ra, w.pk_wall_pos + 6 * (t / 6), k);
     }
     double w_n = __dadd_rn(wa_m, wb_m);
     double w_t = __dadd_rn(__dadd_rn(w_n, __dmul_rn(__dmul_rn(ra, ra), wa_I)), __dmul_rn(__dmul_rn(rb, rb), wb_I));
@@ -341,13 +379,16 @@ __global__ void k_pair_emit(CdGeom g, CdWork w, const double* __restrict__ pos, 
     CdCtrl* ctrl = w.ctrl;
     if (ctrl->skip) return;
     for (int a = blockIdx.x * blockDim.x + threadIdx.x; a < g.n; a += gridDim.x * blockDim.x) {
+        GridV v;
+        grid_of(g, w, a, v);
+        const double* wp = w.pk_wall_pos + 6 * v.pkid;
         double xa[3] = {0.0, 0.0, 0.0};
 #pragma unroll
         for (int k = 0; k < DIM; ++k) xa[k] = pos[a * DIM + k];
         double ra = radius[a];
         int found[CD_MAXLOC];
         int nf = 0;
-        for_each_partner<DIM>(g, a, xa, ra, pos, radius, w.cell_of, w.cell_start, w.cell_pid, [&](int b) {
+        for_each_partner<DIM>(g, v, a, xa, ra, pos, radius, w.cell_of, w.cell_start, w.cell_pid, [&](int b) {
             if (nf < CD_MAXLOC) {
                 // insertion into the sorted prefix
                 int j = nf++;
@@ -358,14 +399,15 @@ __global__ void k_pair_emit(CdGeom g, CdWork w, const double* __restrict__ pos, 
         int o = w.poff[a];
         for (int f = 0; f < nf; ++f) {
             double nv[3], gap, mn, mt;
-            contact_geometry<DIM>(g, a, found[f], pos, radius, inv_m, inv_I, ctrl->wall_pos, nv, &gap, &mn, &mt);
+            contact_geometry<DIM>(g, w, a, found[f], pos, radius, inv_m, inv_I, nv, &gap, &mn, &mt);
             store_geometry<DIM>(w, o++, a, found[f], nv, gap, mn, mt);
         }
         for (int k = 0; k < 2 * DIM; ++k) {
-            if (wall_on(g, k) && wall_gap(xa, ra, ctrl->wall_pos, k) < g.delta) {
+            if (wall_on(v, DIM, k) && wall_gap(xa, ra, wp, k) < g.delta) {
+                const int wid = g.n + 6 * v.pkid + k;
                 double nv[3], gap, mn, mt;
-                contact_geometry<DIM>(g, a, g.n + k, pos, radius, inv_m, inv_I, ctrl->wall_pos, nv, &gap, &mn, &mt);
-                store_geometry<DIM>(w, o++, a, g.n + k, nv, gap, mn, mt);
+                contact_geometry<DIM>(g, w, a, wid, pos, radius, inv_m, inv_I, nv, &gap, &mn, &mt);
+                store_geometry<DIM>(w, o++, a, wid, nv, gap, mn, mt);
             }
         }
     }
@@ -380,7 +422,7 @@ __global__ void k_geometry_given(CdGeom g, CdWork w, int nc, const double* __res
     for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < nc; c += gridDim.x * blockDim.x) {
         int2 ab = w.pairs_nx[c];
         double nv[3], gap, mn, mt;
-        contact_geometry<DIM>(g, ab.x, ab.y, pos, radius, inv_m, inv_I, w.ctrl->wall_pos, nv, &gap, &mn, &mt);
+        contact_geometry<DIM>(g, w, ab.x, ab.y, pos, radius, inv_m, inv_I, nv, &gap, &mn, &mt);
         store_geometry<DIM>(w, c, ab.x, ab.y, nv, gap, mn, mt);
     }
 }
@@ -468,20 +510,22 @@ static int grid_for(int n, int per_block = CD_BLOCK)
 cudaError_t cd_launch_detect(const CdGeom& g, const CdWork& w, const double* pos, const double* radius,
                              const double* inv_m, const double* inv_I, int warm, int pw, cudaStream_t s, int* nl)
 {
-    int ncell = g.ncell[0] * g.ncell[1] * g.ncell[2];
+    int ncell = g.ncell_total;
     cudaError_t e;
     if ((e = cudaMemsetAsync(w.cell_cnt, 0, sizeof(int) * (size_t)(ncell + 1), s)) != cudaSuccess) return e;
     if ((e = cudaMemsetAsync(w.cell_fill, 0, sizeof(int) * (size_t)ncell, s)) != cudaSuccess) return e;
     int gb = grid_for(g.n);
-    if (g.dim == 2) k_cell_count<2><<<gb, CD_BLOCK, 0, s>>>(g, pos, w.cell_of, w.cell_cnt, w.ctrl);
-    else k_cell_count<3><<<gb, CD_BLOCK, 0, s>>>(g, pos, w.cell_of, w.cell_cnt, w.ctrl);
+    if (g.dim == 2) k_cell_count<2><<<gb, CD_BLOCK, 0, s>>>(g, w, pos, w.cell_of, w.cell_cnt, w.ctrl);
+    else k_cell_count<3><<<gb, CD_BLOCK, 0, s>>>(g, w, pos, w.cell_of, w.cell_cnt, w.ctrl);
     ++*nl;
     if ((e = cd_scan_exclusive(w.cell_cnt, w.cell_start, ncell + 1, w.scan_tmp, nullptr, s, nl)) != cudaSuccess) return e;
     k_cell_fill<<<gb, CD_BLOCK, 0, s>>>(g.n, w.cell_of, w.cell_start, w.cell_fill, w.cell_pid, w.ctrl); ++*nl;
     if (g.dim == 2)
-        k_pair_count<2><<<gb, CD_BLOCK, 0, s>>>(g, pos, radius, w.cell_of, w.cell_start, w.cell_pid, w.pcnt, w.ctrl);
+        k_pair_count<2><<<gb, CD_BLOCK, 0, s>>>(g, w, pos, radius, w.cell_of, w.cell_start, w.cell_pid, w.pcnt,
+                                                w.ctrl);
     else
-        k_pair_count<3><<<gb, CD_BLOCK, 0, s>>>(g, pos, radius, w.cell_of, w.cell_start, w.cell_pid, w.pcnt, w.ctrl);
+        k_pair_count<3><<<gb, CD_BLOCK, 0, s>>>(g, w, pos, radius, w.cell_of, w.cell_start, w.cell_pid, w.pcnt,
+                                                w.ctrl);
     ++*nl;
     if ((e = cudaMemsetAsync(w.pcnt + g.n, 0, sizeof(int), s)) != cudaSuccess) return e;
     if ((e = cd_scan_exclusive(w.pcnt, w.poff, g.n + 1, w.scan_tmp, &w.ctrl->nc_needed, s, nl)) != cudaSuccess) return e;

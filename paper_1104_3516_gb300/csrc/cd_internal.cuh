@@ -45,6 +45,25 @@ struct CdCtrl {
     long long n_not_conv;
 };
 
+// Parameters of one packing of a batched system (a plain system is a batch of
+// one).  Each packing has its own cell grid, walls, friction and gravity.
+struct CdPack {
+    double lo[3];
+    double hi[3];
+    double L[3];
+    double cs[3];
+    int ncell[3];
+    int cell_base;      // first global cell id of this packing
+    int periodic[3];
+    int wall_mask;
+    double mu;
+    double gravity[3];
+    double wall_vel[18];
+    int first;          // first particle of the packing
+    int count;          // particles of the packing
+    unsigned long long seed;  // colouring seed of the packing
+};
+
 // Pointers into the caller's workspace.
 struct CdWork {
     CdCtrl* ctrl;
@@ -96,7 +115,20 @@ struct CdWork {
     // dataflow schedule
     int2* c_need;       // cap (colour order): updates of body a / b that precede the contact in a sweep
     int* deg;           // n: contacts per particle
+    // batched systems (npk packings)
+    CdPack* pk;         // npk packing parameters
+    int* pack_of;       // n: packing of each particle
+    double* pk_wall_pos;// npk * 6 wall planes (aliases ctrl->wall_pos for one packing)
+    int* pk_coff;       // npk + 1: key-order contact range of each packing
+    int* pk_done;       // npk: 1 once the packing's convergence test passed
+    double* pk_stats;   // npk * CD_PKSTATS per-packing statistics
+    double* c_abs;      // cap (key order): |P| of the last update
+    int* c_flag;        // cap (key order): local test bits of the last update
+    int* act_cnt;       // 3 counters of packings still iterating
 };
+
+// Per-packing statistics layout in pk_stats.
+enum { PKS_SWEEPS = 0, PKS_CONV, PKS_RESID, PKS_RAVG, PKS_RPREV, PKS_NC, PKS_WF0, CD_PKSTATS = PKS_WF0 + 6 };
 
 // Geometry of the problem in the form the kernels need.
 struct CdGeom {
@@ -123,6 +155,8 @@ struct CdGeom {
     int ntiles;
     int ntc;            // tile colours (2^dim) or 1
     int dataflow;       // 1: per-particle update counts instead of per-colour barriers
+    int npk;            // packings (1 for a plain system)
+    int ncell_total;    // cells of all packings' grids
 };
 
 // ---------------------------------------------------------------------------
@@ -224,6 +258,7 @@ cudaError_t cd_launch_pack(const CdGeom& g, const CdWork& w, const double* vel, 
 cudaError_t cd_launch_order_tiled(const CdGeom& g, const CdWork& w, const double* pos, int precision, int pw,
                                   cudaStream_t stream, int* nl);
 cudaError_t cd_launch_need(const CdGeom& g, const CdWork& w, cudaStream_t stream, int* nl);
+cudaError_t cd_launch_pk_ranges(const CdGeom& g, const CdWork& w, cudaStream_t stream, int* nl);
 cudaError_t cd_launch_sweep(const CdGeom& g, const CdWork& w, int coop_blocks, int precision, int criterion,
                             double alpha, int max_sweeps, int pw, cudaStream_t stream, int* nl);
 cudaError_t cd_launch_unpack(const CdGeom& g, const CdWork& w, double* pos, double* vel, double* omega,

@@ -157,6 +157,7 @@ extern "C" cd_status cd_detect_contacts_noalloc(const cd_params* params, int64_t
     g.mu = p.mu;
     g.rotations = (int)p.rotations;
     g.seed = p.seed;
+    g.npk = 1;
     const double ell = 2.0 * rmax + p.delta;
     long long ncell = 1;
     for (int k = 0; k < 3; ++k) {
@@ -179,6 +180,7 @@ extern "C" cd_status cd_detect_contacts_noalloc(const cd_params* params, int64_t
     }
     if (ncell > CD_NOALLOC_MAX_CELLS)
         return na_error(CD_ERR_INVALID_ARG, "the box needs more than 65536 cells for the no-allocation entry point");
+    g.ncell_total = (int)ncell;
 
     CdWork w;
     memset(&w, 0, sizeof w);
@@ -199,6 +201,7 @@ extern "C" cd_status cd_detect_contacts_noalloc(const cd_params* params, int64_t
     w.pairs = (int2*)pairs;
     w.nrm = normal;
     w.gap = gap;
+    w.pk_wall_pos = ctrl->wall_pos;   // device address inside the scratch
     const int pw = (p.dim == 2) ? 2 : 4;
     int nl = 0;
     if ((e = cd_launch_detect(g, w, pos, radius, inv_mass, inv_inertia, 0, pw, s, &nl)) != cudaSuccess)

@@ -62,7 +62,8 @@ __global__ void k_pack(CdGeom g, CdWork w, const double* __restrict__ vel, const
         for (int k = 0; k < DIM; ++k) {
             double vk = vel[i * DIM + k];
             if (free_flight) {
-                double a = (im == 0.0) ? 0.0 : g.gravity[k];
+                double gk = (g.npk > 1) ? w.pk[w.pack_of[i]].gravity[k] : g.gravity[k];
+                double a = (im == 0.0) ? 0.0 : gk;
                 if (f_ext) a = __dadd_rn(a, __dmul_rn(f_ext[i * DIM + k], im));
                 vk = __dadd_rn(vk, __dmul_rn(a, g.dt));
             }
@@ -124,10 +125,14 @@ __global__ void k_unpack(CdGeom g, CdWork w, double* __restrict__ pos, double* _
             omega[3 * i] = om[0]; omega[3 * i + 1] = om[1]; omega[3 * i + 2] = om[2];
         }
     }
-    if (integrate && blockIdx.x == 0 && threadIdx.x == 0) {
-        for (int k = 0; k < 2 * DIM; ++k)
-            if ((g.wall_mask >> k) & 1)
-                ctrl->wall_pos[k] = __dadd_rn(ctrl->wall_pos[k], __dmul_rn(g.wall_vel[3 * k + (k >> 1)], g.dt));
+    if (integrate) {
+        for (int b = blockIdx.x * blockDim.x + threadIdx.x; b < g.npk; b += gridDim.x * blockDim.x) {
+            const CdPack& pb = w.pk[b];
+            for (int k = 0; k < 2 * DIM; ++k)
+                if ((pb.wall_mask >> k) & 1)
+                    w.pk_wall_pos[6 * b + k] = __dadd_rn(w.pk_wall_pos[6 * b + k],
+                                                         __dmul_rn(pb.wall_vel[3 * k + (k >> 1)], g.dt));
+        }
     }
 }
 
@@ -195,6 +200,8 @@ template <int DIM, typename T> struct Rec;
 template <typename T> struct Rec<2, T> {
     typedef typename Vec<T>::V4 T4;
     typedef typename Vec<T>::V2 T2;
+    T mu;        // friction coefficient of the contact's packing
+    int pk;      // packing of body a
     int2 ab;
     T4 geo;      // nx, ny, b = g/dt, m_n
     T mt;
@@ -204,6 +211,8 @@ template <typename T> struct Rec<2, T> {
 template <typename T> struct Rec<3, T> {
     typedef typename Vec<T>::V4 T4;
     typedef typename Vec<T>::V2 T2;
+    T mu;
+    int pk;
     int2 ab;
     T4 geo;      // nx, ny, nz, b = g/dt
     T2 m;        // m_n, m_t
@@ -218,6 +227,13 @@ __device__ __forceinline__ void load_rec(const CdGeom& g, const CdWork& w, int p
     typedef typename Vec<T>::V2 T2;
     const T4* S = (const T4*)w.S;
     r.ab = w.c_ab[pos];
+    if (g.npk > 1) {
+        r.pk = w.pack_of[r.ab.x];
+        r.mu = (T)w.pk[r.pk].mu;
+    } else {
+        r.pk = 0;
+        r.mu = (T)g.mu;
+    }
     r.geo = ((const T4*)w.c_geo)[pos];
     if constexpr (DIM == 2) {
         r.mt = ((const T*)w.c_m)[pos];
@@ -273,7 +289,7 @@ __device__ __forceinline__ UpdOut core2d(const CdGeom& g, const Rec<2, T>& r, ty
         T un = dvx * nx + dvy * ny;
         T ut = (dvy * nx - dvx * ny) - (r.sa.y * va.z + r.sb.y * vb.z);
         Pn = pos_part(r.P.x - mn * (b + un));
-        T lim = (T)g.mu * Pn;
+        T lim = r.mu * Pn;
         Pt = clamp_sym(r.P.y - r.mt * ut, lim);
         dPn = Pn - r.P.x; dPt = Pt - r.P.y;
     }
@@ -297,10 +313,18 @@ __device__ __forceinline__ UpdOut core2d(const CdGeom& g, const Rec<2, T>& r, ty
     return o;
 }
 
-template <typename T>
-__device__ __forceinline__ void wall_vel2(const CdGeom& g, int k, typename Vec<T>::V4& vb)
+// Velocity of wall body n + 6 * packing + k.
+__device__ __forceinline__ const double* wall_velocity(const CdGeom& g, const CdWork& w, int wid)
 {
-    vb.x = (T)g.wall_vel[3 * k]; vb.y = (T)g.wall_vel[3 * k + 1]; vb.z = (T)0; vb.w = (T)0;
+    const int t = wid - g.n;
+    return (g.npk > 1) ? w.pk[t / 6].wall_vel + 3 * (t % 6) : g.wall_vel + 3 * t;
+}
+
+template <typename T>
+__device__ __forceinline__ void wall_vel2(const CdGeom& g, const CdWork& w, int wid, typename Vec<T>::V4& vb)
+{
+    const double* u = wall_velocity(g, w, wid);
+    vb.x = (T)u[0]; vb.y = (T)u[1]; vb.z = (T)0; vb.w = (T)0;
 }
 
 template <typename T>
@@ -314,7 +338,7 @@ __device__ __forceinline__ UpdOut apply2d(const CdGeom& g, const CdWork& w, int 
     T4 va = V[r.ab.x];
     T4 vb;
     if (!wall) vb = V[r.ab.y];
-    else wall_vel2<T>(g, r.ab.y - g.n, vb);
+    else wall_vel2<T>(g, w, r.ab.y, vb);
     T2 Pnew;
     UpdOut o = core2d<T>(g, r, va, vb, wall, apply_only, crit, alpha, ravg_prev, Pnew);
     V[r.ab.x] = va;
@@ -346,7 +370,7 @@ __device__ __forceinline__ UpdOut core3d(const CdGeom& g, const Rec<3, T>& r, ty
         T tx = gx - un * nx, ty = gy - un * ny, tz = gz - un * nz;
         Pn = pos_part(r.P.x - mn * (b + un));
         Ptx = r.P.y - mt * tx; Pty = r.P.z - mt * ty; Ptz = r.P.w - mt * tz;
-        T lim = (T)g.mu * Pn;
+        T lim = r.mu * Pn;
         T q2 = Ptx * Ptx + Pty * Pty + Ptz * Ptz;
         if (q2 > lim * lim) {
             T sc = lim / sqrt(q2);
@@ -380,9 +404,11 @@ __device__ __forceinline__ UpdOut core3d(const CdGeom& g, const Rec<3, T>& r, ty
 }
 
 template <typename T>
-__device__ __forceinline__ void wall_vel3(const CdGeom& g, int k, typename Vec<T>::V4& vb, typename Vec<T>::V4& wb)
+__device__ __forceinline__ void wall_vel3(const CdGeom& g, const CdWork& w, int wid, typename Vec<T>::V4& vb,
+                                          typename Vec<T>::V4& wb)
 {
-    vb.x = (T)g.wall_vel[3 * k]; vb.y = (T)g.wall_vel[3 * k + 1]; vb.z = (T)g.wall_vel[3 * k + 2]; vb.w = (T)0;
+    const double* u = wall_velocity(g, w, wid);
+    vb.x = (T)u[0]; vb.y = (T)u[1]; vb.z = (T)u[2]; vb.w = (T)0;
     wb.x = wb.y = wb.z = wb.w = (T)0;
 }
 
@@ -396,7 +422,7 @@ __device__ __forceinline__ UpdOut apply3d(const CdGeom& g, const CdWork& w, int 
     T4 va = V[2 * r.ab.x], wa = V[2 * r.ab.x + 1];
     T4 vb, wb;
     if (!wall) { vb = V[2 * r.ab.y]; wb = V[2 * r.ab.y + 1]; }
-    else wall_vel3<T>(g, r.ab.y - g.n, vb, wb);
+    else wall_vel3<T>(g, w, r.ab.y, vb, wb);
     T4 Pnew;
     UpdOut o = core3d<T>(g, r, va, wa, vb, wb, wall, apply_only, crit, alpha, ravg_prev, Pnew);
     V[2 * r.ab.x] = va; V[2 * r.ab.x + 1] = wa;
@@ -586,6 +612,195 @@ k_sweep(CdGeom g, CdWork w, int crit, double alpha, int max_sweeps)
 }
 
 // ---------------------------------------------------------------------------
+// Batched systems: independent packings share the colour phases (so each
+// grid barrier is amortised over all of them) but each has its own
+// convergence test.  After a sweep every block reduces |P| over the
+// contiguous key-order contact range of the packings it owns (fixed order:
+// deterministic), decides convergence, and a converged packing's contacts are
+// skipped from the next sweep on, exactly as if it were solved alone.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ void pk_reduce(const CdGeom& g, const CdWork& w, int sweep, int crit, double alpha,
+                                          int* act_slot, double (*s_red)[3])
+{
+    for (int b = blockIdx.x; b < g.npk; b += gridDim.x) {
+        double* st = w.pk_stats + CD_PKSTATS * b;
+        if (sweep >= 0 && cd_ld_volatile_int(&w.pk_done[b])) continue;
+        const int c0 = w.pk_coff[b], c1 = w.pk_coff[b + 1];
+        double a3[3] = {0.0, 0.0, 0.0};
+        for (int c = c0 + threadIdx.x; c < c1; c += blockDim.x) {
+            a3[0] += w.c_abs[c];
+            if (crit == CD_CONV_LOCAL && sweep >= 0) {
+                int f = w.c_flag[c];
+                a3[1] += (double)(f & 1);
+                a3[2] += (double)((f >> 1) & 1);
+            }
+        }
+        block_sum<3>(a3, s_red);
+        if (threadIdx.x == 0) {
+            const int ncb = c1 - c0;
+            const double R = (ncb > 0) ? a3[0] / (double)ncb : 0.0;
+            if (sweep < 0) {
+                st[PKS_SWEEPS] = 0.0;
+                st[PKS_CONV] = (ncb == 0) ? 1.0 : 0.0;
+                st[PKS_RESID] = 0.0;
+                st[PKS_RAVG] = R;
+                st[PKS_RPREV] = R;
+                st[PKS_NC] = (double)ncb;
+                w.pk_done[b] = (ncb == 0) ? 1 : 0;
+            } else {
+                const double Rp = st[PKS_RPREV], den = R + Rp;
+                double resid;
+                int conv;
+                if (crit == CD_CONV_GLOBAL_REL) {
+                    resid = (den > 0.0) ? fabs(R - Rp) / den : 0.0;
+                    conv = resid < alpha;
+                } else if (crit == CD_CONV_GLOBAL_SQ) {
+                    double q = (den > 0.0) ? (R - Rp) / den : 0.0;
+                    resid = q * q;
+                    conv = resid < alpha;
+                } else if (crit == CD_CONV_LOCAL) {
+                    resid = (ncb > 0) ? (double)(ncb - (long long)a3[1]) / (double)ncb : 0.0;
+                    conv = (10.0 * a3[1] >= 9.0 * (double)ncb) && a3[2] == 0.0;
+                } else {
+                    resid = (den > 0.0) ? fabs(R - Rp) / den : 0.0;
+                    conv = 0;
+                }
+                st[PKS_SWEEPS] = (double)(sweep + 1);
+                st[PKS_RESID] = resid;
+                st[PKS_RAVG] = R;
+                st[PKS_RPREV] = R;
+                if (conv) {
+                    st[PKS_CONV] = 1.0;
+                    w.pk_done[b] = 1;
+                } else {
+                    atomicAdd(act_slot, 1);
+                }
+            }
+        }
+        __syncthreads();
+    }
+}
+
+template <int DIM, typename T>
+__global__ void __launch_bounds__(CD_SWEEP_THREADS, 1)
+k_sweep_batch(CdGeom g, CdWork w, int crit, double alpha, int max_sweeps)
+{
+    __shared__ int s_off[CD_KMAX + 1];
+    __shared__ double s_red[CD_SWEEP_THREADS / 32][3];
+    CdCtrl* ctrl = w.ctrl;
+    if (ctrl->skip) return;
+    const int nc = ctrl->nc;
+    const int K = ctrl->ncolours;
+    const int nb = gridDim.x;
+    const int tid = blockIdx.x * blockDim.x + threadIdx.x;
+    const int stride = gridDim.x * blockDim.x;
+    unsigned long long epoch = 0;
+    for (int k = threadIdx.x; k <= CD_KMAX; k += blockDim.x) s_off[k] = w.colour_off[k];
+    if (tid == 0) { w.act_cnt[0] = 0; w.act_cnt[1] = 0; w.act_cnt[2] = 0; }
+    __syncthreads();
+
+    // starting impulses, colour by colour
+    for (int k = 0; k < K; ++k) {
+        for (int p = s_off[k] + tid; p < s_off[k + 1]; p += stride) {
+            Rec<DIM, T> r;
+            load_rec<DIM, T>(g, w, p, r);
+            UpdOut o = apply_rec<DIM, T>(g, w, p, r, true, crit, alpha, 0.0);
+            w.c_abs[w.perm[p]] = o.pabs;
+        }
+        if (!cd_grid_sync(ctrl, nb, epoch)) return;
+    }
+    pk_reduce(g, w, -1, crit, alpha, nullptr, s_red);
+    if (!cd_grid_sync(ctrl, nb, epoch)) return;
+
+    for (int sweep = 0; sweep < max_sweeps && nc > 0; ++sweep) {
+        if (tid == 0) w.act_cnt[(sweep + 1) % 3] = 0;
+        for (int k = 0; k < K; ++k) {
+            for (int p = s_off[k] + tid; p < s_off[k + 1]; p += stride) {
+                Rec<DIM, T> r;
+                load_rec<DIM, T>(g, w, p, r);
+                if (w.pk_done[r.pk]) continue;
+                const double rprev = (crit == CD_CONV_LOCAL) ? w.pk_stats[CD_PKSTATS * r.pk + PKS_RPREV] : 0.0;
+                UpdOut o = apply_rec<DIM, T>(g, w, p, r, false, crit, alpha, rprev);
+                const int c = w.perm[p];
+                w.c_abs[c] = o.pabs;
+                w.c_flag[c] = o.rel_ok | (o.bad << 1);
+            }
+            if (!cd_grid_sync(ctrl, nb, epoch)) return;
+        }
+        pk_reduce(g, w, sweep, crit, alpha, &w.act_cnt[sweep % 3], s_red);
+        if (!cd_grid_sync(ctrl, nb, epoch)) return;
+        if (cd_ld_volatile_int(&w.act_cnt[sweep % 3]) == 0) break;
+    }
+
+    // impulses back to key order
+    typedef typename Vec<T>::V4 T4;
+    typedef typename Vec<T>::V2 T2;
+    for (int p = tid; p < nc; p += stride) {
+        int c = w.perm[p];
+        if (DIM == 2) {
+            T2 P = ((const T2*)w.c_P)[p];
+            w.Pk[2 * c] = (double)P.x;
+            w.Pk[2 * c + 1] = (double)P.y;
+        } else {
+            T4 P = ((const T4*)w.c_P)[p];
+            w.Pk[4 * c] = (double)P.x; w.Pk[4 * c + 1] = (double)P.y;
+            w.Pk[4 * c + 2] = (double)P.z; w.Pk[4 * c + 3] = (double)P.w;
+        }
+    }
+    if (!cd_grid_sync(ctrl, nb, epoch)) return;
+    // per-packing wall forces and the call's totals
+    const int pw = (DIM == 2) ? 2 : 4;
+    for (int b = blockIdx.x; b < g.npk; b += gridDim.x) {
+        const int c0 = w.pk_coff[b], c1 = w.pk_coff[b + 1];
+        double lo3[3] = {0.0, 0.0, 0.0}, hi3[3] = {0.0, 0.0, 0.0};
+        for (int c = c0 + threadIdx.x; c < c1; c += blockDim.x) {
+            int bb = w.pairs[c].y;
+            if (bb < g.n) continue;
+            int k = (bb - g.n) % 6;
+            double pn = w.Pk[pw * c];
+#pragma unroll
+            for (int q = 0; q < 3; ++q) {
+                if (q == k) lo3[q] += pn;
+                if (q + 3 == k) hi3[q] += pn;
+            }
+        }
+        block_sum<3>(lo3, s_red);
+        block_sum<3>(hi3, s_red);
+        if (threadIdx.x == 0) {
+            double* st = w.pk_stats + CD_PKSTATS * b;
+            for (int q = 0; q < 3; ++q) {
+                st[PKS_WF0 + q] = lo3[q] / g.dt;
+                st[PKS_WF0 + 3 + q] = hi3[q] / g.dt;
+            }
+            const long long sw = (long long)st[PKS_SWEEPS];
+            atomicAdd((unsigned long long*)&ctrl->total_updates, (unsigned long long)(sw * (long long)(c1 - c0)));
+            atomicMax((unsigned long long*)&ctrl->max_sweeps_step, (unsigned long long)sw);
+            if (st[PKS_CONV] == 0.0) atomicAdd((unsigned long long*)&ctrl->n_not_conv, 1ULL);
+            if (b == 0) {
+                for (int q = 0; q < 6; ++q) ctrl->wall_force[q] = st[PKS_WF0 + q];
+                ctrl->r_avg = st[PKS_RAVG];
+                ctrl->residual = st[PKS_RESID];
+            }
+        }
+        __syncthreads();
+    }
+    if (!cd_grid_sync(ctrl, nb, epoch)) return;
+    if (tid == 0) {
+        ctrl->steps_done += 1;
+        long long tot = 0, mx = 0, open = 0;
+        for (int b = 0; b < g.npk; ++b) {
+            const long long sw = (long long)w.pk_stats[CD_PKSTATS * b + PKS_SWEEPS];
+            tot += sw;
+            if (sw > mx) mx = sw;
+            if (w.pk_stats[CD_PKSTATS * b + PKS_CONV] == 0.0) ++open;
+        }
+        ctrl->total_sweeps += tot;
+        ctrl->sweeps = mx;
+        ctrl->converged = (open == 0);
+    }
+}
+
+// ---------------------------------------------------------------------------
 // Dataflow schedule.  Every particle's first velocity record carries, in its
 // pad word, the number of contact updates applied to it so far in this solve.
 // In phase s (0 = starting impulses, then one per sweep) the contact at
@@ -670,7 +885,7 @@ __device__ __forceinline__ bool flow_update(const CdGeom& g, const CdWork& w, in
     if constexpr (DIM == 2) {
         T4 va = V[r.ab.x], vb;
         if (!wall) vb = V[r.ab.y];
-        else wall_vel2<T>(g, r.ab.y - g.n, vb);
+        else wall_vel2<T>(g, w, r.ab.y, vb);
         T2 Pnew;
         o = core2d<T>(g, r, va, vb, wall, apply_only, crit, alpha, ravg_prev, Pnew);
         store_xyz<T>(V + r.ab.x, va);
@@ -679,7 +894,7 @@ __device__ __forceinline__ bool flow_update(const CdGeom& g, const CdWork& w, in
     } else {
         T4 va = V[2 * r.ab.x], wa = V[2 * r.ab.x + 1], vb, wb;
         if (!wall) { vb = V[2 * r.ab.y]; wb = V[2 * r.ab.y + 1]; }
-        else wall_vel3<T>(g, r.ab.y - g.n, vb, wb);
+        else wall_vel3<T>(g, w, r.ab.y, vb, wb);
         T4 Pnew;
         o = core3d<T>(g, r, va, wa, vb, wb, wall, apply_only, crit, alpha, ravg_prev, Pnew);
         store_xyz<T>(V + 2 * r.ab.x, va);
@@ -815,6 +1030,8 @@ __device__ __forceinline__ UpdOut apply_staged(const CdGeom& g, const CdWork& w,
     typedef typename Vec<T>::V4 T4;
     typedef typename Vec<T>::V2 T2;
     Rec<DIM, T> r;
+    r.pk = 0;
+    r.mu = (T)g.mu;
     r.ab = sm.ab[i];
     r.geo = sm.geo[i];
     const bool wall = r.ab.y >= g.n;
@@ -829,7 +1046,7 @@ __device__ __forceinline__ UpdOut apply_staged(const CdGeom& g, const CdWork& w,
         r.P = sm.P[i];
         T4 va = sm.V[ia], vb;
         if (!wall) vb = sm.V[ib];
-        else wall_vel2<T>(g, r.ab.y - g.n, vb);
+        else wall_vel2<T>(g, w, r.ab.y, vb);
         T2 Pnew;
         o = core2d<T>(g, r, va, vb, wall, apply_only, crit, alpha, ravg_prev, Pnew);
         sm.V[ia] = va;
@@ -840,7 +1057,7 @@ __device__ __forceinline__ UpdOut apply_staged(const CdGeom& g, const CdWork& w,
         r.P = sm.P[i];
         T4 va = sm.V[2 * ia], wa = sm.V[2 * ia + 1], vb, wb;
         if (!wall) { vb = sm.V[2 * ib]; wb = sm.V[2 * ib + 1]; }
-        else wall_vel3<T>(g, r.ab.y - g.n, vb, wb);
+        else wall_vel3<T>(g, w, r.ab.y, vb, wb);
         T4 Pnew;
         o = core3d<T>(g, r, va, wa, vb, wb, wall, apply_only, crit, alpha, ravg_prev, Pnew);
         sm.V[2 * ia] = va; sm.V[2 * ia + 1] = wa;
@@ -1062,6 +1279,11 @@ cudaError_t cd_launch_unpack(const CdGeom& g, const CdWork& w, double* pos, doub
 
 static const void* sweep_fn(int dim, int precision, int tiled)
 {
+    if (tiled == 3) {
+        if (dim == 2)
+            return precision == CD_FP64 ? (const void*)k_sweep_batch<2, double> : (const void*)k_sweep_batch<2, float>;
+        return precision == CD_FP64 ? (const void*)k_sweep_batch<3, double> : (const void*)k_sweep_batch<3, float>;
+    }
     if (tiled == 2) {
         if (dim == 2)
             return precision == CD_FP64 ? (const void*)k_sweep_flow<2, double> : (const void*)k_sweep_flow<2, float>;
@@ -1087,7 +1309,7 @@ static size_t tile_smem(int dim, int precision)
 int cd_sweep_max_blocks(int precision, int dim, int num_sms)
 {
     int per_sm = 0;
-    for (int tiled = 0; tiled < 3; ++tiled) {
+    for (int tiled = 0; tiled < 4; ++tiled) {
         const void* fn = sweep_fn(dim, precision, tiled);
         size_t dyn = (tiled == 1) ? tile_smem(dim, precision) : 0;
         if (tiled && cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn) != cudaSuccess)
@@ -1112,7 +1334,7 @@ cudaError_t cd_launch_sweep(const CdGeom& g, const CdWork& w, int coop_blocks, i
     double al = alpha;
     int ms = max_sweeps;
     void* args[] = {&ga, &wa, &crit, &al, &ms};
-    const int kind = (g.tile_cells >= 2) ? 1 : (g.dataflow ? 2 : 0);
+    const int kind = (g.npk > 1) ? 3 : ((g.tile_cells >= 2) ? 1 : (g.dataflow ? 2 : 0));
     ++*nl;
     return cudaLaunchCooperativeKernel(sweep_fn(g.dim, precision, kind), dim3(coop_blocks), dim3(CD_SWEEP_THREADS),
                                        args, kind == 1 ? tile_smem(g.dim, precision) : 0, s);
