@@ -69,6 +69,9 @@ def parse():
                     help="0: global colour order; >= 2: tiled colour order with tiles of this many cells")
     ap.add_argument("--dataflow", type=int, default=0,
                     help="1: per-particle update counts instead of a grid barrier per colour")
+    ap.add_argument("--batched-steps", type=int, default=3,
+                    help="timed steps of the 512-packing batched workload (0: skip)")
+    ap.add_argument("--packings", type=int, default=512)
     ap.add_argument("--cpu-sweeps", type=int, default=30,
                     help="sweep cap of the oracle's bounded sample step")
     return ap.parse_args()
@@ -323,6 +326,10 @@ def run_ours(args):
     else:
         roofline = dict(hbm_view, traffic=traffic, kernel=kname, avg_launch_ms=ph["sweep"] / max(args.steps, 1))
 
+    batched = None
+    if args.batched_steps > 0:
+        batched = run_batched(args, device, rank, flush)
+
     e2e = None
     if not args.no_e2e:
         e2e = run_e2e(args, sysg, wl, device, ws)
@@ -345,9 +352,53 @@ def run_ours(args):
                                         "sweeps_per_step": sweeps / max(args.steps, 1),
                                         "steps_not_converged": not_conv, "parallelism": f"replicas x{ws}"}),
             "phase_ms_per_step": {k: v / max(args.steps, 1) for k, v in ph.items()},
-            "wall_s": wall_max, "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
+            "wall_s": wall_max, "roofline": roofline, "batched": batched, "cpu_baseline": cpu, "e2e": e2e,
             "gpu_launches": launches, "clocks": clk}
     print(json.dumps(line), flush=True)
+
+
+def run_batched(args, device, rank, flush):
+    """The batched workload: independent 2D packings (disc counts log-uniform
+    in [200, 20000], mu ~ U[0.1, 0.6], each a pile settled under gravity in a
+    periodic-x box sized to packing fraction 0.5), all stepped by one batched
+    system."""
+    import torch
+    from paper_1104_3516_gb300 import cd, workloads as W
+    batch = W.batched_settling(seed=1108 + rank, n_packings=args.packings)
+    for b in batch:
+        b.max_sweeps = args.max_sweeps
+        b.alpha = args.alpha
+    prec = cd.CD_FP64 if args.precision == "f64" else cd.CD_FP32
+    g = cd.CDSystem(batch[0], device=device, batch=batch, precision=prec, criterion=cd.CD_CONV_GLOBAL_REL,
+                    timing=1, max_contacts=6 * sum(b.n for b in batch))
+    flush.zero_()
+    g.step(1)
+    upd = sweeps = 0
+    ms = sweep_ms = 0.0
+    for _ in range(args.batched_steps):
+        flush.zero_()
+        st = g.step(1)
+        upd += st["total_contact_updates"]
+        sweeps = max(sweeps, st["max_sweeps_in_step"])
+        ms += sum(st["phase_ms"].values())
+        sweep_ms += st["phase_ms"]["sweep"]
+        nc = st["last"]["n_contacts"]
+    stats = g.packing_stats()
+    sw = np.array([p["sweeps"] for p in stats])
+    out = {"value": upd / (ms / 1e3), "unit": UNIT, "packings": len(batch), "particles": int(sum(b.n for b in batch)),
+           "contacts": nc, "steps": args.batched_steps, "ms_per_step": ms / args.batched_steps,
+           "sweep_kernel_ms_per_step": sweep_ms / args.batched_steps,
+           "steps_per_s": args.batched_steps / (ms / 1e3), "max_sweeps_in_step": int(sweeps),
+           "sweeps_last_step": {"min": int(sw.min()), "median": float(np.median(sw)), "max": int(sw.max())},
+           "packings_converged_last_step": int(sum(p["converged"] for p in stats)),
+           "workload": "batched_settling_2d: disc counts log-uniform [200, 20000], mu ~ U[0.1, 0.6], "
+                       "gravity-settled piles in periodic-x boxes at packing fraction 0.5"}
+    if args.precision == "f64":
+        out["fp64_tflops"] = FLOPS_PER_UPDATE_2D * upd / (sweep_ms / 1e3) / 1e12
+        out["alu_frac"] = out["fp64_tflops"] / FP64_PEAK_TFLOPS
+    del g
+    torch.cuda.empty_cache()
+    return out
 
 
 def run_e2e(args, sysg, wl, device, ws):

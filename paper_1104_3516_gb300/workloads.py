@@ -276,16 +276,31 @@ def batch_sizes(seed=1108, n_packings=512, nmin=200, nmax=20000) -> np.ndarray:
     return np.floor(np.exp(math.log(nmin) + u * (math.log(nmax) - math.log(nmin)))).astype(np.int64)
 
 
+def settled_pile(seed, n, phi=0.5, mu=0.3, steps=100):
+    """n discs r ~ U[0.8, 1.2] gravity-deposited into a box of width
+    sqrt(sum pi r^2 / phi) (the square box at packing fraction phi),
+    periodic in x, floor at y = 0, open top: a settled, loaded pile."""
+    r = uniform(seed, n, 0.8, 1.2)
+    area = float(np.sum(math.pi * r * r))
+    L = math.sqrt(area / phi)
+    x = deposit2d(n, r, L, 4.0 * L, seed)
+    top = float(np.max(x[:, 1] + r))
+    wp = np.zeros(6)
+    return _finish("settled_pile_2d", 2, x, r, mu=mu, gravity=(0.0, -1.0, 0.0), box_lo=(0.0, 0.0, 0.0),
+                   box_hi=(L, max(L, top + 2.4), 1.0), periodic=(1, 0, 0), wall_mask=0b0100, wall_pos=wp,
+                   steps=steps, seed=seed)
+
+
 def batched_settling(seed=1108, n_packings=512, nmin=200, nmax=20000, steps=100):
-    """Independent packings: sizes log-uniform, mu ~ U[0.1, 0.6] each, loose
-    jittered lattices at packing fraction 0.5 in square boxes, gravity
-    settling."""
+    """Independent packings: disc counts log-uniform in [nmin, nmax], mu ~
+    U[0.1, 0.6] each, every packing settled under gravity in its box sized
+    to packing fraction 0.5 (see settled_pile)."""
     sizes = batch_sizes(seed, n_packings, nmin, nmax)
     mus = uniform(seed, n_packings, 0.1, 0.6, stream=4)
     out = []
     for b in range(n_packings):
-        w = settling_discs(seed=_seed(seed, 100 + b) & 0xFFFFFFFF, n=int(sizes[b]), phi=0.5, mu=float(mus[b]),
-                           vsig=0.0, steps=steps)
+        w = settled_pile(seed=_seed(seed, 100 + b) & 0xFFFFFFFF, n=int(sizes[b]), phi=0.5, mu=float(mus[b]),
+                         steps=steps)
         w.name = "batched_settling_2d"
         out.append(w)
     return out
