@@ -112,6 +112,14 @@ typedef struct {
                                bounded waits), so colours overlap; one grid
                                barrier per sweep remains for the residual.
                                Same update order, bit-identical results. */
+    double parallel_p;      /* mixed update of Sec. 2.3: the contacts whose key
+                               hashes below p (splitmix64(key ^ seed *
+                               0xD1B54A32D192ED03) / 2^64 < p) are updated in
+                               parallel within each sweep (from the velocities
+                               at the sweep start, applied at its end), the
+                               rest sequentially.  0: pure Gauss-Seidel.
+                               Plain systems with the colour-barrier schedule
+                               only. */
 } cd_params;
 
 typedef struct cd_system cd_system;

@@ -60,6 +60,7 @@ class cd_params(C.Structure):
         ("timing", C.c_int64),
         ("tile_cells", C.c_int64),
         ("dataflow", C.c_int64),
+        ("parallel_p", C.c_double),
     ]
 
 
@@ -282,7 +283,8 @@ def cd_last_error(sysptr=None) -> str:
 # --- convenience object ----------------------------------------------------------
 
 def make_params(wl, precision=CD_FP64, criterion=CD_CONV_GLOBAL_REL, max_contacts=None, warm_start=1, rotations=1,
-                seed=None, max_sweeps=None, alpha=None, timing=0, tile_cells=0, dataflow=0) -> cd_params:
+                seed=None, max_sweeps=None, alpha=None, timing=0, tile_cells=0, dataflow=0,
+                parallel_p=0.0) -> cd_params:
     p = cd_params()
     p.dim = wl.dim
     p.precision = precision
@@ -311,6 +313,7 @@ def make_params(wl, precision=CD_FP64, criterion=CD_CONV_GLOBAL_REL, max_contact
     p.timing = int(timing)
     p.tile_cells = int(tile_cells)
     p.dataflow = int(dataflow)
+    p.parallel_p = float(parallel_p)
     return p
 
 

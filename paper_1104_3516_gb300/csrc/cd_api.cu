@@ -153,6 +153,7 @@ static size_t layout(cd_system* s, char* base, CdWork* w)
     t.c_abs = L.take<double>(base, cap);
     t.c_flag = L.take<int>(base, cap);
     t.act_cnt = L.take<int>(base, 4);
+    t.c_dpar = L.take<double>(base, s->g.par_p > 0.0 ? cap * s->pw : 1);
     if (w) *w = t;
     return (L.off + 255) & ~(size_t)255;
 }
@@ -454,6 +455,15 @@ static cd_status create_impl(const cd_params* params, int64_t npk, const int64_t
     }
     g.ntc = (g.tile_cells >= 2) ? (1 << p.dim) : 1;
     g.dataflow = (p.dataflow && g.tile_cells == 0 && npk == 1) ? 1 : 0;
+    if (!(p.parallel_p >= 0.0 && p.parallel_p <= 1.0)) {
+        delete s;
+        return fail(nullptr, CD_ERR_INVALID_ARG, "parallel_p must be in [0, 1]");
+    }
+    if (p.parallel_p > 0.0 && (npk > 1 || g.tile_cells != 0 || g.dataflow)) {
+        delete s;
+        return fail(nullptr, CD_ERR_INVALID_ARG, "parallel_p needs a plain system with the colour-barrier schedule");
+    }
+    g.par_p = p.parallel_p;
     if (g.tile_cells >= 2 && (double)g.ntiles * CD_KLOCAL > 1.0e8) {
         delete s;
         return fail(nullptr, CD_ERR_INVALID_ARG, "too many tiles: raise tile_cells");

@@ -47,6 +47,23 @@ __global__ void k_p2c_fill(CdGeom g, CdWork w)
     }
 }
 
+// Each particle's contact list in ascending key order (the atomic fill leaves
+// it in arrival order); makes every later per-particle accumulation
+// deterministic.
+__global__ void k_p2c_sort(CdGeom g, CdWork w)
+{
+    if (w.ctrl->skip) return;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < g.n; i += gridDim.x * blockDim.x) {
+        int b = w.p2c_off[i], e = w.p2c_off[i + 1];
+        for (int k = b + 1; k < e; ++k) {
+            int v = w.p2c[k];
+            int j = k - 1;
+            while (j >= b && w.p2c[j] > v) { w.p2c[j + 1] = w.p2c[j]; --j; }
+            w.p2c[j + 1] = v;
+        }
+    }
+}
+
 // Persistent cooperative kernel: Jones-Plassmann rounds separated by the
 // bounded grid barrier.  `prio` scratch lives in the chunk buffer (8 bytes per
 // contact is reserved there by the workspace layout).
@@ -404,6 +421,11 @@ cudaError_t cd_launch_colour(const CdGeom& g, const CdWork& w, int coop_blocks, 
     k_p2c_count<<<gc, CD_BLOCK, 0, s>>>(g, w); ++*nl;
     if ((e = cd_scan_exclusive(w.p2c_cnt, w.p2c_off, g.n + 1, w.scan_tmp, nullptr, s, nl)) != cudaSuccess) return e;
     k_p2c_fill<<<gc, CD_BLOCK, 0, s>>>(g, w); ++*nl;
+    {
+        int gn = (g.n + CD_BLOCK - 1) / CD_BLOCK;
+        if (gn > 4096) gn = 4096;
+        k_p2c_sort<<<gn, CD_BLOCK, 0, s>>>(g, w); ++*nl;
+    }
     if (tiled) {
         if (g.dim == 2) k_contact_tile<2><<<gc, CD_BLOCK, 0, s>>>(g, w, pos);
         else k_contact_tile<3><<<gc, CD_BLOCK, 0, s>>>(g, w, pos);

@@ -125,7 +125,9 @@ struct CdWork {
     double* c_abs;      // cap (key order): |P| of the last update
     int* c_flag;        // cap (key order): local test bits of the last update
     int* act_cnt;       // 3 counters of packings still iterating
+    double* c_dpar;     // cap * pw (key order): impulse change of a parallel contact
 };
+
 
 // Per-packing statistics layout in pk_stats.
 enum { PKS_SWEEPS = 0, PKS_CONV, PKS_RESID, PKS_RAVG, PKS_RPREV, PKS_NC, PKS_WF0, CD_PKSTATS = PKS_WF0 + 6 };
@@ -157,6 +159,7 @@ struct CdGeom {
     int dataflow;       // 1: per-particle update counts instead of per-colour barriers
     int npk;            // packings (1 for a plain system)
     int ncell_total;    // cells of all packings' grids
+    double par_p;       // parallel fraction of the mixed update (0: Gauss-Seidel)
 };
 
 // ---------------------------------------------------------------------------
@@ -174,6 +177,17 @@ __host__ __device__ __forceinline__ unsigned long long cd_splitmix64(unsigned lo
 __host__ __device__ __forceinline__ unsigned long long cd_key(int a, int b)
 {
     return ((unsigned long long)(unsigned)a << 32) | (unsigned long long)(unsigned)b;
+}
+
+// Mixed update (Sec. 2.3): a contact is in the parallel subset when the hash
+// of its key falls below p.
+__device__ __forceinline__ bool cd_is_parallel(double p, unsigned long long seed, unsigned long long key)
+{
+    if (p <= 0.0) return false;
+    if (p >= 1.0) return true;
+    unsigned long long h = cd_splitmix64(key ^ (seed * 0xD1B54A32D192ED03ULL));
+    double u = (double)(h >> 11) * (1.0 / 9007199254740992.0);
+    return u < p;
 }
 
 // ---------------------------------------------------------------------------

@@ -26,6 +26,17 @@ template <typename T> struct Vec;
 template <> struct Vec<double> { typedef double4 V4; typedef double2 V2; };
 template <> struct Vec<float> { typedef float4 V4; typedef float2 V2; };
 
+// Stores the first three components of a velocity record, leaving the fourth.
+template <typename T>
+__device__ __forceinline__ void store_xyz_plain(typename Vec<T>::V4* dst, const typename Vec<T>::V4& v)
+{
+    typedef typename Vec<T>::V2 T2;
+    T2 xy;
+    xy.x = v.x; xy.y = v.y;
+    *reinterpret_cast<T2*>(dst) = xy;
+    reinterpret_cast<T*>(dst)[2] = v.z;
+}
+
 // ---------------------------------------------------------------------------
 // Static per-particle record (inv_m, r, r / I, 0) in the sweep's real type.
 // ---------------------------------------------------------------------------
@@ -449,13 +460,17 @@ __device__ __forceinline__ void colour_phase(const CdGeom& g, const CdWork& w, c
 {
     const int end = s_off[k + 1];
     int p = s_off[k] + tid;
+    const bool mixed = !apply_only && g.par_p > 0.0;   // parallel contacts were done in their own phase
     if (p < end) {
-        UpdOut o = apply_rec<DIM, T>(g, w, p, nxt, apply_only, crit, alpha, ravg_prev);
-        acc[0] += o.pabs; acc[1] += (double)o.rel_ok; acc[2] += (double)o.bad;
+        if (!(mixed && cd_is_parallel(g.par_p, g.seed, cd_key(nxt.ab.x, nxt.ab.y)))) {
+            UpdOut o = apply_rec<DIM, T>(g, w, p, nxt, apply_only, crit, alpha, ravg_prev);
+            acc[0] += o.pabs; acc[1] += (double)o.rel_ok; acc[2] += (double)o.bad;
+        }
         for (p += stride; p < end; p += stride) {
             Rec<DIM, T> r;
             load_rec<DIM, T>(g, w, p, r);
-            o = apply_rec<DIM, T>(g, w, p, r, apply_only, crit, alpha, ravg_prev);
+            if (mixed && cd_is_parallel(g.par_p, g.seed, cd_key(r.ab.x, r.ab.y))) continue;
+            UpdOut o = apply_rec<DIM, T>(g, w, p, r, apply_only, crit, alpha, ravg_prev);
             acc[0] += o.pabs; acc[1] += (double)o.rel_ok; acc[2] += (double)o.bad;
         }
     }
@@ -529,6 +544,90 @@ __device__ __forceinline__ void finish_solve(const CdGeom& g, const CdWork& w, i
 }
 
 // ---------------------------------------------------------------------------
+// Mixed update (Sec. 2.3).  Parallel contacts compute their new impulse from
+// the velocities at the start of the sweep (no velocity change yet) and keep
+// the change; after the sequential colours each particle adds the changes of
+// its parallel contacts in ascending key order.
+// ---------------------------------------------------------------------------
+template <int DIM, typename T>
+__device__ __forceinline__ UpdOut par_compute(const CdGeom& g, const CdWork& w, int p, const Rec<DIM, T>& r, int crit,
+                                              double alpha, double ravg_prev)
+{
+    typedef typename Vec<T>::V4 T4;
+    typedef typename Vec<T>::V2 T2;
+    const T4* V = (const T4*)w.V;
+    const bool wall = r.ab.y >= g.n;
+    const int c = w.perm[p];
+    UpdOut o;
+    if constexpr (DIM == 2) {
+        T4 va = V[r.ab.x], vb;
+        if (!wall) vb = V[r.ab.y];
+        else wall_vel2<T>(g, w, r.ab.y, vb);
+        T2 Pnew;
+        o = core2d<T>(g, r, va, vb, wall, false, crit, alpha, ravg_prev, Pnew);
+        ((T2*)w.c_P)[p] = Pnew;
+        w.c_dpar[2 * c] = (double)(Pnew.x - r.P.x);
+        w.c_dpar[2 * c + 1] = (double)(Pnew.y - r.P.y);
+    } else {
+        T4 va = V[2 * r.ab.x], wa = V[2 * r.ab.x + 1], vb, wb;
+        if (!wall) { vb = V[2 * r.ab.y]; wb = V[2 * r.ab.y + 1]; }
+        else wall_vel3<T>(g, w, r.ab.y, vb, wb);
+        T4 Pnew;
+        o = core3d<T>(g, r, va, wa, vb, wb, wall, false, crit, alpha, ravg_prev, Pnew);
+        ((T4*)w.c_P)[p] = Pnew;
+        w.c_dpar[4 * c] = (double)(Pnew.x - r.P.x);
+        w.c_dpar[4 * c + 1] = (double)(Pnew.y - r.P.y);
+        w.c_dpar[4 * c + 2] = (double)(Pnew.z - r.P.z);
+        w.c_dpar[4 * c + 3] = (double)(Pnew.w - r.P.w);
+    }
+    return o;
+}
+
+template <int DIM, typename T>
+__device__ __forceinline__ void par_apply(const CdGeom& g, const CdWork& w, int tid, int stride)
+{
+    typedef typename Vec<T>::V4 T4;
+    T4* V = (T4*)w.V;
+    const T4* S = (const T4*)w.S;
+    for (int i = tid; i < g.n; i += stride) {
+        const int e = w.p2c_off[i + 1];
+        bool any = false;
+        T4 v, om;
+        const T4 si = S[i];
+        for (int q = w.p2c_off[i]; q < e; ++q) {
+            const int c = w.p2c[q];
+            const int2 ab = w.pairs[c];
+            if (!cd_is_parallel(g.par_p, g.seed, cd_key(ab.x, ab.y))) continue;
+            if (!any) {
+                any = true;
+                if (DIM == 2) v = V[i];
+                else { v = V[2 * i]; om = V[2 * i + 1]; }
+            }
+            const T sign = (ab.x == i) ? (T)-1 : (T)1;
+            const T nx = (T)w.nrm[3 * c], ny = (T)w.nrm[3 * c + 1], nz = (T)w.nrm[3 * c + 2];
+            if (DIM == 2) {
+                const T dPn = (T)w.c_dpar[2 * c], dPt = (T)w.c_dpar[2 * c + 1];
+                const T dx = dPn * nx - dPt * ny, dy = dPn * ny + dPt * nx;
+                v.x += sign * si.x * dx; v.y += sign * si.x * dy;
+                v.z -= si.z * dPt;
+            } else {
+                const T dPn = (T)w.c_dpar[4 * c];
+                const T dx = dPn * nx + (T)w.c_dpar[4 * c + 1];
+                const T dy = dPn * ny + (T)w.c_dpar[4 * c + 2];
+                const T dz = dPn * nz + (T)w.c_dpar[4 * c + 3];
+                const T cx = ny * dz - nz * dy, cy = nz * dx - nx * dz, cz = nx * dy - ny * dx;
+                v.x += sign * si.x * dx; v.y += sign * si.x * dy; v.z += sign * si.x * dz;
+                om.x -= si.z * cx; om.y -= si.z * cy; om.z -= si.z * cz;
+            }
+        }
+        if (any) {
+            if (DIM == 2) store_xyz_plain<T>(V + i, v);
+            else { store_xyz_plain<T>(V + 2 * i, v); V[2 * i + 1] = om; }
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
 // The persistent sweep kernel
 // ---------------------------------------------------------------------------
 template <int DIM, typename T>
@@ -572,9 +671,27 @@ k_sweep(CdGeom g, CdWork w, int crit, double alpha, int max_sweeps)
             const int buf = (sweeps & 1) ? 0 : 1;   // alternate with the buffer of the previous sweep
             double* part = w.partials + (size_t)buf * 3 * nb;
             double a3[3] = {0.0, 0.0, 0.0};
+            const bool mixed = g.par_p > 0.0;
+            if (mixed) {
+                for (int p = tid; p < nc; p += stride) {
+                    Rec<DIM, T> r;
+                    load_rec<DIM, T>(g, w, p, r);
+                    if (!cd_is_parallel(g.par_p, g.seed, cd_key(r.ab.x, r.ab.y))) continue;
+                    UpdOut o = par_compute<DIM, T>(g, w, p, r, crit, alpha, ravg_prev);
+                    a3[0] += o.pabs; a3[1] += (double)o.rel_ok; a3[2] += (double)o.bad;
+                }
+                if (!cd_grid_sync(ctrl, nb, epoch)) return;
+                // the prefetched record of colour 0 may belong to a parallel contact whose
+                // impulse just changed: reload it
+                if (s_off[0] + tid < s_off[1]) load_rec<DIM, T>(g, w, s_off[0] + tid, nxt);
+            }
             for (int k = 0; k < K; ++k) {
                 colour_phase<DIM, T>(g, w, s_off, k, (k + 1 < K) ? k + 1 : 0, tid, stride, nxt, false, crit, alpha,
                                      ravg_prev, a3);
+                if (mixed && k == K - 1) {
+                    if (!cd_grid_sync(ctrl, nb, epoch)) return;
+                    par_apply<DIM, T>(g, w, tid, stride);
+                }
                 if (k == K - 1) {
                     block_sum<3>(a3, s_red);
                     if (threadIdx.x == 0) {

@@ -369,3 +369,34 @@ def test_dataflow_fp32_and_convergence():
     for a, b in zip(gst, ost):
         assert a["last"]["sweeps"] == b["sweeps"]
     assert impulse_err(g.contacts()["impulse"], o.impulses) <= 1e-11
+
+
+# --- mixed parallel / sequential update (Sec. 2.3) -------------------------------
+
+@pytest.mark.parametrize("p", [0.3, 1.0])
+@pytest.mark.parametrize("k", [1, 5, 20])
+def test_mixed_update_sweep_by_sweep(p, k):
+    from paper_1104_3516_gb300 import cd
+    wl = CASES["dense_deposit"]
+    g, o, gst, ost = run_pair(wl, criterion=cd.CD_CONV_NONE, max_sweeps=k, parallel_p=p)
+    assert impulse_err(g.contacts()["impulse"], o.impulses) <= FP64_TOL
+    s = g.state()
+    vs = max(float(np.abs(o.v).max()), 1e-300)
+    assert float(np.abs(s["v"].reshape(-1) - o.v).max()) <= FP64_TOL * vs
+
+
+def test_parallel_fraction_destabilises_a_dense_packing():
+    """Sec. 2.3: a large enough parallel fraction makes the iteration diverge
+    in a dense packing while the sequential scheme stays bounded; GPU and
+    oracle agree on both."""
+    from paper_1104_3516_gb300 import cd
+    wl = W.dense_biaxial_discs(n=2000, wall_speed=1.0)
+    wl.gravity = (0.0, 0.0, 0.0)
+    peak = {}
+    for p in (0.0, 0.5):
+        g, o, gst, ost = run_pair(wl, criterion=cd.CD_CONV_NONE, max_sweeps=120, parallel_p=p, warm_start=0)
+        pg = float(np.abs(g.contacts()["impulse"]).max())
+        po = float(np.abs(o.impulses).max())
+        assert pg == pytest.approx(po, rel=1e-9)
+        peak[p] = pg
+    assert peak[0.5] > 1e6 * peak[0.0]
