@@ -245,6 +245,22 @@ typedef struct {
  * packing 0) into a host array of count entries.  Synchronises. */
 cd_status cd_get_packing_stats(cd_system* sys, int64_t first, int64_t count, cd_packing_stats* out_host);
 
+/* Distribution of contact-force orientations (Sec. 4.4, Fig. 14), 2D: over
+ * the contacts with a nonzero impulse, phi = arctan(R_y / R_x) folded into
+ * [0, pi) is counted in nbins equal bins (host array of nbins).  Uses the
+ * current contact set and impulses.  Synchronises. */
+cd_status cd_force_orientation(cd_system* sys, int64_t nbins, int64_t* counts_host);
+
+/* Stress profile (Sec. 4.4, Fig. 15): for stripes [lo + i w, lo + (i+1) w)
+ * along axis (i < nstripes), sigma_{axis,axis} = (1/V) sum R_axis l_axis over
+ * the contacts whose contact point (middle of the gap, Sec. 3.1) lies in the
+ * stripe, R = P / dt the contact force on body b, l the branch vector from
+ * body a's centre to body b's centre (minimum image) or to the wall surface,
+ * V = w times the box extents of the other axes (compression positive).  Host
+ * array of nstripes.  Plain systems.  Synchronises. */
+cd_status cd_stress_profile(cd_system* sys, int64_t axis, double lo, double width, int64_t nstripes,
+                            double* sigma_host);
+
 /* Current wall plane positions (6 doubles, host memory; packing 0 of a
  * batch).  Synchronises. */
 cd_status cd_get_walls(cd_system* sys, double* wall_pos_host);

@@ -320,3 +320,62 @@ class OracleSystem:
     @property
     def impulses(self):
         return self.P[: self.nc].copy()
+
+
+# ---------------------------------------------------------------------------
+# Observables of Sec. 4.4 (Figs. 14-15), restated in numpy from the impulses.
+# ---------------------------------------------------------------------------
+
+def force_orientation(P, normal, nbins=18):
+    """Fig. 14: phi = arctan(R_y / R_x) of every contact force with a nonzero
+    impulse, folded into [0, pi), counted in nbins equal bins (2D)."""
+    P = np.asarray(P, dtype=np.float64).reshape(-1, 2)
+    normal = np.asarray(normal, dtype=np.float64).reshape(-1, 3)
+    keep = ~((P[:, 0] == 0.0) & (P[:, 1] == 0.0))
+    pn, pt = P[keep, 0], P[keep, 1]
+    nx, ny = normal[keep, 0], normal[keep, 1]
+    rx = pn * nx - pt * ny
+    ry = pn * ny + pt * nx
+    phi = np.arctan2(ry, rx)
+    phi = np.where(phi < 0.0, phi + np.pi, phi)
+    phi = np.where(phi >= np.pi, phi - np.pi, phi)
+    b = np.floor(phi / (np.pi / nbins)).astype(np.int64)
+    b = np.clip(b, 0, nbins - 1)
+    return np.bincount(b, minlength=nbins)
+
+
+def stress_profile(x, r, n_particles, pairs, normal, gap, P, dt, axis, lo, width, nstripes, box_extent,
+                   periodic_length=None):
+    """Fig. 15: sigma_kk per stripe along axis k, sum of R_k l_k over the
+    contacts whose contact point (middle of the gap, Sec. 3.1) lies in the
+    stripe, divided by the stripe volume (width x box_extent of the other
+    axes); l is the branch vector a -> b, or a's centre -> wall surface."""
+    pairs = np.asarray(pairs)
+    D = 2 if np.asarray(P).reshape(len(pairs), -1).shape[1] == 2 else 3
+    x = np.asarray(x, dtype=np.float64).reshape(-1, D)
+    P = np.asarray(P, dtype=np.float64).reshape(len(pairs), -1)
+    normal = np.asarray(normal, dtype=np.float64).reshape(-1, 3)
+    sig = np.zeros(nstripes)
+    for c, (a, b) in enumerate(pairs):
+        n = normal[c]
+        if D == 2:
+            t = np.array([-n[1], n[0], 0.0])
+            R = (P[c, 0] * n + P[c, 1] * t) / dt
+        else:
+            R = (P[c, 0] * n + np.concatenate([P[c, 1:], []])) / dt
+        if R[axis] == 0.0:
+            continue
+        point = x[a, axis] + (r[a] + 0.5 * gap[c]) * n[axis]
+        if b < n_particles:
+            l = x[b, axis] - x[a, axis]
+            if periodic_length:
+                if l > 0.5 * periodic_length:
+                    l -= periodic_length
+                elif l < -0.5 * periodic_length:
+                    l += periodic_length
+        else:
+            l = (r[a] + gap[c]) * n[axis]
+        q = np.floor((point - lo) / width)
+        if 0 <= q < nstripes:
+            sig[int(q)] += R[axis] * l
+    return sig / (width * box_extent)

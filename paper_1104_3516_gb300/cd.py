@@ -139,6 +139,8 @@ SIGNATURES = [
     ("cd_get_contacts", C.c_int, [_P, C.POINTER(C.c_int64), _P, _P, _P, _P, _P]),
     ("cd_get_walls", C.c_int, [_P, C.POINTER(C.c_double)]),
     ("cd_get_packing_stats", C.c_int, [_P, C.c_int64, C.c_int64, C.POINTER(cd_packing_stats)]),
+    ("cd_force_orientation", C.c_int, [_P, C.c_int64, C.POINTER(C.c_int64)]),
+    ("cd_stress_profile", C.c_int, [_P, C.c_int64, C.c_double, C.c_double, C.c_int64, C.POINTER(C.c_double)]),
     ("cd_upload_state", C.c_int, [_P, _P, _P, _P]),
     ("cd_download_state", C.c_int, [_P, _P, _P, _P]),
     ("cd_detect_contacts_noalloc", C.c_int, [C.POINTER(cd_params), C.c_int64, _P, _P, _P, _P, C.c_int64, _P, _P,
@@ -198,6 +200,18 @@ def cd_get_packing_stats(sysptr, first, count):
     arr = (cd_packing_stats * max(count, 1))()
     _check(sysptr, lib().cd_get_packing_stats(sysptr, int(first), int(count), arr))
     return [arr[i].as_dict() for i in range(count)]
+
+
+def cd_force_orientation(sysptr, nbins=18) -> np.ndarray:
+    out = (C.c_int64 * nbins)()
+    _check(sysptr, lib().cd_force_orientation(sysptr, int(nbins), out))
+    return np.array(list(out), dtype=np.int64)
+
+
+def cd_stress_profile(sysptr, axis, lo, width, nstripes) -> np.ndarray:
+    out = (C.c_double * nstripes)()
+    _check(sysptr, lib().cd_stress_profile(sysptr, int(axis), float(lo), float(width), int(nstripes), out))
+    return np.array(list(out))
 
 
 def cd_workspace_size(sysptr) -> int:
@@ -416,6 +430,12 @@ class CDSystem:
 
     def walls(self) -> np.ndarray:
         return cd_get_walls(self._h)
+
+    def force_orientation(self, nbins=18):
+        return cd_force_orientation(self._h, nbins)
+
+    def stress_profile(self, axis, lo, width, nstripes):
+        return cd_stress_profile(self._h, axis, lo, width, nstripes)
 
     def packing_stats(self):
         return cd_get_packing_stats(self._h, 0, getattr(self, "n_packings", 1))

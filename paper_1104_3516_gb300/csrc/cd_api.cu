@@ -154,6 +154,7 @@ static size_t layout(cd_system* s, char* base, CdWork* w)
     t.c_flag = L.take<int>(base, cap);
     t.act_cnt = L.take<int>(base, 4);
     t.c_dpar = L.take<double>(base, s->g.par_p > 0.0 ? cap * s->pw : 1);
+    t.obs = L.take<double>(base, CD_OBS_MAX);
     if (w) *w = t;
     return (L.off + 255) & ~(size_t)255;
 }
@@ -727,6 +728,44 @@ extern "C" cd_status cd_get_packing_stats(cd_system* s, int64_t first, int64_t c
             o.wall_pos[k] = hw[(size_t)(6 * i + k)];
         }
     }
+    return CD_OK;
+}
+
+extern "C" cd_status cd_force_orientation(cd_system* s, int64_t nbins, int64_t* counts_host)
+{
+    cd_status st = need_ready(s);
+    if (st != CD_OK) return st;
+    if (s->p.dim != 2) return fail(s, CD_ERR_INVALID_ARG, "the force-orientation distribution is defined in 2D");
+    if (nbins < 1 || nbins > CD_OBS_MAX || !counts_host) return fail(s, CD_ERR_INVALID_ARG, "bad nbins or output");
+    if (!s->has_contacts) return fail(s, CD_ERR_STATE, "no contact set");
+    unsigned long long* d = reinterpret_cast<unsigned long long*>(s->w.obs);
+    CD_CUDA(s, cd_launch_orient(s->g, s->w, (int)nbins, d, s->stream, &s->launches));
+    std::vector<unsigned long long> h((size_t)nbins);
+    CD_CUDA(s, cudaMemcpyAsync(h.data(), d, sizeof(unsigned long long) * h.size(), cudaMemcpyDeviceToHost, s->stream));
+    CD_CUDA(s, cudaStreamSynchronize(s->stream));
+    for (int64_t i = 0; i < nbins; ++i) counts_host[i] = (int64_t)h[(size_t)i];
+    return CD_OK;
+}
+
+extern "C" cd_status cd_stress_profile(cd_system* s, int64_t axis, double lo, double width, int64_t nstripes,
+                                       double* sigma_host)
+{
+    cd_status st = need_ready(s);
+    if (st != CD_OK) return st;
+    if (axis < 0 || axis >= s->p.dim) return fail(s, CD_ERR_INVALID_ARG, "axis out of range");
+    if (!(width > 0.0) || nstripes < 1 || nstripes > CD_OBS_MAX || !sigma_host)
+        return fail(s, CD_ERR_INVALID_ARG, "bad stripes or output");
+    if (s->g.npk > 1) return fail(s, CD_ERR_INVALID_ARG, "stress profiles are per system (use a plain system)");
+    if (!s->has_contacts) return fail(s, CD_ERR_STATE, "no contact set");
+    CD_CUDA(s, cd_launch_stress(s->g, s->w, s->pos, s->radius, (int)axis, lo, width, (int)nstripes, s->w.obs,
+                                s->stream, &s->launches));
+    CD_CUDA(s, cudaMemcpyAsync(sigma_host, s->w.obs, sizeof(double) * (size_t)nstripes, cudaMemcpyDeviceToHost,
+                               s->stream));
+    CD_CUDA(s, cudaStreamSynchronize(s->stream));
+    double area = width;
+    for (int k = 0; k < s->p.dim; ++k)
+        if (k != axis) area *= s->g.L[k];
+    for (int64_t i = 0; i < nstripes; ++i) sigma_host[i] /= area;
     return CD_OK;
 }
 

@@ -126,7 +126,9 @@ struct CdWork {
     int* c_flag;        // cap (key order): local test bits of the last update
     int* act_cnt;       // 3 counters of packings still iterating
     double* c_dpar;     // cap * pw (key order): impulse change of a parallel contact
+    double* obs;        // CD_OBS_MAX doubles: observable results
 };
+#define CD_OBS_MAX 65536
 
 
 // Per-packing statistics layout in pk_stats.
@@ -273,6 +275,10 @@ cudaError_t cd_launch_order_tiled(const CdGeom& g, const CdWork& w, const double
                                   cudaStream_t stream, int* nl);
 cudaError_t cd_launch_need(const CdGeom& g, const CdWork& w, cudaStream_t stream, int* nl);
 cudaError_t cd_launch_pk_ranges(const CdGeom& g, const CdWork& w, cudaStream_t stream, int* nl);
+cudaError_t cd_launch_orient(const CdGeom& g, const CdWork& w, int nbins, unsigned long long* counts,
+                             cudaStream_t stream, int* nl);
+cudaError_t cd_launch_stress(const CdGeom& g, const CdWork& w, const double* pos, const double* radius, int axis,
+                             double lo, double width, int ns, double* sig, cudaStream_t stream, int* nl);
 cudaError_t cd_launch_sweep(const CdGeom& g, const CdWork& w, int coop_blocks, int precision, int criterion,
                             double alpha, int max_sweeps, int pw, cudaStream_t stream, int* nl);
 cudaError_t cd_launch_unpack(const CdGeom& g, const CdWork& w, double* pos, double* vel, double* omega,

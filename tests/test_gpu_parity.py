@@ -400,3 +400,41 @@ def test_parallel_fraction_destabilises_a_dense_packing():
         assert pg == pytest.approx(po, rel=1e-9)
         peak[p] = pg
     assert peak[0.5] > 1e6 * peak[0.0]
+
+
+# --- observables (Sec. 4.4, Figs. 14-15) -------------------------------------------
+
+def test_observables_match_the_oracle():
+    """Orientation histogram: bins may differ by the contacts whose angle sits
+    within an ulp of a bin edge (atan2 of the C library vs CUDA) or whose
+    impulse is within rounding of zero; the stress profile to 1e-9."""
+    from paper_1104_3516_gb300 import cd
+    wl = CASES["dense_deposit"]
+    g, o, gst, ost = run_pair(wl, criterion=cd.CD_CONV_NONE, max_sweeps=40)
+    hg = g.force_orientation(18)
+    ho = O.force_orientation(o.impulses, o.normal[: o.nc], 18)
+    assert abs(int(hg.sum()) - int(ho.sum())) <= 2
+    assert int(np.abs(hg - ho).max()) <= 2
+    w = 2.0 * float(wl.r.max())
+    ns = int(np.ceil(wl.box_hi[1] / w))
+    sg = g.stress_profile(1, 0.0, w, ns)
+    so = O.stress_profile(o.x, wl.r, wl.n, o.contacts, o.normal[: o.nc], o.gap[: o.nc], o.impulses, wl.dt, 1, 0.0, w,
+                          ns, wl.box_hi[0] - wl.box_lo[0], periodic_length=wl.box_hi[0] - wl.box_lo[0])
+    assert np.allclose(sg, so, rtol=0, atol=1e-9 * float(np.abs(so).max()))
+
+
+def test_gpu_column_stress_closed_form():
+    n = 6
+    wl = cases.column(n=n)
+    g = gpu_system(wl, alpha=1e-15, max_sweeps=20000)
+    g.step(1)
+    hist = g.force_orientation(18)
+    assert hist.sum() == n and hist[9] == n
+    m, r = 1.0 / wl.inv_m[0], wl.r[0]
+    Lx = wl.box_hi[0] - wl.box_lo[0]
+    expect = np.zeros(n + 1)
+    expect[0] = n * m * cases.G * r / (Lx * 2 * r)
+    for k in range(1, n):
+        expect[k] = (n - k) * m * cases.G * 2 * r / (Lx * 2 * r)
+    # positions moved by one Euler step of a static column: contacts keep their stripes
+    assert np.allclose(g.stress_profile(1, 0.0, 2 * r, n + 1), expect, rtol=1e-9, atol=0)

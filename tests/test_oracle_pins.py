@@ -303,3 +303,26 @@ def test_jacobi_update_needs_more_sweeps_than_gauss_seidel():
         assert np.allclose(s.impulses[:, 0], F * DT, rtol=1e-5)
         out[p] = st["sweeps"]
     assert out[1.0] > 1.2 * out[0.0]
+
+
+# --- observables of Sec. 4.4 ---------------------------------------------------
+
+def test_column_observables_closed_form():
+    """A static column: every force is vertical (orientation bin of pi/2), and
+    the stress in a stripe of width 2 r equals (load x branch) / (L_x x 2 r):
+    the floor contact carries n m g with branch r, the contact below disc k
+    (from the top) carries k m g with branch 2 r."""
+    n = 6
+    wl = cases.column(n=n)
+    s, st = _one_step(wl, order=O.ORDER_COLOUR, criterion=O.CRIT_GLOBAL_REL, alpha=1e-15, max_sweeps=20000)
+    hist = O.force_orientation(s.impulses, s.normal[: s.nc], nbins=18)
+    assert hist.sum() == n and hist[9] == n
+    m, r = 1.0 / wl.inv_m[0], wl.r[0]
+    Lx = wl.box_hi[0] - wl.box_lo[0]
+    sig = O.stress_profile(s.x, wl.r, wl.n, s.contacts, s.normal[: s.nc], s.gap[: s.nc], s.impulses, DT, 1, 0.0,
+                           2 * r, n + 1, Lx)
+    expect = np.zeros(n + 1)
+    expect[0] = n * m * G * r / (Lx * 2 * r)
+    for k in range(1, n):       # contact between disc k-1 and k (from the bottom) lies at y = 2 k r
+        expect[k] = (n - k) * m * G * 2 * r / (Lx * 2 * r)
+    assert np.allclose(sig, expect, rtol=1e-9, atol=0)
