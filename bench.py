@@ -60,7 +60,7 @@ def parse():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--precision", choices=["f64", "f32"], default="f64")
-    ap.add_argument("--n", type=int, default=100_000)
+    ap.add_argument("--n-discs", "--n", dest="n", type=int, default=100_000)
     ap.add_argument("--max-sweeps", type=int, default=1000)
     ap.add_argument("--alpha", type=float, default=1e-6)
     ap.add_argument("--no-e2e", action="store_true")
@@ -179,17 +179,23 @@ class ClockSampler:
         return {"sm_mhz": statistics.median(sm), "sm_max_mhz": smax, "samples": len(sm), "reasons": sorted(reasons)}
 
 
-def dist_init(args):
+def dist_init(args, backend=None):
+    """Joins the process group torchrun set up (RANK / WORLD_SIZE /
+    MASTER_* in the environment); returns (rank, world size, local rank).
+    The CUDA arm uses NCCL for its two timing reductions, the oracle arm gloo."""
     ws = int(os.environ.get("WORLD_SIZE", "1"))
     if ws > 1:
         import torch.distributed as dist
-        backend = "nccl" if args.impl == "ours" else "gloo"
+        if backend is None:
+            backend = "nccl" if args.impl == "ours" else "gloo"
         dist.init_process_group(backend=backend)
         return dist.get_rank(), ws, int(os.environ.get("LOCAL_RANK", "0"))
     return 0, 1, 0
 
 
 def reduce_max_sum(vals_max, vals_sum, ws, device):
+    """Max over ranks of the times, sum over ranks of the work: the only
+    cross-rank traffic of the benchmark (no data-path collective)."""
     if ws == 1:
         return vals_max, vals_sum
     import torch
