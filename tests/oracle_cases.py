@@ -76,3 +76,40 @@ def head_on(v1, v2, r1=1.0, r2=1.0, gap=None):
     x = [[0.0, 0.0], [r1 + r2 + gap, 0.0]]
     return _wl("head_on", 2, x, [r1, r2], v=[[v1, 0.0], [v2, 0.0]], dt=DT, mu=0.3, gravity=(0.0, 0.0, 0.0),
                box_lo=(-20.0, -20.0, 0.0), box_hi=(20.0, 20.0, 1.0))
+
+
+def colliding_gas(n=40, seed=1110, vsig=2.0, dt=0.01, phi=0.55, mu=0.3):
+    """A loose lattice of discs in a box with floor and side walls, gravity 1,
+    fast random velocities and a long time step, so that within a few steps
+    many pairs collide (open, sticking and sliding contacts side by side)."""
+    from paper_1104_3516_gb300.workloads import settling_discs
+    wl = settling_discs(seed=seed, n=n, phi=phi, mu=mu, vsig=vsig, steps=5)
+    wl.dt = dt
+    return wl
+
+
+def periodic_gas(n=36, seed=1111, vsig=2.0, dt=0.01, phi=0.55, mu=0.3):
+    """The same gas in a box periodic in x and y: no walls, no gravity (total
+    momentum is then conserved by every step)."""
+    wl = colliding_gas(n=n, seed=seed, vsig=vsig, dt=dt, phi=phi, mu=mu)
+    top = float(np.max(wl.x[:, 1] + wl.r)) + 0.3
+    wl.box_lo = (0.0, 0.0, 0.0)
+    wl.box_hi = (float(wl.box_hi[0]), top, 1.0)
+    wl.periodic = (1, 1, 0)
+    wl.wall_mask = 0
+    wl.gravity = (0.0, 0.0, 0.0)
+    return wl
+
+
+def leaning_column(offsets=(0.2, -0.6, 0.3, -0.25, 0.65), radius=1.0, mu=0.3, rotations=True):
+    """Equal discs stacked on the floor, each touching the one below with
+    the horizontal offset given (gaps exactly 0 up to rounding), gravity 1:
+    every contact carries weight; the larger offsets make contacts slide."""
+    x = [[0.0, radius]]
+    for dx in offsets:
+        px, py = x[-1]
+        x.append([px + dx, py + math.sqrt((2.0 * radius) ** 2 - dx * dx)])
+    n = len(x)
+    inv_I = None if rotations else np.zeros(n)
+    return _wl("leaning_column", 2, x, np.full(n, radius), inv_I=inv_I, dt=DT, mu=mu, gravity=(0.0, -G, 0.0),
+               box_lo=(-10.0, 0.0, 0.0), box_hi=(10.0, 2.0 * radius * n + 5.0, 1.0), wall_mask=0b0100)
