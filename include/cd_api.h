@@ -120,6 +120,13 @@ typedef struct {
                                rest sequentially.  0: pure Gauss-Seidel.
                                Plain systems with the colour-barrier schedule
                                only. */
+    int64_t tape_steps;     /* 0: no adjoint.  T > 0: every cd_step records the
+                               data cd_adjoint_step needs (colour-order contact
+                               records with their converged impulses, and the
+                               velocities the step produced) into a ring of T
+                               slots in the workspace (about 64 B per contact of
+                               capacity and 32 B per particle each); plain 2D
+                               FP64 systems with tile_cells 0 only. */
 } cd_params;
 
 typedef struct cd_system cd_system;
@@ -300,6 +307,60 @@ cd_status cd_detect_contacts_noalloc(const cd_params* params, int64_t n, const d
                                      const double* inv_mass, const double* inv_inertia, int64_t max_contacts,
                                      int32_t* pairs, double* normal, double* gap, int64_t* n_contacts,
                                      void* cuda_stream);
+
+/* ---- Reverse-mode derivatives of time steps --------------------------------
+ * The paper has no derivative of its method.  These calls differentiate the
+ * time step map (x, v, omega, mu) -> (x', v', omega') of Eqs. 1-2 with the
+ * converged impulses of the iteration (Sec. 2.1, Fig. 2, Eqs. 3-11), for
+ * gradient-based calibration of friction and initial conditions.  The
+ * derivative is taken at fixed contact set and fixed contact states, read off
+ * the converged impulses: open (P_n at most 1e-9 times the step's largest
+ * P_n: Eq. 3, or bodies left touching with no force), sliding (|P_t| equal to
+ * the rounded product mu P_n: Eqs. 9-11) or sticking (Eq. 5).  Where a small
+ * change of the inputs changes a state or the contact set the map has a kink
+ * and this is the derivative of the side with the recorded states.  2D, FP64,
+ * plain systems with params.tape_steps > 0. */
+typedef struct {
+    int64_t sweeps;           /* Gauss-Seidel sweeps of the transposed system */
+    int64_t converged;        /* 1 if the last sweep changed the multipliers Y by
+                                 sum |dY| <= alpha max(sum |Y|, sum m_n |W lambda|
+                                 at the contact's two bodies) */
+    double residual;          /* that ratio after the last sweep */
+    int64_t n_contacts;
+    int64_t n_open;
+    int64_t n_stick;
+    int64_t n_slide;
+    double dL_dmu;            /* this step's contribution to dL/dmu */
+    int64_t kernel_launches;
+} cd_adjoint_stats;
+
+/* Back-propagates through the most recent step recorded on the tape and
+ * removes it from the tape (call once per step, newest first).  Inputs
+ * (device): dL_dpos, dL_dvel n*2, dL_domega n -- the gradient of a loss L with
+ * respect to that step's output positions, velocities and angular
+ * velocities.  Outputs (device, n*2, n*2, n): the gradient with respect to
+ * the step's input state (positions before the step, velocities before the
+ * external forces of Eq. 1).  Outputs may alias the inputs.  The transposed
+ * system is solved by Gauss-Seidel in the forward colour order from zero
+ * until a sweep changes the multipliers by less than alpha relative (see
+ * cd_adjoint_stats) or max_sweeps;
+ * returns CD_ERR_NOT_CONVERGED (outputs written) if the cap was hit.
+ * CD_ERR_STATE if the tape is empty or the recorded step had failed.
+ * out_host may be NULL.  Synchronises. */
+cd_status cd_adjoint_step(cd_system* sys, const double* dL_dpos, const double* dL_dvel, const double* dL_domega,
+                          double* dL_dpos_prev, double* dL_dvel_prev, double* dL_domega_prev, double alpha,
+                          int64_t max_sweeps, cd_adjoint_stats* out_host);
+
+/* Checkpoints of the full stepping state: positions, velocities, angular
+ * velocities, orientations (if the system has them), wall planes, and the
+ * contact set with its impulses (the warm start of the next step), so that
+ * stepping on from a loaded checkpoint repeats the original steps bit for
+ * bit.  The buffer is caller-owned device memory of cd_checkpoint_size()
+ * bytes, 256-byte aligned; copies are enqueued on the system's stream.
+ * Loading also empties the tape. */
+cd_status cd_checkpoint_size(const cd_system* sys, size_t* bytes);
+cd_status cd_save_checkpoint(cd_system* sys, void* dev_buf, size_t bytes);
+cd_status cd_load_checkpoint(cd_system* sys, const void* dev_buf, size_t bytes);
 
 /* Releases the host-side system object (not the caller's arrays or
  * workspace).  Safe on NULL. */

@@ -61,6 +61,7 @@ class cd_params(C.Structure):
         ("tile_cells", C.c_int64),
         ("dataflow", C.c_int64),
         ("parallel_p", C.c_double),
+        ("tape_steps", C.c_int64),
     ]
 
 
@@ -125,6 +126,23 @@ _lib = None
 
 # (name, restype, argtypes) of every entry point declared in include/cd_api.h
 _P = C.c_void_p
+class cd_adjoint_stats(C.Structure):
+    _fields_ = [
+        ("sweeps", C.c_int64),
+        ("converged", C.c_int64),
+        ("residual", C.c_double),
+        ("n_contacts", C.c_int64),
+        ("n_open", C.c_int64),
+        ("n_stick", C.c_int64),
+        ("n_slide", C.c_int64),
+        ("dL_dmu", C.c_double),
+        ("kernel_launches", C.c_int64),
+    ]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
 SIGNATURES = [
     ("cd_create_system", C.c_int, [C.POINTER(cd_params), C.c_int64, _P, _P, _P, _P, _P, _P, _P, _P, _P,
                                    C.POINTER(_P)]),
@@ -145,6 +163,10 @@ SIGNATURES = [
     ("cd_download_state", C.c_int, [_P, _P, _P, _P]),
     ("cd_detect_contacts_noalloc", C.c_int, [C.POINTER(cd_params), C.c_int64, _P, _P, _P, _P, C.c_int64, _P, _P,
                                              _P, C.POINTER(C.c_int64), _P]),
+    ("cd_adjoint_step", C.c_int, [_P, _P, _P, _P, _P, _P, _P, C.c_double, C.c_int64, C.POINTER(cd_adjoint_stats)]),
+    ("cd_checkpoint_size", C.c_int, [_P, C.POINTER(C.c_size_t)]),
+    ("cd_save_checkpoint", C.c_int, [_P, _P, C.c_size_t]),
+    ("cd_load_checkpoint", C.c_int, [_P, _P, C.c_size_t]),
     ("cd_destroy_system", None, [_P]),
     ("cd_last_error", C.c_char_p, [_P]),
 ]
@@ -285,6 +307,29 @@ def cd_detect_contacts_noalloc(params: cd_params, n, pos, radius, inv_mass, inv_
     return int(nc.value)
 
 
+def cd_adjoint_step(sysptr, dL_dpos, dL_dvel, dL_domega, out_pos, out_vel, out_omega, alpha, max_sweeps) -> dict:
+    st = cd_adjoint_stats()
+    _check(sysptr, lib().cd_adjoint_step(sysptr, dL_dpos.data_ptr(), dL_dvel.data_ptr(), dL_domega.data_ptr(),
+                                         out_pos.data_ptr(), out_vel.data_ptr(), out_omega.data_ptr(), float(alpha),
+                                         int(max_sweeps), C.byref(st)),
+           allow=(CD_OK, CD_ERR_NOT_CONVERGED))
+    return st.as_dict()
+
+
+def cd_checkpoint_size(sysptr) -> int:
+    b = C.c_size_t()
+    _check(sysptr, lib().cd_checkpoint_size(sysptr, C.byref(b)))
+    return int(b.value)
+
+
+def cd_save_checkpoint(sysptr, buf: torch.Tensor):
+    _check(sysptr, lib().cd_save_checkpoint(sysptr, buf.data_ptr(), buf.numel() * buf.element_size()))
+
+
+def cd_load_checkpoint(sysptr, buf: torch.Tensor):
+    _check(sysptr, lib().cd_load_checkpoint(sysptr, buf.data_ptr(), buf.numel() * buf.element_size()))
+
+
 def cd_destroy_system(sysptr):
     lib().cd_destroy_system(sysptr)
 
@@ -298,7 +343,7 @@ def cd_last_error(sysptr=None) -> str:
 
 def make_params(wl, precision=CD_FP64, criterion=CD_CONV_GLOBAL_REL, max_contacts=None, warm_start=1, rotations=1,
                 seed=None, max_sweeps=None, alpha=None, timing=0, tile_cells=0, dataflow=0,
-                parallel_p=0.0) -> cd_params:
+                parallel_p=0.0, tape_steps=0) -> cd_params:
     p = cd_params()
     p.dim = wl.dim
     p.precision = precision
@@ -328,6 +373,7 @@ def make_params(wl, precision=CD_FP64, criterion=CD_CONV_GLOBAL_REL, max_contact
     p.tile_cells = int(tile_cells)
     p.dataflow = int(dataflow)
     p.parallel_p = float(parallel_p)
+    p.tape_steps = int(tape_steps)
     return p
 
 
@@ -436,6 +482,33 @@ class CDSystem:
 
     def stress_profile(self, axis, lo, width, nstripes):
         return cd_stress_profile(self._h, axis, lo, width, nstripes)
+
+    def adjoint_step(self, dL_dpos, dL_dvel, dL_domega, alpha=1e-13, max_sweeps=100000):
+        """Gradients with respect to the input state of the most recent
+        recorded step, given those of its output state (device tensors of
+        the state's shapes); returns (dL_dpos, dL_dvel, dL_domega, stats)."""
+        gx = torch.empty_like(self.pos)
+        gv = torch.empty_like(self.vel)
+        gw = torch.empty_like(self.omega)
+        args = [t.contiguous().to(device=self.device, dtype=torch.float64).reshape(-1)
+                for t in (dL_dpos, dL_dvel, dL_domega)]
+        st = cd_adjoint_step(self._h, *args, gx, gv, gw, alpha, max_sweeps)
+        return gx, gv, gw, st
+
+    def new_checkpoint(self) -> torch.Tensor:
+        """A device buffer (256-byte aligned view) for save/load_checkpoint."""
+        nbytes = cd_checkpoint_size(self._h)
+        raw = torch.empty(nbytes + 256, dtype=torch.uint8, device=self.device)
+        off = (-raw.data_ptr()) % 256
+        return raw[off: off + nbytes]
+
+    def save_checkpoint(self, buf=None) -> torch.Tensor:
+        buf = self.new_checkpoint() if buf is None else buf
+        cd_save_checkpoint(self._h, buf)
+        return buf
+
+    def load_checkpoint(self, buf):
+        cd_load_checkpoint(self._h, buf)
 
     def packing_stats(self):
         return cd_get_packing_stats(self._h, 0, getattr(self, "n_packings", 1))

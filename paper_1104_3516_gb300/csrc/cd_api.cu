@@ -36,6 +36,9 @@ struct cd_system {
     std::vector<CdPack> pk_host;       // packing table (one entry for a plain system)
     std::vector<int> pack_of_host;     // packing of each particle (batched systems)
     std::vector<double> pk_wall0;      // initial wall planes, 6 per packing
+    int tape_head;                     // next tape slot a step records into
+    int tape_count;                    // recorded steps not yet consumed by cd_adjoint_step
+    int adj_blocks;                    // cooperative grid of the adjoint kernel
     std::vector<cudaEvent_t> events;   // phase events (params.timing)
     size_t ev_used;
     std::string err;
@@ -155,6 +158,12 @@ static size_t layout(cd_system* s, char* base, CdWork* w)
     t.act_cnt = L.take<int>(base, 4);
     t.c_dpar = L.take<double>(base, s->g.par_p > 0.0 ? cap * s->pw : 1);
     t.obs = L.take<double>(base, CD_OBS_MAX);
+    const size_t T = (size_t)s->p.tape_steps;
+    t.tape = L.take<char>(base, T ? T * cd_tape_slot_bytes((int64_t)n, (int64_t)cap) : 1);
+    t.adj_Y = L.take<double2>(base, T ? cap : 1);
+    t.adj_B = L.take<double4>(base, T ? 2 * n : 1);
+    t.adj_lam = L.take<double4>(base, T ? n : 1);
+    t.adj_gx = L.take<double2>(base, T ? n : 1);
     if (w) *w = t;
     return (L.off + 255) & ~(size_t)255;
 }
@@ -230,6 +239,7 @@ static cd_status ctrl_status(cd_system* s, const CdCtrl& h)
     if (h.error == CDE_TIMEOUT) return fail(s, CD_ERR_TIMEOUT, "a bounded device-side wait ran out");
     if (h.error == CDE_COLOURS) return fail(s, CD_ERR_CAPACITY, "the contact graph needs more than 64 colours");
     if (h.error == CDE_PER_PARTICLE) return fail(s, CD_ERR_CAPACITY, "a particle has more than 64 contact candidates");
+    if (h.error == CDE_TAPE) return fail(s, CD_ERR_STATE, "the recorded step had failed (contact overflow or timeout)");
     return CD_OK;
 }
 
@@ -469,6 +479,20 @@ static cd_status create_impl(const cd_params* params, int64_t npk, const int64_t
         delete s;
         return fail(nullptr, CD_ERR_INVALID_ARG, "too many tiles: raise tile_cells");
     }
+    if (p.tape_steps < 0 || p.tape_steps > 100000) {
+        delete s;
+        return fail(nullptr, CD_ERR_INVALID_ARG, "tape_steps must be in [0, 100000]");
+    }
+    if (p.tape_steps > 0 && (p.dim != 2 || p.precision != CD_FP64 || npk > 1 || g.tile_cells != 0)) {
+        delete s;
+        return fail(nullptr, CD_ERR_INVALID_ARG,
+                    "tape_steps (the adjoint) needs a plain 2D FP64 system with the global colour order");
+    }
+    s->adj_blocks = (p.tape_steps > 0 && cd_adjoint_blocks_per_sm() >= 1) ? s->num_sms : 0;
+    if (p.tape_steps > 0 && s->adj_blocks == 0) {
+        delete s;
+        return fail(nullptr, CD_ERR_CUDA, "the adjoint kernel does not fit on this device");
+    }
     s->sweep_blocks = cd_sweep_max_blocks((int)p.precision, (int)p.dim, s->num_sms);
     s->colour_blocks = cd_colour_max_blocks(s->num_sms);
     if (s->sweep_blocks <= 0 || s->colour_blocks <= 0) {
@@ -554,6 +578,8 @@ extern "C" cd_status cd_set_workspace(cd_system* s, void* dev_ptr, size_t bytes)
                                 &s->launches));
     CD_CUDA(s, cudaStreamSynchronize(s->stream));
     s->has_contacts = 0;
+    s->tape_head = 0;
+    s->tape_count = 0;
     return CD_OK;
 }
 
@@ -625,6 +651,14 @@ extern "C" cd_status cd_step(cd_system* s, int64_t n_steps, cd_step_stats* out)
         CD_CUDA(s, cd_launch_unpack(s->g, s->w, s->pos, s->vel, s->omega, s->theta, 1, (int)s->p.precision,
                                     s->stream, &s->launches));
         if ((st = mark(s)) != CD_OK) return st;
+        if (s->p.tape_steps > 0) {
+            const int T = (int)s->p.tape_steps;
+            CD_CUDA(s, cd_launch_tape_record(s->g, s->w, cd_tape_slot(s->w.tape, s->n, s->p.max_contacts,
+                                                                      s->tape_head),
+                                             s->stream, &s->launches));
+            s->tape_head = (s->tape_head + 1) % T;
+            if (s->tape_count < T) ++s->tape_count;
+        }
     }
     if (n_steps > 0) s->has_contacts = 1;
     if (!out) return CD_OK;
@@ -767,6 +801,129 @@ extern "C" cd_status cd_stress_profile(cd_system* s, int64_t axis, double lo, do
         if (k != axis) area *= s->g.L[k];
     for (int64_t i = 0; i < nstripes; ++i) sigma_host[i] /= area;
     return CD_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Adjoint and checkpoints
+// ---------------------------------------------------------------------------
+extern "C" cd_status cd_adjoint_step(cd_system* s, const double* dL_dpos, const double* dL_dvel,
+                                     const double* dL_domega, double* dL_dpos_prev, double* dL_dvel_prev,
+                                     double* dL_domega_prev, double alpha, int64_t max_sweeps,
+                                     cd_adjoint_stats* out_host)
+{
+    cd_status st = need_ready(s);
+    if (st != CD_OK) return st;
+    if (s->p.tape_steps <= 0) return fail(s, CD_ERR_STATE, "no tape: create the system with tape_steps > 0");
+    if (s->tape_count <= 0) return fail(s, CD_ERR_STATE, "no recorded step left on the tape");
+    if (!dL_dpos || !dL_dvel || !dL_domega || !dL_dpos_prev || !dL_dvel_prev || !dL_domega_prev)
+        return fail(s, CD_ERR_INVALID_ARG, "a gradient array is NULL");
+    if (!(alpha >= 0.0) || max_sweeps < 1 || max_sweeps > (int64_t)0x7fffffff)
+        return fail(s, CD_ERR_INVALID_ARG, "alpha must be >= 0 and max_sweeps >= 1");
+    const int T = (int)s->p.tape_steps;
+    const int slot = (s->tape_head + T - 1) % T;
+    s->launches = 0;
+    k_begin_call<<<1, 1, 0, s->stream>>>(s->w.ctrl, 0);
+    ++s->launches;
+    CD_CUDA(s, cudaGetLastError());
+    CdAdjIO io;
+    io.dLx = dL_dpos; io.dLv = dL_dvel; io.dLw = dL_domega;
+    io.ox = dL_dpos_prev; io.ov = dL_dvel_prev; io.ow = dL_domega_prev;
+    io.inv_I = s->inv_I;
+    CD_CUDA(s, cd_launch_adjoint(s->g, s->w, cd_tape_slot(s->w.tape, s->n, s->p.max_contacts, slot), io, alpha,
+                                 (int)max_sweeps, s->adj_blocks, s->stream, &s->launches));
+    CdCtrl h;
+    if ((st = read_ctrl(s, &h)) != CD_OK) return st;
+    if ((st = ctrl_status(s, h)) != CD_OK) return st;
+    s->tape_head = slot;
+    --s->tape_count;
+    if (out_host) {
+        out_host->sweeps = h.adj_sweeps;
+        out_host->converged = h.adj_converged;
+        out_host->residual = h.adj_residual;
+        out_host->n_contacts = h.adj_nc;
+        out_host->n_stick = h.adj_nstick;
+        out_host->n_slide = h.adj_nslide;
+        out_host->n_open = h.adj_nc - h.adj_nstick - h.adj_nslide;
+        out_host->dL_dmu = h.adj_dmu;
+        out_host->kernel_launches = s->launches;
+    }
+    return h.adj_converged ? CD_OK : CD_ERR_NOT_CONVERGED;
+}
+
+// Checkpoint sections, each 256-byte aligned: pos, vel, omega, theta (if
+// any), wall planes (6 per packing), contact count, contact keys and
+// impulses of the current set (the warm start of the next step).
+struct CkptLayout {
+    size_t pos, vel, omega, theta, walls, nc, pairs, P, total;
+};
+
+static CkptLayout ckpt_layout(const cd_system* s)
+{
+    auto al = [](size_t x) { return (x + 255) & ~(size_t)255; };
+    const size_t n = (size_t)s->n, D = (size_t)s->p.dim, cap = (size_t)s->p.max_contacts;
+    const size_t rot = (D == 2) ? 1 : 3;
+    CkptLayout L;
+    size_t o = 0;
+    L.pos = o; o += al(n * D * 8);
+    L.vel = o; o += al(n * D * 8);
+    L.omega = o; o += al(n * rot * 8);
+    L.theta = o; o += s->theta ? al(n * 8) : 0;
+    L.walls = o; o += al((size_t)s->g.npk * 6 * 8);
+    L.nc = o; o += 256;
+    L.pairs = o; o += al(cap * sizeof(int2));
+    L.P = o; o += al(cap * (size_t)s->pw * 8);
+    L.total = o;
+    return L;
+}
+
+extern "C" cd_status cd_checkpoint_size(const cd_system* s, size_t* bytes)
+{
+    if (!s || !bytes) return CD_ERR_INVALID_ARG;
+    *bytes = ckpt_layout(s).total;
+    return CD_OK;
+}
+
+static cd_status ckpt_copy(cd_system* s, void* buf, size_t bytes, bool save)
+{
+    cd_status st = need_ready(s);
+    if (st != CD_OK) return st;
+    const CkptLayout L = ckpt_layout(s);
+    if (!buf || bytes < L.total) return fail(s, CD_ERR_INVALID_ARG, "checkpoint buffer missing or smaller than cd_checkpoint_size()");
+    if (((uintptr_t)buf & 255) != 0) return fail(s, CD_ERR_INVALID_ARG, "checkpoint buffer must be 256-byte aligned");
+    char* b = (char*)buf;
+    const size_t n = (size_t)s->n, D = (size_t)s->p.dim, cap = (size_t)s->p.max_contacts;
+    const size_t rot = (D == 2) ? 1 : 3;
+    struct Sec { void* dev; size_t off, len; } sec[] = {
+        {s->pos, L.pos, n * D * 8},
+        {s->vel, L.vel, n * D * 8},
+        {s->omega, L.omega, n * rot * 8},
+        {s->theta, L.theta, s->theta ? n * 8 : 0},
+        {s->w.pk_wall_pos, L.walls, (size_t)s->g.npk * 6 * 8},
+        {&s->w.ctrl->nc, L.nc, sizeof(int)},
+        {s->w.pairs, L.pairs, cap * sizeof(int2)},
+        {s->w.Pk, L.P, cap * (size_t)s->pw * 8},
+    };
+    for (const Sec& q : sec) {
+        if (q.len == 0) continue;
+        if (save) CD_CUDA(s, cudaMemcpyAsync(b + q.off, q.dev, q.len, cudaMemcpyDeviceToDevice, s->stream));
+        else CD_CUDA(s, cudaMemcpyAsync(q.dev, b + q.off, q.len, cudaMemcpyDeviceToDevice, s->stream));
+    }
+    if (!save) {
+        s->has_contacts = 1;
+        s->tape_head = 0;
+        s->tape_count = 0;
+    }
+    return CD_OK;
+}
+
+extern "C" cd_status cd_save_checkpoint(cd_system* s, void* dev_buf, size_t bytes)
+{
+    return ckpt_copy(s, dev_buf, bytes, true);
+}
+
+extern "C" cd_status cd_load_checkpoint(cd_system* s, const void* dev_buf, size_t bytes)
+{
+    return ckpt_copy(s, const_cast<void*>(dev_buf), bytes, false);
 }
 
 extern "C" void cd_destroy_system(cd_system* s)

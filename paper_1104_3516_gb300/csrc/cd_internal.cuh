@@ -17,7 +17,7 @@
 #define CD_HT 1024            // slots of a tile's shared-memory particle table
 
 // Device error codes written into CdCtrl::error.
-enum { CDE_NONE = 0, CDE_TIMEOUT = 1, CDE_COLOURS = 2, CDE_PER_PARTICLE = 3 };
+enum { CDE_NONE = 0, CDE_TIMEOUT = 1, CDE_COLOURS = 2, CDE_PER_PARTICLE = 3, CDE_TAPE = 4 };
 
 // Control block at the start of the workspace.
 struct CdCtrl {
@@ -43,6 +43,14 @@ struct CdCtrl {
     long long total_updates;
     long long max_sweeps_step;
     long long n_not_conv;
+    // last adjoint step
+    long long adj_sweeps;
+    long long adj_converged;
+    double adj_residual;
+    double adj_dmu;
+    long long adj_nc;
+    long long adj_nstick;
+    long long adj_nslide;
 };
 
 // Parameters of one packing of a batched system (a plain system is a batch of
@@ -127,7 +135,34 @@ struct CdWork {
     int* act_cnt;       // 3 counters of packings still iterating
     double* c_dpar;     // cap * pw (key order): impulse change of a parallel contact
     double* obs;        // CD_OBS_MAX doubles: observable results
+    // adjoint (params.tape_steps > 0)
+    char* tape;         // tape_steps slots of CdTapeHdr + one step's records
+    double2* adj_Y;     // cap: adjoint multipliers (Y_n, Y_t) of the contacts
+    double4* adj_B;     // 2 n: per particle Gamma (x, y, w, 0) then Lambda (x, y, w, 0)
+    double4* adj_lam;   // n: dL/dv of the step's velocities (x, y, w, 0)
+    double2* adj_gx;    // n: dL/dx being accumulated
 };
+
+// One recorded time step for the adjoint (2D, FP64): the colour-order
+// contact records after the solve and the velocities the step produced.
+#define CD_GRAZING 1e-9   // P_n <= CD_GRAZING * max P_n: taken as open (touching, no force)
+struct CdTapeHdr {
+    int nc;
+    int ncolours;
+    int valid;          // 0 if the step was skipped or failed
+    int pad;
+    int colour_off[CD_KMAX + 1];
+};
+struct CdTape {
+    CdTapeHdr* hdr;
+    int2* ab;
+    double4* geo;       // nx, ny, b = g/dt, m_n
+    double* mt;
+    double2* P;         // converged (P_n, P_t)
+    double4* V;         // n: velocities after the step (vx, vy, w, 0)
+};
+size_t cd_tape_slot_bytes(int64_t n, int64_t cap);
+CdTape cd_tape_slot(char* tape, int64_t n, int64_t cap, int slot);
 #define CD_OBS_MAX 65536
 
 
@@ -277,6 +312,19 @@ cudaError_t cd_launch_need(const CdGeom& g, const CdWork& w, cudaStream_t stream
 cudaError_t cd_launch_pk_ranges(const CdGeom& g, const CdWork& w, cudaStream_t stream, int* nl);
 cudaError_t cd_launch_orient(const CdGeom& g, const CdWork& w, int nbins, unsigned long long* counts,
                              cudaStream_t stream, int* nl);
+cudaError_t cd_launch_tape_record(const CdGeom& g, const CdWork& w, const CdTape& t, cudaStream_t stream, int* nl);
+struct CdAdjIO {
+    const double* dLx;      // n*2: dL/dx' of the step's output positions
+    const double* dLv;      // n*2: dL/dv'
+    const double* dLw;      // n:   dL/domega'
+    double* ox;             // n*2: dL/dx of the step's input positions
+    double* ov;             // n*2: dL/dv
+    double* ow;             // n:   dL/domega
+    const double* inv_I;    // n
+};
+cudaError_t cd_launch_adjoint(const CdGeom& g, const CdWork& w, const CdTape& t, const CdAdjIO& io, double alpha,
+                              int max_sweeps, int coop_blocks, cudaStream_t stream, int* nl);
+int cd_adjoint_blocks_per_sm();
 cudaError_t cd_launch_stress(const CdGeom& g, const CdWork& w, const double* pos, const double* radius, int axis,
                              double lo, double width, int ns, double* sig, cudaStream_t stream, int* nl);
 cudaError_t cd_launch_sweep(const CdGeom& g, const CdWork& w, int coop_blocks, int precision, int criterion,

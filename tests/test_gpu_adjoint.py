@@ -1,0 +1,222 @@
+"""GPU parity of the adjoint (cd_adjoint_step) with the oracle's complex-step
+derivatives of the frozen-state step map, the closed forms of single
+contacts, conservation of momentum, central differences of the GPU's own
+forward rollout, and the checkpointed torch.autograd rollout."""
+import copy
+
+import numpy as np
+import pytest
+
+import oracle as O
+from oracle import adjoint as A
+from oracle_adapter import system as oracle_system
+from oracle_cases import DT, G, colliding_gas, head_on, leaning_column, periodic_gas, resting_disc
+
+from gpu_common import needs_gpu
+
+pytestmark = [pytest.mark.gpu, needs_gpu]
+
+FWD_ALPHA = 1e-15
+ADJ_ALPHA = 1e-13
+MAX_SWEEPS = 200000
+
+
+def gpu_grad(wl, steps, weights, tape=None):
+    """Steps the workload on the GPU (recording every step) and
+    back-propagates L = <c_x, x_T> + <c_v, v_T> + <c_w, w_T>; returns
+    (dL/dx0, dL/dv0, dL/dw0, dL/dmu, per-step adjoint stats newest first)."""
+    import torch
+    from paper_1104_3516_gb300 import cd
+    g = cd.CDSystem(wl, device="cuda:0", criterion=cd.CD_CONV_GLOBAL_REL, alpha=FWD_ALPHA, max_sweeps=MAX_SWEEPS,
+                    tape_steps=tape or steps)
+    g.step(steps)
+    cx, cv, cw = (torch.as_tensor(np.asarray(c, dtype=np.float64).reshape(-1), device="cuda:0") for c in weights)
+    gx, gv, gw = cx, cv, cw
+    gmu, stats = 0.0, []
+    for _ in range(steps):
+        gx, gv, gw, st = g.adjoint_step(gx, gv, gw, ADJ_ALPHA, MAX_SWEEPS)
+        assert st["converged"] == 1, st
+        gmu += st["dL_dmu"]
+        stats.append(st)
+    return (gx.cpu().numpy().reshape(wl.n, 2), gv.cpu().numpy().reshape(wl.n, 2), gw.cpu().numpy(), gmu, stats)
+
+
+def oracle_recs(wl, steps):
+    s = oracle_system(wl, criterion=O.CRIT_GLOBAL_REL, alpha=FWD_ALPHA, max_sweeps=MAX_SWEEPS,
+                      order=O.ORDER_COLOUR)
+    recs = A.record_rollout(s, steps)
+    return s, recs
+
+
+def directions(wl, k, seed, xscale=1.0):
+    rng = np.random.default_rng(seed)
+    return [(xscale * rng.standard_normal(wl.x.shape), rng.standard_normal(wl.v.shape),
+             rng.standard_normal(wl.w.shape), float(rng.standard_normal())) for _ in range(k)]
+
+
+def project(grad, e):
+    gx, gv, gw, gmu = grad
+    ex, ev, ew, em = e
+    return float(np.sum(gx * ex) + np.sum(gv * ev) + np.sum(gw * ew) + gmu * em)
+
+
+def check_parity(wl, steps, seed=3, ndir=32, xscale=1.0, tol=1e-9):
+    rng = np.random.default_rng(seed)
+    weights = (rng.standard_normal(wl.x.shape), rng.standard_normal(wl.v.shape), rng.standard_normal(wl.w.shape))
+    gx, gv, gw, gmu, stats = gpu_grad(wl, steps, weights)
+    s, recs = oracle_recs(wl, steps)
+    # the contact states of every step agree (stats are newest first)
+    for st, rec in zip(stats, reversed(recs)):
+        cnt = np.bincount(rec.state, minlength=3)
+        assert (st["n_contacts"], st["n_open"], st["n_stick"], st["n_slide"]) == \
+            (len(rec.pairs), cnt[A.OPEN], cnt[A.STICK], cnt[A.SLIDE])
+    cs = A.consts_of(s)
+    dirs = directions(wl, ndir, seed + 1, xscale)
+    ref = A.directional_derivatives(cs, recs, wl.x, wl.v, wl.w, wl.mu, weights, dirs)
+    got = np.array([project((gx, gv, gw, gmu), e) for e in dirs])
+    scale = max(np.abs(ref).max(), 1.0)
+    err = np.abs(got - ref).max() / scale
+    assert err <= tol, (err, got[:4], ref[:4])
+    return stats, recs
+
+
+def test_gpu_adjoint_one_step_of_collisions():
+    wl = colliding_gas(n=300, phi=0.62, vsig=3.0, dt=0.05)
+    stats, recs = check_parity(wl, 1)
+    assert stats[0]["n_stick"] >= 5 and stats[0]["n_slide"] >= 5
+
+
+def test_gpu_adjoint_over_steps_with_touching_contacts():
+    """Six steps of a fast gas under gravity: contacts left touching after
+    collisions (taken as open), sticking and sliding ones, walls."""
+    wl = colliding_gas(n=100, phi=0.62, vsig=3.0, dt=0.02)
+    stats, _ = check_parity(wl, 6)
+    assert sum(s["n_slide"] for s in stats) > 10 and sum(s["n_stick"] for s in stats) > 10
+
+
+def test_gpu_adjoint_periodic_gas():
+    wl = periodic_gas(n=100, phi=0.62, vsig=3.0, dt=0.02)
+    check_parity(wl, 6)
+
+
+def test_gpu_adjoint_leaning_column():
+    wl = leaning_column(mu=0.18)
+    check_parity(wl, 4, xscale=1e-3)
+
+
+def test_gpu_momentum_gradient_is_the_mass():
+    """No walls, no gravity: d(sum m v_x)/dv0 = (m, 0), and nothing else
+    (positions, spins, friction) changes total momentum."""
+    wl = periodic_gas(n=100, phi=0.62, vsig=3.0, dt=0.02)
+    m = 1.0 / wl.inv_m
+    cv = np.stack([m, np.zeros_like(m)], axis=1)
+    gx, gv, gw, gmu, _ = gpu_grad(wl, 6, (np.zeros_like(wl.x), cv, np.zeros_like(wl.w)))
+    assert np.abs(gv[:, 0] - m).max() <= 1e-12 * m.max()
+    assert np.abs(gv[:, 1]).max() <= 1e-12 * m.max()
+    assert np.abs(gx).max() <= 1e-9 * m.max() / wl.dt
+    assert np.abs(gw).max() <= 1e-12 * m.max()
+    assert abs(gmu) <= 1e-12 * m.max()
+
+
+def test_gpu_rolling_disc_closed_form():
+    r = 0.9
+    wl = resting_disc(radius=r, mu=1.0)
+    wl.v = np.array([[1e-3, 0.0]])
+    wl.w = np.array([2e-4])
+    z2, z1 = np.zeros((1, 2)), np.zeros(1)
+    gx, gv, gw, gmu, st = gpu_grad(wl, 1, (z2, np.array([[1.0, 0.0]]), z1))
+    assert st[0]["n_stick"] == 1
+    assert gv[0, 0] == pytest.approx(2.0 / 3.0, rel=1e-12)
+    assert gw[0] == pytest.approx(-r / 3.0, rel=1e-12)
+    gx, gv, gw, gmu, _ = gpu_grad(wl, 1, (z2, z2, np.ones(1)))
+    assert gv[0, 0] == pytest.approx(-2.0 / (3.0 * r), rel=1e-12)
+    assert gw[0] == pytest.approx(1.0 / 3.0, rel=1e-12)
+    gx, gv, gw, gmu, _ = gpu_grad(wl, 1, (z2, np.array([[0.0, 1.0]]), z1))
+    assert gx[0, 1] == pytest.approx(-1.0 / DT, rel=1e-12)
+
+
+@pytest.mark.parametrize("rotations", [0, 1])
+def test_gpu_sliding_disc_friction_derivative(rotations):
+    r = 1.1
+    wl = resting_disc(radius=r, mu=0.3)
+    wl.v = np.array([[1.0, 0.0]])
+    if not rotations:
+        wl.inv_I = np.zeros(1)
+    z2, z1 = np.zeros((1, 2)), np.zeros(1)
+    gx, gv, gw, gmu, st = gpu_grad(wl, 1, (z2, np.array([[1.0, 0.0]]), z1))
+    assert st[0]["n_slide"] == 1
+    assert gmu == pytest.approx(-G * DT, rel=1e-12)
+    assert gv[0, 0] == pytest.approx(1.0, rel=1e-12)
+    gx, gv, gw, gmu, _ = gpu_grad(wl, 1, (z2, z2, np.ones(1)))
+    assert gmu == pytest.approx(-2.0 * G * DT / r if rotations else 0.0, rel=1e-12, abs=1e-300)
+
+
+def test_gpu_inelastic_collision_closed_form():
+    r1, r2 = 1.0, 1.3
+    wl = head_on(1.0, -1.0, r1=r1, r2=r2)
+    m1, m2 = 1.0 / wl.inv_m[0], 1.0 / wl.inv_m[1]
+    M = m1 + m2
+    z2, z1 = np.zeros((2, 2)), np.zeros(2)
+    c = np.zeros((2, 2))
+    c[0, 0] = 1.0
+    gx, gv, gw, gmu, _ = gpu_grad(wl, 1, (z2, c, z1))
+    assert gv[0, 0] == pytest.approx(m1 / M, rel=1e-12)
+    assert gv[1, 0] == pytest.approx(m2 / M, rel=1e-12)
+    assert gx[1, 0] == pytest.approx(m2 / (M * DT), rel=1e-12)
+    assert gx[0, 0] == pytest.approx(-m2 / (M * DT), rel=1e-12)
+    gx, gv, gw, gmu, _ = gpu_grad(wl, 1, (c, z2, z1))
+    assert gv[0, 0] == pytest.approx(DT * m1 / M, rel=1e-12)
+
+
+def test_gpu_adjoint_matches_finite_differences_of_the_gpu_forward():
+    """Central differences (h = 1e-6) of the GPU's own rollout of the leaning
+    column against the adjoint, on 8 seeded directions."""
+    from paper_1104_3516_gb300 import cd
+    wl = leaning_column(mu=0.18)
+    steps, h = 4, 1e-6
+    rng = np.random.default_rng(11)
+    weights = (rng.standard_normal(wl.x.shape), rng.standard_normal(wl.v.shape), rng.standard_normal(wl.w.shape))
+    grad = gpu_grad(wl, steps, weights)[:4]
+
+    def loss(x, v, w, mu):
+        w2 = copy.copy(wl)
+        w2.x, w2.v, w2.w, w2.mu = x, v, w, mu
+        g = cd.CDSystem(w2, device="cuda:0", criterion=cd.CD_CONV_GLOBAL_REL, alpha=FWD_ALPHA,
+                        max_sweeps=MAX_SWEEPS)
+        g.step(steps)
+        s = g.state()
+        return float(np.sum(weights[0] * s["x"]) + np.sum(weights[1] * s["v"]) + np.sum(weights[2] * s["w"]))
+
+    for e in directions(wl, 8, 12, xscale=1e-3):
+        ex, ev, ew, em = e
+        fd = (loss(wl.x + h * ex, wl.v + h * ev, wl.w + h * ew, wl.mu + h * em)
+              - loss(wl.x - h * ex, wl.v - h * ev, wl.w - h * ew, wl.mu - h * em)) / (2 * h)
+        d = project(grad, e)
+        assert abs(fd - d) <= 1e-5 * max(abs(d), 1.0), (fd, d)
+
+
+def test_checkpointed_rollout_equals_the_full_tape():
+    """torch.autograd through 7 steps with checkpoints every 3 gives the same
+    gradients, bit for bit, as recording all 7 (the recomputed steps repeat
+    the forward exactly), and leaves the system in the post-rollout state."""
+    import torch
+    from paper_1104_3516_gb300 import autodiff, cd
+    wl = colliding_gas(n=100, phi=0.62, vsig=3.0, dt=0.02)
+    out = []
+    for k in (3, 7):
+        g = cd.CDSystem(wl, device="cuda:0", criterion=cd.CD_CONV_GLOBAL_REL, alpha=FWD_ALPHA,
+                        max_sweeps=MAX_SWEEPS, tape_steps=k)
+        dd = dict(dtype=torch.float64, device="cuda:0")
+        x0 = torch.as_tensor(wl.x, **dd).requires_grad_()
+        v0 = torch.as_tensor(wl.v, **dd).requires_grad_()
+        w0 = torch.as_tensor(wl.w, **dd).requires_grad_()
+        mu = torch.tensor(wl.mu, dtype=torch.float64, requires_grad=True)
+        xT, vT, wT = autodiff.rollout(g, x0, v0, w0, mu, 7, checkpoint_every=k, alpha=ADJ_ALPHA,
+                                      max_sweeps=MAX_SWEEPS)
+        L = (xT[:, 1].sum() + (vT ** 2).sum() + wT.sum()).cpu()
+        L.backward()
+        after = g.state()
+        assert np.array_equal(after["x"], xT.detach().cpu().numpy())
+        out.append((x0.grad.cpu().numpy(), v0.grad.cpu().numpy(), w0.grad.cpu().numpy(), float(mu.grad)))
+    for a, b in zip(out[0], out[1]):
+        assert np.array_equal(np.asarray(a), np.asarray(b))
