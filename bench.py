@@ -72,6 +72,8 @@ def parse():
     ap.add_argument("--batched-steps", type=int, default=3,
                     help="timed steps of the 512-packing batched workload (0: skip)")
     ap.add_argument("--packings", type=int, default=512)
+    ap.add_argument("--adjoint-steps", type=int, default=200,
+                    help="steps of the differentiated settling rollout (0: skip the adjoint leg)")
     ap.add_argument("--cpu-sweeps", type=int, default=30,
                     help="sweep cap of the oracle's bounded sample step")
     return ap.parse_args()
@@ -336,6 +338,10 @@ def run_ours(args):
     if args.batched_steps > 0:
         batched = run_batched(args, device, rank, flush)
 
+    adjoint = None
+    if args.adjoint_steps > 0 and args.precision == "f64":
+        adjoint = run_adjoint(args, device, rank, flush)
+
     e2e = None
     if not args.no_e2e:
         e2e = run_e2e(args, sysg, wl, device, ws)
@@ -358,7 +364,8 @@ def run_ours(args):
                                         "sweeps_per_step": sweeps / max(args.steps, 1),
                                         "steps_not_converged": not_conv, "parallelism": f"replicas x{ws}"}),
             "phase_ms_per_step": {k: v / max(args.steps, 1) for k, v in ph.items()},
-            "wall_s": wall_max, "roofline": roofline, "batched": batched, "cpu_baseline": cpu, "e2e": e2e,
+            "wall_s": wall_max, "roofline": roofline, "batched": batched, "adjoint": adjoint, "cpu_baseline": cpu,
+            "e2e": e2e,
             "gpu_launches": launches, "clocks": clk}
     print(json.dumps(line), flush=True)
 
@@ -404,6 +411,119 @@ def run_batched(args, device, rank, flush):
         out["alu_frac"] = out["fp64_tflops"] / FP64_PEAK_TFLOPS
     del g
     torch.cuda.empty_cache()
+    return out
+
+
+def run_adjoint(args, device, rank, flush, every=20, adj_alpha=1e-10):
+    """The differentiated rollouts, with a checkpoint every 20 steps, 10,000
+    discs (radii U[0.8, 1.2], mu = 0.3, gravity 1):
+
+    * settling (`adjoint_steps` steps, 200 by default): a jittered lattice at
+      packing fraction 0.5 in a box with floor and side walls, initial
+      velocities N(0, 0.05), falling under gravity;
+    * settled pile (supplementary, solver-heavy, at most 40 steps): the same
+      discs deposited into a loaded pile on a floor, periodic in x, so that
+      every step solves a hyperstatic contact network.
+
+    Two losses of the final state are differentiated with respect to mu and
+    all initial velocities: the floor pressure of the last step and the
+    packing height (top of the highest disc).  Each backward pass reloads the
+    checkpoints newest first, re-steps the segment and back-propagates
+    through every step."""
+    import torch
+    from paper_1104_3516_gb300 import cd, workloads as W
+    cases = {"settling": (W.settling_discs(seed=1109 + rank, n=10_000), args.adjoint_steps,
+                          "settling_discs_2d: jittered lattice at packing fraction 0.5, floor and side walls, "
+                          "v0 ~ N(0, 0.05)"),
+             "settled_pile": (W.settled_pile(1109 + rank, 10_000), min(args.adjoint_steps, 40),
+                              "settled_pile_2d (supplementary): gravity-deposited pile, floor, periodic x, v0 = 0")}
+    out = {"checkpoint_every": every, "adjoint_alpha": adj_alpha, "n_discs": 10_000, "mu": 0.3}
+    for cname, (wl, steps, desc) in cases.items():
+        out[cname] = adjoint_case(args, device, flush, wl, desc, every, adj_alpha, steps)
+    torch.cuda.empty_cache()
+    return out
+
+
+def adjoint_case(args, device, flush, wl, desc, every, adj_alpha, steps, compliance=0.0):
+    import torch
+    from paper_1104_3516_gb300 import cd
+    wl.max_sweeps = args.max_sweeps
+    wl.alpha = args.alpha
+    T = steps
+    width = float(wl.box_hi[0] - wl.box_lo[0])
+    g = cd.CDSystem(wl, device=device, criterion=cd.CD_CONV_GLOBAL_REL, tape_steps=every,
+                    adjoint_compliance=compliance)
+    stream = g.stream
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    flush.zero_()
+    torch.cuda.synchronize(device)
+    e0.record(stream)
+    segs = []
+    done = fwd_upd = fwd_sweeps = 0
+    last = None
+    while done < T:
+        m = min(every, T - done)
+        segs.append((g.save_checkpoint(), m))
+        st = g.step(m)
+        fwd_upd += st["total_contact_updates"]
+        fwd_sweeps += st["total_sweeps"]
+        last = st["last"]
+        done += m
+    e1.record(stream)
+    e1.synchronize()
+    fwd_ms = e0.elapsed_time(e1)
+    final = g.save_checkpoint()
+    n = wl.n
+    y = g.pos.view(n, 2)[:, 1] + g.radius
+    top = int(torch.argmax(y))
+    losses = {"floor_pressure": (float(last["wall_force"][2]) / width, None, [0, 0, 1.0 / width, 0, 0, 0]),
+              "packing_height": (float(y[top]), top, None)}
+    out = {"workload": desc, "steps": T, "adjoint_compliance": compliance,
+           "forward_ms_per_step": fwd_ms / T, "forward_sweeps_per_step": fwd_sweeps / T,
+           "contacts_last_step": int(last["n_contacts"]),
+           "forward_contact_updates_per_s": fwd_upd / (fwd_ms / 1e3) if fwd_ms > 0 else 0.0, "losses": {}}
+    a0, a1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    for name, (val, top_i, wall) in losses.items():
+        gx = torch.zeros(2 * n, dtype=torch.float64, device=device)
+        if top_i is not None:
+            gx[2 * top_i + 1] = 1.0
+        gv = torch.zeros_like(gx)
+        gw = torch.zeros(n, dtype=torch.float64, device=device)
+        adj_ms = 0.0
+        sweeps = upd = not_conv = max_sw = hyper = diverged = 0
+        gmu = 0.0
+        torch.cuda.synchronize(device)
+        e0.record(stream)
+        for buf, m in reversed(segs):
+            g.load_checkpoint(buf)
+            g.step(m, stats=False)
+            for _ in range(m):
+                a0.record(stream)
+                gx, gv, gw, st = g.adjoint_step(gx, gv, gw, adj_alpha, 100000, dL_dwall_force=wall)
+                a1.record(stream)
+                a1.synchronize()
+                wall = None
+                adj_ms += a0.elapsed_time(a1)
+                sweeps += st["sweeps"]
+                max_sw = max(max_sw, st["sweeps"])
+                upd += st["sweeps"] * st["n_contacts"]
+                not_conv += 1 - st["converged"]
+                hyper += int(st["n_rows"] > st["n_dof"])
+                diverged += st["diverged"]
+                gmu += st["dL_dmu"]
+        e1.record(stream)
+        e1.synchronize()
+        bwd_ms = e0.elapsed_time(e1)
+        out["losses"][name] = {
+            "value": val, "dL_dmu": gmu, "dL_dv0_norm": float(gv.norm()),
+            "backward_ms_per_step": bwd_ms / T, "adjoint_kernel_ms_per_step": adj_ms / T,
+            "adjoint_sweeps_per_step": sweeps / T, "adjoint_sweeps_max": int(max_sw),
+            "adjoint_contact_updates_per_s": upd / (adj_ms / 1e3) if adj_ms > 0 else 0.0,
+            "adjoint_steps_not_converged": int(not_conv), "adjoint_steps_diverged": int(diverged),
+            "steps_hyperstatic": int(hyper),
+            "steps_per_s_forward_plus_backward": T / ((fwd_ms + bwd_ms) / 1e3)}
+    g.load_checkpoint(final)
+    del g
     return out
 
 

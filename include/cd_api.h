@@ -127,6 +127,16 @@ typedef struct {
                                slots in the workspace (about 64 B per contact of
                                capacity and 32 B per particle each); plain 2D
                                FP64 systems with tile_cells 0 only. */
+    double adjoint_compliance; /* 0: the reverse pass solves the rigid
+                               frozen-state system exactly (derivative of
+                               the method as it stands).  eps > 0: each
+                               retained row gets a relative compliance eps
+                               (rows Phi^T (H Gamma + q) - eps diag(w) Y = 0,
+                               w = 1/m_n, 1/m_t), so that hyperstatic contact
+                               networks, where the rigid multipliers are not
+                               unique and the Gauss-Seidel iteration can
+                               drift, give the bounded derivative of slightly
+                               compliant contacts.  Not in the paper. */
 } cd_params;
 
 typedef struct cd_system cd_system;
@@ -332,13 +342,29 @@ typedef struct {
     int64_t n_slide;
     double dL_dmu;            /* this step's contribution to dL/dmu */
     int64_t kernel_launches;
+    int64_t n_rows;           /* equations of the frozen-state system: 2 per sticking,
+                                 1 per sliding contact */
+    int64_t n_dof;            /* degrees of freedom of the particles those contacts
+                                 touch (3 each in 2D, 2 with rotations frozen);
+                                 n_rows > n_dof means a hyperstatic network,
+                                 where the impulses are not unique and the
+                                 multipliers Y are the Gauss-Seidel ones from
+                                 zero (the derivative of the positions is then
+                                 not unique either) */
+    int64_t diverged;         /* 1 if sum |Y| grew past 1e30 times its scale or
+                                 stopped being finite (sweeps stopped; outputs
+                                 are not meaningful) */
 } cd_adjoint_stats;
 
 /* Back-propagates through the most recent step recorded on the tape and
  * removes it from the tape (call once per step, newest first).  Inputs
  * (device): dL_dpos, dL_dvel n*2, dL_domega n -- the gradient of a loss L with
  * respect to that step's output positions, velocities and angular
- * velocities.  Outputs (device, n*2, n*2, n): the gradient with respect to
+ * velocities; dL_dwall_force_host (host, 6 doubles, or NULL for zeros) -- its
+ * gradient with respect to that step's wall forces (the sum of the normal
+ * impulses on wall k divided by dt, as cd_solve_stats.wall_force reports;
+ * a wall pressure is that force over the wall's length or area).
+ * Outputs (device, n*2, n*2, n): the gradient with respect to
  * the step's input state (positions before the step, velocities before the
  * external forces of Eq. 1).  Outputs may alias the inputs.  The transposed
  * system is solved by Gauss-Seidel in the forward colour order from zero
@@ -348,8 +374,8 @@ typedef struct {
  * CD_ERR_STATE if the tape is empty or the recorded step had failed.
  * out_host may be NULL.  Synchronises. */
 cd_status cd_adjoint_step(cd_system* sys, const double* dL_dpos, const double* dL_dvel, const double* dL_domega,
-                          double* dL_dpos_prev, double* dL_dvel_prev, double* dL_domega_prev, double alpha,
-                          int64_t max_sweeps, cd_adjoint_stats* out_host);
+                          const double* dL_dwall_force_host, double* dL_dpos_prev, double* dL_dvel_prev,
+                          double* dL_domega_prev, double alpha, int64_t max_sweeps, cd_adjoint_stats* out_host);
 
 /* Checkpoints of the full stepping state: positions, velocities, angular
  * velocities, orientations (if the system has them), wall planes, and the

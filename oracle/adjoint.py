@@ -222,26 +222,41 @@ def step_map(cs: Consts, rec: StepRecord, x, v, w, mu):
     return xn, vn, wn, P.reshape(nc, 2)
 
 
-def rollout_map(cs: Consts, recs, x0, v0, w0, mu):
-    """The frozen-state map over all recorded steps."""
+def rollout_map(cs: Consts, recs, x0, v0, w0, mu, with_forces=False):
+    """The frozen-state map over all recorded steps; with_forces also
+    returns the wall forces of the last step (sum of the normal impulses on
+    wall k over dt, 6 values)."""
     x, v, w = np.asarray(x0).reshape(cs.n, 2), np.asarray(v0).reshape(cs.n, 2), np.asarray(w0).reshape(cs.n)
+    P = None
     for rec in recs:
-        x, v, w, _ = step_map(cs, rec, x, v, w, mu)
-    return x, v, w
+        x, v, w, P = step_map(cs, rec, x, v, w, mu)
+    if not with_forces:
+        return x, v, w
+    F = np.zeros(6, dtype=np.result_type(x, v, w, np.float64))
+    if recs:
+        for c, (a, b) in enumerate(recs[-1].pairs):
+            if b >= cs.n:
+                F[int(b - cs.n)] += P[c, 0] / cs.dt
+    return x, v, w, F
 
 
-def directional_derivatives(cs: Consts, recs, x0, v0, w0, mu, weights, directions, h=1e-30):
-    """d/de of L = <c_x, x_T> + <c_v, v_T> + <c_w, w_T> along each direction
+def directional_derivatives(cs: Consts, recs, x0, v0, w0, mu, weights, directions, h=1e-30, wall_weights=None):
+    """d/de of L = <c_x, x_T> + <c_v, v_T> + <c_w, w_T> (+ <c_F, F_T> with
+    F_T the wall forces of the last step) along each direction
     e = (e_x, e_v, e_w, e_mu) by the complex step.  `weights` = (c_x, c_v,
-    c_w); `directions` a list of such 4-tuples."""
+    c_w); `wall_weights` = c_F (6 values) or None; `directions` a list of
+    4-tuples."""
     cx, cv, cw = (np.asarray(a, dtype=np.float64) for a in weights)
+    cF = None if wall_weights is None else np.asarray(wall_weights, dtype=np.float64).reshape(6)
     out = []
     for ex, ev, ew, emu in directions:
-        x, v, w = rollout_map(cs, recs, np.asarray(x0).reshape(cs.n, 2) + 1j * h * np.asarray(ex).reshape(cs.n, 2),
-                              np.asarray(v0).reshape(cs.n, 2) + 1j * h * np.asarray(ev).reshape(cs.n, 2),
-                              np.asarray(w0).reshape(cs.n) + 1j * h * np.asarray(ew).reshape(cs.n),
-                              mu + 1j * h * emu)
+        x, v, w, F = rollout_map(cs, recs, np.asarray(x0).reshape(cs.n, 2) + 1j * h * np.asarray(ex).reshape(cs.n, 2),
+                                 np.asarray(v0).reshape(cs.n, 2) + 1j * h * np.asarray(ev).reshape(cs.n, 2),
+                                 np.asarray(w0).reshape(cs.n) + 1j * h * np.asarray(ew).reshape(cs.n),
+                                 mu + 1j * h * emu, with_forces=True)
         L = np.sum(cx.reshape(cs.n, 2) * x) + np.sum(cv.reshape(cs.n, 2) * v) + np.sum(cw.reshape(cs.n) * w)
+        if cF is not None:
+            L = L + np.sum(cF * F)
         out.append(L.imag / h)
     return np.array(out)
 

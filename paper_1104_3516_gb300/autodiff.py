@@ -20,7 +20,9 @@ from . import cd
 
 
 class CDRollout(torch.autograd.Function):
-    """(x0, v0, omega0, mu) -> (x_T, v_T, omega_T) after `steps` CD steps.
+    """(x0, v0, omega0, mu) -> (x_T, v_T, omega_T, F_T) after `steps` CD
+    steps, F_T the 6 wall forces of the last step (sum of the normal impulses
+    on wall k over dt; a floor pressure is F_T[2] over the floor's length).
 
     ``system`` must have been created with ``tape_steps >= checkpoint_every``;
     ``mu`` is a 0-dim tensor holding the system's friction coefficient (the
@@ -38,31 +40,36 @@ class CDRollout(torch.autograd.Function):
         system.omega.copy_(w0.detach().reshape(-1))
         segments = []
         done = 0
+        forces = [0.0] * 6
         while done < steps:
             m = min(checkpoint_every, steps - done)
             segments.append((system.save_checkpoint(), m))
-            system.step(m, stats=False)
+            st = system.step(m)
+            forces = st["last"]["wall_force"]
             done += m
         ctx.final = system.save_checkpoint()
         ctx.system, ctx.segments = system, segments
         ctx.alpha, ctx.max_sweeps = alpha, max_sweeps
         ctx.shapes = (x0.shape, v0.shape, w0.shape)
         ctx.stats = []
+        F = torch.tensor(forces, dtype=torch.float64)
         return (system.pos.clone().reshape(x0.shape), system.vel.clone().reshape(v0.shape),
-                system.omega.clone().reshape(w0.shape))
+                system.omega.clone().reshape(w0.shape), F)
 
     @staticmethod
-    def backward(ctx, gx, gv, gw):
+    def backward(ctx, gx, gv, gw, gF):
         s = ctx.system
         gx = torch.zeros_like(s.pos) if gx is None else gx.reshape(-1).contiguous().clone()
         gv = torch.zeros_like(s.vel) if gv is None else gv.reshape(-1).contiguous().clone()
         gw = torch.zeros_like(s.omega) if gw is None else gw.reshape(-1).contiguous().clone()
+        wall = None if gF is None else gF.detach().cpu().numpy().reshape(6)
         gmu = 0.0
         for buf, m in reversed(ctx.segments):
             s.load_checkpoint(buf)
             s.step(m, stats=False)
             for _ in range(m):
-                gx, gv, gw, st = s.adjoint_step(gx, gv, gw, ctx.alpha, ctx.max_sweeps)
+                gx, gv, gw, st = s.adjoint_step(gx, gv, gw, ctx.alpha, ctx.max_sweeps, dL_dwall_force=wall)
+                wall = None            # the wall forces are those of the last step only
                 gmu += st["dL_dmu"]
                 ctx.stats.append(st)
         s.load_checkpoint(ctx.final)

@@ -62,6 +62,7 @@ class cd_params(C.Structure):
         ("dataflow", C.c_int64),
         ("parallel_p", C.c_double),
         ("tape_steps", C.c_int64),
+        ("adjoint_compliance", C.c_double),
     ]
 
 
@@ -137,6 +138,9 @@ class cd_adjoint_stats(C.Structure):
         ("n_slide", C.c_int64),
         ("dL_dmu", C.c_double),
         ("kernel_launches", C.c_int64),
+        ("n_rows", C.c_int64),
+        ("n_dof", C.c_int64),
+        ("diverged", C.c_int64),
     ]
 
     def as_dict(self):
@@ -163,7 +167,8 @@ SIGNATURES = [
     ("cd_download_state", C.c_int, [_P, _P, _P, _P]),
     ("cd_detect_contacts_noalloc", C.c_int, [C.POINTER(cd_params), C.c_int64, _P, _P, _P, _P, C.c_int64, _P, _P,
                                              _P, C.POINTER(C.c_int64), _P]),
-    ("cd_adjoint_step", C.c_int, [_P, _P, _P, _P, _P, _P, _P, C.c_double, C.c_int64, C.POINTER(cd_adjoint_stats)]),
+    ("cd_adjoint_step", C.c_int, [_P, _P, _P, _P, C.POINTER(C.c_double), _P, _P, _P, C.c_double, C.c_int64,
+                                  C.POINTER(cd_adjoint_stats)]),
     ("cd_checkpoint_size", C.c_int, [_P, C.POINTER(C.c_size_t)]),
     ("cd_save_checkpoint", C.c_int, [_P, _P, C.c_size_t]),
     ("cd_load_checkpoint", C.c_int, [_P, _P, C.c_size_t]),
@@ -307,9 +312,13 @@ def cd_detect_contacts_noalloc(params: cd_params, n, pos, radius, inv_mass, inv_
     return int(nc.value)
 
 
-def cd_adjoint_step(sysptr, dL_dpos, dL_dvel, dL_domega, out_pos, out_vel, out_omega, alpha, max_sweeps) -> dict:
+def cd_adjoint_step(sysptr, dL_dpos, dL_dvel, dL_domega, dL_dwall_force, out_pos, out_vel, out_omega, alpha,
+                    max_sweeps) -> dict:
     st = cd_adjoint_stats()
-    _check(sysptr, lib().cd_adjoint_step(sysptr, dL_dpos.data_ptr(), dL_dvel.data_ptr(), dL_domega.data_ptr(),
+    wf = None
+    if dL_dwall_force is not None:
+        wf = (C.c_double * 6)(*[float(x) for x in np.asarray(dL_dwall_force, dtype=np.float64).reshape(6)])
+    _check(sysptr, lib().cd_adjoint_step(sysptr, dL_dpos.data_ptr(), dL_dvel.data_ptr(), dL_domega.data_ptr(), wf,
                                          out_pos.data_ptr(), out_vel.data_ptr(), out_omega.data_ptr(), float(alpha),
                                          int(max_sweeps), C.byref(st)),
            allow=(CD_OK, CD_ERR_NOT_CONVERGED))
@@ -343,7 +352,7 @@ def cd_last_error(sysptr=None) -> str:
 
 def make_params(wl, precision=CD_FP64, criterion=CD_CONV_GLOBAL_REL, max_contacts=None, warm_start=1, rotations=1,
                 seed=None, max_sweeps=None, alpha=None, timing=0, tile_cells=0, dataflow=0,
-                parallel_p=0.0, tape_steps=0) -> cd_params:
+                parallel_p=0.0, tape_steps=0, adjoint_compliance=0.0) -> cd_params:
     p = cd_params()
     p.dim = wl.dim
     p.precision = precision
@@ -374,6 +383,7 @@ def make_params(wl, precision=CD_FP64, criterion=CD_CONV_GLOBAL_REL, max_contact
     p.dataflow = int(dataflow)
     p.parallel_p = float(parallel_p)
     p.tape_steps = int(tape_steps)
+    p.adjoint_compliance = float(adjoint_compliance)
     return p
 
 
@@ -483,16 +493,17 @@ class CDSystem:
     def stress_profile(self, axis, lo, width, nstripes):
         return cd_stress_profile(self._h, axis, lo, width, nstripes)
 
-    def adjoint_step(self, dL_dpos, dL_dvel, dL_domega, alpha=1e-13, max_sweeps=100000):
+    def adjoint_step(self, dL_dpos, dL_dvel, dL_domega, alpha=1e-13, max_sweeps=100000, dL_dwall_force=None):
         """Gradients with respect to the input state of the most recent
         recorded step, given those of its output state (device tensors of
-        the state's shapes); returns (dL_dpos, dL_dvel, dL_domega, stats)."""
+        the state's shapes) and optionally of its 6 wall forces; returns
+        (dL_dpos, dL_dvel, dL_domega, stats)."""
         gx = torch.empty_like(self.pos)
         gv = torch.empty_like(self.vel)
         gw = torch.empty_like(self.omega)
         args = [t.contiguous().to(device=self.device, dtype=torch.float64).reshape(-1)
                 for t in (dL_dpos, dL_dvel, dL_domega)]
-        st = cd_adjoint_step(self._h, *args, gx, gv, gw, alpha, max_sweeps)
+        st = cd_adjoint_step(self._h, *args, dL_dwall_force, gx, gv, gw, alpha, max_sweeps)
         return gx, gv, gw, st
 
     def new_checkpoint(self) -> torch.Tensor:

@@ -25,6 +25,13 @@
 //                  with dGamma, dv' the differences body b - body a and
 //                  R^T (u_x, u_y) = (u_y, -u_x); for a pair dn/dd = (I - n n^T)
 //                  / |d|, dg/dd = n, d = x_b - x_a; for a wall dg/dx_a = -n.
+// A loss that also depends on the step's wall forces (sum of the normal
+// impulses on wall k over dt) adds q_n = dL/dF_k / dt to u_n on that wall's
+// contacts: the rows solved become Phi^T (H Gamma + q) = 0.
+// With params.adjoint_compliance eps > 0 each retained row is softened to
+// Phi^T (H Gamma + q) - eps diag(w_n, w_t) Y = 0 (contacts with a small
+// compliance), which makes the transposed system nonsingular on hyperstatic
+// networks, where the rigid one has no unique multipliers.
 // A contact whose normal impulse is at most CD_GRAZING times the step's
 // largest is taken as open (two bodies left touching by an inelastic
 // collision carry rounding noise there, and the map has a kink).
@@ -46,20 +53,21 @@ __device__ __forceinline__ double warp_max_a(double v)
     return v;
 }
 
-// Block sum of 3 values (fixed tree); valid in thread 0.
-__device__ __forceinline__ void block_sum3(double (&v)[3], double (*s_red)[3])
+// Block sum of NV values per thread (fixed tree); valid in thread 0.
+template <int NV>
+__device__ __forceinline__ void block_sum(double (&v)[NV], double (*s_red)[4])
 {
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
 #pragma unroll
-    for (int j = 0; j < 3; ++j) v[j] = warp_sum_a(v[j]);
+    for (int j = 0; j < NV; ++j) v[j] = warp_sum_a(v[j]);
     if (lane == 0)
 #pragma unroll
-        for (int j = 0; j < 3; ++j) s_red[wid][j] = v[j];
+        for (int j = 0; j < NV; ++j) s_red[wid][j] = v[j];
     __syncthreads();
     if (wid == 0) {
         const int nw = blockDim.x >> 5;
 #pragma unroll
-        for (int j = 0; j < 3; ++j) v[j] = warp_sum_a(lane < nw ? s_red[lane][j] : 0.0);
+        for (int j = 0; j < NV; ++j) v[j] = warp_sum_a(lane < nw ? s_red[lane][j] : 0.0);
     }
     __syncthreads();
 }
@@ -87,8 +95,8 @@ __device__ __forceinline__ bool is_slide(double mu, const double2& P)
 
 // One Gauss-Seidel update of the transposed system on contact p; adds |Y|
 // and |dY| to acc[0], acc[1].
-__device__ __forceinline__ void adj_update(const CdGeom& g, const CdWork& w, const CdTape& t, int p, double thr,
-                                           double (&acc)[3])
+__device__ __forceinline__ void adj_update(const CdGeom& g, const CdWork& w, const CdTape& t, const CdAdjIO& io,
+                                           int p, double thr, double (&acc)[3])
 {
     const double2 P = t.P[p];
     if (!(P.x > thr)) return;                         // open
@@ -106,16 +114,19 @@ __device__ __forceinline__ void adj_update(const CdGeom& g, const CdWork& w, con
         Lb = w.adj_B[2 * ab.y + 1];
     }
     const double dgx = Gb.x - Ga.x, dgy = Gb.y - Ga.y;
-    const double un = dgx * nx + dgy * ny;
+    const double un = dgx * nx + dgy * ny + (wall ? io.wq[ab.y - g.n] : 0.0);
     const double ut = (dgy * nx - dgx * ny) - (sa.y * Ga.z + sb.y * Gb.z);
+    // with compliance eps the rows are Phi^T (H Gamma + q) - eps diag(w) Y = 0
+    double2 Y = w.adj_Y[p];
+    const double eps = io.eps, inv1e = 1.0 / (1.0 + eps);
     double dYn, dYt;
     if (is_slide(g.mu, P)) {
         const double s = (P.y < 0.0) ? -1.0 : 1.0;
-        dYn = mn * (un + s * g.mu * ut);
+        dYn = (mn * (un + s * g.mu * ut) - eps * Y.x) * inv1e;
         dYt = 0.0;
     } else {
-        dYn = mn * un;
-        dYt = mt * ut;
+        dYn = (mn * un - eps * Y.x) * inv1e;
+        dYt = (mt * ut - eps * Y.y) * inv1e;
     }
     const double fx = dYn * nx - dYt * ny, fy = dYn * ny + dYt * nx;
     // Gamma -= W H^T dY;  Lambda += H^T dY  (body a: -f, -r_a dY_t; body b: +f, -r_b dY_t)
@@ -129,7 +140,6 @@ __device__ __forceinline__ void adj_update(const CdGeom& g, const CdWork& w, con
         w.adj_B[2 * ab.y] = Gb;
         w.adj_B[2 * ab.y + 1] = Lb;
     }
-    double2 Y = w.adj_Y[p];
     Y.x += dYn;
     Y.y += dYt;
     w.adj_Y[p] = Y;
@@ -173,6 +183,8 @@ __device__ __forceinline__ void adj_geometry(const CdGeom& g, const CdWork& w, c
     } else {
         acc[1] += 1.0;
     }
+    w.adj_mark[ab.x] = 1;
+    if (!wall) w.adj_mark[ab.y] = 1;
     const double dLg = -Y.x / g.dt;
     double2 ga = w.adj_gx[ab.x];
     if (wall) {
@@ -222,7 +234,7 @@ __global__ void __launch_bounds__(CD_SWEEP_THREADS, 1)
 k_adjoint(CdGeom g, CdWork w, CdTape t, CdAdjIO io, double alpha, int max_sweeps)
 {
     __shared__ int s_off[CD_KMAX + 1];
-    __shared__ double s_red[CD_SWEEP_THREADS / 32][3];
+    __shared__ double s_red[CD_SWEEP_THREADS / 32][4];
     __shared__ double s_bc;
     CdCtrl* ctrl = w.ctrl;
     const int nb = gridDim.x;
@@ -250,6 +262,7 @@ k_adjoint(CdGeom g, CdWork w, CdTape t, CdAdjIO io, double alpha, int max_sweeps
         w.adj_B[2 * i + 1] = make_double4(0.0, 0.0, 0.0, 0.0);
         w.adj_lam[i] = make_double4(lx, ly, lw, 0.0);
         w.adj_gx[i] = make_double2(io.dLx[2 * i], io.dLx[2 * i + 1]);
+        w.adj_mark[i] = 0;
     }
     if (!cd_grid_sync(ctrl, nb, epoch)) return;
     // largest normal impulse (the open threshold) and the scale of the
@@ -266,10 +279,12 @@ k_adjoint(CdGeom g, CdWork w, CdTape t, CdAdjIO io, double alpha, int max_sweeps
             if (ab.y < n) {
                 const double4 Gb = w.adj_B[2 * ab.y];
                 sc += sqrt(Gb.x * Gb.x + Gb.y * Gb.y) + S[ab.y].y * fabs(Gb.z);
+            } else {
+                sc += fabs(io.wq[ab.y - n]);
             }
             acc[0] += t.geo[c].w * sc;
         }
-        block_sum3(acc, s_red);
+        block_sum<3>(acc, s_red);
         pmax = warp_max_a(pmax);
         __shared__ double s_max[CD_SWEEP_THREADS / 32];
         if ((threadIdx.x & 31) == 0) s_max[threadIdx.x >> 5] = pmax;
@@ -286,15 +301,15 @@ k_adjoint(CdGeom g, CdWork w, CdTape t, CdAdjIO io, double alpha, int max_sweeps
     const double yscale = grid_reduce<false>(w.partials + nb, nb, &s_bc);
 
     // sweeps until sum |dY| <= alpha max(sum |Y|, yscale)
-    int sweeps = 0, converged = (nc == 0);
+    int sweeps = 0, converged = (nc == 0), diverged = 0;
     double resid = 0.0;
     while (!converged && sweeps < max_sweeps) {
         double* part = w.partials + (size_t)((sweeps & 1) ? 0 : 1) * 3 * nb;
         double acc[3] = {0.0, 0.0, 0.0};
         for (int k = 0; k < K; ++k) {
-            for (int p = s_off[k] + tid; p < s_off[k + 1]; p += stride) adj_update(g, w, t, p, thr, acc);
+            for (int p = s_off[k] + tid; p < s_off[k + 1]; p += stride) adj_update(g, w, t, io, p, thr, acc);
             if (k == K - 1) {
-                block_sum3(acc, s_red);
+                block_sum<3>(acc, s_red);
                 if (threadIdx.x == 0) {
                     part[blockIdx.x] = acc[0];
                     part[nb + blockIdx.x] = acc[1];
@@ -308,6 +323,11 @@ k_adjoint(CdGeom g, CdWork w, CdTape t, CdAdjIO io, double alpha, int max_sweeps
         const double den = fmax(ysum, yscale);
         resid = (den > 0.0) ? dsum / den : 0.0;
         converged = dsum <= alpha * den;
+        if (!(ysum <= 1e30 * fmax(yscale, 1e-300))) {   // growing without bound, or not finite
+            diverged = 1;
+            converged = 0;
+            break;
+        }
     }
 
     // position gradient, colour by colour (a colour touches each particle once)
@@ -316,12 +336,16 @@ k_adjoint(CdGeom g, CdWork w, CdTape t, CdAdjIO io, double alpha, int max_sweeps
         for (int p = s_off[k] + tid; p < s_off[k + 1]; p += stride) adj_geometry(g, w, t, p, thr, acc);
         if (!cd_grid_sync(ctrl, nb, epoch)) return;
     }
-    block_sum3(acc, s_red);
+    double acc4[4] = {acc[0], acc[1], acc[2], 0.0};
+    for (int i = tid; i < n; i += stride) acc4[3] += (double)w.adj_mark[i];
+    block_sum<4>(acc4, s_red);
     double* part = w.partials + (size_t)((sweeps & 1) ? 0 : 1) * 3 * nb;
     if (threadIdx.x == 0) {
-        part[blockIdx.x] = acc[0];
-        part[nb + blockIdx.x] = acc[1];
-        part[2 * nb + blockIdx.x] = acc[2];
+        part[blockIdx.x] = acc4[0];
+        part[nb + blockIdx.x] = acc4[1];
+        part[2 * nb + blockIdx.x] = acc4[2];
+        // third slot of the other buffer: no sweep or scale reduction uses it
+        w.partials[(size_t)((sweeps & 1) ? 1 : 0) * 3 * nb + 2 * nb + blockIdx.x] = acc4[3];
     }
     for (int i = tid; i < n; i += stride) {
         const double4 lam = w.adj_lam[i];
@@ -338,6 +362,7 @@ k_adjoint(CdGeom g, CdWork w, CdTape t, CdAdjIO io, double alpha, int max_sweeps
         const double dmu = grid_reduce<false>(part, nb, &s_bc);
         const double nst = grid_reduce<false>(part + nb, nb, &s_bc);
         const double nsl = grid_reduce<false>(part + 2 * nb, nb, &s_bc);
+        const double nmk = grid_reduce<false>(w.partials + (size_t)((sweeps & 1) ? 1 : 0) * 3 * nb + 2 * nb, nb, &s_bc);
         if (threadIdx.x == 0) {
             ctrl->adj_sweeps = sweeps;
             ctrl->adj_converged = converged;
@@ -346,6 +371,8 @@ k_adjoint(CdGeom g, CdWork w, CdTape t, CdAdjIO io, double alpha, int max_sweeps
             ctrl->adj_nc = nc;
             ctrl->adj_nstick = (long long)nst;
             ctrl->adj_nslide = (long long)nsl;
+            ctrl->adj_nbodies = (long long)nmk;
+            ctrl->adj_diverged = diverged;
         }
     }
 }

@@ -164,6 +164,7 @@ static size_t layout(cd_system* s, char* base, CdWork* w)
     t.adj_B = L.take<double4>(base, T ? 2 * n : 1);
     t.adj_lam = L.take<double4>(base, T ? n : 1);
     t.adj_gx = L.take<double2>(base, T ? n : 1);
+    t.adj_mark = L.take<int>(base, T ? n : 1);
     if (w) *w = t;
     return (L.off + 255) & ~(size_t)255;
 }
@@ -478,6 +479,10 @@ static cd_status create_impl(const cd_params* params, int64_t npk, const int64_t
     if (g.tile_cells >= 2 && (double)g.ntiles * CD_KLOCAL > 1.0e8) {
         delete s;
         return fail(nullptr, CD_ERR_INVALID_ARG, "too many tiles: raise tile_cells");
+    }
+    if (!(p.adjoint_compliance >= 0.0) || !std::isfinite(p.adjoint_compliance)) {
+        delete s;
+        return fail(nullptr, CD_ERR_INVALID_ARG, "adjoint_compliance must be >= 0");
     }
     if (p.tape_steps < 0 || p.tape_steps > 100000) {
         delete s;
@@ -807,9 +812,9 @@ extern "C" cd_status cd_stress_profile(cd_system* s, int64_t axis, double lo, do
 // Adjoint and checkpoints
 // ---------------------------------------------------------------------------
 extern "C" cd_status cd_adjoint_step(cd_system* s, const double* dL_dpos, const double* dL_dvel,
-                                     const double* dL_domega, double* dL_dpos_prev, double* dL_dvel_prev,
-                                     double* dL_domega_prev, double alpha, int64_t max_sweeps,
-                                     cd_adjoint_stats* out_host)
+                                     const double* dL_domega, const double* dL_dwall_force_host,
+                                     double* dL_dpos_prev, double* dL_dvel_prev, double* dL_domega_prev, double alpha,
+                                     int64_t max_sweeps, cd_adjoint_stats* out_host)
 {
     cd_status st = need_ready(s);
     if (st != CD_OK) return st;
@@ -829,6 +834,12 @@ extern "C" cd_status cd_adjoint_step(cd_system* s, const double* dL_dpos, const 
     io.dLx = dL_dpos; io.dLv = dL_dvel; io.dLw = dL_domega;
     io.ox = dL_dpos_prev; io.ov = dL_dvel_prev; io.ow = dL_domega_prev;
     io.inv_I = s->inv_I;
+    io.eps = s->p.adjoint_compliance;
+    for (int k = 0; k < 6; ++k) {
+        const double f = dL_dwall_force_host ? dL_dwall_force_host[k] : 0.0;
+        if (!std::isfinite(f)) return fail(s, CD_ERR_INVALID_ARG, "dL_dwall_force not finite");
+        io.wq[k] = f / s->p.dt;
+    }
     CD_CUDA(s, cd_launch_adjoint(s->g, s->w, cd_tape_slot(s->w.tape, s->n, s->p.max_contacts, slot), io, alpha,
                                  (int)max_sweeps, s->adj_blocks, s->stream, &s->launches));
     CdCtrl h;
@@ -846,6 +857,9 @@ extern "C" cd_status cd_adjoint_step(cd_system* s, const double* dL_dpos, const 
         out_host->n_open = h.adj_nc - h.adj_nstick - h.adj_nslide;
         out_host->dL_dmu = h.adj_dmu;
         out_host->kernel_launches = s->launches;
+        out_host->n_rows = 2 * h.adj_nstick + h.adj_nslide;
+        out_host->n_dof = h.adj_nbodies * (s->p.rotations ? 3 : 2);
+        out_host->diverged = h.adj_diverged;
     }
     return h.adj_converged ? CD_OK : CD_ERR_NOT_CONVERGED;
 }

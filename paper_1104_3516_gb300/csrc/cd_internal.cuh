@@ -51,6 +51,8 @@ struct CdCtrl {
     long long adj_nc;
     long long adj_nstick;
     long long adj_nslide;
+    long long adj_nbodies;          // particles touched by a non-open contact
+    long long adj_diverged;
 };
 
 // Parameters of one packing of a batched system (a plain system is a batch of
@@ -141,6 +143,7 @@ struct CdWork {
     double4* adj_B;     // 2 n: per particle Gamma (x, y, w, 0) then Lambda (x, y, w, 0)
     double4* adj_lam;   // n: dL/dv of the step's velocities (x, y, w, 0)
     double2* adj_gx;    // n: dL/dx being accumulated
+    int* adj_mark;      // n: 1 if the particle has a non-open contact
 };
 
 // One recorded time step for the adjoint (2D, FP64): the colour-order
@@ -321,6 +324,8 @@ struct CdAdjIO {
     double* ov;             // n*2: dL/dv
     double* ow;             // n:   dL/domega
     const double* inv_I;    // n
+    double wq[6];           // dL/d(wall force k) / dt: weight of the normal impulse of a contact with wall k
+    double eps;             // relative compliance of the rows (params.adjoint_compliance)
 };
 cudaError_t cd_launch_adjoint(const CdGeom& g, const CdWork& w, const CdTape& t, const CdAdjIO& io, double alpha,
                               int max_sweeps, int coop_blocks, cudaStream_t stream, int* nl);

@@ -453,14 +453,14 @@ __device__ __forceinline__ UpdOut apply_rec(const CdGeom& g, const CdWork& w, in
 // One colour phase for this thread: its first contact's record was loaded
 // into `nxt` before the barrier (if it has one); the rest are loaded inline.
 // Afterwards `nxt` holds the first record of colour `knext` (prefetch).
-template <int DIM, typename T>
+template <int DIM, typename T, bool MIXED>
 __device__ __forceinline__ void colour_phase(const CdGeom& g, const CdWork& w, const int* s_off, int k, int knext,
                                              int tid, int stride, Rec<DIM, T>& nxt, bool apply_only, int crit,
                                              double alpha, double ravg_prev, double (&acc)[3])
 {
     const int end = s_off[k + 1];
     int p = s_off[k] + tid;
-    const bool mixed = !apply_only && g.par_p > 0.0;   // parallel contacts were done in their own phase
+    const bool mixed = MIXED && !apply_only;   // parallel contacts were done in their own phase
     if (p < end) {
         if (!(mixed && cd_is_parallel(g.par_p, g.seed, cd_key(nxt.ab.x, nxt.ab.y)))) {
             UpdOut o = apply_rec<DIM, T>(g, w, p, nxt, apply_only, crit, alpha, ravg_prev);
@@ -630,7 +630,8 @@ __device__ __forceinline__ void par_apply(const CdGeom& g, const CdWork& w, int 
 // ---------------------------------------------------------------------------
 // The persistent sweep kernel
 // ---------------------------------------------------------------------------
-template <int DIM, typename T>
+// MIXED: the mixed update of Sec. 2.3 is compiled in (params.parallel_p > 0).
+template <int DIM, typename T, bool MIXED>
 __global__ void __launch_bounds__(CD_SWEEP_THREADS, 1)
 k_sweep(CdGeom g, CdWork w, int crit, double alpha, int max_sweeps)
 {
@@ -656,7 +657,7 @@ k_sweep(CdGeom g, CdWork w, int crit, double alpha, int max_sweeps)
         // starting impulses, colour by colour
         double acc[3] = {0.0, 0.0, 0.0};
         for (int k = 0; k < K; ++k) {
-            colour_phase<DIM, T>(g, w, s_off, k, (k + 1 < K) ? k + 1 : 0, tid, stride, nxt, true, crit, alpha, 0.0,
+            colour_phase<DIM, T, MIXED>(g, w, s_off, k, (k + 1 < K) ? k + 1 : 0, tid, stride, nxt, true, crit, alpha, 0.0,
                                  acc);
             if (k == K - 1) {
                 block_sum<3>(acc, s_red);
@@ -671,7 +672,7 @@ k_sweep(CdGeom g, CdWork w, int crit, double alpha, int max_sweeps)
             const int buf = (sweeps & 1) ? 0 : 1;   // alternate with the buffer of the previous sweep
             double* part = w.partials + (size_t)buf * 3 * nb;
             double a3[3] = {0.0, 0.0, 0.0};
-            const bool mixed = g.par_p > 0.0;
+            const bool mixed = MIXED;
             if (mixed) {
                 for (int p = tid; p < nc; p += stride) {
                     Rec<DIM, T> r;
@@ -686,7 +687,7 @@ k_sweep(CdGeom g, CdWork w, int crit, double alpha, int max_sweeps)
                 if (s_off[0] + tid < s_off[1]) load_rec<DIM, T>(g, w, s_off[0] + tid, nxt);
             }
             for (int k = 0; k < K; ++k) {
-                colour_phase<DIM, T>(g, w, s_off, k, (k + 1 < K) ? k + 1 : 0, tid, stride, nxt, false, crit, alpha,
+                colour_phase<DIM, T, MIXED>(g, w, s_off, k, (k + 1 < K) ? k + 1 : 0, tid, stride, nxt, false, crit, alpha,
                                      ravg_prev, a3);
                 if (mixed && k == K - 1) {
                     if (!cd_grid_sync(ctrl, nb, epoch)) return;
@@ -1411,8 +1412,14 @@ static const void* sweep_fn(int dim, int precision, int tiled)
             return precision == CD_FP64 ? (const void*)k_sweep_tiled<2, double> : (const void*)k_sweep_tiled<2, float>;
         return precision == CD_FP64 ? (const void*)k_sweep_tiled<3, double> : (const void*)k_sweep_tiled<3, float>;
     }
-    if (dim == 2) return precision == CD_FP64 ? (const void*)k_sweep<2, double> : (const void*)k_sweep<2, float>;
-    return precision == CD_FP64 ? (const void*)k_sweep<3, double> : (const void*)k_sweep<3, float>;
+    if (tiled == 4) {
+        if (dim == 2)
+            return precision == CD_FP64 ? (const void*)k_sweep<2, double, true> : (const void*)k_sweep<2, float, true>;
+        return precision == CD_FP64 ? (const void*)k_sweep<3, double, true> : (const void*)k_sweep<3, float, true>;
+    }
+    if (dim == 2)
+        return precision == CD_FP64 ? (const void*)k_sweep<2, double, false> : (const void*)k_sweep<2, float, false>;
+    return precision == CD_FP64 ? (const void*)k_sweep<3, double, false> : (const void*)k_sweep<3, float, false>;
 }
 
 static size_t tile_smem(int dim, int precision)
@@ -1426,7 +1433,7 @@ static size_t tile_smem(int dim, int precision)
 int cd_sweep_max_blocks(int precision, int dim, int num_sms)
 {
     int per_sm = 0;
-    for (int tiled = 0; tiled < 4; ++tiled) {
+    for (int tiled = 0; tiled < 5; ++tiled) {
         const void* fn = sweep_fn(dim, precision, tiled);
         size_t dyn = (tiled == 1) ? tile_smem(dim, precision) : 0;
         if (tiled && cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn) != cudaSuccess)
@@ -1451,7 +1458,7 @@ cudaError_t cd_launch_sweep(const CdGeom& g, const CdWork& w, int coop_blocks, i
     double al = alpha;
     int ms = max_sweeps;
     void* args[] = {&ga, &wa, &crit, &al, &ms};
-    const int kind = (g.npk > 1) ? 3 : ((g.tile_cells >= 2) ? 1 : (g.dataflow ? 2 : 0));
+    const int kind = (g.npk > 1) ? 3 : ((g.tile_cells >= 2) ? 1 : (g.dataflow ? 2 : (g.par_p > 0.0 ? 4 : 0)));
     ++*nl;
     return cudaLaunchCooperativeKernel(sweep_fn(g.dim, precision, kind), dim3(coop_blocks), dim3(CD_SWEEP_THREADS),
                                        args, kind == 1 ? tile_smem(g.dim, precision) : 0, s);

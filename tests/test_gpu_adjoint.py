@@ -21,7 +21,7 @@ ADJ_ALPHA = 1e-13
 MAX_SWEEPS = 200000
 
 
-def gpu_grad(wl, steps, weights, tape=None):
+def gpu_grad(wl, steps, weights, tape=None, wall_weights=None):
     """Steps the workload on the GPU (recording every step) and
     back-propagates L = <c_x, x_T> + <c_v, v_T> + <c_w, w_T>; returns
     (dL/dx0, dL/dv0, dL/dw0, dL/dmu, per-step adjoint stats newest first)."""
@@ -33,8 +33,10 @@ def gpu_grad(wl, steps, weights, tape=None):
     cx, cv, cw = (torch.as_tensor(np.asarray(c, dtype=np.float64).reshape(-1), device="cuda:0") for c in weights)
     gx, gv, gw = cx, cv, cw
     gmu, stats = 0.0, []
+    wall = wall_weights
     for _ in range(steps):
-        gx, gv, gw, st = g.adjoint_step(gx, gv, gw, ADJ_ALPHA, MAX_SWEEPS)
+        gx, gv, gw, st = g.adjoint_step(gx, gv, gw, ADJ_ALPHA, MAX_SWEEPS, dL_dwall_force=wall)
+        wall = None
         assert st["converged"] == 1, st
         gmu += st["dL_dmu"]
         stats.append(st)
@@ -60,10 +62,10 @@ def project(grad, e):
     return float(np.sum(gx * ex) + np.sum(gv * ev) + np.sum(gw * ew) + gmu * em)
 
 
-def check_parity(wl, steps, seed=3, ndir=32, xscale=1.0, tol=1e-9):
+def check_parity(wl, steps, seed=3, ndir=32, xscale=1.0, tol=1e-9, wall_weights=None):
     rng = np.random.default_rng(seed)
     weights = (rng.standard_normal(wl.x.shape), rng.standard_normal(wl.v.shape), rng.standard_normal(wl.w.shape))
-    gx, gv, gw, gmu, stats = gpu_grad(wl, steps, weights)
+    gx, gv, gw, gmu, stats = gpu_grad(wl, steps, weights, wall_weights=wall_weights)
     s, recs = oracle_recs(wl, steps)
     # the contact states of every step agree (stats are newest first)
     for st, rec in zip(stats, reversed(recs)):
@@ -72,7 +74,7 @@ def check_parity(wl, steps, seed=3, ndir=32, xscale=1.0, tol=1e-9):
             (len(rec.pairs), cnt[A.OPEN], cnt[A.STICK], cnt[A.SLIDE])
     cs = A.consts_of(s)
     dirs = directions(wl, ndir, seed + 1, xscale)
-    ref = A.directional_derivatives(cs, recs, wl.x, wl.v, wl.w, wl.mu, weights, dirs)
+    ref = A.directional_derivatives(cs, recs, wl.x, wl.v, wl.w, wl.mu, weights, dirs, wall_weights=wall_weights)
     got = np.array([project((gx, gv, gw, gmu), e) for e in dirs])
     scale = max(np.abs(ref).max(), 1.0)
     err = np.abs(got - ref).max() / scale
@@ -92,6 +94,25 @@ def test_gpu_adjoint_over_steps_with_touching_contacts():
     wl = colliding_gas(n=100, phi=0.62, vsig=3.0, dt=0.02)
     stats, _ = check_parity(wl, 6)
     assert sum(s["n_slide"] for s in stats) > 10 and sum(s["n_stick"] for s in stats) > 10
+
+
+def test_gpu_adjoint_with_wall_forces():
+    """A loss on the last step's wall forces as well as the final state."""
+    wl = colliding_gas(n=100, phi=0.62, vsig=3.0, dt=0.02)
+    check_parity(wl, 4, wall_weights=[0.3, -0.7, 1.0, 0.0, 0.0, 0.0])
+
+
+def test_gpu_floor_force_closed_form():
+    """dF/dv_y = -m/dt and dF/dy = -m/dt^2 for a disc pressed on the floor."""
+    wl = resting_disc(radius=1.0, mu=0.3)
+    wl.v = np.array([[0.0, -0.01]])
+    m = 1.0 / wl.inv_m[0]
+    z2, z1 = np.zeros((1, 2)), np.zeros(1)
+    gx, gv, gw, gmu, st = gpu_grad(wl, 1, (z2, z2, z1), wall_weights=[0, 0, 1.0, 0, 0, 0])
+    assert st[0]["n_stick"] == 1
+    assert gv[0, 1] == pytest.approx(-m / DT, rel=1e-12)
+    assert gx[0, 1] == pytest.approx(-m / DT ** 2, rel=1e-12)
+    assert abs(gmu) <= 1e-12 * m
 
 
 def test_gpu_adjoint_periodic_gas():
@@ -211,12 +232,107 @@ def test_checkpointed_rollout_equals_the_full_tape():
         v0 = torch.as_tensor(wl.v, **dd).requires_grad_()
         w0 = torch.as_tensor(wl.w, **dd).requires_grad_()
         mu = torch.tensor(wl.mu, dtype=torch.float64, requires_grad=True)
-        xT, vT, wT = autodiff.rollout(g, x0, v0, w0, mu, 7, checkpoint_every=k, alpha=ADJ_ALPHA,
-                                      max_sweeps=MAX_SWEEPS)
-        L = (xT[:, 1].sum() + (vT ** 2).sum() + wT.sum()).cpu()
+        xT, vT, wT, FT = autodiff.rollout(g, x0, v0, w0, mu, 7, checkpoint_every=k, alpha=ADJ_ALPHA,
+                                          max_sweeps=MAX_SWEEPS)
+        L = (xT[:, 1].sum() + (vT ** 2).sum() + wT.sum()).cpu() + FT[2] / 15.0
         L.backward()
         after = g.state()
         assert np.array_equal(after["x"], xT.detach().cpu().numpy())
         out.append((x0.grad.cpu().numpy(), v0.grad.cpu().numpy(), w0.grad.cpu().numpy(), float(mu.grad)))
     for a, b in zip(out[0], out[1]):
         assert np.array_equal(np.asarray(a), np.asarray(b))
+
+
+def test_gpu_adjoint_settling_10k_against_finite_differences():
+    """The differentiated settling rollout at full size: 10,000 discs, 200
+    steps, checkpoints every 20; L = floor pressure of the last step + the
+    packing height (top of the highest disc).  The autograd gradient with
+    respect to (v0, mu) is checked by central differences (h = 1e-6) of the
+    GPU's own rollout on 32 seeded directions.  A direction whose one-sided
+    differences disagree has a kink (a contact changing state or the top disc
+    changing) inside +-h and is reported, not compared; the smooth ones must
+    agree to 1e-5."""
+    import torch
+    from paper_1104_3516_gb300 import autodiff, cd, workloads as W
+    wl = W.settling_discs(n=10_000)
+    steps, every, h = 200, 20, 1e-6
+    width = float(wl.wall_pos[1] - wl.wall_pos[0])
+    kw = dict(criterion=cd.CD_CONV_GLOBAL_REL, alpha=1e-13, max_sweeps=20000)
+
+    def loss_of(v0, mu):
+        w2 = copy.copy(wl)
+        w2.v, w2.mu = v0, mu
+        g = cd.CDSystem(w2, device="cuda:0", **kw)
+        st = g.step(steps)
+        y = g.state()["x"][:, 1]
+        return st["last"]["wall_force"][2] / width + float(np.max(y + wl.r))
+
+    g = cd.CDSystem(wl, device="cuda:0", tape_steps=every, **kw)
+    dd = dict(dtype=torch.float64, device="cuda:0")
+    x0 = torch.as_tensor(wl.x, **dd)
+    v0 = torch.as_tensor(wl.v, **dd).requires_grad_()
+    w0 = torch.as_tensor(wl.w, **dd)
+    mu = torch.tensor(wl.mu, dtype=torch.float64, requires_grad=True)
+    xT, vT, wT, FT = autodiff.rollout(g, x0, v0, w0, mu, steps, checkpoint_every=every, alpha=1e-13,
+                                      max_sweeps=200000)
+    r = torch.as_tensor(wl.r, **dd)
+    L = FT[2] / width + torch.max(xT[:, 1] + r).cpu()
+    L.backward()
+    gv, gmu = v0.grad.cpu().numpy(), float(mu.grad)
+    L0 = loss_of(wl.v, wl.mu)
+    assert abs(L0 - float(L)) <= 1e-12 * abs(L0)
+    rng = np.random.default_rng(2024)
+    smooth, kinked = 0, 0
+    for _ in range(32):
+        ev, em = rng.standard_normal(wl.v.shape), float(rng.standard_normal())
+        Lp = loss_of(wl.v + h * ev, wl.mu + h * em)
+        Lm = loss_of(wl.v - h * ev, wl.mu - h * em)
+        d = float(np.sum(gv * ev) + gmu * em)
+        scale = max(abs(d), 1.0)
+        if abs((Lp - L0) - (L0 - Lm)) / h > 1e-4 * scale:
+            kinked += 1
+            continue
+        smooth += 1
+        fd = (Lp - Lm) / (2 * h)
+        assert abs(fd - d) <= 1e-5 * scale, (fd, d)
+    print(f"settling 10k: {smooth} smooth directions agree, {kinked} kinked")
+    assert smooth >= 16
+
+
+def test_gpu_adjoint_compliance():
+    """A relative compliance of 1e-12 leaves the derivative of a
+    well-posed network unchanged (parity with the rigid oracle holds); on a
+    loaded pile, whose contact network is hyperstatic, a compliance of 1e-3
+    gives converged, finite gradients through every step."""
+    import torch
+    from paper_1104_3516_gb300 import cd, workloads as W
+    wl = leaning_column(mu=0.18)
+    rng = np.random.default_rng(3)
+    weights = (rng.standard_normal(wl.x.shape), rng.standard_normal(wl.v.shape), rng.standard_normal(wl.w.shape))
+    g = cd.CDSystem(wl, device="cuda:0", criterion=cd.CD_CONV_GLOBAL_REL, alpha=FWD_ALPHA, max_sweeps=MAX_SWEEPS,
+                    tape_steps=4, adjoint_compliance=1e-12)
+    g.step(4)
+    gx, gv, gw = (torch.as_tensor(c.reshape(-1), device="cuda:0") for c in weights)
+    gmu = 0.0
+    for _ in range(4):
+        gx, gv, gw, st = g.adjoint_step(gx, gv, gw, ADJ_ALPHA, MAX_SWEEPS)
+        gmu += st["dL_dmu"]
+    ref = gpu_grad(wl, 4, weights)
+    assert np.abs(gv.cpu().numpy().reshape(-1, 2) - ref[1]).max() <= 1e-9 * max(np.abs(ref[1]).max(), 1.0)
+    assert abs(gmu - ref[3]) <= 1e-9 * max(abs(ref[3]), 1.0)
+
+    pile = W.settled_pile(7, 400)
+    g = cd.CDSystem(pile, device="cuda:0", criterion=cd.CD_CONV_GLOBAL_REL, alpha=1e-12, max_sweeps=20000,
+                    tape_steps=20, adjoint_compliance=1e-3)
+    g.step(20)
+    n = pile.n
+    gx = torch.zeros(2 * n, dtype=torch.float64, device="cuda:0")
+    gx[1::2] = 1.0 / n
+    gv, gw = torch.zeros_like(gx), torch.zeros(n, dtype=torch.float64, device="cuda:0")
+    hyper = 0
+    for _ in range(20):
+        gx, gv, gw, st = g.adjoint_step(gx, gv, gw, 1e-10, 200000, dL_dwall_force=[0, 0, 1.0, 0, 0, 0])
+        assert st["converged"] == 1 and st["diverged"] == 0, st
+        hyper += st["n_rows"] > st["n_dof"]
+    assert hyper > 0
+    assert torch.isfinite(gv).all() and torch.isfinite(gx).all()

@@ -217,3 +217,54 @@ def test_classify_reads_the_branches():
         lo=np.zeros(2), hi=np.ones(2), periodic=np.zeros(2, dtype=int), wall_vel=np.zeros((6, 3))),
         A.StepRecord(pairs=np.array([[0, 3]]), state=np.array([A.STICK]), sign=np.ones(1), shift=np.zeros((1, 2)),
                      wall_pos=np.zeros(6), P=np.zeros((1, 2))), np.array([[0.5, 1.0]]), 0.3))
+
+
+def test_floor_force_closed_form():
+    """A disc pressed on the floor (gap 0, moving down at v_y): it sticks,
+    v_y' = -gap/dt, so the floor force F = P_n / dt = m (g - v_y / dt - gap /
+    dt^2) and dF/dv_y = -m/dt, dF/dy = -m/dt^2, dF/dmu = 0."""
+    wl = resting_disc(radius=1.0, mu=0.3)
+    wl.v = np.array([[0.0, -0.01]])
+    s, recs = rollout(wl, 1)
+    assert recs[0].state.tolist() == [A.STICK]
+    m = 1.0 / wl.inv_m[0]
+    cs = A.consts_of(s)
+    z2, z1 = np.zeros((1, 2)), np.zeros(1)
+    cF = np.zeros(6)
+    cF[2] = 1.0
+    ey = np.array([[0.0, 1.0]])
+    d = A.directional_derivatives(cs, recs, wl.x, wl.v, wl.w, wl.mu, (z2, z2, z1),
+                                  [(z2, ey, z1, 0.0), (ey, z2, z1, 0.0), (z2, z2, z1, 1.0)], wall_weights=cF)
+    assert d == pytest.approx([-m / DT, -m / DT ** 2, 0.0], rel=1e-12, abs=1e-9)
+    x, v, w, F = A.rollout_map(cs, recs, wl.x, wl.v, wl.w, wl.mu, with_forces=True)
+    assert F[2] == pytest.approx(wall_force(s, 2), rel=1e-12)
+
+
+def test_wall_force_derivatives_match_finite_differences():
+    """The complex step of a loss on the last step's wall forces against
+    central differences of the oracle's iteration (one step of the gas)."""
+    wl = colliding_gas(n=300, phi=0.62, vsig=3.0, dt=0.05)
+    s, recs = rollout(wl, 1)
+    cs = A.consts_of(s)
+    cF = np.array([0.3, -0.7, 1.0, 0.0, 0.0, 0.0])
+    zero = (np.zeros_like(wl.x), np.zeros_like(wl.v), np.zeros_like(wl.w))
+    dirs = directions(wl, 6, seed=21)
+    d = A.directional_derivatives(cs, recs, wl.x, wl.v, wl.w, wl.mu, zero, dirs, wall_weights=cF)
+    h, clean = 1e-6, 0
+    for (ex, ev, ew, em), dd in zip(dirs, d):
+        sp, rp = rollout(wl, 1, wl.x + h * ex, wl.v + h * ev, wl.w + h * ew, wl.mu + h * em)
+        sm, rm = rollout(wl, 1, wl.x - h * ex, wl.v - h * ev, wl.w - h * ew, wl.mu - h * em)
+        if not (same_states(recs, rp) and same_states(recs, rm)):
+            continue
+        clean += 1
+        Fp = np.array([wall_force(sp, k) for k in range(6)])
+        Fm = np.array([wall_force(sm, k) for k in range(6)])
+        fd = float(np.sum(cF * (Fp - Fm)) / (2 * h))
+        assert abs(fd - dd) <= 1e-5 * max(abs(dd), 1.0), (fd, dd)
+    assert clean >= 4
+
+
+def wall_force(sys, k):
+    """Force on wall k in the oracle's last step, from its own impulses."""
+    pairs, P = sys.contacts, sys.impulses
+    return float(sum(P[c, 0] for c in range(len(pairs)) if pairs[c, 1] == sys.n + k) / sys.p.dt)
