@@ -307,7 +307,8 @@ k_adjoint(CdGeom g, CdWork w, CdTape t, CdAdjIO io, double alpha, int max_sweeps
         double* part = w.partials + (size_t)((sweeps & 1) ? 0 : 1) * 3 * nb;
         double acc[3] = {0.0, 0.0, 0.0};
         for (int k = 0; k < K; ++k) {
-            for (int p = s_off[k] + tid; p < s_off[k + 1]; p += stride) adj_update(g, w, t, io, p, thr, acc);
+            const CdSpan sp = cd_colour_span(s_off[k], s_off[k + 1]);
+            for (int p = sp.p; p < sp.end; p += blockDim.x) adj_update(g, w, t, io, p, thr, acc);
             if (k == K - 1) {
                 block_sum<3>(acc, s_red);
                 if (threadIdx.x == 0) {
@@ -333,7 +334,8 @@ k_adjoint(CdGeom g, CdWork w, CdTape t, CdAdjIO io, double alpha, int max_sweeps
     // position gradient, colour by colour (a colour touches each particle once)
     double acc[3] = {0.0, 0.0, 0.0};
     for (int k = 0; k < K; ++k) {
-        for (int p = s_off[k] + tid; p < s_off[k + 1]; p += stride) adj_geometry(g, w, t, p, thr, acc);
+        const CdSpan sp = cd_colour_span(s_off[k], s_off[k + 1]);
+        for (int p = sp.p; p < sp.end; p += blockDim.x) adj_geometry(g, w, t, p, thr, acc);
         if (!cd_grid_sync(ctrl, nb, epoch)) return;
     }
     double acc4[4] = {acc[0], acc[1], acc[2], 0.0};

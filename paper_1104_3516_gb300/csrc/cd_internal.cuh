@@ -293,6 +293,28 @@ __device__ __forceinline__ bool cd_grid_sync(CdCtrl* ctrl, unsigned long long nb
 }
 
 // ---------------------------------------------------------------------------
+// The contacts [lo, hi) of one colour class spread evenly over the blocks of
+// a persistent grid: block b takes the contiguous chunk b of ceil(count /
+// blocks) positions and its threads stride over it.  (Handing out positions
+// by global thread id would put a colour of 25k contacts on the first 49 of
+// 152 SMs and make their FP64 pipes the bottleneck of every colour phase.)
+// ---------------------------------------------------------------------------
+struct CdSpan {
+    int p;      // this thread's first position
+    int end;    // end of the block's chunk
+};
+__device__ __forceinline__ CdSpan cd_colour_span(int lo, int hi)
+{
+    const int cnt = hi - lo;
+    const int chunk = (cnt + (int)gridDim.x - 1) / (int)gridDim.x;
+    const int b0 = lo + (int)blockIdx.x * chunk;
+    CdSpan s;
+    s.p = b0 + (int)threadIdx.x;
+    s.end = (b0 + chunk < hi) ? b0 + chunk : hi;
+    return s;
+}
+
+// ---------------------------------------------------------------------------
 // Host-side launchers (defined in the .cu files), all on `stream`.
 // ---------------------------------------------------------------------------
 cudaError_t cd_scan_exclusive(const int* in, int* out, int n, int* tmp, int* total_dst, cudaStream_t stream,

@@ -458,15 +458,16 @@ __device__ __forceinline__ void colour_phase(const CdGeom& g, const CdWork& w, c
                                              int tid, int stride, Rec<DIM, T>& nxt, bool apply_only, int crit,
                                              double alpha, double ravg_prev, double (&acc)[3])
 {
-    const int end = s_off[k + 1];
-    int p = s_off[k] + tid;
+    const CdSpan sp = cd_colour_span(s_off[k], s_off[k + 1]);
+    const int end = sp.end;
+    int p = sp.p;
     const bool mixed = MIXED && !apply_only;   // parallel contacts were done in their own phase
     if (p < end) {
         if (!(mixed && cd_is_parallel(g.par_p, g.seed, cd_key(nxt.ab.x, nxt.ab.y)))) {
             UpdOut o = apply_rec<DIM, T>(g, w, p, nxt, apply_only, crit, alpha, ravg_prev);
             acc[0] += o.pabs; acc[1] += (double)o.rel_ok; acc[2] += (double)o.bad;
         }
-        for (p += stride; p < end; p += stride) {
+        for (p += blockDim.x; p < end; p += blockDim.x) {
             Rec<DIM, T> r;
             load_rec<DIM, T>(g, w, p, r);
             if (mixed && cd_is_parallel(g.par_p, g.seed, cd_key(r.ab.x, r.ab.y))) continue;
@@ -475,9 +476,10 @@ __device__ __forceinline__ void colour_phase(const CdGeom& g, const CdWork& w, c
         }
     }
     if (knext >= 0) {
-        int q = s_off[knext] + tid;
-        if (q < s_off[knext + 1]) load_rec<DIM, T>(g, w, q, nxt);
+        const CdSpan sq = cd_colour_span(s_off[knext], s_off[knext + 1]);
+        if (sq.p < sq.end) load_rec<DIM, T>(g, w, sq.p, nxt);
     }
+    (void)tid; (void)stride;
 }
 
 // Epilogue shared by both sweep kernels: impulses back to key order (FP64),
@@ -653,7 +655,10 @@ k_sweep(CdGeom g, CdWork w, int crit, double alpha, int max_sweeps)
     double resid = 0.0, ravg = 0.0, ravg_prev = 0.0;
     if (nc > 0) {
         Rec<DIM, T> nxt;
-        if (s_off[0] + tid < s_off[1]) load_rec<DIM, T>(g, w, s_off[0] + tid, nxt);
+        {
+            const CdSpan s0 = cd_colour_span(s_off[0], s_off[1]);
+            if (s0.p < s0.end) load_rec<DIM, T>(g, w, s0.p, nxt);
+        }
         // starting impulses, colour by colour
         double acc[3] = {0.0, 0.0, 0.0};
         for (int k = 0; k < K; ++k) {
@@ -684,7 +689,8 @@ k_sweep(CdGeom g, CdWork w, int crit, double alpha, int max_sweeps)
                 if (!cd_grid_sync(ctrl, nb, epoch)) return;
                 // the prefetched record of colour 0 may belong to a parallel contact whose
                 // impulse just changed: reload it
-                if (s_off[0] + tid < s_off[1]) load_rec<DIM, T>(g, w, s_off[0] + tid, nxt);
+                const CdSpan s0 = cd_colour_span(s_off[0], s_off[1]);
+                if (s0.p < s0.end) load_rec<DIM, T>(g, w, s0.p, nxt);
             }
             for (int k = 0; k < K; ++k) {
                 colour_phase<DIM, T, MIXED>(g, w, s_off, k, (k + 1 < K) ? k + 1 : 0, tid, stride, nxt, false, crit, alpha,
@@ -819,7 +825,8 @@ k_sweep_batch(CdGeom g, CdWork w, int crit, double alpha, int max_sweeps)
 
     // starting impulses, colour by colour
     for (int k = 0; k < K; ++k) {
-        for (int p = s_off[k] + tid; p < s_off[k + 1]; p += stride) {
+        const CdSpan sp = cd_colour_span(s_off[k], s_off[k + 1]);
+        for (int p = sp.p; p < sp.end; p += blockDim.x) {
             Rec<DIM, T> r;
             load_rec<DIM, T>(g, w, p, r);
             UpdOut o = apply_rec<DIM, T>(g, w, p, r, true, crit, alpha, 0.0);
@@ -833,7 +840,8 @@ k_sweep_batch(CdGeom g, CdWork w, int crit, double alpha, int max_sweeps)
     for (int sweep = 0; sweep < max_sweeps && nc > 0; ++sweep) {
         if (tid == 0) w.act_cnt[(sweep + 1) % 3] = 0;
         for (int k = 0; k < K; ++k) {
-            for (int p = s_off[k] + tid; p < s_off[k + 1]; p += stride) {
+            const CdSpan sp = cd_colour_span(s_off[k], s_off[k + 1]);
+            for (int p = sp.p; p < sp.end; p += blockDim.x) {
                 Rec<DIM, T> r;
                 load_rec<DIM, T>(g, w, p, r);
                 if (w.pk_done[r.pk]) continue;
@@ -1397,6 +1405,11 @@ cudaError_t cd_launch_unpack(const CdGeom& g, const CdWork& w, double* pos, doub
 
 static const void* sweep_fn(int dim, int precision, int tiled)
 {
+    if (tiled == 4) {
+        if (dim == 2)
+            return precision == CD_FP64 ? (const void*)k_sweep<2, double, true> : (const void*)k_sweep<2, float, true>;
+        return precision == CD_FP64 ? (const void*)k_sweep<3, double, true> : (const void*)k_sweep<3, float, true>;
+    }
     if (tiled == 3) {
         if (dim == 2)
             return precision == CD_FP64 ? (const void*)k_sweep_batch<2, double> : (const void*)k_sweep_batch<2, float>;
@@ -1411,11 +1424,6 @@ static const void* sweep_fn(int dim, int precision, int tiled)
         if (dim == 2)
             return precision == CD_FP64 ? (const void*)k_sweep_tiled<2, double> : (const void*)k_sweep_tiled<2, float>;
         return precision == CD_FP64 ? (const void*)k_sweep_tiled<3, double> : (const void*)k_sweep_tiled<3, float>;
-    }
-    if (tiled == 4) {
-        if (dim == 2)
-            return precision == CD_FP64 ? (const void*)k_sweep<2, double, true> : (const void*)k_sweep<2, float, true>;
-        return precision == CD_FP64 ? (const void*)k_sweep<3, double, true> : (const void*)k_sweep<3, float, true>;
     }
     if (dim == 2)
         return precision == CD_FP64 ? (const void*)k_sweep<2, double, false> : (const void*)k_sweep<2, float, false>;
