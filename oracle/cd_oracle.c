@@ -311,8 +311,10 @@ void ora_contact_geometry(const ora_params* p, long long n, const double* x, con
 /* ------------------------------------------------------------------------ */
 /* Colouring of the contact graph: two contacts conflict when they share a  */
 /* particle (walls are kinematic and never conflict).  Greedy in descending */
-/* priority prio = splitmix64(seed ^ key), ties by ascending key; each      */
-/* contact takes the smallest colour not used by an earlier neighbour.      */
+/* priority, ties by ascending key; each contact takes the smallest colour  */
+/* not used by an earlier neighbour.  prio = (d_a + d_b) * 2^56 +           */
+/* (splitmix64(seed ^ key) >> 8), d = contacts of a particle (walls 0),     */
+/* the sum capped at 255: largest degree first, random among equals.        */
 /* ------------------------------------------------------------------------ */
 typedef struct { uint64_t prio; uint64_t key; long long idx; } prio_item;
 
@@ -358,7 +360,15 @@ static int colour_greedy_in(long long n, long long nc, const int32_t* pairs, uin
     prio_item* it = (prio_item*)malloc(sizeof(prio_item) * (size_t)nc);
     for (long long c = 0; c < nc; ++c) {
         uint64_t k = key_of(pairs[2 * c], pairs[2 * c + 1]);
-        it[c].prio = ora_splitmix64(seed ^ k);
+        /* largest degree first: contacts per particle of both ends, summed
+         * (capped at 255), in the top byte; the hash below it */
+        uint64_t ds = 0;
+        for (int s = 0; s < 2; ++s) {
+            long long q = pairs[2 * c + s];
+            if (q < n) ds += (uint64_t)(deg[q + 1] - deg[q]);
+        }
+        if (ds > 255) ds = 255;
+        it[c].prio = (ds << 56) | (ora_splitmix64(seed ^ k) >> 8);
         it[c].key = k;
         it[c].idx = c;
         colour[c] = -1;

@@ -5,8 +5,10 @@
 // share no particle are independent, so one colour class is updated in
 // parallel and every freshly computed impulse is seen by the later colours.
 //
-// Colouring: Jones-Plassmann with priority splitmix64(seed ^ key) (ties by
-// ascending key).  A contact takes the smallest colour not used by any
+// Colouring: Jones-Plassmann with priority (d_a + d_b) * 2^56 +
+// (splitmix64(seed ^ key) >> 8), d the contacts of a particle (largest degree
+// first, which needs one colour fewer than a random order on dense piles),
+// ties by ascending key.  A contact takes the smallest colour not used by any
 // higher-priority neighbour once all of those are coloured; the fixed point
 // equals the greedy colouring in descending priority, so the result does not
 // depend on scheduling.  Walls never conflict.
@@ -79,16 +81,22 @@ __global__ void __launch_bounds__(CD_SWEEP_THREADS) k_jp(CdGeom g, CdWork w, uns
     const int stride = gridDim.x * blockDim.x;
     for (int c = tid; c < nc; c += stride) {
         int2 ab = w.pairs[c];
+        unsigned long long h;
         if (g.npk > 1) {
             // a packing of a batch is coloured with its own seed and local
             // ids (walls n_b + k), exactly as if it were a system alone
             const CdPack& P = w.pk[w.pack_of[ab.x]];
             const int al = ab.x - P.first;
             const int bl = (ab.y < g.n) ? ab.y - P.first : P.count + (ab.y - g.n) % 6;
-            prio[c] = cd_splitmix64(P.seed ^ cd_key(al, bl));
+            h = cd_splitmix64(P.seed ^ cd_key(al, bl));
         } else {
-            prio[c] = cd_splitmix64(g.seed ^ cd_key(ab.x, ab.y));
+            h = cd_splitmix64(g.seed ^ cd_key(ab.x, ab.y));
         }
+        // largest degree first (contacts of both ends, capped at 255), then the hash
+        unsigned long long ds = (unsigned long long)(w.p2c_off[ab.x + 1] - w.p2c_off[ab.x]);
+        if (ab.y < g.n) ds += (unsigned long long)(w.p2c_off[ab.y + 1] - w.p2c_off[ab.y]);
+        if (ds > 255ULL) ds = 255ULL;
+        prio[c] = (ds << 56) | (h >> 8);
         w.colour[c] = -1;
     }
     if (tid == 0) { round_cnt[0] = 0; round_cnt[1] = 0; round_cnt[2] = 0; ctrl->ncolours = 0; }
