@@ -312,7 +312,9 @@ __device__ __forceinline__ UpdOut core2d(const CdGeom& g, const Rec<2, T>& r, ty
     Pnew.x = Pn; Pnew.y = Pt;
     UpdOut o;
     double pn = (double)Pn, pt = (double)Pt;
-    o.pabs = sqrt(pn * pn + pt * pt);
+    // FP32 impulses carry 1e-7 anyway: their magnitude is taken in FP32 (the sum stays FP64)
+    if constexpr (sizeof(T) == 4) o.pabs = (double)sqrtf(Pn * Pn + Pt * Pt);
+    else o.pabs = sqrt(pn * pn + pt * pt);
     o.rel_ok = 0; o.bad = 0;
     if (!apply_only && crit == CD_CONV_LOCAL) {
         double d0 = (double)dPn, d1 = (double)dPt;
@@ -401,7 +403,8 @@ __device__ __forceinline__ UpdOut core3d(const CdGeom& g, const Rec<3, T>& r, ty
     Pnew.x = Pn; Pnew.y = Ptx; Pnew.z = Pty; Pnew.w = Ptz;
     UpdOut o;
     double pn = (double)Pn, px = (double)Ptx, py = (double)Pty, pz = (double)Ptz;
-    o.pabs = sqrt(pn * pn + px * px + py * py + pz * pz);
+    if constexpr (sizeof(T) == 4) o.pabs = (double)sqrtf(Pn * Pn + Ptx * Ptx + Pty * Pty + Ptz * Ptz);
+    else o.pabs = sqrt(pn * pn + px * px + py * py + pz * pz);
     o.rel_ok = 0; o.bad = 0;
     if (!apply_only && crit == CD_CONV_LOCAL) {
         double d0 = (double)dPn, d1 = (double)dtx, d2_ = (double)dty, d3 = (double)dtz;
@@ -465,14 +468,16 @@ __device__ __forceinline__ void colour_phase(const CdGeom& g, const CdWork& w, c
     if (p < end) {
         if (!(mixed && cd_is_parallel(g.par_p, g.seed, cd_key(nxt.ab.x, nxt.ab.y)))) {
             UpdOut o = apply_rec<DIM, T>(g, w, p, nxt, apply_only, crit, alpha, ravg_prev);
-            acc[0] += o.pabs; acc[1] += (double)o.rel_ok; acc[2] += (double)o.bad;
+            acc[0] += o.pabs;
+            if (crit == CD_CONV_LOCAL) { acc[1] += (double)o.rel_ok; acc[2] += (double)o.bad; }
         }
         for (p += blockDim.x; p < end; p += blockDim.x) {
             Rec<DIM, T> r;
             load_rec<DIM, T>(g, w, p, r);
             if (mixed && cd_is_parallel(g.par_p, g.seed, cd_key(r.ab.x, r.ab.y))) continue;
             UpdOut o = apply_rec<DIM, T>(g, w, p, r, apply_only, crit, alpha, ravg_prev);
-            acc[0] += o.pabs; acc[1] += (double)o.rel_ok; acc[2] += (double)o.bad;
+            acc[0] += o.pabs;
+            if (crit == CD_CONV_LOCAL) { acc[1] += (double)o.rel_ok; acc[2] += (double)o.bad; }
         }
     }
     if (knext >= 0) {
@@ -684,7 +689,8 @@ k_sweep(CdGeom g, CdWork w, int crit, double alpha, int max_sweeps)
                     load_rec<DIM, T>(g, w, p, r);
                     if (!cd_is_parallel(g.par_p, g.seed, cd_key(r.ab.x, r.ab.y))) continue;
                     UpdOut o = par_compute<DIM, T>(g, w, p, r, crit, alpha, ravg_prev);
-                    a3[0] += o.pabs; a3[1] += (double)o.rel_ok; a3[2] += (double)o.bad;
+                    a3[0] += o.pabs;
+                    if (crit == CD_CONV_LOCAL) { a3[1] += (double)o.rel_ok; a3[2] += (double)o.bad; }
                 }
                 if (!cd_grid_sync(ctrl, nb, epoch)) return;
                 // the prefetched record of colour 0 may belong to a parallel contact whose
@@ -1030,7 +1036,8 @@ __device__ __forceinline__ bool flow_update(const CdGeom& g, const CdWork& w, in
     }
     st_release_s32(ca, ea + 1);
     if (!wall) st_release_s32(cb, eb + 1);
-    acc[0] += o.pabs; acc[1] += (double)o.rel_ok; acc[2] += (double)o.bad;
+    acc[0] += o.pabs;
+            if (crit == CD_CONV_LOCAL) { acc[1] += (double)o.rel_ok; acc[2] += (double)o.bad; }
     return true;
 }
 
@@ -1256,7 +1263,8 @@ __device__ __forceinline__ void process_tile(const CdGeom& g, const CdWork& w, i
                 load_rec<DIM, T>(g, w, p, r);
                 o = apply_rec<DIM, T>(g, w, p, r, apply_only, crit, alpha, ravg_prev);
             }
-            acc[0] += o.pabs; acc[1] += (double)o.rel_ok; acc[2] += (double)o.bad;
+            acc[0] += o.pabs;
+            if (crit == CD_CONV_LOCAL) { acc[1] += (double)o.rel_ok; acc[2] += (double)o.bad; }
         }
         __syncthreads();
     }
