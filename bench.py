@@ -44,10 +44,19 @@ WORKLOAD = "dense_biaxial_discs_2d"
 # read + write 2 x 24, inv_m, r, r/I 24); FP32 halves the real-valued parts
 BYTES_PER_CONTACT = {"f64": 80, "f32": 44}
 BYTES_PER_PARTICLE = {"f64": 72, "f32": 36}
+# 3D: contact record ids 8, geometry 32, (m_n, m_t) 16, impulse read 32 +
+# write 32; particle v, w read + write 2 x 64, static 32 (FP32 halves the reals)
+BYTES_PER_CONTACT_3D = {"f64": 120, "f32": 64}
+BYTES_PER_PARTICLE_3D = {"f64": 160, "f32": 80}
 # algorithmic FP64 flops of one 2D contact update as the sweep kernel writes
 # it: relative velocity 2 + 2 (u_n) + 7 (u_t), P_n 3, mu P_n 1, P_t 2,
 # impulse change 2, its vector 6, both bodies' velocities 12, |P| 4 (3 + sqrt)
 FLOPS_PER_UPDATE_2D = 42
+# 3D (FMA = 2): lever sums 9, relative velocity 15, u_n 5, tangential part 6,
+# P_n 3, trial P_t 6, mu P_n 1, cone test 6, impulse change 4, its vector 6,
+# n x dP 9, both bodies' v and w 24, |P| 7 (+ square root; the cone scaling
+# of sliding contacts is not counted)
+FLOPS_PER_UPDATE_3D = 101
 # FP64 peak of GB300 from unit counts and clock: 152 SMs x 2 FP64 FMA/clk x 2
 # flops x 2.07 GHz (nominal 1.25 TFLOP/s)
 FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12
@@ -60,7 +69,12 @@ def parse():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--precision", choices=["f64", "f32"], default="f64")
-    ap.add_argument("--n-discs", "--n", dest="n", type=int, default=100_000)
+    ap.add_argument("--workload", choices=["dense_biaxial_discs_2d", "sphere_gas_3d"],
+                    default="dense_biaxial_discs_2d",
+                    help="the 2D dense pile (default) or the 1e6-sphere 3D gas (its own run; no batched or "
+                         "adjoint legs)")
+    ap.add_argument("--n-discs", "--n", dest="n", type=int, default=None,
+                    help="particles (default 100,000 discs or 1,000,000 spheres)")
     ap.add_argument("--max-sweeps", type=int, default=1000)
     ap.add_argument("--alpha", type=float, default=1e-6)
     ap.add_argument("--no-e2e", action="store_true")
@@ -81,19 +95,28 @@ def parse():
 
 def workload(args, rank):
     from paper_1104_3516_gb300 import workloads as W
-    wl = W.dense_biaxial_discs(seed=1106 + rank, n=args.n)
+    if args.workload == "sphere_gas_3d":
+        wl = W.sphere_gas(seed=1107 + rank, n=args.n or 1_000_000)
+    else:
+        wl = W.dense_biaxial_discs(seed=1106 + rank, n=args.n or 100_000)
     wl.max_sweeps = args.max_sweeps
     wl.alpha = args.alpha
     return wl
 
 
 def config(args, wl, extra=None):
-    c = {"workload": WORKLOAD, "n_discs": wl.n, "packing_fraction_box": 0.80, "mu": wl.mu, "dt": wl.dt,
-         "gravity": 1.0, "top_wall_speed": 1e-3, "periodic": "x", "criterion": "global |dR_avg|/(R^j+R^j-1)",
-         "alpha": args.alpha, "max_sweeps": args.max_sweeps, "warm_start": True,
-         "order": ("colour (JP greedy)" if args.tile_cells == 0 else
-                   f"tiled colour order, {args.tile_cells}-cell tiles"),
-         "l2": "flushed (512 MiB write) before every timed step"}
+    if wl.dim == 3:
+        c = {"workload": "sphere_gas_3d", "n_spheres": wl.n, "packing_fraction_gas": 0.3, "mu": wl.mu,
+             "dt": wl.dt, "gravity": 1.0, "floor": "100 x 100, 4 side walls", "v0": "N(0, 0.1)",
+             "rotations": True}
+    else:
+        c = {"workload": WORKLOAD, "n_discs": wl.n, "packing_fraction_box": 0.80, "mu": wl.mu, "dt": wl.dt,
+             "gravity": 1.0, "top_wall_speed": 1e-3, "periodic": "x"}
+    c.update({"criterion": "global |dR_avg|/(R^j+R^j-1)", "alpha": args.alpha, "max_sweeps": args.max_sweeps,
+              "warm_start": True,
+              "order": ("colour (largest degree first, then hash)" if args.tile_cells == 0 else
+                        f"tiled colour order, {args.tile_cells}-cell tiles"),
+              "l2": "flushed (512 MiB write) before every timed step"})
     if extra:
         c.update(extra)
     return c
@@ -247,7 +270,7 @@ def run_reference(args):
     oracle_steps(wl, args.warmup, args.cpu_sweeps) if args.warmup > 0 else None
     upd, sec, sweeps, nc = oracle_steps(wl, args.steps, args.cpu_sweeps)
     value = upd / sec
-    sample = (f"{args.steps} oracle time steps of the {wl.n}-disc workload, random sequential order, sweep cap "
+    sample = (f"{args.steps} oracle time steps of the {wl.n}-particle workload, random sequential order, sweep cap "
               f"lowered to {args.cpu_sweeps} ({sweeps} sweeps over {nc} contacts)")
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * sec / max(args.steps, 1),
@@ -289,7 +312,11 @@ def run_ours(args):
     ph = {"detect": 0.0, "colour_order_pack": 0.0, "sweep": 0.0, "integrate": 0.0}
     sweep_bytes = 0.0
     ncs, colours = [], []
-    bpc, bpp = BYTES_PER_CONTACT[args.precision], BYTES_PER_PARTICLE[args.precision]
+    if wl.dim == 3:
+        bpc, bpp = BYTES_PER_CONTACT_3D[args.precision], BYTES_PER_PARTICLE_3D[args.precision]
+    else:
+        bpc, bpp = BYTES_PER_CONTACT[args.precision], BYTES_PER_PARTICLE[args.precision]
+    flops_per_update = FLOPS_PER_UPDATE_3D if wl.dim == 3 else FLOPS_PER_UPDATE_2D
     for _ in range(args.steps):
         flush.zero_()
         st = sysg.step(1)
@@ -317,7 +344,7 @@ def run_ours(args):
     peak, peak_kind = peaks()
     kname = ("k_sweep" if args.tile_cells == 0 and args.dataflow == 0 else
              ("k_sweep_tiled" if args.tile_cells else "k_sweep_flow"))
-    kname += f"<2,{'double' if args.precision == 'f64' else 'float'}>"
+    kname += f"<{wl.dim},{'double' if args.precision == 'f64' else 'float'}>"
     sweep_s = ph["sweep"] / 1e3
     gbs = sweep_bytes / sweep_s / 1e9 if sweep_s > 0 else 0.0
     hbm_view = {"bound": "hbm", "achieved": gbs, "peak": peak, "unit": "GB/s", "frac": gbs / peak,
@@ -325,21 +352,21 @@ def run_ours(args):
                 "bytes_model": f"per sweep {bpc} B x contacts + {bpp} B x particles"}
     traffic = profiled_traffic(kname, args.precision, wl.n)
     if args.precision == "f64":
-        tf = FLOPS_PER_UPDATE_2D * upd / sweep_s / 1e12 if sweep_s > 0 else 0.0
+        tf = flops_per_update * upd / sweep_s / 1e12 if sweep_s > 0 else 0.0
         roofline = {"bound": "alu", "achieved": tf, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
                     "frac": tf / FP64_PEAK_TFLOPS, "traffic": traffic, "kernel": kname,
                     "peak_source": "FP64 unit count x clock (152 SMs x 2 FMA/clk x 2 x 2.07 GHz)",
-                    "flops_model": f"{FLOPS_PER_UPDATE_2D} FP64 flops per contact update",
+                    "flops_model": f"{flops_per_update} FP64 flops per contact update",
                     "avg_launch_ms": ph["sweep"] / max(args.steps, 1), "hbm_view": hbm_view}
     else:
         roofline = dict(hbm_view, traffic=traffic, kernel=kname, avg_launch_ms=ph["sweep"] / max(args.steps, 1))
 
     batched = None
-    if args.batched_steps > 0:
+    if args.batched_steps > 0 and wl.dim == 2:
         batched = run_batched(args, device, rank, flush)
 
     adjoint = None
-    if args.adjoint_steps > 0 and args.precision == "f64":
+    if args.adjoint_steps > 0 and args.precision == "f64" and wl.dim == 2:
         adjoint = run_adjoint(args, device, rank, flush)
 
     e2e = None
@@ -350,7 +377,7 @@ def run_ours(args):
     if rank == 0 and not args.no_cpu_baseline:
         o_upd, o_sec, o_sweeps, o_nc = oracle_steps(wl, 1, args.cpu_sweeps)
         cpu = {"value": o_upd / o_sec, "unit": UNIT, "cores": 1, "kind": "oracle",
-               "sample": f"1 oracle time step of the same {wl.n}-disc packing, random sequential order, sweep cap "
+               "sample": f"1 oracle time step of the same {wl.n}-particle packing, random sequential order, sweep cap "
                          f"{args.cpu_sweeps} ({o_sweeps} sweeps over {o_nc} contacts, {o_sec:.1f} s)",
                "cpu": platform.processor() or platform.machine()}
 
@@ -536,9 +563,10 @@ def run_e2e(args, sysg, wl, device, ws):
     n, D = wl.n, wl.dim
     pos_h = torch.empty(n * D, dtype=torch.float64, pin_memory=True)
     vel_h = torch.empty(n * D, dtype=torch.float64, pin_memory=True)
-    om_h = torch.empty(n, dtype=torch.float64, pin_memory=True)
+    rot = 1 if D == 2 else 3
+    om_h = torch.empty(n * rot, dtype=torch.float64, pin_memory=True)
     cd.cd_download_state(sysg.handle, pos_h, vel_h, om_h)
-    h2d = d2h = (2 * n * D + n) * 8
+    h2d = d2h = (2 * n * D + n * rot) * 8
     barrier(ws)
     torch.cuda.synchronize(device)
     t0 = time.perf_counter()

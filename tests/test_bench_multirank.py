@@ -30,7 +30,7 @@ def _rank_body(rank, ws, port, out_dir):
     import argparse
     import bench
     import torch.distributed as dist
-    args = argparse.Namespace(impl="ours", n=300, max_sweeps=50, alpha=1e-6)
+    args = argparse.Namespace(impl="ours", workload="dense_biaxial_discs_2d", n=300, max_sweeps=50, alpha=1e-6)
     r, w, local = bench.dist_init(args, backend="gloo")
     assert (r, w, local) == (rank, ws, rank)
     wl = bench.workload(args, r)
