@@ -190,6 +190,24 @@ __global__ void k_cell_fill(int n, const int* __restrict__ cell_of, const int* _
     }
 }
 
+// Each cell's particle list in ascending id order (the atomic fill leaves it
+// in arrival order): lets the pair walk skip a whole cell whose last id is
+// not above the particle's own.
+__global__ void k_cell_sort(int ncell, const int* __restrict__ cell_start, int* __restrict__ cell_pid,
+                            const CdCtrl* ctrl)
+{
+    if (ctrl->skip) return;
+    for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < ncell; c += gridDim.x * blockDim.x) {
+        const int b = cell_start[c], e = cell_start[c + 1];
+        for (int k = b + 1; k < e; ++k) {
+            const int v = cell_pid[k];
+            int j = k - 1;
+            while (j >= b && cell_pid[j] > v) { cell_pid[j + 1] = cell_pid[j]; --j; }
+            cell_pid[j + 1] = v;
+        }
+    }
+}
+
 // Separation b - a along axis k with the minimum-image rule (same operations
 // as the oracle).
 __device__ __forceinline__ double sep_axis(const GridV& v, int k, double xa, double xb)
@@ -232,12 +250,19 @@ __device__ __forceinline__ bool wall_on(const GridV& v, int dim, int k)
 
 // Visits the candidate partners b > a of particle a in the 3^DIM cells around
 // it (in a's packing grid); calls f(b) for each b that passes the pair test.
+// Needs each cell's list sorted by id (k_cell_sort).
+// The cell ranges are gathered first (independent loads) and the candidates
+// are then walked as one flat sequence, so the lanes of a warp loop about as
+// many times as their total candidate counts, not the per-cell maxima.
 template <int DIM, typename F>
 __device__ __forceinline__ void for_each_partner(const CdGeom& g, const GridV& v, int a, const double* xa, double ra,
                                                  const double* __restrict__ pos, const double* __restrict__ radius,
                                                  const int* __restrict__ cell_of, const int* __restrict__ cell_start,
                                                  const int* __restrict__ cell_pid, F f)
 {
+    constexpr int NC = (DIM == 3) ? 27 : 9;
+    int lo[NC], hi[NC];
+    int m = 0;
     int c = cell_of[a] - v.base;
     int q0 = c % v.ncell[0];
     int q1 = (c / v.ncell[0]) % v.ncell[1];
@@ -263,15 +288,27 @@ __device__ __forceinline__ void for_each_partner(const CdGeom& g, const GridV& v
                     if (!v.periodic[0]) continue;
                     t0 = (t0 + v.ncell[0]) % v.ncell[0];
                 }
-                int cc = v.base + (t2 * v.ncell[1] + t1) * v.ncell[0] + t0;
-                int e = cell_start[cc + 1];
-                for (int s = cell_start[cc]; s < e; ++s) {
-                    int b = cell_pid[s];
-                    if (b <= a) continue;
-                    if (pair_touches<DIM>(v, g.delta, xa, ra, pos, radius, b)) f(b);
+                const int cc = v.base + (t2 * v.ncell[1] + t1) * v.ncell[0] + t0;
+                const int l = cell_start[cc], h = cell_start[cc + 1];
+                // ids ascend within a cell: a cell whose last id is <= a has no partner b > a
+                if (h > l && cell_pid[h - 1] > a) {
+                    lo[m] = l;
+                    hi[m] = h;
+                    ++m;
                 }
             }
         }
+    }
+    int j = 0;
+    int s = (m > 0) ? lo[0] : 0;
+    for (;;) {
+        while (j < m && s >= hi[j]) {
+            ++j;
+            if (j < m) s = lo[j];
+        }
+        if (j >= m) break;
+        const int b = cell_pid[s++];
+        if (b > a && pair_touches<DIM>(v, g.delta, xa, ra, pos, radius, b)) f(b);
     }
 }
 
@@ -520,6 +557,7 @@ cudaError_t cd_launch_detect(const CdGeom& g, const CdWork& w, const double* pos
     ++*nl;
     if ((e = cd_scan_exclusive(w.cell_cnt, w.cell_start, ncell + 1, w.scan_tmp, nullptr, s, nl)) != cudaSuccess) return e;
     k_cell_fill<<<gb, CD_BLOCK, 0, s>>>(g.n, w.cell_of, w.cell_start, w.cell_fill, w.cell_pid, w.ctrl); ++*nl;
+    k_cell_sort<<<grid_for(ncell), CD_BLOCK, 0, s>>>(ncell, w.cell_start, w.cell_pid, w.ctrl); ++*nl;
     if (g.dim == 2)
         k_pair_count<2><<<gb, CD_BLOCK, 0, s>>>(g, w, pos, radius, w.cell_of, w.cell_start, w.cell_pid, w.pcnt,
                                                 w.ctrl);
