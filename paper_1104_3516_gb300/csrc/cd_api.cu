@@ -155,7 +155,17 @@ static size_t layout(cd_system* s, char* base, CdWork* w)
     t.pk_stats = L.take<double>(base, CD_PKSTATS * npk);
     t.c_abs = L.take<double>(base, cap);
     t.c_flag = L.take<int>(base, cap);
-    t.act_cnt = L.take<int>(base, 4);
+    t.act_cnt = L.take<int>(base, 8);
+    {
+        const size_t cb = (npk > 1) ? cap : 1;
+        t.c_ab2 = L.take<int2>(base, cb);
+        t.c_geo2 = L.take<char>(base, cb * 4 * real);
+        t.c_m2 = L.take<char>(base, cb * (s->p.dim == 2 ? 1 : 2) * real);
+        t.c_P2 = L.take<char>(base, cb * (s->p.dim == 2 ? 2 : 4) * real);
+        t.perm2 = L.take<int>(base, cb);
+        t.cmp_blk = L.take<int>(base, G);
+        t.cmp_off = L.take<int>(base, CD_KMAX + 1);
+    }
     t.c_dpar = L.take<double>(base, s->g.par_p > 0.0 ? cap * s->pw : 1);
     t.obs = L.take<double>(base, CD_OBS_MAX);
     const size_t T = (size_t)s->p.tape_steps;

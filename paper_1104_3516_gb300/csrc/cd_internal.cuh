@@ -134,7 +134,16 @@ struct CdWork {
     double* pk_stats;   // npk * CD_PKSTATS per-packing statistics
     double* c_abs;      // cap (key order): |P| of the last update
     int* c_flag;        // cap (key order): local test bits of the last update
-    int* act_cnt;       // 3 counters of packings still iterating
+    int* act_cnt;       // 3 counters of packings still iterating, then 3 of their contacts
+    // batched systems: second set of colour-order arrays for dropping the
+    // contacts of converged packings during the solve
+    int2* c_ab2;
+    void* c_geo2;
+    void* c_m2;
+    void* c_P2;
+    int* perm2;
+    int* cmp_blk;       // G: kept contacts per block
+    int* cmp_off;       // CD_KMAX + 1: colour offsets after dropping
     double* c_dpar;     // cap * pw (key order): impulse change of a parallel contact
     double* obs;        // CD_OBS_MAX doubles: observable results
     // adjoint (params.tape_steps > 0)

@@ -750,7 +750,7 @@ k_sweep(CdGeom g, CdWork w, int crit, double alpha, int max_sweeps)
 // skipped from the next sweep on, exactly as if it were solved alone.
 // ---------------------------------------------------------------------------
 __device__ __forceinline__ void pk_reduce(const CdGeom& g, const CdWork& w, int sweep, int crit, double alpha,
-                                          int* act_slot, double (*s_red)[3])
+                                          int* act_slot, int* act_c_slot, double (*s_red)[3])
 {
     for (int b = blockIdx.x; b < g.npk; b += gridDim.x) {
         double* st = w.pk_stats + CD_PKSTATS * b;
@@ -804,11 +804,133 @@ __device__ __forceinline__ void pk_reduce(const CdGeom& g, const CdWork& w, int 
                     w.pk_done[b] = 1;
                 } else {
                     atomicAdd(act_slot, 1);
+                    atomicAdd(act_c_slot, ncb);
                 }
             }
         }
         __syncthreads();
     }
+}
+
+// Exclusive scan of a 0/1 flag over the block (ballot per warp, warp totals in
+// shared memory); returns the flags before this thread, *total the block's sum.
+__device__ __forceinline__ int block_excl_scan01(int f, int* s_warp, int* total)
+{
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    const unsigned m = __ballot_sync(0xffffffffu, f);
+    const int in_warp = __popc(m & ((1u << lane) - 1u));
+    if (lane == 0) s_warp[wid] = __popc(m);
+    __syncthreads();
+    int before = 0, tot = 0;
+    for (int q = 0; q < nw; ++q) {
+        const int c = s_warp[q];
+        if (q < wid) before += c;
+        tot += c;
+    }
+    __syncthreads();
+    *total = tot;
+    return before + in_warp;
+}
+
+// Drops the contacts of converged packings from the colour-order arrays: a
+// stable partition into the second set of arrays, copied back to the front of
+// the first, so that later sweeps spread only the active contacts over the
+// grid.  A dropped contact's final impulse goes back to key order here.
+// Colour order and the updates themselves are unchanged, so results are
+// identical.  Returns the new number of positions (same in every block).
+template <int DIM, typename T>
+__device__ __forceinline__ int compact_batch(const CdGeom& g, const CdWork& w, int nact, int K, int* s_off,
+                                             unsigned long long& epoch, bool& ok)
+{
+    typedef typename Vec<T>::V4 T4;
+    typedef typename Vec<T>::V2 T2;
+    __shared__ int s_warp[CD_SWEEP_THREADS / 32];
+    __shared__ int s_base;
+    CdCtrl* ctrl = w.ctrl;
+    const int nb = gridDim.x;
+    const int chunk = (nact + nb - 1) / nb;
+    const int lo = min((int)blockIdx.x * chunk, nact), hi = min(lo + chunk, nact);
+    auto keep = [&](int p) { return cd_ld_volatile_int(&w.pk_done[w.pack_of[w.c_ab[p].x]]) == 0; };
+    int cnt = 0;
+    for (int p = lo + (int)threadIdx.x; p < hi; p += blockDim.x) cnt += keep(p) ? 1 : 0;
+    cnt = __reduce_add_sync(0xffffffffu, cnt);
+    if ((threadIdx.x & 31) == 0) s_warp[threadIdx.x >> 5] = cnt;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        int t = 0;
+        for (int q = 0; q < (int)(blockDim.x >> 5); ++q) t += s_warp[q];
+        w.cmp_blk[blockIdx.x] = t;
+    }
+    if (!cd_grid_sync(ctrl, nb, epoch)) { ok = false; return nact; }
+    if (threadIdx.x == 0) {
+        int b0 = 0, tot = 0;
+        for (int q = 0; q < nb; ++q) {
+            const int c = cd_ld_volatile_int(&w.cmp_blk[q]);
+            if (q < (int)blockIdx.x) b0 += c;
+            tot += c;
+        }
+        s_base = b0;
+        if (blockIdx.x == 0)
+            for (int k = 0; k <= K; ++k)
+                if (s_off[k] == nact) w.cmp_off[k] = tot;
+    }
+    __syncthreads();
+    int running = s_base;
+    const int pw = (DIM == 2) ? 2 : 4;
+    for (int t0 = lo; t0 < hi; t0 += blockDim.x) {
+        const int p = t0 + (int)threadIdx.x;
+        const int f = (p < hi) && keep(p);
+        int tile_tot;
+        const int ex = block_excl_scan01(f, s_warp, &tile_tot);
+        if (p < hi) {
+            for (int k = 0; k <= K; ++k)
+                if (s_off[k] == p) w.cmp_off[k] = running + ex;
+            if (f) {
+                const int q = running + ex;
+                w.c_ab2[q] = w.c_ab[p];
+                ((T4*)w.c_geo2)[q] = ((const T4*)w.c_geo)[p];
+                if constexpr (DIM == 2) {
+                    ((T*)w.c_m2)[q] = ((const T*)w.c_m)[p];
+                    ((T2*)w.c_P2)[q] = ((const T2*)w.c_P)[p];
+                } else {
+                    ((T2*)w.c_m2)[q] = ((const T2*)w.c_m)[p];
+                    ((T4*)w.c_P2)[q] = ((const T4*)w.c_P)[p];
+                }
+                w.perm2[q] = w.perm[p];
+            } else {
+                const int c = w.perm[p];
+                if constexpr (DIM == 2) {
+                    const T2 P = ((const T2*)w.c_P)[p];
+                    w.Pk[pw * c] = (double)P.x;
+                    w.Pk[pw * c + 1] = (double)P.y;
+                } else {
+                    const T4 P = ((const T4*)w.c_P)[p];
+                    w.Pk[pw * c] = (double)P.x; w.Pk[pw * c + 1] = (double)P.y;
+                    w.Pk[pw * c + 2] = (double)P.z; w.Pk[pw * c + 3] = (double)P.w;
+                }
+            }
+        }
+        running += tile_tot;
+    }
+    if (!cd_grid_sync(ctrl, nb, epoch)) { ok = false; return nact; }
+    int tot = 0;
+    for (int q = 0; q < nb; ++q) tot += cd_ld_volatile_int(&w.cmp_blk[q]);
+    for (int q = blockIdx.x * blockDim.x + threadIdx.x; q < tot; q += gridDim.x * blockDim.x) {
+        w.c_ab[q] = w.c_ab2[q];
+        ((T4*)w.c_geo)[q] = ((const T4*)w.c_geo2)[q];
+        if constexpr (DIM == 2) {
+            ((T*)w.c_m)[q] = ((const T*)w.c_m2)[q];
+            ((T2*)w.c_P)[q] = ((const T2*)w.c_P2)[q];
+        } else {
+            ((T2*)w.c_m)[q] = ((const T2*)w.c_m2)[q];
+            ((T4*)w.c_P)[q] = ((const T4*)w.c_P2)[q];
+        }
+        w.perm[q] = w.perm2[q];
+    }
+    if (!cd_grid_sync(ctrl, nb, epoch)) { ok = false; return nact; }
+    for (int k = threadIdx.x; k <= K; k += blockDim.x) s_off[k] = cd_ld_volatile_int(&w.cmp_off[k]);
+    __syncthreads();
+    return tot;
 }
 
 template <int DIM, typename T>
@@ -826,8 +948,10 @@ k_sweep_batch(CdGeom g, CdWork w, int crit, double alpha, int max_sweeps)
     const int stride = gridDim.x * blockDim.x;
     unsigned long long epoch = 0;
     for (int k = threadIdx.x; k <= CD_KMAX; k += blockDim.x) s_off[k] = w.colour_off[k];
-    if (tid == 0) { w.act_cnt[0] = 0; w.act_cnt[1] = 0; w.act_cnt[2] = 0; }
+    if (tid == 0)
+        for (int q = 0; q < 6; ++q) w.act_cnt[q] = 0;
     __syncthreads();
+    int nact = nc;   // positions still in the colour-order arrays
 
     // starting impulses, colour by colour
     for (int k = 0; k < K; ++k) {
@@ -840,11 +964,11 @@ k_sweep_batch(CdGeom g, CdWork w, int crit, double alpha, int max_sweeps)
         }
         if (!cd_grid_sync(ctrl, nb, epoch)) return;
     }
-    pk_reduce(g, w, -1, crit, alpha, nullptr, s_red);
+    pk_reduce(g, w, -1, crit, alpha, nullptr, nullptr, s_red);
     if (!cd_grid_sync(ctrl, nb, epoch)) return;
 
     for (int sweep = 0; sweep < max_sweeps && nc > 0; ++sweep) {
-        if (tid == 0) w.act_cnt[(sweep + 1) % 3] = 0;
+        if (tid == 0) { w.act_cnt[(sweep + 1) % 3] = 0; w.act_cnt[3 + (sweep + 1) % 3] = 0; }
         for (int k = 0; k < K; ++k) {
             const CdSpan sp = cd_colour_span(s_off[k], s_off[k + 1]);
             for (int p = sp.p; p < sp.end; p += blockDim.x) {
@@ -859,15 +983,22 @@ k_sweep_batch(CdGeom g, CdWork w, int crit, double alpha, int max_sweeps)
             }
             if (!cd_grid_sync(ctrl, nb, epoch)) return;
         }
-        pk_reduce(g, w, sweep, crit, alpha, &w.act_cnt[sweep % 3], s_red);
+        pk_reduce(g, w, sweep, crit, alpha, &w.act_cnt[sweep % 3], &w.act_cnt[3 + sweep % 3], s_red);
         if (!cd_grid_sync(ctrl, nb, epoch)) return;
         if (cd_ld_volatile_int(&w.act_cnt[sweep % 3]) == 0) break;
+        // once a third of the positions belong to converged packings, drop them
+        const int live = cd_ld_volatile_int(&w.act_cnt[3 + sweep % 3]);
+        if (3 * (nact - live) >= nact && sweep + 1 < max_sweeps) {
+            bool ok = true;
+            nact = compact_batch<DIM, T>(g, w, nact, K, s_off, epoch, ok);
+            if (!ok) return;
+        }
     }
 
-    // impulses back to key order
+    // impulses back to key order (those of dropped contacts were written when dropped)
     typedef typename Vec<T>::V4 T4;
     typedef typename Vec<T>::V2 T2;
-    for (int p = tid; p < nc; p += stride) {
+    for (int p = tid; p < nact; p += stride) {
         int c = w.perm[p];
         if (DIM == 2) {
             T2 P = ((const T2*)w.c_P)[p];
