@@ -478,8 +478,9 @@ def adjoint_case(args, device, flush, wl, desc, every, adj_alpha, steps, complia
     wl.alpha = args.alpha
     T = steps
     width = float(wl.box_hi[0] - wl.box_lo[0])
+    # steps replayed from a captured CUDA graph (one step = ~25 launches)
     g = cd.CDSystem(wl, device=device, criterion=cd.CD_CONV_GLOBAL_REL, tape_steps=every,
-                    adjoint_compliance=compliance)
+                    adjoint_compliance=compliance, use_graph=1, stream=torch.cuda.Stream(device=device))
     stream = g.stream
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     flush.zero_()
@@ -505,7 +506,7 @@ def adjoint_case(args, device, flush, wl, desc, every, adj_alpha, steps, complia
     top = int(torch.argmax(y))
     losses = {"floor_pressure": (float(last["wall_force"][2]) / width, None, [0, 0, 1.0 / width, 0, 0, 0]),
               "packing_height": (float(y[top]), top, None)}
-    out = {"workload": desc, "steps": T, "adjoint_compliance": compliance,
+    out = {"workload": desc, "steps": T, "adjoint_compliance": compliance, "steps_from_cuda_graph": True,
            "forward_ms_per_step": fwd_ms / T, "forward_sweeps_per_step": fwd_sweeps / T,
            "contacts_last_step": int(last["n_contacts"]),
            "forward_contact_updates_per_s": fwd_upd / (fwd_ms / 1e3) if fwd_ms > 0 else 0.0, "losses": {}}

@@ -137,6 +137,12 @@ typedef struct {
                                unique and the Gauss-Seidel iteration can
                                drift, give the bounded derivative of slightly
                                compliant contacts.  Not in the paper. */
+    int64_t use_graph;      /* 1: cd_step captures the launches of one time
+                               step into a CUDA graph on first use and replays
+                               it for every step (fewer launch overheads for
+                               small systems); same results.  Needs a
+                               non-default stream and timing 0; the graph is
+                               dropped by cd_set_workspace. */
 } cd_params;
 
 typedef struct cd_system cd_system;

@@ -63,6 +63,7 @@ class cd_params(C.Structure):
         ("parallel_p", C.c_double),
         ("tape_steps", C.c_int64),
         ("adjoint_compliance", C.c_double),
+        ("use_graph", C.c_int64),
     ]
 
 
@@ -352,7 +353,7 @@ def cd_last_error(sysptr=None) -> str:
 
 def make_params(wl, precision=CD_FP64, criterion=CD_CONV_GLOBAL_REL, max_contacts=None, warm_start=1, rotations=1,
                 seed=None, max_sweeps=None, alpha=None, timing=0, tile_cells=0, dataflow=0,
-                parallel_p=0.0, tape_steps=0, adjoint_compliance=0.0) -> cd_params:
+                parallel_p=0.0, tape_steps=0, adjoint_compliance=0.0, use_graph=0) -> cd_params:
     p = cd_params()
     p.dim = wl.dim
     p.precision = precision
@@ -384,6 +385,7 @@ def make_params(wl, precision=CD_FP64, criterion=CD_CONV_GLOBAL_REL, max_contact
     p.parallel_p = float(parallel_p)
     p.tape_steps = int(tape_steps)
     p.adjoint_compliance = float(adjoint_compliance)
+    p.use_graph = int(use_graph)
     return p
 
 

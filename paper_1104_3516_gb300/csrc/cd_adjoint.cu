@@ -206,9 +206,10 @@ __device__ __forceinline__ void adj_geometry(const CdGeom& g, const CdWork& w, c
     w.adj_gx[ab.y] = gb;
 }
 
-__global__ void k_tape_record(CdWork w, CdTape t, int n)
+__global__ void k_tape_record(CdWork w, int n, int64_t cap)
 {
     const CdCtrl* ctrl = w.ctrl;
+    const CdTape t = cd_tape_slot(w.tape, n, cap, ctrl->tape_slot);
     const int nc = ctrl->nc;
     const int tid = blockIdx.x * blockDim.x + threadIdx.x;
     const int stride = gridDim.x * blockDim.x;
@@ -225,6 +226,16 @@ __global__ void k_tape_record(CdWork w, CdTape t, int n)
         t.P[c] = ((const double2*)w.c_P)[c];
     }
     for (int i = tid; i < n; i += stride) t.V[i] = ((const double4*)w.V)[i];
+}
+
+__global__ void k_tape_advance(CdCtrl* ctrl, int T)
+{
+    ctrl->tape_slot = (ctrl->tape_slot + 1) % T;
+}
+
+__global__ void k_set_tape_slot(CdCtrl* ctrl, int slot)
+{
+    ctrl->tape_slot = slot;
 }
 
 // The whole reverse step as one cooperative kernel: initial Gamma, the
@@ -379,43 +390,22 @@ k_adjoint(CdGeom g, CdWork w, CdTape t, CdAdjIO io, double alpha, int max_sweeps
     }
 }
 
-size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
-
 }  // namespace
 
-size_t cd_tape_slot_bytes(int64_t n, int64_t cap)
-{
-    const size_t c = (size_t)(cap > 0 ? cap : 1), m = (size_t)(n > 0 ? n : 1);
-    return align256(sizeof(CdTapeHdr)) + align256(c * sizeof(int2)) + align256(c * sizeof(double4)) +
-           align256(c * sizeof(double)) + align256(c * sizeof(double2)) + align256(m * sizeof(double4));
-}
-
-CdTape cd_tape_slot(char* tape, int64_t n, int64_t cap, int slot)
-{
-    const size_t c = (size_t)(cap > 0 ? cap : 1), m = (size_t)(n > 0 ? n : 1);
-    char* p = tape + (size_t)slot * cd_tape_slot_bytes(n, cap);
-    CdTape t;
-    t.hdr = (CdTapeHdr*)p;
-    p += align256(sizeof(CdTapeHdr));
-    t.ab = (int2*)p;
-    p += align256(c * sizeof(int2));
-    t.geo = (double4*)p;
-    p += align256(c * sizeof(double4));
-    t.mt = (double*)p;
-    p += align256(c * sizeof(double));
-    t.P = (double2*)p;
-    p += align256(c * sizeof(double2));
-    t.V = (double4*)p;
-    (void)m;
-    return t;
-}
-
-cudaError_t cd_launch_tape_record(const CdGeom& g, const CdWork& w, const CdTape& t, cudaStream_t s, int* nl)
+cudaError_t cd_launch_tape_record(const CdGeom& g, const CdWork& w, int64_t cap, int T, cudaStream_t s, int* nl)
 {
     int blocks = (g.n + CD_BLOCK - 1) / CD_BLOCK;
     if (blocks < 64) blocks = 64;
     if (blocks > 4096) blocks = 4096;
-    k_tape_record<<<blocks, CD_BLOCK, 0, s>>>(w, t, g.n);
+    k_tape_record<<<blocks, CD_BLOCK, 0, s>>>(w, g.n, cap);
+    k_tape_advance<<<1, 1, 0, s>>>(w.ctrl, T);
+    *nl += 2;
+    return cudaGetLastError();
+}
+
+cudaError_t cd_launch_set_tape_slot(const CdWork& w, int slot, cudaStream_t s, int* nl)
+{
+    k_set_tape_slot<<<1, 1, 0, s>>>(w.ctrl, slot);
     ++*nl;
     return cudaGetLastError();
 }

@@ -36,6 +36,8 @@ struct cd_system {
     std::vector<CdPack> pk_host;       // packing table (one entry for a plain system)
     std::vector<int> pack_of_host;     // packing of each particle (batched systems)
     std::vector<double> pk_wall0;      // initial wall planes, 6 per packing
+    cudaGraphExec_t step_graph;        // params.use_graph: one captured time step
+    int graph_launches;                // kernels in the captured step
     int tape_head;                     // next tape slot a step records into
     int tape_count;                    // recorded steps not yet consumed by cd_adjoint_step
     int adj_blocks;                    // cooperative grid of the adjoint kernel
@@ -490,6 +492,10 @@ static cd_status create_impl(const cd_params* params, int64_t npk, const int64_t
         delete s;
         return fail(nullptr, CD_ERR_INVALID_ARG, "too many tiles: raise tile_cells");
     }
+    if (p.use_graph && p.timing) {
+        delete s;
+        return fail(nullptr, CD_ERR_INVALID_ARG, "use_graph needs timing 0 (a replayed step records no phase events)");
+    }
     if (!(p.adjoint_compliance >= 0.0) || !std::isfinite(p.adjoint_compliance)) {
         delete s;
         return fail(nullptr, CD_ERR_INVALID_ARG, "adjoint_compliance must be >= 0");
@@ -595,6 +601,10 @@ extern "C" cd_status cd_set_workspace(cd_system* s, void* dev_ptr, size_t bytes)
     s->has_contacts = 0;
     s->tape_head = 0;
     s->tape_count = 0;
+    if (s->step_graph) {
+        cudaGraphExecDestroy(s->step_graph);
+        s->step_graph = nullptr;
+    }
     return CD_OK;
 }
 
@@ -650,6 +660,49 @@ extern "C" cd_status cd_solve_contacts(cd_system* s, cd_solve_stats* out)
     return h.converged ? CD_OK : CD_ERR_NOT_CONVERGED;
 }
 
+// The launches of one time step (Fig. 3): detection, colouring and order,
+// free flight, the solve, the Euler update and, with a tape, its record.
+static cd_status launch_step(cd_system* s, int timed)
+{
+    cd_status st;
+    if (timed && (st = mark(s)) != CD_OK) return st;
+    if ((st = launch_detect_chain(s, timed)) != CD_OK) return st;
+    if ((st = launch_solve(s, 1, timed)) != CD_OK) return st;
+    if (timed && (st = mark(s)) != CD_OK) return st;
+    CD_CUDA(s, cd_launch_unpack(s->g, s->w, s->pos, s->vel, s->omega, s->theta, 1, (int)s->p.precision, s->stream,
+                                &s->launches));
+    if (timed && (st = mark(s)) != CD_OK) return st;
+    if (s->p.tape_steps > 0)
+        CD_CUDA(s, cd_launch_tape_record(s->g, s->w, s->p.max_contacts, (int)s->p.tape_steps, s->stream,
+                                         &s->launches));
+    return CD_OK;
+}
+
+// Captures launch_step into a CUDA graph on the system's stream.
+static cd_status capture_step(cd_system* s)
+{
+    cudaError_t e = cudaStreamBeginCapture(s->stream, cudaStreamCaptureModeThreadLocal);
+    if (e != cudaSuccess) return cuda_fail(s, e, "cudaStreamBeginCapture (use_graph needs a non-default stream)");
+    const int l0 = s->launches;
+    cd_status st = launch_step(s, 0);
+    cudaGraph_t graph = nullptr;
+    e = cudaStreamEndCapture(s->stream, &graph);
+    if (st != CD_OK) {
+        if (graph) cudaGraphDestroy(graph);
+        return st;
+    }
+    if (e != cudaSuccess) return cuda_fail(s, e, "cudaStreamEndCapture");
+    s->graph_launches = s->launches - l0;
+    s->launches = l0;
+    e = cudaGraphInstantiate(&s->step_graph, graph, 0);
+    cudaGraphDestroy(graph);
+    if (e != cudaSuccess) {
+        s->step_graph = nullptr;
+        return cuda_fail(s, e, "cudaGraphInstantiate");
+    }
+    return CD_OK;
+}
+
 extern "C" cd_status cd_step(cd_system* s, int64_t n_steps, cd_step_stats* out)
 {
     cd_status st = need_ready(s);
@@ -658,19 +711,17 @@ extern "C" cd_status cd_step(cd_system* s, int64_t n_steps, cd_step_stats* out)
     s->launches = 0;
     k_begin_call<<<1, 1, 0, s->stream>>>(s->w.ctrl, 1);
     ++s->launches;
+    const bool graph = s->p.use_graph != 0;
+    if (graph && n_steps > 0 && !s->step_graph && (st = capture_step(s)) != CD_OK) return st;
     for (int64_t i = 0; i < n_steps; ++i) {
-        if ((st = mark(s)) != CD_OK) return st;
-        if ((st = launch_detect_chain(s, 1)) != CD_OK) return st;
-        if ((st = launch_solve(s, 1, 1)) != CD_OK) return st;
-        if ((st = mark(s)) != CD_OK) return st;
-        CD_CUDA(s, cd_launch_unpack(s->g, s->w, s->pos, s->vel, s->omega, s->theta, 1, (int)s->p.precision,
-                                    s->stream, &s->launches));
-        if ((st = mark(s)) != CD_OK) return st;
+        if (graph) {
+            CD_CUDA(s, cudaGraphLaunch(s->step_graph, s->stream));
+            s->launches += s->graph_launches;
+        } else if ((st = launch_step(s, 1)) != CD_OK) {
+            return st;
+        }
         if (s->p.tape_steps > 0) {
             const int T = (int)s->p.tape_steps;
-            CD_CUDA(s, cd_launch_tape_record(s->g, s->w, cd_tape_slot(s->w.tape, s->n, s->p.max_contacts,
-                                                                      s->tape_head),
-                                             s->stream, &s->launches));
             s->tape_head = (s->tape_head + 1) % T;
             if (s->tape_count < T) ++s->tape_count;
         }
@@ -857,6 +908,7 @@ extern "C" cd_status cd_adjoint_step(cd_system* s, const double* dL_dpos, const 
     if ((st = ctrl_status(s, h)) != CD_OK) return st;
     s->tape_head = slot;
     --s->tape_count;
+    CD_CUDA(s, cd_launch_set_tape_slot(s->w, slot, s->stream, &s->launches));
     if (out_host) {
         out_host->sweeps = h.adj_sweeps;
         out_host->converged = h.adj_converged;
@@ -936,6 +988,7 @@ static cd_status ckpt_copy(cd_system* s, void* buf, size_t bytes, bool save)
         s->has_contacts = 1;
         s->tape_head = 0;
         s->tape_count = 0;
+        if (s->p.tape_steps > 0) CD_CUDA(s, cd_launch_set_tape_slot(s->w, 0, s->stream, &s->launches));
     }
     return CD_OK;
 }
@@ -954,6 +1007,7 @@ extern "C" void cd_destroy_system(cd_system* s)
 {
     if (!s) return;
     for (cudaEvent_t e : s->events) cudaEventDestroy(e);
+    if (s->step_graph) cudaGraphExecDestroy(s->step_graph);
     delete s;
 }
 

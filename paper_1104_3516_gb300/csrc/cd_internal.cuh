@@ -53,6 +53,8 @@ struct CdCtrl {
     long long adj_nslide;
     long long adj_nbodies;          // particles touched by a non-open contact
     long long adj_diverged;
+    int tape_slot;                  // slot the next recorded step goes to
+    int tape_pad;
 };
 
 // Parameters of one packing of a batched system (a plain system is a batch of
@@ -173,8 +175,31 @@ struct CdTape {
     double2* P;         // converged (P_n, P_t)
     double4* V;         // n: velocities after the step (vx, vy, w, 0)
 };
-size_t cd_tape_slot_bytes(int64_t n, int64_t cap);
-CdTape cd_tape_slot(char* tape, int64_t n, int64_t cap, int slot);
+__host__ __device__ inline size_t cd_align256(size_t x) { return (x + 255) & ~(size_t)255; }
+__host__ __device__ inline size_t cd_tape_slot_bytes(int64_t n, int64_t cap)
+{
+    const size_t c = (size_t)(cap > 0 ? cap : 1), m = (size_t)(n > 0 ? n : 1);
+    return cd_align256(sizeof(CdTapeHdr)) + cd_align256(c * sizeof(int2)) + cd_align256(c * sizeof(double4)) +
+           cd_align256(c * sizeof(double)) + cd_align256(c * sizeof(double2)) + cd_align256(m * sizeof(double4));
+}
+__host__ __device__ inline CdTape cd_tape_slot(char* tape, int64_t n, int64_t cap, int slot)
+{
+    const size_t c = (size_t)(cap > 0 ? cap : 1);
+    char* p = tape + (size_t)slot * cd_tape_slot_bytes(n, cap);
+    CdTape t;
+    t.hdr = (CdTapeHdr*)p;
+    p += cd_align256(sizeof(CdTapeHdr));
+    t.ab = (int2*)p;
+    p += cd_align256(c * sizeof(int2));
+    t.geo = (double4*)p;
+    p += cd_align256(c * sizeof(double4));
+    t.mt = (double*)p;
+    p += cd_align256(c * sizeof(double));
+    t.P = (double2*)p;
+    p += cd_align256(c * sizeof(double2));
+    t.V = (double4*)p;
+    return t;
+}
 #define CD_OBS_MAX 65536
 
 
@@ -346,7 +371,11 @@ cudaError_t cd_launch_need(const CdGeom& g, const CdWork& w, cudaStream_t stream
 cudaError_t cd_launch_pk_ranges(const CdGeom& g, const CdWork& w, cudaStream_t stream, int* nl);
 cudaError_t cd_launch_orient(const CdGeom& g, const CdWork& w, int nbins, unsigned long long* counts,
                              cudaStream_t stream, int* nl);
-cudaError_t cd_launch_tape_record(const CdGeom& g, const CdWork& w, const CdTape& t, cudaStream_t stream, int* nl);
+// Records the step just taken into slot ctrl->tape_slot of the tape (T slots)
+// and advances the slot, all on the device (so a captured step graph can be
+// replayed).
+cudaError_t cd_launch_tape_record(const CdGeom& g, const CdWork& w, int64_t cap, int T, cudaStream_t stream, int* nl);
+cudaError_t cd_launch_set_tape_slot(const CdWork& w, int slot, cudaStream_t stream, int* nl);
 struct CdAdjIO {
     const double* dLx;      // n*2: dL/dx' of the step's output positions
     const double* dLv;      // n*2: dL/dv'
