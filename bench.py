@@ -86,6 +86,8 @@ def parse():
     ap.add_argument("--batched-steps", type=int, default=3,
                     help="timed steps of the 512-packing batched workload (0: skip)")
     ap.add_argument("--packings", type=int, default=512)
+    ap.add_argument("--no-autotune", action="store_true",
+                    help="skip the autotuner and use the default 512 x 1 sweep grid")
     ap.add_argument("--adjoint-steps", type=int, default=200,
                     help="steps of the differentiated settling rollout (0: skip the adjoint leg)")
     ap.add_argument("--cpu-sweeps", type=int, default=30,
@@ -295,8 +297,16 @@ def run_ours(args):
     wl = workload(args, rank)
     prec = cd.CD_FP64 if args.precision == "f64" else cd.CD_FP32
     stream = torch.cuda.current_stream(device)
+    shape, tuned = {}, None
+    if not args.no_autotune and args.tile_cells == 0 and args.dataflow == 0:
+        # block shape of the sweep grid chosen by timing short solves of this system (untimed)
+        from paper_1104_3516_gb300 import autotune
+        shape, table = autotune.tune(wl, precision=prec, device=device, max_contacts=4 * wl.n,
+                                     candidates=[dict(sweep_threads=t, sweep_blocks_per_sm=b)
+                                                 for t, b in autotune.BLOCK_SHAPES])
+        tuned = {"choice": shape, "ms_per_sweep": [[c, m] for c, m in table]}
     sysg = cd.CDSystem(wl, device=device, precision=prec, criterion=cd.CD_CONV_GLOBAL_REL, max_contacts=4 * wl.n,
-                       timing=1, stream=stream, tile_cells=args.tile_cells, dataflow=args.dataflow)
+                       timing=1, stream=stream, tile_cells=args.tile_cells, dataflow=args.dataflow, **shape)
     flush = torch.empty(512 << 20, dtype=torch.uint8, device=device)
 
     for _ in range(args.warmup):
@@ -391,7 +401,8 @@ def run_ours(args):
                                         "sweeps_per_step": sweeps / max(args.steps, 1),
                                         "steps_not_converged": not_conv, "parallelism": f"replicas x{ws}"}),
             "phase_ms_per_step": {k: v / max(args.steps, 1) for k, v in ph.items()},
-            "wall_s": wall_max, "roofline": roofline, "batched": batched, "adjoint": adjoint, "cpu_baseline": cpu,
+            "wall_s": wall_max, "roofline": roofline, "autotune": tuned, "batched": batched, "adjoint": adjoint,
+            "cpu_baseline": cpu,
             "e2e": e2e,
             "gpu_launches": launches, "clocks": clk}
     print(json.dumps(line), flush=True)
@@ -409,8 +420,16 @@ def run_batched(args, device, rank, flush):
         b.max_sweeps = args.max_sweeps
         b.alpha = args.alpha
     prec = cd.CD_FP64 if args.precision == "f64" else cd.CD_FP32
+    shape, tuned = {}, None
+    if not args.no_autotune:
+        from paper_1104_3516_gb300 import autotune
+        shape, table = autotune.tune(batch[0], batch=batch, precision=prec, device=device, steps=1,
+                                     max_contacts=6 * sum(b.n for b in batch),
+                                     candidates=[dict(sweep_threads=t, sweep_blocks_per_sm=b)
+                                                 for t, b in autotune.BLOCK_SHAPES])
+        tuned = {"choice": shape, "ms_per_sweep": [[c, m] for c, m in table]}
     g = cd.CDSystem(batch[0], device=device, batch=batch, precision=prec, criterion=cd.CD_CONV_GLOBAL_REL,
-                    timing=1, max_contacts=6 * sum(b.n for b in batch))
+                    timing=1, max_contacts=6 * sum(b.n for b in batch), **shape)
     flush.zero_()
     g.step(1)
     upd = sweeps = 0
@@ -430,7 +449,7 @@ def run_batched(args, device, rank, flush):
            "sweep_kernel_ms_per_step": sweep_ms / args.batched_steps,
            "steps_per_s": args.batched_steps / (ms / 1e3), "max_sweeps_in_step": int(sweeps),
            "sweeps_last_step": {"min": int(sw.min()), "median": float(np.median(sw)), "max": int(sw.max())},
-           "packings_converged_last_step": int(sum(p["converged"] for p in stats)),
+           "packings_converged_last_step": int(sum(p["converged"] for p in stats)), "autotune": tuned,
            "workload": "batched_settling_2d: disc counts log-uniform [200, 20000], mu ~ U[0.1, 0.6], "
                        "gravity-settled piles in periodic-x boxes at packing fraction 0.5"}
     if args.precision == "f64":

@@ -143,6 +143,15 @@ typedef struct {
                                small systems); same results.  Needs a
                                non-default stream and timing 0; the graph is
                                dropped by cd_set_workspace. */
+    int64_t sweep_threads;  /* block shape of the persistent sweep grid: threads
+                               per block, 128, 256 or 512 (0: 512) ... */
+    int64_t sweep_blocks_per_sm; /* ... and blocks per SM, 1, 2 or 4 (0: 1), at
+                               most 1024 threads per SM; the tiled and dataflow
+                               schedules need 512 x 1.  The colour classes are
+                               spread over all blocks; results do not depend on
+                               the shape except for the summation order of the
+                               residual.  Chosen by the autotuner of the
+                               Python package, or left at 512 x 1. */
 } cd_params;
 
 typedef struct cd_system cd_system;

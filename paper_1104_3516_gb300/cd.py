@@ -64,6 +64,8 @@ class cd_params(C.Structure):
         ("tape_steps", C.c_int64),
         ("adjoint_compliance", C.c_double),
         ("use_graph", C.c_int64),
+        ("sweep_threads", C.c_int64),
+        ("sweep_blocks_per_sm", C.c_int64),
     ]
 
 
@@ -353,7 +355,8 @@ def cd_last_error(sysptr=None) -> str:
 
 def make_params(wl, precision=CD_FP64, criterion=CD_CONV_GLOBAL_REL, max_contacts=None, warm_start=1, rotations=1,
                 seed=None, max_sweeps=None, alpha=None, timing=0, tile_cells=0, dataflow=0,
-                parallel_p=0.0, tape_steps=0, adjoint_compliance=0.0, use_graph=0) -> cd_params:
+                parallel_p=0.0, tape_steps=0, adjoint_compliance=0.0, use_graph=0, sweep_threads=0,
+                sweep_blocks_per_sm=0) -> cd_params:
     p = cd_params()
     p.dim = wl.dim
     p.precision = precision
@@ -386,6 +389,8 @@ def make_params(wl, precision=CD_FP64, criterion=CD_CONV_GLOBAL_REL, max_contact
     p.tape_steps = int(tape_steps)
     p.adjoint_compliance = float(adjoint_compliance)
     p.use_graph = int(use_graph)
+    p.sweep_threads = int(sweep_threads)
+    p.sweep_blocks_per_sm = int(sweep_blocks_per_sm)
     return p
 
 

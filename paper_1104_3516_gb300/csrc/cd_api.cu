@@ -26,6 +26,7 @@ struct cd_system {
     int num_sms;
     int pw;
     int sweep_blocks;
+    int sweep_threads;
     int colour_blocks;
     int has_contacts;
     size_t ws_bytes;
@@ -298,7 +299,8 @@ static cd_status launch_solve(cd_system* s, int free_flight, int timed)
     CD_CUDA(s, cd_launch_pack(s->g, s->w, s->vel, s->omega, s->radius, s->inv_m, s->inv_I, s->f_ext, free_flight,
                               (int)s->p.precision, s->stream, &s->launches));
     if (timed && (st = mark(s)) != CD_OK) return st;
-    CD_CUDA(s, cd_launch_sweep(s->g, s->w, s->sweep_blocks, (int)s->p.precision, (int)s->p.criterion, s->p.alpha,
+    CD_CUDA(s, cd_launch_sweep(s->g, s->w, s->sweep_blocks, s->sweep_threads, (int)s->p.precision,
+                               (int)s->p.criterion, s->p.alpha,
                                (int)s->p.max_sweeps, s->pw, s->stream, &s->launches));
     return CD_OK;
 }
@@ -519,6 +521,27 @@ static cd_status create_impl(const cd_params* params, int64_t npk, const int64_t
     if (s->sweep_blocks <= 0 || s->colour_blocks <= 0) {
         delete s;
         return fail(nullptr, CD_ERR_CUDA, "cooperative kernels do not fit on this device");
+    }
+    {
+        // block shape of the persistent sweep grid (params.sweep_threads / sweep_blocks_per_sm)
+        const int th = p.sweep_threads ? (int)p.sweep_threads : CD_SWEEP_THREADS;
+        const int per = p.sweep_blocks_per_sm ? (int)p.sweep_blocks_per_sm : 1;
+        if ((th != 128 && th != 256 && th != 512) || (per != 1 && per != 2 && per != 4) || th * per > 1024) {
+            delete s;
+            return fail(nullptr, CD_ERR_INVALID_ARG,
+                        "sweep_threads must be 128, 256 or 512 and sweep_blocks_per_sm 1, 2 or 4 (at most 1024 "
+                        "threads per SM)");
+        }
+        if ((th != CD_SWEEP_THREADS || per != 1) && (g.tile_cells >= 2 || g.dataflow)) {
+            delete s;
+            return fail(nullptr, CD_ERR_INVALID_ARG, "the tiled and dataflow schedules use 512 x 1 blocks per SM");
+        }
+        if (!cd_sweep_fits(g, (int)p.precision, th, per)) {
+            delete s;
+            return fail(nullptr, CD_ERR_INVALID_ARG, "that many sweep blocks do not fit on one SM");
+        }
+        s->sweep_threads = th;
+        s->sweep_blocks = s->num_sms * per;
     }
     *out = s;
     return CD_OK;

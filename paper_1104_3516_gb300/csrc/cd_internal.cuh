@@ -392,8 +392,9 @@ cudaError_t cd_launch_adjoint(const CdGeom& g, const CdWork& w, const CdTape& t,
 int cd_adjoint_blocks_per_sm();
 cudaError_t cd_launch_stress(const CdGeom& g, const CdWork& w, const double* pos, const double* radius, int axis,
                              double lo, double width, int ns, double* sig, cudaStream_t stream, int* nl);
-cudaError_t cd_launch_sweep(const CdGeom& g, const CdWork& w, int coop_blocks, int precision, int criterion,
-                            double alpha, int max_sweeps, int pw, cudaStream_t stream, int* nl);
+cudaError_t cd_launch_sweep(const CdGeom& g, const CdWork& w, int coop_blocks, int threads, int precision,
+                            int criterion, double alpha, int max_sweeps, int pw, cudaStream_t stream, int* nl);
+int cd_sweep_fits(const CdGeom& g, int precision, int threads, int per_sm);
 cudaError_t cd_launch_unpack(const CdGeom& g, const CdWork& w, double* pos, double* vel, double* omega,
                              double* theta, int integrate, int precision, cudaStream_t stream, int* nl);
 cudaError_t cd_launch_static(const CdGeom& g, const CdWork& w, const double* radius, const double* inv_m,

@@ -1593,8 +1593,21 @@ int cd_sweep_max_blocks(int precision, int dim, int num_sms)
     return per_sm * num_sms;
 }
 
-cudaError_t cd_launch_sweep(const CdGeom& g, const CdWork& w, int coop_blocks, int precision, int criterion,
-                            double alpha, int max_sweeps, int pw, cudaStream_t s, int* nl)
+// 1 if `per_sm` blocks of `threads` threads of the sweep kernel the system
+// uses can be resident on one SM.
+int cd_sweep_fits(const CdGeom& g, int precision, int threads, int per_sm)
+{
+    const int kind = (g.npk > 1) ? 3 : ((g.tile_cells >= 2) ? 1 : (g.dataflow ? 2 : (g.par_p > 0.0 ? 4 : 0)));
+    int b = 0;
+    const size_t dyn = (kind == 1) ? tile_smem(g.dim, precision) : 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, sweep_fn(g.dim, precision, kind), threads, dyn) !=
+        cudaSuccess)
+        return 0;
+    return b >= per_sm ? 1 : 0;
+}
+
+cudaError_t cd_launch_sweep(const CdGeom& g, const CdWork& w, int coop_blocks, int threads, int precision,
+                            int criterion, double alpha, int max_sweeps, int pw, cudaStream_t s, int* nl)
 {
     (void)pw;
     cudaError_t e = cudaMemsetAsync(w.ctrl, 0, 2 * sizeof(unsigned long long), s);
@@ -1607,6 +1620,6 @@ cudaError_t cd_launch_sweep(const CdGeom& g, const CdWork& w, int coop_blocks, i
     void* args[] = {&ga, &wa, &crit, &al, &ms};
     const int kind = (g.npk > 1) ? 3 : ((g.tile_cells >= 2) ? 1 : (g.dataflow ? 2 : (g.par_p > 0.0 ? 4 : 0)));
     ++*nl;
-    return cudaLaunchCooperativeKernel(sweep_fn(g.dim, precision, kind), dim3(coop_blocks), dim3(CD_SWEEP_THREADS),
+    return cudaLaunchCooperativeKernel(sweep_fn(g.dim, precision, kind), dim3(coop_blocks), dim3(threads),
                                        args, kind == 1 ? tile_smem(g.dim, precision) : 0, s);
 }
