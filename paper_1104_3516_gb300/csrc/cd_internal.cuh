@@ -295,16 +295,29 @@ __device__ __forceinline__ int cd_ld_volatile_int(const int* p)
     return *(volatile const int*)p;
 }
 
-__device__ __forceinline__ bool cd_grid_sync(CdCtrl* ctrl, unsigned long long nblocks, unsigned long long& epoch)
+// Split form: cd_grid_arrive publishes the block's writes and adds its
+// arrival (thread 0 gets the counter's old value); the block may then issue
+// work that touches nothing another block reads before the barrier (loads of
+// read-only records) while the others arrive; cd_grid_wait completes it.
+__device__ __forceinline__ unsigned cd_grid_arrive(CdCtrl* ctrl, unsigned long long nblocks)
 {
-    __shared__ int s_ok;
     __syncthreads();
+    unsigned old = 0;
     if (threadIdx.x == 0) {
         unsigned* word = reinterpret_cast<unsigned*>(&ctrl->bar_count);
         const unsigned add = (blockIdx.x == 0) ? (0x80000000u - (unsigned)(nblocks - 1)) : 1u;
-        int ok = 1;
         __threadfence();
-        const unsigned old = atomicAdd(word, add);
+        old = atomicAdd(word, add);
+    }
+    return old;
+}
+
+__device__ __forceinline__ bool cd_grid_wait(CdCtrl* ctrl, unsigned old, unsigned long long& epoch)
+{
+    __shared__ int s_ok;
+    if (threadIdx.x == 0) {
+        const unsigned* word = reinterpret_cast<const unsigned*>(&ctrl->bar_count);
+        int ok = 1;
         unsigned long long t0 = 0;
         unsigned spins = 0;
         while (((cd_ld_acquire_u32(word) ^ old) & 0x80000000u) == 0u) {
@@ -324,6 +337,12 @@ __device__ __forceinline__ bool cd_grid_sync(CdCtrl* ctrl, unsigned long long nb
     }
     __syncthreads();
     return s_ok != 0;
+}
+
+__device__ __forceinline__ bool cd_grid_sync(CdCtrl* ctrl, unsigned long long nblocks, unsigned long long& epoch)
+{
+    const unsigned old = cd_grid_arrive(ctrl, nblocks);
+    return cd_grid_wait(ctrl, old, epoch);
 }
 
 // ---------------------------------------------------------------------------

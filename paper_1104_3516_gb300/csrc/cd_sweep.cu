@@ -453,6 +453,15 @@ __device__ __forceinline__ UpdOut apply_rec(const CdGeom& g, const CdWork& w, in
     else return apply3d<T>(g, w, pos, r, apply_only, crit, alpha, ravg_prev);
 }
 
+// Loads this thread's first record of colour k (if it has one) into nxt.
+template <int DIM, typename T>
+__device__ __forceinline__ void prefetch_first(const CdGeom& g, const CdWork& w, const int* s_off, int k,
+                                               Rec<DIM, T>& nxt)
+{
+    const CdSpan sq = cd_colour_span(s_off[k], s_off[k + 1]);
+    if (sq.p < sq.end) load_rec<DIM, T>(g, w, sq.p, nxt);
+}
+
 // One colour phase for this thread: its first contact's record was loaded
 // into `nxt` before the barrier (if it has one); the rest are loaded inline.
 // Afterwards `nxt` holds the first record of colour `knext` (prefetch).
@@ -480,10 +489,7 @@ __device__ __forceinline__ void colour_phase(const CdGeom& g, const CdWork& w, c
             if (crit == CD_CONV_LOCAL) { acc[1] += (double)o.rel_ok; acc[2] += (double)o.bad; }
         }
     }
-    if (knext >= 0) {
-        const CdSpan sq = cd_colour_span(s_off[knext], s_off[knext + 1]);
-        if (sq.p < sq.end) load_rec<DIM, T>(g, w, sq.p, nxt);
-    }
+    if (knext >= 0) prefetch_first<DIM, T>(g, w, s_off, knext, nxt);
     (void)tid; (void)stride;
 }
 
@@ -699,8 +705,9 @@ k_sweep(CdGeom g, CdWork w, int crit, double alpha, int max_sweeps)
                 if (s0.p < s0.end) load_rec<DIM, T>(g, w, s0.p, nxt);
             }
             for (int k = 0; k < K; ++k) {
-                colour_phase<DIM, T, MIXED>(g, w, s_off, k, (k + 1 < K) ? k + 1 : 0, tid, stride, nxt, false, crit, alpha,
-                                     ravg_prev, a3);
+                // no prefetch inside the phase: it is issued after the barrier arrival
+                // below, so that the arriving thread's fence does not wait for it
+                colour_phase<DIM, T, MIXED>(g, w, s_off, k, -1, tid, stride, nxt, false, crit, alpha, ravg_prev, a3);
                 if (mixed && k == K - 1) {
                     if (!cd_grid_sync(ctrl, nb, epoch)) return;
                     par_apply<DIM, T>(g, w, tid, stride);
@@ -713,7 +720,9 @@ k_sweep(CdGeom g, CdWork w, int crit, double alpha, int max_sweeps)
                         part[2 * nb + blockIdx.x] = a3[2];
                     }
                 }
-                if (!cd_grid_sync(ctrl, nb, epoch)) return;
+                const unsigned old = cd_grid_arrive(ctrl, nb);
+                if (!mixed || k + 1 < K) prefetch_first<DIM, T>(g, w, s_off, (k + 1 < K) ? k + 1 : 0, nxt);
+                if (!cd_grid_wait(ctrl, old, epoch)) return;
             }
             ++sweeps;
             ravg = grid_total(part, nb, &s_bc) / (double)nc;
