@@ -331,7 +331,8 @@ __device__ __forceinline__ bool cd_grid_wait(CdCtrl* ctrl, unsigned old, unsigne
                 if (cd_ld_volatile_int(&ctrl->error) != CDE_NONE) { ok = 0; break; }
             }
         }
-        __threadfence();
+        // the acquire load that saw the flip orders thread 0's later accesses;
+        // the block barrier below extends that to the other threads
         s_ok = ok;
         ++epoch;
     }
