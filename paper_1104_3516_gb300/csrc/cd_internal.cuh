@@ -306,8 +306,9 @@ __device__ __forceinline__ unsigned cd_grid_arrive(CdCtrl* ctrl, unsigned long l
     if (threadIdx.x == 0) {
         unsigned* word = reinterpret_cast<unsigned*>(&ctrl->bar_count);
         const unsigned add = (blockIdx.x == 0) ? (0x80000000u - (unsigned)(nblocks - 1)) : 1u;
-        __threadfence();
-        old = atomicAdd(word, add);
+        // release: the block's writes (ordered before this thread by the block
+        // barrier above) are visible to whoever acquires the flipped word
+        asm volatile("atom.add.release.gpu.global.u32 %0, [%1], %2;" : "=r"(old) : "l"(word), "r"(add) : "memory");
     }
     return old;
 }

@@ -281,6 +281,13 @@ __device__ __forceinline__ double clamp_sym(double x, double lim)
 }
 __device__ __forceinline__ float clamp_sym(float x, float lim) { return x < -lim ? -lim : (x > lim ? lim : x); }
 
+// |P| from |P|^2 for the residual only: s * rsqrt(s) (within a few ulp; the
+// correctly rounded square root costs more FP64 instructions).
+__device__ __forceinline__ double norm_of_sq(double s)
+{
+    return s > 0.0 ? s * rsqrt(s) : 0.0;
+}
+
 // 2D: P_n = max(0, P_n,old - m_n (b + u_n)); P_t = clamp(P_t,old - m_t u_t, +-mu P_n).
 // The core works on the two bodies' velocity records wherever they live
 // (global memory or a tile's shared-memory table).
@@ -314,7 +321,7 @@ __device__ __forceinline__ UpdOut core2d(const CdGeom& g, const Rec<2, T>& r, ty
     double pn = (double)Pn, pt = (double)Pt;
     // FP32 impulses carry 1e-7 anyway: their magnitude is taken in FP32 (the sum stays FP64)
     if constexpr (sizeof(T) == 4) o.pabs = (double)sqrtf(Pn * Pn + Pt * Pt);
-    else o.pabs = sqrt(pn * pn + pt * pt);
+    else o.pabs = norm_of_sq(pn * pn + pt * pt);
     o.rel_ok = 0; o.bad = 0;
     if (!apply_only && crit == CD_CONV_LOCAL) {
         double d0 = (double)dPn, d1 = (double)dPt;
@@ -404,7 +411,7 @@ __device__ __forceinline__ UpdOut core3d(const CdGeom& g, const Rec<3, T>& r, ty
     UpdOut o;
     double pn = (double)Pn, px = (double)Ptx, py = (double)Pty, pz = (double)Ptz;
     if constexpr (sizeof(T) == 4) o.pabs = (double)sqrtf(Pn * Pn + Ptx * Ptx + Pty * Pty + Ptz * Ptz);
-    else o.pabs = sqrt(pn * pn + px * px + py * py + pz * pz);
+    else o.pabs = norm_of_sq(pn * pn + px * px + py * py + pz * pz);
     o.rel_ok = 0; o.bad = 0;
     if (!apply_only && crit == CD_CONV_LOCAL) {
         double d0 = (double)dPn, d1 = (double)dtx, d2_ = (double)dty, d3 = (double)dtz;
