@@ -244,15 +244,16 @@ def barrier(ws):
 # CPU oracle timing (reference arm and the cpu_baseline leg)
 # ---------------------------------------------------------------------------
 
-def oracle_steps(wl, steps, sweep_cap):
+def oracle_steps(wl, steps, sweep_cap, colour_order=False):
     """Times `steps` oracle time steps (random sequential order, the paper's
-    scheme) of the workload with the sweep cap lowered to `sweep_cap`;
-    returns (contact updates, seconds, sweeps, contacts)."""
+    scheme, or with colour_order the GPU's colour order) of the workload with
+    the sweep cap lowered to `sweep_cap`; returns (contact updates, seconds,
+    sweeps, contacts)."""
     import oracle as O
     p = O.make_params(dim=wl.dim, dt=wl.dt, mu=wl.mu, gravity=wl.gravity, box_lo=wl.box_lo, box_hi=wl.box_hi,
                       periodic=wl.periodic, wall_mask=wl.wall_mask, wall_vel=np.asarray(wl.wall_vel).reshape(18),
                       delta=wl.delta, alpha=wl.alpha, criterion=O.CRIT_GLOBAL_REL, max_sweeps=sweep_cap,
-                      order=O.ORDER_RANDOM, seed=wl.seed)
+                      order=O.ORDER_COLOUR if colour_order else O.ORDER_RANDOM, seed=wl.seed)
     s = O.OracleSystem(p, wl.x, wl.v, wl.w, wl.r, wl.inv_m, wl.inv_I, np.asarray(wl.wall_pos, dtype=np.float64),
                        cap=6 * wl.n)
     upd, sweeps = 0, 0
@@ -386,7 +387,9 @@ def run_ours(args):
     cpu = None
     if rank == 0 and not args.no_cpu_baseline:
         o_upd, o_sec, o_sweeps, o_nc = oracle_steps(wl, 1, args.cpu_sweeps)
+        c_upd, c_sec, _, _ = oracle_steps(wl, 1, args.cpu_sweeps, colour_order=True)
         cpu = {"value": o_upd / o_sec, "unit": UNIT, "cores": 1, "kind": "oracle",
+               "colour_order_value": c_upd / c_sec,
                "sample": f"1 oracle time step of the same {wl.n}-particle packing, random sequential order, sweep cap "
                          f"{args.cpu_sweeps} ({o_sweeps} sweeps over {o_nc} contacts, {o_sec:.1f} s)",
                "cpu": platform.processor() or platform.machine()}

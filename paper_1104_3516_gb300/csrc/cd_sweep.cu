@@ -393,7 +393,7 @@ __device__ __forceinline__ UpdOut core3d(const CdGeom& g, const Rec<3, T>& r, ty
         T lim = r.mu * Pn;
         T q2 = Ptx * Ptx + Pty * Pty + Ptz * Ptz;
         if (q2 > lim * lim) {
-            T sc = lim / sqrt(q2);
+            T sc = lim * rsqrt(q2);   // onto the cone (q2 > lim^2 >= 0)
             Ptx *= sc; Pty *= sc; Ptz *= sc;
         }
         dPn = Pn - r.P.x; dtx = Ptx - r.P.y; dty = Pty - r.P.z; dtz = Ptz - r.P.w;
