@@ -185,10 +185,12 @@ typedef struct {
 /* Creates a system over caller-owned device arrays (layouts above).
  * inv_mass / inv_inertia: 1/m and 1/I per particle (0 for an immovable
  * particle).  f_ext: n*dim explicit external forces, or NULL.  cuda_stream:
- * a cudaStream_t (NULL = legacy default stream).  Validates the parameters
- * and the radii on the device (one synchronisation) and returns
- * CD_ERR_INVALID_ARG for a non-positive or NaN radius or a box/cell grid the
- * periodic wrap cannot handle.  The system needs a workspace before use. */
+ * a cudaStream_t (NULL = legacy default stream).  Validates the parameters,
+ * and the radii, inverse masses, positions and velocities (copied to the host
+ * once), and returns CD_ERR_INVALID_ARG for a non-positive or NaN radius, a
+ * negative or NaN inverse mass, a non-finite position or velocity, or a
+ * box/cell grid the periodic wrap cannot handle.  The system needs a
+ * workspace before use. */
 cd_status cd_create_system(const cd_params* params, int64_t n, double* pos, double* vel, double* omega,
                            double* theta, const double* radius, const double* inv_mass,
                            const double* inv_inertia, const double* f_ext, void* cuda_stream,
@@ -402,6 +404,17 @@ cd_status cd_adjoint_step(cd_system* sys, const double* dL_dpos, const double* d
 cd_status cd_checkpoint_size(const cd_system* sys, size_t* bytes);
 cd_status cd_save_checkpoint(cd_system* sys, void* dev_buf, size_t bytes);
 cd_status cd_load_checkpoint(cd_system* sys, const void* dev_buf, size_t bytes);
+
+/* Self-check of the bounded device-side waits (no counterpart in the paper):
+ * launches the library's grid barrier as a cooperative grid (one small block
+ * per SM) in which one block never arrives.  The others must give up after
+ * the bound (2 s), flag the timeout and return, leaving the context usable.
+ * dev_scratch: caller-owned device memory of at least 1024 bytes, 256-byte
+ * aligned.  Returns
+ * CD_OK when the withheld barrier ended by its bound with the timeout
+ * flagged (*elapsed_ms_host: the kernel's duration), CD_ERR_STATE if the
+ * barrier completed or no timeout was flagged.  Synchronises the stream. */
+cd_status cd_selfcheck_wait_bound(void* dev_scratch, size_t bytes, void* cuda_stream, double* elapsed_ms_host);
 
 /* Releases the host-side system object (not the caller's arrays or
  * workspace).  Safe on NULL. */

@@ -175,6 +175,7 @@ SIGNATURES = [
     ("cd_checkpoint_size", C.c_int, [_P, C.POINTER(C.c_size_t)]),
     ("cd_save_checkpoint", C.c_int, [_P, _P, C.c_size_t]),
     ("cd_load_checkpoint", C.c_int, [_P, _P, C.c_size_t]),
+    ("cd_selfcheck_wait_bound", C.c_int, [_P, C.c_size_t, _P, C.POINTER(C.c_double)]),
     ("cd_destroy_system", None, [_P]),
     ("cd_last_error", C.c_char_p, [_P]),
 ]
@@ -340,6 +341,15 @@ def cd_save_checkpoint(sysptr, buf: torch.Tensor):
 
 def cd_load_checkpoint(sysptr, buf: torch.Tensor):
     _check(sysptr, lib().cd_load_checkpoint(sysptr, buf.data_ptr(), buf.numel() * buf.element_size()))
+
+
+def cd_selfcheck_wait_bound(buf: torch.Tensor, stream) -> float:
+    """Runs the bounded-wait self-check on `stream`; returns the kernel's
+    duration in ms (raises CDError if the bound did not fire)."""
+    ms = C.c_double()
+    _check(None, lib().cd_selfcheck_wait_bound(buf.data_ptr(), buf.numel() * buf.element_size(), stream,
+                                               C.byref(ms)))
+    return float(ms.value)
 
 
 def cd_destroy_system(sysptr):

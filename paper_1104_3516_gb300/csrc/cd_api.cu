@@ -375,11 +375,19 @@ static cd_status create_impl(const cd_params* params, int64_t npk, const int64_t
     if (e != cudaSuccess) { cuda_fail(nullptr, e, "device query"); delete s; return CD_ERR_CUDA; }
     if (!coop) { delete s; return fail(nullptr, CD_ERR_CUDA, "device lacks cooperative launch"); }
 
-    // radii and inverse masses: validated on the host once
-    std::vector<double> hr((size_t)n), hm((size_t)n);
+    // radii, inverse masses, positions and velocities: validated on the host once
+    std::vector<double> hr((size_t)n), hm((size_t)n), hx((size_t)(n * p.dim)), hv((size_t)(n * p.dim));
     e = cudaMemcpy(hr.data(), radius, sizeof(double) * (size_t)n, cudaMemcpyDeviceToHost);
     if (e == cudaSuccess) e = cudaMemcpy(hm.data(), inv_mass, sizeof(double) * (size_t)n, cudaMemcpyDeviceToHost);
-    if (e != cudaSuccess) { cuda_fail(nullptr, e, "reading radius/inv_mass"); delete s; return CD_ERR_CUDA; }
+    if (e == cudaSuccess) e = cudaMemcpy(hx.data(), pos, sizeof(double) * hx.size(), cudaMemcpyDeviceToHost);
+    if (e == cudaSuccess) e = cudaMemcpy(hv.data(), vel, sizeof(double) * hv.size(), cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) { cuda_fail(nullptr, e, "reading the particle state"); delete s; return CD_ERR_CUDA; }
+    for (size_t i = 0; i < hx.size(); ++i) {
+        if (!std::isfinite(hx[i]) || !std::isfinite(hv[i])) {
+            delete s;
+            return fail(nullptr, CD_ERR_INVALID_ARG, "positions and velocities must be finite");
+        }
+    }
     double rmax = 0.0;
     for (int64_t i = 0; i < n; ++i) {
         if (!(hr[(size_t)i] > 0.0) || !std::isfinite(hr[(size_t)i])) {
@@ -1024,6 +1032,53 @@ extern "C" cd_status cd_save_checkpoint(cd_system* s, void* dev_buf, size_t byte
 extern "C" cd_status cd_load_checkpoint(cd_system* s, const void* dev_buf, size_t bytes)
 {
     return ckpt_copy(s, const_cast<void*>(dev_buf), bytes, false);
+}
+
+// ---------------------------------------------------------------------------
+// Self-check of the bounded waits
+// ---------------------------------------------------------------------------
+__global__ void k_barrier_withheld(CdCtrl* ctrl, int withheld)
+{
+    if ((int)blockIdx.x == withheld) return;   // this block never arrives
+    unsigned long long epoch = 0;
+    cd_grid_sync(ctrl, gridDim.x, epoch);
+}
+
+extern "C" cd_status cd_selfcheck_wait_bound(void* dev_scratch, size_t bytes, void* cuda_stream,
+                                             double* elapsed_ms_host)
+{
+    static_assert(sizeof(CdCtrl) <= 1024, "control block larger than the self-check scratch");
+    if (!dev_scratch || bytes < 1024) return fail(nullptr, CD_ERR_INVALID_ARG, "dev_scratch must hold at least 1024 bytes");
+    if (((uintptr_t)dev_scratch & 255) != 0) return fail(nullptr, CD_ERR_INVALID_ARG, "dev_scratch must be 256-byte aligned");
+    cudaStream_t st = (cudaStream_t)cuda_stream;
+    int dev = 0, sms = 0, coop = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev);
+    if (e != cudaSuccess) return cuda_fail(nullptr, e, "device query");
+    if (!coop) return fail(nullptr, CD_ERR_CUDA, "device lacks cooperative launch");
+    CdCtrl* ctrl = (CdCtrl*)dev_scratch;
+    if ((e = cudaMemsetAsync(ctrl, 0, sizeof(CdCtrl), st)) != cudaSuccess) return cuda_fail(nullptr, e, "memset");
+    cudaEvent_t e0, e1;
+    if ((e = cudaEventCreate(&e0)) != cudaSuccess) return cuda_fail(nullptr, e, "cudaEventCreate");
+    if ((e = cudaEventCreate(&e1)) != cudaSuccess) { cudaEventDestroy(e0); return cuda_fail(nullptr, e, "cudaEventCreate"); }
+    int withheld = sms - 1;
+    void* args[] = {&ctrl, &withheld};
+    cudaEventRecord(e0, st);
+    e = cudaLaunchCooperativeKernel((const void*)k_barrier_withheld, dim3(sms), dim3(32), args, 0, st);
+    cudaEventRecord(e1, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    float ms = 0.0f;
+    if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (e != cudaSuccess) return cuda_fail(nullptr, e, "withheld barrier");
+    int err = 0;
+    if ((e = cudaMemcpy(&err, &ctrl->error, sizeof(int), cudaMemcpyDeviceToHost)) != cudaSuccess)
+        return cuda_fail(nullptr, e, "reading the flag");
+    if (elapsed_ms_host) *elapsed_ms_host = (double)ms;
+    if (err != CDE_TIMEOUT) return fail(nullptr, CD_ERR_STATE, "the withheld barrier did not report a timeout");
+    return CD_OK;
 }
 
 extern "C" void cd_destroy_system(cd_system* s)

@@ -438,3 +438,21 @@ def test_gpu_column_stress_closed_form():
         expect[k] = (n - k) * m * cases.G * 2 * r / (Lx * 2 * r)
     # positions moved by one Euler step of a static column: contacts keep their stripes
     assert np.allclose(g.stress_profile(1, 0.0, 2 * r, n + 1), expect, rtol=1e-9, atol=0)
+
+
+# --- failure detection (bounded waits) --------------------------------------------
+
+def test_withheld_barrier_times_out_and_the_context_stays_usable():
+    """One block of a cooperative grid never reaches the barrier: the others
+    give up after the 2 s bound, flag the timeout and return; the same
+    process then steps a system as usual."""
+    import torch
+    from paper_1104_3516_gb300 import cd
+    buf = torch.empty(1024 + 256, dtype=torch.uint8, device="cuda:0")
+    stream = torch.cuda.current_stream()
+    ms = cd.cd_selfcheck_wait_bound(buf[(-buf.data_ptr()) % 256:][:1024], stream.cuda_stream)
+    assert 1500.0 <= ms <= 10000.0
+    wl = cases.resting_disc()
+    g = gpu_system(wl, criterion=cd.CD_CONV_NONE, max_sweeps=1)
+    g.step(1)
+    assert g.contacts()["impulse"][0, 0] > 0.0
