@@ -456,3 +456,30 @@ def test_withheld_barrier_times_out_and_the_context_stays_usable():
     g = gpu_system(wl, criterion=cd.CD_CONV_NONE, max_sweeps=1)
     g.step(1)
     assert g.contacts()["impulse"][0, 0] > 0.0
+
+
+def test_particle_with_more_candidates_than_supported_is_a_capacity_error():
+    """A disc of radius 20 ringed by 80 small discs has 80 contact candidates,
+    more than the 64 one particle may emit: the step is refused with
+    CD_ERR_CAPACITY before anything is written, and the state is kept."""
+    from paper_1104_3516_gb300 import cd
+    ang = np.arange(80) * (2.0 * math.pi / 80)
+    x = np.concatenate([[[0.0, 0.0]], np.stack([20.55 * np.cos(ang), 20.55 * np.sin(ang)], axis=1)])
+    r = np.concatenate([[20.0], np.full(80, 0.5)])
+    wl = cases._wl("crowded", 2, x, r, dt=cases.DT, mu=0.3, gravity=(0.0, 0.0, 0.0), box_lo=(-30.0, -30.0, 0.0),
+                   box_hi=(30.0, 30.0, 1.0))
+    g = gpu_system(wl)
+    x0 = g.pos.clone()
+    with pytest.raises(cd.CDError) as e:
+        g.step(1)
+    assert e.value.status == cd.CD_ERR_CAPACITY and "64" in str(e.value)
+    assert bool((g.pos == x0).all())
+
+
+def test_empty_system_is_rejected():
+    from paper_1104_3516_gb300 import cd
+    p = cd.make_params(cases.resting_disc())
+    t = __import__("torch").zeros(1, dtype=__import__("torch").float64, device="cuda:0")
+    with pytest.raises(cd.CDError) as e:
+        cd.cd_create_system(p, 0, t, t, t, None, t, t, t, None, None)
+    assert e.value.status == cd.CD_ERR_INVALID_ARG
