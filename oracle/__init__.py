@@ -60,6 +60,8 @@ class Params(C.Structure):
         ("parallel_p", C.c_double),
         ("rotations", C.c_int64),
         ("tile_cells", C.c_int64),
+        ("wall_push", C.c_double * 6),
+        ("wall_mass", C.c_double * 6),
     ]
 
 
@@ -116,7 +118,7 @@ def lib():
             _lib.ora_contact_geometry.argtypes = [P(Params), i64, P(d), P(d), P(d), P(d), P(d), i64, P(i32),
                                                   P(d), P(d), P(d), P(d)]
             _lib.ora_colour_greedy.restype = C.c_int
-            _lib.ora_colour_greedy.argtypes = [i64, i64, P(i32), C.c_uint64, P(i32)]
+            _lib.ora_colour_greedy.argtypes = [i64, i64, P(i32), C.c_uint64, C.c_int64, P(i32)]
             _lib.ora_solve.restype = C.c_int
             _lib.ora_solve.argtypes = [P(Params), i64, P(d), P(d), P(d), P(d), P(d), i64, P(i32), P(d), P(d),
                                        P(d), P(d), P(i32), P(C.c_int64), P(i32), i64, P(d), P(d), P(SolveStats)]
@@ -142,7 +144,7 @@ def _f64(a):
 def make_params(dim=2, dt=1e-3, mu=0.3, gravity=(0.0, -1.0, 0.0), box_lo=(0, 0, 0), box_hi=(1, 1, 1),
                 periodic=(0, 0, 0), wall_mask=0, wall_vel=None, delta=0.24, alpha=1e-6,
                 criterion=CRIT_GLOBAL_REL, max_sweeps=1000, order=ORDER_COLOUR, warm_start=1, seed=0,
-                parallel_p=0.0, rotations=1, tile_cells=0) -> Params:
+                parallel_p=0.0, rotations=1, tile_cells=0, wall_push=None, wall_mass=None) -> Params:
     p = Params()
     p.dim = dim
     p.dt = dt
@@ -166,6 +168,11 @@ def make_params(dim=2, dt=1e-3, mu=0.3, gravity=(0.0, -1.0, 0.0), box_lo=(0, 0, 
     p.parallel_p = parallel_p
     p.rotations = int(rotations)
     p.tile_cells = int(tile_cells)
+    wp = np.zeros(6) if wall_push is None else np.asarray(wall_push, dtype=np.float64).reshape(6)
+    wm = np.zeros(6) if wall_mass is None else np.asarray(wall_mass, dtype=np.float64).reshape(6)
+    for k in range(6):
+        p.wall_push[k] = float(wp[k])
+        p.wall_mass[k] = float(wm[k])
     return p
 
 
@@ -213,13 +220,15 @@ def contact_geometry(p: Params, x, r, inv_m, inv_I, wall_pos, pairs):
     return normal[:nc], gap[:nc], mn[:nc], mt[:nc]
 
 
-def colour_greedy(n, pairs, seed):
-    """Greedy colouring in descending splitmix64 priority; returns (colour, K)."""
+def colour_greedy(n, pairs, seed, dyn_walls=0):
+    """Greedy colouring in descending priority (largest degree first, then the
+    splitmix64 hash); dyn_walls: bit k for a force-controlled wall k, whose
+    contacts conflict.  Returns (colour, K)."""
     pairs = np.ascontiguousarray(pairs, dtype=np.int32)
     nc = pairs.shape[0]
     colour = np.zeros(max(nc, 1), dtype=np.int32)
     K = lib().ora_colour_greedy(n, nc, _ptr(pairs, C.c_int32), C.c_uint64(int(seed) & (2**64 - 1)),
-                                _ptr(colour, C.c_int32))
+                                int(dyn_walls), _ptr(colour, C.c_int32))
     return colour[:nc], int(K)
 
 

@@ -71,7 +71,23 @@ typedef struct {
     double parallel_p;      /* fraction of contacts updated in parallel */
     int64_t rotations;      /* 0: rotational degrees of freedom frozen */
     int64_t tile_cells;     /* >= 2: tiled colour order (see ora_tile_colour) */
+    double wall_push[6];    /* external force pushing wall k along its inward normal */
+    double wall_mass[6];    /* > 0: wall k is a rigid body of this mass moving along
+                               its normal (force-controlled); 0: kinematic */
 } ora_params;
+
+/* A force-controlled wall: present, with a positive mass. */
+static int wall_dynamic(const ora_params* p, int k)
+{
+    return (int)((p->wall_mask >> k) & 1) && (k / 2) < (int)p->dim && p->wall_mass[k] > 0.0;
+}
+
+static int64_t dyn_wall_mask(const ora_params* p)
+{
+    int64_t m = 0;
+    for (int k = 0; k < 6; ++k) if (wall_dynamic(p, k)) m |= (int64_t)1 << k;
+    return m;
+}
 
 typedef struct {
     int64_t sweeps;
@@ -298,9 +314,12 @@ void ora_contact_geometry(const ora_params* p, long long n, const double* x, con
             int axis = k / 2;
             nv[axis] = (k & 1) ? 1.0 : -1.0;   /* from the particle into the wall */
             g = wall_gap(p, x, r, wall_pos, a, k);
+            /* a force-controlled wall moves along its normal only: it adds
+             * its inverse mass to the normal row, nothing to the tangential */
+            if (wall_dynamic(p, k)) wb_m = 1.0 / p->wall_mass[k];
         }
         double w_n = wa_m + wb_m;
-        double w_t = (w_n + ra * ra * wa_I) + rb * rb * wb_I;
+        double w_t = (((b < n) ? w_n : wa_m) + ra * ra * wa_I) + rb * rb * wb_I;
         for (int k = 0; k < 3; ++k) normal[c * 3 + k] = nv[k];
         gap[c] = g;
         mn[c] = (w_n > 0.0) ? 1.0 / w_n : 0.0;
@@ -328,33 +347,39 @@ static int cmp_prio(const void* u, const void* v)
 }
 
 static int colour_greedy_in(long long n, long long nc, const int32_t* pairs, uint64_t seed,
-                            const int64_t* tile, int32_t* colour);
+                            const int64_t* tile, int64_t dyn_walls, int32_t* colour);
 
-int ora_colour_greedy(long long n, long long nc, const int32_t* pairs, uint64_t seed, int32_t* colour)
+/* dyn_walls: bit k set when wall k is a force-controlled body, whose
+ * contacts then conflict with each other like those of a particle. */
+int ora_colour_greedy(long long n, long long nc, const int32_t* pairs, uint64_t seed, int64_t dyn_walls,
+                      int32_t* colour)
 {
-    return colour_greedy_in(n, nc, pairs, seed, NULL, colour);
+    return colour_greedy_in(n, nc, pairs, seed, NULL, dyn_walls, colour);
 }
 
 /* Greedy colouring as above; with `tile` non-NULL two contacts conflict only
  * when they share a particle and lie in the same tile. */
 static int colour_greedy_in(long long n, long long nc, const int32_t* pairs, uint64_t seed,
-                            const int64_t* tile, int32_t* colour)
+                            const int64_t* tile, int64_t dyn_walls, int32_t* colour)
 {
     if (nc == 0) return 0;
-    long long* deg = (long long*)calloc((size_t)n + 1, sizeof(long long));
+    /* bodies that create conflicts: the particles and the force-controlled walls n + k */
+    const long long nb = n + 6;
+#define CONFLICTS(q) ((q) < n || ((dyn_walls >> ((q) - n)) & 1))
+    long long* deg = (long long*)calloc((size_t)nb + 1, sizeof(long long));
     for (long long c = 0; c < nc; ++c) {
         for (int s = 0; s < 2; ++s) {
             long long q = pairs[2 * c + s];
-            if (q < n) deg[q + 1]++;
+            if (CONFLICTS(q)) deg[q + 1]++;
         }
     }
-    for (long long i = 0; i < n; ++i) deg[i + 1] += deg[i];
-    long long* fill = (long long*)calloc((size_t)n + 1, sizeof(long long));
-    long long* adj = (long long*)malloc(sizeof(long long) * (size_t)(deg[n] > 0 ? deg[n] : 1));
+    for (long long i = 0; i < nb; ++i) deg[i + 1] += deg[i];
+    long long* fill = (long long*)calloc((size_t)nb + 1, sizeof(long long));
+    long long* adj = (long long*)malloc(sizeof(long long) * (size_t)(deg[nb] > 0 ? deg[nb] : 1));
     for (long long c = 0; c < nc; ++c) {
         for (int s = 0; s < 2; ++s) {
             long long q = pairs[2 * c + s];
-            if (q < n) adj[deg[q] + fill[q]++] = c;
+            if (CONFLICTS(q)) adj[deg[q] + fill[q]++] = c;
         }
     }
     prio_item* it = (prio_item*)malloc(sizeof(prio_item) * (size_t)nc);
@@ -365,7 +390,7 @@ static int colour_greedy_in(long long n, long long nc, const int32_t* pairs, uin
         uint64_t ds = 0;
         for (int s = 0; s < 2; ++s) {
             long long q = pairs[2 * c + s];
-            if (q < n) ds += (uint64_t)(deg[q + 1] - deg[q]);
+            if (CONFLICTS(q)) ds += (uint64_t)(deg[q + 1] - deg[q]);
         }
         if (ds > 255) ds = 255;
         it[c].prio = (ds << 56) | (ora_splitmix64(seed ^ k) >> 8);
@@ -382,7 +407,7 @@ static int colour_greedy_in(long long n, long long nc, const int32_t* pairs, uin
         memset(used, 0, (size_t)cap);
         for (int s = 0; s < 2; ++s) {
             long long q = pairs[2 * c + s];
-            if (q >= n) continue;
+            if (!CONFLICTS(q)) continue;
             for (long long e = deg[q]; e < deg[q + 1]; ++e) {
                 long long d = adj[e];
                 if (d == c || colour[d] < 0) continue;
@@ -408,6 +433,7 @@ static int colour_greedy_in(long long n, long long nc, const int32_t* pairs, uin
     }
     free(used); free(it); free(adj); free(fill); free(deg);
     return kmax;
+#undef CONFLICTS
 }
 
 /* ------------------------------------------------------------------------ */
@@ -458,7 +484,7 @@ int ora_tile_colour(const ora_params* p, long long n, const double* x, const dou
         tile[c] = t;
         group[c] = tc * ntiles + t;
     }
-    int K = colour_greedy_in(n, nc, pairs, p->seed, tile, colour);
+    int K = colour_greedy_in(n, nc, pairs, p->seed, tile, dyn_wall_mask(p), colour);
     free(tile);
     return K;
 }
@@ -479,7 +505,8 @@ typedef struct {
     const double* gap;
     const double* mn;
     const double* mt;
-    const double* wall_vel;
+    double* wall_vel;       /* 18: wall velocities (force-controlled ones change) */
+    double wall_im[6];      /* inverse mass of a force-controlled wall, else 0 */
 } solve_ctx;
 
 static int pw_of(int D) { return D == 2 ? 2 : 4; }
@@ -500,7 +527,7 @@ static void body(const solve_ctx* s, long long q, double vq[3], double wq[3], do
     } else {
         int k = (int)(q - s->n);
         for (int j = 0; j < D; ++j) vq[j] = s->wall_vel[k * 3 + j];
-        *rq = 0.0; *im = 0.0; *iI = 0.0;
+        *rq = 0.0; *im = s->wall_im[k]; *iI = 0.0;
     }
 }
 
@@ -536,8 +563,13 @@ static void apply_impulse(solve_ctx* s, long long c, const double dP[3])
     const double* n = s->normal + c * 3;
     for (int side = 0; side < 2; ++side) {
         long long q = s->pairs[2 * c + side];
-        if (q >= s->n) continue;
         double sign = side ? 1.0 : -1.0;
+        if (q >= s->n) {
+            /* a force-controlled wall takes the impulse along its normal */
+            int k = (int)(q - s->n);
+            if (s->wall_im[k] > 0.0) s->wall_vel[k * 3 + k / 2] += sign * s->wall_im[k] * dP[k / 2];
+            continue;
+        }
         double im = s->inv_m[q];
         double iI = s->p->rotations ? s->inv_I[q] : 0.0;
         double rq = s->r[q];
@@ -582,7 +614,8 @@ static void solve_one(solve_ctx* s, long long c, double* Pc, double* dP_out)
     body(s, s->pairs[2 * c], va_, wa_, &ra, &ima, &iIa);
     body(s, s->pairs[2 * c + 1], vb_, wb_, &rb, &imb, &iIb);
     double wn = ima + imb;
-    double wt = (wn + ra * ra * iIa) + rb * rb * iIb;
+    /* a wall moves along its normal only: no share in the tangential row */
+    double wt = (((s->pairs[2 * c + 1] < s->n) ? wn : ima) + ra * ra * iIa) + rb * rb * iIb;
     double vg[3];
     contact_velocity(s, c, vg);
     double Pnew[4] = {0.0, 0.0, 0.0, 0.0};
@@ -693,7 +726,7 @@ static int cmp_group_colour(const void* u, const void* v)
  *   ravg_hist  if non-NULL, R_avg after sweep j is stored at [j]
  *              ([0] = starting impulses); room for max_sweeps + 1.
  * Returns 0. */
-int ora_solve(const ora_params* p, long long n, double* v, double* w,
+int ora_solve(ora_params* p, long long n, double* v, double* w,
               const double* r, const double* inv_m, const double* inv_I,
               long long nc, const int32_t* pairs, const double* normal, const double* gap,
               const double* mn, const double* mt, const int32_t* colour, const int64_t* group,
@@ -704,7 +737,10 @@ int ora_solve(const ora_params* p, long long n, double* v, double* w,
     solve_ctx s;
     s.p = p; s.n = n; s.v = v; s.w = w; s.r = r; s.inv_m = inv_m; s.inv_I = inv_I;
     s.pairs = pairs; s.normal = normal; s.gap = gap; s.mn = mn; s.mt = mt;
-    s.wall_vel = p->wall_vel;
+    double wall_vel[18];
+    for (int k = 0; k < 18; ++k) wall_vel[k] = p->wall_vel[k];
+    s.wall_vel = wall_vel;
+    for (int k = 0; k < 6; ++k) s.wall_im[k] = wall_dynamic(p, k) ? 1.0 / p->wall_mass[k] : 0.0;
     memset(st, 0, sizeof(*st));
 
     /* apply the starting impulses (key order) */
@@ -818,6 +854,7 @@ int ora_solve(const ora_params* p, long long n, double* v, double* w,
         long long b = pairs[2 * c + 1];
         if (b >= n) st->wall_force[b - n] += P[c * pw] / p->dt;
     }
+    for (int k = 0; k < 18; ++k) p->wall_vel[k] = wall_vel[k];   /* force-controlled walls moved */
     free(dPpar); free(Pprev); free(par); free(order);
     return 0;
 }
@@ -846,7 +883,7 @@ static long long find_key(long long nc, const int32_t* pairs, uint64_t k)
  *   normal_out, gap_out (may be NULL): this step's geometry, cap*3 and cap.
  * Returns 0, or -1 if the contacts exceed `cap` (then *nc_io holds the number
  * needed and nothing is changed). */
-int ora_step(const ora_params* p, long long n, double* x, double* v, double* w, double* theta,
+int ora_step(ora_params* p, long long n, double* x, double* v, double* w, double* theta,
              const double* r, const double* inv_m, const double* inv_I, const double* f_ext,
              double* wall_pos, long long cap, long long* nc_io, int32_t* pairs_io, double* P_io,
              long long step_index, int use_cells, int32_t* colour_out,
@@ -896,6 +933,13 @@ int ora_step(const ora_params* p, long long n, double* x, double* v, double* w, 
             v[i * D + k] = v[i * D + k] + a * p->dt;
         }
     }
+    /* a force-controlled wall: its push along the inward normal, explicitly (Eq. 1) */
+    for (int k = 0; k < ORA_MAX_WALLS; ++k) {
+        if (!wall_dynamic(p, k)) continue;
+        double a = p->wall_push[k] / p->wall_mass[k];
+        if (k & 1) a = -a;
+        p->wall_vel[k * 3 + k / 2] = p->wall_vel[k * 3 + k / 2] + a * p->dt;
+    }
 
     ora_params q = *p;
     int64_t* group = NULL;
@@ -903,13 +947,14 @@ int ora_step(const ora_params* p, long long n, double* x, double* v, double* w, 
         group = (int64_t*)malloc(sizeof(int64_t) * ncz);
         ora_tile_colour(p, n, x, r, nc, pairs, colour, group);
     } else if (p->order == ORA_ORDER_COLOUR) {
-        int K = ora_colour_greedy(n, nc, pairs, p->seed, colour);
+        int K = ora_colour_greedy(n, nc, pairs, p->seed, dyn_wall_mask(p), colour);
         (void)K;
     } else {
         for (long long c = 0; c < nc; ++c) colour[c] = 0;
     }
     ora_solve(&q, n, v, w, r, inv_m, inv_I, nc, pairs, normal, gap, mn, mt, colour, group, NULL,
               step_index, P, NULL, st);
+    for (int k = 0; k < 18; ++k) p->wall_vel[k] = q.wall_vel[k];
     free(group);
 
     /* Eq. 2: positions with the new velocities; orientation likewise */

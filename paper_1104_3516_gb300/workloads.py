@@ -97,6 +97,8 @@ class Workload:
     wall_mask: int = 0
     wall_pos: np.ndarray = dataclasses.field(default_factory=lambda: np.zeros(6))
     wall_vel: np.ndarray = dataclasses.field(default_factory=lambda: np.zeros((6, 3)))
+    wall_push: np.ndarray = dataclasses.field(default_factory=lambda: np.zeros(6))   # force-controlled walls
+    wall_mass: np.ndarray = dataclasses.field(default_factory=lambda: np.zeros(6))   # (mass 0: kinematic)
     delta: float = 0.24
     alpha: float = 1e-6
     max_sweeps: int = 1000

@@ -113,3 +113,20 @@ def leaning_column(offsets=(0.2, -0.6, 0.3, -0.25, 0.65), radius=1.0, mu=0.3, ro
     inv_I = None if rotations else np.zeros(n)
     return _wl("leaning_column", 2, x, np.full(n, radius), inv_I=inv_I, dt=DT, mu=mu, gravity=(0.0, -G, 0.0),
                box_lo=(-10.0, 0.0, 0.0), box_hi=(10.0, 2.0 * radius * n + 5.0, 1.0), wall_mask=0b0100)
+
+
+def pressed_column(n=5, radius=1.0, push=2.0, lid_mass=50.0, mu=0.3, lid_gap=0.0):
+    """n equal discs stacked on a fixed floor under a force-controlled lid
+    (wall 3, mass lid_mass, pushed down with force `push`), no gravity; the
+    lid starts at rest lid_gap above the top disc."""
+    y = radius + 2.0 * radius * np.arange(n)
+    x = np.stack([np.zeros(n), y], axis=1)
+    top = float(y[-1] + radius) + lid_gap
+    wl = _wl("pressed_column", 2, x, np.full(n, radius), dt=DT, mu=mu, gravity=(0.0, 0.0, 0.0),
+             box_lo=(-5.0, 0.0, 0.0), box_hi=(5.0, top + 5.0, 1.0), wall_mask=0b1100)
+    wp = np.zeros(6)
+    wp[3] = top
+    wl.wall_pos = wp
+    wl.wall_push = np.array([0.0, 0.0, 0.0, push, 0.0, 0.0])
+    wl.wall_mass = np.array([0.0, 0.0, 0.0, lid_mass, 0.0, 0.0])
+    return wl

@@ -326,3 +326,47 @@ def test_column_observables_closed_form():
     for k in range(1, n):       # contact between disc k-1 and k (from the bottom) lies at y = 2 k r
         expect[k] = (n - k) * m * G * 2 * r / (Lx * 2 * r)
     assert np.allclose(sig, expect, rtol=1e-9, atol=0)
+
+
+# --- force-controlled walls (the pressure walls of Fig. 10) ------------------------
+
+def test_pressed_column_carries_the_push():
+    """A lid of mass M pushed with force F onto a column resting on a fixed
+    floor, no gravity: the lid's momentum F dt (Eq. 1) is stopped by the
+    rigid column in the step, so every contact carries F dt, the floor and
+    the lid both see the force F, and nothing moves."""
+    F = 2.0
+    wl = cases.pressed_column(n=5, push=F, lid_mass=50.0)
+    s = system(wl, order=O.ORDER_RANDOM, alpha=1e-14, max_sweeps=20000)
+    for _ in range(3):
+        st = s.step()
+        assert st["converged"]
+        assert np.allclose(s.impulses[:, 0], F * DT, rtol=1e-9, atol=0)
+        assert np.allclose(s.impulses[:, 1], 0.0, atol=1e-15)
+        assert st["wall_force"][2] == pytest.approx(F, rel=1e-9)
+        assert st["wall_force"][3] == pytest.approx(F, rel=1e-9)
+        assert abs(s.p.wall_vel[3 * 3 + 1]) <= 1e-12
+        assert np.abs(s.v).max() <= 1e-12
+    assert s.wall_pos[3] == pytest.approx(wl.wall_pos[3], abs=1e-14)
+
+
+def test_free_lid_accelerates_with_its_push():
+    """With no contact the lid follows Eq. 1-2 alone: after k steps it has
+    moved down by (F/M) dt^2 k (k + 1) / 2."""
+    F, M = 3.0, 7.0
+    wl = cases.pressed_column(n=2, push=F, lid_mass=M, lid_gap=2.0)
+    s = system(wl, order=O.ORDER_RANDOM)
+    k = 6
+    for _ in range(k):
+        s.step()
+    assert s.wall_pos[3] == pytest.approx(wl.wall_pos[3] - (F / M) * DT * DT * k * (k + 1) / 2, rel=0, abs=1e-13)
+
+
+def test_contacts_on_a_force_controlled_wall_conflict():
+    """On a kinematic wall contacts never conflict; on a force-controlled
+    wall (a body) they must all get different colours."""
+    n = 6
+    pairs = np.array([[i, n + 2] for i in range(n)], dtype=np.int32)
+    c0, K0 = O.colour_greedy(n, pairs, seed=5)
+    c1, K1 = O.colour_greedy(n, pairs, seed=5, dyn_walls=1 << 2)
+    assert K0 == 1 and K1 == n and len(set(c1.tolist())) == n
