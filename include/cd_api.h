@@ -152,6 +152,18 @@ typedef struct {
                                the shape except for the summation order of the
                                residual.  Chosen by the autotuner of the
                                Python package, or left at 512 x 1. */
+    double wall_push[6];    /* force-controlled walls (the pressure walls of the
+                               Fig. 10 setup): wall k with wall_mass[k] > 0 is a
+                               rigid body of that mass moving along its normal
+                               only, pushed along its inward normal by the force
+                               wall_push[k] (applied explicitly, Eq. 1) and
+                               taking part in the impulse solve like a particle:
+                               its inverse mass enters the normal row of its
+                               contacts, and its contacts conflict in the
+                               colouring.  wall_vel holds its velocity, which
+                               the steps update.  Plain systems with the global
+                               colour order, no mixed update, no tape. */
+    double wall_mass[6];    /* 0: wall k kinematic (prescribed velocity) */
 } cd_params;
 
 typedef struct cd_system cd_system;

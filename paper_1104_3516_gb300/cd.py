@@ -66,6 +66,8 @@ class cd_params(C.Structure):
         ("use_graph", C.c_int64),
         ("sweep_threads", C.c_int64),
         ("sweep_blocks_per_sm", C.c_int64),
+        ("wall_push", C.c_double * 6),
+        ("wall_mass", C.c_double * 6),
     ]
 
 
@@ -401,6 +403,11 @@ def make_params(wl, precision=CD_FP64, criterion=CD_CONV_GLOBAL_REL, max_contact
     p.use_graph = int(use_graph)
     p.sweep_threads = int(sweep_threads)
     p.sweep_blocks_per_sm = int(sweep_blocks_per_sm)
+    push = np.asarray(getattr(wl, "wall_push", np.zeros(6)), dtype=np.float64).reshape(6)
+    mass = np.asarray(getattr(wl, "wall_mass", np.zeros(6)), dtype=np.float64).reshape(6)
+    for k in range(6):
+        p.wall_push[k] = float(push[k])
+        p.wall_mass[k] = float(mass[k])
     return p
 
 

@@ -100,13 +100,14 @@ static size_t layout(cd_system* s, char* base, CdWork* w)
     const size_t nchunk = (cap + CD_CHUNK - 1) / CD_CHUNK;
     const size_t G = (size_t)(s->sweep_blocks > s->colour_blocks ? s->sweep_blocks : s->colour_blocks) + 1;
     size_t scan_max = ncell + 1;
-    if (n + 1 > scan_max) scan_max = n + 1;
+    if (n + 7 > scan_max) scan_max = n + 7;
     if (CD_KMAX * nchunk > scan_max) scan_max = CD_KMAX * nchunk;
     if ((size_t)s->g.ntiles * CD_KLOCAL + 1 > scan_max) scan_max = (size_t)s->g.ntiles * CD_KLOCAL + 1;
     CdWork t;
     t.ctrl = L.take<CdCtrl>(base, 1);
-    t.V = L.take<char>(base, n * vrec);
-    t.S = L.take<char>(base, n * 4 * real);
+    // records n .. n + 5 belong to force-controlled walls
+    t.V = L.take<char>(base, (n + 6) * vrec);
+    t.S = L.take<char>(base, (n + 6) * 4 * real);
     t.cell_of = L.take<int>(base, n);
     t.cell_cnt = L.take<int>(base, ncell + 1);
     t.cell_start = L.take<int>(base, ncell + 1);
@@ -124,9 +125,9 @@ static size_t layout(cd_system* s, char* base, CdWork* w)
     t.mn = L.take<double>(base, cap);
     t.mt = L.take<double>(base, cap);
     t.colour = L.take<int>(base, cap);
-    t.p2c_cnt = L.take<int>(base, n + 1);
-    t.p2c_off = L.take<int>(base, n + 1);
-    t.p2c_fill = L.take<int>(base, n);
+    t.p2c_cnt = L.take<int>(base, n + 7);
+    t.p2c_off = L.take<int>(base, n + 7);
+    t.p2c_fill = L.take<int>(base, n + 6);
     t.p2c = L.take<int>(base, 2 * cap);
     t.prio = L.take<unsigned long long>(base, cap);
     t.round_cnt = L.take<int>(base, 4);
@@ -501,6 +502,35 @@ static cd_status create_impl(const cd_params* params, int64_t npk, const int64_t
     if (g.tile_cells >= 2 && (double)g.ntiles * CD_KLOCAL > 1.0e8) {
         delete s;
         return fail(nullptr, CD_ERR_INVALID_ARG, "too many tiles: raise tile_cells");
+    }
+    {
+        // force-controlled walls
+        int dyn = 0;
+        for (int k = 0; k < 6; ++k) {
+            if (!std::isfinite(p.wall_push[k]) || !(p.wall_mass[k] >= 0.0) || !std::isfinite(p.wall_mass[k])) {
+                delete s;
+                return fail(nullptr, CD_ERR_INVALID_ARG, "wall_push must be finite and wall_mass >= 0");
+            }
+            if (p.wall_mass[k] > 0.0) {
+                if (!((p.wall_mask >> k) & 1) || (k >> 1) >= p.dim) {
+                    delete s;
+                    return fail(nullptr, CD_ERR_INVALID_ARG, "a force-controlled wall must be present");
+                }
+                dyn |= 1 << k;
+                g.wall_im[k] = 1.0 / p.wall_mass[k];
+                g.wall_push[k] = p.wall_push[k];
+            }
+        }
+        for (int64_t b = 1; b < npk; ++b)
+            for (int k = 0; k < 6; ++k)
+                if (params[b].wall_mass[k] > 0.0) dyn |= 1 << 8;
+        if (dyn && (npk > 1 || g.tile_cells != 0 || g.dataflow || p.parallel_p > 0.0 || p.tape_steps > 0)) {
+            delete s;
+            return fail(nullptr, CD_ERR_INVALID_ARG,
+                        "force-controlled walls need a plain system with the global colour order, no mixed "
+                        "update and no tape");
+        }
+        g.dyn_walls = dyn;
     }
     if (p.use_graph && p.timing) {
         delete s;
@@ -961,7 +991,7 @@ extern "C" cd_status cd_adjoint_step(cd_system* s, const double* dL_dpos, const 
 // any), wall planes (6 per packing), contact count, contact keys and
 // impulses of the current set (the warm start of the next step).
 struct CkptLayout {
-    size_t pos, vel, omega, theta, walls, nc, pairs, P, total;
+    size_t pos, vel, omega, theta, walls, pk, nc, pairs, P, total;
 };
 
 static CkptLayout ckpt_layout(const cd_system* s)
@@ -976,6 +1006,7 @@ static CkptLayout ckpt_layout(const cd_system* s)
     L.omega = o; o += al(n * rot * 8);
     L.theta = o; o += s->theta ? al(n * 8) : 0;
     L.walls = o; o += al((size_t)s->g.npk * 6 * 8);
+    L.pk = o; o += al((size_t)s->g.npk * sizeof(CdPack));   // wall velocities of force-controlled walls
     L.nc = o; o += 256;
     L.pairs = o; o += al(cap * sizeof(int2));
     L.P = o; o += al(cap * (size_t)s->pw * 8);
@@ -1006,6 +1037,7 @@ static cd_status ckpt_copy(cd_system* s, void* buf, size_t bytes, bool save)
         {s->omega, L.omega, n * rot * 8},
         {s->theta, L.theta, s->theta ? n * 8 : 0},
         {s->w.pk_wall_pos, L.walls, (size_t)s->g.npk * 6 * 8},
+        {s->w.pk, L.pk, (size_t)s->g.npk * sizeof(CdPack)},
         {&s->w.ctrl->nc, L.nc, sizeof(int)},
         {s->w.pairs, L.pairs, cap * sizeof(int2)},
         {s->w.Pk, L.P, cap * (size_t)s->pw * 8},

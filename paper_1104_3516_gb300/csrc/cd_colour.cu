@@ -29,7 +29,7 @@ __global__ void k_p2c_count(CdGeom g, CdWork w)
     for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < nc; c += gridDim.x * blockDim.x) {
         int2 ab = w.pairs[c];
         atomicAdd(&w.p2c_cnt[ab.x], 1);
-        if (ab.y < g.n) atomicAdd(&w.p2c_cnt[ab.y], 1);
+        if (cd_is_body(g, ab.y)) atomicAdd(&w.p2c_cnt[ab.y], 1);
     }
 }
 
@@ -42,7 +42,7 @@ __global__ void k_p2c_fill(CdGeom g, CdWork w)
         int2 ab = w.pairs[c];
         int s = atomicAdd(&w.p2c_fill[ab.x], 1);
         w.p2c[w.p2c_off[ab.x] + s] = c;
-        if (ab.y < g.n) {
+        if (cd_is_body(g, ab.y)) {
             s = atomicAdd(&w.p2c_fill[ab.y], 1);
             w.p2c[w.p2c_off[ab.y] + s] = c;
         }
@@ -55,7 +55,8 @@ __global__ void k_p2c_fill(CdGeom g, CdWork w)
 __global__ void k_p2c_sort(CdGeom g, CdWork w)
 {
     if (w.ctrl->skip) return;
-    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < g.n; i += gridDim.x * blockDim.x) {
+    const int nbody = g.n + (g.dyn_walls ? 6 : 0);
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < nbody; i += gridDim.x * blockDim.x) {
         int b = w.p2c_off[i], e = w.p2c_off[i + 1];
         for (int k = b + 1; k < e; ++k) {
             int v = w.p2c[k];
@@ -94,7 +95,7 @@ __global__ void __launch_bounds__(CD_SWEEP_THREADS) k_jp(CdGeom g, CdWork w, uns
         }
         // largest degree first (contacts of both ends, capped at 255), then the hash
         unsigned long long ds = (unsigned long long)(w.p2c_off[ab.x + 1] - w.p2c_off[ab.x]);
-        if (ab.y < g.n) ds += (unsigned long long)(w.p2c_off[ab.y + 1] - w.p2c_off[ab.y]);
+        if (cd_is_body(g, ab.y)) ds += (unsigned long long)(w.p2c_off[ab.y + 1] - w.p2c_off[ab.y]);
         if (ds > 255ULL) ds = 255ULL;
         prio[c] = (ds << 56) | (h >> 8);
         w.colour[c] = -1;
@@ -116,7 +117,7 @@ __global__ void __launch_bounds__(CD_SWEEP_THREADS) k_jp(CdGeom g, CdWork w, uns
             bool ready = true;
             for (int side = 0; side < 2 && ready; ++side) {
                 int q = side ? ab.y : ab.x;
-                if (q >= g.n) continue;
+                if (!cd_is_body(g, q)) continue;
                 int e = w.p2c_off[q + 1];
                 for (int s = w.p2c_off[q]; s < e; ++s) {
                     int d = w.p2c[s];
@@ -424,13 +425,14 @@ cudaError_t cd_launch_colour(const CdGeom& g, const CdWork& w, int coop_blocks, 
     if (gc < 1) gc = 1;
     if (gc > 4096) gc = 4096;
     const bool tiled = g.tile_cells >= 2;
-    if ((e = cudaMemsetAsync(w.p2c_cnt, 0, sizeof(int) * (size_t)(g.n + 1), s)) != cudaSuccess) return e;
-    if ((e = cudaMemsetAsync(w.p2c_fill, 0, sizeof(int) * (size_t)g.n, s)) != cudaSuccess) return e;
+    const int nbody = g.n + (g.dyn_walls ? 6 : 0);   // particles, then force-controlled walls n + k
+    if ((e = cudaMemsetAsync(w.p2c_cnt, 0, sizeof(int) * (size_t)(nbody + 1), s)) != cudaSuccess) return e;
+    if ((e = cudaMemsetAsync(w.p2c_fill, 0, sizeof(int) * (size_t)nbody, s)) != cudaSuccess) return e;
     k_p2c_count<<<gc, CD_BLOCK, 0, s>>>(g, w); ++*nl;
-    if ((e = cd_scan_exclusive(w.p2c_cnt, w.p2c_off, g.n + 1, w.scan_tmp, nullptr, s, nl)) != cudaSuccess) return e;
+    if ((e = cd_scan_exclusive(w.p2c_cnt, w.p2c_off, nbody + 1, w.scan_tmp, nullptr, s, nl)) != cudaSuccess) return e;
     k_p2c_fill<<<gc, CD_BLOCK, 0, s>>>(g, w); ++*nl;
     {
-        int gn = (g.n + CD_BLOCK - 1) / CD_BLOCK;
+        int gn = (nbody + CD_BLOCK - 1) / CD_BLOCK;
         if (gn > 4096) gn = 4096;
         k_p2c_sort<<<gn, CD_BLOCK, 0, s>>>(g, w); ++*nl;
     }

@@ -389,9 +389,13 @@ __device__ __forceinline__ void contact_geometry(const CdGeom& g, const CdWork& 
         int k = t % 6;
         nv[k >> 1] = (k & 1) ? 1.0 : -1.0;
         *gap = wall_gap(xa, ra, w.pk_wall_pos + 6 * (t / 6), k);
+        // a force-controlled wall moves along its normal only: its inverse
+        // mass enters the normal row, not the tangential one
+        if (cd_is_body(g, b)) wb_m = g.wall_im[k];
     }
     double w_n = __dadd_rn(wa_m, wb_m);
-    double w_t = __dadd_rn(__dadd_rn(w_n, __dmul_rn(__dmul_rn(ra, ra), wa_I)), __dmul_rn(__dmul_rn(rb, rb), wb_I));
+    double w_t = __dadd_rn(__dadd_rn((b < g.n) ? w_n : wa_m, __dmul_rn(__dmul_rn(ra, ra), wa_I)),
+                           __dmul_rn(__dmul_rn(rb, rb), wb_I));
     *mn = (w_n > 0.0) ? __ddiv_rn(1.0, w_n) : 0.0;
     *mt = (w_t > 0.0) ? __ddiv_rn(1.0, w_t) : 0.0;
 }

@@ -234,7 +234,18 @@ struct CdGeom {
     int npk;            // packings (1 for a plain system)
     int ncell_total;    // cells of all packings' grids
     double par_p;       // parallel fraction of the mixed update (0: Gauss-Seidel)
+    int dyn_walls;      // bit k: wall k is force-controlled (a body n + k in V, S, p2c)
+    int pad2;
+    double wall_im[6];  // inverse mass of a force-controlled wall, else 0
+    double wall_push[6];// its push along the inward normal
 };
+
+// Body b takes part in conflicts and carries a velocity record: a particle or
+// a force-controlled wall (plain systems).
+__host__ __device__ __forceinline__ bool cd_is_body(const CdGeom& g, int b)
+{
+    return b < g.n || (g.dyn_walls != 0 && b - g.n < 6 && ((g.dyn_walls >> (b - g.n)) & 1));
+}
 
 // ---------------------------------------------------------------------------
 // splitmix64 (Steele, Lea and Flood 2014) from its published definition; the

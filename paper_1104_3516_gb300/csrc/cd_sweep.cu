@@ -41,9 +41,17 @@ __device__ __forceinline__ void store_xyz_plain(typename Vec<T>::V4* dst, const 
 // Static per-particle record (inv_m, r, r / I, 0) in the sweep's real type.
 // ---------------------------------------------------------------------------
 template <typename T>
-__global__ void k_static(int n, int rotations, const double* __restrict__ radius, const double* __restrict__ inv_m,
-                         const double* __restrict__ inv_I, typename Vec<T>::V4* __restrict__ S)
+__global__ void k_static(CdGeom g, int n, int rotations, const double* __restrict__ radius,
+                         const double* __restrict__ inv_m, const double* __restrict__ inv_I,
+                         typename Vec<T>::V4* __restrict__ S)
 {
+    // records n .. n + 5: force-controlled walls (inverse mass, no radius, no rotation)
+    if (blockIdx.x == 0 && threadIdx.x < 6) {
+        typename Vec<T>::V4 s;
+        s.x = (T)(((g.dyn_walls >> threadIdx.x) & 1) ? g.wall_im[threadIdx.x] : 0.0);
+        s.y = (T)0; s.z = (T)0; s.w = (T)0;
+        S[n + threadIdx.x] = s;
+    }
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
         typename Vec<T>::V4 s;
         double r = radius[i];
@@ -66,6 +74,26 @@ __global__ void k_pack(CdGeom g, CdWork w, const double* __restrict__ vel, const
     if (w.ctrl->skip) return;
     typedef typename Vec<T>::V4 T4;
     T4* V = (T4*)w.V;
+    // force-controlled walls: velocity records n + k, pushed along the inward normal (Eq. 1)
+    if (g.dyn_walls && blockIdx.x == 0 && threadIdx.x < 6 && ((g.dyn_walls >> threadIdx.x) & 1)) {
+        const int k = threadIdx.x, ax = k >> 1;
+        double u[3] = {w.pk[0].wall_vel[3 * k], w.pk[0].wall_vel[3 * k + 1], w.pk[0].wall_vel[3 * k + 2]};
+        if (free_flight) {
+            double a = __dmul_rn(g.wall_push[k], g.wall_im[k]);
+            if (k & 1) a = -a;
+            u[ax] = __dadd_rn(u[ax], __dmul_rn(a, g.dt));
+        }
+        T4 s;
+        s.x = (T)u[0]; s.y = (T)u[1]; s.z = (T)((DIM == 3) ? u[2] : 0.0); s.w = (T)0;
+        if (DIM == 2) {
+            V[g.n + k] = s;
+        } else {
+            T4 o;
+            o.x = (T)0; o.y = (T)0; o.z = (T)0; o.w = (T)0;
+            V[2 * (g.n + k)] = s;
+            V[2 * (g.n + k) + 1] = o;
+        }
+    }
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < g.n; i += gridDim.x * blockDim.x) {
         double v[3] = {0.0, 0.0, 0.0};
         double im = inv_m[i];
@@ -136,7 +164,17 @@ __global__ void k_unpack(CdGeom g, CdWork w, double* __restrict__ pos, double* _
             omega[3 * i] = om[0]; omega[3 * i + 1] = om[1]; omega[3 * i + 2] = om[2];
         }
     }
+    if (g.dyn_walls && blockIdx.x == 0 && threadIdx.x == 0) {
+        // force-controlled walls: their velocity after the solve becomes the wall velocity
+        for (int k = 0; k < 2 * DIM; ++k) {
+            if (!((g.dyn_walls >> k) & 1)) continue;
+            const T4 s = (DIM == 2) ? V[g.n + k] : V[2 * (g.n + k)];
+            const double u[3] = {(double)s.x, (double)s.y, (double)s.z};
+            w.pk[0].wall_vel[3 * k + (k >> 1)] = u[k >> 1];
+        }
+    }
     if (integrate) {
+        if (g.dyn_walls) __syncthreads();   // block 0 moves the walls after their velocities are written
         for (int b = blockIdx.x * blockDim.x + threadIdx.x; b < g.npk; b += gridDim.x * blockDim.x) {
             const CdPack& pb = w.pk[b];
             for (int k = 0; k < 2 * DIM; ++k)
@@ -254,7 +292,7 @@ __device__ __forceinline__ void load_rec(const CdGeom& g, const CdWork& w, int p
         r.P = ((const T4*)w.c_P)[pos];
     }
     r.sa = S[r.ab.x];
-    if (r.ab.y < g.n) {
+    if (cd_is_body(g, r.ab.y)) {   // a particle, or a force-controlled wall (record n + k)
         r.sb = S[r.ab.y];
     } else {
         r.sb.x = (T)0; r.sb.y = (T)0; r.sb.z = (T)0; r.sb.w = (T)0;
@@ -354,7 +392,7 @@ __device__ __forceinline__ UpdOut apply2d(const CdGeom& g, const CdWork& w, int 
     typedef typename Vec<T>::V4 T4;
     typedef typename Vec<T>::V2 T2;
     T4* V = (T4*)w.V;
-    const bool wall = r.ab.y >= g.n;
+    const bool wall = !cd_is_body(g, r.ab.y);   // kinematic wall
     T4 va = V[r.ab.x];
     T4 vb;
     if (!wall) vb = V[r.ab.y];
@@ -362,7 +400,14 @@ __device__ __forceinline__ UpdOut apply2d(const CdGeom& g, const CdWork& w, int 
     T2 Pnew;
     UpdOut o = core2d<T>(g, r, va, vb, wall, apply_only, crit, alpha, ravg_prev, Pnew);
     V[r.ab.x] = va;
-    if (!wall) V[r.ab.y] = vb;
+    if (!wall) {
+        if (r.ab.y >= g.n) {
+            // a force-controlled wall moves along its normal only
+            if (((r.ab.y - g.n) >> 1) == 0) vb.y = (T)0; else vb.x = (T)0;
+            vb.z = (T)0;
+        }
+        V[r.ab.y] = vb;
+    }
     if (!apply_only) ((T2*)w.c_P)[pos] = Pnew;
     return o;
 }
@@ -439,7 +484,7 @@ __device__ __forceinline__ UpdOut apply3d(const CdGeom& g, const CdWork& w, int 
 {
     typedef typename Vec<T>::V4 T4;
     T4* V = (T4*)w.V;
-    const bool wall = r.ab.y >= g.n;
+    const bool wall = !cd_is_body(g, r.ab.y);   // kinematic wall
     T4 va = V[2 * r.ab.x], wa = V[2 * r.ab.x + 1];
     T4 vb, wb;
     if (!wall) { vb = V[2 * r.ab.y]; wb = V[2 * r.ab.y + 1]; }
@@ -447,7 +492,17 @@ __device__ __forceinline__ UpdOut apply3d(const CdGeom& g, const CdWork& w, int 
     T4 Pnew;
     UpdOut o = core3d<T>(g, r, va, wa, vb, wb, wall, apply_only, crit, alpha, ravg_prev, Pnew);
     V[2 * r.ab.x] = va; V[2 * r.ab.x + 1] = wa;
-    if (!wall) { V[2 * r.ab.y] = vb; V[2 * r.ab.y + 1] = wb; }
+    if (!wall) {
+        if (r.ab.y >= g.n) {
+            // a force-controlled wall moves along its normal only
+            const int ax = (r.ab.y - g.n) >> 1;
+            if (ax != 0) vb.x = (T)0;
+            if (ax != 1) vb.y = (T)0;
+            if (ax != 2) vb.z = (T)0;
+            wb.x = wb.y = wb.z = (T)0;
+        }
+        V[2 * r.ab.y] = vb; V[2 * r.ab.y + 1] = wb;
+    }
     if (!apply_only) ((T4*)w.c_P)[pos] = Pnew;
     return o;
 }
@@ -1517,9 +1572,9 @@ cudaError_t cd_launch_static(const CdGeom& g, const CdWork& w, const double* rad
                              const double* inv_I, int precision, cudaStream_t s, int* nl)
 {
     if (precision == CD_FP64)
-        k_static<double><<<grid_n(g.n), CD_BLOCK, 0, s>>>(g.n, g.rotations, radius, inv_m, inv_I, (double4*)w.S);
+        k_static<double><<<grid_n(g.n), CD_BLOCK, 0, s>>>(g, g.n, g.rotations, radius, inv_m, inv_I, (double4*)w.S);
     else
-        k_static<float><<<grid_n(g.n), CD_BLOCK, 0, s>>>(g.n, g.rotations, radius, inv_m, inv_I, (float4*)w.S);
+        k_static<float><<<grid_n(g.n), CD_BLOCK, 0, s>>>(g, g.n, g.rotations, radius, inv_m, inv_I, (float4*)w.S);
     ++*nl;
     return cudaGetLastError();
 }

@@ -272,6 +272,33 @@ def settling_discs(seed=1109, n=10_000, phi=0.5, mu=0.3, vsig=0.05, steps=200, w
                    seed=seed)
 
 
+def pressure_column(seed=1112, n=8000, width_diameters=20, pressure=0.25, mu=0.3, lid_mass=None,
+                    steps=200) -> Workload:
+    """The medium test system of Fig. 10: n discs with 20% polydispersity
+    (r ~ U[0.8, 1.2]) in a box periodic in x, width_diameters mean diameters
+    wide, between a fixed floor and a force-controlled lid (wall 3) pressing
+    with `pressure` times the width; no gravity.  The discs are deposited
+    first (every disc resting on two supports), the lid starts on the
+    highest one.  lid_mass defaults to the mass of one layer of discs."""
+    r = uniform(seed, n, 0.8, 1.2)
+    Lx = 2.0 * float(np.mean(r)) * width_diameters
+    area = float(np.sum(math.pi * r * r))
+    x = deposit2d(n, r, Lx, 4.0 * area / Lx, seed)
+    top = float(np.max(x[:, 1] + r))
+    wp = np.zeros(6)
+    wp[3] = top
+    push = np.zeros(6)
+    push[3] = pressure * Lx
+    mass = np.zeros(6)
+    mass[3] = lid_mass if lid_mass is not None else float(width_diameters) * math.pi
+    wl = _finish("pressure_column_2d", 2, x, r, mu=mu, gravity=(0.0, 0.0, 0.0), box_lo=(0.0, 0.0, 0.0),
+                 box_hi=(Lx, top + 2.0, 1.0), periodic=(1, 0, 0), wall_mask=0b1100, wall_pos=wp, steps=steps,
+                 seed=seed)
+    wl.wall_push = push
+    wl.wall_mass = mass
+    return wl
+
+
 def batch_sizes(seed=1108, n_packings=512, nmin=200, nmax=20000) -> np.ndarray:
     """Disc counts log-uniform in [nmin, nmax] per packing."""
     u = uniform(seed, n_packings, 0.0, 1.0, stream=3)

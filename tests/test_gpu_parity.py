@@ -483,3 +483,74 @@ def test_empty_system_is_rejected():
     with pytest.raises(cd.CDError) as e:
         cd.cd_create_system(p, 0, t, t, t, None, t, t, t, None, None)
     assert e.value.status == cd.CD_ERR_INVALID_ARG
+
+
+# --- force-controlled walls (the pressure walls of Fig. 10) ------------------------
+
+def test_gpu_pressed_column_carries_the_push():
+    from paper_1104_3516_gb300 import cd
+    F = 2.0
+    wl = cases.pressed_column(n=5, push=F, lid_mass=50.0)
+    g = gpu_system(wl, criterion=cd.CD_CONV_GLOBAL_REL, alpha=1e-14, max_sweeps=20000)
+    for _ in range(3):
+        st = g.step(1)
+        P = g.contacts()["impulse"]
+        assert np.allclose(P[:, 0], F * wl.dt, rtol=1e-9, atol=0)
+        assert st["last"]["wall_force"][2] == pytest.approx(F, rel=1e-9)
+        assert st["last"]["wall_force"][3] == pytest.approx(F, rel=1e-9)
+        assert np.abs(g.state()["v"]).max() <= 1e-12
+    assert g.walls()[3] == pytest.approx(wl.wall_pos[3], abs=1e-13)
+
+
+def test_gpu_free_lid_accelerates_with_its_push():
+    F, M, k = 3.0, 7.0, 6
+    wl = cases.pressed_column(n=2, push=F, lid_mass=M, lid_gap=2.0)
+    g = gpu_system(wl)
+    g.step(k)
+    assert g.walls()[3] == pytest.approx(wl.wall_pos[3] - (F / M) * wl.dt ** 2 * k * (k + 1) / 2, abs=1e-13)
+
+
+@pytest.mark.parametrize("precision,tol", [(0, FP64_TOL), (1, FP32_TOL)])
+def test_force_controlled_wall_sweep_by_sweep(precision, tol):
+    """A deposited column under a force-controlled lid, no gravity: colours
+    (the lid's contacts conflict), impulses sweep by sweep, velocities and
+    the lid's position against the oracle over several steps."""
+    from paper_1104_3516_gb300 import cd
+    wl = W.pressure_column(n=300, pressure=2.0)
+    g, o, gst, ost = run_pair(wl, steps=4, criterion=cd.CD_CONV_NONE, max_sweeps=25, precision=precision)
+    c = g.contacts()
+    assert np.array_equal(c["pairs"], o.contacts)
+    assert np.array_equal(c["colour"], o.colour[: o.nc])
+    assert impulse_err(c["impulse"], o.impulses) <= tol
+    s = g.state()
+    vs = max(float(np.abs(o.v).max()), 1e-300)
+    assert float(np.abs(s["v"].reshape(-1) - o.v).max()) <= tol * vs
+    assert g.walls()[3] == pytest.approx(o.wall_pos[3], rel=tol, abs=0)
+    lid = [k for k in range(o.nc) if o.contacts[k, 1] == wl.n + 3]
+    assert len(set(o.colour[lid].tolist())) == len(lid) >= 2
+
+
+def test_fig10_pressure_box_observables_match_the_oracle():
+    """The small system of Fig. 10 (500 discs, 20% polydispersity, 20 mean
+    diameters wide, periodic in x, a force-controlled lid pressing with 0.25
+    per unit width, no gravity), stepped 5 times on the GPU and in the
+    oracle (colour order): the force-orientation histogram (Fig. 14) and the
+    sigma_yy profile in stripes of height 2 r_max (Fig. 15) agree, and so do
+    the lid's position and force."""
+    from paper_1104_3516_gb300 import cd
+    wl = W.pressure_column(n=500)
+    g, o, gst, ost = run_pair(wl, steps=5, criterion=cd.CD_CONV_NONE, max_sweeps=60)
+    assert impulse_err(g.contacts()["impulse"], o.impulses) <= FP64_TOL
+    assert g.walls()[3] == pytest.approx(o.wall_pos[3], rel=1e-13)
+    assert gst[-1]["last"]["wall_force"][3] == pytest.approx(ost[-1]["wall_force"][3], rel=1e-9)
+    top = g.walls()[3]
+    ns = int(top // 2.4)
+    prof_g = g.stress_profile(1, 0.0, 2.4, ns)
+    Lx = wl.box_hi[0] - wl.box_lo[0]
+    prof_o = O.stress_profile(o.x, wl.r, wl.n, o.contacts, o.normal[: o.nc], o.gap[: o.nc], o.impulses, wl.dt, 1,
+                              0.0, 2.4, ns, Lx, periodic_length=Lx)
+    assert np.allclose(prof_g, prof_o, rtol=0, atol=1e-9 * float(np.abs(prof_o).max()))
+    assert float(np.abs(prof_o).max()) > 0.0
+    h_g = g.force_orientation(18)
+    h_o = O.force_orientation(o.impulses, o.normal[: o.nc], 18)
+    assert int(np.abs(h_g - h_o).max()) <= 2 and h_g.sum() > 100
