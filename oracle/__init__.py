@@ -16,7 +16,7 @@ it restates:
   the GPU sweeps in; not in the paper, which sweeps sequentially).
 * :func:`solve` -- iterative Gauss-Seidel force calculation, Sec. 2.1 and
   Fig. 2 (Eqs. 3-11), convergence tests (I)/(II); mixed parallel update of
-  Sec. 2.3.
+  Sec. 2.3; domain-wise update of Sec. 3.1 (with :func:`contact_domains`).
 * :func:`step` -- one time step, Fig. 3 with Eqs. 1-2.
 """
 from __future__ import annotations
@@ -62,6 +62,7 @@ class Params(C.Structure):
         ("tile_cells", C.c_int64),
         ("wall_push", C.c_double * 6),
         ("wall_mass", C.c_double * 6),
+        ("domains", C.c_int64 * 3),
     ]
 
 
@@ -121,7 +122,10 @@ def lib():
             _lib.ora_colour_greedy.argtypes = [i64, i64, P(i32), C.c_uint64, C.c_int64, P(i32)]
             _lib.ora_solve.restype = C.c_int
             _lib.ora_solve.argtypes = [P(Params), i64, P(d), P(d), P(d), P(d), P(d), i64, P(i32), P(d), P(d),
-                                       P(d), P(d), P(i32), P(C.c_int64), P(i32), i64, P(d), P(d), P(SolveStats)]
+                                       P(d), P(d), P(i32), P(C.c_int64), P(i32), P(i32), i64, P(d), P(d),
+                                       P(SolveStats)]
+            _lib.ora_contact_domains.restype = i64
+            _lib.ora_contact_domains.argtypes = [P(Params), i64, P(d), P(d), i64, P(i32), P(d), P(d), P(i32)]
             _lib.ora_tile_colour.restype = C.c_int
             _lib.ora_tile_colour.argtypes = [P(Params), i64, P(d), P(d), i64, P(i32), P(i32), P(C.c_int64)]
             _lib.ora_step.restype = C.c_int
@@ -144,7 +148,7 @@ def _f64(a):
 def make_params(dim=2, dt=1e-3, mu=0.3, gravity=(0.0, -1.0, 0.0), box_lo=(0, 0, 0), box_hi=(1, 1, 1),
                 periodic=(0, 0, 0), wall_mask=0, wall_vel=None, delta=0.24, alpha=1e-6,
                 criterion=CRIT_GLOBAL_REL, max_sweeps=1000, order=ORDER_COLOUR, warm_start=1, seed=0,
-                parallel_p=0.0, rotations=1, tile_cells=0, wall_push=None, wall_mass=None) -> Params:
+                parallel_p=0.0, rotations=1, tile_cells=0, wall_push=None, wall_mass=None, domains=(1, 1, 1)) -> Params:
     p = Params()
     p.dim = dim
     p.dt = dt
@@ -173,6 +177,8 @@ def make_params(dim=2, dt=1e-3, mu=0.3, gravity=(0.0, -1.0, 0.0), box_lo=(0, 0, 
     for k in range(6):
         p.wall_push[k] = float(wp[k])
         p.wall_mass[k] = float(wm[k])
+    for k in range(3):
+        p.domains[k] = int(domains[k])
     return p
 
 
@@ -245,12 +251,14 @@ def tile_colour(p: Params, x, r, pairs):
 
 
 def solve(p: Params, v_free, w_free, r, inv_m, inv_I, pairs, normal, gap, mn, mt, P0=None, colour=None,
-          fixed=None, step_index=0, history=False, group=None):
+          fixed=None, step_index=0, history=False, group=None, domain=None):
     """Gauss-Seidel impulse solve (Sec. 2.1, Fig. 2).
 
     ``v_free``/``w_free`` are the velocities without contact impulses; returns
     ``(P, v, w, stats[, ravg_history])`` where ``v``/``w`` include the final
     impulses.  P has 2 columns (Pn, Pt) in 2D and 4 (Pn, Ptx, Pty, Ptz) in 3D.
+    ``domain`` (one id per contact, see :func:`contact_domains`) selects the
+    domain-wise update of Sec. 3.1.
     """
     D = int(p.dim)
     pw = 2 if D == 2 else 4
@@ -264,6 +272,7 @@ def solve(p: Params, v_free, w_free, r, inv_m, inv_I, pairs, normal, gap, mn, mt
     col = None if colour is None else np.ascontiguousarray(colour, dtype=np.int32)
     fx = None if fixed is None else np.ascontiguousarray(fixed, dtype=np.int32)
     grp = None if group is None else np.ascontiguousarray(group, dtype=np.int64)
+    dom = None if domain is None else np.ascontiguousarray(domain, dtype=np.int32)
     hist = np.zeros(int(p.max_sweeps) + 1) if history else None
     st = SolveStats()
     normal = np.ascontiguousarray(normal, dtype=np.float64).reshape(-1, 3)
@@ -271,11 +280,25 @@ def solve(p: Params, v_free, w_free, r, inv_m, inv_I, pairs, normal, gap, mn, mt
                     _ptr(_f64(r), C.c_double), _ptr(_f64(inv_m), C.c_double), _ptr(_f64(inv_I), C.c_double),
                     nc, _ptr(pairs, C.c_int32), _ptr(normal, C.c_double), _ptr(_f64(gap), C.c_double),
                     _ptr(_f64(mn), C.c_double), _ptr(_f64(mt), C.c_double), _ptr(col, C.c_int32),
-                    _ptr(grp, C.c_int64), _ptr(fx, C.c_int32), step_index, _ptr(P, C.c_double), _ptr(hist, C.c_double), C.byref(st))
+                    _ptr(grp, C.c_int64), _ptr(fx, C.c_int32), _ptr(dom, C.c_int32), step_index, _ptr(P, C.c_double), _ptr(hist, C.c_double), C.byref(st))
     out = (P[:nc].copy(), v, w, st.as_dict())
     if history:
         return out + (hist[: st.sweeps + 1].copy(),)
     return out
+
+
+def contact_domains(p: Params, x, r, pairs, normal, gap):
+    """Domain of every contact for the domain-wise update of Sec. 3.1 (the
+    slab grid of ``p.domains`` over the box, by the middle of the gap);
+    returns (ids, number of domains)."""
+    pairs = np.ascontiguousarray(pairs, dtype=np.int32).reshape(-1, 2)
+    nc = pairs.shape[0]
+    out = np.zeros(max(nc, 1), dtype=np.int32)
+    normal = np.ascontiguousarray(normal, dtype=np.float64).reshape(-1, 3)
+    nd = lib().ora_contact_domains(C.byref(p), _f64(r).shape[0], _ptr(_f64(x).reshape(-1), C.c_double),
+                                   _ptr(_f64(r), C.c_double), nc, _ptr(pairs, C.c_int32),
+                                   _ptr(normal, C.c_double), _ptr(_f64(gap), C.c_double), _ptr(out, C.c_int32))
+    return out[:nc], int(nd)
 
 
 class OracleSystem:

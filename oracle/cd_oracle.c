@@ -23,7 +23,10 @@
  *   - the iterative nonlinear Gauss-Seidel over the contact network
  *     (Sec. 2.1): random sequential order re-drawn every sweep, a fixed
  *     order, or the colour order used by the GPU; the mixed parallel /
- *     sequential update with parallelness p (Sec. 2.3);
+ *     sequential update with parallelness p (Sec. 2.3); the domain-wise
+ *     update of the parallel algorithm (Sec. 3.1), where every domain sweeps
+ *     its own contacts while the other domains' contacts keep the impulses
+ *     of the previous sweep;
  *   - the convergence tests (I) local and (II) global (Sec. 2.1, alpha);
  *   - the first-order Euler time step, Eqs. 1-2.
  *
@@ -39,6 +42,11 @@
  *     squared form (II); ORA_CRIT_LOCAL is test (I).
  *   - warm start: impulses are carried over by contact key from the previous
  *     time step (off: the iteration starts from zero forces).
+ *   - domain-wise update: domains are a grid of equal slabs of the box (the
+ *     paper's domains come from its load balancer, out of scope here); a
+ *     contact is native to the domain of the middle of its gap (Sec. 3.1);
+ *     a domain sees the sweep-start velocities changed by its own updates,
+ *     and the changes of all domains are summed at the end of the sweep.
  */
 #include <math.h>
 #include <stdint.h>
@@ -74,6 +82,9 @@ typedef struct {
     double wall_push[6];    /* external force pushing wall k along its inward normal */
     double wall_mass[6];    /* > 0: wall k is a rigid body of this mass moving along
                                its normal (force-controlled); 0: kinematic */
+    int64_t domains[3];     /* domain-wise update of Sec. 3.1: the box is cut
+                               into domains[k] equal slabs along axis k (<= 1:
+                               one); 1 x 1 x 1 is plain Gauss-Seidel */
 } ora_params;
 
 /* A force-controlled wall: present, with a positive mass. */
@@ -693,6 +704,52 @@ static uint64_t rng_next(uint64_t* state)
     return z ^ (z >> 31);
 }
 
+/* ------------------------------------------------------------------------ */
+/* Domain-wise update (Sec. 3.1).  The box is cut into a grid of equal      */
+/* domains; a contact belongs to the domain holding its position, the       */
+/* middle of the gap between the two surfaces: q = x_a + n (r_a + g / 2)    */
+/* (a wall contact likewise, n pointing from the particle into the wall),   */
+/* wrapped on a periodic axis.  Slab index along axis k:                    */
+/* floor(((q - lo) / (hi - lo)) * domains[k]), clamped; domain id = ix +     */
+/* nx (iy + ny iz).  Returns the number of domains.                         */
+/* ------------------------------------------------------------------------ */
+static int64_t n_domains_axis(const ora_params* p, int k)
+{
+    return (k < (int)p->dim && p->domains[k] > 1) ? p->domains[k] : 1;
+}
+
+int64_t ora_contact_domains(const ora_params* p, long long n, const double* x, const double* r, long long nc,
+                            const int32_t* pairs, const double* normal, const double* gap, int32_t* out)
+{
+    int D = (int)p->dim;
+    int64_t total = 1;
+    for (int k = 0; k < 3; ++k) total *= n_domains_axis(p, k);
+    (void)n;
+    for (long long c = 0; c < nc; ++c) {
+        long long a = pairs[2 * c];
+        int64_t id = 0, mult = 1;
+        for (int k = 0; k < D; ++k) {
+            int64_t nd = n_domains_axis(p, k);
+            if (nd > 1) {
+                double q = x[a * D + k] + normal[c * 3 + k] * (r[a] + 0.5 * gap[c]);
+                double lo = p->box_lo[k], hi = p->box_hi[k];
+                if (p->periodic[k]) {
+                    if (q >= hi) q = q - (hi - lo);
+                    else if (q < lo) q = q + (hi - lo);
+                }
+                double t = ((q - lo) / (hi - lo)) * (double)nd;
+                int64_t ix = (int64_t)floor(t);
+                if (ix < 0) ix = 0;
+                if (ix > nd - 1) ix = nd - 1;
+                id += ix * mult;
+            }
+            mult *= nd;
+        }
+        out[c] = (int32_t)id;
+    }
+    return total;
+}
+
 /* A contact is in the parallel-update set of Sec. 2.3 when a hash of its key
  * falls below p (a fixed subset per contact key). */
 static int is_parallel(const ora_params* p, uint64_t key)
@@ -723,6 +780,8 @@ static int cmp_group_colour(const void* u, const void* v)
  *   colour   colour per contact (ORA_ORDER_COLOUR), may be NULL otherwise.
  *   group    colour-order group per contact (tiled order), or NULL.
  *   fixed    the order for ORA_ORDER_FIXED, may be NULL otherwise.
+ *   domain   domain of each contact (ora_contact_domains) for the
+ *            domain-wise update of Sec. 3.1, or NULL (one domain).
  *   ravg_hist  if non-NULL, R_avg after sweep j is stored at [j]
  *              ([0] = starting impulses); room for max_sweeps + 1.
  * Returns 0. */
@@ -730,7 +789,8 @@ int ora_solve(ora_params* p, long long n, double* v, double* w,
               const double* r, const double* inv_m, const double* inv_I,
               long long nc, const int32_t* pairs, const double* normal, const double* gap,
               const double* mn, const double* mt, const int32_t* colour, const int64_t* group,
-              const int32_t* fixed, long long step_index, double* P, double* ravg_hist, ora_solve_stats* st)
+              const int32_t* fixed, const int32_t* domain, long long step_index, double* P, double* ravg_hist,
+              ora_solve_stats* st)
 {
     int D = (int)p->dim;
     int pw = pw_of(D);
@@ -766,11 +826,19 @@ int ora_solve(ora_params* p, long long n, double* v, double* w,
     char* par = (char*)malloc((size_t)(nc > 0 ? nc : 1));
     long long npar = 0;
     for (long long c = 0; c < nc; ++c) {
-        par[c] = (char)is_parallel(p, key_of(pairs[2 * c], pairs[2 * c + 1]));
+        /* the domain-wise update replaces the mixed update of Sec. 2.3 */
+        par[c] = domain ? 0 : (char)is_parallel(p, key_of(pairs[2 * c], pairs[2 * c + 1]));
         npar += par[c];
     }
     double* Pprev = (double*)malloc(sizeof(double) * (size_t)(nc > 0 ? nc : 1) * (size_t)pw);
     double* dPpar = (double*)malloc(sizeof(double) * (size_t)(nc > 0 ? nc : 1) * 3);
+    int32_t ndom = 1;
+    if (domain) for (long long c = 0; c < nc; ++c) if (domain[c] + 1 > ndom) ndom = domain[c] + 1;
+    const size_t nv = (size_t)(n > 0 ? n : 1) * (size_t)D, nw = (size_t)(n > 0 ? n : 1) * (size_t)(D == 2 ? 1 : 3);
+    double* v0 = (double*)malloc(sizeof(double) * nv);
+    double* w0 = (double*)malloc(sizeof(double) * nw);
+    double* vsum = (double*)malloc(sizeof(double) * nv);
+    double* wsum = (double*)malloc(sizeof(double) * nw);
 
     double ravg_prev = 0.0;
     for (long long c = 0; c < nc; ++c) ravg_prev += impulse_norm(D, P + c * pw);
@@ -800,10 +868,40 @@ int ora_solve(ora_params* p, long long n, double* v, double* w,
             for (long long c = 0; c < nc; ++c)
                 if (par[c]) solve_one(&s, c, P + c * pw, dPpar + c * 3);
         }
-        for (long long o = 0; o < nc; ++o) {
-            long long c = order[o];
-            if (par[c]) continue;
-            solve_one(&s, c, P + c * pw, NULL);
+        if (domain) {
+            /* Sec. 3.1: every domain sweeps its own (native) contacts in the
+             * sweep order, seeing the velocities of the sweep start changed
+             * by its own updates only: the contacts of other domains keep
+             * the impulses of the last sweep.  At the end of the sweep the
+             * velocity changes of all domains are added up. */
+            double u0[18], usum[18];   /* force-controlled walls: the same */
+            memcpy(v0, v, sizeof(double) * nv);
+            memcpy(w0, w, sizeof(double) * nw);
+            memcpy(u0, wall_vel, sizeof(u0));
+            memcpy(vsum, v0, sizeof(double) * nv);
+            memcpy(wsum, w0, sizeof(double) * nw);
+            memcpy(usum, u0, sizeof(u0));
+            for (int32_t d = 0; d < ndom; ++d) {
+                memcpy(v, v0, sizeof(double) * nv);
+                memcpy(w, w0, sizeof(double) * nw);
+                memcpy(wall_vel, u0, sizeof(u0));
+                for (long long o = 0; o < nc; ++o) {
+                    long long c = order[o];
+                    if (domain[c] == d) solve_one(&s, c, P + c * pw, NULL);
+                }
+                for (size_t i = 0; i < nv; ++i) vsum[i] = vsum[i] + (v[i] - v0[i]);
+                for (size_t i = 0; i < nw; ++i) wsum[i] = wsum[i] + (w[i] - w0[i]);
+                for (int k = 0; k < 18; ++k) usum[k] = usum[k] + (wall_vel[k] - u0[k]);
+            }
+            memcpy(v, vsum, sizeof(double) * nv);
+            memcpy(w, wsum, sizeof(double) * nw);
+            memcpy(wall_vel, usum, sizeof(usum));
+        } else {
+            for (long long o = 0; o < nc; ++o) {
+                long long c = order[o];
+                if (par[c]) continue;
+                solve_one(&s, c, P + c * pw, NULL);
+            }
         }
         if (npar > 0) {
             for (long long c = 0; c < nc; ++c)
@@ -855,6 +953,7 @@ int ora_solve(ora_params* p, long long n, double* v, double* w,
         if (b >= n) st->wall_force[b - n] += P[c * pw] / p->dt;
     }
     for (int k = 0; k < 18; ++k) p->wall_vel[k] = wall_vel[k];   /* force-controlled walls moved */
+    free(wsum); free(vsum); free(w0); free(v0);
     free(dPpar); free(Pprev); free(par); free(order);
     return 0;
 }
@@ -952,9 +1051,15 @@ int ora_step(ora_params* p, long long n, double* x, double* v, double* w, double
     } else {
         for (long long c = 0; c < nc; ++c) colour[c] = 0;
     }
-    ora_solve(&q, n, v, w, r, inv_m, inv_I, nc, pairs, normal, gap, mn, mt, colour, group, NULL,
+    int32_t* domain = NULL;
+    if (n_domains_axis(p, 0) * n_domains_axis(p, 1) * n_domains_axis(p, 2) > 1) {
+        domain = (int32_t*)malloc(sizeof(int32_t) * ncz);
+        ora_contact_domains(p, n, x, r, nc, pairs, normal, gap, domain);
+    }
+    ora_solve(&q, n, v, w, r, inv_m, inv_I, nc, pairs, normal, gap, mn, mt, colour, group, NULL, domain,
               step_index, P, NULL, st);
     for (int k = 0; k < 18; ++k) p->wall_vel[k] = q.wall_vel[k];
+    free(domain);
     free(group);
 
     /* Eq. 2: positions with the new velocities; orientation likewise */

@@ -130,3 +130,32 @@ def pressed_column(n=5, radius=1.0, push=2.0, lid_mass=50.0, mu=0.3, lid_gap=0.0
     wl.wall_push = np.array([0.0, 0.0, 0.0, push, 0.0, 0.0])
     wl.wall_mass = np.array([0.0, 0.0, 0.0, lid_mass, 0.0, 0.0])
     return wl
+
+
+def stack2(radius=1.0, mu=0.3):
+    """Two equal discs stacked on the floor (gaps 0), gravity 1; the box
+    [-5, 5] x [0, 4.5] cut into 3 slabs along y puts the floor contact
+    (middle of its gap at y = 0) and the disc-disc contact (y = 2 r) in
+    different domains."""
+    return _wl("stack2", 2, [[0.0, radius], [0.0, 3.0 * radius]], [radius, radius], dt=DT, mu=mu,
+               gravity=(0.0, -G, 0.0), box_lo=(-5.0, 0.0, 0.0), box_hi=(5.0, 4.5 * radius, 1.0), wall_mask=0b0100)
+
+
+def two_columns(n=4, radius=1.0, mu=0.3):
+    """Two columns of n discs on the floor at x = -3 and x = +3: two slabs
+    along x separate them completely."""
+    y = radius + 2.0 * radius * np.arange(n)
+    x = np.concatenate([np.stack([np.full(n, -3.0), y], axis=1), np.stack([np.full(n, 3.0), y], axis=1)])
+    return _wl("two_columns", 2, x, np.full(2 * n, radius), dt=DT, mu=mu, gravity=(0.0, -G, 0.0),
+               box_lo=(-6.0, 0.0, 0.0), box_hi=(6.0, 2.0 * radius * n + 5.0, 1.0), wall_mask=0b0100)
+
+
+def chain_slabs(n=8, radius=1.0, force=1.0):
+    """The chain of :func:`chain` in the box [-r, (2 n - 1) r] along x, so
+    that n equal slabs along x are centred on the contact points 2 k r
+    (k = 0: the wall contact); with N_p slabs, N_p dividing n, every slab
+    holds n / N_p contacts.  Returns (workload, f_ext)."""
+    wl, f = chain(n=n, radius=radius, force=force)
+    wl.box_lo = (-radius, -5.0, 0.0)
+    wl.box_hi = ((2.0 * n - 1.0) * radius, 5.0, 1.0)
+    return wl, f

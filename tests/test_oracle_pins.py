@@ -370,3 +370,98 @@ def test_contacts_on_a_force_controlled_wall_conflict():
     c0, K0 = O.colour_greedy(n, pairs, seed=5)
     c1, K1 = O.colour_greedy(n, pairs, seed=5, dyn_walls=1 << 2)
     assert K0 == 1 and K1 == n and len(set(c1.tolist())) == n
+
+
+# --- domain-wise update of the parallel algorithm (Sec. 3.1, Sec. 4.3) -----------
+
+def test_domains_sharing_no_particle_give_gauss_seidel():
+    """Two columns in two slabs share no particle, so each domain's sweep is
+    the Gauss-Seidel sweep of its column: same sweeps, same impulses (up to
+    the rounding of summing the domains' velocity changes)."""
+    wl = cases.two_columns(n=4)
+    a, st_a = _one_step(wl, order=O.ORDER_COLOUR, alpha=1e-13, max_sweeps=5000)
+    b, st_b = _one_step(wl, order=O.ORDER_COLOUR, alpha=1e-13, max_sweeps=5000, domains=(2, 1, 1))
+    assert st_a["sweeps"] == st_b["sweeps"]
+    assert np.array_equal(a.contacts, b.contacts)
+    assert np.allclose(b.impulses, a.impulses, rtol=1e-13, atol=1e-18)
+    assert np.allclose(b.v, a.v, rtol=0, atol=1e-15)
+
+
+@pytest.mark.parametrize("k", [1, 2, 3, 4, 5, 6])
+def test_stack_split_between_two_domains_is_a_jacobi_pair(k):
+    """Two discs on the floor (floor contact A, disc-disc contact B), forces
+    from zero, in units of m g dt.  One domain, colour order (B first, its
+    particles have more contacts): Gauss-Seidel gives B_k = A_{k-1} / 2,
+    A_k = 1 + B_k, i.e. A_k = 2 - 2^(1-k), B_k = 1 - 2^(1-k).  A and B in
+    different domains see each other's impulse of the previous sweep only
+    (Sec. 3.1): A_k = 1 + B_{k-1}, B_k = A_{k-1} / 2, i.e.
+    A_k = 2 - 2^(1 - ceil(k/2)), B_k = 1 - 2^(-floor(k/2))."""
+    wl = cases.stack2()
+    unit = G * DT / wl.inv_m[0]
+    gs, _ = _one_step(wl, order=O.ORDER_COLOUR, criterion=O.CRIT_NONE, max_sweeps=k, warm_start=0)
+    jac, _ = _one_step(wl, order=O.ORDER_COLOUR, criterion=O.CRIT_NONE, max_sweeps=k, warm_start=0,
+                       domains=(1, 3, 1))
+    # contact 0 is (0, 1) = B, contact 1 is (0, wall 2) = A
+    assert gs.contacts.tolist() == [[0, 1], [0, 4]]
+    A_gs, B_gs = 2.0 - 2.0 ** (1 - k), 1.0 - 2.0 ** (1 - k)
+    A_j, B_j = 2.0 - 2.0 ** (1 - math.ceil(k / 2)), 1.0 - 2.0 ** (-(k // 2))
+    assert gs.impulses[1, 0] == pytest.approx(A_gs * unit, rel=1e-12)
+    assert gs.impulses[0, 0] == pytest.approx(B_gs * unit, rel=1e-12, abs=1e-18)
+    assert jac.impulses[1, 0] == pytest.approx(A_j * unit, rel=1e-12)
+    assert jac.impulses[0, 0] == pytest.approx(B_j * unit, rel=1e-12, abs=1e-18)
+
+
+def test_contact_domains_follow_the_middle_of_the_gap():
+    """The domain of a contact is the slab of the middle of its gap: the
+    chain's contacts sit at x = 2 k r, one per slab of width 2 r."""
+    n = 6
+    wl, _ = cases.chain_slabs(n=n)
+    p = params(wl, domains=(n, 1, 1))
+    pairs = O.detect_brute(p, wl.x, wl.r, wl.wall_pos)
+    normal, gap, _, _ = O.contact_geometry(p, wl.x, wl.r, wl.inv_m, wl.inv_I, wl.wall_pos, pairs)
+    dom, nd = O.contact_domains(p, wl.x, wl.r, pairs, normal, gap)
+    assert nd == n
+    expect = [b if b < n else 0 for a, b in pairs.tolist()]   # (k-1, k) at x = 2 k r; the wall contact at 0
+    assert dom.tolist() == expect
+
+
+def test_every_contact_in_its_own_domain_is_the_parallel_update():
+    """With one contact per domain nothing is sequential: every contact is
+    computed from the velocities of the sweep start and applied at its end,
+    which is the mixed update of Sec. 2.3 with p = 1 (Jacobi)."""
+    n = 6
+    wl, f = cases.chain_slabs(n=n, force=1.0)
+    kw = dict(f_ext=f, order=O.ORDER_COLOUR, criterion=O.CRIT_NONE, max_sweeps=40, warm_start=0)
+    dom, _ = _one_step(wl, domains=(n, 1, 1), **kw)
+    jac, _ = _one_step(wl, parallel_p=1.0, **kw)
+    seq, _ = _one_step(wl, **kw)
+    assert np.allclose(dom.impulses, jac.impulses, rtol=1e-12, atol=1e-18)
+    assert np.allclose(dom.v, jac.v, rtol=0, atol=1e-14)
+    assert not np.allclose(dom.impulses, seq.impulses, rtol=1e-3)
+
+
+def test_domain_boundaries_slow_the_chain_like_a_parallel_fraction():
+    """Sec. 4.3, Fig. 13(b): a chain of n discs pressed against a wall,
+    forces from zero, random sequential order within each of N_p domains.
+    Boundaries act as parallel update, so the sweeps to reach the squared
+    global test at 1e-12 grow with N_p as D_s / D_eff with
+    D_eff = D_p p + D_s (1 - p), p = N_p / n.  The fitted ratio D_s / D_p
+    lies near the paper's values (1.53 fitted, ~1.59 from q_s / q_p)."""
+    n = 24
+    mean = {}
+    for Np in (1, 4, 12):
+        sw = []
+        for seed in range(4):
+            wl, f = cases.chain_slabs(n=n, force=1.0)
+            s, st = _one_step(wl, f_ext=f, order=O.ORDER_RANDOM, criterion=O.CRIT_GLOBAL_SQ, alpha=1e-12,
+                              max_sweeps=200000, domains=(Np, 1, 1), seed=seed, warm_start=0)
+            assert st["converged"]
+            sw.append(st["sweeps"])
+        mean[Np] = float(np.mean(sw))
+    assert mean[1] < mean[4] < mean[12]
+    ratios = []
+    for Np in (4, 12):
+        p = Np / n
+        nt = mean[Np] / mean[1]            # = 1 / (1 - p + p D_p / D_s)
+        ratios.append(p / (1.0 / nt - 1.0 + p))
+    assert all(1.35 < q < 1.85 for q in ratios), ratios
