@@ -83,6 +83,8 @@ def parse():
                     help="0: global colour order; >= 2: tiled colour order with tiles of this many cells")
     ap.add_argument("--dataflow", type=int, default=0,
                     help="1: per-particle update counts instead of a grid barrier per colour")
+    ap.add_argument("--domains", type=int, nargs=3, default=[1, 1, 1], metavar=("NX", "NY", "NZ"),
+                    help="domain-wise update of Sec. 3.1: slabs per axis (1 1 1: Gauss-Seidel)")
     ap.add_argument("--batched-steps", type=int, default=3,
                     help="timed steps of the 512-packing batched workload (0: skip)")
     ap.add_argument("--packings", type=int, default=512)
@@ -118,6 +120,7 @@ def config(args, wl, extra=None):
               "warm_start": True,
               "order": ("colour (largest degree first, then hash)" if args.tile_cells == 0 else
                         f"tiled colour order, {args.tile_cells}-cell tiles"),
+              "domains": list(args.domains),
               "l2": "flushed (512 MiB write) before every timed step"})
     if extra:
         c.update(extra)
@@ -299,7 +302,8 @@ def run_ours(args):
     prec = cd.CD_FP64 if args.precision == "f64" else cd.CD_FP32
     stream = torch.cuda.current_stream(device)
     shape, tuned = {}, None
-    if not args.no_autotune and args.tile_cells == 0 and args.dataflow == 0:
+    plain = args.tile_cells == 0 and args.dataflow == 0 and list(args.domains) == [1, 1, 1]
+    if not args.no_autotune and plain:
         # block shape of the sweep grid chosen by timing short solves of this system (untimed)
         from paper_1104_3516_gb300 import autotune
         shape, table = autotune.tune(wl, precision=prec, device=device, max_contacts=4 * wl.n,
@@ -307,7 +311,8 @@ def run_ours(args):
                                                  for t, b in autotune.BLOCK_SHAPES])
         tuned = {"choice": shape, "ms_per_sweep": [[c, m] for c, m in table]}
     sysg = cd.CDSystem(wl, device=device, precision=prec, criterion=cd.CD_CONV_GLOBAL_REL, max_contacts=4 * wl.n,
-                       timing=1, stream=stream, tile_cells=args.tile_cells, dataflow=args.dataflow, **shape)
+                       timing=1, stream=stream, tile_cells=args.tile_cells, dataflow=args.dataflow,
+                       domains=tuple(args.domains), **shape)
     flush = torch.empty(512 << 20, dtype=torch.uint8, device=device)
 
     for _ in range(args.warmup):
@@ -355,6 +360,8 @@ def run_ours(args):
     peak, peak_kind = peaks()
     kname = ("k_sweep" if args.tile_cells == 0 and args.dataflow == 0 else
              ("k_sweep_tiled" if args.tile_cells else "k_sweep_flow"))
+    if list(args.domains) != [1, 1, 1]:
+        kname = "k_sweep_domains"
     kname += f"<{wl.dim},{'double' if args.precision == 'f64' else 'float'}>"
     sweep_s = ph["sweep"] / 1e3
     gbs = sweep_bytes / sweep_s / 1e9 if sweep_s > 0 else 0.0

@@ -164,6 +164,24 @@ typedef struct {
                                the steps update.  Plain systems with the global
                                colour order, no mixed update, no tape. */
     double wall_mass[6];    /* 0: wall k kinematic (prescribed velocity) */
+    int64_t domains[3];     /* domain-wise update of the parallel algorithm
+                               (Sec. 3.1): the box [box_lo, box_hi] is cut
+                               into domains[k] equal slabs along axis k (0 or
+                               1: not cut); a contact belongs to the domain
+                               holding the middle of its gap, x_a + n (r_a +
+                               g / 2) (wrapped on a periodic axis).  In every
+                               sweep each domain updates its own contacts in
+                               the colour order, seeing the velocities of the
+                               sweep start changed by its own updates only
+                               (the other domains' contacts keep the impulses
+                               of the previous sweep), and the domains'
+                               velocity changes are summed at the end of the
+                               sweep: what a multi-processor run of the paper
+                               computes, on one GPU.  The workspace grows by
+                               2 velocity records (and their start copies) per
+                               contact of capacity.  Plain systems with the
+                               colour-barrier schedule, kinematic walls, no
+                               mixed update, no tape.  All 1: Gauss-Seidel. */
 } cd_params;
 
 typedef struct cd_system cd_system;

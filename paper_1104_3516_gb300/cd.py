@@ -68,6 +68,7 @@ class cd_params(C.Structure):
         ("sweep_blocks_per_sm", C.c_int64),
         ("wall_push", C.c_double * 6),
         ("wall_mass", C.c_double * 6),
+        ("domains", C.c_int64 * 3),
     ]
 
 
@@ -368,7 +369,7 @@ def cd_last_error(sysptr=None) -> str:
 def make_params(wl, precision=CD_FP64, criterion=CD_CONV_GLOBAL_REL, max_contacts=None, warm_start=1, rotations=1,
                 seed=None, max_sweeps=None, alpha=None, timing=0, tile_cells=0, dataflow=0,
                 parallel_p=0.0, tape_steps=0, adjoint_compliance=0.0, use_graph=0, sweep_threads=0,
-                sweep_blocks_per_sm=0) -> cd_params:
+                sweep_blocks_per_sm=0, domains=(1, 1, 1)) -> cd_params:
     p = cd_params()
     p.dim = wl.dim
     p.precision = precision
@@ -408,6 +409,8 @@ def make_params(wl, precision=CD_FP64, criterion=CD_CONV_GLOBAL_REL, max_contact
     for k in range(6):
         p.wall_push[k] = float(push[k])
         p.wall_mass[k] = float(mass[k])
+    for k in range(3):
+        p.domains[k] = int(domains[k])
     return p
 
 

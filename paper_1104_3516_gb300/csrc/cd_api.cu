@@ -105,8 +105,9 @@ static size_t layout(cd_system* s, char* base, CdWork* w)
     if ((size_t)s->g.ntiles * CD_KLOCAL + 1 > scan_max) scan_max = (size_t)s->g.ntiles * CD_KLOCAL + 1;
     CdWork t;
     t.ctrl = L.take<CdCtrl>(base, 1);
-    // records n .. n + 5 belong to force-controlled walls
-    t.V = L.take<char>(base, (n + 6) * vrec);
+    // records n .. n + 5 belong to force-controlled walls, then the domain views
+    const size_t vcap = (s->g.ndom_total > 1) ? 2 * cap : 0;
+    t.V = L.take<char>(base, (n + 6 + vcap) * vrec);
     t.S = L.take<char>(base, (n + 6) * 4 * real);
     t.cell_of = L.take<int>(base, n);
     t.cell_cnt = L.take<int>(base, ncell + 1);
@@ -171,6 +172,16 @@ static size_t layout(cd_system* s, char* base, CdWork* w)
         t.cmp_off = L.take<int>(base, CD_KMAX + 1);
     }
     t.c_dpar = L.take<double>(base, s->g.par_p > 0.0 ? cap * s->pw : 1);
+    {
+        const bool dom = s->g.ndom_total > 1;
+        t.dom_key = L.take<int>(base, dom ? cap : 1);
+        t.dom_home = L.take<int>(base, dom ? n : 1);
+        t.view_cnt = L.take<int>(base, dom ? n + 1 : 1);
+        t.view_off = L.take<int>(base, dom ? n + 1 : 1);
+        t.view_owner = L.take<int>(base, dom ? vcap : 1);
+        t.V0 = L.take<char>(base, (dom ? vcap : 1) * vrec);
+        t.c_vab = L.take<int2>(base, dom ? cap : 1);
+    }
     t.obs = L.take<double>(base, CD_OBS_MAX);
     const size_t T = (size_t)s->p.tape_steps;
     t.tape = L.take<char>(base, T ? T * cd_tape_slot_bytes((int64_t)n, (int64_t)cap) : 1);
@@ -291,6 +302,8 @@ static cd_status launch_detect_chain(cd_system* s, int timed)
     ++s->launches;
     CD_CUDA(s, cudaGetLastError());
     if (s->g.dataflow) CD_CUDA(s, cd_launch_need(s->g, s->w, s->stream, &s->launches));
+    if (s->g.ndom_total > 1)
+        CD_CUDA(s, cd_launch_domains(s->g, s->w, s->pos, s->radius, s->stream, &s->launches));
     return CD_OK;
 }
 
@@ -532,6 +545,33 @@ static cd_status create_impl(const cd_params* params, int64_t npk, const int64_t
         }
         g.dyn_walls = dyn;
     }
+    {
+        // domain-wise update (Sec. 3.1)
+        long long total = 1;
+        for (int k = 0; k < 3; ++k) {
+            if (p.domains[k] < 0 || p.domains[k] > 65536) {
+                delete s;
+                return fail(nullptr, CD_ERR_INVALID_ARG, "domains must be in [0, 65536] per axis");
+            }
+            g.ndom[k] = (k < p.dim && p.domains[k] > 1) ? (int)p.domains[k] : 1;
+            total *= g.ndom[k];
+        }
+        for (int64_t b = 1; b < npk; ++b)
+            for (int k = 0; k < 3; ++k)
+                if (params[b].domains[k] > 1) total = total > 1 ? total : 2;
+        if (total > (1LL << 24)) {
+            delete s;
+            return fail(nullptr, CD_ERR_INVALID_ARG, "at most 2^24 domains");
+        }
+        if (total > 1 && (npk > 1 || g.tile_cells != 0 || g.dataflow || p.parallel_p > 0.0 || g.dyn_walls ||
+                          p.tape_steps > 0)) {
+            delete s;
+            return fail(nullptr, CD_ERR_INVALID_ARG,
+                        "domains need a plain system with the colour-barrier schedule, kinematic walls, no mixed "
+                        "update and no tape");
+        }
+        g.ndom_total = (int)total;
+    }
     if (p.use_graph && p.timing) {
         delete s;
         return fail(nullptr, CD_ERR_INVALID_ARG, "use_graph needs timing 0 (a replayed step records no phase events)");
@@ -697,6 +737,8 @@ extern "C" cd_status cd_set_contacts(cd_system* s, int64_t nc, const int32_t* pa
                                 s->pos));
     k_error_gate<<<1, 1, 0, s->stream>>>(s->w.ctrl);
     if (s->g.dataflow) CD_CUDA(s, cd_launch_need(s->g, s->w, s->stream, &s->launches));
+    if (s->g.ndom_total > 1)
+        CD_CUDA(s, cd_launch_domains(s->g, s->w, s->pos, s->radius, s->stream, &s->launches));
     CdCtrl h;
     if ((st = read_ctrl(s, &h)) != CD_OK) return st;
     st = ctrl_status(s, h);

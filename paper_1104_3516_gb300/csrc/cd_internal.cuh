@@ -147,6 +147,17 @@ struct CdWork {
     int* cmp_blk;       // G: kept contacts per block
     int* cmp_off;       // CD_KMAX + 1: colour offsets after dropping
     double* c_dpar;     // cap * pw (key order): impulse change of a parallel contact
+    // domain-wise update (ndom_total > 1).  A particle whose contacts lie in
+    // several domains has one velocity record per domain: its own record for
+    // the lowest of them (its home), view records for the others (ascending
+    // domain), each with the velocity of the sweep start beside it.
+    int* dom_key;       // cap (key order): domain of each contact
+    int* dom_home;      // n: lowest domain among the particle's contacts
+    int* view_cnt;      // n + 1: view records of each particle
+    int* view_off;      // n + 1: exclusive offsets; view_off[n] = views in use
+    int* view_owner;    // 2 cap: particle of each view record
+    void* V0;           // 2 cap velocity records: the sweep-start velocity of the view's particle
+    int2* c_vab;        // cap (colour order): velocity records of bodies a and b
     double* obs;        // CD_OBS_MAX doubles: observable results
     // adjoint (params.tape_steps > 0)
     char* tape;         // tape_steps slots of CdTapeHdr + one step's records
@@ -238,7 +249,13 @@ struct CdGeom {
     int pad2;
     double wall_im[6];  // inverse mass of a force-controlled wall, else 0
     double wall_push[6];// its push along the inward normal
+    int ndom[3];        // domain-wise update (Sec. 3.1): slabs per axis (1: not cut)
+    int ndom_total;     // product; > 1 selects the domain-wise sweep
 };
+
+// Velocity records of the domain views start after the particles' and the
+// walls' records.
+__host__ __device__ __forceinline__ int cd_view_base(const CdGeom& g) { return g.n + 6; }
 
 // Body b takes part in conflicts and carries a velocity record: a particle or
 // a force-controlled wall (plain systems).
@@ -400,6 +417,8 @@ cudaError_t cd_launch_pack(const CdGeom& g, const CdWork& w, const double* vel, 
 cudaError_t cd_launch_order_tiled(const CdGeom& g, const CdWork& w, const double* pos, int precision, int pw,
                                   cudaStream_t stream, int* nl);
 cudaError_t cd_launch_need(const CdGeom& g, const CdWork& w, cudaStream_t stream, int* nl);
+cudaError_t cd_launch_domains(const CdGeom& g, const CdWork& w, const double* pos, const double* radius,
+                              cudaStream_t stream, int* nl);
 cudaError_t cd_launch_pk_ranges(const CdGeom& g, const CdWork& w, cudaStream_t stream, int* nl);
 cudaError_t cd_launch_orient(const CdGeom& g, const CdWork& w, int nbins, unsigned long long* counts,
                              cudaStream_t stream, int* nl);

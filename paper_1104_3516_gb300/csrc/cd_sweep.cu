@@ -22,6 +22,10 @@
 
 #include "cd_internal.cuh"
 
+// Variants of the persistent colour-barrier sweep: plain Gauss-Seidel, the
+// mixed update of Sec. 2.3, the domain-wise update of Sec. 3.1.
+enum { CD_SWEEP_PLAIN = 0, CD_SWEEP_MIXED = 1, CD_SWEEP_DOMAINS = 2 };
+
 template <typename T> struct Vec;
 template <> struct Vec<double> { typedef double4 V4; typedef double2 V2; };
 template <> struct Vec<float> { typedef float4 V4; typedef float2 V2; };
@@ -256,6 +260,7 @@ template <typename T> struct Rec<2, T> {
     T mt;
     T2 P;        // P_n, P_t before the update
     T4 sa, sb;   // inv_m, r, r/I, 0 (sb = 0 for a wall)
+    int2 vab;    // domain-wise update only: velocity records of a and b
 };
 template <typename T> struct Rec<3, T> {
     typedef typename Vec<T>::V4 T4;
@@ -267,9 +272,12 @@ template <typename T> struct Rec<3, T> {
     T2 m;        // m_n, m_t
     T4 P;        // P_n, P_tx, P_ty, P_tz before the update
     T4 sa, sb;
+    int2 vab;
 };
 
-template <int DIM, typename T>
+// VIEWS: the domain-wise update, whose contacts work on their domain's
+// velocity records (c_vab); otherwise the records are the bodies' own.
+template <int DIM, typename T, bool VIEWS = false>
 __device__ __forceinline__ void load_rec(const CdGeom& g, const CdWork& w, int pos, Rec<DIM, T>& r)
 {
     typedef typename Vec<T>::V4 T4;
@@ -297,6 +305,7 @@ __device__ __forceinline__ void load_rec(const CdGeom& g, const CdWork& w, int p
     } else {
         r.sb.x = (T)0; r.sb.y = (T)0; r.sb.z = (T)0; r.sb.w = (T)0;
     }
+    if constexpr (VIEWS) r.vab = w.c_vab[pos];
 }
 
 // max(x, 0) and the projection of x onto [-lim, lim] (lim >= 0).  For FP64
@@ -385,28 +394,30 @@ __device__ __forceinline__ void wall_vel2(const CdGeom& g, const CdWork& w, int 
     vb.x = (T)u[0]; vb.y = (T)u[1]; vb.z = (T)0; vb.w = (T)0;
 }
 
-template <typename T>
+// VIEWS: the bodies' velocity records are the domain views r.vab, else their own.
+template <typename T, bool VIEWS = false>
 __device__ __forceinline__ UpdOut apply2d(const CdGeom& g, const CdWork& w, int pos, const Rec<2, T>& r,
                                           bool apply_only, int crit, double alpha, double ravg_prev)
 {
     typedef typename Vec<T>::V4 T4;
     typedef typename Vec<T>::V2 T2;
     T4* V = (T4*)w.V;
+    const int ia = VIEWS ? r.vab.x : r.ab.x, ib = VIEWS ? r.vab.y : r.ab.y;
     const bool wall = !cd_is_body(g, r.ab.y);   // kinematic wall
-    T4 va = V[r.ab.x];
+    T4 va = V[ia];
     T4 vb;
-    if (!wall) vb = V[r.ab.y];
+    if (!wall) vb = V[ib];
     else wall_vel2<T>(g, w, r.ab.y, vb);
     T2 Pnew;
     UpdOut o = core2d<T>(g, r, va, vb, wall, apply_only, crit, alpha, ravg_prev, Pnew);
-    V[r.ab.x] = va;
+    V[ia] = va;
     if (!wall) {
         if (r.ab.y >= g.n) {
             // a force-controlled wall moves along its normal only
             if (((r.ab.y - g.n) >> 1) == 0) vb.y = (T)0; else vb.x = (T)0;
             vb.z = (T)0;
         }
-        V[r.ab.y] = vb;
+        V[ib] = vb;
     }
     if (!apply_only) ((T2*)w.c_P)[pos] = Pnew;
     return o;
@@ -478,20 +489,21 @@ __device__ __forceinline__ void wall_vel3(const CdGeom& g, const CdWork& w, int 
     wb.x = wb.y = wb.z = wb.w = (T)0;
 }
 
-template <typename T>
+template <typename T, bool VIEWS = false>
 __device__ __forceinline__ UpdOut apply3d(const CdGeom& g, const CdWork& w, int pos, const Rec<3, T>& r,
                                           bool apply_only, int crit, double alpha, double ravg_prev)
 {
     typedef typename Vec<T>::V4 T4;
     T4* V = (T4*)w.V;
+    const int ia = VIEWS ? r.vab.x : r.ab.x, ib = VIEWS ? r.vab.y : r.ab.y;
     const bool wall = !cd_is_body(g, r.ab.y);   // kinematic wall
-    T4 va = V[2 * r.ab.x], wa = V[2 * r.ab.x + 1];
+    T4 va = V[2 * ia], wa = V[2 * ia + 1];
     T4 vb, wb;
-    if (!wall) { vb = V[2 * r.ab.y]; wb = V[2 * r.ab.y + 1]; }
+    if (!wall) { vb = V[2 * ib]; wb = V[2 * ib + 1]; }
     else wall_vel3<T>(g, w, r.ab.y, vb, wb);
     T4 Pnew;
     UpdOut o = core3d<T>(g, r, va, wa, vb, wb, wall, apply_only, crit, alpha, ravg_prev, Pnew);
-    V[2 * r.ab.x] = va; V[2 * r.ab.x + 1] = wa;
+    V[2 * ia] = va; V[2 * ia + 1] = wa;
     if (!wall) {
         if (r.ab.y >= g.n) {
             // a force-controlled wall moves along its normal only
@@ -501,57 +513,59 @@ __device__ __forceinline__ UpdOut apply3d(const CdGeom& g, const CdWork& w, int 
             if (ax != 2) vb.z = (T)0;
             wb.x = wb.y = wb.z = (T)0;
         }
-        V[2 * r.ab.y] = vb; V[2 * r.ab.y + 1] = wb;
+        V[2 * ib] = vb; V[2 * ib + 1] = wb;
     }
     if (!apply_only) ((T4*)w.c_P)[pos] = Pnew;
     return o;
 }
 
-template <int DIM, typename T>
+template <int DIM, typename T, bool VIEWS = false>
 __device__ __forceinline__ UpdOut apply_rec(const CdGeom& g, const CdWork& w, int pos, const Rec<DIM, T>& r,
                                             bool apply_only, int crit, double alpha, double ravg_prev)
 {
-    if constexpr (DIM == 2) return apply2d<T>(g, w, pos, r, apply_only, crit, alpha, ravg_prev);
-    else return apply3d<T>(g, w, pos, r, apply_only, crit, alpha, ravg_prev);
+    if constexpr (DIM == 2) return apply2d<T, VIEWS>(g, w, pos, r, apply_only, crit, alpha, ravg_prev);
+    else return apply3d<T, VIEWS>(g, w, pos, r, apply_only, crit, alpha, ravg_prev);
 }
 
 // Loads this thread's first record of colour k (if it has one) into nxt.
-template <int DIM, typename T>
+template <int DIM, typename T, bool VIEWS = false>
 __device__ __forceinline__ void prefetch_first(const CdGeom& g, const CdWork& w, const int* s_off, int k,
                                                Rec<DIM, T>& nxt)
 {
     const CdSpan sq = cd_colour_span(s_off[k], s_off[k + 1]);
-    if (sq.p < sq.end) load_rec<DIM, T>(g, w, sq.p, nxt);
+    if (sq.p < sq.end) load_rec<DIM, T, VIEWS>(g, w, sq.p, nxt);
 }
 
 // One colour phase for this thread: its first contact's record was loaded
 // into `nxt` before the barrier (if it has one); the rest are loaded inline.
 // Afterwards `nxt` holds the first record of colour `knext` (prefetch).
-template <int DIM, typename T, bool MIXED>
+template <int DIM, typename T, int MODE>
 __device__ __forceinline__ void colour_phase(const CdGeom& g, const CdWork& w, const int* s_off, int k, int knext,
                                              int tid, int stride, Rec<DIM, T>& nxt, bool apply_only, int crit,
                                              double alpha, double ravg_prev, double (&acc)[3])
 {
+    constexpr bool MIXED = (MODE == CD_SWEEP_MIXED);
+    constexpr bool VIEWS = (MODE == CD_SWEEP_DOMAINS);
     const CdSpan sp = cd_colour_span(s_off[k], s_off[k + 1]);
     const int end = sp.end;
     int p = sp.p;
     const bool mixed = MIXED && !apply_only;   // parallel contacts were done in their own phase
     if (p < end) {
         if (!(mixed && cd_is_parallel(g.par_p, g.seed, cd_key(nxt.ab.x, nxt.ab.y)))) {
-            UpdOut o = apply_rec<DIM, T>(g, w, p, nxt, apply_only, crit, alpha, ravg_prev);
+            UpdOut o = apply_rec<DIM, T, VIEWS>(g, w, p, nxt, apply_only, crit, alpha, ravg_prev);
             acc[0] += o.pabs;
             if (crit == CD_CONV_LOCAL) { acc[1] += (double)o.rel_ok; acc[2] += (double)o.bad; }
         }
         for (p += blockDim.x; p < end; p += blockDim.x) {
             Rec<DIM, T> r;
-            load_rec<DIM, T>(g, w, p, r);
+            load_rec<DIM, T, VIEWS>(g, w, p, r);
             if (mixed && cd_is_parallel(g.par_p, g.seed, cd_key(r.ab.x, r.ab.y))) continue;
-            UpdOut o = apply_rec<DIM, T>(g, w, p, r, apply_only, crit, alpha, ravg_prev);
+            UpdOut o = apply_rec<DIM, T, VIEWS>(g, w, p, r, apply_only, crit, alpha, ravg_prev);
             acc[0] += o.pabs;
             if (crit == CD_CONV_LOCAL) { acc[1] += (double)o.rel_ok; acc[2] += (double)o.bad; }
         }
     }
-    if (knext >= 0) prefetch_first<DIM, T>(g, w, s_off, knext, nxt);
+    if (knext >= 0) prefetch_first<DIM, T, VIEWS>(g, w, s_off, knext, nxt);
     (void)tid; (void)stride;
 }
 
@@ -703,13 +717,77 @@ __device__ __forceinline__ void par_apply(const CdGeom& g, const CdWork& w, int 
 }
 
 // ---------------------------------------------------------------------------
+// Domain-wise update (Sec. 3.1).  Each contact updates the velocity records
+// of its domain (c_vab).  Before the first pass every view record takes its
+// particle's velocity; after every pass (the starting impulses, then each
+// sweep) a particle with views gets v0 + (v_home - v0) + sum over its views
+// in ascending domain order of (v_view - v0), v0 being the velocity of the
+// pass start, and every view starts the next pass from that sum.
+// ---------------------------------------------------------------------------
+template <int DIM, typename T>
+__device__ __forceinline__ void dom_init(const CdGeom& g, const CdWork& w, int tid, int stride)
+{
+    typedef typename Vec<T>::V4 T4;
+    constexpr int RW = (DIM == 2) ? 1 : 2;   // records per body
+    T4* V = (T4*)w.V;
+    T4* V0 = (T4*)w.V0;
+    const int nv = w.view_off[g.n], base = cd_view_base(g);
+    for (int q = tid; q < nv; q += stride) {
+        const int i = w.view_owner[q];
+#pragma unroll
+        for (int h = 0; h < RW; ++h) {
+            const T4 x = V[RW * i + h];
+            V[RW * (base + q) + h] = x;
+            V0[RW * q + h] = x;
+        }
+    }
+}
+
+template <int DIM, typename T>
+__device__ __forceinline__ void dom_combine(const CdGeom& g, const CdWork& w, int tid, int stride)
+{
+    typedef typename Vec<T>::V4 T4;
+    constexpr int RW = (DIM == 2) ? 1 : 2;
+    T4* V = (T4*)w.V;
+    T4* V0 = (T4*)w.V0;
+    const int nv = w.view_off[g.n], base = cd_view_base(g);
+    for (int q = tid; q < nv; q += stride) {
+        const int i = w.view_owner[q];
+        if (q != w.view_off[i]) continue;   // one thread per particle: its first view
+        const int e = w.view_off[i + 1];
+#pragma unroll
+        for (int h = 0; h < RW; ++h) {
+            const T4 s0 = V0[RW * q + h];
+            T4 x = V[RW * i + h];
+            T sx = s0.x + (x.x - s0.x), sy = s0.y + (x.y - s0.y), sz = s0.z + (x.z - s0.z);
+            for (int u = q; u < e; ++u) {
+                const T4 a = V[RW * (base + u) + h];
+                sx = sx + (a.x - s0.x);
+                sy = sy + (a.y - s0.y);
+                sz = sz + (a.z - s0.z);
+            }
+            x.x = sx; x.y = sy; x.z = sz;
+            V[RW * i + h] = x;
+            for (int u = q; u < e; ++u) {
+                V[RW * (base + u) + h] = x;
+                V0[RW * u + h] = x;
+            }
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
 // The persistent sweep kernel
 // ---------------------------------------------------------------------------
-// MIXED: the mixed update of Sec. 2.3 is compiled in (params.parallel_p > 0).
-template <int DIM, typename T, bool MIXED>
+// MODE: CD_SWEEP_PLAIN, CD_SWEEP_MIXED (the mixed update of Sec. 2.3,
+// params.parallel_p > 0) or CD_SWEEP_DOMAINS (the domain-wise update of
+// Sec. 3.1, params.domains); each variant carries only its own code.
+template <int DIM, typename T, int MODE>
 __global__ void __launch_bounds__(CD_SWEEP_THREADS, 1)
 k_sweep(CdGeom g, CdWork w, int crit, double alpha, int max_sweeps)
 {
+    constexpr bool MIXED = (MODE == CD_SWEEP_MIXED);
+    constexpr bool VIEWS = (MODE == CD_SWEEP_DOMAINS);
     __shared__ int s_off[CD_KMAX + 1];
     __shared__ double s_red[CD_SWEEP_THREADS / 32][3];
     __shared__ double s_bc;
@@ -727,20 +805,28 @@ k_sweep(CdGeom g, CdWork w, int crit, double alpha, int max_sweeps)
     int sweeps = 0, converged = (nc == 0);
     double resid = 0.0, ravg = 0.0, ravg_prev = 0.0;
     if (nc > 0) {
+        if constexpr (VIEWS) {
+            dom_init<DIM, T>(g, w, tid, stride);
+            if (!cd_grid_sync(ctrl, nb, epoch)) return;
+        }
         Rec<DIM, T> nxt;
         {
             const CdSpan s0 = cd_colour_span(s_off[0], s_off[1]);
-            if (s0.p < s0.end) load_rec<DIM, T>(g, w, s0.p, nxt);
+            if (s0.p < s0.end) load_rec<DIM, T, VIEWS>(g, w, s0.p, nxt);
         }
         // starting impulses, colour by colour
         double acc[3] = {0.0, 0.0, 0.0};
         for (int k = 0; k < K; ++k) {
-            colour_phase<DIM, T, MIXED>(g, w, s_off, k, (k + 1 < K) ? k + 1 : 0, tid, stride, nxt, true, crit, alpha, 0.0,
-                                 acc);
+            colour_phase<DIM, T, MODE>(g, w, s_off, k, (k + 1 < K) ? k + 1 : 0, tid, stride, nxt, true, crit, alpha,
+                                       0.0, acc);
             if (k == K - 1) {
                 block_sum<3>(acc, s_red);
                 if (threadIdx.x == 0) w.partials[blockIdx.x] = acc[0];
             }
+            if (!cd_grid_sync(ctrl, nb, epoch)) return;
+        }
+        if constexpr (VIEWS) {
+            dom_combine<DIM, T>(g, w, tid, stride);
             if (!cd_grid_sync(ctrl, nb, epoch)) return;
         }
         ravg_prev = grid_total(w.partials, nb, &s_bc) / (double)nc;
@@ -769,7 +855,7 @@ k_sweep(CdGeom g, CdWork w, int crit, double alpha, int max_sweeps)
             for (int k = 0; k < K; ++k) {
                 // no prefetch inside the phase: it is issued after the barrier arrival
                 // below, so that the arriving thread's fence does not wait for it
-                colour_phase<DIM, T, MIXED>(g, w, s_off, k, -1, tid, stride, nxt, false, crit, alpha, ravg_prev, a3);
+                colour_phase<DIM, T, MODE>(g, w, s_off, k, -1, tid, stride, nxt, false, crit, alpha, ravg_prev, a3);
                 if (mixed && k == K - 1) {
                     if (!cd_grid_sync(ctrl, nb, epoch)) return;
                     par_apply<DIM, T>(g, w, tid, stride);
@@ -783,8 +869,12 @@ k_sweep(CdGeom g, CdWork w, int crit, double alpha, int max_sweeps)
                     }
                 }
                 const unsigned old = cd_grid_arrive(ctrl, nb);
-                if (!mixed || k + 1 < K) prefetch_first<DIM, T>(g, w, s_off, (k + 1 < K) ? k + 1 : 0, nxt);
+                if (!mixed || k + 1 < K) prefetch_first<DIM, T, VIEWS>(g, w, s_off, (k + 1 < K) ? k + 1 : 0, nxt);
                 if (!cd_grid_wait(ctrl, old, epoch)) return;
+            }
+            if constexpr (VIEWS) {
+                dom_combine<DIM, T>(g, w, tid, stride);
+                if (!cd_grid_sync(ctrl, nb, epoch)) return;
             }
             ++sweeps;
             ravg = grid_total(part, nb, &s_bc) / (double)nc;
@@ -1613,12 +1703,33 @@ cudaError_t cd_launch_unpack(const CdGeom& g, const CdWork& w, double* pos, doub
     return cudaGetLastError();
 }
 
+// Kernel of each schedule: 0 colour barrier, 1 tiled, 2 dataflow, 3 batched,
+// 4 mixed update, 5 domain-wise update.
+static int sweep_kind(const CdGeom& g)
+{
+    if (g.npk > 1) return 3;
+    if (g.tile_cells >= 2) return 1;
+    if (g.dataflow) return 2;
+    if (g.par_p > 0.0) return 4;
+    if (g.ndom_total > 1) return 5;
+    return 0;
+}
+
 static const void* sweep_fn(int dim, int precision, int tiled)
 {
+    if (tiled == 5) {
+        if (dim == 2)
+            return precision == CD_FP64 ? (const void*)k_sweep<2, double, CD_SWEEP_DOMAINS>
+                                        : (const void*)k_sweep<2, float, CD_SWEEP_DOMAINS>;
+        return precision == CD_FP64 ? (const void*)k_sweep<3, double, CD_SWEEP_DOMAINS>
+                                    : (const void*)k_sweep<3, float, CD_SWEEP_DOMAINS>;
+    }
     if (tiled == 4) {
         if (dim == 2)
-            return precision == CD_FP64 ? (const void*)k_sweep<2, double, true> : (const void*)k_sweep<2, float, true>;
-        return precision == CD_FP64 ? (const void*)k_sweep<3, double, true> : (const void*)k_sweep<3, float, true>;
+            return precision == CD_FP64 ? (const void*)k_sweep<2, double, CD_SWEEP_MIXED>
+                                        : (const void*)k_sweep<2, float, CD_SWEEP_MIXED>;
+        return precision == CD_FP64 ? (const void*)k_sweep<3, double, CD_SWEEP_MIXED>
+                                    : (const void*)k_sweep<3, float, CD_SWEEP_MIXED>;
     }
     if (tiled == 3) {
         if (dim == 2)
@@ -1636,8 +1747,10 @@ static const void* sweep_fn(int dim, int precision, int tiled)
         return precision == CD_FP64 ? (const void*)k_sweep_tiled<3, double> : (const void*)k_sweep_tiled<3, float>;
     }
     if (dim == 2)
-        return precision == CD_FP64 ? (const void*)k_sweep<2, double, false> : (const void*)k_sweep<2, float, false>;
-    return precision == CD_FP64 ? (const void*)k_sweep<3, double, false> : (const void*)k_sweep<3, float, false>;
+        return precision == CD_FP64 ? (const void*)k_sweep<2, double, CD_SWEEP_PLAIN>
+                                    : (const void*)k_sweep<2, float, CD_SWEEP_PLAIN>;
+    return precision == CD_FP64 ? (const void*)k_sweep<3, double, CD_SWEEP_PLAIN>
+                                : (const void*)k_sweep<3, float, CD_SWEEP_PLAIN>;
 }
 
 static size_t tile_smem(int dim, int precision)
@@ -1651,7 +1764,7 @@ static size_t tile_smem(int dim, int precision)
 int cd_sweep_max_blocks(int precision, int dim, int num_sms)
 {
     int per_sm = 0;
-    for (int tiled = 0; tiled < 5; ++tiled) {
+    for (int tiled = 0; tiled < 6; ++tiled) {
         const void* fn = sweep_fn(dim, precision, tiled);
         size_t dyn = (tiled == 1) ? tile_smem(dim, precision) : 0;
         if (tiled && cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn) != cudaSuccess)
@@ -1668,7 +1781,7 @@ int cd_sweep_max_blocks(int precision, int dim, int num_sms)
 // uses can be resident on one SM.
 int cd_sweep_fits(const CdGeom& g, int precision, int threads, int per_sm)
 {
-    const int kind = (g.npk > 1) ? 3 : ((g.tile_cells >= 2) ? 1 : (g.dataflow ? 2 : (g.par_p > 0.0 ? 4 : 0)));
+    const int kind = sweep_kind(g);
     int b = 0;
     const size_t dyn = (kind == 1) ? tile_smem(g.dim, precision) : 0;
     if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, sweep_fn(g.dim, precision, kind), threads, dyn) !=
@@ -1689,7 +1802,7 @@ cudaError_t cd_launch_sweep(const CdGeom& g, const CdWork& w, int coop_blocks, i
     double al = alpha;
     int ms = max_sweeps;
     void* args[] = {&ga, &wa, &crit, &al, &ms};
-    const int kind = (g.npk > 1) ? 3 : ((g.tile_cells >= 2) ? 1 : (g.dataflow ? 2 : (g.par_p > 0.0 ? 4 : 0)));
+    const int kind = sweep_kind(g);
     ++*nl;
     return cudaLaunchCooperativeKernel(sweep_fn(g.dim, precision, kind), dim3(coop_blocks), dim3(threads),
                                        args, kind == 1 ? tile_smem(g.dim, precision) : 0, s);
