@@ -244,7 +244,8 @@ __device__ __forceinline__ double grid_total(const double* part, int nblocks, do
 // the velocity loads sit on the critical path after it.
 // ---------------------------------------------------------------------------
 struct UpdOut {
-    double pabs;     // |P| after the update
+    double pabs;     // |P| after the update (deferred form: |P| of the thread's previous update)
+    double psq;      // deferred form: |P|^2 after the update
     int rel_ok;      // local test (I), relative branch
     int bad;         // local test (I): fails both branches
 };
@@ -335,10 +336,20 @@ __device__ __forceinline__ double norm_of_sq(double s)
     return s > 0.0 ? s * rsqrt(s) : 0.0;
 }
 
+// |P| from the |P|^2 an update left (in the sweep's real type: FP32 impulses
+// carry 1e-7 anyway, their magnitude is taken in FP32).  The persistent FP64
+// 2D sweep defers it: a thread takes the magnitude of its previous update
+// while the velocity loads of its next one are in flight, when the narrow
+// FP64 pipe has nothing else to do; the per-thread sum sees the same terms in
+// the same order, so the residual is bit-identical.
+template <typename T> __device__ __forceinline__ double abs_of_sq(double s);
+template <> __device__ __forceinline__ double abs_of_sq<double>(double s) { return norm_of_sq(s); }
+template <> __device__ __forceinline__ double abs_of_sq<float>(double s) { return (double)sqrtf((float)s); }
+
 // 2D: P_n = max(0, P_n,old - m_n (b + u_n)); P_t = clamp(P_t,old - m_t u_t, +-mu P_n).
 // The core works on the two bodies' velocity records wherever they live
 // (global memory or a tile's shared-memory table).
-template <typename T>
+template <typename T, bool SQ = false>
 __device__ __forceinline__ UpdOut core2d(const CdGeom& g, const Rec<2, T>& r, typename Vec<T>::V4& va,
                                          typename Vec<T>::V4& vb, bool wall, bool apply_only, int crit,
                                          double alpha, double ravg_prev, typename Vec<T>::V2& Pnew)
@@ -366,9 +377,10 @@ __device__ __forceinline__ UpdOut core2d(const CdGeom& g, const Rec<2, T>& r, ty
     Pnew.x = Pn; Pnew.y = Pt;
     UpdOut o;
     double pn = (double)Pn, pt = (double)Pt;
-    // FP32 impulses carry 1e-7 anyway: their magnitude is taken in FP32 (the sum stays FP64)
-    if constexpr (sizeof(T) == 4) o.pabs = (double)sqrtf(Pn * Pn + Pt * Pt);
-    else o.pabs = norm_of_sq(pn * pn + pt * pt);
+    // SQ: |P|^2 only, the magnitude is taken later (abs_of_sq)
+    if constexpr (sizeof(T) == 4) o.psq = (double)(Pn * Pn + Pt * Pt);
+    else o.psq = pn * pn + pt * pt;
+    o.pabs = SQ ? 0.0 : abs_of_sq<T>(o.psq);
     o.rel_ok = 0; o.bad = 0;
     if (!apply_only && crit == CD_CONV_LOCAL) {
         double d0 = (double)dPn, d1 = (double)dPt;
@@ -395,9 +407,13 @@ __device__ __forceinline__ void wall_vel2(const CdGeom& g, const CdWork& w, int 
 }
 
 // VIEWS: the bodies' velocity records are the domain views r.vab, else their own.
-template <typename T, bool VIEWS = false>
+// DEFER: the result's pabs is |P| of the thread's previous update, taken from
+// its |P|^2 `pend` after this update's velocity loads are issued; psq holds
+// this update's |P|^2.
+template <typename T, bool VIEWS = false, bool DEFER = false>
 __device__ __forceinline__ UpdOut apply2d(const CdGeom& g, const CdWork& w, int pos, const Rec<2, T>& r,
-                                          bool apply_only, int crit, double alpha, double ravg_prev)
+                                          bool apply_only, int crit, double alpha, double ravg_prev,
+                                          double pend = 0.0)
 {
     typedef typename Vec<T>::V4 T4;
     typedef typename Vec<T>::V2 T2;
@@ -408,8 +424,10 @@ __device__ __forceinline__ UpdOut apply2d(const CdGeom& g, const CdWork& w, int 
     T4 vb;
     if (!wall) vb = V[ib];
     else wall_vel2<T>(g, w, r.ab.y, vb);
+    const double prev = DEFER ? abs_of_sq<T>(pend) : 0.0;
     T2 Pnew;
-    UpdOut o = core2d<T>(g, r, va, vb, wall, apply_only, crit, alpha, ravg_prev, Pnew);
+    UpdOut o = core2d<T, DEFER>(g, r, va, vb, wall, apply_only, crit, alpha, ravg_prev, Pnew);
+    if constexpr (DEFER) o.pabs = prev;
     V[ia] = va;
     if (!wall) {
         if (r.ab.y >= g.n) {
@@ -424,7 +442,7 @@ __device__ __forceinline__ UpdOut apply2d(const CdGeom& g, const CdWork& w, int 
 }
 
 // 3D: the same with the tangential impulse a vector, scaled onto the cone.
-template <typename T>
+template <typename T, bool SQ = false>
 __device__ __forceinline__ UpdOut core3d(const CdGeom& g, const Rec<3, T>& r, typename Vec<T>::V4& va,
                                          typename Vec<T>::V4& wa, typename Vec<T>::V4& vb, typename Vec<T>::V4& wb,
                                          bool wall, bool apply_only, int crit, double alpha, double ravg_prev,
@@ -466,8 +484,9 @@ __device__ __forceinline__ UpdOut core3d(const CdGeom& g, const Rec<3, T>& r, ty
     Pnew.x = Pn; Pnew.y = Ptx; Pnew.z = Pty; Pnew.w = Ptz;
     UpdOut o;
     double pn = (double)Pn, px = (double)Ptx, py = (double)Pty, pz = (double)Ptz;
-    if constexpr (sizeof(T) == 4) o.pabs = (double)sqrtf(Pn * Pn + Ptx * Ptx + Pty * Pty + Ptz * Ptz);
-    else o.pabs = norm_of_sq(pn * pn + px * px + py * py + pz * pz);
+    if constexpr (sizeof(T) == 4) o.psq = (double)(Pn * Pn + Ptx * Ptx + Pty * Pty + Ptz * Ptz);
+    else o.psq = pn * pn + px * px + py * py + pz * pz;
+    o.pabs = SQ ? 0.0 : abs_of_sq<T>(o.psq);
     o.rel_ok = 0; o.bad = 0;
     if (!apply_only && crit == CD_CONV_LOCAL) {
         double d0 = (double)dPn, d1 = (double)dtx, d2_ = (double)dty, d3 = (double)dtz;
@@ -489,9 +508,10 @@ __device__ __forceinline__ void wall_vel3(const CdGeom& g, const CdWork& w, int 
     wb.x = wb.y = wb.z = wb.w = (T)0;
 }
 
-template <typename T, bool VIEWS = false>
+template <typename T, bool VIEWS = false, bool DEFER = false>
 __device__ __forceinline__ UpdOut apply3d(const CdGeom& g, const CdWork& w, int pos, const Rec<3, T>& r,
-                                          bool apply_only, int crit, double alpha, double ravg_prev)
+                                          bool apply_only, int crit, double alpha, double ravg_prev,
+                                          double pend = 0.0)
 {
     typedef typename Vec<T>::V4 T4;
     T4* V = (T4*)w.V;
@@ -501,8 +521,10 @@ __device__ __forceinline__ UpdOut apply3d(const CdGeom& g, const CdWork& w, int 
     T4 vb, wb;
     if (!wall) { vb = V[2 * ib]; wb = V[2 * ib + 1]; }
     else wall_vel3<T>(g, w, r.ab.y, vb, wb);
+    const double prev = DEFER ? abs_of_sq<T>(pend) : 0.0;
     T4 Pnew;
-    UpdOut o = core3d<T>(g, r, va, wa, vb, wb, wall, apply_only, crit, alpha, ravg_prev, Pnew);
+    UpdOut o = core3d<T, DEFER>(g, r, va, wa, vb, wb, wall, apply_only, crit, alpha, ravg_prev, Pnew);
+    if constexpr (DEFER) o.pabs = prev;
     V[2 * ia] = va; V[2 * ia + 1] = wa;
     if (!wall) {
         if (r.ab.y >= g.n) {
@@ -519,12 +541,14 @@ __device__ __forceinline__ UpdOut apply3d(const CdGeom& g, const CdWork& w, int 
     return o;
 }
 
-template <int DIM, typename T, bool VIEWS = false>
+template <int DIM, typename T, bool VIEWS = false, bool DEFER = false>
 __device__ __forceinline__ UpdOut apply_rec(const CdGeom& g, const CdWork& w, int pos, const Rec<DIM, T>& r,
-                                            bool apply_only, int crit, double alpha, double ravg_prev)
+                                            bool apply_only, int crit, double alpha, double ravg_prev,
+                                            double pend = 0.0)
 {
-    if constexpr (DIM == 2) return apply2d<T, VIEWS>(g, w, pos, r, apply_only, crit, alpha, ravg_prev);
-    else return apply3d<T, VIEWS>(g, w, pos, r, apply_only, crit, alpha, ravg_prev);
+    if constexpr (DIM == 2)
+        return apply2d<T, VIEWS, DEFER>(g, w, pos, r, apply_only, crit, alpha, ravg_prev, pend);
+    else return apply3d<T, VIEWS, DEFER>(g, w, pos, r, apply_only, crit, alpha, ravg_prev, pend);
 }
 
 // Loads this thread's first record of colour k (if it has one) into nxt.
@@ -539,29 +563,37 @@ __device__ __forceinline__ void prefetch_first(const CdGeom& g, const CdWork& w,
 // One colour phase for this thread: its first contact's record was loaded
 // into `nxt` before the barrier (if it has one); the rest are loaded inline.
 // Afterwards `nxt` holds the first record of colour `knext` (prefetch).
+// `pend` carries the |P|^2 of the thread's last update whose magnitude is not
+// yet in acc[0] (0 if none) from phase to phase; the caller adds it before
+// the block sum at the end of a pass.
 template <int DIM, typename T, int MODE>
 __device__ __forceinline__ void colour_phase(const CdGeom& g, const CdWork& w, const int* s_off, int k, int knext,
                                              int tid, int stride, Rec<DIM, T>& nxt, bool apply_only, int crit,
-                                             double alpha, double ravg_prev, double (&acc)[3])
+                                             double alpha, double ravg_prev, double (&acc)[3], double& pend)
 {
     constexpr bool MIXED = (MODE == CD_SWEEP_MIXED);
     constexpr bool VIEWS = (MODE == CD_SWEEP_DOMAINS);
+    // FP64 2D only: FP32 takes its square root on the fast pipe, and in 3D the
+    // extra live value spills
+    constexpr bool DEFER = (DIM == 2) && std::is_same<T, double>::value;
     const CdSpan sp = cd_colour_span(s_off[k], s_off[k + 1]);
     const int end = sp.end;
     int p = sp.p;
     const bool mixed = MIXED && !apply_only;   // parallel contacts were done in their own phase
     if (p < end) {
         if (!(mixed && cd_is_parallel(g.par_p, g.seed, cd_key(nxt.ab.x, nxt.ab.y)))) {
-            UpdOut o = apply_rec<DIM, T, VIEWS>(g, w, p, nxt, apply_only, crit, alpha, ravg_prev);
+            UpdOut o = apply_rec<DIM, T, VIEWS, DEFER>(g, w, p, nxt, apply_only, crit, alpha, ravg_prev, pend);
             acc[0] += o.pabs;
+            if (DEFER) pend = o.psq;
             if (crit == CD_CONV_LOCAL) { acc[1] += (double)o.rel_ok; acc[2] += (double)o.bad; }
         }
         for (p += blockDim.x; p < end; p += blockDim.x) {
             Rec<DIM, T> r;
             load_rec<DIM, T, VIEWS>(g, w, p, r);
             if (mixed && cd_is_parallel(g.par_p, g.seed, cd_key(r.ab.x, r.ab.y))) continue;
-            UpdOut o = apply_rec<DIM, T, VIEWS>(g, w, p, r, apply_only, crit, alpha, ravg_prev);
+            UpdOut o = apply_rec<DIM, T, VIEWS, DEFER>(g, w, p, r, apply_only, crit, alpha, ravg_prev, pend);
             acc[0] += o.pabs;
+            if (DEFER) pend = o.psq;
             if (crit == CD_CONV_LOCAL) { acc[1] += (double)o.rel_ok; acc[2] += (double)o.bad; }
         }
     }
@@ -816,10 +848,13 @@ k_sweep(CdGeom g, CdWork w, int crit, double alpha, int max_sweeps)
         }
         // starting impulses, colour by colour
         double acc[3] = {0.0, 0.0, 0.0};
+        double pend = 0.0;   // |P|^2 of this thread's last update not yet in the residual sum
         for (int k = 0; k < K; ++k) {
             colour_phase<DIM, T, MODE>(g, w, s_off, k, (k + 1 < K) ? k + 1 : 0, tid, stride, nxt, true, crit, alpha,
-                                       0.0, acc);
+                                       0.0, acc, pend);
             if (k == K - 1) {
+                acc[0] += abs_of_sq<T>(pend);
+                pend = 0.0;
                 block_sum<3>(acc, s_red);
                 if (threadIdx.x == 0) w.partials[blockIdx.x] = acc[0];
             }
@@ -855,7 +890,12 @@ k_sweep(CdGeom g, CdWork w, int crit, double alpha, int max_sweeps)
             for (int k = 0; k < K; ++k) {
                 // no prefetch inside the phase: it is issued after the barrier arrival
                 // below, so that the arriving thread's fence does not wait for it
-                colour_phase<DIM, T, MODE>(g, w, s_off, k, -1, tid, stride, nxt, false, crit, alpha, ravg_prev, a3);
+                colour_phase<DIM, T, MODE>(g, w, s_off, k, -1, tid, stride, nxt, false, crit, alpha, ravg_prev, a3,
+                                           pend);
+                if (k == K - 1) {
+                    a3[0] += abs_of_sq<T>(pend);
+                    pend = 0.0;
+                }
                 if (mixed && k == K - 1) {
                     if (!cd_grid_sync(ctrl, nb, epoch)) return;
                     par_apply<DIM, T>(g, w, tid, stride);
