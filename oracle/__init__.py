@@ -120,6 +120,8 @@ def lib():
                                                   P(d), P(d), P(d), P(d)]
             _lib.ora_colour_greedy.restype = C.c_int
             _lib.ora_colour_greedy.argtypes = [i64, i64, P(i32), C.c_uint64, C.c_int64, P(i32)]
+            _lib.ora_colour_repair.restype = C.c_int
+            _lib.ora_colour_repair.argtypes = [i64, i64, P(i32), C.c_int64, P(i32)]
             _lib.ora_solve.restype = C.c_int
             _lib.ora_solve.argtypes = [P(Params), i64, P(d), P(d), P(d), P(d), P(d), i64, P(i32), P(d), P(d),
                                        P(d), P(d), P(i32), P(C.c_int64), P(i32), P(i32), i64, P(d), P(d),
@@ -228,14 +230,27 @@ def contact_geometry(p: Params, x, r, inv_m, inv_I, wall_pos, pairs):
 
 def colour_greedy(n, pairs, seed, dyn_walls=0):
     """Greedy colouring in descending priority (largest degree first, then the
-    splitmix64 hash); dyn_walls: bit k for a force-controlled wall k, whose
-    contacts conflict.  Returns (colour, K)."""
+    splitmix64 hash), then the Kempe-chain repair of its highest colour
+    (:func:`colour_repair`); dyn_walls: bit k for a force-controlled wall k,
+    whose contacts conflict.  Returns (colour, K)."""
     pairs = np.ascontiguousarray(pairs, dtype=np.int32)
     nc = pairs.shape[0]
     colour = np.zeros(max(nc, 1), dtype=np.int32)
     K = lib().ora_colour_greedy(n, nc, _ptr(pairs, C.c_int32), C.c_uint64(int(seed) & (2**64 - 1)),
                                 int(dyn_walls), _ptr(colour, C.c_int32))
     return colour[:nc], int(K)
+
+
+def colour_repair(n, pairs, colour, dyn_walls=0):
+    """Kempe-chain repair of the highest colour of a proper contact colouring
+    (see ora_colour_repair); returns (new colour, K)."""
+    pairs = np.ascontiguousarray(pairs, dtype=np.int32)
+    nc = pairs.shape[0]
+    col = np.ascontiguousarray(colour, dtype=np.int32).copy()
+    if nc == 0:
+        return col, 0
+    K = lib().ora_colour_repair(n, nc, _ptr(pairs, C.c_int32), int(dyn_walls), _ptr(col, C.c_int32))
+    return col[:nc], int(K)
 
 
 def tile_colour(p: Params, x, r, pairs):

@@ -22,7 +22,9 @@
  *     sliding force (Eqs. 9-11), written in impulses P = R dt;
  *   - the iterative nonlinear Gauss-Seidel over the contact network
  *     (Sec. 2.1): random sequential order re-drawn every sweep, a fixed
- *     order, or the colour order used by the GPU; the mixed parallel /
+ *     order, or the colour order used by the GPU (greedy colouring of the
+ *     contact graph with a Kempe-chain repair of its highest colour; not in
+ *     the paper, a definition the GPU must reproduce); the mixed parallel /
  *     sequential update with parallelness p (Sec. 2.3); the domain-wise
  *     update of the parallel algorithm (Sec. 3.1), where every domain sweeps
  *     its own contacts while the other domains' contacts keep the impulses
@@ -359,13 +361,117 @@ static int cmp_prio(const void* u, const void* v)
 
 static int colour_greedy_in(long long n, long long nc, const int32_t* pairs, uint64_t seed,
                             const int64_t* tile, int64_t dyn_walls, int32_t* colour);
+int ora_colour_repair(long long n, long long nc, const int32_t* pairs, int64_t dyn_walls, int32_t* colour);
 
 /* dyn_walls: bit k set when wall k is a force-controlled body, whose
- * contacts then conflict with each other like those of a particle. */
+ * contacts then conflict with each other like those of a particle.  The
+ * greedy colouring is followed by the repair of its highest colour
+ * (ora_colour_repair). */
 int ora_colour_greedy(long long n, long long nc, const int32_t* pairs, uint64_t seed, int64_t dyn_walls,
                       int32_t* colour)
 {
-    return colour_greedy_in(n, nc, pairs, seed, NULL, dyn_walls, colour);
+    colour_greedy_in(n, nc, pairs, seed, NULL, dyn_walls, colour);
+    return ora_colour_repair(n, nc, pairs, dyn_walls, colour);
+}
+
+/* ------------------------------------------------------------------------ */
+/* Repair of the highest colour by Kempe chains (the recolouring step of    */
+/* the classical proof of Vizing's theorem, used here as a heuristic).  Let */
+/* T be the highest colour and D the largest number of contacts of one      */
+/* body.  If T + 1 > D (a colour more than any body needs) and colour T     */
+/* holds at most max(1, min(1024, nc / 256)) contacts, those contacts are   */
+/* visited one by one in ascending key order.  For contact c = (u, v), let  */
+/* M(x) be the colours below T that no other contact of body x has (all of */
+/* them for a wall that is not a body).  If M(u) and M(v) share a colour, c */
+/* takes the smallest.  Otherwise, for a in M(u) and then b in M(v), both   */
+/* ascending: follow from v the path whose contacts alternate colours a, b, */
+/* starting with v's contact of colour a, until a body has no contact of    */
+/* the next colour or the path reaches a wall; if the path reaches u, try   */
+/* the next pair; else swap a and b along it (the colouring stays proper    */
+/* and a is now free at v) and give c colour a.  A contact for which no     */
+/* pair works keeps colour T.  Returns the number of colours afterwards.    */
+/* ------------------------------------------------------------------------ */
+int ora_colour_repair(long long n, long long nc, const int32_t* pairs, int64_t dyn_walls, int32_t* colour)
+{
+    if (nc <= 0) return 0;
+#define CONFLICTS(q) ((q) < n || ((dyn_walls >> ((q) - n)) & 1))
+    int kmax = 0;
+    for (long long c = 0; c < nc; ++c) if (colour[c] + 1 > kmax) kmax = colour[c] + 1;
+    const int T = kmax - 1;
+    if (T <= 0 || T > 63) return kmax;
+    const long long nb = n + 6;
+    long long* deg = (long long*)calloc((size_t)nb + 1, sizeof(long long));
+    for (long long c = 0; c < nc; ++c)
+        for (int s = 0; s < 2; ++s) {
+            long long q = pairs[2 * c + s];
+            if (CONFLICTS(q)) deg[q + 1]++;
+        }
+    long long dmax = 0;
+    for (long long i = 0; i < nb; ++i) if (deg[i + 1] > dmax) dmax = deg[i + 1];
+    long long top = 0;
+    for (long long c = 0; c < nc; ++c) top += (colour[c] == T);
+    long long limit = nc / 256;
+    if (limit > 1024) limit = 1024;
+    if (limit < 1) limit = 1;
+    if ((long long)kmax <= dmax || top > limit) { free(deg); return kmax; }
+    for (long long i = 0; i < nb; ++i) deg[i + 1] += deg[i];
+    long long* fill = (long long*)calloc((size_t)nb, sizeof(long long));
+    long long* adj = (long long*)malloc(sizeof(long long) * (size_t)(deg[nb] > 0 ? deg[nb] : 1));
+    for (long long c = 0; c < nc; ++c)
+        for (int s = 0; s < 2; ++s) {
+            long long q = pairs[2 * c + s];
+            if (CONFLICTS(q)) adj[deg[q] + fill[q]++] = c;
+        }
+    long long* path = (long long*)malloc(sizeof(long long) * (size_t)nc);
+    const uint64_t below = (1ULL << T) - 1ULL;
+    for (long long c = 0; c < nc; ++c) {
+        if (colour[c] != T) continue;
+        const long long u = pairs[2 * c], v = pairs[2 * c + 1];
+        uint64_t mu = below, mv = below;
+        for (long long e = deg[u]; e < deg[u + 1]; ++e)
+            if (adj[e] != c && colour[adj[e]] < T) mu &= ~(1ULL << colour[adj[e]]);
+        if (CONFLICTS(v))
+            for (long long e = deg[v]; e < deg[v + 1]; ++e)
+                if (adj[e] != c && colour[adj[e]] < T) mv &= ~(1ULL << colour[adj[e]]);
+        if (mu & mv) {
+            int k = 0;
+            while (!((mu & mv) >> k & 1ULL)) ++k;
+            colour[c] = k;
+            continue;
+        }
+        if (!CONFLICTS(v)) continue;
+        int done = 0;
+        for (int a = 0; a < T && !done; ++a) {
+            if (!(mu >> a & 1ULL)) continue;
+            for (int b = 0; b < T && !done; ++b) {
+                if (!(mv >> b & 1ULL)) continue;
+                long long len = 0, x = v;
+                int cur = a, fail = 0;
+                for (;;) {
+                    long long e = -1;
+                    for (long long f = deg[x]; f < deg[x + 1]; ++f)
+                        if (colour[adj[f]] == cur) { e = adj[f]; break; }
+                    if (e < 0) break;
+                    long long y = (pairs[2 * e] == x) ? pairs[2 * e + 1] : pairs[2 * e];
+                    path[len++] = e;
+                    if (y == u) { fail = 1; break; }
+                    if (!CONFLICTS(y)) break;
+                    x = y;
+                    cur = (cur == a) ? b : a;
+                    if (len >= nc) { fail = 1; break; }
+                }
+                if (fail) continue;
+                for (long long i = 0; i < len; ++i) colour[path[i]] = (colour[path[i]] == a) ? b : a;
+                colour[c] = a;
+                done = 1;
+            }
+        }
+    }
+    kmax = 0;
+    for (long long c = 0; c < nc; ++c) if (colour[c] + 1 > kmax) kmax = colour[c] + 1;
+    free(path); free(adj); free(fill); free(deg);
+    return kmax;
+#undef CONFLICTS
 }
 
 /* Greedy colouring as above; with `tile` non-NULL two contacts conflict only

@@ -152,6 +152,61 @@ def test_star_needs_all_colours_and_walls_do_not_conflict():
     assert K == 1
 
 
+def test_repair_moves_the_top_colour_along_a_kempe_chain():
+    """A path of four contacts p0-p1-p2-p3-p4 coloured 0, 1, 2, 0 (greedy in
+    the order e1, e4, e2, e3).  Contact e3 = (p2, p3) has colour 2 while no
+    particle has more than two contacts.  Colour 0 is free at p2, colour 1 at
+    p3; the (0, 1) path from p3 is e4 alone, swapping it gives e4 colour 1
+    and frees 0 at p3, so e3 takes 0: colours 0, 1, 0, 1."""
+    n = 5
+    pairs = np.array([[0, 1], [1, 2], [2, 3], [3, 4]], dtype=np.int32)
+    col, K = O.colour_repair(n, pairs, np.array([0, 1, 2, 0]))
+    assert K == 2 and col.tolist() == [0, 1, 0, 1]
+
+
+def test_repair_keeps_an_odd_cycle_at_three_colours():
+    """A triangle of particles needs three colours although each has two
+    contacts: the (1, 0) path from the third particle returns to the first,
+    so the repair fails and leaves the colouring alone."""
+    n = 3
+    pairs = np.array([[0, 1], [0, 2], [1, 2]], dtype=np.int32)
+    col, K = O.colour_repair(n, pairs, np.array([0, 2, 1]))
+    assert K == 3 and col.tolist() == [0, 2, 1]
+
+
+def test_repair_takes_a_colour_free_at_both_ends_and_skips_large_classes():
+    """A contact whose ends both lack a lower colour takes the smallest one
+    directly; a top class larger than max(1, min(1024, nc / 256)) is left as
+    it is; a three-contact path coloured 0, 2, 1 is repaired through the
+    (1, 0) chain of its third contact."""
+    n = 4
+    pairs = np.array([[0, 1], [2, 3]], dtype=np.int32)
+    col, K = O.colour_repair(n, pairs, np.array([0, 1]))
+    assert K == 1 and col.tolist() == [0, 0]
+    m = 300
+    pairs = np.array([[2 * i, 2 * i + 1] for i in range(m)], dtype=np.int32)
+    start = np.array([i % 2 for i in range(m)])
+    col, K = O.colour_repair(2 * m, pairs, start)
+    assert K == 2 and np.array_equal(col, start)  # 150 contacts of colour 1 > max(1, 300 // 256)
+    pairs = np.array([[0, 1], [1, 2], [2, 3]], dtype=np.int32)
+    col, K = O.colour_repair(n, pairs, np.array([0, 2, 1]))
+    # (1, 2) has colour 2; colour 0 is taken at p1, free at p2; colour 1 is free at p1, taken at p2
+    # -> path from p2 with colour 1: (2, 3); swap -> (2, 3) gets 0; (1, 2) gets 1
+    assert K == 2 and col.tolist() == [0, 1, 0]
+
+
+def test_repaired_pile_uses_as_many_colours_as_the_busiest_particle():
+    """On the dense deposit the greedy colouring needs one colour more than
+    the largest particle degree; the repair removes it and stays proper."""
+    wl = W.dense_biaxial_discs(n=5000)
+    p = params(wl)
+    pairs = O.detect_cells(p, wl.x, wl.r, np.asarray(wl.wall_pos, dtype=np.float64))
+    colour, K = O.colour_greedy(wl.n, pairs, wl.seed)
+    deg = np.bincount(pairs[:, 0], minlength=wl.n) + np.bincount(pairs[:, 1][pairs[:, 1] < wl.n], minlength=wl.n)
+    assert _conflicts(wl.n, pairs, colour) == 0
+    assert K == int(deg.max())
+
+
 @pytest.mark.parametrize("dim,periodic,tile_cells", [(2, (1, 0), 2), (2, (0, 0), 3), (3, (0, 0, 0), 2),
                                                      (2, (1, 1), 4)])
 def test_tiled_colouring_orders_independent_contacts(dim, periodic, tile_cells):
