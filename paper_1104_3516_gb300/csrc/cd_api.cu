@@ -103,6 +103,7 @@ static size_t layout(cd_system* s, char* base, CdWork* w)
     if (n + 7 > scan_max) scan_max = n + 7;
     if (CD_KMAX * nchunk > scan_max) scan_max = CD_KMAX * nchunk;
     if ((size_t)s->g.ntiles * CD_KLOCAL + 1 > scan_max) scan_max = (size_t)s->g.ntiles * CD_KLOCAL + 1;
+    if (cap + 1 > scan_max) scan_max = cap + 1;   // the colour repair's scan over the contacts
     CdWork t;
     t.ctrl = L.take<CdCtrl>(base, 1);
     // records n .. n + 5 belong to force-controlled walls, then the domain views
@@ -182,6 +183,12 @@ static size_t layout(cd_system* s, char* base, CdWork* w)
         t.V0 = L.take<char>(base, (dom ? vcap : 1) * vrec);
         t.c_vab = L.take<int2>(base, dom ? cap : 1);
     }
+    t.rep_top = L.take<int>(base, npk);
+    t.rep_dmax = L.take<int>(base, npk);
+    t.rep_flag = L.take<int>(base, cap + 1);
+    t.rep_pos = L.take<int>(base, cap + 1);
+    t.rep_list = L.take<int>(base, cap);
+    t.rep_path = L.take<int>(base, cap);
     t.obs = L.take<double>(base, CD_OBS_MAX);
     const size_t T = (size_t)s->p.tape_steps;
     t.tape = L.take<char>(base, T ? T * cd_tape_slot_bytes((int64_t)n, (int64_t)cap) : 1);

@@ -153,6 +153,226 @@ __global__ void __launch_bounds__(CD_SWEEP_THREADS) k_jp(CdGeom g, CdWork w, uns
     }
 }
 
+// ---------------------------------------------------------------------------
+// Repair of the highest colour (Kempe chains; the recolouring step of the
+// classical proof of Vizing's theorem, used as a heuristic).  For each
+// packing (a plain system is one): if its greedy colouring has a colour more
+// than its busiest body has contacts, and that top colour T holds at most
+// max(1, min(1024, nc_b / 256)) contacts, one warp visits them in key
+// order.  Contact c = (u, v) takes the smallest colour below T that neither
+// u nor v has; failing that, for a free at u and b free at v (ascending),
+// the path leaving v on its colour-a contact and alternating a, b is
+// followed to its end (a body without the next colour, or a wall); unless it
+// reaches u, a and b are swapped along it and c takes a.  Fewer colours mean
+// fewer grid barriers per sweep.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ int rep_pack_of(const CdGeom& g, const CdWork& w, int body)
+{
+    return (g.npk > 1) ? w.pack_of[body] : 0;
+}
+
+__global__ void k_rep_init(CdGeom g, CdWork w)
+{
+    for (int b = blockIdx.x * blockDim.x + threadIdx.x; b < g.npk; b += gridDim.x * blockDim.x) {
+        w.rep_top[b] = -1;
+        w.rep_dmax[b] = 0;
+    }
+}
+
+// atomicMax of v into dst[key], one atomic per run of lanes with the same key
+// (the plain system's single packing would otherwise serialise every
+// contact on one address).
+__device__ __forceinline__ void warp_atomic_max(int* dst, int key, int v, bool active)
+{
+    const unsigned grp = __match_any_sync(0xffffffffu, active ? key : -1);
+    const int m = __reduce_max_sync(grp, active ? v : -1);
+    if (active && (threadIdx.x & 31) == __ffs(grp) - 1) atomicMax(&dst[key], m);
+}
+
+__global__ void k_rep_scan_colours(CdGeom g, CdWork w)
+{
+    if (w.ctrl->skip) return;
+    const int nc = w.ctrl->nc;
+    const int nbody = g.n + (g.dyn_walls ? 6 : 0);
+    const int st = gridDim.x * blockDim.x;
+    // whole warps iterate together (the warp collectives need every lane)
+    for (int c0 = blockIdx.x * blockDim.x + (threadIdx.x & ~31); c0 < nc; c0 += st) {
+        const int c = c0 + (threadIdx.x & 31);
+        const bool on = c < nc;
+        warp_atomic_max(w.rep_top, on ? rep_pack_of(g, w, w.pairs[c].x) : 0, on ? w.colour[c] : -1, on);
+    }
+    for (int i0 = blockIdx.x * blockDim.x + (threadIdx.x & ~31); i0 < nbody; i0 += st) {
+        const int i = i0 + (threadIdx.x & 31);
+        const bool on = i < nbody;
+        const int pk = (on && i < g.n) ? rep_pack_of(g, w, i) : 0;
+        warp_atomic_max(w.rep_dmax, pk, on ? w.p2c_off[i + 1] - w.p2c_off[i] : 0, on);
+    }
+}
+
+// Flags over the whole capacity (the scan runs over cap + 1 entries).
+__global__ void k_rep_flag(CdGeom g, CdWork w)
+{
+    if (w.ctrl->skip) return;
+    const int nc = w.ctrl->nc;
+    for (int c = blockIdx.x * blockDim.x + threadIdx.x; c <= g.cap; c += gridDim.x * blockDim.x) {
+        int f = 0;
+        if (c < nc) {
+            const int t = w.rep_top[rep_pack_of(g, w, w.pairs[c].x)];
+            f = (t > 0 && w.colour[c] == t) ? 1 : 0;
+        }
+        w.rep_flag[c] = f;
+    }
+}
+
+__global__ void k_rep_fill(CdWork w)
+{
+    if (w.ctrl->skip) return;
+    const int nc = w.ctrl->nc;
+    for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < nc; c += gridDim.x * blockDim.x)
+        if (w.rep_flag[c]) w.rep_list[w.rep_pos[c]] = c;
+}
+
+// The repair runs one warp per packing: every step is sequential, but the
+// lanes read a body's contact list together, so a step costs a few L2 round
+// trips instead of one per contact of the body.  All lanes follow the same
+// control flow; lane 0 writes.
+
+// Colours below t that body x has on no contact other than c (all of them
+// for a wall that is not a body).
+__device__ __forceinline__ unsigned long long rep_free(const CdGeom& g, const CdWork& w, int x, int c, int t)
+{
+    const unsigned long long all = (1ULL << t) - 1ULL;
+    if (!cd_is_body(g, x)) return all;
+    const int lane = threadIdx.x & 31;
+    const int f0 = w.p2c_off[x], f1 = w.p2c_off[x + 1];
+    unsigned long long used = 0ULL;
+    for (int f = f0; f < f1; f += 32) {
+        unsigned long long bit = 0ULL;
+        if (f + lane < f1) {
+            const int d = w.p2c[f + lane];
+            const int k = w.colour[d];
+            if (d != c && k >= 0 && k < t) bit = 1ULL << k;
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) bit |= __shfl_xor_sync(0xffffffffu, bit, o);
+        used |= bit;
+    }
+    return all & ~used;
+}
+
+// Body x's contact of colour cur (at most one in a proper colouring), or -1.
+__device__ __forceinline__ int rep_find(const CdWork& w, int x, int cur)
+{
+    const int lane = threadIdx.x & 31;
+    const int f0 = w.p2c_off[x], f1 = w.p2c_off[x + 1];
+    for (int f = f0; f < f1; f += 32) {
+        int d = -1;
+        if (f + lane < f1) {
+            const int dd = w.p2c[f + lane];
+            if (w.colour[dd] == cur) d = dd;
+        }
+        const unsigned hit = __ballot_sync(0xffffffffu, d >= 0);
+        if (hit) return __shfl_sync(0xffffffffu, d, __ffs(hit) - 1);
+    }
+    return -1;
+}
+
+__global__ void k_rep_run(CdGeom g, CdWork w)
+{
+    if (w.ctrl->skip || w.ctrl->error != CDE_NONE) return;   // e.g. an uncoloured contact
+    const int nc = w.ctrl->nc;
+    const int lane = threadIdx.x & 31;
+    const int b = (int)((blockIdx.x * blockDim.x + threadIdx.x) >> 5);   // one warp per packing
+    if (b >= g.npk) return;
+    const int c0 = (g.npk > 1) ? w.pk_coff[b] : 0, c1 = (g.npk > 1) ? w.pk_coff[b + 1] : nc;
+    const int ncb = c1 - c0, t = w.rep_top[b];
+    if (ncb <= 0 || t <= 0 || t > 63 || t + 1 <= w.rep_dmax[b]) return;
+    const int l0 = w.rep_pos[c0], l1 = w.rep_pos[c1];
+    int limit = ncb / 256;
+    if (limit > 1024) limit = 1024;
+    if (limit < 1) limit = 1;
+    if (l1 - l0 > limit) return;
+    int* path = w.rep_path + c0;
+    for (int l = l0; l < l1; ++l) {
+        const int c = w.rep_list[l];
+        const int2 uv = w.pairs[c];
+        const int u = uv.x, v = uv.y;
+        const unsigned long long mu = rep_free(g, w, u, c, t), mv = rep_free(g, w, v, c, t);
+        if (mu & mv) {
+            if (lane == 0) w.colour[c] = __ffsll((long long)(mu & mv)) - 1;
+            __syncwarp();
+            continue;
+        }
+        if (!cd_is_body(g, v)) continue;
+        bool done = false;
+        for (int a = 0; a < t && !done; ++a) {
+            if (!((mu >> a) & 1ULL)) continue;
+            for (int bb = 0; bb < t && !done; ++bb) {
+                if (!((mv >> bb) & 1ULL)) continue;
+                int len = 0, x = v, cur = a;
+                bool fail = false;
+                for (;;) {
+                    const int e = rep_find(w, x, cur);
+                    if (e < 0) break;
+                    const int2 pe = w.pairs[e];
+                    const int y = (pe.x == x) ? pe.y : pe.x;
+                    if (lane == 0) path[len] = e;
+                    ++len;
+                    if (y == u) { fail = true; break; }
+                    if (!cd_is_body(g, y)) break;
+                    x = y;
+                    cur = (cur == a) ? bb : a;
+                    if (len >= ncb) { fail = true; break; }
+                }
+                __syncwarp();
+                if (fail) continue;
+                for (int i = lane; i < len; i += 32) {
+                    const int e = path[i];
+                    w.colour[e] = (w.colour[e] == a) ? bb : a;
+                }
+                if (lane == 0) w.colour[c] = a;
+                __syncwarp();
+                done = true;
+            }
+        }
+    }
+}
+
+__global__ void k_rep_ncolours_reset(CdCtrl* ctrl)
+{
+    if (!ctrl->skip) ctrl->ncolours = 0;
+}
+
+__global__ void k_rep_ncolours(CdWork w)
+{
+    if (w.ctrl->skip) return;
+    const int nc = w.ctrl->nc;
+    for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < nc; c += gridDim.x * blockDim.x)
+        atomicMax(&w.ctrl->ncolours, w.colour[c] + 1);
+}
+
+static cudaError_t launch_repair(const CdGeom& g, const CdWork& w, int gc, cudaStream_t s, int* nl)
+{
+    cudaError_t e;
+    const int gp = (g.npk + CD_BLOCK - 1) / CD_BLOCK;
+    int m = (g.cap > g.n + 6) ? g.cap : g.n + 6;
+    int gm = (m + CD_BLOCK - 1) / CD_BLOCK;
+    if (gm > 4096) gm = 4096;
+    k_rep_init<<<gp, CD_BLOCK, 0, s>>>(g, w);
+    k_rep_scan_colours<<<gm, CD_BLOCK, 0, s>>>(g, w);
+    k_rep_flag<<<gc, CD_BLOCK, 0, s>>>(g, w);
+    *nl += 3;
+    if ((e = cd_scan_exclusive(w.rep_flag, w.rep_pos, g.cap + 1, w.scan_tmp, nullptr, s, nl)) != cudaSuccess)
+        return e;
+    k_rep_fill<<<gc, CD_BLOCK, 0, s>>>(w);
+    // one warp per packing: a plain system's repair is one sequential walk
+    k_rep_run<<<(g.npk + 1) / 2, 64, 0, s>>>(g, w);
+    k_rep_ncolours_reset<<<1, 1, 0, s>>>(w.ctrl);
+    k_rep_ncolours<<<gc, CD_BLOCK, 0, s>>>(w);
+    *nl += 4;
+    return cudaGetLastError();
+}
+
 // Per-chunk colour histogram, layout [colour][chunk].
 __global__ void k_chunk_hist(CdWork w, int nchunk)
 {
@@ -456,6 +676,7 @@ cudaError_t cd_launch_colour(const CdGeom& g, const CdWork& w, int coop_blocks, 
         ++*nl;
     }
     if (tiled) return cd_launch_order_tiled(g, w, pos, precision, pw, s, nl);
+    if ((e = launch_repair(g, w, gc, s, nl)) != cudaSuccess) return e;
     k_chunk_hist<<<nchunk, CD_CHUNK, 0, s>>>(w, nchunk); ++*nl;
     if ((e = cd_scan_exclusive(w.chunk_cnt, w.chunk_cnt, CD_KMAX * nchunk, w.scan_tmp, nullptr, s, nl)) != cudaSuccess)
         return e;

@@ -158,6 +158,13 @@ struct CdWork {
     int* view_owner;    // 2 cap: particle of each view record
     void* V0;           // 2 cap velocity records: the sweep-start velocity of the view's particle
     int2* c_vab;        // cap (colour order): velocity records of bodies a and b
+    // repair of the highest colour (global colour order)
+    int* rep_top;       // npk: highest colour of each packing
+    int* rep_dmax;      // npk: most contacts of one body of the packing
+    int* rep_flag;      // cap + 1: 1 for a contact of its packing's highest colour
+    int* rep_pos;       // cap + 1: exclusive scan of rep_flag
+    int* rep_list;      // cap: those contacts in key order
+    int* rep_path;      // cap: alternating path being followed (per packing: its contact range)
     double* obs;        // CD_OBS_MAX doubles: observable results
     // adjoint (params.tape_steps > 0)
     char* tape;         // tape_steps slots of CdTapeHdr + one step's records
