@@ -85,6 +85,8 @@ def parse():
                     help="1: per-particle update counts instead of a grid barrier per colour")
     ap.add_argument("--domains", type=int, nargs=3, default=[1, 1, 1], metavar=("NX", "NY", "NZ"),
                     help="domain-wise update of Sec. 3.1: slabs per axis (1 1 1: Gauss-Seidel)")
+    ap.add_argument("--sphere-steps", type=int, default=5,
+                    help="timed steps of the 1e6-sphere 3D gas leg (rank 0 at N=1 only; 0: skip)")
     ap.add_argument("--batched-steps", type=int, default=3,
                     help="timed steps of the 512-packing batched workload (0: skip)")
     ap.add_argument("--packings", type=int, default=512)
@@ -387,6 +389,10 @@ def run_ours(args):
     if args.adjoint_steps > 0 and args.precision == "f64" and wl.dim == 2:
         adjoint = run_adjoint(args, device, rank, flush)
 
+    sphere = None
+    if args.sphere_steps > 0 and wl.dim == 2 and ws == 1:
+        sphere = run_sphere_gas(args, device, flush)
+
     e2e = None
     if not args.no_e2e:
         e2e = run_e2e(args, sysg, wl, device, ws)
@@ -412,6 +418,7 @@ def run_ours(args):
                                         "steps_not_converged": not_conv, "parallelism": f"replicas x{ws}"}),
             "phase_ms_per_step": {k: v / max(args.steps, 1) for k, v in ph.items()},
             "wall_s": wall_max, "roofline": roofline, "autotune": tuned, "batched": batched, "adjoint": adjoint,
+            "sphere_gas_3d": sphere,
             "cpu_baseline": cpu,
             "e2e": e2e,
             "gpu_launches": launches, "clocks": clk}
@@ -465,6 +472,45 @@ def run_batched(args, device, rank, flush):
     if args.precision == "f64":
         out["fp64_tflops"] = FLOPS_PER_UPDATE_2D * upd / (sweep_ms / 1e3) / 1e12
         out["alu_frac"] = out["fp64_tflops"] / FP64_PEAK_TFLOPS
+    del g
+    torch.cuda.empty_cache()
+    return out
+
+
+def run_sphere_gas(args, device, flush):
+    """The 3D configuration alongside the 2D line: 1,000,000 spheres (radii
+    U[0.8, 1.2], mu = 0.5, rotations) falling as a gas at packing fraction
+    0.3 (v0 ~ N(0, 0.1)) onto a 100 x 100 floor with four side walls, FP64,
+    the same convergence test; one untimed step, then `sphere_steps` timed
+    steps with the L2 flushed before each."""
+    import torch
+    from paper_1104_3516_gb300 import cd, workloads as W
+    wl = W.sphere_gas(seed=1107, n=1_000_000)
+    wl.max_sweeps = args.max_sweeps
+    wl.alpha = args.alpha
+    g = cd.CDSystem(wl, device=device, precision=cd.CD_FP64, criterion=cd.CD_CONV_GLOBAL_REL, timing=1,
+                    max_contacts=8 * wl.n)
+    flush.zero_()
+    g.step(1)
+    upd = sweeps = 0
+    ph = {}
+    colours, ncs = [], []
+    for _ in range(args.sphere_steps):
+        flush.zero_()
+        st = g.step(1)
+        upd += st["total_contact_updates"]
+        sweeps += st["total_sweeps"]
+        for k, v in st["phase_ms"].items():
+            ph[k] = ph.get(k, 0.0) + v
+        colours.append(st["last"]["n_colours"])
+        ncs.append(st["last"]["n_contacts"])
+    ms = sum(ph.values())
+    out = {"value": upd / (ms / 1e3), "unit": UNIT, "spheres": wl.n, "steps": args.sphere_steps,
+           "ms_per_step": ms / args.sphere_steps, "steps_per_s": args.sphere_steps / (ms / 1e3),
+           "phase_ms_per_step": {k: v / args.sphere_steps for k, v in ph.items()},
+           "sweeps_per_step": sweeps / args.sphere_steps, "contacts": ncs[-1], "colours": colours,
+           "dtype": "f64", "workload": "sphere_gas_3d: 1e6 spheres, gas at packing fraction 0.3, v0 ~ N(0, 0.1), "
+                                       "mu 0.5, 100 x 100 floor with 4 side walls, rotations"}
     del g
     torch.cuda.empty_cache()
     return out

@@ -327,7 +327,11 @@ __global__ void k_pair_count(CdGeom g, CdWork w, const double* __restrict__ pos,
         for (int k = 0; k < DIM; ++k) xa[k] = pos[a * DIM + k];
         double ra = radius[a];
         int cnt = 0;
-        for_each_partner<DIM>(g, v, a, xa, ra, pos, radius, cell_of, cell_start, cell_pid, [&](int) { ++cnt; });
+        int* keep = w.cand ? w.cand + (size_t)a * CD_CAND : nullptr;
+        for_each_partner<DIM>(g, v, a, xa, ra, pos, radius, cell_of, cell_start, cell_pid, [&](int b) {
+            if (keep && cnt < CD_CAND) keep[cnt] = b;   // the emitting pass reuses them instead of walking again
+            ++cnt;
+        });
         int nw = 0;
         for (int k = 0; k < 2 * DIM; ++k)
             if (wall_on(v, DIM, k) && wall_gap(xa, ra, wp, k) < g.delta) ++nw;
@@ -429,14 +433,24 @@ __global__ void k_pair_emit(CdGeom g, CdWork w, const double* __restrict__ pos, 
         double ra = radius[a];
         int found[CD_MAXLOC];
         int nf = 0;
-        for_each_partner<DIM>(g, v, a, xa, ra, pos, radius, w.cell_of, w.cell_start, w.cell_pid, [&](int b) {
+        auto insert = [&](int b) {
             if (nf < CD_MAXLOC) {
                 // insertion into the sorted prefix
                 int j = nf++;
                 while (j > 0 && found[j - 1] > b) { found[j] = found[j - 1]; --j; }
                 found[j] = b;
             }
-        });
+        };
+        int nw = 0;
+        for (int k = 0; k < 2 * DIM; ++k)
+            if (wall_on(v, DIM, k) && wall_gap(xa, ra, wp, k) < g.delta) ++nw;
+        const int npart = w.pcnt[a] - nw;   // partners the counting pass found
+        if (w.cand && npart <= CD_CAND) {
+            const int* keep = w.cand + (size_t)a * CD_CAND;
+            for (int f = 0; f < npart; ++f) insert(keep[f]);
+        } else {
+            for_each_partner<DIM>(g, v, a, xa, ra, pos, radius, w.cell_of, w.cell_start, w.cell_pid, insert);
+        }
         int o = w.poff[a];
         for (int f = 0; f < nf; ++f) {
             double nv[3], gap, mn, mt;

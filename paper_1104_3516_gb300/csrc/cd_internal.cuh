@@ -9,6 +9,7 @@
 
 #define CD_KMAX 64            // colours the ordering supports (bit mask in the colouring)
 #define CD_MAXLOC 64          // pair candidates one particle may emit
+#define CD_CAND 16            // partners the counting pass keeps per particle for the emitting pass
 #define CD_SWEEP_THREADS 512  // threads per block of the persistent kernels
 #define CD_BLOCK 256          // threads per block of the streaming kernels
 #define CD_CHUNK 256          // contacts per chunk of the stable colour partition
@@ -88,6 +89,7 @@ struct CdWork {
     int* cell_fill;     // ncell
     int* cell_pid;      // n
     int* pcnt;          // n + 1
+    int* cand;          // n * CD_CAND: partners b > a found by the counting pass (first CD_CAND, found order)
     int* poff;          // n + 1
     int* scan_tmp;      // block sums of the scans
     // contacts, key order

@@ -44,7 +44,8 @@
 #define NA_MN (NA_SCAN + NA_I32(CD_NOALLOC_MAX_CELLS / 1024 + 64))
 #define NA_MT (NA_MN + NA_ALIGN(sizeof(double) * CD_NOALLOC_MAX_CONTACTS))
 #define NA_PK (NA_MT + NA_ALIGN(sizeof(double) * CD_NOALLOC_MAX_CONTACTS))
-#define NA_RMAX (NA_PK + NA_ALIGN(sizeof(double) * 4 * CD_NOALLOC_MAX_CONTACTS))
+#define NA_CAND (NA_PK + NA_ALIGN(sizeof(double) * 4 * CD_NOALLOC_MAX_CONTACTS))
+#define NA_RMAX (NA_CAND + NA_I32((size_t)CD_NOALLOC_MAX_N * CD_CAND))
 #define NA_BYTES (NA_RMAX + 256)
 
 static __device__ __align__(256) unsigned char cd_noalloc_scratch[NA_BYTES];
@@ -192,6 +193,7 @@ extern "C" cd_status cd_detect_contacts_noalloc(const cd_params* params, int64_t
     w.cell_pid = (int*)(base + NA_CELL_PID);
     w.pcnt = (int*)(base + NA_PCNT);
     w.poff = (int*)(base + NA_POFF);
+    w.cand = (int*)(base + NA_CAND);
     w.scan_tmp = (int*)(base + NA_SCAN);
     w.mn = (double*)(base + NA_MN);
     w.mt = (double*)(base + NA_MT);
