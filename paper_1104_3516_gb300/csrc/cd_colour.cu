@@ -70,6 +70,42 @@ __global__ void k_p2c_sort(CdGeom g, CdWork w)
 // Persistent cooperative kernel: Jones-Plassmann rounds separated by the
 // bounded grid barrier.  `prio` scratch lives in the chunk buffer (8 bytes per
 // contact is reserved there by the workspace layout).
+//
+// Worklist form: every contact first counts its neighbours of higher
+// priority (contacts sharing a body, in the same tile when tiled); those with
+// none start the first list.  A round colours the contacts of its list (the
+// smallest colour no higher-priority neighbour has; all of those are
+// coloured by then) and decrements the counts of their lower-priority
+// neighbours; a contact whose count reaches zero joins the next list.  Each
+// contact is coloured exactly once, from the same neighbours as in the
+// round-by-round scan, so the colouring is the same greedy fixed point, at a
+// cost proportional to the contacts and their neighbours instead of to
+// rounds x contacts.  Scratch: the colour repair's arrays (used only after
+// the colouring): rep_flag holds the counts, rep_list and rep_path the lists
+// of even and odd rounds; round_cnt[r % 3] is the length of round r's list
+// (three counters, so that one grid barrier per round suffices: round r
+// clears the counter of round r + 2, last read in round r - 1).
+__device__ __forceinline__ bool jp_higher(const CdWork& w, const unsigned long long* prio, int d, int c,
+                                          unsigned long long pc, unsigned long long kc)
+{
+    const unsigned long long pd = prio[d];
+    if (pd != pc) return pd > pc;
+    const int2 dd = w.pairs[d];
+    return cd_key(dd.x, dd.y) < kc;
+}
+
+// Appends c to list (length at *len) with one atomic per warp.
+__device__ __forceinline__ void jp_append(int* list, int* len, int c, bool take)
+{
+    const unsigned m = __ballot_sync(0xffffffffu, take);
+    if (!m) return;
+    const int lane = threadIdx.x & 31;
+    int base = 0;
+    if (lane == __ffs(m) - 1) base = atomicAdd(len, __popc(m));
+    base = __shfl_sync(0xffffffffu, base, __ffs(m) - 1);
+    if (take) list[base + __popc(m & ((1u << lane) - 1u))] = c;
+}
+
 __global__ void __launch_bounds__(CD_SWEEP_THREADS) k_jp(CdGeom g, CdWork w, unsigned long long* prio,
                                                           int* round_cnt, const int* tile, int kmax)
 {
@@ -80,6 +116,8 @@ __global__ void __launch_bounds__(CD_SWEEP_THREADS) k_jp(CdGeom g, CdWork w, uns
     unsigned long long epoch = 0;
     const int tid = blockIdx.x * blockDim.x + threadIdx.x;
     const int stride = gridDim.x * blockDim.x;
+    int* cnt = w.rep_flag;
+    int* lists[2] = {w.rep_list, w.rep_path};
     for (int c = tid; c < nc; c += stride) {
         int2 ab = w.pairs[c];
         unsigned long long h;
@@ -102,53 +140,97 @@ __global__ void __launch_bounds__(CD_SWEEP_THREADS) k_jp(CdGeom g, CdWork w, uns
     }
     if (tid == 0) { round_cnt[0] = 0; round_cnt[1] = 0; round_cnt[2] = 0; ctrl->ncolours = 0; }
     if (!cd_grid_sync(ctrl, nb, epoch)) return;
-    __shared__ int s_rem;
-    for (int round = 0; round < 1 << 20; ++round) {
-        if (threadIdx.x == 0) s_rem = 0;
-        if (tid == 0) round_cnt[(round + 1) % 3] = 0;
-        __syncthreads();
-        int rem = 0;
-        for (int c = tid; c < nc; c += stride) {
-            if (cd_ld_volatile_int(&w.colour[c]) >= 0) continue;
-            unsigned long long pc = prio[c];
-            int2 ab = w.pairs[c];
-            unsigned long long kc = cd_key(ab.x, ab.y);
-            unsigned long long used = 0ULL;
-            bool ready = true;
-            for (int side = 0; side < 2 && ready; ++side) {
-                int q = side ? ab.y : ab.x;
+    // higher-priority neighbours of every contact; the free ones start the first list
+    for (int c0 = blockIdx.x * blockDim.x + (threadIdx.x & ~31); c0 < nc; c0 += stride) {
+        const int c = c0 + (threadIdx.x & 31);
+        int k = 0;
+        if (c < nc) {
+            const unsigned long long pc = prio[c];
+            const int2 ab = w.pairs[c];
+            const unsigned long long kc = cd_key(ab.x, ab.y);
+            for (int side = 0; side < 2; ++side) {
+                const int q = side ? ab.y : ab.x;
                 if (!cd_is_body(g, q)) continue;
-                int e = w.p2c_off[q + 1];
-                for (int s = w.p2c_off[q]; s < e; ++s) {
-                    int d = w.p2c[s];
-                    if (d == c) continue;
-                    if (tile && tile[d] != tile[c]) continue;
-                    unsigned long long pd = prio[d];
-                    bool higher = pd > pc;
-                    if (pd == pc) {
-                        int2 dd = w.pairs[d];
-                        higher = cd_key(dd.x, dd.y) < kc;
-                    }
-                    if (!higher) continue;
-                    int cdl = cd_ld_volatile_int(&w.colour[d]);
-                    if (cdl < 0) { ready = false; break; }
-                    used |= 1ULL << cdl;
+                const int f0 = w.p2c_off[q], f1 = w.p2c_off[q + 1];
+                for (int t = f0; t < f1; t += 4) {
+                    int d[4];
+#pragma unroll
+                    for (int u = 0; u < 4; ++u) d[u] = (t + u < f1) ? w.p2c[t + u] : -1;
+#pragma unroll
+                    for (int u = 0; u < 4; ++u)
+                        if (d[u] >= 0 && d[u] != c && !(tile && tile[d[u]] != tile[c]) &&
+                            jp_higher(w, prio, d[u], c, pc, kc))
+                            ++k;
                 }
             }
-            if (!ready) { ++rem; continue; }
-            int col = (used == ~0ULL) ? 64 : __ffsll((long long)~used) - 1;
-            if (col >= kmax) {
-                atomicCAS(&ctrl->error, CDE_NONE, CDE_COLOURS);
-                continue;
-            }
-            *(volatile int*)&w.colour[c] = col;
-            atomicMax(&ctrl->ncolours, col + 1);
+            cnt[c] = k;
         }
-        if (rem) atomicAdd(&s_rem, rem);
-        __syncthreads();
-        if (threadIdx.x == 0 && s_rem) atomicAdd(&round_cnt[round % 3], s_rem);
+        jp_append(lists[0], &round_cnt[0], c, c < nc && k == 0);   // round 0's list
+    }
+    if (!cd_grid_sync(ctrl, nb, epoch)) return;
+    for (int round = 0; round < (1 << 20); ++round) {
+        const int cur = round & 1, nxt = cur ^ 1;
+        const int len = cd_ld_volatile_int(&round_cnt[round % 3]);
+        if (len == 0) break;
+        if (tid == 0) round_cnt[(round + 2) % 3] = 0;
+        for (int i0 = blockIdx.x * blockDim.x + (threadIdx.x & ~31); i0 < len; i0 += stride) {
+            const int i = i0 + (threadIdx.x & 31);
+            const int c = (i < len) ? lists[cur][i] : -1;
+            int2 ab = make_int2(0, 0);
+            unsigned long long pc = 0ULL, kc = 0ULL;
+            if (c >= 0) {
+                pc = prio[c];
+                ab = w.pairs[c];
+                kc = cd_key(ab.x, ab.y);
+            }
+            // one pass over both bodies' contacts: the colours of the higher-priority
+            // neighbours (all final), and the release of the lower-priority ones (they
+            // read c's colour only in a later round, after the grid barrier)
+            unsigned long long used = 0ULL;
+            for (int side = 0; side < 2; ++side) {
+                const int q = side ? ab.y : ab.x;
+                const bool on = c >= 0 && cd_is_body(g, q);
+                const int f0 = on ? w.p2c_off[q] : 0, f1 = on ? w.p2c_off[q + 1] : 0;
+                int most = f1 - f0;
+#pragma unroll
+                for (int o = 16; o > 0; o >>= 1) most = max(most, __shfl_xor_sync(0xffffffffu, most, o));
+                // four neighbours at a time: their loads and atomics are in flight together
+                for (int t = 0; t < most; t += 4) {
+                    int d[4], v[4];
+                    bool hi[4], lo[4];
+#pragma unroll
+                    for (int u = 0; u < 4; ++u) d[u] = (f0 + t + u < f1) ? w.p2c[f0 + t + u] : -1;
+#pragma unroll
+                    for (int u = 0; u < 4; ++u) {
+                        const bool nb_ok = d[u] >= 0 && d[u] != c && !(tile && tile[d[u]] != tile[c]);
+                        const bool h = nb_ok && jp_higher(w, prio, d[u], c, pc, kc);
+                        hi[u] = h;
+                        lo[u] = nb_ok && !h;
+                    }
+#pragma unroll
+                    for (int u = 0; u < 4; ++u)
+                        v[u] = hi[u] ? cd_ld_volatile_int(&w.colour[d[u]]) : (lo[u] ? atomicSub(&cnt[d[u]], 1) : 0);
+#pragma unroll
+                    for (int u = 0; u < 4; ++u) {
+                        if (hi[u] && v[u] >= 0) used |= 1ULL << v[u];
+                        jp_append(lists[nxt], &round_cnt[(round + 1) % 3], d[u], lo[u] && v[u] == 1);
+                    }
+                }
+            }
+            int top = 0;
+            if (c >= 0) {
+                const int col = (used == ~0ULL) ? 64 : __ffsll((long long)~used) - 1;
+                if (col >= kmax) {
+                    atomicCAS(&ctrl->error, CDE_NONE, CDE_COLOURS);
+                } else {
+                    *(volatile int*)&w.colour[c] = col;
+                    top = col + 1;
+                }
+            }
+            top = __reduce_max_sync(0xffffffffu, top);   // one atomic per warp
+            if ((threadIdx.x & 31) == 0 && top > 0) atomicMax(&ctrl->ncolours, top);
+        }
         if (!cd_grid_sync(ctrl, nb, epoch)) return;
-        if (cd_ld_volatile_int(&round_cnt[round % 3]) == 0) break;
         if (cd_ld_volatile_int(&ctrl->error) != CDE_NONE) break;
     }
 }
