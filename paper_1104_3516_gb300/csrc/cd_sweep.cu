@@ -30,6 +30,11 @@ template <typename T> struct Vec;
 template <> struct Vec<double> { typedef double4 V4; typedef double2 V2; };
 template <> struct Vec<float> { typedef float4 V4; typedef float2 V2; };
 
+// Fused multiply-add of the sweep's real type, rounded once.
+template <typename T> __device__ __forceinline__ T fma_of(T a, T b, T c);
+template <> __device__ __forceinline__ double fma_of<double>(double a, double b, double c) { return __fma_rn(a, b, c); }
+template <> __device__ __forceinline__ float fma_of<float>(float a, float b, float c) { return __fmaf_rn(a, b, c); }
+
 // Stores the first three components of a velocity record, leaving the fourth.
 template <typename T>
 __device__ __forceinline__ void store_xyz_plain(typename Vec<T>::V4* dst, const typename Vec<T>::V4& v)
@@ -245,7 +250,8 @@ __device__ __forceinline__ double grid_total(const double* part, int nblocks, do
 // ---------------------------------------------------------------------------
 struct UpdOut {
     double pabs;     // |P| after the update (deferred form: |P| of the thread's previous update)
-    double psq;      // deferred form: |P|^2 after the update
+    double psq;      // |P|^2 after the update (3D and FP32)
+    double pn, pt;   // deferred form (FP64 2D): P_n, P_t after the update
     int rel_ok;      // local test (I), relative branch
     int bad;         // local test (I): fails both branches
 };
@@ -346,6 +352,11 @@ template <typename T> __device__ __forceinline__ double abs_of_sq(double s);
 template <> __device__ __forceinline__ double abs_of_sq<double>(double s) { return norm_of_sq(s); }
 template <> __device__ __forceinline__ double abs_of_sq<float>(double s) { return (double)sqrtf((float)s); }
 
+// |P|^2 = P_n^2 + P_t^2 with a fixed rounding (the FP64 2D sweeps take it
+// either inline or deferred, and must agree), and |P| from the pair.
+__device__ __forceinline__ double sq2(double a, double b) { return __fma_rn(b, b, __dmul_rn(a, a)); }
+__device__ __forceinline__ double abs_of_pair(double pn, double pt) { return norm_of_sq(sq2(pn, pt)); }
+
 // 2D: P_n = max(0, P_n,old - m_n (b + u_n)); P_t = clamp(P_t,old - m_t u_t, +-mu P_n).
 // The core works on the two bodies' velocity records wherever they live
 // (global memory or a tile's shared-memory table).
@@ -363,7 +374,16 @@ __device__ __forceinline__ UpdOut core2d(const CdGeom& g, const Rec<2, T>& r, ty
         const T b = r.geo.z, mn = r.geo.w;
         T dvx = vb.x - va.x, dvy = vb.y - va.y;
         T un = dvx * nx + dvy * ny;
-        T ut = (dvy * nx - dvx * ny) - (r.sa.y * va.z + r.sb.y * vb.z);
+        // u_t = (dv x n) - (r_a w_a + r_b w_b); in FP64 as one chain of fused
+        // steps (one instruction fewer on the narrow pipe)
+        T ut;
+        if constexpr (sizeof(T) == 8) {
+            ut = fma_of<T>(dvy, nx, -(dvx * ny));
+            ut = fma_of<T>(-r.sa.y, va.z, ut);
+            ut = fma_of<T>(-r.sb.y, vb.z, ut);
+        } else {
+            ut = (dvy * nx - dvx * ny) - (r.sa.y * va.z + r.sb.y * vb.z);
+        }
         Pn = pos_part(r.P.x - mn * (b + un));
         T lim = r.mu * Pn;
         Pt = clamp_sym(r.P.y - r.mt * ut, lim);
@@ -377,10 +397,16 @@ __device__ __forceinline__ UpdOut core2d(const CdGeom& g, const Rec<2, T>& r, ty
     Pnew.x = Pn; Pnew.y = Pt;
     UpdOut o;
     double pn = (double)Pn, pt = (double)Pt;
-    // SQ: |P|^2 only, the magnitude is taken later (abs_of_sq)
-    if constexpr (sizeof(T) == 4) o.psq = (double)(Pn * Pn + Pt * Pt);
-    else o.psq = pn * pn + pt * pt;
-    o.pabs = SQ ? 0.0 : abs_of_sq<T>(o.psq);
+    // SQ (FP64): the pair only, the magnitude is taken later (abs_of_pair)
+    o.pn = pn;
+    o.pt = pt;
+    if constexpr (sizeof(T) == 4) {
+        o.psq = (double)(Pn * Pn + Pt * Pt);
+        o.pabs = abs_of_sq<T>(o.psq);
+    } else {
+        o.psq = 0.0;
+        o.pabs = SQ ? 0.0 : abs_of_pair(pn, pt);
+    }
     o.rel_ok = 0; o.bad = 0;
     if (!apply_only && crit == CD_CONV_LOCAL) {
         double d0 = (double)dPn, d1 = (double)dPt;
@@ -407,13 +433,13 @@ __device__ __forceinline__ void wall_vel2(const CdGeom& g, const CdWork& w, int 
 }
 
 // VIEWS: the bodies' velocity records are the domain views r.vab, else their own.
-// DEFER: the result's pabs is |P| of the thread's previous update, taken from
-// its |P|^2 `pend` after this update's velocity loads are issued; psq holds
-// this update's |P|^2.
+// DEFER (FP64): the result's pabs is |P| of the thread's previous update,
+// taken from its (P_n, P_t) `pend` after this update's velocity loads are
+// issued; pn, pt hold this update's impulse.
 template <typename T, bool VIEWS = false, bool DEFER = false>
 __device__ __forceinline__ UpdOut apply2d(const CdGeom& g, const CdWork& w, int pos, const Rec<2, T>& r,
                                           bool apply_only, int crit, double alpha, double ravg_prev,
-                                          double pend = 0.0)
+                                          double2 pend = make_double2(0.0, 0.0))
 {
     typedef typename Vec<T>::V4 T4;
     typedef typename Vec<T>::V2 T2;
@@ -424,7 +450,7 @@ __device__ __forceinline__ UpdOut apply2d(const CdGeom& g, const CdWork& w, int 
     T4 vb;
     if (!wall) vb = V[ib];
     else wall_vel2<T>(g, w, r.ab.y, vb);
-    const double prev = DEFER ? abs_of_sq<T>(pend) : 0.0;
+    const double prev = DEFER ? abs_of_pair(pend.x, pend.y) : 0.0;
     T2 Pnew;
     UpdOut o = core2d<T, DEFER>(g, r, va, vb, wall, apply_only, crit, alpha, ravg_prev, Pnew);
     if constexpr (DEFER) o.pabs = prev;
@@ -511,7 +537,7 @@ __device__ __forceinline__ void wall_vel3(const CdGeom& g, const CdWork& w, int 
 template <typename T, bool VIEWS = false, bool DEFER = false>
 __device__ __forceinline__ UpdOut apply3d(const CdGeom& g, const CdWork& w, int pos, const Rec<3, T>& r,
                                           bool apply_only, int crit, double alpha, double ravg_prev,
-                                          double pend = 0.0)
+                                          double2 pend = make_double2(0.0, 0.0))
 {
     typedef typename Vec<T>::V4 T4;
     T4* V = (T4*)w.V;
@@ -521,7 +547,7 @@ __device__ __forceinline__ UpdOut apply3d(const CdGeom& g, const CdWork& w, int 
     T4 vb, wb;
     if (!wall) { vb = V[2 * ib]; wb = V[2 * ib + 1]; }
     else wall_vel3<T>(g, w, r.ab.y, vb, wb);
-    const double prev = DEFER ? abs_of_sq<T>(pend) : 0.0;
+    const double prev = DEFER ? abs_of_pair(pend.x, pend.y) : 0.0;
     T4 Pnew;
     UpdOut o = core3d<T, DEFER>(g, r, va, wa, vb, wb, wall, apply_only, crit, alpha, ravg_prev, Pnew);
     if constexpr (DEFER) o.pabs = prev;
@@ -544,7 +570,7 @@ __device__ __forceinline__ UpdOut apply3d(const CdGeom& g, const CdWork& w, int 
 template <int DIM, typename T, bool VIEWS = false, bool DEFER = false>
 __device__ __forceinline__ UpdOut apply_rec(const CdGeom& g, const CdWork& w, int pos, const Rec<DIM, T>& r,
                                             bool apply_only, int crit, double alpha, double ravg_prev,
-                                            double pend = 0.0)
+                                            double2 pend = make_double2(0.0, 0.0))
 {
     if constexpr (DIM == 2)
         return apply2d<T, VIEWS, DEFER>(g, w, pos, r, apply_only, crit, alpha, ravg_prev, pend);
@@ -563,13 +589,13 @@ __device__ __forceinline__ void prefetch_first(const CdGeom& g, const CdWork& w,
 // One colour phase for this thread: its first contact's record was loaded
 // into `nxt` before the barrier (if it has one); the rest are loaded inline.
 // Afterwards `nxt` holds the first record of colour `knext` (prefetch).
-// `pend` carries the |P|^2 of the thread's last update whose magnitude is not
-// yet in acc[0] (0 if none) from phase to phase; the caller adds it before
-// the block sum at the end of a pass.
+// `pend` carries (P_n, P_t) of the thread's last update whose magnitude is
+// not yet in acc[0] (zeros if none) from phase to phase; the caller adds it
+// before the block sum at the end of a pass.
 template <int DIM, typename T, int MODE>
 __device__ __forceinline__ void colour_phase(const CdGeom& g, const CdWork& w, const int* s_off, int k, int knext,
                                              int tid, int stride, Rec<DIM, T>& nxt, bool apply_only, int crit,
-                                             double alpha, double ravg_prev, double (&acc)[3], double& pend)
+                                             double alpha, double ravg_prev, double (&acc)[3], double2& pend)
 {
     constexpr bool MIXED = (MODE == CD_SWEEP_MIXED);
     constexpr bool VIEWS = (MODE == CD_SWEEP_DOMAINS);
@@ -584,7 +610,7 @@ __device__ __forceinline__ void colour_phase(const CdGeom& g, const CdWork& w, c
         if (!(mixed && cd_is_parallel(g.par_p, g.seed, cd_key(nxt.ab.x, nxt.ab.y)))) {
             UpdOut o = apply_rec<DIM, T, VIEWS, DEFER>(g, w, p, nxt, apply_only, crit, alpha, ravg_prev, pend);
             acc[0] += o.pabs;
-            if (DEFER) pend = o.psq;
+            if (DEFER) pend = make_double2(o.pn, o.pt);
             if (crit == CD_CONV_LOCAL) { acc[1] += (double)o.rel_ok; acc[2] += (double)o.bad; }
         }
         for (p += blockDim.x; p < end; p += blockDim.x) {
@@ -593,7 +619,7 @@ __device__ __forceinline__ void colour_phase(const CdGeom& g, const CdWork& w, c
             if (mixed && cd_is_parallel(g.par_p, g.seed, cd_key(r.ab.x, r.ab.y))) continue;
             UpdOut o = apply_rec<DIM, T, VIEWS, DEFER>(g, w, p, r, apply_only, crit, alpha, ravg_prev, pend);
             acc[0] += o.pabs;
-            if (DEFER) pend = o.psq;
+            if (DEFER) pend = make_double2(o.pn, o.pt);
             if (crit == CD_CONV_LOCAL) { acc[1] += (double)o.rel_ok; acc[2] += (double)o.bad; }
         }
     }
@@ -848,13 +874,13 @@ k_sweep(CdGeom g, CdWork w, int crit, double alpha, int max_sweeps)
         }
         // starting impulses, colour by colour
         double acc[3] = {0.0, 0.0, 0.0};
-        double pend = 0.0;   // |P|^2 of this thread's last update not yet in the residual sum
+        double2 pend = make_double2(0.0, 0.0);   // this thread's last impulse not yet in the residual sum
         for (int k = 0; k < K; ++k) {
             colour_phase<DIM, T, MODE>(g, w, s_off, k, (k + 1 < K) ? k + 1 : 0, tid, stride, nxt, true, crit, alpha,
                                        0.0, acc, pend);
             if (k == K - 1) {
-                acc[0] += abs_of_sq<T>(pend);
-                pend = 0.0;
+                acc[0] += abs_of_pair(pend.x, pend.y);
+                pend = make_double2(0.0, 0.0);
                 block_sum<3>(acc, s_red);
                 if (threadIdx.x == 0) w.partials[blockIdx.x] = acc[0];
             }
@@ -893,8 +919,8 @@ k_sweep(CdGeom g, CdWork w, int crit, double alpha, int max_sweeps)
                 colour_phase<DIM, T, MODE>(g, w, s_off, k, -1, tid, stride, nxt, false, crit, alpha, ravg_prev, a3,
                                            pend);
                 if (k == K - 1) {
-                    a3[0] += abs_of_sq<T>(pend);
-                    pend = 0.0;
+                    a3[0] += abs_of_pair(pend.x, pend.y);
+                    pend = make_double2(0.0, 0.0);
                 }
                 if (mixed && k == K - 1) {
                     if (!cd_grid_sync(ctrl, nb, epoch)) return;
