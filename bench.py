@@ -85,6 +85,8 @@ def parse():
                     help="1: per-particle update counts instead of a grid barrier per colour")
     ap.add_argument("--domains", type=int, nargs=3, default=[1, 1, 1], metavar=("NX", "NY", "NZ"),
                     help="domain-wise update of Sec. 3.1: slabs per axis (1 1 1: Gauss-Seidel)")
+    ap.add_argument("--merge-last-colour", type=int, default=1,
+                    help="1: run the two last colours as one phase when the last class is small")
     ap.add_argument("--sphere-steps", type=int, default=5,
                     help="timed steps of the 1e6-sphere 3D gas leg (rank 0 at N=1 only; 0: skip)")
     ap.add_argument("--batched-steps", type=int, default=3,
@@ -123,6 +125,7 @@ def config(args, wl, extra=None):
               "order": ("colour (largest degree first, then hash)" if args.tile_cells == 0 else
                         f"tiled colour order, {args.tile_cells}-cell tiles"),
               "domains": list(args.domains),
+              "merge_last_colour": bool(args.merge_last_colour),
               "l2": "flushed (512 MiB write) before every timed step"})
     if extra:
         c.update(extra)
@@ -314,7 +317,7 @@ def run_ours(args):
         tuned = {"choice": shape, "ms_per_sweep": [[c, m] for c, m in table]}
     sysg = cd.CDSystem(wl, device=device, precision=prec, criterion=cd.CD_CONV_GLOBAL_REL, max_contacts=4 * wl.n,
                        timing=1, stream=stream, tile_cells=args.tile_cells, dataflow=args.dataflow,
-                       domains=tuple(args.domains), **shape)
+                       domains=tuple(args.domains), merge_last_colour=args.merge_last_colour, **shape)
     flush = torch.empty(512 << 20, dtype=torch.uint8, device=device)
 
     for _ in range(args.warmup):
@@ -329,7 +332,7 @@ def run_ours(args):
     upd = sweeps = launches = not_conv = 0
     ph = {"detect": 0.0, "colour_order_pack": 0.0, "sweep": 0.0, "integrate": 0.0}
     sweep_bytes = 0.0
-    ncs, colours = [], []
+    ncs, colours, phases = [], [], []
     if wl.dim == 3:
         bpc, bpp = BYTES_PER_CONTACT_3D[args.precision], BYTES_PER_PARTICLE_3D[args.precision]
     else:
@@ -345,6 +348,7 @@ def run_ours(args):
         nc = st["last"]["n_contacts"]
         ncs.append(nc)
         colours.append(st["last"]["n_colours"])
+        phases.append(st["last"]["n_phases"])
         sweep_bytes += st["total_sweeps"] * (nc * bpc + wl.n * bpp)
         for k in ph:
             ph[k] += st["phase_ms"][k]
@@ -414,6 +418,7 @@ def run_ours(args):
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": args.precision,
             "data": "synthetic (seeded gravity deposition)",
             "config": config(args, wl, {"mean_contacts": float(np.mean(ncs)), "mean_colours": float(np.mean(colours)),
+                                        "mean_phases_per_sweep": float(np.mean(phases)),
                                         "sweeps_per_step": sweeps / max(args.steps, 1),
                                         "steps_not_converged": not_conv, "parallelism": f"replicas x{ws}"}),
             "phase_ms_per_step": {k: v / max(args.steps, 1) for k, v in ph.items()},

@@ -182,6 +182,19 @@ typedef struct {
                                contact of capacity.  Plain systems with the
                                colour-barrier schedule, kinematic walls, no
                                mixed update, no tape.  All 1: Gauss-Seidel. */
+    int64_t merge_last_colour; /* colour-barrier schedule of a plain system:
+                               1 lets a step run its two last colours in one
+                               phase when the last class is small (at most a
+                               quarter of the one before): the contacts of
+                               the two colours are grouped into the chains
+                               that share particles (each at most 64
+                               contacts), every chain goes whole to one block,
+                               which updates the chains' contacts of the
+                               earlier colour, synchronises its threads and
+                               then updates those of the last colour.  The
+                               order is the colour order, so results equal
+                               those without merging; one grid barrier per
+                               sweep fewer.  0: every colour its own phase. */
 } cd_params;
 
 typedef struct cd_system cd_system;
@@ -194,6 +207,9 @@ typedef struct {
     int64_t n_contacts;
     int64_t n_colours;
     double wall_force[6];     /* sum of normal impulses on each wall / dt */
+    int64_t n_phases;         /* grid-barrier phases per sweep: n_colours, or
+                                 one fewer when the two last colours ran as
+                                 one phase (params.merge_last_colour) */
 } cd_solve_stats;
 
 typedef struct {

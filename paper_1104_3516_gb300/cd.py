@@ -69,6 +69,7 @@ class cd_params(C.Structure):
         ("wall_push", C.c_double * 6),
         ("wall_mass", C.c_double * 6),
         ("domains", C.c_int64 * 3),
+        ("merge_last_colour", C.c_int64),
     ]
 
 
@@ -81,12 +82,13 @@ class cd_solve_stats(C.Structure):
         ("n_contacts", C.c_int64),
         ("n_colours", C.c_int64),
         ("wall_force", C.c_double * 6),
+        ("n_phases", C.c_int64),
     ]
 
     def as_dict(self):
         return {"sweeps": int(self.sweeps), "converged": bool(self.converged), "residual": float(self.residual),
                 "r_avg": float(self.r_avg), "n_contacts": int(self.n_contacts), "n_colours": int(self.n_colours),
-                "wall_force": [float(v) for v in self.wall_force]}
+                "wall_force": [float(v) for v in self.wall_force], "n_phases": int(self.n_phases)}
 
 
 class cd_step_stats(C.Structure):
@@ -369,7 +371,7 @@ def cd_last_error(sysptr=None) -> str:
 def make_params(wl, precision=CD_FP64, criterion=CD_CONV_GLOBAL_REL, max_contacts=None, warm_start=1, rotations=1,
                 seed=None, max_sweeps=None, alpha=None, timing=0, tile_cells=0, dataflow=0,
                 parallel_p=0.0, tape_steps=0, adjoint_compliance=0.0, use_graph=0, sweep_threads=0,
-                sweep_blocks_per_sm=0, domains=(1, 1, 1)) -> cd_params:
+                sweep_blocks_per_sm=0, domains=(1, 1, 1), merge_last_colour=1) -> cd_params:
     p = cd_params()
     p.dim = wl.dim
     p.precision = precision
@@ -411,6 +413,7 @@ def make_params(wl, precision=CD_FP64, criterion=CD_CONV_GLOBAL_REL, max_contact
         p.wall_mass[k] = float(mass[k])
     for k in range(3):
         p.domains[k] = int(domains[k])
+    p.merge_last_colour = int(merge_last_colour)
     return p
 
 

@@ -184,6 +184,21 @@ static size_t layout(cd_system* s, char* base, CdWork* w)
         t.V0 = L.take<char>(base, (dom ? vcap : 1) * vrec);
         t.c_vab = L.take<int2>(base, dom ? cap : 1);
     }
+    {
+        const bool mg = s->g.merge_last != 0;
+        const size_t nbk = 2 * (size_t)s->g.merge_blocks + 1;
+        t.mg_pa = L.take<int>(base, mg ? n : 1);
+        t.mg_pb = L.take<int>(base, mg ? n : 1);
+        t.mg_label = L.take<int>(base, mg ? cap : 1);
+        t.mg_size = L.take<int>(base, mg ? cap + 1 : 1);
+        t.mg_start = L.take<int>(base, mg ? cap + 1 : 1);
+        t.mg_bucket = L.take<int>(base, mg ? cap : 1);
+        t.mg_list = L.take<int>(base, mg ? cap : 1);
+        t.mg_bcnt = L.take<int>(base, mg ? nbk : 1);
+        t.mg_boff = L.take<int>(base, mg ? nbk : 1);
+        t.mg_bmin = L.take<int>(base, mg ? nbk : 1);
+        t.mg_bmax = L.take<int>(base, mg ? nbk : 1);
+    }
     t.rep_top = L.take<int>(base, npk);
     t.rep_dmax = L.take<int>(base, npk);
     t.rep_flag = L.take<int>(base, cap + 1);
@@ -286,7 +301,7 @@ static void fill_solve_stats(const cd_system* s, const CdCtrl& h, cd_solve_stats
     o->n_contacts = h.nc;
     o->n_colours = h.ncolours;
     for (int k = 0; k < 6; ++k) o->wall_force[k] = h.wall_force[k];
-    (void)s;
+    o->n_phases = h.ncolours - ((s->g.merge_last && h.merge) ? 1 : 0);
 }
 
 static cd_status need_ready(cd_system* s)
@@ -312,6 +327,7 @@ static cd_status launch_detect_chain(cd_system* s, int timed)
     if (s->g.dataflow) CD_CUDA(s, cd_launch_need(s->g, s->w, s->stream, &s->launches));
     if (s->g.ndom_total > 1)
         CD_CUDA(s, cd_launch_domains(s->g, s->w, s->pos, s->radius, s->stream, &s->launches));
+    if (s->g.merge_last) CD_CUDA(s, cd_launch_merge(s->g, s->w, s->colour_blocks, s->stream, &s->launches));
     return CD_OK;
 }
 
@@ -629,6 +645,20 @@ static cd_status create_impl(const cd_params* params, int64_t npk, const int64_t
         s->sweep_threads = th;
         s->sweep_blocks = s->num_sms * per;
     }
+    // merging of the two last colours: plain systems with the colour-barrier
+    // schedule (ignored otherwise)
+    if (p.merge_last_colour != 0 && p.merge_last_colour != 1) {
+        delete s;
+        return fail(nullptr, CD_ERR_INVALID_ARG, "merge_last_colour must be 0 or 1");
+    }
+    g.merge_last = (p.merge_last_colour && npk == 1 && g.tile_cells == 0 && !g.dataflow && g.par_p == 0.0 &&
+                    g.ndom_total == 1 && !g.dyn_walls && p.tape_steps == 0 && cd_merge_label_blocks_per_sm() >= 1)
+                       ? 1 : 0;
+    g.merge_blocks = s->sweep_blocks;
+    if (g.merge_last && !cd_sweep_fits(g, (int)p.precision, s->sweep_threads, s->sweep_blocks / s->num_sms)) {
+        delete s;
+        return fail(nullptr, CD_ERR_INVALID_ARG, "that many sweep blocks do not fit on one SM");
+    }
     *out = s;
     return CD_OK;
 }
@@ -747,6 +777,7 @@ extern "C" cd_status cd_set_contacts(cd_system* s, int64_t nc, const int32_t* pa
     if (s->g.dataflow) CD_CUDA(s, cd_launch_need(s->g, s->w, s->stream, &s->launches));
     if (s->g.ndom_total > 1)
         CD_CUDA(s, cd_launch_domains(s->g, s->w, s->pos, s->radius, s->stream, &s->launches));
+    if (s->g.merge_last) CD_CUDA(s, cd_launch_merge(s->g, s->w, s->colour_blocks, s->stream, &s->launches));
     CdCtrl h;
     if ((st = read_ctrl(s, &h)) != CD_OK) return st;
     st = ctrl_status(s, h);

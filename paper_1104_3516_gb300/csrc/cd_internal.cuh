@@ -56,6 +56,11 @@ struct CdCtrl {
     long long adj_diverged;
     int tape_slot;                  // slot the next recorded step goes to
     int tape_pad;
+    // merging of the two last colours (params.merge_last_colour)
+    int merge;                      // 1: this step's sweeps run the two last colours as one phase
+    int mg_changed;                 // chain labelling: a label moved in the current round
+    int mg_maxsize;                 // largest chain
+    int mg_pad;
 };
 
 // Parameters of one packing of a batched system (a plain system is a batch of
@@ -160,6 +165,20 @@ struct CdWork {
     int* view_owner;    // 2 cap: particle of each view record
     void* V0;           // 2 cap velocity records: the sweep-start velocity of the view's particle
     int2* c_vab;        // cap (colour order): velocity records of bodies a and b
+    // merging of the two last colours: the colour-order positions of the two
+    // last colours form chains (contacts linked through a shared particle);
+    // chains are assigned whole to the blocks of the sweep grid
+    int* mg_pa;         // n: position of the particle's contact of the second-last colour, or -1
+    int* mg_pb;         // n: position of its contact of the last colour, or -1
+    int* mg_label;      // cap: chain label (smallest position of the chain)
+    int* mg_size;       // cap + 1: contacts of the chain labelled by the index
+    int* mg_start;      // cap + 1: exclusive scan of mg_size
+    int* mg_bucket;     // cap: block (second-last colour) or G + block (last colour)
+    int* mg_list;       // cap: positions grouped by bucket, ascending inside each
+    int* mg_bcnt;       // 2 G + 1: contacts per bucket
+    int* mg_boff;       // 2 G + 1: exclusive scan of mg_bcnt
+    int* mg_bmin;       // 2 G: lowest position of the bucket
+    int* mg_bmax;       // 2 G: highest position of the bucket
     // repair of the highest colour (global colour order)
     int* rep_top;       // npk: highest colour of each packing
     int* rep_dmax;      // npk: most contacts of one body of the packing
@@ -260,6 +279,8 @@ struct CdGeom {
     double wall_push[6];// its push along the inward normal
     int ndom[3];        // domain-wise update (Sec. 3.1): slabs per axis (1: not cut)
     int ndom_total;     // product; > 1 selects the domain-wise sweep
+    int merge_last;     // params.merge_last_colour
+    int merge_blocks;   // blocks of the sweep grid the chains are assigned to
 };
 
 // Velocity records of the domain views start after the particles' and the
@@ -428,6 +449,8 @@ cudaError_t cd_launch_order_tiled(const CdGeom& g, const CdWork& w, const double
 cudaError_t cd_launch_need(const CdGeom& g, const CdWork& w, cudaStream_t stream, int* nl);
 cudaError_t cd_launch_domains(const CdGeom& g, const CdWork& w, const double* pos, const double* radius,
                               cudaStream_t stream, int* nl);
+cudaError_t cd_launch_merge(const CdGeom& g, const CdWork& w, int coop_blocks, cudaStream_t stream, int* nl);
+int cd_merge_label_blocks_per_sm();
 cudaError_t cd_launch_pk_ranges(const CdGeom& g, const CdWork& w, cudaStream_t stream, int* nl);
 cudaError_t cd_launch_orient(const CdGeom& g, const CdWork& w, int nbins, unsigned long long* counts,
                              cudaStream_t stream, int* nl);

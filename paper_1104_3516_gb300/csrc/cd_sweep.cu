@@ -24,16 +24,40 @@
 
 // Variants of the persistent colour-barrier sweep: plain Gauss-Seidel, the
 // mixed update of Sec. 2.3, the domain-wise update of Sec. 3.1.
-enum { CD_SWEEP_PLAIN = 0, CD_SWEEP_MIXED = 1, CD_SWEEP_DOMAINS = 2 };
+enum { CD_SWEEP_PLAIN = 0, CD_SWEEP_MIXED = 1, CD_SWEEP_DOMAINS = 2, CD_SWEEP_MERGE = 3 };
+
+// Merged last phase of a step (params.merge_last_colour): this block's lists
+// of second-last-colour positions [a0, a1) and last-colour positions [b0, b1)
+// in mg_list; phase `klast` runs them in place of the two last colours.  The
+// block's items are numbered A first, then B; item q goes to thread
+// q % blockDim, so a thread's first item (prefetched before the grid
+// barrier) is an A or a B contact and the B contacts wait after the block
+// barrier only for their velocities.
+struct MgInfo {
+    int on;
+    int klast;
+    int a0, a1, b0, b1;
+};
 
 template <typename T> struct Vec;
 template <> struct Vec<double> { typedef double4 V4; typedef double2 V2; };
 template <> struct Vec<float> { typedef float4 V4; typedef float2 V2; };
 
-// Fused multiply-add of the sweep's real type, rounded once.
+// Arithmetic of the sweep's real type with the rounding written out (no
+// contraction left to the compiler): fused multiply-add rounded once,
+// product, sum and difference.
 template <typename T> __device__ __forceinline__ T fma_of(T a, T b, T c);
 template <> __device__ __forceinline__ double fma_of<double>(double a, double b, double c) { return __fma_rn(a, b, c); }
 template <> __device__ __forceinline__ float fma_of<float>(float a, float b, float c) { return __fmaf_rn(a, b, c); }
+template <typename T> __device__ __forceinline__ T mul_of(T a, T b);
+template <> __device__ __forceinline__ double mul_of<double>(double a, double b) { return __dmul_rn(a, b); }
+template <> __device__ __forceinline__ float mul_of<float>(float a, float b) { return __fmul_rn(a, b); }
+template <typename T> __device__ __forceinline__ T add_of(T a, T b);
+template <> __device__ __forceinline__ double add_of<double>(double a, double b) { return __dadd_rn(a, b); }
+template <> __device__ __forceinline__ float add_of<float>(float a, float b) { return __fadd_rn(a, b); }
+template <typename T> __device__ __forceinline__ T sub_of(T a, T b);
+template <> __device__ __forceinline__ double sub_of<double>(double a, double b) { return __dsub_rn(a, b); }
+template <> __device__ __forceinline__ float sub_of<float>(float a, float b) { return __fsub_rn(a, b); }
 
 // Stores the first three components of a velocity record, leaving the fourth.
 template <typename T>
@@ -365,6 +389,9 @@ __device__ __forceinline__ UpdOut core2d(const CdGeom& g, const Rec<2, T>& r, ty
                                          typename Vec<T>::V4& vb, bool wall, bool apply_only, int crit,
                                          double alpha, double ravg_prev, typename Vec<T>::V2& Pnew)
 {
+    // every operation is written out (fused steps where they save an
+    // instruction): each kernel and call site that inlines this computes the
+    // same bits
     const T nx = r.geo.x, ny = r.geo.y;
     T Pn, Pt, dPn, dPt;
     if (apply_only) {
@@ -372,36 +399,36 @@ __device__ __forceinline__ UpdOut core2d(const CdGeom& g, const Rec<2, T>& r, ty
         dPn = Pn; dPt = Pt;
     } else {
         const T b = r.geo.z, mn = r.geo.w;
-        T dvx = vb.x - va.x, dvy = vb.y - va.y;
-        T un = dvx * nx + dvy * ny;
-        // u_t = (dv x n) - (r_a w_a + r_b w_b); in FP64 as one chain of fused
-        // steps (one instruction fewer on the narrow pipe)
-        T ut;
-        if constexpr (sizeof(T) == 8) {
-            ut = fma_of<T>(dvy, nx, -(dvx * ny));
-            ut = fma_of<T>(-r.sa.y, va.z, ut);
-            ut = fma_of<T>(-r.sb.y, vb.z, ut);
-        } else {
-            ut = (dvy * nx - dvx * ny) - (r.sa.y * va.z + r.sb.y * vb.z);
-        }
-        Pn = pos_part(r.P.x - mn * (b + un));
-        T lim = r.mu * Pn;
-        Pt = clamp_sym(r.P.y - r.mt * ut, lim);
-        dPn = Pn - r.P.x; dPt = Pt - r.P.y;
+        const T dvx = sub_of<T>(vb.x, va.x), dvy = sub_of<T>(vb.y, va.y);
+        const T un = fma_of<T>(dvy, ny, mul_of<T>(dvx, nx));
+        // u_t = (dv x n) - (r_a w_a + r_b w_b)
+        T ut = fma_of<T>(dvy, nx, -mul_of<T>(dvx, ny));
+        ut = fma_of<T>(-r.sa.y, va.z, ut);
+        ut = fma_of<T>(-r.sb.y, vb.z, ut);
+        Pn = pos_part(fma_of<T>(-mn, add_of<T>(b, un), r.P.x));
+        const T lim = mul_of<T>(r.mu, Pn);
+        Pt = clamp_sym(fma_of<T>(-r.mt, ut, r.P.y), lim);
+        dPn = sub_of<T>(Pn, r.P.x);
+        dPt = sub_of<T>(Pt, r.P.y);
     }
-    T dPx = dPn * nx - dPt * ny, dPy = dPn * ny + dPt * nx;
-    va.x -= r.sa.x * dPx; va.y -= r.sa.x * dPy; va.z -= r.sa.z * dPt;
+    const T dPx = fma_of<T>(dPn, nx, -mul_of<T>(dPt, ny));
+    const T dPy = fma_of<T>(dPn, ny, mul_of<T>(dPt, nx));
+    va.x = fma_of<T>(-r.sa.x, dPx, va.x);
+    va.y = fma_of<T>(-r.sa.x, dPy, va.y);
+    va.z = fma_of<T>(-r.sa.z, dPt, va.z);
     if (!wall) {
-        vb.x += r.sb.x * dPx; vb.y += r.sb.x * dPy; vb.z -= r.sb.z * dPt;
+        vb.x = fma_of<T>(r.sb.x, dPx, vb.x);
+        vb.y = fma_of<T>(r.sb.x, dPy, vb.y);
+        vb.z = fma_of<T>(-r.sb.z, dPt, vb.z);
     }
     Pnew.x = Pn; Pnew.y = Pt;
     UpdOut o;
-    double pn = (double)Pn, pt = (double)Pt;
+    const double pn = (double)Pn, pt = (double)Pt;
     // SQ (FP64): the pair only, the magnitude is taken later (abs_of_pair)
     o.pn = pn;
     o.pt = pt;
     if constexpr (sizeof(T) == 4) {
-        o.psq = (double)(Pn * Pn + Pt * Pt);
+        o.psq = (double)fma_of<T>(Pt, Pt, mul_of<T>(Pn, Pn));
         o.pabs = abs_of_sq<T>(o.psq);
     } else {
         o.psq = 0.0;
@@ -409,11 +436,11 @@ __device__ __forceinline__ UpdOut core2d(const CdGeom& g, const Rec<2, T>& r, ty
     }
     o.rel_ok = 0; o.bad = 0;
     if (!apply_only && crit == CD_CONV_LOCAL) {
-        double d0 = (double)dPn, d1 = (double)dPt;
-        double s0 = pn + (double)r.P.x, s1 = pt + (double)r.P.y;
-        double d2 = d0 * d0 + d1 * d1, s2 = s0 * s0 + s1 * s1;
-        o.rel_ok = d2 < alpha * s2;
-        o.bad = !o.rel_ok && !(d2 <= alpha * ravg_prev * ravg_prev);
+        const double d0 = (double)dPn, d1 = (double)dPt;
+        const double s0 = __dadd_rn(pn, (double)r.P.x), s1 = __dadd_rn(pt, (double)r.P.y);
+        const double d2 = sq2(d0, d1), s2 = sq2(s0, s1);
+        o.rel_ok = d2 < __dmul_rn(alpha, s2);
+        o.bad = !o.rel_ok && !(d2 <= __dmul_rn(__dmul_rn(alpha, ravg_prev), ravg_prev));
     }
     return o;
 }
@@ -474,6 +501,7 @@ __device__ __forceinline__ UpdOut core3d(const CdGeom& g, const Rec<3, T>& r, ty
                                          bool wall, bool apply_only, int crit, double alpha, double ravg_prev,
                                          typename Vec<T>::V4& Pnew)
 {
+    // every operation written out, as in core2d
     const T nx = r.geo.x, ny = r.geo.y, nz = r.geo.z;
     T Pn, Ptx, Pty, Ptz, dPn, dtx, dty, dtz;
     if (apply_only) {
@@ -482,45 +510,57 @@ __device__ __forceinline__ UpdOut core3d(const CdGeom& g, const Rec<3, T>& r, ty
     } else {
         const T mn = r.m.x, mt = r.m.y, b = r.geo.w;
         // relative velocity of the contact points: (vb - va) - (ra wa + rb wb) x n
-        T lx = r.sa.y * wa.x + r.sb.y * wb.x, ly = r.sa.y * wa.y + r.sb.y * wb.y, lz = r.sa.y * wa.z + r.sb.y * wb.z;
-        T gx = (vb.x - va.x) - (ly * nz - lz * ny);
-        T gy = (vb.y - va.y) - (lz * nx - lx * nz);
-        T gz = (vb.z - va.z) - (lx * ny - ly * nx);
-        T un = gx * nx + gy * ny + gz * nz;
-        T tx = gx - un * nx, ty = gy - un * ny, tz = gz - un * nz;
-        Pn = pos_part(r.P.x - mn * (b + un));
-        Ptx = r.P.y - mt * tx; Pty = r.P.z - mt * ty; Ptz = r.P.w - mt * tz;
-        T lim = r.mu * Pn;
-        T q2 = Ptx * Ptx + Pty * Pty + Ptz * Ptz;
-        if (q2 > lim * lim) {
-            T sc = lim * rsqrt(q2);   // onto the cone (q2 > lim^2 >= 0)
-            Ptx *= sc; Pty *= sc; Ptz *= sc;
+        const T lx = fma_of<T>(r.sb.y, wb.x, mul_of<T>(r.sa.y, wa.x));
+        const T ly = fma_of<T>(r.sb.y, wb.y, mul_of<T>(r.sa.y, wa.y));
+        const T lz = fma_of<T>(r.sb.y, wb.z, mul_of<T>(r.sa.y, wa.z));
+        const T gx = sub_of<T>(sub_of<T>(vb.x, va.x), fma_of<T>(ly, nz, -mul_of<T>(lz, ny)));
+        const T gy = sub_of<T>(sub_of<T>(vb.y, va.y), fma_of<T>(lz, nx, -mul_of<T>(lx, nz)));
+        const T gz = sub_of<T>(sub_of<T>(vb.z, va.z), fma_of<T>(lx, ny, -mul_of<T>(ly, nx)));
+        const T un = fma_of<T>(gz, nz, fma_of<T>(gy, ny, mul_of<T>(gx, nx)));
+        const T tx = fma_of<T>(-un, nx, gx), ty = fma_of<T>(-un, ny, gy), tz = fma_of<T>(-un, nz, gz);
+        Pn = pos_part(fma_of<T>(-mn, add_of<T>(b, un), r.P.x));
+        Ptx = fma_of<T>(-mt, tx, r.P.y);
+        Pty = fma_of<T>(-mt, ty, r.P.z);
+        Ptz = fma_of<T>(-mt, tz, r.P.w);
+        const T lim = mul_of<T>(r.mu, Pn);
+        const T q2 = fma_of<T>(Ptz, Ptz, fma_of<T>(Pty, Pty, mul_of<T>(Ptx, Ptx)));
+        if (q2 > mul_of<T>(lim, lim)) {
+            const T sc = mul_of<T>(lim, rsqrt(q2));   // onto the cone (q2 > lim^2 >= 0)
+            Ptx = mul_of<T>(Ptx, sc); Pty = mul_of<T>(Pty, sc); Ptz = mul_of<T>(Ptz, sc);
         }
-        dPn = Pn - r.P.x; dtx = Ptx - r.P.y; dty = Pty - r.P.z; dtz = Ptz - r.P.w;
+        dPn = sub_of<T>(Pn, r.P.x);
+        dtx = sub_of<T>(Ptx, r.P.y); dty = sub_of<T>(Pty, r.P.z); dtz = sub_of<T>(Ptz, r.P.w);
     }
-    T dx = dPn * nx + dtx, dy = dPn * ny + dty, dz = dPn * nz + dtz;
+    const T dx = fma_of<T>(dPn, nx, dtx), dy = fma_of<T>(dPn, ny, dty), dz = fma_of<T>(dPn, nz, dtz);
     // n x dP
-    T cx = ny * dz - nz * dy, cy = nz * dx - nx * dz, cz = nx * dy - ny * dx;
-    va.x -= r.sa.x * dx; va.y -= r.sa.x * dy; va.z -= r.sa.x * dz;
-    wa.x -= r.sa.z * cx; wa.y -= r.sa.z * cy; wa.z -= r.sa.z * cz;
+    const T cx = fma_of<T>(ny, dz, -mul_of<T>(nz, dy));
+    const T cy = fma_of<T>(nz, dx, -mul_of<T>(nx, dz));
+    const T cz = fma_of<T>(nx, dy, -mul_of<T>(ny, dx));
+    va.x = fma_of<T>(-r.sa.x, dx, va.x); va.y = fma_of<T>(-r.sa.x, dy, va.y); va.z = fma_of<T>(-r.sa.x, dz, va.z);
+    wa.x = fma_of<T>(-r.sa.z, cx, wa.x); wa.y = fma_of<T>(-r.sa.z, cy, wa.y); wa.z = fma_of<T>(-r.sa.z, cz, wa.z);
     if (!wall) {
-        vb.x += r.sb.x * dx; vb.y += r.sb.x * dy; vb.z += r.sb.x * dz;
-        wb.x -= r.sb.z * cx; wb.y -= r.sb.z * cy; wb.z -= r.sb.z * cz;
+        vb.x = fma_of<T>(r.sb.x, dx, vb.x); vb.y = fma_of<T>(r.sb.x, dy, vb.y); vb.z = fma_of<T>(r.sb.x, dz, vb.z);
+        wb.x = fma_of<T>(-r.sb.z, cx, wb.x); wb.y = fma_of<T>(-r.sb.z, cy, wb.y); wb.z = fma_of<T>(-r.sb.z, cz, wb.z);
     }
     Pnew.x = Pn; Pnew.y = Ptx; Pnew.z = Pty; Pnew.w = Ptz;
     UpdOut o;
-    double pn = (double)Pn, px = (double)Ptx, py = (double)Pty, pz = (double)Ptz;
-    if constexpr (sizeof(T) == 4) o.psq = (double)(Pn * Pn + Ptx * Ptx + Pty * Pty + Ptz * Ptz);
-    else o.psq = pn * pn + px * px + py * py + pz * pz;
+    const double pn = (double)Pn, px = (double)Ptx, py = (double)Pty, pz = (double)Ptz;
+    o.pn = pn;
+    o.pt = 0.0;
+    if constexpr (sizeof(T) == 4)
+        o.psq = (double)fma_of<T>(Ptz, Ptz, fma_of<T>(Pty, Pty, fma_of<T>(Ptx, Ptx, mul_of<T>(Pn, Pn))));
+    else
+        o.psq = __fma_rn(pz, pz, __fma_rn(py, py, __fma_rn(px, px, __dmul_rn(pn, pn))));
     o.pabs = SQ ? 0.0 : abs_of_sq<T>(o.psq);
     o.rel_ok = 0; o.bad = 0;
     if (!apply_only && crit == CD_CONV_LOCAL) {
-        double d0 = (double)dPn, d1 = (double)dtx, d2_ = (double)dty, d3 = (double)dtz;
-        double s0 = pn + (double)r.P.x, s1 = px + (double)r.P.y, s2_ = py + (double)r.P.z, s3 = pz + (double)r.P.w;
-        double d2 = d0 * d0 + d1 * d1 + d2_ * d2_ + d3 * d3;
-        double s2 = s0 * s0 + s1 * s1 + s2_ * s2_ + s3 * s3;
-        o.rel_ok = d2 < alpha * s2;
-        o.bad = !o.rel_ok && !(d2 <= alpha * ravg_prev * ravg_prev);
+        const double d0 = (double)dPn, d1 = (double)dtx, d2_ = (double)dty, d3 = (double)dtz;
+        const double s0 = __dadd_rn(pn, (double)r.P.x), s1 = __dadd_rn(px, (double)r.P.y);
+        const double s2_ = __dadd_rn(py, (double)r.P.z), s3 = __dadd_rn(pz, (double)r.P.w);
+        const double d2 = __fma_rn(d3, d3, __fma_rn(d2_, d2_, __fma_rn(d1, d1, __dmul_rn(d0, d0))));
+        const double s2 = __fma_rn(s3, s3, __fma_rn(s2_, s2_, __fma_rn(s1, s1, __dmul_rn(s0, s0))));
+        o.rel_ok = d2 < __dmul_rn(alpha, s2);
+        o.bad = !o.rel_ok && !(d2 <= __dmul_rn(__dmul_rn(alpha, ravg_prev), ravg_prev));
     }
     return o;
 }
@@ -586,6 +626,23 @@ __device__ __forceinline__ void prefetch_first(const CdGeom& g, const CdWork& w,
     if (sq.p < sq.end) load_rec<DIM, T, VIEWS>(g, w, sq.p, nxt);
 }
 
+// Loads this thread's first record of phase k: of the colour class, or of
+// this block's first list of the merged phase.
+template <int DIM, typename T, int MODE>
+__device__ __forceinline__ void prefetch_any(const CdGeom& g, const CdWork& w, const int* s_off, int k,
+                                             Rec<DIM, T>& nxt, const MgInfo& mg)
+{
+    if constexpr (MODE == CD_SWEEP_MERGE) {
+        if (mg.on && k == mg.klast) {
+            const int q = (int)threadIdx.x, nA = mg.a1 - mg.a0, nB = mg.b1 - mg.b0;
+            if (q < nA) load_rec<DIM, T>(g, w, w.mg_list[mg.a0 + q], nxt);
+            else if (q < nA + nB) load_rec<DIM, T>(g, w, w.mg_list[mg.b0 + (q - nA)], nxt);
+            return;
+        }
+    }
+    prefetch_first<DIM, T, MODE == CD_SWEEP_DOMAINS>(g, w, s_off, k, nxt);
+}
+
 // One colour phase for this thread: its first contact's record was loaded
 // into `nxt` before the barrier (if it has one); the rest are loaded inline.
 // Afterwards `nxt` holds the first record of colour `knext` (prefetch).
@@ -595,13 +652,54 @@ __device__ __forceinline__ void prefetch_first(const CdGeom& g, const CdWork& w,
 template <int DIM, typename T, int MODE>
 __device__ __forceinline__ void colour_phase(const CdGeom& g, const CdWork& w, const int* s_off, int k, int knext,
                                              int tid, int stride, Rec<DIM, T>& nxt, bool apply_only, int crit,
-                                             double alpha, double ravg_prev, double (&acc)[3], double2& pend)
+                                             double alpha, double ravg_prev, double (&acc)[3], double2& pend,
+                                             const MgInfo& mg)
 {
     constexpr bool MIXED = (MODE == CD_SWEEP_MIXED);
     constexpr bool VIEWS = (MODE == CD_SWEEP_DOMAINS);
     // FP64 2D only: FP32 takes its square root on the fast pipe, and in 3D the
     // extra live value spills
     constexpr bool DEFER = (DIM == 2) && std::is_same<T, double>::value;
+    if constexpr (MODE == CD_SWEEP_MERGE) {
+        if (mg.on && k == mg.klast) {
+            // the chains' second-last-colour contacts, a block barrier, their last-colour ones
+            const int t = (int)threadIdx.x, bd = (int)blockDim.x;
+            const int nA = mg.a1 - mg.a0, tot = nA + (mg.b1 - mg.b0);
+            for (int q = t; q < nA; q += bd) {
+                const int p = w.mg_list[mg.a0 + q];
+                UpdOut o;
+                if (q == t) {
+                    o = apply_rec<DIM, T, false, DEFER>(g, w, p, nxt, apply_only, crit, alpha, ravg_prev, pend);
+                } else {
+                    Rec<DIM, T> r;
+                    load_rec<DIM, T>(g, w, p, r);
+                    o = apply_rec<DIM, T, false, DEFER>(g, w, p, r, apply_only, crit, alpha, ravg_prev, pend);
+                }
+                acc[0] += o.pabs;
+                if (DEFER) pend = make_double2(o.pn, o.pt);
+                if (crit == CD_CONV_LOCAL) { acc[1] += (double)o.rel_ok; acc[2] += (double)o.bad; }
+            }
+            __syncthreads();
+            int q0 = t;
+            if (q0 < nA) q0 += ((nA - q0 + bd - 1) / bd) * bd;   // this thread's first item past the A items
+            for (int q = q0; q < tot; q += bd) {
+                const int p = w.mg_list[mg.b0 + (q - nA)];
+                UpdOut o;
+                if (q == t) {
+                    o = apply_rec<DIM, T, false, DEFER>(g, w, p, nxt, apply_only, crit, alpha, ravg_prev, pend);
+                } else {
+                    Rec<DIM, T> r;
+                    load_rec<DIM, T>(g, w, p, r);
+                    o = apply_rec<DIM, T, false, DEFER>(g, w, p, r, apply_only, crit, alpha, ravg_prev, pend);
+                }
+                acc[0] += o.pabs;
+                if (DEFER) pend = make_double2(o.pn, o.pt);
+                if (crit == CD_CONV_LOCAL) { acc[1] += (double)o.rel_ok; acc[2] += (double)o.bad; }
+            }
+            if (knext >= 0) prefetch_any<DIM, T, MODE>(g, w, s_off, knext, nxt, mg);
+            return;
+        }
+    }
     const CdSpan sp = cd_colour_span(s_off[k], s_off[k + 1]);
     const int end = sp.end;
     int p = sp.p;
@@ -623,7 +721,7 @@ __device__ __forceinline__ void colour_phase(const CdGeom& g, const CdWork& w, c
             if (crit == CD_CONV_LOCAL) { acc[1] += (double)o.rel_ok; acc[2] += (double)o.bad; }
         }
     }
-    if (knext >= 0) prefetch_first<DIM, T, VIEWS>(g, w, s_off, knext, nxt);
+    if (knext >= 0) prefetch_any<DIM, T, MODE>(g, w, s_off, knext, nxt, mg);
     (void)tid; (void)stride;
 }
 
@@ -852,12 +950,27 @@ k_sweep(CdGeom g, CdWork w, int crit, double alpha, int max_sweeps)
     CdCtrl* ctrl = w.ctrl;
     if (ctrl->skip) return;
     const int nc = ctrl->nc;
-    const int K = ctrl->ncolours;
+    int K = ctrl->ncolours;
     const int nb = gridDim.x;
     const int tid = blockIdx.x * blockDim.x + threadIdx.x;
     const int stride = gridDim.x * blockDim.x;
     unsigned long long epoch = 0;
     for (int k = threadIdx.x; k <= CD_KMAX; k += blockDim.x) s_off[k] = w.colour_off[k];
+    MgInfo mg;
+    mg.on = 0; mg.klast = -1; mg.a0 = mg.a1 = mg.b0 = mg.b1 = 0;
+    if constexpr (MODE == CD_SWEEP_MERGE) {
+        if (ctrl->merge) {
+            // the two last colours run as one phase (lists built for this grid)
+            mg.on = 1;
+            K -= 1;
+            mg.klast = K - 1;
+            const int b = blockIdx.x;
+            mg.a0 = w.mg_boff[b];
+            mg.a1 = w.mg_boff[b + 1];
+            mg.b0 = w.mg_boff[nb + b];
+            mg.b1 = w.mg_boff[nb + b + 1];
+        }
+    }
     __syncthreads();
 
     int sweeps = 0, converged = (nc == 0);
@@ -868,16 +981,13 @@ k_sweep(CdGeom g, CdWork w, int crit, double alpha, int max_sweeps)
             if (!cd_grid_sync(ctrl, nb, epoch)) return;
         }
         Rec<DIM, T> nxt;
-        {
-            const CdSpan s0 = cd_colour_span(s_off[0], s_off[1]);
-            if (s0.p < s0.end) load_rec<DIM, T, VIEWS>(g, w, s0.p, nxt);
-        }
+        prefetch_any<DIM, T, MODE>(g, w, s_off, 0, nxt, mg);
         // starting impulses, colour by colour
         double acc[3] = {0.0, 0.0, 0.0};
         double2 pend = make_double2(0.0, 0.0);   // this thread's last impulse not yet in the residual sum
         for (int k = 0; k < K; ++k) {
             colour_phase<DIM, T, MODE>(g, w, s_off, k, (k + 1 < K) ? k + 1 : 0, tid, stride, nxt, true, crit, alpha,
-                                       0.0, acc, pend);
+                                       0.0, acc, pend, mg);
             if (k == K - 1) {
                 acc[0] += abs_of_pair(pend.x, pend.y);
                 pend = make_double2(0.0, 0.0);
@@ -917,7 +1027,7 @@ k_sweep(CdGeom g, CdWork w, int crit, double alpha, int max_sweeps)
                 // no prefetch inside the phase: it is issued after the barrier arrival
                 // below, so that the arriving thread's fence does not wait for it
                 colour_phase<DIM, T, MODE>(g, w, s_off, k, -1, tid, stride, nxt, false, crit, alpha, ravg_prev, a3,
-                                           pend);
+                                           pend, mg);
                 if (k == K - 1) {
                     a3[0] += abs_of_pair(pend.x, pend.y);
                     pend = make_double2(0.0, 0.0);
@@ -935,7 +1045,7 @@ k_sweep(CdGeom g, CdWork w, int crit, double alpha, int max_sweeps)
                     }
                 }
                 const unsigned old = cd_grid_arrive(ctrl, nb);
-                if (!mixed || k + 1 < K) prefetch_first<DIM, T, VIEWS>(g, w, s_off, (k + 1 < K) ? k + 1 : 0, nxt);
+                if (!mixed || k + 1 < K) prefetch_any<DIM, T, MODE>(g, w, s_off, (k + 1 < K) ? k + 1 : 0, nxt, mg);
                 if (!cd_grid_wait(ctrl, old, epoch)) return;
             }
             if constexpr (VIEWS) {
@@ -1778,11 +1888,19 @@ static int sweep_kind(const CdGeom& g)
     if (g.dataflow) return 2;
     if (g.par_p > 0.0) return 4;
     if (g.ndom_total > 1) return 5;
+    if (g.merge_last) return 6;
     return 0;
 }
 
 static const void* sweep_fn(int dim, int precision, int tiled)
 {
+    if (tiled == 6) {
+        if (dim == 2)
+            return precision == CD_FP64 ? (const void*)k_sweep<2, double, CD_SWEEP_MERGE>
+                                        : (const void*)k_sweep<2, float, CD_SWEEP_MERGE>;
+        return precision == CD_FP64 ? (const void*)k_sweep<3, double, CD_SWEEP_MERGE>
+                                    : (const void*)k_sweep<3, float, CD_SWEEP_MERGE>;
+    }
     if (tiled == 5) {
         if (dim == 2)
             return precision == CD_FP64 ? (const void*)k_sweep<2, double, CD_SWEEP_DOMAINS>
@@ -1830,7 +1948,7 @@ static size_t tile_smem(int dim, int precision)
 int cd_sweep_max_blocks(int precision, int dim, int num_sms)
 {
     int per_sm = 0;
-    for (int tiled = 0; tiled < 6; ++tiled) {
+    for (int tiled = 0; tiled < 7; ++tiled) {
         const void* fn = sweep_fn(dim, precision, tiled);
         size_t dyn = (tiled == 1) ? tile_smem(dim, precision) : 0;
         if (tiled && cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn) != cudaSuccess)
