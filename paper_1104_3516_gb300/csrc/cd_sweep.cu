@@ -228,23 +228,38 @@ __device__ __forceinline__ double warp_sum(double v)
     return v;
 }
 
-// Block sum of NV values per thread (fixed tree); result valid in thread 0.
+// Sum over the warp, or +0 without any FP64 instruction when every lane
+// holds +0 (a warp of idle threads: the narrow FP64 pipe would spend the
+// same time on it as on a busy warp).  The same bits as warp_sum.
+__device__ __forceinline__ double warp_sum_nz(double v)
+{
+    if (!__any_sync(0xffffffffu, __double_as_longlong(v) != 0)) return v;
+    return warp_sum(v);
+}
+
+// Block sum of the first nv of NV values per thread (fixed tree); result
+// valid in thread 0.  Values nv .. NV-1 stay the thread's own (callers pass
+// nv < NV only when those values are zero everywhere).
 template <int NV>
-__device__ __forceinline__ void block_sum(double (&v)[NV], double (*s_red)[NV])
+__device__ __forceinline__ void block_sum(double (&v)[NV], double (*s_red)[NV], int nv = NV)
 {
     int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
 #pragma unroll
-    for (int j = 0; j < NV; ++j) v[j] = warp_sum(v[j]);
+    for (int j = 0; j < NV; ++j)
+        if (j < nv) v[j] = warp_sum_nz(v[j]);
     if (lane == 0)
 #pragma unroll
-        for (int j = 0; j < NV; ++j) s_red[wid][j] = v[j];
+        for (int j = 0; j < NV; ++j)
+            if (j < nv) s_red[wid][j] = v[j];
     __syncthreads();
     if (wid == 0) {
         int nw = blockDim.x >> 5;
 #pragma unroll
         for (int j = 0; j < NV; ++j) {
-            double x = (lane < nw) ? s_red[lane][j] : 0.0;
-            v[j] = warp_sum(x);
+            if (j < nv) {
+                double x = (lane < nw) ? s_red[lane][j] : 0.0;
+                v[j] = warp_sum_nz(x);
+            }
         }
     }
     __syncthreads();
@@ -264,6 +279,58 @@ __device__ __forceinline__ double grid_total(const double* part, int nblocks, do
     double r = *s_bcast;
     __syncthreads();
     return r;
+}
+
+// Values of the per-block partials a sweep's convergence test reads (the
+// counts of test II only under that test).
+__device__ __forceinline__ int test_values(int crit) { return crit == CD_CONV_LOCAL ? 3 : 1; }
+
+// The convergence test after a sweep (tests I and II) from the block
+// partials part[0 .. 3 nb): warp 0 sums them (the order of grid_total) and
+// thread 0 decides; the result reaches the block through shared memory
+// (s_b3, three doubles), so the FP64 divisions run once per block.
+__device__ __forceinline__ void sweep_test(const double* part, int nb, int nc, int crit, double alpha,
+                                           double ravg_prev, double& ravg, double& resid, int& converged,
+                                           double* s_b3)
+{
+    if (threadIdx.x < 32) {
+        const bool local = (crit == CD_CONV_LOCAL);
+        double x = 0.0, xr = 0.0, xb = 0.0;
+        for (int b = threadIdx.x; b < nb; b += 32) {
+            x += part[b];
+            if (local) { xr += part[nb + b]; xb += part[2 * nb + b]; }
+        }
+        x = warp_sum(x);
+        if (local) { xr = warp_sum(xr); xb = warp_sum(xb); }
+        if (threadIdx.x == 0) {
+            const double ra = x / (double)nc;
+            const double den = ra + ravg_prev;
+            double rs;
+            int cv;
+            if (crit == CD_CONV_GLOBAL_REL) {
+                rs = (den > 0.0) ? fabs(ra - ravg_prev) / den : 0.0;
+                cv = rs < alpha;
+            } else if (crit == CD_CONV_GLOBAL_SQ) {
+                double q = (den > 0.0) ? (ra - ravg_prev) / den : 0.0;
+                rs = q * q;
+                cv = rs < alpha;
+            } else if (local) {
+                rs = (double)(nc - (long long)xr) / (double)nc;
+                cv = (10.0 * xr >= 9.0 * (double)nc) && xb == 0.0;
+            } else {
+                rs = (den > 0.0) ? fabs(ra - ravg_prev) / den : 0.0;
+                cv = 0;
+            }
+            s_b3[0] = ra;
+            s_b3[1] = rs;
+            s_b3[2] = (double)cv;
+        }
+    }
+    __syncthreads();
+    ravg = s_b3[0];
+    resid = s_b3[1];
+    converged = (s_b3[2] != 0.0);
+    __syncthreads();
 }
 
 // ---------------------------------------------------------------------------
@@ -363,7 +430,9 @@ __device__ __forceinline__ float clamp_sym(float x, float lim) { return x < -lim
 // correctly rounded square root costs more FP64 instructions).
 __device__ __forceinline__ double norm_of_sq(double s)
 {
-    return s > 0.0 ? s * rsqrt(s) : 0.0;
+    // 0 < s <= inf on the bit pattern (as s > 0.0, without an FP64 compare)
+    const long long b = __double_as_longlong(s);
+    return (b > 0 && b <= 0x7FF0000000000000LL) ? s * rsqrt(s) : 0.0;
 }
 
 // |P| from the |P|^2 an update left (in the sweep's real type: FP32 impulses
@@ -991,7 +1060,7 @@ k_sweep(CdGeom g, CdWork w, int crit, double alpha, int max_sweeps)
             if (k == K - 1) {
                 acc[0] += abs_of_pair(pend.x, pend.y);
                 pend = make_double2(0.0, 0.0);
-                block_sum<3>(acc, s_red);
+                block_sum<3>(acc, s_red, 1);
                 if (threadIdx.x == 0) w.partials[blockIdx.x] = acc[0];
             }
             if (!cd_grid_sync(ctrl, nb, epoch)) return;
@@ -1029,7 +1098,9 @@ k_sweep(CdGeom g, CdWork w, int crit, double alpha, int max_sweeps)
                 colour_phase<DIM, T, MODE>(g, w, s_off, k, -1, tid, stride, nxt, false, crit, alpha, ravg_prev, a3,
                                            pend, mg);
                 if (k == K - 1) {
-                    a3[0] += abs_of_pair(pend.x, pend.y);
+                    // (a thread without a pending impulse adds nothing: skip the FP64 work)
+                    if ((__double_as_longlong(pend.x) | __double_as_longlong(pend.y)) != 0)
+                        a3[0] += abs_of_pair(pend.x, pend.y);
                     pend = make_double2(0.0, 0.0);
                 }
                 if (mixed && k == K - 1) {
@@ -1037,7 +1108,7 @@ k_sweep(CdGeom g, CdWork w, int crit, double alpha, int max_sweeps)
                     par_apply<DIM, T>(g, w, tid, stride);
                 }
                 if (k == K - 1) {
-                    block_sum<3>(a3, s_red);
+                    block_sum<3>(a3, s_red, test_values(crit));
                     if (threadIdx.x == 0) {
                         part[blockIdx.x] = a3[0];
                         part[nb + blockIdx.x] = a3[1];
@@ -1053,24 +1124,7 @@ k_sweep(CdGeom g, CdWork w, int crit, double alpha, int max_sweeps)
                 if (!cd_grid_sync(ctrl, nb, epoch)) return;
             }
             ++sweeps;
-            ravg = grid_total(part, nb, &s_bc) / (double)nc;
-            double den = ravg + ravg_prev;
-            if (crit == CD_CONV_GLOBAL_REL) {
-                resid = (den > 0.0) ? fabs(ravg - ravg_prev) / den : 0.0;
-                converged = resid < alpha;
-            } else if (crit == CD_CONV_GLOBAL_SQ) {
-                double q = (den > 0.0) ? (ravg - ravg_prev) / den : 0.0;
-                resid = q * q;
-                converged = resid < alpha;
-            } else if (crit == CD_CONV_LOCAL) {
-                double nrel = grid_total(part + nb, nb, &s_bc);
-                double nbad = grid_total(part + 2 * nb, nb, &s_bc);
-                resid = (double)(nc - (long long)nrel) / (double)nc;
-                converged = (10.0 * nrel >= 9.0 * (double)nc) && nbad == 0.0;
-            } else {
-                resid = (den > 0.0) ? fabs(ravg - ravg_prev) / den : 0.0;
-                converged = 0;
-            }
+            sweep_test(part, nb, nc, crit, alpha, ravg_prev, ravg, resid, converged, s_red[0]);
             ravg_prev = ravg;
         }
     }
@@ -1102,7 +1156,7 @@ __device__ __forceinline__ void pk_reduce(const CdGeom& g, const CdWork& w, int 
                 a3[2] += (double)((f >> 1) & 1);
             }
         }
-        block_sum<3>(a3, s_red);
+        block_sum<3>(a3, s_red, (crit == CD_CONV_LOCAL && sweep >= 0) ? 3 : 1);
         if (threadIdx.x == 0) {
             const int ncb = c1 - c0;
             const double R = (ncb > 0) ? a3[0] / (double)ncb : 0.0;
@@ -1541,7 +1595,7 @@ k_sweep_flow(CdGeom g, CdWork w, int crit, double alpha, int max_sweeps)
             if (!ok) s_fail = 1;
             const int buf = (phase & 1);
             double* part = w.partials + (size_t)buf * 3 * nb;
-            block_sum<3>(a3, s_red);
+            block_sum<3>(a3, s_red, apply_only ? 1 : test_values(crit));
             if (threadIdx.x == 0) {
                 part[blockIdx.x] = a3[0];
                 part[nb + blockIdx.x] = a3[1];
@@ -1549,29 +1603,13 @@ k_sweep_flow(CdGeom g, CdWork w, int crit, double alpha, int max_sweeps)
             }
             if (s_fail) return;
             if (!cd_grid_sync(ctrl, nb, epoch)) return;
-            ravg = grid_total(part, nb, &s_bc) / (double)nc;
             if (apply_only) {
+                ravg = grid_total(part, nb, &s_bc) / (double)nc;
                 ravg_prev = ravg;
                 continue;
             }
             ++sweeps;
-            double den = ravg + ravg_prev;
-            if (crit == CD_CONV_GLOBAL_REL) {
-                resid = (den > 0.0) ? fabs(ravg - ravg_prev) / den : 0.0;
-                converged = resid < alpha;
-            } else if (crit == CD_CONV_GLOBAL_SQ) {
-                double q = (den > 0.0) ? (ravg - ravg_prev) / den : 0.0;
-                resid = q * q;
-                converged = resid < alpha;
-            } else if (crit == CD_CONV_LOCAL) {
-                double nrel = grid_total(part + nb, nb, &s_bc);
-                double nbad = grid_total(part + 2 * nb, nb, &s_bc);
-                resid = (double)(nc - (long long)nrel) / (double)nc;
-                converged = (10.0 * nrel >= 9.0 * (double)nc) && nbad == 0.0;
-            } else {
-                resid = (den > 0.0) ? fabs(ravg - ravg_prev) / den : 0.0;
-                converged = 0;
-            }
+            sweep_test(part, nb, nc, crit, alpha, ravg_prev, ravg, resid, converged, s_red[0]);
             ravg_prev = ravg;
         }
     }
@@ -1776,7 +1814,7 @@ k_sweep_tiled(CdGeom g, CdWork w, int crit, double alpha, int max_sweeps)
             for (int rk = s_tc[tc] + blockIdx.x; rk < s_tc[tc + 1]; rk += nb)
                 process_tile<DIM, T>(g, w, rk, sm, true, crit, alpha, 0.0, acc);
             if (tc == g.ntc - 1) {
-                block_sum<3>(acc, s_red);
+                block_sum<3>(acc, s_red, 1);
                 if (threadIdx.x == 0) w.partials[blockIdx.x] = acc[0];
             }
             if (!cd_grid_sync(ctrl, nb, epoch)) return;
@@ -1791,7 +1829,7 @@ k_sweep_tiled(CdGeom g, CdWork w, int crit, double alpha, int max_sweeps)
                 for (int rk = s_tc[tc] + blockIdx.x; rk < s_tc[tc + 1]; rk += nb)
                     process_tile<DIM, T>(g, w, rk, sm, false, crit, alpha, ravg_prev, a3);
                 if (tc == g.ntc - 1) {
-                    block_sum<3>(a3, s_red);
+                    block_sum<3>(a3, s_red, test_values(crit));
                     if (threadIdx.x == 0) {
                         part[blockIdx.x] = a3[0];
                         part[nb + blockIdx.x] = a3[1];
@@ -1801,24 +1839,7 @@ k_sweep_tiled(CdGeom g, CdWork w, int crit, double alpha, int max_sweeps)
                 if (!cd_grid_sync(ctrl, nb, epoch)) return;
             }
             ++sweeps;
-            ravg = grid_total(part, nb, &s_bc) / (double)nc;
-            double den = ravg + ravg_prev;
-            if (crit == CD_CONV_GLOBAL_REL) {
-                resid = (den > 0.0) ? fabs(ravg - ravg_prev) / den : 0.0;
-                converged = resid < alpha;
-            } else if (crit == CD_CONV_GLOBAL_SQ) {
-                double q = (den > 0.0) ? (ravg - ravg_prev) / den : 0.0;
-                resid = q * q;
-                converged = resid < alpha;
-            } else if (crit == CD_CONV_LOCAL) {
-                double nrel = grid_total(part + nb, nb, &s_bc);
-                double nbad = grid_total(part + 2 * nb, nb, &s_bc);
-                resid = (double)(nc - (long long)nrel) / (double)nc;
-                converged = (10.0 * nrel >= 9.0 * (double)nc) && nbad == 0.0;
-            } else {
-                resid = (den > 0.0) ? fabs(ravg - ravg_prev) / den : 0.0;
-                converged = 0;
-            }
+            sweep_test(part, nb, nc, crit, alpha, ravg_prev, ravg, resid, converged, s_red[0]);
             ravg_prev = ravg;
         }
     }
