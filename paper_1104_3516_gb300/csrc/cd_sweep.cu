@@ -426,13 +426,34 @@ __device__ __forceinline__ double clamp_sym(double x, double lim)
 }
 __device__ __forceinline__ float clamp_sym(float x, float lim) { return x < -lim ? -lim : (x > lim ? lim : x); }
 
-// |P| from |P|^2 for the residual only: s * rsqrt(s) (within a few ulp; the
-// correctly rounded square root costs more FP64 instructions).
+// |P| = sqrt(s) from |P|^2 for the residual only, in three FP64
+// instructions (the FP64 pipe is the narrow one).  Write s = m 4^k with m in
+// [1, 4) by exponent arithmetic on the bit pattern; take the FP32 reciprocal
+// square root z of m rounded to FP32 (correctly rounded, __frsqrt_rn, on the
+// wide FP32 pipe); then one Newton step of Heron's iteration for sqrt(m)
+// from y = m z, with z / 2 for 1 / (2 y): y + (m - y^2) z / 2; scale by 2^k.
+// With |z sqrt(m) - 1| = e of order 2^-24 the result is sqrt(s) (1 - 1.5 e^2
+// + O(e^3)), within 1e-14 relative.  Zero, subnormal, infinite, negative and
+// NaN s take s * rsqrt(s) (zero for s <= 0 and NaN, as s > 0.0 would decide).
 __device__ __forceinline__ double norm_of_sq(double s)
 {
-    // 0 < s <= inf on the bit pattern (as s > 0.0, without an FP64 compare)
     const long long b = __double_as_longlong(s);
-    return (b > 0 && b <= 0x7FF0000000000000LL) ? s * rsqrt(s) : 0.0;
+    const int be = (int)(b >> 52);   // biased exponent (sign clear for s >= 0)
+    if (be <= 0 || be >= 0x7FF) return (b > 0 && b <= 0x7FF0000000000000LL) ? s * rsqrt(s) : 0.0;
+    const int e = be - 1023;
+    const int k = e >> 1;   // floor(e / 2)
+    const long long mb = (b & 0x000FFFFFFFFFFFFFLL) | ((long long)(1023 + e - 2 * k) << 52);
+    const double m = __longlong_as_double(mb);
+    // m to FP32, rounded to nearest (a carry into the exponent is the rounding)
+    const float mf = __int_as_float((int)(((mb + (1LL << 28)) >> 29) - (896LL << 23)));
+    const float zf = __frsqrt_rn(mf);   // in [0.5, 1]
+    const long long zb = ((long long)__float_as_int(zf) << 29) + (896LL << 52);   // exact widening
+    const double z = __longlong_as_double(zb);
+    const double h = __longlong_as_double(zb - (1LL << 52));                      // z / 2
+    const double y = __dmul_rn(m, z);
+    const double r = __fma_rn(-y, y, m);
+    const double y1 = __fma_rn(r, h, y);
+    return __longlong_as_double(__double_as_longlong(y1) + ((long long)k << 52));
 }
 
 // |P| from the |P|^2 an update left (in the sweep's real type: FP32 impulses
