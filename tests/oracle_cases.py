@@ -55,17 +55,21 @@ def chain(n=8, radius=1.0, force=1.0):
     return wl, f
 
 
-def incline(theta, mu, dim=2, frozen=True, radius=1.0):
+def incline(theta, mu, dim=2, frozen=True, radius=1.0, azimuth=0.0):
     """One particle resting on the floor with gravity tilted by theta:
-    g = (sin theta, -cos theta) (2D) or (sin theta, 0, -cos theta) (3D)."""
+    g = (sin theta, -cos theta) (2D) or (sin theta cos phi, sin theta sin phi,
+    -cos theta) (3D, phi = azimuth: the slope's downhill direction in the
+    floor plane)."""
     if dim == 2:
         inv_I = np.zeros(1) if frozen else None
         return _wl("incline", 2, [[0.0, radius]], [radius], inv_I=inv_I, dt=DT, mu=mu,
                    gravity=(G * math.sin(theta), -G * math.cos(theta), 0.0), box_lo=(-10.0, 0.0, 0.0),
                    box_hi=(10.0, 10.0, 1.0), wall_mask=0b0100)
     inv_I = np.zeros(1) if frozen else None
+    gx = G * math.sin(theta) * math.cos(azimuth)
+    gy = G * math.sin(theta) * math.sin(azimuth) if azimuth != 0.0 else 0.0
     return _wl("incline3", 3, [[0.0, 0.0, radius]], [radius], inv_I=inv_I, dt=DT, mu=mu,
-               gravity=(G * math.sin(theta), 0.0, -G * math.cos(theta)), box_lo=(-10.0, -10.0, 0.0),
+               gravity=(gx, gy, -G * math.cos(theta)), box_lo=(-10.0, -10.0, 0.0),
                box_hi=(10.0, 10.0, 10.0), wall_mask=0b010000)
 
 

@@ -170,6 +170,72 @@ def test_incline_free_rotation_rolls_until_threshold(dim, factor, roll_frac):
     assert slip > 1e-9
 
 
+PHI = 0.7   # an azimuth off both floor axes
+
+
+def _tangential(P):
+    """(P_t along the slope's downhill direction, across it, its z part)."""
+    c, s = math.cos(PHI), math.sin(PHI)
+    return P[1] * c + P[2] * s, -P[1] * s + P[2] * c, P[3]
+
+
+def test_oblique_incline_3d_stick_keeps_the_downhill_direction():
+    """A sphere (rotation frozen) on a slope whose downhill direction is at
+    azimuth phi: below tan(theta) = mu it sticks, with the whole tangential
+    impulse m g sin(theta) dt along the slope and none across it."""
+    mu = 0.4
+    th = math.atan(0.9 * mu)
+    wl = cases.incline(th, mu, dim=3, frozen=True, azimuth=PHI)
+    s, _ = _one_step(wl, alpha=1e-15, max_sweeps=100)
+    m = 1.0 / wl.inv_m[0]
+    P = s.impulses[0]
+    along, across, z = _tangential(P)
+    assert P[0] == pytest.approx(m * G * math.cos(th) * DT, rel=1e-13)
+    assert abs(along) == pytest.approx(m * G * math.sin(th) * DT, rel=1e-13)
+    assert abs(across) <= 1e-15 * abs(along) and z == 0.0
+    assert np.max(np.abs(s.v)) < 1e-15
+
+
+def test_oblique_incline_3d_slides_along_the_trial_velocity():
+    """Above tan(theta) = mu the sphere slides downhill: |P_t| = mu P_n,
+    P_t parallel to the trial tangential velocity (Eqs. 9-11 with an
+    isotropic tangential mass), and v = g (sin(theta) - mu cos(theta)) dt
+    along (cos phi, sin phi)."""
+    mu = 0.4
+    th = math.atan(1.1 * mu)
+    wl = cases.incline(th, mu, dim=3, frozen=True, azimuth=PHI)
+    s, _ = _one_step(wl, alpha=1e-15, max_sweeps=100)
+    P = s.impulses[0]
+    along, across, z = _tangential(P)
+    assert math.hypot(along, across) == pytest.approx(mu * P[0], rel=1e-14)
+    assert abs(across) <= 1e-14 * abs(along) and z == 0.0
+    speed = G * (math.sin(th) - mu * math.cos(th)) * DT
+    v = np.asarray(s.v).reshape(-1)[:3]   # particle 0: (v_x, v_y, v_z)
+    assert v[0] == pytest.approx(speed * math.cos(PHI), rel=1e-12)
+    assert v[1] == pytest.approx(speed * math.sin(PHI), rel=1e-12)
+    assert abs(v[2]) < 1e-15
+
+
+def test_oblique_incline_3d_rolls_about_the_cross_slope_axis():
+    """A free sphere below tan(theta) = 7 mu / 2 rolls without slipping:
+    v = (5/7) g sin(theta) dt downhill and the contact point (arm -r e_z) is
+    at rest, v_x - r w_y = 0 and v_y + r w_x = 0, so w is about the axis
+    across the slope."""
+    mu = 0.2
+    th = math.atan(0.9 * 3.5 * mu)
+    wl = cases.incline(th, mu, dim=3, frozen=False, azimuth=PHI)
+    s, _ = _one_step(wl, alpha=1e-15, max_sweeps=100)
+    r = wl.r[0]
+    v = np.asarray(s.v).reshape(-1)[:3]    # particle 0: (v_x, v_y, v_z)
+    wv = np.asarray(s.w).reshape(-1)[:3]   # (w_x, w_y, w_z)
+    speed = 5.0 / 7.0 * G * math.sin(th) * DT
+    assert v[0] == pytest.approx(speed * math.cos(PHI), rel=1e-12)
+    assert v[1] == pytest.approx(speed * math.sin(PHI), rel=1e-12)
+    assert abs(v[0] - r * wv[1]) < 1e-15
+    assert abs(v[1] + r * wv[0]) < 1e-15
+    assert abs(wv[2]) < 1e-15
+
+
 # --- perfectly inelastic collision (Sec. 2.1, Eq. 4) -------------------------
 
 @pytest.mark.parametrize("r1,r2,v1,v2", [(1.0, 1.0, 2.0, -2.0), (1.2, 0.8, 3.0, -0.5)])
