@@ -236,6 +236,117 @@ def test_oblique_incline_3d_rolls_about_the_cross_slope_axis():
     assert abs(wv[2]) < 1e-15
 
 
+# --- glancing collision of touching particles (Fig. 2, Eqs. 3-11) -----------
+
+def _glancing(dim, mu):
+    """Particles a and b touching along an oblique unit normal e, approaching
+    with a tangential relative velocity and spinning; no gravity, no walls.
+    The centre offset and its length are exact in binary (3-4-5 and 1-2-2-3
+    triangles), so the gap is exactly 0."""
+    if dim == 2:
+        ra, rb = 1.5, 1.0
+        off = np.array([1.5, 2.0])              # length 2.5 = ra + rb
+        xa = np.array([5.0, 5.0])
+        va, vb = [0.3, -0.1], [-0.2, 0.1]
+        w = [0.4, -0.3]
+        lo, hi = (0.0, 0.0, 0.0), (20.0, 20.0, 1.0)
+    else:
+        ra, rb = 1.75, 1.25
+        off = np.array([1.0, 2.0, 2.0])         # length 3 = ra + rb
+        xa = np.array([5.0, 5.0, 5.0])
+        va, vb = [0.3, -0.1, 0.2], [-0.2, 0.4, -0.3]
+        w = [[0.1, 0.0, -0.2], [0.0, 0.3, 0.1]]
+        lo, hi = (0.0, 0.0, 0.0), (20.0, 20.0, 20.0)
+    e = off / (ra + rb)
+    xb = xa + off
+    wl = cases._wl("glancing", dim, [xa, xb], [ra, rb], v=[va, vb], w=w, dt=DT, mu=mu,
+                   gravity=(0.0, 0.0, 0.0), box_lo=lo, box_hi=hi)
+    return wl, e
+
+
+def _point_velocity(dim, v, w, arm):
+    """Velocity of the material point at `arm` from the centre: v + w x arm."""
+    if dim == 2:
+        return v + w * np.array([-arm[1], arm[0]])
+    return v + np.cross(w, arm)
+
+
+def _contact_velocity(wl, e, v, w):
+    d = wl.dim
+    v = np.asarray(v).reshape(2, d)
+    w = np.asarray(w).reshape(2, -1) if d == 3 else np.asarray(w).reshape(2)
+    pa = _point_velocity(d, v[0], w[0], wl.r[0] * e)
+    pb = _point_velocity(d, v[1], w[1], -wl.r[1] * e)
+    return pb - pa
+
+
+def _momenta(wl, x, v, w):
+    """Linear momentum and angular momentum about the origin."""
+    d = wl.dim
+    m = 1.0 / wl.inv_m
+    I = 1.0 / wl.inv_I
+    x = np.asarray(x).reshape(2, d)
+    v = np.asarray(v).reshape(2, d)
+    p = (m[:, None] * v).sum(axis=0)
+    if d == 2:
+        w = np.asarray(w).reshape(2)
+        L = float((m * (x[:, 0] * v[:, 1] - x[:, 1] * v[:, 0])).sum() + (I * w).sum())
+        return p, np.array([L])
+    w = np.asarray(w).reshape(2, 3)
+    L = (m[:, None] * np.cross(x, v)).sum(axis=0) + (I[:, None] * w).sum(axis=0)
+    return p, L
+
+
+@pytest.mark.parametrize("dim", [2, 3])
+def test_glancing_collision_sticks_at_the_contact_point(dim):
+    """With ample friction the single contact sticks: afterwards the two
+    material points at the contact have the same velocity (normal: Eq. 4 with
+    gap 0; tangential: the stick solution of Eq. 5), while linear momentum
+    and angular momentum about the origin are those of before (an equal and
+    opposite impulse pair at one point)."""
+    wl, e = _glancing(dim, mu=10.0)
+    p0, L0 = _momenta(wl, wl.x, wl.v, wl.w)
+    u0 = _contact_velocity(wl, e, wl.v, wl.w)
+    assert float(u0 @ e) < 0.0                       # approaching
+    s, st = _one_step(wl, alpha=1e-15, max_sweeps=100)
+    assert s.impulses.shape[0] == 1 and st["converged"]
+    u = _contact_velocity(wl, e, s.v, s.w)
+    assert np.max(np.abs(u)) <= 1e-15 * 1e2 * np.max(np.abs(u0))
+    p1, L1 = _momenta(wl, wl.x, s.v, s.w)
+    assert np.max(np.abs(p1 - p0)) <= 1e-15 * np.max(np.abs(p0)) * 10
+    assert np.max(np.abs(L1 - L0)) <= 1e-14 * (np.max(np.abs(L0)) + 1.0)
+    P = s.impulses[0]
+    pt = abs(P[1]) if dim == 2 else float(np.linalg.norm(P[1:]))
+    assert 0.0 < pt < 10.0 * P[0]
+
+
+@pytest.mark.parametrize("dim", [2, 3])
+def test_glancing_collision_slides_against_the_tangential_velocity(dim):
+    """With little friction the contact slides: the normal relative velocity
+    of the contact points vanishes, |P_t| = mu P_n, and the tangential
+    relative velocity keeps its direction and shrinks (Eqs. 9-11 with an
+    isotropic tangential mass); the momenta are unchanged."""
+    mu = 0.05
+    wl, e = _glancing(dim, mu=mu)
+    p0, L0 = _momenta(wl, wl.x, wl.v, wl.w)
+    u0 = _contact_velocity(wl, e, wl.v, wl.w)
+    u0t = u0 - (u0 @ e) * e
+    s, st = _one_step(wl, alpha=1e-15, max_sweeps=100)
+    assert s.impulses.shape[0] == 1 and st["converged"]
+    u = _contact_velocity(wl, e, s.v, s.w)
+    ut = u - (u @ e) * e
+    assert abs(float(u @ e)) <= 1e-14 * np.max(np.abs(u0))
+    P = s.impulses[0]
+    pt = abs(P[1]) if dim == 2 else float(np.linalg.norm(P[1:]))
+    assert pt == pytest.approx(mu * P[0], rel=1e-13)
+    cosang = float(ut @ u0t) / (np.linalg.norm(ut) * np.linalg.norm(u0t))
+    assert cosang == pytest.approx(1.0, abs=1e-13)
+    assert 0.0 < np.linalg.norm(ut) < np.linalg.norm(u0t)
+    p1, L1 = _momenta(wl, wl.x, s.v, s.w)
+    assert np.max(np.abs(p1 - p0)) <= 1e-15 * np.max(np.abs(p0)) * 10
+    assert np.max(np.abs(L1 - L0)) <= 1e-14 * (np.max(np.abs(L0)) + 1.0)
+
+
 # --- perfectly inelastic collision (Sec. 2.1, Eq. 4) -------------------------
 
 @pytest.mark.parametrize("r1,r2,v1,v2", [(1.0, 1.0, 2.0, -2.0), (1.2, 0.8, 3.0, -0.5)])
