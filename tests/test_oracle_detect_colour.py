@@ -17,15 +17,17 @@ from paper_1104_3516_gb300 import workloads as W
 GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
 
 
-def load_hand_case():
+def load_hand_case(name="detect_hand_2d.txt"):
+    """Particles (x..., r), expected pairs and parameters of a golden file:
+    `disc x y r` (2D) or `sphere x y z r` (3D) lines, `expect a b`, `param`."""
     disc, expect, prm = [], [], {}
-    with open(os.path.join(GOLDEN, "detect_hand_2d.txt")) as f:
+    with open(os.path.join(GOLDEN, name)) as f:
         for line in f:
             line = line.split("#")[0].strip()
             if not line:
                 continue
             tok = line.split()
-            if tok[0] == "disc":
+            if tok[0] in ("disc", "sphere"):
                 disc.append([float(t) for t in tok[1:]])
             elif tok[0] == "expect":
                 expect.append((int(tok[1]), int(tok[2])))
@@ -35,21 +37,27 @@ def load_hand_case():
     return disc, expect, prm
 
 
-def hand_params():
-    disc, expect, prm = load_hand_case()
+def hand_params(name="detect_hand_2d.txt"):
+    disc, expect, prm = load_hand_case(name)
+    dim = int(prm.get("dim", [2])[0])
     box = prm["box"]
-    p = O.make_params(dim=2, delta=prm["delta"][0], box_lo=(box[0], box[2], 0), box_hi=(box[1], box[3], 1),
-                      periodic=(int(prm["periodic"][0]), int(prm["periodic"][1]), 0),
+    per = [int(v) for v in prm["periodic"]]
+    if dim == 2:
+        lo, hi, per3 = (box[0], box[2], 0), (box[1], box[3], 1), (per[0], per[1], 0)
+    else:
+        lo, hi, per3 = (box[0], box[2], box[4]), (box[1], box[3], box[5]), tuple(per)
+    p = O.make_params(dim=dim, delta=prm["delta"][0], box_lo=lo, box_hi=hi, periodic=per3,
                       wall_mask=int(prm["wall_mask"][0]))
-    return p, disc, expect
+    wp = np.array(prm.get("wall_pos", [0.0] * 6), dtype=np.float64)
+    return p, disc, expect, dim, wp
 
 
+@pytest.mark.parametrize("name", ["detect_hand_2d.txt", "detect_hand_3d.txt"])
 @pytest.mark.parametrize("method", ["brute", "cells"])
-def test_hand_derived_contact_set(method):
-    p, disc, expect = hand_params()
-    wp = np.zeros(6)
+def test_hand_derived_contact_set(method, name):
+    p, disc, expect, dim, wp = hand_params(name)
     f = O.detect_brute if method == "brute" else O.detect_cells
-    pairs = f(p, disc[:, :2], disc[:, 2], wp)
+    pairs = f(p, disc[:, :dim], disc[:, dim], wp)
     assert [tuple(map(int, q)) for q in pairs] == expect
 
 
