@@ -40,6 +40,51 @@ def test_resting_particle_normal_impulse_is_weight(dim):
     assert st["wall_force"][2 if dim == 2 else 4] == pytest.approx(m * G, rel=1e-14)
 
 
+def _moving_floor(dim, u):
+    """A particle resting on a kinematic floor that moves along its normal
+    (up, +y in 2D and +z in 3D) at speed u."""
+    wl = cases.resting_disc(dim=dim)
+    k = 2 if dim == 2 else 4
+    wv = np.zeros((6, 3))
+    wv[k, dim - 1] = u
+    wl.wall_vel = wv
+    return wl, k
+
+
+@pytest.mark.parametrize("dim", [2, 3])
+def test_rising_floor_carries_the_particle(dim):
+    """A kinematic wall (infinite mass, prescribed velocity) moving up at u
+    under a touching particle: the contact closes perfectly inelastically, so
+    the particle leaves with the wall's velocity, P_n = m (u + g dt), and
+    both advance by u dt (Eqs. 1-5, the walls moving kinematically)."""
+    u = 0.5
+    wl, k = _moving_floor(dim, u)
+    y0 = float(wl.x[0, dim - 1])
+    s, st = _one_step(wl, alpha=1e-15, max_sweeps=100)
+    m = 1.0 / wl.inv_m[0]
+    P = s.impulses
+    assert s.nc == 1
+    assert P[0, 0] == pytest.approx(m * (u + G * DT), rel=1e-14)
+    v = np.asarray(s.v).reshape(-1)
+    assert v[dim - 1] == pytest.approx(u, rel=1e-14)
+    assert np.all(np.abs(np.delete(v, dim - 1)) < 1e-18)
+    assert s.wall_pos[k] == pytest.approx(u * DT, rel=1e-14)
+    assert float(np.asarray(s.x).reshape(-1)[dim - 1]) == pytest.approx(y0 + u * DT, rel=1e-14)
+
+
+@pytest.mark.parametrize("dim", [2, 3])
+def test_receding_floor_opens_the_contact(dim):
+    """The floor moving down faster than the particle falls in one step
+    (u > g dt): the contact opens (P = 0, Eq. 3) and the particle falls
+    freely, v = -g dt."""
+    wl, k = _moving_floor(dim, -10.0 * G * DT)
+    s, st = _one_step(wl, alpha=1e-15, max_sweeps=100)
+    assert s.nc == 1
+    assert np.all(s.impulses == 0.0)
+    v = np.asarray(s.v).reshape(-1)
+    assert v[dim - 1] == pytest.approx(-G * DT, rel=1e-15)
+
+
 def test_open_contact_keeps_zero_force():
     """Eq. 3: a contact whose gap stays positive with R = 0 gets no force."""
     wl = cases.resting_disc()
