@@ -470,6 +470,28 @@ def test_free_fall_is_semi_implicit_euler():
 
 # --- convergence tests (Sec. 2.1) ----------------------------------------------
 
+def test_free_spin_and_periodic_wrap():
+    """Eq. 2 without contacts: a spinning disc's orientation advances by
+    omega dt per step with omega unchanged, and a disc crossing the periodic
+    x boundary re-enters at the other side (x + v dt - L)."""
+    L = 10.0
+    wl = cases._wl("spin", 2, [[9.875, 5.0]], [1.0], v=[[50.0, 0.0]], w=[2.0], dt=DT, mu=0.3,
+                   gravity=(0.0, 0.0, 0.0), box_lo=(0.0, 0.0, 0.0), box_hi=(L, 10.0, 1.0), periodic=(1, 0, 0))
+    s = system(wl, alpha=1e-15, max_sweeps=10)
+    x = [float(s.x[0])]
+    for k in range(1, 4):
+        s.step()
+        assert s.nc == 0
+        assert s.w[0] == 2.0
+        assert s.theta[0] == pytest.approx(k * 2.0 * DT, rel=1e-15)
+        x.append(float(s.x[0]))
+        assert 0.0 <= x[-1] < L
+    # 9.875 -> 9.925 -> 9.975 -> 10.025 - L = 0.025
+    assert x[1] == pytest.approx(9.925, rel=1e-15)
+    assert x[2] == pytest.approx(9.975, rel=1e-15)
+    assert x[3] == pytest.approx(0.025, rel=1e-12)
+
+
 def test_squared_global_test_matches_plain_test_at_sqrt_alpha():
     """Test (II) compares the squared ratio with alpha: equivalent to the
     plain ratio against sqrt(alpha)."""
