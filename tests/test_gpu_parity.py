@@ -13,6 +13,7 @@ import pytest
 
 import oracle as O
 import oracle_cases as cases
+from golden_cases import hand_workload
 from gpu_common import gpu_system, impulse_err, needs_gpu, run_pair
 from oracle_adapter import params as oparams
 from oracle_adapter import system as osystem
@@ -49,6 +50,18 @@ def test_detection_is_bit_exact_against_brute_force(name):
                                              np.asarray(wl.wall_pos, dtype=np.float64), ref)
     assert np.array_equal(got["normal"], normal)
     assert np.array_equal(got["gap"], gap)
+
+
+@pytest.mark.parametrize("name", ["detect_hand_2d.txt", "detect_hand_3d.txt"])
+def test_detection_equals_the_hand_derived_set(name):
+    """The hand-derived golden sets (exact distances: touching pairs, strict <
+    at gap delta, periodic minimum images, floor and ceiling gaps)."""
+    wl, expect = hand_workload(name)
+    g = gpu_system(wl)
+    nc = g.detect_contacts()
+    pairs = g.contacts()["pairs"]
+    assert nc == len(expect)
+    assert [tuple(map(int, q)) for q in pairs] == expect
 
 
 @pytest.mark.parametrize("name", list(CASES))

@@ -5,50 +5,20 @@ force over all pairs on seeded random inputs.  Colouring: validity (no two
 contacts of one colour share a particle), the greedy bound K <= Delta + 1 of
 the contact graph, and a star whose contacts all need distinct colours.
 """
-import os
 
 import numpy as np
 import pytest
 
 import oracle as O
 from oracle_adapter import params
+from golden_cases import hand_geometry, load_hand_case
 from paper_1104_3516_gb300 import workloads as W
-
-GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
-
-
-def load_hand_case(name="detect_hand_2d.txt"):
-    """Particles (x..., r), expected pairs and parameters of a golden file:
-    `disc x y r` (2D) or `sphere x y z r` (3D) lines, `expect a b`, `param`."""
-    disc, expect, prm = [], [], {}
-    with open(os.path.join(GOLDEN, name)) as f:
-        for line in f:
-            line = line.split("#")[0].strip()
-            if not line:
-                continue
-            tok = line.split()
-            if tok[0] in ("disc", "sphere"):
-                disc.append([float(t) for t in tok[1:]])
-            elif tok[0] == "expect":
-                expect.append((int(tok[1]), int(tok[2])))
-            elif tok[0] == "param":
-                prm[tok[1]] = [float(t) for t in tok[2:]]
-    disc = np.array(disc)
-    return disc, expect, prm
 
 
 def hand_params(name="detect_hand_2d.txt"):
     disc, expect, prm = load_hand_case(name)
-    dim = int(prm.get("dim", [2])[0])
-    box = prm["box"]
-    per = [int(v) for v in prm["periodic"]]
-    if dim == 2:
-        lo, hi, per3 = (box[0], box[2], 0), (box[1], box[3], 1), (per[0], per[1], 0)
-    else:
-        lo, hi, per3 = (box[0], box[2], box[4]), (box[1], box[3], box[5]), tuple(per)
-    p = O.make_params(dim=dim, delta=prm["delta"][0], box_lo=lo, box_hi=hi, periodic=per3,
-                      wall_mask=int(prm["wall_mask"][0]))
-    wp = np.array(prm.get("wall_pos", [0.0] * 6), dtype=np.float64)
+    dim, lo, hi, per3, mask, wp = hand_geometry(prm)
+    p = O.make_params(dim=dim, delta=prm["delta"][0], box_lo=lo, box_hi=hi, periodic=per3, wall_mask=mask)
     return p, disc, expect, dim, wp
 
 
