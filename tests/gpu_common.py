@@ -33,6 +33,52 @@ def impulse_err(P_gpu, P_ref):
     return float(np.abs(P_gpu - P_ref).max()) / p_scale(P_ref)
 
 
+def branch(P, mu, rel=1e-12):
+    """Branch of the single-contact solve (Fig. 2) each final impulse lies on:
+    0 open (P_n = 0), 1 stick (|P_t| below mu P_n), 2 slide (|P_t| = mu P_n
+    within `rel`)."""
+    P = np.asarray(P, dtype=np.float64)
+    pn = P[:, 0]
+    pt = np.abs(P[:, 1]) if P.shape[1] == 2 else np.linalg.norm(P[:, 1:], axis=1)
+    lim = mu * pn
+    out = np.ones(pn.shape[0], dtype=np.int64)
+    out[pt >= lim * (1.0 - rel)] = 2
+    out[pn <= 0.0] = 0
+    return out
+
+
+def near_switch(P, mu, rel=1e-10):
+    """Contacts whose impulse lies within `rel` (relative) of a switch of the
+    single-contact solve, counted from the oracle's impulses: closed contacts
+    with 0 < P_n <= rel max P_n (near the gap test's switch to open), and
+    sticking contacts with mu P_n - |P_t| <= rel mu P_n (near the Coulomb
+    switch to sliding).  Returns (near_open, near_slide)."""
+    P = np.asarray(P, dtype=np.float64)
+    if P.shape[0] == 0:
+        return 0, 0
+    pn = P[:, 0]
+    pt = np.abs(P[:, 1]) if P.shape[1] == 2 else np.linalg.norm(P[:, 1:], axis=1)
+    scale = max(float(pn.max()), 1e-300)
+    lim = mu * pn
+    near_open = int(np.count_nonzero((pn > 0.0) & (pn <= rel * scale)))
+    slack = lim - pt
+    # (a slack within 1e-12 of mu P_n is the slide branch itself, as in branch())
+    near_slide = int(np.count_nonzero((pn > 0.0) & (slack > 1e-12 * lim) & (slack <= rel * lim)))
+    return near_open, near_slide
+
+
+def switch_report(P_gpu, P_ref, mu, branch_rel=1e-12):
+    """What the sweep-by-sweep parity tests record beside the impulse bound
+    (no contact is excluded from it): the contacts near a switch, and those
+    whose final branch differs between the two sides (`branch_rel`: how close
+    to the cone counts as sliding; an FP32 slide lies on the FP32 cone, ~1e-8
+    from the FP64 one)."""
+    no, ns = near_switch(P_ref, mu)
+    differ = (int(np.count_nonzero(branch(P_gpu, mu, branch_rel) != branch(P_ref, mu, branch_rel)))
+              if len(P_ref) else 0)
+    return {"contacts": int(len(P_ref)), "near_open": no, "near_slide": ns, "branch_differs": differ}
+
+
 def oracle_crit(gpu_crit):
     from paper_1104_3516_gb300 import cd
     return {cd.CD_CONV_NONE: O.CRIT_NONE, cd.CD_CONV_GLOBAL_REL: O.CRIT_GLOBAL_REL,
