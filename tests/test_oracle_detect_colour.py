@@ -90,6 +90,32 @@ def test_geometry_normal_gap_and_mass_matrix():
     assert mn[0] == pytest.approx(ma, rel=1e-14)
 
 
+def test_geometry_3d_spheres_periodic_image_and_ceiling():
+    """3D: the normal follows the periodic minimum image (offset (2, 2, 1),
+    length 3, exact), the gap is |d| - r_a - r_b; for spheres r^2 / I =
+    5 / (2 m), so the tangential mass of Eq. 5 is m_t = 2 m_n / 7, for a pair
+    and against a wall (infinite mass); the ceiling's normal points from the
+    particle into the wall (+z) and its gap is z_wall - z - r."""
+    p = O.make_params(dim=3, delta=0.5, box_lo=(0, 0, 0), box_hi=(10, 10, 20), periodic=(1, 0, 0),
+                      wall_mask=0b110000)
+    r = np.array([1.25, 1.0])
+    inv_m, inv_I = W.masses(3, r)
+    wp = np.array([0.0, 0.0, 0.0, 0.0, 0.0, 20.0])
+    x = np.array([[9.5, 3.0, 5.0], [1.5, 5.0, 6.0]])          # min image dx = 1.5 - 9.5 + 10 = 2
+    normal, gap, mn, mt = O.contact_geometry(p, x, r, inv_m, inv_I, wp, np.array([[0, 1]], dtype=np.int32))
+    assert np.allclose(normal[0], [2.0 / 3.0, 2.0 / 3.0, 1.0 / 3.0], rtol=0, atol=1e-16)
+    assert gap[0] == 3.0 - 2.25
+    ma, mb = 1 / inv_m[0], 1 / inv_m[1]
+    assert mn[0] == pytest.approx(ma * mb / (ma + mb), rel=1e-14)
+    assert mt[0] == pytest.approx(2.0 * mn[0] / 7.0, rel=1e-14)
+    x2 = np.array([[5.0, 5.0, 18.5], [2.0, 2.0, 5.0]])
+    normal, gap, mn, mt = O.contact_geometry(p, x2, r, inv_m, inv_I, wp, np.array([[0, 2 + 5]], dtype=np.int32))
+    assert np.array_equal(normal[0], [0.0, 0.0, 1.0])
+    assert gap[0] == 20.0 - 18.5 - 1.25
+    assert mn[0] == pytest.approx(ma, rel=1e-14)
+    assert mt[0] == pytest.approx(2.0 * ma / 7.0, rel=1e-14)
+
+
 def _conflicts(n, pairs, colour):
     bad = 0
     for k in np.unique(colour):
