@@ -198,7 +198,7 @@ def test_gpu_head_on_collision():
 
 # --- converged macroscopic quantities vs the random-sequential oracle -------------
 
-def test_macroscopic_parity_with_random_sequential_order():
+def test_macroscopic_parity_with_random_sequential_order(record_property):
     """Forces of a hyperstatic packing are not unique (Sec. 4.4), so only
     macroscopic quantities are compared between the GPU colour order and the
     paper's random sequential order: the floor force of a deposited pile
@@ -224,9 +224,14 @@ def test_macroscopic_parity_with_random_sequential_order():
     inner = pairs[:, 1] < wl.n
     thr_g = 1e-9 * float(Pg[:, 0].mean())
     thr_o = 1e-9 * float(Po[:, 0].mean())
-    z_g = 2.0 * np.count_nonzero(Pg[inner, 0] > thr_g) / wl.n
-    z_o = 2.0 * np.count_nonzero(Po[inner, 0] > thr_o) / wl.n
-    assert abs(z_g - z_o) <= 0.02 * z_o
+    n_g = int(np.count_nonzero(Pg[inner, 0] > thr_g))
+    n_o = int(np.count_nonzero(Po[inner, 0] > thr_o))
+    # the force network is not unique: the count of force-carrying contacts may
+    # differ by a few between orders (the oracle's colour and random orders
+    # differ by 4 of ~1,930 here); the difference is recorded and bounded
+    record_property("force_carrying_contacts", {"gpu_colour_order": n_g, "oracle_random_order": n_o})
+    z_g, z_o = 2.0 * n_g / wl.n, 2.0 * n_o / wl.n
+    assert abs(z_g - z_o) <= 0.02 * z_o, (n_g, n_o)
 
 
 # --- edge cases ----------------------------------------------------------------------
