@@ -492,6 +492,26 @@ def test_free_spin_and_periodic_wrap():
     assert x[3] == pytest.approx(0.025, rel=1e-12)
 
 
+def test_colour_and_random_orders_agree_on_a_settled_pile():
+    """The colour order is a sequential order of the same scheme (Sec. 2.1):
+    on a 1000-disc pile resting on the floor both orders converge (1e-10) to
+    the same floor force, equal to the pile's weight, and the same height;
+    the forces themselves need not agree (hyperstatic network, Sec. 4.4)."""
+    from paper_1104_3516_gb300 import workloads as W
+    wl = W.dense_biaxial_discs(n=1000)
+    wl.wall_mask = 0b0100
+    out = {}
+    for order in (O.ORDER_COLOUR, O.ORDER_RANDOM):
+        s = system(wl, alpha=1e-10, max_sweeps=200000, order=order)
+        st = s.step()
+        assert st["converged"]
+        out[order] = (st["wall_force"][2], float(np.max(s.x.reshape(-1, 2)[:, 1] + wl.r)))
+    (fc, hc), (fr, hr) = out[O.ORDER_COLOUR], out[O.ORDER_RANDOM]
+    assert fc == pytest.approx(fr, rel=1e-6)
+    assert fc == pytest.approx(float(np.sum(1.0 / wl.inv_m)), rel=1e-4)
+    assert hc == pytest.approx(hr, rel=1e-6)
+
+
 def test_squared_global_test_matches_plain_test_at_sqrt_alpha():
     """Test (II) compares the squared ratio with alpha: equivalent to the
     plain ratio against sqrt(alpha)."""
