@@ -879,7 +879,9 @@ static int cmp_group_colour(const void* u, const void* v)
     return (a > b) - (a < b);
 }
 
-/* Solve the contact impulses of one time step.
+/* Solve the contact impulses of one time step: the iterative nonlinear
+ * Gauss-Seidel of Sec. 2.1 over the single-contact solve of Fig. 2, in the
+ * chosen order, until the convergence test (I) or (II) passes.
  *   v, w     in: free velocities (external forces applied, no contact
  *                impulses); out: velocities with the final impulses applied.
  *   P        in: starting impulses (warm start or zeros); out: solution.
@@ -1079,7 +1081,10 @@ static long long find_key(long long nc, const int32_t* pairs, uint64_t k)
     return -1;
 }
 
-/* State arrays are updated in place.
+/* One CD time step (Fig. 3): free flight (Eq. 1), detection (Sec. 3.2),
+ * warm start, ordering, the force calculation (ora_solve) and the Euler
+ * update of positions and orientations (Eq. 2).
+ * State arrays are updated in place.
  *   x, v: n*D; w: n (2D) or n*3 (3D); theta: n (2D orientation, may be NULL)
  *   f_ext: n*D explicit external forces (may be NULL)
  *   wall_pos: 6 plane positions, moved with the wall velocities
