@@ -132,6 +132,22 @@ def config(args, wl, extra=None):
     return c
 
 
+def host_cpu():
+    """The host CPU the oracle is timed on: its model (from /proc/cpuinfo where
+    it names one, else the architecture) and the number of logical CPUs."""
+    model = None
+    try:
+        with open("/proc/cpuinfo") as f:
+            for line in f:
+                key, _, val = line.partition(":")
+                if key.strip().lower() in ("model name", "hardware") and val.strip():
+                    model = val.strip()
+                    break
+    except OSError:
+        pass
+    return {"cpu": model or platform.processor() or platform.machine(), "nproc": os.cpu_count()}
+
+
 def profiled_traffic(kernel, precision, n):
     """DRAM bytes per launch from the committed ncu summary, or None if the
     sweep kernel's source changed since the counters were taken."""
@@ -288,7 +304,7 @@ def run_reference(args):
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": config(args, wl),
             "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample,
-                             "cpu": platform.processor() or platform.machine()},
+                             **host_cpu()},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 
@@ -409,7 +425,7 @@ def run_ours(args):
                "colour_order_value": c_upd / c_sec,
                "sample": f"1 oracle time step of the same {wl.n}-particle packing, random sequential order, sweep cap "
                          f"{args.cpu_sweeps} ({o_sweeps} sweeps over {o_nc} contacts, {o_sec:.1f} s)",
-               "cpu": platform.processor() or platform.machine()}
+               **host_cpu()}
 
     if rank != 0:
         return
