@@ -163,3 +163,13 @@ def chain_slabs(n=8, radius=1.0, force=1.0):
     wl.box_lo = (-radius, -5.0, 0.0)
     wl.box_hi = ((2.0 * n - 1.0) * radius, 5.0, 1.0)
     return wl, f
+
+
+def floor_row(radii, spacing=3.0, mu=0.3):
+    """Discs of the given radii resting on the floor (gaps 0), `spacing`
+    apart along x so that no two touch; gravity 1."""
+    r = np.asarray(radii, dtype=np.float64)
+    n = r.shape[0]
+    x = np.stack([spacing * np.arange(n), r], axis=1)
+    return _wl("floor_row", 2, x, r, dt=DT, mu=mu, gravity=(0.0, -G, 0.0), box_lo=(-5.0, 0.0, 0.0),
+               box_hi=(spacing * n + 5.0, 10.0, 1.0), wall_mask=0b0100)
