@@ -79,10 +79,6 @@ def parse():
     ap.add_argument("--alpha", type=float, default=1e-6)
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--tile-cells", type=int, default=0,
-                    help="0: global colour order; >= 2: tiled colour order with tiles of this many cells")
-    ap.add_argument("--dataflow", type=int, default=0,
-                    help="1: per-particle update counts instead of a grid barrier per colour")
     ap.add_argument("--domains", type=int, nargs=3, default=[1, 1, 1], metavar=("NX", "NY", "NZ"),
                     help="domain-wise update of Sec. 3.1: slabs per axis (1 1 1: Gauss-Seidel)")
     ap.add_argument("--merge-last-colour", type=int, default=1,
@@ -122,8 +118,7 @@ def config(args, wl, extra=None):
              "gravity": 1.0, "top_wall_speed": 1e-3, "periodic": "x"}
     c.update({"criterion": "global |dR_avg|/(R^j+R^j-1)", "alpha": args.alpha, "max_sweeps": args.max_sweeps,
               "warm_start": True,
-              "order": ("colour (largest degree first, then hash)" if args.tile_cells == 0 else
-                        f"tiled colour order, {args.tile_cells}-cell tiles"),
+              "order": "colour (largest degree first, then hash)",
               "domains": list(args.domains),
               "merge_last_colour": bool(args.merge_last_colour),
               "l2": "flushed (512 MiB write) before every timed step"})
@@ -323,7 +318,7 @@ def run_ours(args):
     prec = cd.CD_FP64 if args.precision == "f64" else cd.CD_FP32
     stream = torch.cuda.current_stream(device)
     shape, tuned = {}, None
-    plain = args.tile_cells == 0 and args.dataflow == 0 and list(args.domains) == [1, 1, 1]
+    plain = list(args.domains) == [1, 1, 1]
     if not args.no_autotune and plain:
         # block shape of the sweep grid chosen by timing short solves of this system (untimed)
         from paper_1104_3516_gb300 import autotune
@@ -332,7 +327,7 @@ def run_ours(args):
                                                  for t, b in autotune.BLOCK_SHAPES])
         tuned = {"choice": shape, "ms_per_sweep": [[c, m] for c, m in table]}
     sysg = cd.CDSystem(wl, device=device, precision=prec, criterion=cd.CD_CONV_GLOBAL_REL, max_contacts=4 * wl.n,
-                       timing=1, stream=stream, tile_cells=args.tile_cells, dataflow=args.dataflow,
+                       timing=1, stream=stream,
                        domains=tuple(args.domains), merge_last_colour=args.merge_last_colour, **shape)
     flush = torch.empty(512 << 20, dtype=torch.uint8, device=device)
 
@@ -380,8 +375,7 @@ def run_ours(args):
     steps_per_s = steps_sum / (dev_ms_max / 1e3)
 
     peak, peak_kind = peaks()
-    kname = ("k_sweep" if args.tile_cells == 0 and args.dataflow == 0 else
-             ("k_sweep_tiled" if args.tile_cells else "k_sweep_flow"))
+    kname = "k_sweep"
     if list(args.domains) != [1, 1, 1]:
         kname = "k_sweep_domains"
     kname += f"<{wl.dim},{'double' if args.precision == 'f64' else 'float'}>"

@@ -91,42 +91,20 @@ typedef struct {
     int64_t max_contacts;   /* contact capacity of the workspace */
     int64_t timing;         /* 1: record CUDA events around the phases of each
                                step on the system's stream (see cd_step_stats) */
-    int64_t tile_cells;     /* 0: global colour order (every colour class spread
-                               over the whole GPU, one grid barrier per colour).
-                               >= 2: tiled colour order: the cell grid is cut
-                               into tiles of tile_cells cells per axis
-                               (nt = cells / tile_cells per axis, even on a
-                               periodic axis); a contact belongs to the tile of
-                               its body a; tiles are coloured by coordinate
-                               parity (4 tile colours in 2D, 8 in 3D) and the
-                               contacts of a tile by greedy colouring inside
-                               the tile; the sweep order is (tile colour,
-                               tile, colour, key), one grid barrier per tile
-                               colour, a tile's particle state staged in
-                               shared memory */
-    int64_t dataflow;       /* with tile_cells = 0: 1 replaces the grid barrier
-                               after every colour by per-particle update
-                               counts: a contact waits until both particles
-                               have received every update that precedes it in
-                               the colour order (acquire/release through L2,
-                               bounded waits), so colours overlap; one grid
-                               barrier per sweep remains for the residual.
-                               Same update order, bit-identical results. */
     double parallel_p;      /* mixed update of Sec. 2.3: the contacts whose key
                                hashes below p (splitmix64(key ^ seed *
                                0xD1B54A32D192ED03) / 2^64 < p) are updated in
                                parallel within each sweep (from the velocities
                                at the sweep start, applied at its end), the
                                rest sequentially.  0: pure Gauss-Seidel.
-                               Plain systems with the colour-barrier schedule
-                               only. */
+                               Plain (not batched) systems only. */
     int64_t tape_steps;     /* 0: no adjoint.  T > 0: every cd_step records the
                                data cd_adjoint_step needs (colour-order contact
                                records with their converged impulses, and the
                                velocities the step produced) into a ring of T
                                slots in the workspace (about 64 B per contact of
                                capacity and 32 B per particle each); plain 2D
-                               FP64 systems with tile_cells 0 only. */
+                               FP64 systems only. */
     double adjoint_compliance; /* 0: the reverse pass solves the rigid
                                frozen-state system exactly (derivative of
                                the method as it stands).  eps > 0: each
@@ -146,8 +124,7 @@ typedef struct {
     int64_t sweep_threads;  /* block shape of the persistent sweep grid: threads
                                per block, 128, 256 or 512 (0: 512) ... */
     int64_t sweep_blocks_per_sm; /* ... and blocks per SM, 1, 2 or 4 (0: 1), at
-                               most 1024 threads per SM; the tiled and dataflow
-                               schedules need 512 x 1.  The colour classes are
+                               most 1024 threads per SM.  The colour classes are
                                spread over all blocks; results do not depend on
                                the shape except for the summation order of the
                                residual.  Chosen by the autotuner of the
@@ -250,7 +227,7 @@ cd_status cd_create_system(const cd_params* params, int64_t n, double* pos, doub
  * axes, walls (mask, positions, velocities) are taken from its own entry;
  * dim, precision, dt, delta, alpha, criterion, max_sweeps, warm_start,
  * rotations, seed, timing and max_contacts (total over the batch) from
- * entry 0; tile_cells must be 0.  State arrays as in cd_create_system over
+ * entry 0.  State arrays as in cd_create_system over
  * all n particles.  Each packing keeps its own cell grid and walls (wall k of
  * packing b is body n + 6 b + k), contacts never join two packings, and each
  * packing has its own convergence test (Sec. 2.1): the colour phases are

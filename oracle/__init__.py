@@ -59,7 +59,6 @@ class Params(C.Structure):
         ("seed", C.c_uint64),
         ("parallel_p", C.c_double),
         ("rotations", C.c_int64),
-        ("tile_cells", C.c_int64),
         ("wall_push", C.c_double * 6),
         ("wall_mass", C.c_double * 6),
         ("domains", C.c_int64 * 3),
@@ -124,12 +123,10 @@ def lib():
             _lib.ora_colour_repair.argtypes = [i64, i64, P(i32), C.c_int64, P(i32)]
             _lib.ora_solve.restype = C.c_int
             _lib.ora_solve.argtypes = [P(Params), i64, P(d), P(d), P(d), P(d), P(d), i64, P(i32), P(d), P(d),
-                                       P(d), P(d), P(i32), P(C.c_int64), P(i32), P(i32), i64, P(d), P(d),
+                                       P(d), P(d), P(i32), P(i32), P(i32), i64, P(d), P(d),
                                        P(SolveStats)]
             _lib.ora_contact_domains.restype = i64
             _lib.ora_contact_domains.argtypes = [P(Params), i64, P(d), P(d), i64, P(i32), P(d), P(d), P(i32)]
-            _lib.ora_tile_colour.restype = C.c_int
-            _lib.ora_tile_colour.argtypes = [P(Params), i64, P(d), P(d), i64, P(i32), P(i32), P(C.c_int64)]
             _lib.ora_step.restype = C.c_int
             _lib.ora_step.argtypes = [P(Params), i64, P(d), P(d), P(d), P(d), P(d), P(d), P(d), P(d), P(d),
                                       i64, P(i64), P(i32), P(d), i64, C.c_int, P(i32), P(d), P(d),
@@ -150,7 +147,7 @@ def _f64(a):
 def make_params(dim=2, dt=1e-3, mu=0.3, gravity=(0.0, -1.0, 0.0), box_lo=(0, 0, 0), box_hi=(1, 1, 1),
                 periodic=(0, 0, 0), wall_mask=0, wall_vel=None, delta=0.24, alpha=1e-6,
                 criterion=CRIT_GLOBAL_REL, max_sweeps=1000, order=ORDER_COLOUR, warm_start=1, seed=0,
-                parallel_p=0.0, rotations=1, tile_cells=0, wall_push=None, wall_mass=None, domains=(1, 1, 1)) -> Params:
+                parallel_p=0.0, rotations=1, wall_push=None, wall_mass=None, domains=(1, 1, 1)) -> Params:
     p = Params()
     p.dim = dim
     p.dt = dt
@@ -173,7 +170,6 @@ def make_params(dim=2, dt=1e-3, mu=0.3, gravity=(0.0, -1.0, 0.0), box_lo=(0, 0, 
     p.seed = int(seed) & (2**64 - 1)
     p.parallel_p = parallel_p
     p.rotations = int(rotations)
-    p.tile_cells = int(tile_cells)
     wp = np.zeros(6) if wall_push is None else np.asarray(wall_push, dtype=np.float64).reshape(6)
     wm = np.zeros(6) if wall_mass is None else np.asarray(wall_mass, dtype=np.float64).reshape(6)
     for k in range(6):
@@ -253,20 +249,8 @@ def colour_repair(n, pairs, colour, dyn_walls=0):
     return col[:nc], int(K)
 
 
-def tile_colour(p: Params, x, r, pairs):
-    """Tiled colouring: (colour within the tile, group = tile_colour * ntiles + tile)."""
-    x, r = _f64(x).reshape(-1), _f64(r)
-    pairs = np.ascontiguousarray(pairs, dtype=np.int32)
-    nc = pairs.shape[0]
-    colour = np.zeros(max(nc, 1), dtype=np.int32)
-    group = np.zeros(max(nc, 1), dtype=np.int64)
-    K = lib().ora_tile_colour(C.byref(p), r.shape[0], _ptr(x, C.c_double), _ptr(r, C.c_double), nc,
-                              _ptr(pairs, C.c_int32), _ptr(colour, C.c_int32), _ptr(group, C.c_int64))
-    return colour[:nc], group[:nc], int(K)
-
-
 def solve(p: Params, v_free, w_free, r, inv_m, inv_I, pairs, normal, gap, mn, mt, P0=None, colour=None,
-          fixed=None, step_index=0, history=False, group=None, domain=None):
+          fixed=None, step_index=0, history=False, domain=None):
     """Gauss-Seidel impulse solve (Sec. 2.1, Fig. 2).
 
     ``v_free``/``w_free`` are the velocities without contact impulses; returns
@@ -286,7 +270,6 @@ def solve(p: Params, v_free, w_free, r, inv_m, inv_I, pairs, normal, gap, mn, mt
         P = np.zeros((1, pw))
     col = None if colour is None else np.ascontiguousarray(colour, dtype=np.int32)
     fx = None if fixed is None else np.ascontiguousarray(fixed, dtype=np.int32)
-    grp = None if group is None else np.ascontiguousarray(group, dtype=np.int64)
     dom = None if domain is None else np.ascontiguousarray(domain, dtype=np.int32)
     hist = np.zeros(int(p.max_sweeps) + 1) if history else None
     st = SolveStats()
@@ -295,7 +278,7 @@ def solve(p: Params, v_free, w_free, r, inv_m, inv_I, pairs, normal, gap, mn, mt
                     _ptr(_f64(r), C.c_double), _ptr(_f64(inv_m), C.c_double), _ptr(_f64(inv_I), C.c_double),
                     nc, _ptr(pairs, C.c_int32), _ptr(normal, C.c_double), _ptr(_f64(gap), C.c_double),
                     _ptr(_f64(mn), C.c_double), _ptr(_f64(mt), C.c_double), _ptr(col, C.c_int32),
-                    _ptr(grp, C.c_int64), _ptr(fx, C.c_int32), _ptr(dom, C.c_int32), step_index, _ptr(P, C.c_double), _ptr(hist, C.c_double), C.byref(st))
+                    _ptr(fx, C.c_int32), _ptr(dom, C.c_int32), step_index, _ptr(P, C.c_double), _ptr(hist, C.c_double), C.byref(st))
     out = (P[:nc].copy(), v, w, st.as_dict())
     if history:
         return out + (hist[: st.sweeps + 1].copy(),)

@@ -80,7 +80,6 @@ typedef struct {
     uint64_t seed;          /* seeds the random order and the colouring */
     double parallel_p;      /* fraction of contacts updated in parallel */
     int64_t rotations;      /* 0: rotational degrees of freedom frozen */
-    int64_t tile_cells;     /* >= 2: tiled colour order (see ora_tile_colour) */
     double wall_push[6];    /* external force pushing wall k along its inward normal */
     double wall_mass[6];    /* > 0: wall k is a rigid body of this mass moving along
                                its normal (force-controlled); 0: kinematic */
@@ -360,7 +359,7 @@ static int cmp_prio(const void* u, const void* v)
 }
 
 static int colour_greedy_in(long long n, long long nc, const int32_t* pairs, uint64_t seed,
-                            const int64_t* tile, int64_t dyn_walls, int32_t* colour);
+                            int64_t dyn_walls, int32_t* colour);
 int ora_colour_repair(long long n, long long nc, const int32_t* pairs, int64_t dyn_walls, int32_t* colour);
 
 /* dyn_walls: bit k set when wall k is a force-controlled body, whose
@@ -370,7 +369,7 @@ int ora_colour_repair(long long n, long long nc, const int32_t* pairs, int64_t d
 int ora_colour_greedy(long long n, long long nc, const int32_t* pairs, uint64_t seed, int64_t dyn_walls,
                       int32_t* colour)
 {
-    colour_greedy_in(n, nc, pairs, seed, NULL, dyn_walls, colour);
+    colour_greedy_in(n, nc, pairs, seed, dyn_walls, colour);
     return ora_colour_repair(n, nc, pairs, dyn_walls, colour);
 }
 
@@ -474,10 +473,10 @@ int ora_colour_repair(long long n, long long nc, const int32_t* pairs, int64_t d
 #undef CONFLICTS
 }
 
-/* Greedy colouring as above; with `tile` non-NULL two contacts conflict only
- * when they share a particle and lie in the same tile. */
+/* Greedy colouring as above: two contacts conflict when they share a particle
+ * (or a force-controlled wall). */
 static int colour_greedy_in(long long n, long long nc, const int32_t* pairs, uint64_t seed,
-                            const int64_t* tile, int64_t dyn_walls, int32_t* colour)
+                            int64_t dyn_walls, int32_t* colour)
 {
     if (nc == 0) return 0;
     /* bodies that create conflicts: the particles and the force-controlled walls n + k */
@@ -528,7 +527,6 @@ static int colour_greedy_in(long long n, long long nc, const int32_t* pairs, uin
             for (long long e = deg[q]; e < deg[q + 1]; ++e) {
                 long long d = adj[e];
                 if (d == c || colour[d] < 0) continue;
-                if (tile && tile[d] != tile[c]) continue;
                 if (colour[d] >= cap) {
                     int ncap = cap * 2;
                     while (ncap <= colour[d]) ncap *= 2;
@@ -551,59 +549,6 @@ static int colour_greedy_in(long long n, long long nc, const int32_t* pairs, uin
     free(used); free(it); free(adj); free(fill); free(deg);
     return kmax;
 #undef CONFLICTS
-}
-
-/* ------------------------------------------------------------------------ */
-/* Tiled colour order.  The cell grid of the detection (side >= l) is cut   */
-/* into tiles of tile_cells cells per axis (nt_k = m_k / tile_cells tiles,  */
-/* made even on a periodic axis, at least 1); cell q lies in tile           */
-/* floor(q nt / m).  A contact belongs to the tile of its body a.  Tiles are */
-/* coloured by the parity of their coordinates (2^dim tile colours): two    */
-/* tiles of one colour are at least one whole tile (>= 2 cells) apart, so   */
-/* their contacts share no particle.  Inside a tile, contacts are coloured  */
-/* greedily as in ora_colour_greedy, with conflicts only inside the tile.   */
-/* The sweep order is (tile colour, tile, colour, key).                     */
-/* group[c] = tile_colour * ntiles + tile; returns the number of colours.   */
-/* ------------------------------------------------------------------------ */
-int ora_tile_colour(const ora_params* p, long long n, const double* x, const double* r, long long nc,
-                    const int32_t* pairs, int32_t* colour, int64_t* group)
-{
-    int D = (int)p->dim;
-    double rmax = 0.0;
-    for (long long i = 0; i < n; ++i) if (r[i] > rmax) rmax = r[i];
-    double ell = 2.0 * rmax + p->delta;
-    long long m[3] = {1, 1, 1}, nt[3] = {1, 1, 1};
-    double cs[3] = {1.0, 1.0, 1.0};
-    for (int k = 0; k < D; ++k) {
-        double L = p->box_hi[k] - p->box_lo[k];
-        long long mk = (long long)floor(L / ell);
-        if (mk < 1) mk = 1;
-        m[k] = mk;
-        cs[k] = L / (double)mk;
-        long long t = (p->tile_cells > 0) ? mk / p->tile_cells : 1;
-        if (t < 1) t = 1;
-        if (p->periodic[k] && t > 1 && (t & 1)) t -= 1;
-        nt[k] = t;
-    }
-    long long ntiles = nt[0] * nt[1] * nt[2];
-    int64_t* tile = (int64_t*)malloc(sizeof(int64_t) * (size_t)(nc > 0 ? nc : 1));
-    for (long long c = 0; c < nc; ++c) {
-        long long a = pairs[2 * c];
-        long long tq[3] = {0, 0, 0};
-        for (int k = 0; k < D; ++k) {
-            long long q = (long long)floor((x[a * D + k] - p->box_lo[k]) / cs[k]);
-            if (q < 0) q = 0;
-            if (q > m[k] - 1) q = m[k] - 1;
-            tq[k] = (q * nt[k]) / m[k];
-        }
-        long long t = (tq[2] * nt[1] + tq[1]) * nt[0] + tq[0];
-        long long tc = (tq[0] & 1) | ((tq[1] & 1) << 1) | ((tq[2] & 1) << 2);
-        tile[c] = t;
-        group[c] = tc * ntiles + t;
-    }
-    int K = colour_greedy_in(n, nc, pairs, p->seed, tile, dyn_wall_mask(p), colour);
-    free(tile);
-    return K;
 }
 
 /* ------------------------------------------------------------------------ */
@@ -867,14 +812,11 @@ static int is_parallel(const ora_params* p, uint64_t key)
     return u < p->parallel_p;
 }
 
-static const int64_t* g_sort_group;
 static const int32_t* g_sort_colour;
 
-static int cmp_group_colour(const void* u, const void* v)
+static int cmp_colour(const void* u, const void* v)
 {
     long long a = *(const long long*)u, b = *(const long long*)v;
-    int64_t ga = g_sort_group ? g_sort_group[a] : 0, gb = g_sort_group ? g_sort_group[b] : 0;
-    if (ga != gb) return (ga < gb) ? -1 : 1;
     if (g_sort_colour[a] != g_sort_colour[b]) return (g_sort_colour[a] < g_sort_colour[b]) ? -1 : 1;
     return (a > b) - (a < b);
 }
@@ -886,7 +828,6 @@ static int cmp_group_colour(const void* u, const void* v)
  *                impulses); out: velocities with the final impulses applied.
  *   P        in: starting impulses (warm start or zeros); out: solution.
  *   colour   colour per contact (ORA_ORDER_COLOUR), may be NULL otherwise.
- *   group    colour-order group per contact (tiled order), or NULL.
  *   fixed    the order for ORA_ORDER_FIXED, may be NULL otherwise.
  *   domain   domain of each contact (ora_contact_domains) for the
  *            domain-wise update of Sec. 3.1, or NULL (one domain).
@@ -896,7 +837,7 @@ static int cmp_group_colour(const void* u, const void* v)
 int ora_solve(ora_params* p, long long n, double* v, double* w,
               const double* r, const double* inv_m, const double* inv_I,
               long long nc, const int32_t* pairs, const double* normal, const double* gap,
-              const double* mn, const double* mt, const int32_t* colour, const int64_t* group,
+              const double* mn, const double* mt, const int32_t* colour,
               const int32_t* fixed, const int32_t* domain, long long step_index, double* P, double* ravg_hist,
               ora_solve_stats* st)
 {
@@ -920,14 +861,13 @@ int ora_solve(ora_params* p, long long n, double* v, double* w,
 
     long long* order = (long long*)malloc(sizeof(long long) * (size_t)(nc > 0 ? nc : 1));
     if (p->order == ORA_ORDER_COLOUR) {
-        /* (group, colour, key): a stable sort of the key-ordered contacts */
+        /* (colour, key): a stable sort of the key-ordered contacts */
         int K = 0;
         for (long long c = 0; c < nc; ++c) if (colour[c] + 1 > K) K = colour[c] + 1;
         st->n_colours = K;
         for (long long c = 0; c < nc; ++c) order[c] = c;
-        g_sort_group = group;
         g_sort_colour = colour;
-        qsort(order, (size_t)nc, sizeof(long long), cmp_group_colour);
+        qsort(order, (size_t)nc, sizeof(long long), cmp_colour);
     } else {
         for (long long c = 0; c < nc; ++c) order[c] = (p->order == ORA_ORDER_FIXED && fixed) ? fixed[c] : c;
     }
@@ -1152,11 +1092,7 @@ int ora_step(ora_params* p, long long n, double* x, double* v, double* w, double
     }
 
     ora_params q = *p;
-    int64_t* group = NULL;
-    if (p->order == ORA_ORDER_COLOUR && p->tile_cells >= 2) {
-        group = (int64_t*)malloc(sizeof(int64_t) * ncz);
-        ora_tile_colour(p, n, x, r, nc, pairs, colour, group);
-    } else if (p->order == ORA_ORDER_COLOUR) {
+    if (p->order == ORA_ORDER_COLOUR) {
         int K = ora_colour_greedy(n, nc, pairs, p->seed, dyn_wall_mask(p), colour);
         (void)K;
     } else {
@@ -1167,11 +1103,10 @@ int ora_step(ora_params* p, long long n, double* x, double* v, double* w, double
         domain = (int32_t*)malloc(sizeof(int32_t) * ncz);
         ora_contact_domains(p, n, x, r, nc, pairs, normal, gap, domain);
     }
-    ora_solve(&q, n, v, w, r, inv_m, inv_I, nc, pairs, normal, gap, mn, mt, colour, group, NULL, domain,
+    ora_solve(&q, n, v, w, r, inv_m, inv_I, nc, pairs, normal, gap, mn, mt, colour, NULL, domain,
               step_index, P, NULL, st);
     for (int k = 0; k < 18; ++k) p->wall_vel[k] = q.wall_vel[k];
     free(domain);
-    free(group);
 
     /* Eq. 2: positions with the new velocities; orientation likewise */
     for (long long i = 0; i < n; ++i) {

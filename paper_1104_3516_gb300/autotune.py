@@ -2,13 +2,8 @@
 
 Times short solves of the caller's own system under candidate launch
 configurations and returns the fastest: the block shape of the cooperative
-sweep grid (threads per block x blocks per SM) and, optionally, the
-schedules that change the Gauss-Seidel order (tiled colour order with a
-range of tile sizes).  The candidates that keep the order (block shapes, the
-dataflow schedule) give the same impulses as the default, so choosing among
-them changes only the speed; the tiled order is an admissible sequential
-order too but gives different (equally converged) impulses, so it is tried
-only with ``allow_reorder=True``.
+sweep grid (threads per block x blocks per SM).  Every candidate keeps the
+Gauss-Seidel order, so choosing among them changes only the speed.
 
 Everything runs through the CUDA library (``cd.CDSystem``); each trial is
 timed with the CUDA events the library records around the sweep kernel.
@@ -18,12 +13,11 @@ from __future__ import annotations
 from . import cd
 
 BLOCK_SHAPES = [(512, 1), (256, 2), (256, 1), (128, 4), (128, 2)]
-ORDER_KEEPING = [dict(sweep_threads=t, sweep_blocks_per_sm=b) for t, b in BLOCK_SHAPES] + [dict(dataflow=1)]
-REORDERING = [dict(tile_cells=t) for t in (8, 10, 12, 16)]
+ORDER_KEEPING = [dict(sweep_threads=t, sweep_blocks_per_sm=b) for t, b in BLOCK_SHAPES]
 
 
-def tune(wl, batch=None, precision=cd.CD_FP64, sweeps=40, steps=2, device="cuda", allow_reorder=False,
-         candidates=None, max_contacts=None):
+def tune(wl, batch=None, precision=cd.CD_FP64, sweeps=40, steps=2, device="cuda", candidates=None,
+         max_contacts=None):
     """Returns (best parameter dict, table of (parameters, ms per sweep)).
 
     Each candidate system is built over the workload (or the batch), stepped
@@ -32,8 +26,6 @@ def tune(wl, batch=None, precision=cd.CD_FP64, sweeps=40, steps=2, device="cuda"
     device or the system cannot run (a schedule a batch does not support, a
     shape that does not fit) are skipped."""
     cands = list(candidates) if candidates is not None else list(ORDER_KEEPING)
-    if candidates is None and allow_reorder and batch is None:
-        cands += REORDERING
     table = []
     for kw in cands:
         extra = dict(kw)

@@ -58,8 +58,6 @@ class cd_params(C.Structure):
         ("seed", C.c_uint64),
         ("max_contacts", C.c_int64),
         ("timing", C.c_int64),
-        ("tile_cells", C.c_int64),
-        ("dataflow", C.c_int64),
         ("parallel_p", C.c_double),
         ("tape_steps", C.c_int64),
         ("adjoint_compliance", C.c_double),
@@ -369,7 +367,7 @@ def cd_last_error(sysptr=None) -> str:
 # --- convenience object ----------------------------------------------------------
 
 def make_params(wl, precision=CD_FP64, criterion=CD_CONV_GLOBAL_REL, max_contacts=None, warm_start=1, rotations=1,
-                seed=None, max_sweeps=None, alpha=None, timing=0, tile_cells=0, dataflow=0,
+                seed=None, max_sweeps=None, alpha=None, timing=0,
                 parallel_p=0.0, tape_steps=0, adjoint_compliance=0.0, use_graph=0, sweep_threads=0,
                 sweep_blocks_per_sm=0, domains=(1, 1, 1), merge_last_colour=1) -> cd_params:
     p = cd_params()
@@ -398,8 +396,6 @@ def make_params(wl, precision=CD_FP64, criterion=CD_CONV_GLOBAL_REL, max_contact
     p.seed = int(wl.seed if seed is None else seed) & (2**64 - 1)
     p.max_contacts = int(max_contacts if max_contacts is not None else max(64, 6 * wl.n))
     p.timing = int(timing)
-    p.tile_cells = int(tile_cells)
-    p.dataflow = int(dataflow)
     p.parallel_p = float(parallel_p)
     p.tape_steps = int(tape_steps)
     p.adjoint_compliance = float(adjoint_compliance)

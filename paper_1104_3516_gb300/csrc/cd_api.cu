@@ -102,7 +102,6 @@ static size_t layout(cd_system* s, char* base, CdWork* w)
     size_t scan_max = ncell + 1;
     if (n + 7 > scan_max) scan_max = n + 7;
     if (CD_KMAX * nchunk > scan_max) scan_max = CD_KMAX * nchunk;
-    if ((size_t)s->g.ntiles * CD_KLOCAL + 1 > scan_max) scan_max = (size_t)s->g.ntiles * CD_KLOCAL + 1;
     if (cap + 1 > scan_max) scan_max = cap + 1;   // the colour repair's scan over the contacts
     CdWork t;
     t.ctrl = L.take<CdCtrl>(base, 1);
@@ -143,15 +142,6 @@ static size_t layout(cd_system* s, char* base, CdWork* w)
     t.c_P = L.take<char>(base, cap * (s->p.dim == 2 ? 2 : 4) * real);
     t.partials = L.take<double>(base, 2 * 3 * G);
     t.wpart = L.take<double>(base, 6 * G);
-    const size_t nseg = (size_t)s->g.ntiles * CD_KLOCAL;
-    t.c_tile = L.take<int>(base, cap);
-    t.tile_rank = L.take<int>(base, (size_t)s->g.ntiles);
-    t.tc_off = L.take<int>(base, 9);
-    t.seg_cnt = L.take<int>(base, nseg + 1);
-    t.seg_off = L.take<int>(base, nseg + 1);
-    t.seg_fill = L.take<int>(base, nseg);
-    t.c_need = L.take<int2>(base, cap);
-    t.deg = L.take<int>(base, n);
     const size_t npk = (size_t)s->g.npk;
     t.pk = L.take<CdPack>(base, npk);
     t.pack_of = L.take<int>(base, npk > 1 ? n : 1);
@@ -324,7 +314,6 @@ static cd_status launch_detect_chain(cd_system* s, int timed)
     k_error_gate<<<1, 1, 0, s->stream>>>(s->w.ctrl);
     ++s->launches;
     CD_CUDA(s, cudaGetLastError());
-    if (s->g.dataflow) CD_CUDA(s, cd_launch_need(s->g, s->w, s->stream, &s->launches));
     if (s->g.ndom_total > 1)
         CD_CUDA(s, cd_launch_domains(s->g, s->w, s->pos, s->radius, s->stream, &s->launches));
     if (s->g.merge_last) CD_CUDA(s, cd_launch_merge(s->g, s->w, s->colour_blocks, s->stream, &s->launches));
@@ -397,7 +386,6 @@ static cd_status create_impl(const cd_params* params, int64_t npk, const int64_t
         cd_status st = check_packing(params[b], (int)p.dim);
         if (st != CD_OK) return st;
     }
-    if (npk > 1 && p.tile_cells != 0) return fail(nullptr, CD_ERR_INVALID_ARG, "a batch uses the colour order (tile_cells 0)");
 
     cd_system* s = new cd_system();
     s->p = p;
@@ -508,38 +496,15 @@ static cd_status create_impl(const cd_params* params, int64_t npk, const int64_t
         for (int64_t b = 0; b < npk; ++b)
             for (int64_t i = offsets[b]; i < offsets[b + 1]; ++i) s->pack_of_host[(size_t)i] = (int)b;
     }
-    // tiled order: nt = cells / tile_cells per axis (>= 1, even on a periodic axis)
-    if (p.tile_cells < 0 || p.tile_cells == 1) {
-        delete s;
-        return fail(nullptr, CD_ERR_INVALID_ARG, "tile_cells must be 0 or >= 2");
-    }
-    g.tile_cells = (int)p.tile_cells;
-    g.ntiles = 1;
-    for (int k = 0; k < 3; ++k) {
-        int t = 1;
-        if (k < p.dim && g.tile_cells >= 2) {
-            t = g.ncell[k] / g.tile_cells;
-            if (t < 1) t = 1;
-            if (g.periodic[k] && t > 1 && (t & 1)) t -= 1;
-        }
-        g.ntile[k] = t;
-        g.ntiles *= t;
-    }
-    g.ntc = (g.tile_cells >= 2) ? (1 << p.dim) : 1;
-    g.dataflow = (p.dataflow && g.tile_cells == 0 && npk == 1) ? 1 : 0;
     if (!(p.parallel_p >= 0.0 && p.parallel_p <= 1.0)) {
         delete s;
         return fail(nullptr, CD_ERR_INVALID_ARG, "parallel_p must be in [0, 1]");
     }
-    if (p.parallel_p > 0.0 && (npk > 1 || g.tile_cells != 0 || g.dataflow)) {
+    if (p.parallel_p > 0.0 && npk > 1) {
         delete s;
         return fail(nullptr, CD_ERR_INVALID_ARG, "parallel_p needs a plain system with the colour-barrier schedule");
     }
     g.par_p = p.parallel_p;
-    if (g.tile_cells >= 2 && (double)g.ntiles * CD_KLOCAL > 1.0e8) {
-        delete s;
-        return fail(nullptr, CD_ERR_INVALID_ARG, "too many tiles: raise tile_cells");
-    }
     {
         // force-controlled walls
         int dyn = 0;
@@ -561,11 +526,10 @@ static cd_status create_impl(const cd_params* params, int64_t npk, const int64_t
         for (int64_t b = 1; b < npk; ++b)
             for (int k = 0; k < 6; ++k)
                 if (params[b].wall_mass[k] > 0.0) dyn |= 1 << 8;
-        if (dyn && (npk > 1 || g.tile_cells != 0 || g.dataflow || p.parallel_p > 0.0 || p.tape_steps > 0)) {
+        if (dyn && (npk > 1 || p.parallel_p > 0.0 || p.tape_steps > 0)) {
             delete s;
             return fail(nullptr, CD_ERR_INVALID_ARG,
-                        "force-controlled walls need a plain system with the global colour order, no mixed "
-                        "update and no tape");
+                        "force-controlled walls need a plain system with no mixed update and no tape");
         }
         g.dyn_walls = dyn;
     }
@@ -587,12 +551,11 @@ static cd_status create_impl(const cd_params* params, int64_t npk, const int64_t
             delete s;
             return fail(nullptr, CD_ERR_INVALID_ARG, "at most 2^24 domains");
         }
-        if (total > 1 && (npk > 1 || g.tile_cells != 0 || g.dataflow || p.parallel_p > 0.0 || g.dyn_walls ||
+        if (total > 1 && (npk > 1 || p.parallel_p > 0.0 || g.dyn_walls ||
                           p.tape_steps > 0)) {
             delete s;
             return fail(nullptr, CD_ERR_INVALID_ARG,
-                        "domains need a plain system with the colour-barrier schedule, kinematic walls, no mixed "
-                        "update and no tape");
+                        "domains need a plain system with kinematic walls, no mixed update and no tape");
         }
         g.ndom_total = (int)total;
     }
@@ -608,10 +571,10 @@ static cd_status create_impl(const cd_params* params, int64_t npk, const int64_t
         delete s;
         return fail(nullptr, CD_ERR_INVALID_ARG, "tape_steps must be in [0, 100000]");
     }
-    if (p.tape_steps > 0 && (p.dim != 2 || p.precision != CD_FP64 || npk > 1 || g.tile_cells != 0)) {
+    if (p.tape_steps > 0 && (p.dim != 2 || p.precision != CD_FP64 || npk > 1)) {
         delete s;
         return fail(nullptr, CD_ERR_INVALID_ARG,
-                    "tape_steps (the adjoint) needs a plain 2D FP64 system with the global colour order");
+                    "tape_steps (the adjoint) needs a plain 2D FP64 system");
     }
     s->adj_blocks = (p.tape_steps > 0 && cd_adjoint_blocks_per_sm() >= 1) ? s->num_sms : 0;
     if (p.tape_steps > 0 && s->adj_blocks == 0) {
@@ -634,10 +597,6 @@ static cd_status create_impl(const cd_params* params, int64_t npk, const int64_t
                         "sweep_threads must be 128, 256 or 512 and sweep_blocks_per_sm 1, 2 or 4 (at most 1024 "
                         "threads per SM)");
         }
-        if ((th != CD_SWEEP_THREADS || per != 1) && (g.tile_cells >= 2 || g.dataflow)) {
-            delete s;
-            return fail(nullptr, CD_ERR_INVALID_ARG, "the tiled and dataflow schedules use 512 x 1 blocks per SM");
-        }
         if (!cd_sweep_fits(g, (int)p.precision, th, per)) {
             delete s;
             return fail(nullptr, CD_ERR_INVALID_ARG, "that many sweep blocks do not fit on one SM");
@@ -651,7 +610,7 @@ static cd_status create_impl(const cd_params* params, int64_t npk, const int64_t
         delete s;
         return fail(nullptr, CD_ERR_INVALID_ARG, "merge_last_colour must be 0 or 1");
     }
-    g.merge_last = (p.merge_last_colour && npk == 1 && g.tile_cells == 0 && !g.dataflow && g.par_p == 0.0 &&
+    g.merge_last = (p.merge_last_colour && npk == 1 && g.par_p == 0.0 &&
                     g.ndom_total == 1 && !g.dyn_walls && p.tape_steps == 0 && cd_merge_label_blocks_per_sm() >= 1)
                        ? 1 : 0;
     g.merge_blocks = s->sweep_blocks;
@@ -712,28 +671,6 @@ extern "C" cd_status cd_set_workspace(cd_system* s, void* dev_ptr, size_t bytes)
         CD_CUDA(s, cudaMemcpyAsync(s->w.pk_wall_pos, s->pk_wall0.data(), sizeof(double) * s->pk_wall0.size(),
                                    cudaMemcpyHostToDevice, s->stream));
     }
-    {
-        // tiles in (tile colour, tile) order; colour = parity of the tile coordinates
-        const CdGeom& g = s->g;
-        std::vector<int> rank((size_t)g.ntiles), off(9, 0);
-        std::vector<int> cnt(9, 0);
-        auto colour_of = [&](int t) {
-            int t0 = t % g.ntile[0], t1 = (t / g.ntile[0]) % g.ntile[1], t2 = t / (g.ntile[0] * g.ntile[1]);
-            return (g.ntc > 1) ? ((t0 & 1) | ((t1 & 1) << 1) | ((t2 & 1) << 2)) : 0;
-        };
-        for (int t = 0; t < g.ntiles; ++t) cnt[colour_of(t) + 1]++;
-        for (int c = 0; c < 8; ++c) cnt[c + 1] += cnt[c];
-        for (int c = 0; c <= 8; ++c) off[c] = cnt[c];
-        std::vector<int> fill(9, 0);
-        for (int t = 0; t < g.ntiles; ++t) {
-            int c = colour_of(t);
-            rank[(size_t)t] = off[c] + fill[c]++;
-        }
-        CD_CUDA(s, cudaMemcpyAsync(s->w.tile_rank, rank.data(), sizeof(int) * rank.size(), cudaMemcpyHostToDevice,
-                                   s->stream));
-        CD_CUDA(s, cudaMemcpyAsync(s->w.tc_off, off.data(), sizeof(int) * 9, cudaMemcpyHostToDevice, s->stream));
-        CD_CUDA(s, cudaStreamSynchronize(s->stream));
-    }
     CD_CUDA(s, cd_launch_static(s->g, s->w, s->radius, s->inv_m, s->inv_I, (int)s->p.precision, s->stream,
                                 &s->launches));
     CD_CUDA(s, cudaStreamSynchronize(s->stream));
@@ -774,7 +711,6 @@ extern "C" cd_status cd_set_contacts(cd_system* s, int64_t nc, const int32_t* pa
     CD_CUDA(s, cd_launch_colour(s->g, s->w, s->colour_blocks, (int)s->p.precision, s->pw, s->stream, &s->launches,
                                 s->pos));
     k_error_gate<<<1, 1, 0, s->stream>>>(s->w.ctrl);
-    if (s->g.dataflow) CD_CUDA(s, cd_launch_need(s->g, s->w, s->stream, &s->launches));
     if (s->g.ndom_total > 1)
         CD_CUDA(s, cd_launch_domains(s->g, s->w, s->pos, s->radius, s->stream, &s->launches));
     if (s->g.merge_last) CD_CUDA(s, cd_launch_merge(s->g, s->w, s->colour_blocks, s->stream, &s->launches));

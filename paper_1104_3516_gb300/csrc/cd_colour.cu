@@ -72,7 +72,7 @@ __global__ void k_p2c_sort(CdGeom g, CdWork w)
 // contact is reserved there by the workspace layout).
 //
 // Worklist form: every contact first counts its neighbours of higher
-// priority (contacts sharing a body, in the same tile when tiled); those with
+// priority (contacts sharing a body); those with
 // none start the first list.  A round colours the contacts of its list (the
 // smallest colour no higher-priority neighbour has; all of those are
 // coloured by then) and decrements the counts of their lower-priority
@@ -107,7 +107,7 @@ __device__ __forceinline__ void jp_append(int* list, int* len, int c, bool take)
 }
 
 __global__ void __launch_bounds__(CD_SWEEP_THREADS) k_jp(CdGeom g, CdWork w, unsigned long long* prio,
-                                                          int* round_cnt, const int* tile, int kmax)
+                                                          int* round_cnt)
 {
     CdCtrl* ctrl = w.ctrl;
     if (ctrl->skip) return;
@@ -158,7 +158,7 @@ __global__ void __launch_bounds__(CD_SWEEP_THREADS) k_jp(CdGeom g, CdWork w, uns
                     for (int u = 0; u < 4; ++u) d[u] = (t + u < f1) ? w.p2c[t + u] : -1;
 #pragma unroll
                     for (int u = 0; u < 4; ++u)
-                        if (d[u] >= 0 && d[u] != c && !(tile && tile[d[u]] != tile[c]) &&
+                        if (d[u] >= 0 && d[u] != c &&
                             jp_higher(w, prio, d[u], c, pc, kc))
                             ++k;
                 }
@@ -202,7 +202,7 @@ __global__ void __launch_bounds__(CD_SWEEP_THREADS) k_jp(CdGeom g, CdWork w, uns
                     for (int u = 0; u < 4; ++u) d[u] = (f0 + t + u < f1) ? w.p2c[f0 + t + u] : -1;
 #pragma unroll
                     for (int u = 0; u < 4; ++u) {
-                        const bool nb_ok = d[u] >= 0 && d[u] != c && !(tile && tile[d[u]] != tile[c]);
+                        const bool nb_ok = d[u] >= 0 && d[u] != c;
                         const bool h = nb_ok && jp_higher(w, prio, d[u], c, pc, kc);
                         hi[u] = h;
                         lo[u] = nb_ok && !h;
@@ -220,7 +220,7 @@ __global__ void __launch_bounds__(CD_SWEEP_THREADS) k_jp(CdGeom g, CdWork w, uns
             int top = 0;
             if (c >= 0) {
                 const int col = (used == ~0ULL) ? 64 : __ffsll((long long)~used) - 1;
-                if (col >= kmax) {
+                if (col >= CD_KMAX) {
                     atomicCAS(&ctrl->error, CDE_NONE, CDE_COLOURS);
                 } else {
                     *(volatile int*)&w.colour[c] = col;
@@ -541,135 +541,6 @@ __global__ void k_colour_offsets(CdWork w, int nchunk)
     if (k == 0) w.colour_off[CD_KMAX] = ctrl->nc;
 }
 
-// Tile of each contact: the tile of the cell of its body a (same cell formula
-// as the detection).
-__device__ __forceinline__ int tile_axis(const CdGeom& g, int k, double x)
-{
-    double q = floor(__ddiv_rn(__dsub_rn(x, g.lo[k]), g.cs[k]));
-    int c = (q < 0.0) ? 0 : (q > (double)(g.ncell[k] - 1) ? g.ncell[k] - 1 : (int)q);
-    return (int)(((long long)c * g.ntile[k]) / g.ncell[k]);
-}
-
-template <int DIM>
-__global__ void k_contact_tile(CdGeom g, CdWork w, const double* __restrict__ pos)
-{
-    CdCtrl* ctrl = w.ctrl;
-    if (ctrl->skip) return;
-    int nc = ctrl->nc;
-    for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < nc; c += gridDim.x * blockDim.x) {
-        int a = w.pairs[c].x;
-        int t0 = tile_axis(g, 0, pos[a * DIM + 0]);
-        int t1 = tile_axis(g, 1, pos[a * DIM + 1]);
-        int t2 = (DIM == 3) ? tile_axis(g, 2, pos[a * DIM + 2]) : 0;
-        w.c_tile[c] = (t2 * g.ntile[1] + t1) * g.ntile[0] + t0;
-    }
-}
-
-// Segment = (tile rank, colour inside the tile).
-__global__ void k_seg_count(CdWork w)
-{
-    CdCtrl* ctrl = w.ctrl;
-    if (ctrl->skip) return;
-    int nc = ctrl->nc;
-    for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < nc; c += gridDim.x * blockDim.x) {
-        int k = w.colour[c];
-        if (k < 0 || k >= CD_KLOCAL) continue;
-        atomicAdd(&w.seg_cnt[w.tile_rank[w.c_tile[c]] * CD_KLOCAL + k], 1);
-    }
-}
-
-__global__ void k_seg_scatter(CdWork w)
-{
-    CdCtrl* ctrl = w.ctrl;
-    if (ctrl->skip) return;
-    int nc = ctrl->nc;
-    for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < nc; c += gridDim.x * blockDim.x) {
-        int k = w.colour[c];
-        if (k < 0 || k >= CD_KLOCAL) continue;
-        int s = w.tile_rank[w.c_tile[c]] * CD_KLOCAL + k;
-        int slot = atomicAdd(&w.seg_fill[s], 1);
-        w.perm[w.seg_off[s] + slot] = c;
-    }
-}
-
-// Contacts of one segment are independent; sorting them by key index only
-// makes the assignment to threads (and so the residual sums) deterministic.
-__global__ void k_seg_sort(CdWork w, int nseg)
-{
-    if (w.ctrl->skip) return;
-    for (int s = blockIdx.x * blockDim.x + threadIdx.x; s < nseg; s += gridDim.x * blockDim.x) {
-        int b = w.seg_off[s], e = w.seg_off[s + 1];
-        if (e - b > 1024) continue;   // oversized tile: order left as scattered (still a valid order)
-        for (int i = b + 1; i < e; ++i) {
-            int v = w.perm[i];
-            int j = i - 1;
-            while (j >= b && w.perm[j] > v) { w.perm[j + 1] = w.perm[j]; --j; }
-            w.perm[j + 1] = v;
-        }
-    }
-}
-
-// Colour-order contact data gathered through perm.
-template <int DIM, typename T>
-__global__ void k_gather(CdGeom g, CdWork w)
-{
-    CdCtrl* ctrl = w.ctrl;
-    if (ctrl->skip) return;
-    int nc = ctrl->nc;
-    typedef typename std::conditional<sizeof(T) == 8, double4, float4>::type T4;
-    typedef typename std::conditional<sizeof(T) == 8, double2, float2>::type T2;
-    for (int pos = blockIdx.x * blockDim.x + threadIdx.x; pos < nc; pos += gridDim.x * blockDim.x) {
-        int c = w.perm[pos];
-        w.c_ab[pos] = w.pairs[c];
-        double b = __ddiv_rn(w.gap[c], g.dt);
-        T4 geo;
-        if (DIM == 2) {
-            geo.x = (T)w.nrm[3 * c]; geo.y = (T)w.nrm[3 * c + 1]; geo.z = (T)b; geo.w = (T)w.mn[c];
-            ((T4*)w.c_geo)[pos] = geo;
-            ((T*)w.c_m)[pos] = (T)w.mt[c];
-            T2 P;
-            P.x = (T)w.Pk[2 * c]; P.y = (T)w.Pk[2 * c + 1];
-            ((T2*)w.c_P)[pos] = P;
-        } else {
-            geo.x = (T)w.nrm[3 * c]; geo.y = (T)w.nrm[3 * c + 1]; geo.z = (T)w.nrm[3 * c + 2]; geo.w = (T)b;
-            ((T4*)w.c_geo)[pos] = geo;
-            T2 m;
-            m.x = (T)w.mn[c]; m.y = (T)w.mt[c];
-            ((T2*)w.c_m)[pos] = m;
-            T4 P;
-            P.x = (T)w.Pk[4 * c]; P.y = (T)w.Pk[4 * c + 1]; P.z = (T)w.Pk[4 * c + 2]; P.w = (T)w.Pk[4 * c + 3];
-            ((T4*)w.c_P)[pos] = P;
-        }
-    }
-}
-
-// Dataflow schedule: for the contact at colour position pos, the number of
-// updates its bodies receive earlier in a sweep (their contacts of lower
-// colour; two contacts of one particle never share a colour), and the number
-// of contacts per particle.
-__global__ void k_need(CdGeom g, CdWork w)
-{
-    CdCtrl* ctrl = w.ctrl;
-    if (ctrl->skip) return;
-    int nc = ctrl->nc;
-    for (int pos = blockIdx.x * blockDim.x + threadIdx.x; pos < nc; pos += gridDim.x * blockDim.x) {
-        int c = w.perm[pos];
-        int2 ab = w.pairs[c];
-        int kc = w.colour[c];
-        int need[2] = {0, 0};
-        for (int side = 0; side < 2; ++side) {
-            int q = side ? ab.y : ab.x;
-            if (q >= g.n) continue;
-            int e = w.p2c_off[q + 1], cnt = 0;
-            for (int s = w.p2c_off[q]; s < e; ++s) cnt += (w.colour[w.p2c[s]] < kc) ? 1 : 0;
-            need[side] = cnt;
-        }
-        w.c_need[pos] = make_int2(need[0], need[1]);
-    }
-    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < g.n; i += gridDim.x * blockDim.x)
-        w.deg[i] = w.p2c_off[i + 1] - w.p2c_off[i];
-}
-
 // Key-order contact range of each packing: contacts are sorted by body a and
 // the packings' particles are consecutive, so packing b's contacts start at
 // the first key whose a >= the packing's first particle.
@@ -698,17 +569,6 @@ cudaError_t cd_launch_pk_ranges(const CdGeom& g, const CdWork& w, cudaStream_t s
     return cudaGetLastError();
 }
 
-cudaError_t cd_launch_need(const CdGeom& g, const CdWork& w, cudaStream_t s, int* nl)
-{
-    int m = (g.cap > g.n) ? g.cap : g.n;
-    int gc = (m + CD_BLOCK - 1) / CD_BLOCK;
-    if (gc < 1) gc = 1;
-    if (gc > 4096) gc = 4096;
-    k_need<<<gc, CD_BLOCK, 0, s>>>(g, w);
-    ++*nl;
-    return cudaGetLastError();
-}
-
 int cd_colour_max_blocks(int num_sms)
 {
     int per_sm = 0;
@@ -726,7 +586,6 @@ cudaError_t cd_launch_colour(const CdGeom& g, const CdWork& w, int coop_blocks, 
     int gc = (g.cap + CD_BLOCK - 1) / CD_BLOCK;
     if (gc < 1) gc = 1;
     if (gc > 4096) gc = 4096;
-    const bool tiled = g.tile_cells >= 2;
     const int nbody = g.n + (g.dyn_walls ? 6 : 0);   // particles, then force-controlled walls n + k
     if ((e = cudaMemsetAsync(w.p2c_cnt, 0, sizeof(int) * (size_t)(nbody + 1), s)) != cudaSuccess) return e;
     if ((e = cudaMemsetAsync(w.p2c_fill, 0, sizeof(int) * (size_t)nbody, s)) != cudaSuccess) return e;
@@ -738,26 +597,18 @@ cudaError_t cd_launch_colour(const CdGeom& g, const CdWork& w, int coop_blocks, 
         if (gn > 4096) gn = 4096;
         k_p2c_sort<<<gn, CD_BLOCK, 0, s>>>(g, w); ++*nl;
     }
-    if (tiled) {
-        if (g.dim == 2) k_contact_tile<2><<<gc, CD_BLOCK, 0, s>>>(g, w, pos);
-        else k_contact_tile<3><<<gc, CD_BLOCK, 0, s>>>(g, w, pos);
-        ++*nl;
-    }
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     if (coop_blocks > 0) {
         CdGeom ga = g;
         CdWork wa = w;
         unsigned long long* prio = w.prio;
         int* rc = w.round_cnt;
-        const int* tl = tiled ? w.c_tile : nullptr;
-        int kmax = tiled ? CD_KLOCAL : CD_KMAX;
-        void* args[] = {&ga, &wa, &prio, &rc, &tl, &kmax};
+        void* args[] = {&ga, &wa, &prio, &rc};
         if ((e = cudaMemsetAsync(w.ctrl, 0, 2 * sizeof(unsigned long long), s)) != cudaSuccess) return e;
         e = cudaLaunchCooperativeKernel((const void*)k_jp, dim3(coop_blocks), dim3(CD_SWEEP_THREADS), args, 0, s);
         if (e != cudaSuccess) return e;
         ++*nl;
     }
-    if (tiled) return cd_launch_order_tiled(g, w, pos, precision, pw, s, nl);
     if ((e = launch_repair(g, w, gc, s, nl)) != cudaSuccess) return e;
     k_chunk_hist<<<nchunk, CD_CHUNK, 0, s>>>(w, nchunk); ++*nl;
     if ((e = cd_scan_exclusive(w.chunk_cnt, w.chunk_cnt, CD_KMAX * nchunk, w.scan_tmp, nullptr, s, nl)) != cudaSuccess)
@@ -772,33 +623,5 @@ cudaError_t cd_launch_colour(const CdGeom& g, const CdWork& w, int coop_blocks, 
         ++*nl;
     }
     k_colour_offsets<<<1, CD_KMAX, 0, s>>>(w, nchunk); ++*nl;
-    return cudaGetLastError();
-}
-
-cudaError_t cd_launch_order_tiled(const CdGeom& g, const CdWork& w, const double* pos, int precision, int pw,
-                                  cudaStream_t s, int* nl)
-{
-    (void)pos; (void)pw;
-    cudaError_t e;
-    const int nseg = g.ntiles * CD_KLOCAL;
-    int gc = (g.cap + CD_BLOCK - 1) / CD_BLOCK;
-    if (gc < 1) gc = 1;
-    if (gc > 4096) gc = 4096;
-    int gs = (nseg + CD_BLOCK - 1) / CD_BLOCK;
-    if (gs > 4096) gs = 4096;
-    if ((e = cudaMemsetAsync(w.seg_cnt, 0, sizeof(int) * (size_t)(nseg + 1), s)) != cudaSuccess) return e;
-    if ((e = cudaMemsetAsync(w.seg_fill, 0, sizeof(int) * (size_t)nseg, s)) != cudaSuccess) return e;
-    k_seg_count<<<gc, CD_BLOCK, 0, s>>>(w); ++*nl;
-    if ((e = cd_scan_exclusive(w.seg_cnt, w.seg_off, nseg + 1, w.scan_tmp, nullptr, s, nl)) != cudaSuccess) return e;
-    k_seg_scatter<<<gc, CD_BLOCK, 0, s>>>(w); ++*nl;
-    k_seg_sort<<<gs, CD_BLOCK, 0, s>>>(w, nseg); ++*nl;
-    if (g.dim == 2) {
-        if (precision == CD_FP64) k_gather<2, double><<<gc, CD_BLOCK, 0, s>>>(g, w);
-        else k_gather<2, float><<<gc, CD_BLOCK, 0, s>>>(g, w);
-    } else {
-        if (precision == CD_FP64) k_gather<3, double><<<gc, CD_BLOCK, 0, s>>>(g, w);
-        else k_gather<3, float><<<gc, CD_BLOCK, 0, s>>>(g, w);
-    }
-    ++*nl;
     return cudaGetLastError();
 }

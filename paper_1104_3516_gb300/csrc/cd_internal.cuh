@@ -14,8 +14,6 @@
 #define CD_BLOCK 256          // threads per block of the streaming kernels
 #define CD_CHUNK 256          // contacts per chunk of the stable colour partition
 #define CD_WAIT_NS 2000000000ULL  // bound on any device-side wait (2 s)
-#define CD_KLOCAL 32          // colours inside one tile (tiled order)
-#define CD_HT 1024            // slots of a tile's shared-memory particle table
 
 // Device error codes written into CdCtrl::error.
 enum { CDE_NONE = 0, CDE_TIMEOUT = 1, CDE_COLOURS = 2, CDE_PER_PARTICLE = 3, CDE_TAPE = 4 };
@@ -124,16 +122,6 @@ struct CdWork {
     void* c_P;          // 2D: (Pn, Pt)          3D: (Pn, Ptx, Pty, Ptz)
     double* partials;   // 2 * G * 4 reduction partials
     double* wpart;      // G * 6 wall-force partials
-    // tiled order
-    int* c_tile;        // cap: tile of each contact (key order)
-    int* tile_rank;     // ntiles: position of a tile in (tile colour, tile) order
-    int* tc_off;        // 9: first rank of each tile colour
-    int* seg_cnt;       // ntiles * CD_KLOCAL + 1 (counts, then exclusive offsets)
-    int* seg_off;       // ntiles * CD_KLOCAL + 1
-    int* seg_fill;      // ntiles * CD_KLOCAL
-    // dataflow schedule
-    int2* c_need;       // cap (colour order): updates of body a / b that precede the contact in a sweep
-    int* deg;           // n: contacts per particle
     // batched systems (npk packings)
     CdPack* pk;         // npk packing parameters
     int* pack_of;       // n: packing of each particle
@@ -265,11 +253,6 @@ struct CdGeom {
     int rotations;
     int pad;
     unsigned long long seed;
-    int tile_cells;     // 0: global colour order
-    int ntile[3];
-    int ntiles;
-    int ntc;            // tile colours (2^dim) or 1
-    int dataflow;       // 1: per-particle update counts instead of per-colour barriers
     int npk;            // packings (1 for a plain system)
     int ncell_total;    // cells of all packings' grids
     double par_p;       // parallel fraction of the mixed update (0: Gauss-Seidel)
@@ -444,9 +427,6 @@ cudaError_t cd_launch_colour(const CdGeom& g, const CdWork& w, int coop_blocks, 
 cudaError_t cd_launch_pack(const CdGeom& g, const CdWork& w, const double* vel, const double* omega,
                            const double* radius, const double* inv_m, const double* inv_I, const double* f_ext,
                            int free_flight, int precision, cudaStream_t stream, int* nl);
-cudaError_t cd_launch_order_tiled(const CdGeom& g, const CdWork& w, const double* pos, int precision, int pw,
-                                  cudaStream_t stream, int* nl);
-cudaError_t cd_launch_need(const CdGeom& g, const CdWork& w, cudaStream_t stream, int* nl);
 cudaError_t cd_launch_domains(const CdGeom& g, const CdWork& w, const double* pos, const double* radius,
                               cudaStream_t stream, int* nl);
 cudaError_t cd_launch_merge(const CdGeom& g, const CdWork& w, int coop_blocks, cudaStream_t stream, int* nl);

@@ -472,8 +472,6 @@ __device__ __forceinline__ double sq2(double a, double b) { return __fma_rn(b, b
 __device__ __forceinline__ double abs_of_pair(double pn, double pt) { return norm_of_sq(sq2(pn, pt)); }
 
 // 2D: P_n = max(0, P_n,old - m_n (b + u_n)); P_t = clamp(P_t,old - m_t u_t, +-mu P_n).
-// The core works on the two bodies' velocity records wherever they live
-// (global memory or a tile's shared-memory table).
 template <typename T, bool SQ = false>
 __device__ __forceinline__ UpdOut core2d(const CdGeom& g, const Rec<2, T>& r, typename Vec<T>::V4& va,
                                          typename Vec<T>::V4& vb, bool wall, bool apply_only, int crit,
@@ -1476,398 +1474,6 @@ k_sweep_batch(CdGeom g, CdWork w, int crit, double alpha, int max_sweeps)
 }
 
 // ---------------------------------------------------------------------------
-// Dataflow schedule.  Every particle's first velocity record carries, in its
-// pad word, the number of contact updates applied to it so far in this solve.
-// In phase s (0 = starting impulses, then one per sweep) the contact at
-// colour position p may update body q once q has received need_q(p) +
-// s * deg(q) updates: exactly those that precede p in the colour order (the
-// particle's contacts of lower colour in this phase and all of its updates in
-// earlier phases).  The thread waits with acquire loads (bounded by
-// %globaltimer), updates, stores the velocities and publishes the count + 1
-// with a release store.  No two threads ever hold the same particle at once,
-// the update order equals the barrier schedule's, and the results are
-// bit-identical to it; colours overlap instead of waiting for the whole grid.
-// Progress: the earliest unfinished contact of the phase always has its
-// counts ready, and each thread walks its contacts in colour order.
-// ---------------------------------------------------------------------------
-__device__ __forceinline__ int ld_acquire_s32(const int* p)
-{
-    int v;
-    asm volatile("ld.acquire.gpu.global.s32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
-    return v;
-}
-
-__device__ __forceinline__ void st_release_s32(int* p, int v)
-{
-    asm volatile("st.release.gpu.global.s32 [%0], %1;" :: "l"(p), "r"(v) : "memory");
-}
-
-template <int DIM, typename T>
-__device__ __forceinline__ int* count_ptr(void* V, int i)
-{
-    typedef typename Vec<T>::V4 T4;
-    return reinterpret_cast<int*>(reinterpret_cast<char*>((T4*)V + (DIM == 2 ? i : 2 * i)) + 3 * sizeof(T));
-}
-
-// Waits until *cp >= need; false if the wait ran out or another block failed.
-__device__ __forceinline__ bool wait_count(const int* cp, int need, CdCtrl* ctrl)
-{
-    if (ld_acquire_s32(cp) >= need) return true;
-    unsigned long long t0 = cd_globaltimer();
-    unsigned spins = 0;
-    while (ld_acquire_s32(cp) < need) {
-        if ((++spins & 63u) == 0u) {
-            if (cd_ld_volatile_int(&ctrl->error) != CDE_NONE) return false;
-            if (cd_globaltimer() - t0 > CD_WAIT_NS) {
-                atomicCAS(&ctrl->error, CDE_NONE, CDE_TIMEOUT);
-                return false;
-            }
-        }
-        __nanosleep(32);
-    }
-    return true;
-}
-
-// Stores the first three components of a velocity record, leaving the count.
-template <typename T>
-__device__ __forceinline__ void store_xyz(typename Vec<T>::V4* dst, const typename Vec<T>::V4& v)
-{
-    typedef typename Vec<T>::V2 T2;
-    T2 xy;
-    xy.x = v.x; xy.y = v.y;
-    *reinterpret_cast<T2*>(dst) = xy;
-    reinterpret_cast<T*>(dst)[2] = v.z;
-}
-
-template <int DIM, typename T>
-__device__ __forceinline__ bool flow_update(const CdGeom& g, const CdWork& w, int p, int phase, bool apply_only,
-                                            int crit, double alpha, double ravg_prev, const Rec<DIM, T>& r,
-                                            double (&acc)[3])
-{
-    typedef typename Vec<T>::V4 T4;
-    typedef typename Vec<T>::V2 T2;
-    CdCtrl* ctrl = w.ctrl;
-    T4* V = (T4*)w.V;
-    const bool wall = r.ab.y >= g.n;
-    const int2 nd = w.c_need[p];
-    const int ea = nd.x + phase * w.deg[r.ab.x];
-    const int eb = wall ? 0 : nd.y + phase * w.deg[r.ab.y];
-    int* ca = count_ptr<DIM, T>(w.V, r.ab.x);
-    int* cb = wall ? nullptr : count_ptr<DIM, T>(w.V, r.ab.y);
-    if (!wait_count(ca, ea, ctrl)) return false;
-    if (!wall && !wait_count(cb, eb, ctrl)) return false;
-    UpdOut o;
-    if constexpr (DIM == 2) {
-        T4 va = V[r.ab.x], vb;
-        if (!wall) vb = V[r.ab.y];
-        else wall_vel2<T>(g, w, r.ab.y, vb);
-        T2 Pnew;
-        o = core2d<T>(g, r, va, vb, wall, apply_only, crit, alpha, ravg_prev, Pnew);
-        store_xyz<T>(V + r.ab.x, va);
-        if (!wall) store_xyz<T>(V + r.ab.y, vb);
-        if (!apply_only) ((T2*)w.c_P)[p] = Pnew;
-    } else {
-        T4 va = V[2 * r.ab.x], wa = V[2 * r.ab.x + 1], vb, wb;
-        if (!wall) { vb = V[2 * r.ab.y]; wb = V[2 * r.ab.y + 1]; }
-        else wall_vel3<T>(g, w, r.ab.y, vb, wb);
-        T4 Pnew;
-        o = core3d<T>(g, r, va, wa, vb, wb, wall, apply_only, crit, alpha, ravg_prev, Pnew);
-        store_xyz<T>(V + 2 * r.ab.x, va);
-        V[2 * r.ab.x + 1] = wa;
-        if (!wall) { store_xyz<T>(V + 2 * r.ab.y, vb); V[2 * r.ab.y + 1] = wb; }
-        if (!apply_only) ((T4*)w.c_P)[p] = Pnew;
-    }
-    st_release_s32(ca, ea + 1);
-    if (!wall) st_release_s32(cb, eb + 1);
-    acc[0] += o.pabs;
-            if (crit == CD_CONV_LOCAL) { acc[1] += (double)o.rel_ok; acc[2] += (double)o.bad; }
-    return true;
-}
-
-template <int DIM, typename T>
-__global__ void __launch_bounds__(CD_SWEEP_THREADS, 1)
-k_sweep_flow(CdGeom g, CdWork w, int crit, double alpha, int max_sweeps)
-{
-    __shared__ double s_red[CD_SWEEP_THREADS / 32][3];
-    __shared__ double s_bc;
-    __shared__ int s_fail;
-    CdCtrl* ctrl = w.ctrl;
-    if (ctrl->skip) return;
-    const int nc = ctrl->nc;
-    const int nb = gridDim.x;
-    const int tid = blockIdx.x * blockDim.x + threadIdx.x;
-    const int stride = gridDim.x * blockDim.x;
-    unsigned long long epoch = 0;
-    if (threadIdx.x == 0) s_fail = 0;
-    __syncthreads();
-
-    int sweeps = 0, converged = (nc == 0);
-    double resid = 0.0, ravg = 0.0, ravg_prev = 0.0;
-    if (nc > 0) {
-        for (int phase = 0; phase <= max_sweeps && !converged; ++phase) {
-            const bool apply_only = (phase == 0);
-            double a3[3] = {0.0, 0.0, 0.0};
-            bool ok = true;
-            for (int p = tid; p < nc && ok; p += stride) {
-                Rec<DIM, T> r;
-                load_rec<DIM, T>(g, w, p, r);
-                ok = flow_update<DIM, T>(g, w, p, phase, apply_only, crit, alpha, ravg_prev, r, a3);
-            }
-            if (!ok) s_fail = 1;
-            const int buf = (phase & 1);
-            double* part = w.partials + (size_t)buf * 3 * nb;
-            block_sum<3>(a3, s_red, apply_only ? 1 : test_values(crit));
-            if (threadIdx.x == 0) {
-                part[blockIdx.x] = a3[0];
-                part[nb + blockIdx.x] = a3[1];
-                part[2 * nb + blockIdx.x] = a3[2];
-            }
-            if (s_fail) return;
-            if (!cd_grid_sync(ctrl, nb, epoch)) return;
-            if (apply_only) {
-                ravg = grid_total(part, nb, &s_bc) / (double)nc;
-                ravg_prev = ravg;
-                continue;
-            }
-            ++sweeps;
-            sweep_test(part, nb, nc, crit, alpha, ravg_prev, ravg, resid, converged, s_red[0]);
-            ravg_prev = ravg;
-        }
-    }
-    finish_solve<DIM, T>(g, w, nc, nb, tid, stride, epoch, sweeps, converged, resid, ravg, s_red, s_bc);
-}
-
-// ---------------------------------------------------------------------------
-// Tiled order: one block per tile at a time.  The particles the tile's
-// contacts touch (its own and a one-cell halo) are gathered into a
-// shared-memory table (particle id -> slot, bounded linear probing) and the
-// tile's contact records are staged in shared memory, the tile's colours run
-// with block barriers only, and the table is written back.
-// Tiles of one tile colour share no particle, so blocks never race; a grid
-// barrier separates the tile colours.  A tile whose particles overflow the
-// table is processed through global memory instead (same order, same result).
-// ---------------------------------------------------------------------------
-__device__ __forceinline__ unsigned ht_hash(int id)
-{
-    return ((unsigned)id * 2654435761u) >> (32 - 10);   // CD_HT = 1024 slots
-}
-
-__device__ __forceinline__ int ht_insert(int* keys, int id)
-{
-    unsigned h = ht_hash(id);
-    for (int probe = 0; probe < CD_HT; ++probe) {
-        int old = atomicCAS(&keys[h], -1, id);
-        if (old == -1 || old == id) return (int)h;
-        h = (h + 1) & (CD_HT - 1);
-    }
-    return -1;
-}
-
-#define CD_TREC 1024   // contact records of one tile staged in shared memory
-
-template <int DIM, typename T>
-struct TileSmem {
-    typedef typename Vec<T>::V4 T4;
-    typedef typename Vec<T>::V2 T2;
-    typedef typename std::conditional<DIM == 2, T, T2>::type TM;   // m_t (2D) or (m_n, m_t)
-    typedef typename std::conditional<DIM == 2, T2, T4>::type TP;  // impulse
-    int keys[CD_HT];
-    T4 V[CD_HT * (DIM == 2 ? 1 : 2)];
-    T4 S[CD_HT];
-    int2 ab[CD_TREC];
-    int2 slot[CD_TREC];
-    T4 geo[CD_TREC];
-    TM m[CD_TREC];
-    TP P[CD_TREC];
-    int off[CD_KLOCAL + 1];
-    int ovf;
-};
-
-template <int DIM, typename T>
-__device__ __forceinline__ UpdOut apply_staged(const CdGeom& g, const CdWork& w, int p, int i, TileSmem<DIM, T>& sm,
-                                               bool apply_only, int crit, double alpha, double ravg_prev)
-{
-    typedef typename Vec<T>::V4 T4;
-    typedef typename Vec<T>::V2 T2;
-    Rec<DIM, T> r;
-    r.pk = 0;
-    r.mu = (T)g.mu;
-    r.ab = sm.ab[i];
-    r.geo = sm.geo[i];
-    const bool wall = r.ab.y >= g.n;
-    const int ia = sm.slot[i].x;
-    const int ib = sm.slot[i].y;
-    r.sa = sm.S[ia];
-    if (!wall) r.sb = sm.S[ib];
-    else { r.sb.x = (T)0; r.sb.y = (T)0; r.sb.z = (T)0; r.sb.w = (T)0; }
-    UpdOut o;
-    if constexpr (DIM == 2) {
-        r.mt = sm.m[i];
-        r.P = sm.P[i];
-        T4 va = sm.V[ia], vb;
-        if (!wall) vb = sm.V[ib];
-        else wall_vel2<T>(g, w, r.ab.y, vb);
-        T2 Pnew;
-        o = core2d<T>(g, r, va, vb, wall, apply_only, crit, alpha, ravg_prev, Pnew);
-        sm.V[ia] = va;
-        if (!wall) sm.V[ib] = vb;
-        if (!apply_only) ((T2*)w.c_P)[p] = Pnew;
-    } else {
-        r.m = sm.m[i];
-        r.P = sm.P[i];
-        T4 va = sm.V[2 * ia], wa = sm.V[2 * ia + 1], vb, wb;
-        if (!wall) { vb = sm.V[2 * ib]; wb = sm.V[2 * ib + 1]; }
-        else wall_vel3<T>(g, w, r.ab.y, vb, wb);
-        T4 Pnew;
-        o = core3d<T>(g, r, va, wa, vb, wb, wall, apply_only, crit, alpha, ravg_prev, Pnew);
-        sm.V[2 * ia] = va; sm.V[2 * ia + 1] = wa;
-        if (!wall) { sm.V[2 * ib] = vb; sm.V[2 * ib + 1] = wb; }
-        if (!apply_only) ((T4*)w.c_P)[p] = Pnew;
-    }
-    return o;
-}
-
-template <int DIM, typename T>
-__device__ __forceinline__ void process_tile(const CdGeom& g, const CdWork& w, int rank, TileSmem<DIM, T>& sm,
-                                             bool apply_only, int crit, double alpha, double ravg_prev,
-                                             double (&acc)[3])
-{
-    typedef typename Vec<T>::V4 T4;
-    typedef typename TileSmem<DIM, T>::TM TM;
-    typedef typename TileSmem<DIM, T>::TP TP;
-    const int base = rank * CD_KLOCAL;
-    const int bd = blockDim.x;
-    for (int k = threadIdx.x; k <= CD_KLOCAL; k += bd) sm.off[k] = w.seg_off[base + k];
-    for (int i = threadIdx.x; i < CD_HT; i += bd) sm.keys[i] = -1;
-    if (threadIdx.x == 0) sm.ovf = 0;
-    __syncthreads();
-    const int c0 = sm.off[0], c1 = sm.off[CD_KLOCAL];
-    if (c0 == c1) {
-        __syncthreads();
-        return;
-    }
-    if (c1 - c0 > CD_TREC) {
-        if (threadIdx.x == 0) sm.ovf = 1;
-    } else {
-        // contact records of the tile and their particles' table slots
-        for (int p = c0 + threadIdx.x; p < c1; p += bd) {
-            const int i = p - c0;
-            int2 ab = w.c_ab[p];
-            sm.ab[i] = ab;
-            sm.geo[i] = ((const T4*)w.c_geo)[p];
-            sm.m[i] = ((const TM*)w.c_m)[p];
-            sm.P[i] = ((const TP*)w.c_P)[p];
-            int ia = ht_insert(sm.keys, ab.x);
-            int ib = (ab.y < g.n) ? ht_insert(sm.keys, ab.y) : 0;
-            if (ia < 0 || ib < 0) sm.ovf = 1;
-            sm.slot[i] = make_int2(ia, ib);
-        }
-    }
-    __syncthreads();
-    const bool staged = (sm.ovf == 0);
-    const T4* Vg = (const T4*)w.V;
-    const T4* Sg = (const T4*)w.S;
-    if (staged) {
-        for (int i = threadIdx.x; i < CD_HT; i += bd) {
-            int id = sm.keys[i];
-            if (id >= 0) {
-                if (DIM == 2) sm.V[i] = Vg[id];
-                else { sm.V[2 * i] = Vg[2 * id]; sm.V[2 * i + 1] = Vg[2 * id + 1]; }
-                sm.S[i] = Sg[id];
-            }
-        }
-        __syncthreads();
-    }
-    for (int lc = 0; lc < CD_KLOCAL; ++lc) {
-        const int s0 = sm.off[lc], s1 = sm.off[lc + 1];
-        if (s0 == s1) continue;
-        for (int p = s0 + threadIdx.x; p < s1; p += bd) {
-            UpdOut o;
-            if (staged) {
-                o = apply_staged<DIM, T>(g, w, p, p - c0, sm, apply_only, crit, alpha, ravg_prev);
-            } else {
-                Rec<DIM, T> r;
-                load_rec<DIM, T>(g, w, p, r);
-                o = apply_rec<DIM, T>(g, w, p, r, apply_only, crit, alpha, ravg_prev);
-            }
-            acc[0] += o.pabs;
-            if (crit == CD_CONV_LOCAL) { acc[1] += (double)o.rel_ok; acc[2] += (double)o.bad; }
-        }
-        __syncthreads();
-    }
-    if (staged) {
-        T4* Vw = (T4*)w.V;
-        for (int i = threadIdx.x; i < CD_HT; i += bd) {
-            int id = sm.keys[i];
-            if (id >= 0) {
-                if (DIM == 2) Vw[id] = sm.V[i];
-                else { Vw[2 * id] = sm.V[2 * i]; Vw[2 * id + 1] = sm.V[2 * i + 1]; }
-            }
-        }
-    }
-    __syncthreads();
-}
-
-template <int DIM, typename T>
-__global__ void __launch_bounds__(CD_SWEEP_THREADS, 1)
-k_sweep_tiled(CdGeom g, CdWork w, int crit, double alpha, int max_sweeps)
-{
-    extern __shared__ __align__(16) unsigned char smraw[];
-    TileSmem<DIM, T>& sm = *reinterpret_cast<TileSmem<DIM, T>*>(smraw);
-    __shared__ int s_tc[9];
-    __shared__ double s_red[CD_SWEEP_THREADS / 32][3];
-    __shared__ double s_bc;
-    CdCtrl* ctrl = w.ctrl;
-    if (ctrl->skip) return;
-    const int nc = ctrl->nc;
-    const int nb = gridDim.x;
-    const int tid = blockIdx.x * blockDim.x + threadIdx.x;
-    const int stride = gridDim.x * blockDim.x;
-    unsigned long long epoch = 0;
-    if (threadIdx.x < 9) s_tc[threadIdx.x] = w.tc_off[threadIdx.x];
-    __syncthreads();
-
-    int sweeps = 0, converged = (nc == 0);
-    double resid = 0.0, ravg = 0.0, ravg_prev = 0.0;
-    if (nc > 0) {
-        double acc[3] = {0.0, 0.0, 0.0};
-        for (int tc = 0; tc < g.ntc; ++tc) {
-            for (int rk = s_tc[tc] + blockIdx.x; rk < s_tc[tc + 1]; rk += nb)
-                process_tile<DIM, T>(g, w, rk, sm, true, crit, alpha, 0.0, acc);
-            if (tc == g.ntc - 1) {
-                block_sum<3>(acc, s_red, 1);
-                if (threadIdx.x == 0) w.partials[blockIdx.x] = acc[0];
-            }
-            if (!cd_grid_sync(ctrl, nb, epoch)) return;
-        }
-        ravg_prev = grid_total(w.partials, nb, &s_bc) / (double)nc;
-        ravg = ravg_prev;
-        while (!converged && sweeps < max_sweeps) {
-            const int buf = (sweeps & 1) ? 0 : 1;
-            double* part = w.partials + (size_t)buf * 3 * nb;
-            double a3[3] = {0.0, 0.0, 0.0};
-            for (int tc = 0; tc < g.ntc; ++tc) {
-                for (int rk = s_tc[tc] + blockIdx.x; rk < s_tc[tc + 1]; rk += nb)
-                    process_tile<DIM, T>(g, w, rk, sm, false, crit, alpha, ravg_prev, a3);
-                if (tc == g.ntc - 1) {
-                    block_sum<3>(a3, s_red, test_values(crit));
-                    if (threadIdx.x == 0) {
-                        part[blockIdx.x] = a3[0];
-                        part[nb + blockIdx.x] = a3[1];
-                        part[2 * nb + blockIdx.x] = a3[2];
-                    }
-                }
-                if (!cd_grid_sync(ctrl, nb, epoch)) return;
-            }
-            ++sweeps;
-            sweep_test(part, nb, nc, crit, alpha, ravg_prev, ravg, resid, converged, s_red[0]);
-            ravg_prev = ravg;
-        }
-    }
-    finish_solve<DIM, T>(g, w, nc, nb, tid, stride, epoch, sweeps, converged, resid, ravg, s_red, s_bc);
-}
-
-// ---------------------------------------------------------------------------
 // Launchers
 // ---------------------------------------------------------------------------
 static int grid_n(int n)
@@ -1921,56 +1527,44 @@ cudaError_t cd_launch_unpack(const CdGeom& g, const CdWork& w, double* pos, doub
     return cudaGetLastError();
 }
 
-// Kernel of each schedule: 0 colour barrier, 1 tiled, 2 dataflow, 3 batched,
-// 4 mixed update, 5 domain-wise update.
+// Kernel of each schedule: 0 colour barrier, 3 batched, 4 mixed update,
+// 5 domain-wise update, 6 merged last colours.
 static int sweep_kind(const CdGeom& g)
 {
     if (g.npk > 1) return 3;
-    if (g.tile_cells >= 2) return 1;
-    if (g.dataflow) return 2;
     if (g.par_p > 0.0) return 4;
     if (g.ndom_total > 1) return 5;
     if (g.merge_last) return 6;
     return 0;
 }
 
-static const void* sweep_fn(int dim, int precision, int tiled)
+static const void* sweep_fn(int dim, int precision, int kind)
 {
-    if (tiled == 6) {
+    if (kind == 6) {
         if (dim == 2)
             return precision == CD_FP64 ? (const void*)k_sweep<2, double, CD_SWEEP_MERGE>
                                         : (const void*)k_sweep<2, float, CD_SWEEP_MERGE>;
         return precision == CD_FP64 ? (const void*)k_sweep<3, double, CD_SWEEP_MERGE>
                                     : (const void*)k_sweep<3, float, CD_SWEEP_MERGE>;
     }
-    if (tiled == 5) {
+    if (kind == 5) {
         if (dim == 2)
             return precision == CD_FP64 ? (const void*)k_sweep<2, double, CD_SWEEP_DOMAINS>
                                         : (const void*)k_sweep<2, float, CD_SWEEP_DOMAINS>;
         return precision == CD_FP64 ? (const void*)k_sweep<3, double, CD_SWEEP_DOMAINS>
                                     : (const void*)k_sweep<3, float, CD_SWEEP_DOMAINS>;
     }
-    if (tiled == 4) {
+    if (kind == 4) {
         if (dim == 2)
             return precision == CD_FP64 ? (const void*)k_sweep<2, double, CD_SWEEP_MIXED>
                                         : (const void*)k_sweep<2, float, CD_SWEEP_MIXED>;
         return precision == CD_FP64 ? (const void*)k_sweep<3, double, CD_SWEEP_MIXED>
                                     : (const void*)k_sweep<3, float, CD_SWEEP_MIXED>;
     }
-    if (tiled == 3) {
+    if (kind == 3) {
         if (dim == 2)
             return precision == CD_FP64 ? (const void*)k_sweep_batch<2, double> : (const void*)k_sweep_batch<2, float>;
         return precision == CD_FP64 ? (const void*)k_sweep_batch<3, double> : (const void*)k_sweep_batch<3, float>;
-    }
-    if (tiled == 2) {
-        if (dim == 2)
-            return precision == CD_FP64 ? (const void*)k_sweep_flow<2, double> : (const void*)k_sweep_flow<2, float>;
-        return precision == CD_FP64 ? (const void*)k_sweep_flow<3, double> : (const void*)k_sweep_flow<3, float>;
-    }
-    if (tiled) {
-        if (dim == 2)
-            return precision == CD_FP64 ? (const void*)k_sweep_tiled<2, double> : (const void*)k_sweep_tiled<2, float>;
-        return precision == CD_FP64 ? (const void*)k_sweep_tiled<3, double> : (const void*)k_sweep_tiled<3, float>;
     }
     if (dim == 2)
         return precision == CD_FP64 ? (const void*)k_sweep<2, double, CD_SWEEP_PLAIN>
@@ -1979,38 +1573,28 @@ static const void* sweep_fn(int dim, int precision, int tiled)
                                 : (const void*)k_sweep<3, float, CD_SWEEP_PLAIN>;
 }
 
-static size_t tile_smem(int dim, int precision)
-{
-    if (dim == 2) return precision == CD_FP64 ? sizeof(TileSmem<2, double>) : sizeof(TileSmem<2, float>);
-    return precision == CD_FP64 ? sizeof(TileSmem<3, double>) : sizeof(TileSmem<3, float>);
-}
+static const int kSweepKinds[] = {0, 3, 4, 5, 6};
 
 // Blocks of the cooperative sweep grid: one per SM (keeps the grid barrier
-// cheap), for whichever of the two kernels the system uses.
+// cheap), for whichever of the kernels the system uses.
 int cd_sweep_max_blocks(int precision, int dim, int num_sms)
 {
-    int per_sm = 0;
-    for (int tiled = 0; tiled < 7; ++tiled) {
-        const void* fn = sweep_fn(dim, precision, tiled);
-        size_t dyn = (tiled == 1) ? tile_smem(dim, precision) : 0;
-        if (tiled && cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn) != cudaSuccess)
-            return 0;
+    for (int kind : kSweepKinds) {
         int b = 0;
-        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, fn, CD_SWEEP_THREADS, dyn) != cudaSuccess) return 0;
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, sweep_fn(dim, precision, kind), CD_SWEEP_THREADS, 0) !=
+            cudaSuccess)
+            return 0;
         if (b < 1) return 0;
-        per_sm = 1;
     }
-    return per_sm * num_sms;
+    return num_sms;
 }
 
 // 1 if `per_sm` blocks of `threads` threads of the sweep kernel the system
 // uses can be resident on one SM.
 int cd_sweep_fits(const CdGeom& g, int precision, int threads, int per_sm)
 {
-    const int kind = sweep_kind(g);
     int b = 0;
-    const size_t dyn = (kind == 1) ? tile_smem(g.dim, precision) : 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, sweep_fn(g.dim, precision, kind), threads, dyn) !=
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, sweep_fn(g.dim, precision, sweep_kind(g)), threads, 0) !=
         cudaSuccess)
         return 0;
     return b >= per_sm ? 1 : 0;
@@ -2031,5 +1615,5 @@ cudaError_t cd_launch_sweep(const CdGeom& g, const CdWork& w, int coop_blocks, i
     const int kind = sweep_kind(g);
     ++*nl;
     return cudaLaunchCooperativeKernel(sweep_fn(g.dim, precision, kind), dim3(coop_blocks), dim3(threads),
-                                       args, kind == 1 ? tile_smem(g.dim, precision) : 0, s);
+                                       args, 0, s);
 }

@@ -86,7 +86,7 @@ def oracle_crit(gpu_crit):
 
 
 def run_pair(wl, steps=1, criterion=None, max_sweeps=None, alpha=None, precision=0, warm_start=1, f_ext=None,
-             use_cells=True, max_contacts=None, tile_cells=0, **gpu_kw):
+             use_cells=True, max_contacts=None, **gpu_kw):
     """Steps the workload on the GPU and in the oracle (colour order, same
     seed); returns (gpu_system, oracle_system, gpu_stats, oracle_stats)."""
     from paper_1104_3516_gb300 import cd
@@ -94,10 +94,10 @@ def run_pair(wl, steps=1, criterion=None, max_sweeps=None, alpha=None, precision
     ms = wl.max_sweeps if max_sweeps is None else max_sweeps
     al = wl.alpha if alpha is None else alpha
     g = gpu_system(wl, criterion=criterion, max_sweeps=ms, alpha=al, precision=precision, warm_start=warm_start,
-                   f_ext=f_ext, max_contacts=max_contacts, tile_cells=tile_cells, **gpu_kw)
+                   f_ext=f_ext, max_contacts=max_contacts, **gpu_kw)
     o = oracle_system(wl, f_ext=f_ext, use_cells=use_cells, criterion=oracle_crit(criterion), max_sweeps=ms,
                       alpha=al, warm_start=warm_start, order=O.ORDER_COLOUR,
-                      cap=max_contacts or max(64, 8 * wl.n), tile_cells=tile_cells,
+                      cap=max_contacts or max(64, 8 * wl.n),
                       parallel_p=gpu_kw.get("parallel_p", 0.0), domains=gpu_kw.get("domains", (1, 1, 1)))
     gst, ost = [], []
     for _ in range(steps):

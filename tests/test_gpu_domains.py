@@ -117,7 +117,7 @@ def test_chain_needs_more_sweeps_with_more_domains():
     assert sweeps[1] < sweeps[4] < sweeps[12]
 
 
-@pytest.mark.parametrize("kw", [dict(tile_cells=4), dict(dataflow=1), dict(parallel_p=0.3), dict(tape_steps=2)])
+@pytest.mark.parametrize("kw", [dict(parallel_p=0.3), dict(tape_steps=2)])
 def test_domains_refuse_other_schedules(kw):
     from paper_1104_3516_gb300 import cd
     wl, _ = CASES["dense_deposit"]

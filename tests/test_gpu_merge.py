@@ -91,7 +91,7 @@ def test_merged_phase_full_size_pile():
     assert sb[0]["last"]["n_phases"] == sb[0]["last"]["n_colours"] - 1
 
 
-@pytest.mark.parametrize("kw", [dict(tile_cells=4), dict(dataflow=1), dict(parallel_p=0.3)])
+@pytest.mark.parametrize("kw", [dict(parallel_p=0.3), dict(domains=(2, 2, 1))])
 def test_merge_is_ignored_by_other_schedules(kw):
     from paper_1104_3516_gb300 import cd
     g = gpu_system(CASES["dense_deposit"], merge_last_colour=1, criterion=cd.CD_CONV_NONE, max_sweeps=3, **kw)

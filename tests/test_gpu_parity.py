@@ -303,98 +303,6 @@ def test_given_contact_list_and_warm_impulses():
     assert float(np.abs(s["v"].reshape(-1) - v).max()) <= FP64_TOL * float(np.abs(v).max())
 
 
-# --- tiled colour order ----------------------------------------------------------
-
-TILED = [("dense_deposit", 4), ("settling_discs", 3), ("sphere_gas", 2), ("dense_deposit", 26)]
-
-
-@pytest.mark.parametrize("name,tile", TILED)
-def test_tiled_colours_equal_oracle(name, tile):
-    wl = CASES[name]
-    g = gpu_system(wl, tile_cells=tile)
-    g.detect_contacts()
-    got = g.contacts()
-    p = oparams(wl, tile_cells=tile)
-    colour, group, K = O.tile_colour(p, wl.x, wl.r, got["pairs"])
-    assert np.array_equal(got["colour"], colour)
-
-
-@pytest.mark.parametrize("name,tile", TILED)
-@pytest.mark.parametrize("k", [1, 7, 40])
-def test_tiled_fp64_sweep_by_sweep(name, tile, k):
-    """Tile 26 on the 5000-disc deposit overflows the shared-memory table and
-    exercises the global-memory fallback."""
-    from paper_1104_3516_gb300 import cd
-    wl = CASES[name]
-    g, o, gst, ost = run_pair(wl, criterion=cd.CD_CONV_NONE, max_sweeps=k, tile_cells=tile)
-    c = g.contacts()
-    assert np.array_equal(c["pairs"], o.contacts)
-    assert impulse_err(c["impulse"], o.impulses) <= FP64_TOL
-    s = g.state()
-    vs = max(float(np.abs(o.v).max()), 1e-300)
-    assert float(np.abs(s["v"].reshape(-1) - o.v).max()) <= FP64_TOL * vs
-
-
-@pytest.mark.parametrize("name,tile", [("dense_deposit", 4), ("sphere_gas", 2)])
-def test_tiled_fp32_sweep_by_sweep(name, tile):
-    from paper_1104_3516_gb300 import cd
-    wl = CASES[name]
-    g, o, gst, ost = run_pair(wl, criterion=cd.CD_CONV_NONE, max_sweeps=40, precision=cd.CD_FP32, tile_cells=tile)
-    assert impulse_err(g.contacts()["impulse"], o.impulses) <= FP32_TOL
-
-
-def test_tiled_convergence_and_multi_step():
-    wl = W.settling_discs(n=2000, vsig=0.3, seed=31)
-    g, o, gst, ost = run_pair(wl, steps=6, max_sweeps=300, alpha=1e-8, tile_cells=3)
-    for a, b in zip(gst, ost):
-        assert a["last"]["sweeps"] == b["sweeps"]
-    assert impulse_err(g.contacts()["impulse"], o.impulses) <= 1e-11
-
-
-# --- dataflow schedule (per-particle update counts instead of colour barriers) ---
-
-@pytest.mark.parametrize("name", ["dense_deposit", "settling_discs", "sphere_gas"])
-@pytest.mark.parametrize("k", [1, 7, 40])
-def test_dataflow_fp64_sweep_by_sweep(name, k):
-    from paper_1104_3516_gb300 import cd
-    wl = CASES[name]
-    g, o, gst, ost = run_pair(wl, criterion=cd.CD_CONV_NONE, max_sweeps=k, dataflow=1)
-    c = g.contacts()
-    assert gst[0]["last"]["sweeps"] == k
-    assert impulse_err(c["impulse"], o.impulses) <= FP64_TOL
-    s = g.state()
-    vs = max(float(np.abs(o.v).max()), 1e-300)
-    assert float(np.abs(s["v"].reshape(-1) - o.v).max()) <= FP64_TOL * vs
-
-
-@pytest.mark.parametrize("prec", [0, 1])
-def test_dataflow_is_bit_identical_to_the_barrier_schedule(prec):
-    """Same update order, so the same bits, including the convergence stop."""
-    from paper_1104_3516_gb300 import cd
-    wl = CASES["dense_deposit"]
-    out = []
-    for flow in (0, 1):
-        g = gpu_system(wl, criterion=cd.CD_CONV_GLOBAL_REL, max_sweeps=300, alpha=1e-7, precision=prec,
-                       dataflow=flow)
-        st = g.step(2)
-        out.append((st["total_sweeps"], g.contacts()["impulse"], g.state()["v"]))
-    assert out[0][0] == out[1][0]
-    assert np.array_equal(out[0][1], out[1][1])
-    assert np.array_equal(out[0][2], out[1][2])
-
-
-def test_dataflow_fp32_and_convergence():
-    from paper_1104_3516_gb300 import cd
-    wl = CASES["sphere_gas"]
-    g, o, gst, ost = run_pair(wl, criterion=cd.CD_CONV_NONE, max_sweeps=30, precision=cd.CD_FP32, dataflow=1)
-    assert impulse_err(g.contacts()["impulse"], o.impulses) <= FP32_TOL
-    wl = W.settling_discs(n=2000, vsig=0.3, seed=31)
-    g, o, gst, ost = run_pair(wl, steps=5, max_sweeps=300, alpha=1e-8, dataflow=1)
-    for a, b in zip(gst, ost):
-        assert a["last"]["sweeps"] == b["sweeps"]
-    assert impulse_err(g.contacts()["impulse"], o.impulses) <= 1e-11
-
-
 # --- mixed parallel / sequential update (Sec. 2.3) -------------------------------
 
 @pytest.mark.parametrize("p", [0.3, 1.0])

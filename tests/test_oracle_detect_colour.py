@@ -209,64 +209,3 @@ def test_repaired_pile_uses_as_many_colours_as_the_busiest_particle():
     deg = np.bincount(pairs[:, 0], minlength=wl.n) + np.bincount(pairs[:, 1][pairs[:, 1] < wl.n], minlength=wl.n)
     assert _conflicts(wl.n, pairs, colour) == 0
     assert K == int(deg.max())
-
-
-@pytest.mark.parametrize("dim,periodic,tile_cells", [(2, (1, 0), 2), (2, (0, 0), 3), (3, (0, 0, 0), 2),
-                                                     (2, (1, 1), 4)])
-def test_tiled_colouring_orders_independent_contacts(dim, periodic, tile_cells):
-    """Tiled order: inside a tile, one colour never repeats a particle; across
-    tiles, two tiles of the same tile colour never share a particle (they are
-    at least one whole tile of >= 2 cells apart), so each (tile colour,
-    colour) class is a set of independent contacts."""
-    walls = 0 if all(periodic) else (0b1100 if dim == 2 else 0b110000)
-    p, x, r, wp = random_case(dim, 700 if dim == 2 else 900, periodic, walls, 11, phi=0.45 if dim == 2 else 0.25)
-    p.tile_cells = tile_cells
-    pairs = O.detect_cells(p, x, r, wp)
-    n = r.shape[0]
-    colour, group, K = O.tile_colour(p, x, r, pairs)
-    ntc = 1 << dim
-    tiles = np.unique(group % (group.max() + 1))
-    assert len(np.unique(group)) > ntc            # several tiles per tile colour
-    ntiles_guess = None
-    # tile colour = group // ntiles; recover ntiles from the group values
-    tc_vals = np.unique(group)
-    for k in range(K):
-        # same colour, same tile: no shared particle
-        for gval in np.unique(group[colour == k]):
-            sel = pairs[(colour == k) & (group == gval)].ravel()
-            sel = sel[sel < n]
-            assert len(sel) == len(np.unique(sel))
-    # the whole class (tile colour, colour) across tiles: no shared particle
-    # (group = tc * ntiles + tile with ntiles the tile count; tiles of one tile
-    # colour share tc, so classes are keyed by (group // ntiles, colour))
-    D = dim
-    rmax = float(r.max())
-    ell = 2 * rmax + p.delta
-    m = [max(1, int(np.floor((p.box_hi[k] - p.box_lo[k]) / ell))) for k in range(D)]
-    nt = []
-    for k in range(D):
-        t = max(1, m[k] // tile_cells)
-        if periodic[k] and t > 1 and t % 2:
-            t -= 1
-        nt.append(t)
-    ntiles = int(np.prod(nt))
-    tc = group // ntiles
-    for c in np.unique(tc):
-        for k in range(K):
-            sel = pairs[(tc == c) & (colour == k)].ravel()
-            sel = sel[sel < n]
-            assert len(sel) == len(np.unique(sel)), (c, k)
-
-
-def test_tiled_order_reaches_the_column_closed_form():
-    import oracle_cases as cases
-    from oracle_adapter import system
-    n = 6
-    wl = cases.column(n=n)
-    s = system(wl, order=O.ORDER_COLOUR, criterion=O.CRIT_GLOBAL_REL, alpha=1e-15, max_sweeps=20000, tile_cells=2)
-    st = s.step()
-    assert st["converged"]
-    m = 1.0 / wl.inv_m[0]
-    for (a, b), (pn, pt) in zip(s.contacts, s.impulses):
-        k = n - a if b == n + 2 else n - 1 - a
-        assert pn == pytest.approx(k * m * 1.0 * 1e-3, rel=1e-9)
