@@ -81,8 +81,8 @@ def test_domains_stop_at_the_oracle_sweep_over_warm_started_steps():
                               domains=(5, 3, 1))
     for a, b in zip(gst, ost):
         assert a["last"]["sweeps"] == b["sweeps"]
-    assert impulse_err(g.contacts()["impulse"], o.impulses) <= 1e-11
-    check_state(g, o, 1e-11)
+    assert impulse_err(g.contacts()["impulse"], o.impulses) <= 1e-12
+    check_state(g, o, 1e-12)
 
 
 def test_domains_sharing_no_particle_equal_gauss_seidel():
@@ -112,7 +112,7 @@ def test_chain_needs_more_sweeps_with_more_domains():
                                   warm_start=0, domains=(Np, 1, 1))
         assert gst[0]["last"]["sweeps"] == ost[0]["sweeps"]
         assert gst[0]["last"]["converged"]
-        assert impulse_err(g.contacts()["impulse"], o.impulses) <= 1e-11
+        assert impulse_err(g.contacts()["impulse"], o.impulses) <= 1e-12
         sweeps[Np] = ost[0]["sweeps"]
     assert sweeps[1] < sweeps[4] < sweeps[12]
 
