@@ -82,7 +82,7 @@ def parse():
     ap.add_argument("--domains", type=int, nargs=3, default=[1, 1, 1], metavar=("NX", "NY", "NZ"),
                     help="domain-wise update of Sec. 3.1: slabs per axis (1 1 1: Gauss-Seidel)")
     ap.add_argument("--merge-last-colour", type=int, default=1,
-                    help="1: run the two last colours as one phase when the last class is small")
+                    help="1: run the three (else two) last colours as one phase when the last class is small; 2: two at most; 0: off")
     ap.add_argument("--sphere-steps", type=int, default=5,
                     help="timed steps of the 1e6-sphere 3D gas leg (rank 0 at N=1 only; 0: skip)")
     ap.add_argument("--batched-steps", type=int, default=3,
@@ -120,7 +120,7 @@ def config(args, wl, extra=None):
               "warm_start": True,
               "order": "colour (largest degree first, then hash)",
               "domains": list(args.domains),
-              "merge_last_colour": bool(args.merge_last_colour),
+              "merge_last_colour": args.merge_last_colour,
               "l2": "flushed (512 MiB write) before every timed step"})
     if extra:
         c.update(extra)

@@ -176,11 +176,11 @@ static size_t layout(cd_system* s, char* base, CdWork* w)
     }
     {
         const bool mg = s->g.merge_last != 0;
-        const size_t nbk = 2 * (size_t)s->g.merge_blocks + 1;
-        t.mg_pa = L.take<int>(base, mg ? n : 1);
-        t.mg_pb = L.take<int>(base, mg ? n : 1);
+        const size_t nbk = CD_MG_MAXC * (size_t)s->g.merge_blocks + 1;
+        t.mg_slot = L.take<int>(base, mg ? CD_MG_MAXC * n : 1);
         t.mg_label = L.take<int>(base, mg ? cap : 1);
         t.mg_size = L.take<int>(base, mg ? cap + 1 : 1);
+        t.mg_w = L.take<int>(base, mg ? cap + 1 : 1);
         t.mg_start = L.take<int>(base, mg ? cap + 1 : 1);
         t.mg_bucket = L.take<int>(base, mg ? cap : 1);
         t.mg_list = L.take<int>(base, mg ? cap : 1);
@@ -291,7 +291,7 @@ static void fill_solve_stats(const cd_system* s, const CdCtrl& h, cd_solve_stats
     o->n_contacts = h.nc;
     o->n_colours = h.ncolours;
     for (int k = 0; k < 6; ++k) o->wall_force[k] = h.wall_force[k];
-    o->n_phases = h.ncolours - ((s->g.merge_last && h.merge) ? 1 : 0);
+    o->n_phases = h.ncolours - ((s->g.merge_last && h.merge >= 2) ? h.merge - 1 : 0);
 }
 
 static cd_status need_ready(cd_system* s)
@@ -606,13 +606,13 @@ static cd_status create_impl(const cd_params* params, int64_t npk, const int64_t
     }
     // merging of the two last colours: plain systems with the colour-barrier
     // schedule (ignored otherwise)
-    if (p.merge_last_colour != 0 && p.merge_last_colour != 1) {
+    if (p.merge_last_colour < 0 || p.merge_last_colour > 3) {
         delete s;
-        return fail(nullptr, CD_ERR_INVALID_ARG, "merge_last_colour must be 0 or 1");
+        return fail(nullptr, CD_ERR_INVALID_ARG, "merge_last_colour must be 0, 1, 2 or 3");
     }
     g.merge_last = (p.merge_last_colour && npk == 1 && g.par_p == 0.0 &&
                     g.ndom_total == 1 && !g.dyn_walls && p.tape_steps == 0 && cd_merge_label_blocks_per_sm() >= 1)
-                       ? 1 : 0;
+                       ? (p.merge_last_colour == 2 ? 2 : 3) : 0;
     g.merge_blocks = s->sweep_blocks;
     if (g.merge_last && !cd_sweep_fits(g, (int)p.precision, s->sweep_threads, s->sweep_blocks / s->num_sms)) {
         delete s;

@@ -14,6 +14,7 @@
 #define CD_BLOCK 256          // threads per block of the streaming kernels
 #define CD_CHUNK 256          // contacts per chunk of the stable colour partition
 #define CD_WAIT_NS 2000000000ULL  // bound on any device-side wait (2 s)
+#define CD_MG_MAXC 3          // most colours one merged sweep phase takes
 
 // Device error codes written into CdCtrl::error.
 enum { CDE_NONE = 0, CDE_TIMEOUT = 1, CDE_COLOURS = 2, CDE_PER_PARTICLE = 3, CDE_TAPE = 4 };
@@ -54,8 +55,8 @@ struct CdCtrl {
     long long adj_diverged;
     int tape_slot;                  // slot the next recorded step goes to
     int tape_pad;
-    // merging of the two last colours (params.merge_last_colour)
-    int merge;                      // 1: this step's sweeps run the two last colours as one phase
+    // merging of the last colours (params.merge_last_colour)
+    int merge;                      // M > 0: this step's sweeps run the M last colours as one phase
     int mg_changed;                 // chain labelling: a label moved in the current round
     int mg_maxsize;                 // largest chain
     int mg_pad;
@@ -156,17 +157,17 @@ struct CdWork {
     // merging of the two last colours: the colour-order positions of the two
     // last colours form chains (contacts linked through a shared particle);
     // chains are assigned whole to the blocks of the sweep grid
-    int* mg_pa;         // n: position of the particle's contact of the second-last colour, or -1
-    int* mg_pb;         // n: position of its contact of the last colour, or -1
+    int* mg_slot;       // CD_MG_MAXC x n: [m n + i] position of particle i's contact of colour K-M+m, or -1
     int* mg_label;      // cap: chain label (smallest position of the chain)
     int* mg_size;       // cap + 1: contacts of the chain labelled by the index
-    int* mg_start;      // cap + 1: exclusive scan of mg_size
-    int* mg_bucket;     // cap: block (second-last colour) or G + block (last colour)
+    int* mg_w;          // cap + 1: its contacts of colour K-M
+    int* mg_start;      // cap + 1: exclusive scan of mg_w
+    int* mg_bucket;     // cap: m G + block (colour K-M+m)
     int* mg_list;       // cap: positions grouped by bucket, ascending inside each
-    int* mg_bcnt;       // 2 G + 1: contacts per bucket
-    int* mg_boff;       // 2 G + 1: exclusive scan of mg_bcnt
-    int* mg_bmin;       // 2 G: lowest position of the bucket
-    int* mg_bmax;       // 2 G: highest position of the bucket
+    int* mg_bcnt;       // CD_MG_MAXC G + 1: contacts per bucket
+    int* mg_boff;       // CD_MG_MAXC G + 1: exclusive scan of mg_bcnt
+    int* mg_bmin;       // CD_MG_MAXC G: lowest position of the bucket
+    int* mg_bmax;       // CD_MG_MAXC G: highest position of the bucket
     // repair of the highest colour (global colour order)
     int* rep_top;       // npk: highest colour of each packing
     int* rep_dmax;      // npk: most contacts of one body of the packing
@@ -262,7 +263,7 @@ struct CdGeom {
     double wall_push[6];// its push along the inward normal
     int ndom[3];        // domain-wise update (Sec. 3.1): slabs per axis (1: not cut)
     int ndom_total;     // product; > 1 selects the domain-wise sweep
-    int merge_last;     // params.merge_last_colour
+    int merge_last;     // params.merge_last_colour (0 off, 2: at most two colours, 3: three, else two)
     int merge_blocks;   // blocks of the sweep grid the chains are assigned to
 };
 

@@ -1,27 +1,27 @@
-// Merging of the two last colours of a step into one sweep phase.
+// Merging of the last colours of a step into one sweep phase.
 //
-// Every colour costs a grid barrier per sweep; after the colour repair the
-// last class of a dense packing is small (2,293 of 223,196 contacts on the
-// 1e5-disc pile) but still a whole phase.  The contacts of the second-last
-// colour (A) and of the last colour (B) form chains: an A contact and a B
-// contact are linked when they share a particle, and since a particle has at
-// most one contact of each colour, a chain is a path or a cycle alternating
-// A and B.  Different chains share no particle.  If every chain goes whole
-// to one block of the persistent grid, the block can update its chains' A
-// contacts, synchronise its threads and then update their B contacts: the
-// same order as the two phases, with a block barrier in place of a grid
-// barrier.
+// Every colour costs a grid barrier per sweep.  Take the contacts of the M
+// last colours (M = 3 or 2) and link two of them when they share a particle;
+// since a particle has at most one contact of each colour, the linked groups
+// ("chains": paths and cycles for M = 2, small trees and meshes for M = 3)
+// are small on a dense packing, and different chains share no particle.  If
+// every chain goes whole to one block of the persistent grid, the block can
+// update its chains' contacts of colour K-M, synchronise its threads, update
+// those of colour K-M+1, and so on: the same order as M separate phases, with
+// block barriers in place of M - 1 grid barriers.
 //
-// Per step (after the colour order is built): label every position of the
-// two colours with the smallest position of its chain (minimum propagation
-// along the links, bounded rounds), count the chains, order them by label
-// and cut that order into G pieces of about equal contact counts (one per
-// block), and list each block's A positions and B positions in ascending
-// order (one warp per list scans the window of positions the list spans, so
-// the lists do not depend on timing).  The step is merged only if the
-// labelling converged, no chain holds more than 64 contacts and the B class
-// is at most a quarter of the A class; the sweep reads the decision from the
-// control block.
+// Per step (after the colour order is built): label every position of the M
+// colours with the smallest position of its chain (minimum propagation along
+// the links, bounded rounds), count the chains, order them by label and cut
+// that order into G pieces of about equal numbers of colour-(K-M) contacts
+// (the largest sub-step; one piece per block), and list each block's
+// positions of each colour in ascending order (one warp per list scans the
+// window of positions the list spans, so the lists do not depend on timing).
+// The step is merged only if the labelling converged, no chain holds more
+// than 64 contacts and the last class is at most a quarter of the class
+// K-M.  params.merge_last_colour 1 (or 3) tries M = 3 first and, if that is
+// not taken, M = 2; 2 tries M = 2 only.  The sweep reads the decision, M or
+// 0, from the control block.
 #include <climits>
 
 #include "cd_internal.cuh"
@@ -29,40 +29,59 @@
 #define CD_MG_MAX_CHAIN 64
 #define CD_MG_ROUNDS 80
 
-// Positions [a0, b0) hold the second-last colour, [b0, e) the last one.
-__device__ __forceinline__ bool mg_segment(const CdWork& w, int& a0, int& b0, int& e)
+// Colour-order positions of the M last colours: colour K-M+m at [bnd[m],
+// bnd[m+1]), m = 0 .. M-1.  False when there are not at least M + 1 colours
+// or one of the M classes is empty.
+__device__ __forceinline__ bool mg_segment(const CdWork& w, int M, int (&bnd)[CD_MG_MAXC + 1])
 {
     const int K = w.ctrl->ncolours;
-    if (K < 3 || K > CD_KMAX) return false;
-    a0 = w.colour_off[K - 2];
-    b0 = w.colour_off[K - 1];
-    e = w.colour_off[K];
-    return b0 > a0 && e > b0;
+    if (M < 2 || M > CD_MG_MAXC || K < M + 1 || K > CD_KMAX) return false;
+    for (int m = 0; m <= M; ++m) bnd[m] = w.colour_off[K - M + m];
+    for (int m = 0; m < M; ++m)
+        if (bnd[m + 1] <= bnd[m]) return false;
+    return true;
 }
 
-__global__ void k_mg_init(CdGeom g, CdWork w)
+// Merged colour (0 .. M-1) of position p in [bnd[0], bnd[M]).
+__device__ __forceinline__ int mg_colour(const int (&bnd)[CD_MG_MAXC + 1], int M, int p)
 {
+    int m = 0;
+    while (m + 1 < M && p >= bnd[m + 1]) ++m;
+    return m;
+}
+
+// A pass for M colours runs only if no earlier pass of this step merged
+// (first: the pass that resets the decision).
+__device__ __forceinline__ bool mg_pass_live(const CdCtrl* ctrl)
+{
+    return !ctrl->skip && ctrl->merge == 0;
+}
+
+__global__ void k_mg_init(CdGeom g, CdWork w, int M, int first)
+{
+    CdCtrl* ctrl = w.ctrl;
+    if (!first && !mg_pass_live(ctrl)) return;
     const int i0 = blockIdx.x * blockDim.x + threadIdx.x, st = gridDim.x * blockDim.x;
-    for (int i = i0; i < g.n; i += st) { w.mg_pa[i] = -1; w.mg_pb[i] = -1; }
-    for (int i = i0; i <= g.cap; i += st) w.mg_size[i] = 0;
-    const int nbk = 2 * g.merge_blocks;
+    for (int i = i0; i < M * g.n; i += st) w.mg_slot[i] = -1;
+    for (int i = i0; i <= g.cap; i += st) { w.mg_size[i] = 0; w.mg_w[i] = 0; }
+    const int nbk = M * g.merge_blocks;
     for (int i = i0; i <= nbk; i += st) w.mg_bcnt[i] = 0;
     for (int i = i0; i < nbk; i += st) { w.mg_bmin[i] = INT_MAX; w.mg_bmax[i] = -1; }
     if (i0 == 0) {
-        w.ctrl->merge = 0;
-        w.ctrl->mg_changed = 1;
-        w.ctrl->mg_maxsize = 0;
+        if (first) ctrl->merge = 0;
+        ctrl->mg_changed = 1;
+        ctrl->mg_maxsize = 0;
     }
 }
 
-__global__ void k_mg_mark(CdGeom g, CdWork w)
+__global__ void k_mg_mark(CdGeom g, CdWork w, int M)
 {
-    if (w.ctrl->skip) return;
-    int a0, b0, e;
-    if (!mg_segment(w, a0, b0, e)) return;
-    for (int p = a0 + blockIdx.x * blockDim.x + threadIdx.x; p < e; p += gridDim.x * blockDim.x) {
+    if (!mg_pass_live(w.ctrl)) return;
+    int bnd[CD_MG_MAXC + 1];
+    if (!mg_segment(w, M, bnd)) return;
+    for (int p = bnd[0] + blockIdx.x * blockDim.x + threadIdx.x; p < bnd[M]; p += gridDim.x * blockDim.x) {
         const int2 ab = w.c_ab[p];
-        int* slot = (p < b0) ? w.mg_pa : w.mg_pb;
+        int* slot = w.mg_slot + mg_colour(bnd, M, p) * g.n;
         slot[ab.x] = p;
         if (ab.y < g.n) slot[ab.y] = p;
         w.mg_label[p] = p;
@@ -73,12 +92,12 @@ __global__ void k_mg_mark(CdGeom g, CdWork w)
 // label moves (labels only decrease, so reading a neighbour's label while it
 // changes is harmless).  round_cnt (free after the colouring) holds three
 // rotating "moved" flags.
-__global__ void k_mg_label(CdGeom g, CdWork w, int* flag)
+__global__ void k_mg_label(CdGeom g, CdWork w, int* flag, int M)
 {
     CdCtrl* ctrl = w.ctrl;
-    if (ctrl->skip) return;
-    int a0, b0, e;
-    if (!mg_segment(w, a0, b0, e)) return;
+    if (!mg_pass_live(ctrl)) return;
+    int bnd[CD_MG_MAXC + 1];
+    if (!mg_segment(w, M, bnd)) return;
     const unsigned long long nb = gridDim.x;
     unsigned long long epoch = 0;
     const int tid = blockIdx.x * blockDim.x + threadIdx.x, st = gridDim.x * blockDim.x;
@@ -89,16 +108,20 @@ __global__ void k_mg_label(CdGeom g, CdWork w, int* flag)
         // flag (r + 1) % 3 was last read before the previous barrier
         if (tid == 0) flag[(round + 1) % 3] = 0;
         int moved = 0;
-        for (int p = a0 + tid; p < e; p += st) {
+        for (int p = bnd[0] + tid; p < bnd[M]; p += st) {
             const int2 ab = w.c_ab[p];
-            const int* other = (p < b0) ? w.mg_pb : w.mg_pa;
+            const int mp = mg_colour(bnd, M, p);
             int m = cd_ld_volatile_int(&w.mg_label[p]);
             const int own = m;
-            const int d0 = other[ab.x];
-            if (d0 >= 0) m = min(m, cd_ld_volatile_int(&w.mg_label[d0]));
-            if (ab.y < g.n) {
-                const int d1 = other[ab.y];
-                if (d1 >= 0) m = min(m, cd_ld_volatile_int(&w.mg_label[d1]));
+            for (int q = 0; q < M; ++q) {
+                if (q == mp) continue;
+                const int* other = w.mg_slot + q * g.n;
+                const int d0 = other[ab.x];
+                if (d0 >= 0) m = min(m, cd_ld_volatile_int(&w.mg_label[d0]));
+                if (ab.y < g.n) {
+                    const int d1 = other[ab.y];
+                    if (d1 >= 0) m = min(m, cd_ld_volatile_int(&w.mg_label[d1]));
+                }
             }
             if (m < own) {
                 *(volatile int*)&w.mg_label[p] = m;
@@ -114,35 +137,39 @@ __global__ void k_mg_label(CdGeom g, CdWork w, int* flag)
     }
 }
 
-__global__ void k_mg_size(CdGeom g, CdWork w)
+// Chain sizes (all contacts, for the size limit) and weights (contacts of
+// colour K-M, which the pieces balance).
+__global__ void k_mg_size(CdGeom g, CdWork w, int M)
 {
-    if (w.ctrl->skip) return;
-    int a0, b0, e;
-    if (!mg_segment(w, a0, b0, e)) return;
-    for (int p = a0 + blockIdx.x * blockDim.x + threadIdx.x; p < e; p += gridDim.x * blockDim.x) {
-        const int s = atomicAdd(&w.mg_size[w.mg_label[p]], 1) + 1;
+    if (!mg_pass_live(w.ctrl)) return;
+    int bnd[CD_MG_MAXC + 1];
+    if (!mg_segment(w, M, bnd)) return;
+    for (int p = bnd[0] + blockIdx.x * blockDim.x + threadIdx.x; p < bnd[M]; p += gridDim.x * blockDim.x) {
+        const int lab = w.mg_label[p];
+        const int s = atomicAdd(&w.mg_size[lab], 1) + 1;
         atomicMax(&w.ctrl->mg_maxsize, s);
+        if (p < bnd[1]) atomicAdd(&w.mg_w[lab], 1);
     }
 }
 
-// The decision, then each position's bucket: chains in label order cut into
-// G pieces of about equal size.
-__global__ void k_mg_bucket(CdGeom g, CdWork w)
+// The decision, then each position's bucket m G + block: chains in label
+// order cut into G pieces of about equal colour-(K-M) counts.
+__global__ void k_mg_bucket(CdGeom g, CdWork w, int M)
 {
     CdCtrl* ctrl = w.ctrl;
-    if (ctrl->skip) return;
-    int a0, b0, e;
-    if (!mg_segment(w, a0, b0, e)) return;
-    const bool ok = ctrl->mg_changed == 0 && ctrl->mg_maxsize <= CD_MG_MAX_CHAIN && 4 * (e - b0) <= (b0 - a0);
+    if (!mg_pass_live(ctrl)) return;
+    int bnd[CD_MG_MAXC + 1];
+    if (!mg_segment(w, M, bnd)) return;
+    const bool ok = ctrl->mg_changed == 0 && ctrl->mg_maxsize <= CD_MG_MAX_CHAIN &&
+                    4 * (bnd[M] - bnd[M - 1]) <= (bnd[1] - bnd[0]);
     if (!ok) return;
-    if (blockIdx.x == 0 && threadIdx.x == 0) ctrl->merge = 1;
     const int G = g.merge_blocks;
-    const long long total = e - a0;
-    for (int p = a0 + blockIdx.x * blockDim.x + threadIdx.x; p < e; p += gridDim.x * blockDim.x) {
-        const long long off = w.mg_start[w.mg_label[p]];   // chains before this one, in label order
+    const long long total = bnd[1] - bnd[0];
+    for (int p = bnd[0] + blockIdx.x * blockDim.x + threadIdx.x; p < bnd[M]; p += gridDim.x * blockDim.x) {
+        const long long off = w.mg_start[w.mg_label[p]];   // colour-(K-M) contacts of the chains before
         int blk = (int)((off * G) / total);
         if (blk > G - 1) blk = G - 1;
-        const int k = (p < b0) ? blk : G + blk;
+        const int k = mg_colour(bnd, M, p) * G + blk;
         w.mg_bucket[p] = k;
         atomicAdd(&w.mg_bcnt[k], 1);
         atomicMin(&w.mg_bmin[k], p);
@@ -150,13 +177,27 @@ __global__ void k_mg_bucket(CdGeom g, CdWork w)
     }
 }
 
-// One warp per bucket lists its positions in ascending order.
-__global__ void k_mg_fill(CdGeom g, CdWork w)
+// Publishes the decision after every block of k_mg_bucket has run (a kernel
+// of its own: the bucket kernel's blocks read ctrl->merge through
+// mg_pass_live while they work).
+__global__ void k_mg_decide(CdWork w, int M)
 {
-    if (w.ctrl->skip || !w.ctrl->merge) return;
+    CdCtrl* ctrl = w.ctrl;
+    if (!mg_pass_live(ctrl)) return;
+    int bnd[CD_MG_MAXC + 1];
+    if (!mg_segment(w, M, bnd)) return;
+    const bool ok = ctrl->mg_changed == 0 && ctrl->mg_maxsize <= CD_MG_MAX_CHAIN &&
+                    4 * (bnd[M] - bnd[M - 1]) <= (bnd[1] - bnd[0]);
+    if (ok) ctrl->merge = M;
+}
+
+// One warp per bucket lists its positions in ascending order.
+__global__ void k_mg_fill(CdGeom g, CdWork w, int M)
+{
+    if (w.ctrl->skip || w.ctrl->merge != M) return;
     const int lane = threadIdx.x & 31;
     const int k = (int)((blockIdx.x * blockDim.x + threadIdx.x) >> 5);
-    if (k >= 2 * g.merge_blocks) return;
+    if (k >= M * g.merge_blocks) return;
     const int lo = w.mg_bmin[k], hi = w.mg_bmax[k];
     int base = w.mg_boff[k];
     for (int p0 = lo; p0 <= hi; p0 += 32) {
@@ -168,41 +209,57 @@ __global__ void k_mg_fill(CdGeom g, CdWork w)
     }
 }
 
-cudaError_t cd_launch_merge(const CdGeom& g, const CdWork& w, int coop_blocks, cudaStream_t s, int* nl)
+// One pass of the pipeline for M colours.
+static cudaError_t merge_pass(const CdGeom& g, const CdWork& w, int coop_blocks, int M, int first, cudaStream_t s,
+                              int* nl)
 {
     cudaError_t e;
-    const int nbk = 2 * g.merge_blocks;
+    const int nbk = M * g.merge_blocks;
     int m = g.cap + 1;
-    if (g.n > m) m = g.n;
+    if (M * g.n > m) m = M * g.n;
     if (nbk + 1 > m) m = nbk + 1;
     int gm = (m + CD_BLOCK - 1) / CD_BLOCK;
     if (gm > 4096) gm = 4096;
     int gc = (g.cap + CD_BLOCK - 1) / CD_BLOCK;
     if (gc < 1) gc = 1;
     if (gc > 4096) gc = 4096;
-    k_mg_init<<<gm, CD_BLOCK, 0, s>>>(g, w);
-    k_mg_mark<<<gc, CD_BLOCK, 0, s>>>(g, w);
+    k_mg_init<<<gm, CD_BLOCK, 0, s>>>(g, w, M, first);
+    k_mg_mark<<<gc, CD_BLOCK, 0, s>>>(g, w, M);
     *nl += 2;
     {
         CdGeom ga = g;
         CdWork wa = w;
         int* flag = w.round_cnt;
-        void* args[] = {&ga, &wa, &flag};
+        int mm = M;
+        void* args[] = {&ga, &wa, &flag, &mm};
         if ((e = cudaMemsetAsync(w.ctrl, 0, 2 * sizeof(unsigned long long), s)) != cudaSuccess) return e;
         if ((e = cudaLaunchCooperativeKernel((const void*)k_mg_label, dim3(coop_blocks), dim3(CD_SWEEP_THREADS), args, 0,
                                              s)) != cudaSuccess)
             return e;
         ++*nl;
     }
-    k_mg_size<<<gc, CD_BLOCK, 0, s>>>(g, w);
+    k_mg_size<<<gc, CD_BLOCK, 0, s>>>(g, w, M);
     ++*nl;
-    if ((e = cd_scan_exclusive(w.mg_size, w.mg_start, g.cap + 1, w.scan_tmp, nullptr, s, nl)) != cudaSuccess) return e;
-    k_mg_bucket<<<gc, CD_BLOCK, 0, s>>>(g, w);
-    ++*nl;
+    if ((e = cd_scan_exclusive(w.mg_w, w.mg_start, g.cap + 1, w.scan_tmp, nullptr, s, nl)) != cudaSuccess) return e;
+    k_mg_bucket<<<gc, CD_BLOCK, 0, s>>>(g, w, M);
+    k_mg_decide<<<1, 1, 0, s>>>(w, M);
+    *nl += 2;
     if ((e = cd_scan_exclusive(w.mg_bcnt, w.mg_boff, nbk + 1, w.scan_tmp, nullptr, s, nl)) != cudaSuccess) return e;
-    k_mg_fill<<<(nbk * 32 + 255) / 256, 256, 0, s>>>(g, w);
+    k_mg_fill<<<(nbk * 32 + 255) / 256, 256, 0, s>>>(g, w, M);
     ++*nl;
     return cudaGetLastError();
+}
+
+// The passes run in turn on the stream; a pass after one that merged does
+// nothing but its two scans, which recompute the same offsets from the
+// unchanged counts (the first M G + 1 bucket counts and the chain weights).
+cudaError_t cd_launch_merge(const CdGeom& g, const CdWork& w, int coop_blocks, cudaStream_t s, int* nl)
+{
+    cudaError_t e;
+    const int mmax = (g.merge_last == 2) ? 2 : CD_MG_MAXC;
+    for (int M = mmax; M >= 2; --M)
+        if ((e = merge_pass(g, w, coop_blocks, M, M == mmax, s, nl)) != cudaSuccess) return e;
+    return cudaSuccess;
 }
 
 int cd_merge_label_blocks_per_sm()

@@ -26,17 +26,18 @@
 // mixed update of Sec. 2.3, the domain-wise update of Sec. 3.1.
 enum { CD_SWEEP_PLAIN = 0, CD_SWEEP_MIXED = 1, CD_SWEEP_DOMAINS = 2, CD_SWEEP_MERGE = 3 };
 
-// Merged last phase of a step (params.merge_last_colour): this block's lists
-// of second-last-colour positions [a0, a1) and last-colour positions [b0, b1)
-// in mg_list; phase `klast` runs them in place of the two last colours.  The
-// block's items are numbered A first, then B; item q goes to thread
-// q % blockDim, so a thread's first item (prefetched before the grid
-// barrier) is an A or a B contact and the B contacts wait after the block
-// barrier only for their velocities.
+// Merged last phase of a step (params.merge_last_colour): phase `klast` runs
+// the M last colours in place of M phases.  This block's positions of colour
+// K-M+m are mg_list[lst[2m] .. lst[2m + 1]) (lst in shared memory).  The
+// block's items are numbered through the M lists in turn;
+// item q goes to thread q % blockDim, so a thread's first item (prefetched
+// before the grid barrier) may belong to any of the lists, and the later
+// sub-steps wait after their block barrier only for their velocities.
 struct MgInfo {
     int on;
     int klast;
-    int a0, a1, b0, b1;
+    int M;
+    const int* lst;
 };
 
 template <typename T> struct Vec;
@@ -722,9 +723,16 @@ __device__ __forceinline__ void prefetch_any(const CdGeom& g, const CdWork& w, c
 {
     if constexpr (MODE == CD_SWEEP_MERGE) {
         if (mg.on && k == mg.klast) {
-            const int q = (int)threadIdx.x, nA = mg.a1 - mg.a0, nB = mg.b1 - mg.b0;
-            if (q < nA) load_rec<DIM, T>(g, w, w.mg_list[mg.a0 + q], nxt);
-            else if (q < nA + nB) load_rec<DIM, T>(g, w, w.mg_list[mg.b0 + (q - nA)], nxt);
+            // item q = threadIdx.x of the block's lists taken in turn
+            int q = (int)threadIdx.x;
+            for (int m = 0; m < mg.M; ++m) {
+                const int cnt = mg.lst[2 * m + 1] - mg.lst[2 * m];
+                if (q < cnt) {
+                    load_rec<DIM, T>(g, w, w.mg_list[mg.lst[2 * m] + q], nxt);
+                    break;
+                }
+                q -= cnt;
+            }
             return;
         }
     }
@@ -750,39 +758,29 @@ __device__ __forceinline__ void colour_phase(const CdGeom& g, const CdWork& w, c
     constexpr bool DEFER = (DIM == 2) && std::is_same<T, double>::value;
     if constexpr (MODE == CD_SWEEP_MERGE) {
         if (mg.on && k == mg.klast) {
-            // the chains' second-last-colour contacts, a block barrier, their last-colour ones
+            // the chains' contacts of colour K-M, a block barrier, those of K-M+1, ...
             const int t = (int)threadIdx.x, bd = (int)blockDim.x;
-            const int nA = mg.a1 - mg.a0, tot = nA + (mg.b1 - mg.b0);
-            for (int q = t; q < nA; q += bd) {
-                const int p = w.mg_list[mg.a0 + q];
-                UpdOut o;
-                if (q == t) {
-                    o = apply_rec<DIM, T, false, DEFER>(g, w, p, nxt, apply_only, crit, alpha, ravg_prev, pend);
-                } else {
-                    Rec<DIM, T> r;
-                    load_rec<DIM, T>(g, w, p, r);
-                    o = apply_rec<DIM, T, false, DEFER>(g, w, p, r, apply_only, crit, alpha, ravg_prev, pend);
+            int base = 0;   // items of the earlier lists
+            for (int m = 0; m < mg.M; ++m) {
+                const int l0 = mg.lst[2 * m], cnt = mg.lst[2 * m + 1] - l0;
+                int q0 = t;
+                if (q0 < base) q0 += ((base - q0 + bd - 1) / bd) * bd;   // this thread's first item of list m
+                for (int q = q0; q < base + cnt; q += bd) {
+                    const int p = w.mg_list[l0 + (q - base)];
+                    UpdOut o;
+                    if (q == t) {
+                        o = apply_rec<DIM, T, false, DEFER>(g, w, p, nxt, apply_only, crit, alpha, ravg_prev, pend);
+                    } else {
+                        Rec<DIM, T> r;
+                        load_rec<DIM, T>(g, w, p, r);
+                        o = apply_rec<DIM, T, false, DEFER>(g, w, p, r, apply_only, crit, alpha, ravg_prev, pend);
+                    }
+                    acc[0] += o.pabs;
+                    if (DEFER) pend = make_double2(o.pn, o.pt);
+                    if (crit == CD_CONV_LOCAL) { acc[1] += (double)o.rel_ok; acc[2] += (double)o.bad; }
                 }
-                acc[0] += o.pabs;
-                if (DEFER) pend = make_double2(o.pn, o.pt);
-                if (crit == CD_CONV_LOCAL) { acc[1] += (double)o.rel_ok; acc[2] += (double)o.bad; }
-            }
-            __syncthreads();
-            int q0 = t;
-            if (q0 < nA) q0 += ((nA - q0 + bd - 1) / bd) * bd;   // this thread's first item past the A items
-            for (int q = q0; q < tot; q += bd) {
-                const int p = w.mg_list[mg.b0 + (q - nA)];
-                UpdOut o;
-                if (q == t) {
-                    o = apply_rec<DIM, T, false, DEFER>(g, w, p, nxt, apply_only, crit, alpha, ravg_prev, pend);
-                } else {
-                    Rec<DIM, T> r;
-                    load_rec<DIM, T>(g, w, p, r);
-                    o = apply_rec<DIM, T, false, DEFER>(g, w, p, r, apply_only, crit, alpha, ravg_prev, pend);
-                }
-                acc[0] += o.pabs;
-                if (DEFER) pend = make_double2(o.pn, o.pt);
-                if (crit == CD_CONV_LOCAL) { acc[1] += (double)o.rel_ok; acc[2] += (double)o.bad; }
+                base += cnt;
+                if (m + 1 < mg.M) __syncthreads();
             }
             if (knext >= 0) prefetch_any<DIM, T, MODE>(g, w, s_off, knext, nxt, mg);
             return;
@@ -1045,18 +1043,22 @@ k_sweep(CdGeom g, CdWork w, int crit, double alpha, int max_sweeps)
     unsigned long long epoch = 0;
     for (int k = threadIdx.x; k <= CD_KMAX; k += blockDim.x) s_off[k] = w.colour_off[k];
     MgInfo mg;
-    mg.on = 0; mg.klast = -1; mg.a0 = mg.a1 = mg.b0 = mg.b1 = 0;
+    mg.on = 0; mg.klast = -1; mg.M = 0; mg.lst = nullptr;
+    __shared__ int s_mgl[2 * CD_MG_MAXC];
     if constexpr (MODE == CD_SWEEP_MERGE) {
-        if (ctrl->merge) {
-            // the two last colours run as one phase (lists built for this grid)
+        const int M = ctrl->merge;
+        if (M >= 2 && M <= CD_MG_MAXC && nb == g.merge_blocks) {
+            // the M last colours run as one phase (lists built for this grid)
             mg.on = 1;
-            K -= 1;
+            mg.M = M;
+            K -= M - 1;
             mg.klast = K - 1;
             const int b = blockIdx.x;
-            mg.a0 = w.mg_boff[b];
-            mg.a1 = w.mg_boff[b + 1];
-            mg.b0 = w.mg_boff[nb + b];
-            mg.b1 = w.mg_boff[nb + b + 1];
+            if (threadIdx.x < 2 * M) {
+                const int m = threadIdx.x >> 1;
+                s_mgl[threadIdx.x] = w.mg_boff[m * nb + b + (threadIdx.x & 1)];
+            }
+            mg.lst = s_mgl;
         }
     }
     __syncthreads();
