@@ -92,6 +92,12 @@ def parse():
                     help="skip the autotuner and use the default 512 x 1 sweep grid")
     ap.add_argument("--adjoint-steps", type=int, default=200,
                     help="steps of the differentiated settling rollout (0: skip the adjoint leg)")
+    ap.add_argument("--fp32-steps", type=int, default=None,
+                    help="timed steps of the FP32 leg on the same pile (default --steps; 0: skip)")
+    ap.add_argument("--dilute-steps", type=int, default=200,
+                    help="timed steps of the 1,000-disc dilute leg (0: skip)")
+    ap.add_argument("--converge-cap", type=int, default=100000,
+                    help="sweep cap of the untimed steps that measure the sweeps to residual 1e-6 (0: skip)")
     ap.add_argument("--cpu-sweeps", type=int, default=30,
                     help="sweep cap of the oracle's bounded sample step")
     return ap.parse_args()
@@ -308,6 +314,69 @@ def run_reference(args):
 # The CUDA path
 # ---------------------------------------------------------------------------
 
+def sweep_bytes_model(dim, precision):
+    """Compulsory bytes of one colour sweep: per contact record and per particle."""
+    if dim == 3:
+        return BYTES_PER_CONTACT_3D[precision], BYTES_PER_PARTICLE_3D[precision]
+    return BYTES_PER_CONTACT[precision], BYTES_PER_PARTICLE[precision]
+
+
+def timed_steps(sysg, wl, steps, flush, precision):
+    """`steps` CD time steps of a system created with timing=1, the L2 flushed
+    (512 MiB written) before each; device times from the library's CUDA events
+    on its stream."""
+    bpc, bpp = sweep_bytes_model(wl.dim, precision)
+    out = {"upd": 0, "sweeps": 0, "launches": 0, "not_conv": 0, "sweep_bytes": 0.0, "ncs": [], "colours": [],
+           "phases": [], "ph": {"detect": 0.0, "colour_order_pack": 0.0, "sweep": 0.0, "integrate": 0.0}}
+    for _ in range(steps):
+        flush.zero_()
+        st = sysg.step(1)
+        out["upd"] += st["total_contact_updates"]
+        out["sweeps"] += st["total_sweeps"]
+        out["launches"] += st["kernel_launches"]
+        out["not_conv"] += st["n_not_converged"]
+        nc = st["last"]["n_contacts"]
+        out["ncs"].append(nc)
+        out["colours"].append(st["last"]["n_colours"])
+        out["phases"].append(st["last"]["n_phases"])
+        out["sweep_bytes"] += st["total_sweeps"] * (nc * bpc + wl.n * bpp)
+        for k in out["ph"]:
+            out["ph"][k] += st["phase_ms"][k]
+    return out
+
+
+def graph_steps(g, steps, flush, stream):
+    """`steps` steps of a system created with use_graph=1 (each replayed from
+    the captured CUDA graph).  The counts come from a first pass with
+    statistics; the system is then put back to its checkpoint and the same
+    steps (bit-identical) are replayed without a host synchronisation inside,
+    the L2 flushed before each, every step bracketed by CUDA events on the
+    system's stream.  Returns (device ms, summed counts)."""
+    import torch
+    ck = g.save_checkpoint()
+    cnt = {"upd": 0, "sweeps": 0, "not_conv": 0, "max_sweeps": 0, "launches": 0, "contacts": 0}
+    for _ in range(steps):
+        st = g.step(1)
+        cnt["upd"] += st["total_contact_updates"]
+        cnt["sweeps"] += st["total_sweeps"]
+        cnt["not_conv"] += st["n_not_converged"]
+        cnt["max_sweeps"] = max(cnt["max_sweeps"], st["max_sweeps_in_step"])
+        cnt["launches"] += st["kernel_launches"]
+        cnt["contacts"] = st["last"]["n_contacts"]
+    g.load_checkpoint(ck)
+    evs = []
+    for _ in range(steps):
+        with torch.cuda.stream(stream):
+            flush.zero_()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        g.step(1, stats=False)
+        e1.record(stream)
+        evs.append((e0, e1))
+    torch.cuda.synchronize()
+    return sum(a.elapsed_time(b) for a, b in evs), cnt
+
+
 def run_ours(args):
     import torch
     rank, ws, local = dist_init(args)
@@ -340,33 +409,15 @@ def run_ours(args):
     clocks = ClockSampler(local)
     clocks.start()
     wall0 = time.perf_counter()
-    upd = sweeps = launches = not_conv = 0
-    ph = {"detect": 0.0, "colour_order_pack": 0.0, "sweep": 0.0, "integrate": 0.0}
-    sweep_bytes = 0.0
-    ncs, colours, phases = [], [], []
-    if wl.dim == 3:
-        bpc, bpp = BYTES_PER_CONTACT_3D[args.precision], BYTES_PER_PARTICLE_3D[args.precision]
-    else:
-        bpc, bpp = BYTES_PER_CONTACT[args.precision], BYTES_PER_PARTICLE[args.precision]
+    bpc, bpp = sweep_bytes_model(wl.dim, args.precision)
     flops_per_update = FLOPS_PER_UPDATE_3D if wl.dim == 3 else FLOPS_PER_UPDATE_2D
-    for _ in range(args.steps):
-        flush.zero_()
-        st = sysg.step(1)
-        upd += st["total_contact_updates"]
-        sweeps += st["total_sweeps"]
-        launches += st["kernel_launches"]
-        not_conv += st["n_not_converged"]
-        nc = st["last"]["n_contacts"]
-        ncs.append(nc)
-        colours.append(st["last"]["n_colours"])
-        phases.append(st["last"]["n_phases"])
-        sweep_bytes += st["total_sweeps"] * (nc * bpc + wl.n * bpp)
-        for k in ph:
-            ph[k] += st["phase_ms"][k]
+    t = timed_steps(sysg, wl, args.steps, flush, args.precision)
     torch.cuda.synchronize(device)
     barrier(ws)
     wall = time.perf_counter() - wall0
     clk = clocks.stop()
+    upd, sweeps, launches, not_conv = t["upd"], t["sweeps"], t["launches"], t["not_conv"]
+    ph, sweep_bytes, ncs, colours, phases = t["ph"], t["sweep_bytes"], t["ncs"], t["colours"], t["phases"]
 
     dev_ms = sum(ph.values())
     (dev_ms_max, wall_max), (upd_sum, steps_sum) = reduce_max_sum([dev_ms, wall], [float(upd), float(args.steps)],
@@ -397,7 +448,7 @@ def run_ours(args):
 
     batched = None
     if args.batched_steps > 0 and wl.dim == 2:
-        batched = run_batched(args, device, rank, flush)
+        batched = run_batched(args, device, rank, flush, ws)
 
     adjoint = None
     if args.adjoint_steps > 0 and args.precision == "f64" and wl.dim == 2:
@@ -406,6 +457,16 @@ def run_ours(args):
     sphere = None
     if args.sphere_steps > 0 and wl.dim == 2 and ws == 1:
         sphere = run_sphere_gas(args, device, flush)
+
+    fp32 = dilute = converge = None
+    fp32_steps = args.steps if args.fp32_steps is None else args.fp32_steps
+    if fp32_steps > 0 and args.precision == "f64" and wl.dim == 2 and ws == 1:
+        a32 = argparse.Namespace(**{**vars(args), "steps": fp32_steps})
+        fp32 = run_fp32(a32, wl, device, flush, shape)
+    if args.dilute_steps > 0 and wl.dim == 2 and ws == 1:
+        dilute = run_dilute(args, device, flush)
+    if args.converge_cap > 0 and args.precision == "f64" and wl.dim == 2 and ws == 1:
+        converge = run_converge(args, sysg, wl, device, shape)
 
     e2e = None
     if not args.no_e2e:
@@ -433,21 +494,117 @@ def run_ours(args):
                                         "steps_not_converged": not_conv, "parallelism": f"replicas x{ws}"}),
             "phase_ms_per_step": {k: v / max(args.steps, 1) for k, v in ph.items()},
             "wall_s": wall_max, "roofline": roofline, "autotune": tuned, "batched": batched, "adjoint": adjoint,
-            "sphere_gas_3d": sphere,
+            "sphere_gas_3d": sphere, "fp32": fp32, "dilute_discs_2d": dilute, "at_residual_1e-6": converge,
             "cpu_baseline": cpu,
             "e2e": e2e,
             "gpu_launches": launches, "clocks": clk}
     print(json.dumps(line), flush=True)
 
 
-def run_batched(args, device, rank, flush):
+def run_fp32(args, wl, device, flush, shape):
+    """The same 1e5-disc pile and convergence test with the sweep in FP32
+    (contact records and sweep-time velocities in FP32; the residual
+    reduction and the integration in FP64): warm-up, then `steps` timed
+    steps with the L2 flushed before each."""
+    import torch
+    from paper_1104_3516_gb300 import cd
+    stream = torch.cuda.current_stream(device)
+    g = cd.CDSystem(wl, device=device, precision=cd.CD_FP32, criterion=cd.CD_CONV_GLOBAL_REL,
+                    max_contacts=4 * wl.n, timing=1, stream=stream, merge_last_colour=args.merge_last_colour,
+                    **shape)
+    for _ in range(args.warmup):
+        flush.zero_()
+        g.step(1)
+    torch.cuda.synchronize(device)
+    t = timed_steps(g, wl, args.steps, flush, "f32")
+    ms = sum(t["ph"].values())
+    sweep_s = t["ph"]["sweep"] / 1e3
+    peak, peak_kind = peaks()
+    gbs = t["sweep_bytes"] / sweep_s / 1e9 if sweep_s > 0 else 0.0
+    bpc, bpp = sweep_bytes_model(2, "f32")
+    out = {"value": t["upd"] / (ms / 1e3), "unit": UNIT, "dtype": "f32", "steps": args.steps,
+           "ms_per_step": ms / args.steps, "steps_per_s": args.steps / (ms / 1e3),
+           "sweeps_per_step": t["sweeps"] / args.steps, "steps_not_converged": t["not_conv"],
+           "mean_phases_per_sweep": float(np.mean(t["phases"])),
+           "phase_ms_per_step": {k: v / args.steps for k, v in t["ph"].items()},
+           "roofline": {"bound": "hbm", "achieved": gbs, "peak": peak, "unit": "GB/s", "frac": gbs / peak,
+                        "kernel": "k_sweep<2,float>", "peak_source": f"{peak_kind} HBM copy bandwidth",
+                        "bytes_model": f"per sweep {bpc} B x contacts + {bpp} B x particles",
+                        "note": "the pile is L2-resident: the sweep is bound by the latency of its colour phases, "
+                                "not by HBM"},
+           "workload": "the same dense_biaxial_discs_2d packing as the headline line"}
+    del g
+    return out
+
+
+def run_dilute(args, device, flush):
+    """The 1,000-disc dilute configuration: discs r ~ U[0.8, 1.2], mu = 0.3,
+    random sequential placement at packing fraction 0.40 in a box 40 wide
+    with floor and side walls, gravity 1, dt = 1e-3, the same convergence
+    test; 3 untimed steps (the first captures the step's CUDA graph), then
+    `dilute_steps` steps replayed from the graph, the L2 flushed before each."""
+    import torch
+    from paper_1104_3516_gb300 import cd, workloads as W
+    wl = W.dilute_discs(seed=1105, n=1000)
+    wl.max_sweeps = args.max_sweeps
+    wl.alpha = args.alpha
+    stream = torch.cuda.Stream(device=device)
+    g = cd.CDSystem(wl, device=device, criterion=cd.CD_CONV_GLOBAL_REL, use_graph=1, stream=stream,
+                    merge_last_colour=args.merge_last_colour)
+    g.step(3)
+    ms, cnt = graph_steps(g, args.dilute_steps, flush, stream)
+    n = args.dilute_steps
+    out = {"value": cnt["upd"] / (ms / 1e3), "unit": UNIT, "dtype": "f64", "discs": wl.n, "steps": n,
+           "ms_per_step": ms / n, "steps_per_s": n / (ms / 1e3), "sweeps_per_step": cnt["sweeps"] / n,
+           "max_sweeps_in_step": cnt["max_sweeps"], "steps_not_converged": cnt["not_conv"],
+           "contacts_last_step": cnt["contacts"], "kernel_launches_per_step": cnt["launches"] / n,
+           "steps_from_cuda_graph": True,
+           "workload": "dilute_discs_2d: 1000 discs, RSA at packing fraction 0.40 in a box 40 wide, floor and "
+                       "side walls, v0 = 0, mu 0.3, 200 steps of dt 1e-3"}
+    del g
+    return out
+
+
+def run_converge(args, sysg, wl, device, shape):
+    """Sweeps the headline pile needs to reach the 1e-6 residual: a system
+    over the state the timed steps left (positions, velocities, walls), with
+    the sweep cap raised to `converge_cap`, stepped twice (untimed for the
+    headline; device time recorded): the first solve starts from zero
+    impulses, the second from the first's (warm start, as in the timed
+    steps), so the second is one CD step at residual 1e-6."""
+    import torch
+    from paper_1104_3516_gb300 import cd, workloads as W
+    s = sysg.state()
+    wl2 = W.Workload(**{**wl.__dict__})
+    wl2.x, wl2.v, wl2.w = s["x"], s["v"], s["w"]
+    wl2.wall_pos = np.asarray(sysg.walls(), dtype=np.float64)
+    wl2.max_sweeps = args.converge_cap
+    stream = torch.cuda.current_stream(device)
+    g = cd.CDSystem(wl2, device=device, precision=cd.CD_FP64, criterion=cd.CD_CONV_GLOBAL_REL,
+                    max_contacts=4 * wl.n, timing=1, stream=stream, merge_last_colour=args.merge_last_colour,
+                    **shape)
+    out = {"sweep_cap": args.converge_cap, "alpha": args.alpha}
+    for name in ("cold_start", "warm_start"):
+        st = g.step(1)
+        ms = sum(st["phase_ms"].values())
+        out[name] = {"sweeps": st["total_sweeps"], "converged": st["n_not_converged"] == 0, "step_ms": ms,
+                     "sweep_ms": st["phase_ms"]["sweep"], "residual": st["last"]["residual"],
+                     "steps_per_s": 1e3 / ms if ms > 0 else None}
+    del g
+    return out
+
+
+def run_batched(args, device, rank, flush, ws=1):
     """The batched workload: independent 2D packings (disc counts log-uniform
     in [200, 20000], mu ~ U[0.1, 0.6], each a pile settled under gravity in a
     periodic-x box sized to packing fraction 0.5), all stepped by one batched
-    system."""
+    system.  Under torchrun the packings are split across the ranks: rank r
+    takes the contiguous index range shard_range(packings, r, N) of the same
+    seeded batch (disjoint, covering it), and the line reports the work of all
+    ranks over the slowest rank's time (no data-path collective)."""
     import torch
     from paper_1104_3516_gb300 import cd, workloads as W
-    batch = W.batched_settling(seed=1108 + rank, n_packings=args.packings)
+    batch = W.batched_settling(seed=1108, n_packings=args.packings, shard=(rank, ws))
     for b in batch:
         b.max_sweeps = args.max_sweeps
         b.alpha = args.alpha
@@ -460,33 +617,41 @@ def run_batched(args, device, rank, flush):
                                      candidates=[dict(sweep_threads=t, sweep_blocks_per_sm=b)
                                                  for t, b in autotune.BLOCK_SHAPES])
         tuned = {"choice": shape, "ms_per_sweep": [[c, m] for c, m in table]}
+    # steps replayed from a captured CUDA graph (use_graph needs its own stream and timing 0);
+    # the batch's working set (~1 GB) is larger than L2, so the steps run back to back
+    stream = torch.cuda.Stream(device=device)
     g = cd.CDSystem(batch[0], device=device, batch=batch, precision=prec, criterion=cd.CD_CONV_GLOBAL_REL,
-                    timing=1, max_contacts=6 * sum(b.n for b in batch), **shape)
-    flush.zero_()
+                    max_contacts=6 * sum(b.n for b in batch), use_graph=1, stream=stream, **shape)
     g.step(1)
-    upd = sweeps = 0
-    ms = sweep_ms = 0.0
-    for _ in range(args.batched_steps):
-        flush.zero_()
-        st = g.step(1)
-        upd += st["total_contact_updates"]
-        sweeps = max(sweeps, st["max_sweeps_in_step"])
-        ms += sum(st["phase_ms"].values())
-        sweep_ms += st["phase_ms"]["sweep"]
-        nc = st["last"]["n_contacts"]
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize(device)
+    barrier(ws)
+    e0.record(stream)
+    st = g.step(args.batched_steps)
+    e1.record(stream)
+    e1.synchronize()
+    ms_rank = e0.elapsed_time(e1)
+    upd_rank, sweeps, nc = st["total_contact_updates"], st["max_sweeps_in_step"], st["last"]["n_contacts"]
+    (ms,), (upd,) = reduce_max_sum([ms_rank], [float(upd_rank)], ws, device)
     stats = g.packing_stats()
     sw = np.array([p["sweeps"] for p in stats])
-    out = {"value": upd / (ms / 1e3), "unit": UNIT, "packings": len(batch), "particles": int(sum(b.n for b in batch)),
-           "contacts": nc, "steps": args.batched_steps, "ms_per_step": ms / args.batched_steps,
-           "sweep_kernel_ms_per_step": sweep_ms / args.batched_steps,
+    lo, hi = W.shard_range(args.packings, rank, ws)
+    out = {"value": upd / (ms / 1e3), "unit": UNIT, "dtype": args.precision, "packings": args.packings,
+           "scaling": "strong" if ws > 1 else None,
+           "shard": f"rank 0 of {ws}: packings [{lo}, {hi}) of {args.packings} (ranks take disjoint contiguous "
+                    f"index ranges)",
+           "particles_rank0": int(sum(b.n for b in batch)),
+           "contacts_rank0": nc, "steps": args.batched_steps, "ms_per_step": ms / args.batched_steps,
            "steps_per_s": args.batched_steps / (ms / 1e3), "max_sweeps_in_step": int(sweeps),
+           "steps_from_cuda_graph": True, "kernel_launches_per_step": st["kernel_launches"] / args.batched_steps,
            "sweeps_last_step": {"min": int(sw.min()), "median": float(np.median(sw)), "max": int(sw.max())},
            "packings_converged_last_step": int(sum(p["converged"] for p in stats)), "autotune": tuned,
            "workload": "batched_settling_2d: disc counts log-uniform [200, 20000], mu ~ U[0.1, 0.6], "
                        "gravity-settled piles in periodic-x boxes at packing fraction 0.5"}
     if args.precision == "f64":
-        out["fp64_tflops"] = FLOPS_PER_UPDATE_2D * upd / (sweep_ms / 1e3) / 1e12
-        out["alu_frac"] = out["fp64_tflops"] / FP64_PEAK_TFLOPS
+        # on the whole step's device time (detection and colouring included): a lower bound for the sweep
+        out["fp64_tflops_whole_step"] = FLOPS_PER_UPDATE_2D * upd / (ms / 1e3) / 1e12
+        out["alu_frac_whole_step"] = out["fp64_tflops_whole_step"] / FP64_PEAK_TFLOPS
     del g
     torch.cuda.empty_cache()
     return out
@@ -510,17 +675,33 @@ def run_sphere_gas(args, device, flush):
     upd = sweeps = 0
     ph = {}
     colours, ncs = [], []
+    sweep_bytes = 0.0
+    bpc, bpp = sweep_bytes_model(3, "f64")
     for _ in range(args.sphere_steps):
         flush.zero_()
         st = g.step(1)
         upd += st["total_contact_updates"]
         sweeps += st["total_sweeps"]
+        sweep_bytes += st["total_sweeps"] * (st["last"]["n_contacts"] * bpc + wl.n * bpp)
         for k, v in st["phase_ms"].items():
             ph[k] = ph.get(k, 0.0) + v
         colours.append(st["last"]["n_colours"])
         ncs.append(st["last"]["n_contacts"])
     ms = sum(ph.values())
-    out = {"value": upd / (ms / 1e3), "unit": UNIT, "spheres": wl.n, "steps": args.sphere_steps,
+    sweep_s = ph["sweep"] / 1e3
+    peak, peak_kind = peaks()
+    gbs = sweep_bytes / sweep_s / 1e9 if sweep_s > 0 else 0.0
+    tf = FLOPS_PER_UPDATE_3D * upd / sweep_s / 1e12 if sweep_s > 0 else 0.0
+    bpc, bpp = sweep_bytes_model(3, "f64")
+    roofline = {"bound": "alu", "achieved": tf, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
+                "frac": tf / FP64_PEAK_TFLOPS, "kernel": "k_sweep<3,double>",
+                "peak_source": "FP64 unit count x clock (152 SMs x 2 FMA/clk x 2 x 2.07 GHz)",
+                "flops_model": f"{FLOPS_PER_UPDATE_3D} FP64 flops per contact update",
+                "avg_launch_ms": ph["sweep"] / args.sphere_steps,
+                "hbm_view": {"bound": "hbm", "achieved": gbs, "peak": peak, "unit": "GB/s", "frac": gbs / peak,
+                             "peak_source": f"{peak_kind} HBM copy bandwidth",
+                             "bytes_model": f"per sweep {bpc} B x contacts + {bpp} B x particles"}}
+    out = {"value": upd / (ms / 1e3), "unit": UNIT, "spheres": wl.n, "steps": args.sphere_steps, "roofline": roofline,
            "ms_per_step": ms / args.sphere_steps, "steps_per_s": args.sphere_steps / (ms / 1e3),
            "phase_ms_per_step": {k: v / args.sphere_steps for k, v in ph.items()},
            "sweeps_per_step": sweeps / args.sphere_steps, "contacts": ncs[-1], "colours": colours,
@@ -540,7 +721,16 @@ def run_adjoint(args, device, rank, flush, every=20, adj_alpha=1e-10):
       velocities N(0, 0.05), falling under gravity;
     * settled pile (supplementary, solver-heavy, at most 40 steps): the same
       discs deposited into a loaded pile on a floor, periodic in x, so that
-      every step solves a hyperstatic contact network.
+      every step solves a hyperstatic contact network;
+    * sliding pyramids (supplementary, friction-dominated, `adjoint_steps`
+      steps): 3,334 pyramids of three discs (10,002 discs) on a floor moving
+      sideways at 1 under them, periodic in x, at rest: the base discs slide
+      on the floor all along, so both losses depend on mu; dL/dmu is checked
+      against central differences of four more forward rollouts (mu +- 1e-4,
+      mu +- 2e-4), Richardson-extrapolated.  The floor pressure carries ~4e-9
+      of rounding noise from the trajectory and a contact opens at mu + 4e-4,
+      so its difference quotient resolves only ~1e-4; the packing height's
+      resolves ~1e-7.
 
     Two losses of the final state are differentiated with respect to mu and
     all initial velocities: the floor pressure of the last step and the
@@ -553,23 +743,32 @@ def run_adjoint(args, device, rank, flush, every=20, adj_alpha=1e-10):
                           "settling_discs_2d: jittered lattice at packing fraction 0.5, floor and side walls, "
                           "v0 ~ N(0, 0.05)"),
              "settled_pile": (W.settled_pile(1109 + rank, 10_000), min(args.adjoint_steps, 40),
-                              "settled_pile_2d (supplementary): gravity-deposited pile, floor, periodic x, v0 = 0")}
+                              "settled_pile_2d (supplementary): gravity-deposited pile, floor, periodic x, v0 = 0"),
+             "sliding_pyramids": (W.sliding_pyramids(1113 + rank, 3334), args.adjoint_steps,
+                                  "sliding_pyramids_2d (supplementary): 3,334 three-disc pyramids on a floor moving "
+                                  "sideways at 1, periodic x, v0 = 0")}
     out = {"checkpoint_every": every, "adjoint_alpha": adj_alpha, "n_discs": 10_000, "mu": 0.3}
     for cname, (wl, steps, desc) in cases.items():
-        out[cname] = adjoint_case(args, device, flush, wl, desc, every, adj_alpha, steps)
+        # the pyramids' forward solves sweep 150 times per step (converged: ~40 reach 1e-13), the same
+        # in every run, so that central differences resolve dL/dmu
+        fd = cname == "sliding_pyramids"
+        out[cname] = adjoint_case(args, device, flush, wl, desc, every, adj_alpha, steps,
+                                  fd_h=1e-4 if fd else None, fixed_sweeps=150 if fd else None)
     torch.cuda.empty_cache()
     return out
 
 
-def adjoint_case(args, device, flush, wl, desc, every, adj_alpha, steps, compliance=0.0):
+def adjoint_case(args, device, flush, wl, desc, every, adj_alpha, steps, compliance=0.0, fd_h=None,
+                 fixed_sweeps=None):
     import torch
     from paper_1104_3516_gb300 import cd
-    wl.max_sweeps = args.max_sweeps
+    wl.max_sweeps = args.max_sweeps if fixed_sweeps is None else fixed_sweeps
     wl.alpha = args.alpha
+    crit = cd.CD_CONV_GLOBAL_REL if fixed_sweeps is None else cd.CD_CONV_NONE
     T = steps
     width = float(wl.box_hi[0] - wl.box_lo[0])
     # steps replayed from a captured CUDA graph (one step = ~25 launches)
-    g = cd.CDSystem(wl, device=device, criterion=cd.CD_CONV_GLOBAL_REL, tape_steps=every,
+    g = cd.CDSystem(wl, device=device, criterion=crit, tape_steps=every,
                     adjoint_compliance=compliance, use_graph=1, stream=torch.cuda.Stream(device=device))
     stream = g.stream
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -597,6 +796,8 @@ def adjoint_case(args, device, flush, wl, desc, every, adj_alpha, steps, complia
     losses = {"floor_pressure": (float(last["wall_force"][2]) / width, None, [0, 0, 1.0 / width, 0, 0, 0]),
               "packing_height": (float(y[top]), top, None)}
     out = {"workload": desc, "steps": T, "adjoint_compliance": compliance, "steps_from_cuda_graph": True,
+           "forward_test": ("fixed sweeps" if fixed_sweeps else f"global residual {wl.alpha}"),
+           "forward_max_sweeps": wl.max_sweeps,
            "forward_ms_per_step": fwd_ms / T, "forward_sweeps_per_step": fwd_sweeps / T,
            "contacts_last_step": int(last["n_contacts"]),
            "forward_contact_updates_per_s": fwd_upd / (fwd_ms / 1e3) if fwd_ms > 0 else 0.0, "losses": {}}
@@ -632,8 +833,17 @@ def adjoint_case(args, device, flush, wl, desc, every, adj_alpha, steps, complia
         e1.record(stream)
         e1.synchronize()
         bwd_ms = e0.elapsed_time(e1)
+        gnorm = float(gv.norm())
+        if diverged or not_conv or not (math.isfinite(gmu) and math.isfinite(gnorm)):
+            # no derivative: the frozen-state reverse system has no bounded solution on some step
+            status = (f"failed: reverse pass diverged on {diverged} and hit the sweep cap on {not_conv} of {T} "
+                      f"steps ({hyper} steps with more retained rows than degrees of freedom)")
+            gmu_out, gnorm_out = None, None
+        else:
+            status = "ok"
+            gmu_out, gnorm_out = gmu, gnorm
         out["losses"][name] = {
-            "value": val, "dL_dmu": gmu, "dL_dv0_norm": float(gv.norm()),
+            "value": val, "status": status, "dL_dmu": gmu_out, "dL_dv0_norm": gnorm_out,
             "backward_ms_per_step": bwd_ms / T, "adjoint_kernel_ms_per_step": adj_ms / T,
             "adjoint_sweeps_per_step": sweeps / T, "adjoint_sweeps_max": int(max_sw),
             "adjoint_contact_updates_per_s": upd / (adj_ms / 1e3) if adj_ms > 0 else 0.0,
@@ -642,6 +852,27 @@ def adjoint_case(args, device, flush, wl, desc, every, adj_alpha, steps, complia
             "steps_per_s_forward_plus_backward": T / ((fwd_ms + bwd_ms) / 1e3)}
     g.load_checkpoint(final)
     del g
+    if fd_h:
+        # central differences in mu of both losses at h and 2 h, Richardson-extrapolated
+        import copy
+        vals = {}
+        for sgn in (1, -1, 2, -2):
+            w2 = copy.copy(wl)
+            w2.mu = wl.mu + sgn * fd_h
+            g2 = cd.CDSystem(w2, device=device, criterion=crit)
+            st2 = g2.step(T)
+            y2 = g2.pos.view(n, 2)[:, 1] + g2.radius
+            vals[sgn] = {"floor_pressure": float(st2["last"]["wall_force"][2]) / width,
+                         "packing_height": float(torch.max(y2))}
+            del g2
+        for name in losses:
+            d1 = (vals[1][name] - vals[-1][name]) / (2 * fd_h)
+            d2 = (vals[2][name] - vals[-2][name]) / (4 * fd_h)
+            fd = (4 * d1 - d2) / 3
+            ad = out["losses"][name]["dL_dmu"]
+            out["losses"][name]["fd_check"] = {
+                "h": fd_h, "central_h": d1, "central_2h": d2, "dL_dmu_fd": fd,
+                "rel_err": (abs(fd - ad) / max(abs(fd), 1e-300)) if ad is not None else None}
     return out
 
 

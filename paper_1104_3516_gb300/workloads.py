@@ -299,6 +299,40 @@ def pressure_column(seed=1112, n=8000, width_diameters=20, pressure=0.25, mu=0.3
     return wl
 
 
+def sliding_pyramids(seed=1113, n_pyramids=3334, spacing=8.0, floor_speed=1.0, base_gap=1.0, mu=0.3,
+                     steps=200) -> Workload:
+    """Pyramids of three discs, r ~ U[0.8, 1.2], on a floor that moves
+    sideways at `floor_speed` under them, periodic in x (one pyramid per
+    `spacing` of floor), at rest, gravity 1: two base discs stand on the
+    floor `base_gap` apart and the third rests on both (all contact gaps 0).
+    The floor slides under the base discs all along a 200-step rollout, so
+    friction drives the pyramids and, through the top disc's inclined
+    contacts, their floor forces and heights: a contact-dominated case
+    whose losses depend on mu, with four contacts per nine degrees of
+    freedom (no hyperstatic network)."""
+    r = uniform(seed, 3 * n_pyramids, 0.8, 1.2).reshape(n_pyramids, 3)
+    x = np.zeros((n_pyramids, 3, 2))
+    for k in range(n_pyramids):
+        r1, r2, r3 = r[k]
+        c1 = np.array([k * spacing + r1, r1])
+        c2 = np.array([c1[0] + r1 + r2 + base_gap, r2])
+        # the top centre: distance r1 + r3 from c1 and r2 + r3 from c2, above them
+        a, b = r1 + r3, r2 + r3
+        d = float(np.linalg.norm(c2 - c1))
+        along = (a * a - b * b + d * d) / (2.0 * d)
+        h = math.sqrt(a * a - along * along)
+        e = (c2 - c1) / d
+        c3 = c1 + along * e + h * np.array([-e[1], e[0]])
+        x[k] = [c1, c2, c3]
+    L = n_pyramids * spacing
+    top = float(np.max(x[:, :, 1] + r))
+    wv = np.zeros((6, 3))
+    wv[2, 0] = floor_speed
+    return _finish("sliding_pyramids_2d", 2, x.reshape(-1, 2), r.reshape(-1), mu=mu, gravity=(0.0, -1.0, 0.0),
+                   box_lo=(0.0, 0.0, 0.0), box_hi=(L, top + 10.0, 1.0), periodic=(1, 0, 0), wall_mask=0b0100,
+                   wall_pos=np.zeros(6), wall_vel=wv, steps=steps, seed=seed)
+
+
 def batch_sizes(seed=1108, n_packings=512, nmin=200, nmax=20000) -> np.ndarray:
     """Disc counts log-uniform in [nmin, nmax] per packing."""
     u = uniform(seed, n_packings, 0.0, 1.0, stream=3)
@@ -320,14 +354,24 @@ def settled_pile(seed, n, phi=0.5, mu=0.3, steps=100):
                    steps=steps, seed=seed)
 
 
-def batched_settling(seed=1108, n_packings=512, nmin=200, nmax=20000, steps=100):
+def shard_range(n_items, rank, world):
+    """The contiguous index range [lo, hi) of the items rank `rank` of
+    `world` takes: the ranks' ranges are disjoint, in rank order, and cover
+    all items (sizes differ by at most one)."""
+    return (n_items * rank) // world, (n_items * (rank + 1)) // world
+
+
+def batched_settling(seed=1108, n_packings=512, nmin=200, nmax=20000, steps=100, shard=None):
     """Independent packings: disc counts log-uniform in [nmin, nmax], mu ~
     U[0.1, 0.6] each, every packing settled under gravity in its box sized
-    to packing fraction 0.5 (see settled_pile)."""
+    to packing fraction 0.5 (see settled_pile).  Packing b depends only on
+    (seed, b), so `shard = (rank, world)` builds just that rank's packings
+    (shard_range): the same ones a single process builds at those indices."""
     sizes = batch_sizes(seed, n_packings, nmin, nmax)
     mus = uniform(seed, n_packings, 0.1, 0.6, stream=4)
     out = []
-    for b in range(n_packings):
+    lo, hi = (0, n_packings) if shard is None else shard_range(n_packings, shard[0], shard[1])
+    for b in range(lo, hi):
         w = settled_pile(seed=_seed(seed, 100 + b) & 0xFFFFFFFF, n=int(sizes[b]), phi=0.5, mu=float(mus[b]),
                          steps=steps)
         w.name = "batched_settling_2d"

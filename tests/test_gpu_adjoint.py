@@ -115,6 +115,18 @@ def test_gpu_floor_force_closed_form():
     assert abs(gmu) <= 1e-12 * m
 
 
+def test_gpu_adjoint_sliding_pyramids_matches_the_oracle():
+    """Six pyramids on the sideways-moving floor, 200 steps, a loss on the
+    final state and on the last step's wall forces: the GPU's reverse pass
+    equals the oracle's complex-step derivative on 32 directions of (x0, v0,
+    omega0, mu), contact states equal step by step, and sliding contacts are
+    present in every step."""
+    from paper_1104_3516_gb300 import workloads as W
+    wl = W.sliding_pyramids(n_pyramids=6)
+    stats, recs = check_parity(wl, 200, wall_weights=[0.0, 0.0, 1.0, 0.0, 0.0, 0.0], xscale=1e-3)
+    assert all(s["n_slide"] >= 6 for s in stats)
+
+
 def test_gpu_adjoint_periodic_gas():
     wl = periodic_gas(n=100, phi=0.62, vsig=3.0, dt=0.02)
     check_parity(wl, 6)
@@ -297,6 +309,97 @@ def test_gpu_adjoint_settling_10k_against_finite_differences():
         assert abs(fd - d) <= 1e-5 * scale, (fd, d)
     print(f"settling 10k: {smooth} smooth directions agree, {kinked} kinked")
     assert smooth >= 16
+
+
+def test_gpu_adjoint_sliding_pyramids_10k_against_finite_differences(record_property):
+    """A friction-dominated rollout at full size: 3,334 pyramids of three
+    discs (10,002 discs) on a floor moving sideways under them, 200 steps,
+    checkpoints every 20.  The base discs slide on the floor throughout, so
+    the packing height H and the floor pressure F of the last step both
+    depend on mu.  Every rollout sweeps 150 times per step (a step converges
+    to 1e-13 in ~40, and a test on the mean impulse of 3,334 independent
+    pyramids would stop at a different sweep in each perturbed run).
+
+    dH/d(v0, mu) from autograd is checked by central differences D(h) of the
+    GPU's own rollout on the pure-mu direction and 16 seeded directions, at
+    h = 1e-4 (H carries ~3e-12 of rounding noise, ~1e-8 in D(h) there): to
+    1e-5 of max(|d|, |D|).  A direction has a kink within +-h, and is
+    reported, not compared, if a perturbed rollout ends in other contact
+    states than the unperturbed one, if another disc is the highest (H is a
+    maximum), or if D(h) and D(h / 2) differ by more than 1e-5.  A random
+    perturbation of all 20,004 initial velocities by 1e-4 moves some contact
+    of some pyramid across a switch in most directions (the detector counts
+    any pyramid, not only the highest one, which alone sets H), so the test
+    asks for the pure-mu direction and at least four more smooth ones.
+
+    F carries ~4e-9 of rounding noise from the trajectory (measured on this
+    rollout: residuals of a cubic fit over mu +- 4e-4), and its nearest kink
+    lies at mu + 4e-4, so its difference quotient cannot resolve 1e-5: dF/dmu
+    is held to 1e-4 (central differences at 1e-4 and 2e-4, Richardson-
+    extrapolated, R = (4 D(h) - D(2 h)) / 3), and to 1e-9 against the
+    oracle's complex-step derivative on six pyramids (test above)."""
+    import torch
+    from paper_1104_3516_gb300 import autodiff, cd, workloads as W
+    wl = W.sliding_pyramids(n_pyramids=3334)
+    steps, every, h = 200, 20, 1e-4
+    width = float(wl.box_hi[0] - wl.box_lo[0])
+    kw = dict(criterion=cd.CD_CONV_NONE, max_sweeps=150)
+
+    def run(v0, mu):
+        """(F, H, contact states at the end, highest disc) of a rollout from (v0, mu)."""
+        w2 = copy.copy(wl)
+        w2.v, w2.mu = v0, mu
+        g = cd.CDSystem(w2, device="cuda:0", **kw)
+        st = g.step(steps)
+        y = g.state()["x"][:, 1]
+        c = g.contacts()
+        pn, pt = c["impulse"][:, 0], np.abs(c["impulse"][:, 1])
+        state = np.where(pn <= 0, 0, np.where(pt >= (1 - 1e-12) * mu * pn, 2, 1))
+        return (st["last"]["wall_force"][2] / width, float(np.max(y + wl.r)), (c["pairs"], state),
+                int(np.argmax(y + wl.r)))
+
+    g = cd.CDSystem(wl, device="cuda:0", tape_steps=every, **kw)
+    dd = dict(dtype=torch.float64, device="cuda:0")
+    x0 = torch.as_tensor(wl.x, **dd)
+    v0 = torch.as_tensor(wl.v, **dd).requires_grad_()
+    w0 = torch.as_tensor(wl.w, **dd)
+    mu = torch.tensor(wl.mu, dtype=torch.float64, requires_grad=True)
+    xT, vT, wT, FT = autodiff.rollout(g, x0, v0, w0, mu, steps, checkpoint_every=every, alpha=1e-13,
+                                      max_sweeps=200000)
+    r = torch.as_tensor(wl.r, **dd)
+    H = torch.max(xT[:, 1] + r)
+    F = FT[2] / width
+    gv_H, gmu_H = torch.autograd.grad(H, [v0, mu], retain_graph=True)
+    gmu_F, = torch.autograd.grad(F, [mu])
+    gv_H, gmu_H, gmu_F = gv_H.cpu().numpy(), float(gmu_H), float(gmu_F)
+    F0, H0, s0, top0 = run(wl.v, wl.mu)
+    assert abs(F0 - float(F)) <= 1e-12 * abs(F0) and abs(H0 - float(H)) <= 1e-12 * abs(H0)
+    assert abs(gmu_H) > 1e-3 and abs(gmu_F) > 0.1       # friction matters for both losses
+    rng = np.random.default_rng(2025)
+    dirs = [(np.zeros_like(wl.v), 1.0)] + [(rng.standard_normal(wl.v.shape), float(rng.standard_normal()))
+                                           for _ in range(16)]
+    smooth, kinked = 0, 0
+    for i, (ev, em) in enumerate(dirs):
+        out = {hh: (run(wl.v + hh * ev, wl.mu + hh * em), run(wl.v - hh * ev, wl.mu - hh * em))
+               for hh in (h, h / 2)}
+        same = all(np.array_equal(o[2][0], s0[0]) and np.array_equal(o[2][1], s0[1]) and o[3] == top0
+                   for p in out.values() for o in p)
+        DH = [(out[hh][0][1] - out[hh][1][1]) / (2 * hh) for hh in (h, h / 2)]
+        d = float(np.sum(gv_H * ev) + gmu_H * em)
+        if not same or abs(DH[0] - DH[1]) > 1e-5 * max(abs(d), abs(DH[0])):
+            kinked += 1
+            assert i > 0, ("the pure-mu direction has a kink", DH, d)
+            continue
+        smooth += 1
+        assert abs(DH[0] - d) <= 1e-5 * max(abs(d), abs(DH[0])), (i, DH, d)
+    hF = 1e-4
+    DF = [(run(wl.v, wl.mu + hh)[0] - run(wl.v, wl.mu - hh)[0]) / (2 * hh) for hh in (hF, 2 * hF)]
+    RF = (4 * DF[0] - DF[1]) / 3
+    record_property("dF_dmu", {"autograd": gmu_F, "richardson": RF, "central": DF})
+    assert abs(RF - gmu_F) <= 1e-4 * abs(gmu_F), (DF, RF, gmu_F)
+    print(f"sliding pyramids 10k: dH/dmu = {gmu_H:.6g}, dF/dmu = {gmu_F:.6g}; {smooth} smooth directions agree, "
+          f"{kinked} kinked")
+    assert smooth >= 5
 
 
 def test_gpu_adjoint_compliance():

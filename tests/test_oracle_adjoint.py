@@ -268,3 +268,27 @@ def wall_force(sys, k):
     """Force on wall k in the oracle's last step, from its own impulses."""
     pairs, P = sys.contacts, sys.impulses
     return float(sum(P[c, 0] for c in range(len(pairs)) if pairs[c, 1] == sys.n + k) / sys.p.dt)
+
+
+def test_sliding_pyramids_mu_derivative_matches_finite_differences():
+    """Pyramids of three discs on a floor sliding sideways under them, 200
+    steps: the complex-step derivative of the last step's floor force with
+    respect to mu against central differences of the oracle's iteration.  The
+    floor impulses carry rounding noise of ~1e-10 (gap / dt terms), so the
+    step is 1e-4 (noise / h and truncation both near 1e-6 relative); the
+    derivative is far from zero (friction drives the pyramids)."""
+    from paper_1104_3516_gb300 import workloads as W
+    wl = W.sliding_pyramids(n_pyramids=3)
+    s, recs = rollout(wl, 200)
+    cs = A.consts_of(s)
+    zero = (np.zeros_like(wl.x), np.zeros_like(wl.v), np.zeros_like(wl.w))
+    cF = np.array([0.0, 0.0, 1.0, 0.0, 0.0, 0.0])
+    e_mu = (np.zeros_like(wl.x), np.zeros_like(wl.v), np.zeros_like(wl.w), 1.0)
+    d = float(A.directional_derivatives(cs, recs, wl.x, wl.v, wl.w, wl.mu, zero, [e_mu], wall_weights=cF)[0])
+    h = 1e-4
+    sp, rp = rollout(wl, 200, mu=wl.mu + h)
+    sm, rm = rollout(wl, 200, mu=wl.mu - h)
+    assert same_states(recs, rp) and same_states(recs, rm)
+    fd = (wall_force(sp, 2) - wall_force(sm, 2)) / (2 * h)
+    assert abs(d) > 1.0
+    assert abs(fd - d) <= 1e-5 * abs(d), (fd, d)
