@@ -117,6 +117,7 @@ static size_t layout(cd_system* s, char* base, CdWork* w)
     t.pcnt = L.take<int>(base, n + 1);
     t.poff = L.take<int>(base, n + 1);
     t.cand = L.take<int>(base, n * CD_CAND);
+    t.pf = L.take<float4>(base, n);
     t.scan_tmp = L.take<int>(base, cd_scan_tmp_ints((int)scan_max) + 32);
     t.pairs = L.take<int2>(base, cap);
     t.pairs_nx = L.take<int2>(base, cap);

@@ -10,6 +10,8 @@
 // The pair test uses the same FP64 operation sequence as the CPU oracle
 // (explicit round-to-nearest intrinsics, no FMA contraction) so the contact
 // set is bit-identical to brute force.
+#include <climits>
+
 #include "cd_internal.cuh"
 
 // ---------------------------------------------------------------------------
@@ -163,13 +165,18 @@ __device__ __forceinline__ int cell_axis(const GridV& v, int k, double x)
 }
 
 template <int DIM>
-__global__ void k_cell_count(CdGeom g, CdWork w, const double* __restrict__ pos, int* __restrict__ cell_of,
-                             int* __restrict__ cell_cnt, const CdCtrl* ctrl)
+__global__ void k_cell_count(CdGeom g, CdWork w, const double* __restrict__ pos, const double* __restrict__ radius,
+                             int* __restrict__ cell_of, int* __restrict__ cell_cnt, const CdCtrl* ctrl)
 {
     if (ctrl->skip) return;
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < g.n; i += gridDim.x * blockDim.x) {
         GridV v;
         grid_of(g, w, i, v);
+        if (w.pf) {
+            // single-precision copy of (x, y, z, r) for the pair pre-filter
+            w.pf[i] = make_float4((float)pos[i * DIM + 0], (float)pos[i * DIM + 1],
+                                  DIM == 3 ? (float)pos[i * DIM + 2] : 0.0f, (float)radius[i]);
+        }
         int c0 = cell_axis(v, 0, pos[i * DIM + 0]);
         int c1 = cell_axis(v, 1, pos[i * DIM + 1]);
         int c2 = (DIM == 3) ? cell_axis(v, 2, pos[i * DIM + 2]) : 0;
@@ -236,6 +243,42 @@ __device__ __forceinline__ bool pair_touches(const GridV& v, double delta, const
     return d2 < __dmul_rn(s, s);
 }
 
+// Single-precision pre-filter of the pair test: true only if the pair is
+// certainly not a contact, so that the exact FP64 test above (which alone
+// decides) runs only for the candidates that may be.  Each coordinate
+// rounded to float is within 2^-24 |x| of the double, so the float
+// separation of an axis is within e_k = 2^-23 (|x_a| + |x_b| (+ L on a
+// periodic axis)) of the exact one (a factor two over the rounding of the
+// conversions, the subtraction and the image shift), and the distance
+// within E = sum_k e_k.  A contact has |d| < s, hence a float distance
+// below s + E; the relative roundings of d2, of s and of the threshold
+// itself are covered by the factors 1 + 2^-20.  An image chosen differently
+// near |d| = L/2 changes nothing: a periodic axis spans at least three cells,
+// so both images are farther apart than any contact distance.
+template <int DIM>
+__device__ __forceinline__ bool pair_far_f32(const GridV& v, const float (&Lf)[3], float delta_f, const float4& pa,
+                                             const float4& pb)
+{
+    const float xa[3] = {pa.x, pa.y, pa.z}, xb[3] = {pb.x, pb.y, pb.z};
+    float d2 = 0.0f, E = 0.0f;
+#pragma unroll
+    for (int k = 0; k < DIM; ++k) {
+        float d = xb[k] - xa[k];
+        float m = fabsf(xa[k]) + fabsf(xb[k]);
+        if (v.periodic[k]) {
+            const float half = 0.5f * Lf[k];
+            if (d > half) d -= Lf[k];
+            else if (d < -half) d += Lf[k];
+            m += Lf[k];
+        }
+        d2 = fmaf(d, d, d2);
+        E = fmaf(m, 1.1920929e-7f, E);   // 2^-23
+    }
+    const float s = pa.w + pb.w + delta_f;
+    const float t = fmaf(s, 1.0f + 9.5367432e-7f, E) * (1.0f + 9.5367432e-7f);   // 1 + 2^-20
+    return d2 > t * t;
+}
+
 __device__ __forceinline__ double wall_gap(const double* xa, double ra, const double* wall_pos, int k)
 {
     int axis = k >> 1;
@@ -251,64 +294,109 @@ __device__ __forceinline__ bool wall_on(const GridV& v, int dim, int k)
 // Visits the candidate partners b > a of particle a in the 3^DIM cells around
 // it (in a's packing grid); calls f(b) for each b that passes the pair test.
 // Needs each cell's list sorted by id (k_cell_sort).
-// The cell ranges are gathered first (independent loads) and the candidates
-// are then walked as one flat sequence, so the lanes of a warp loop about as
-// many times as their total candidate counts, not the per-cell maxima.
+//
+// The three cells x-1, x, x+1 of one row of the stencil are consecutive cell
+// ids, so their particles are one run of cell_pid: 3^(DIM-1) runs (a periodic
+// x axis that wraps adds the wrapped cell as a run of its own).  A cell whose
+// last id is not above a holds no partner: such cells are trimmed off the
+// left end of a run, and a run none of whose cells passes is dropped (ids
+// follow the packing's rows, so that is most runs below a's row).  The
+// candidates of the runs are then walked as one flat sequence, so the lanes
+// of a warp loop about as many times as their own candidate counts.  The
+// runs' bounds live in registers (RUNS fixed, the loops unrolled, the next
+// run picked by comparisons against compile-time indices): an array of cell
+// ranges indexed in a loop went to local memory and dominated the kernel's
+// memory traffic.
+template <int DIM>
+struct Runs {
+    static constexpr int N = (DIM == 3) ? 18 : 6;   // 3^(DIM-1) rows, each with a possible wrapped cell
+    int lo[N], hi[N];
+};
+
+__device__ __forceinline__ int last_id(const int* __restrict__ cell_start, const int* __restrict__ cell_pid, int cc)
+{
+    const int l = cell_start[cc], h = cell_start[cc + 1];
+    return (h > l) ? cell_pid[h - 1] : -1;
+}
+
 template <int DIM, typename F>
 __device__ __forceinline__ void for_each_partner(const CdGeom& g, const GridV& v, int a, const double* xa, double ra,
                                                  const double* __restrict__ pos, const double* __restrict__ radius,
                                                  const int* __restrict__ cell_of, const int* __restrict__ cell_start,
-                                                 const int* __restrict__ cell_pid, F f)
+                                                 const int* __restrict__ cell_pid, const float4* __restrict__ pf, F f)
 {
-    constexpr int NC = (DIM == 3) ? 27 : 9;
-    int lo[NC], hi[NC];
-    int m = 0;
-    int c = cell_of[a] - v.base;
-    int q0 = c % v.ncell[0];
-    int q1 = (c / v.ncell[0]) % v.ncell[1];
-    int q2 = c / (v.ncell[0] * v.ncell[1]);
-    const int zlo = (DIM == 3) ? -1 : 0, zhi = (DIM == 3) ? 1 : 0;
-    for (int dz = zlo; dz <= zhi; ++dz) {
-        int t2 = q2 + dz;
-        if (DIM == 3) {
-            if (t2 < 0 || t2 >= v.ncell[2]) {
+    const int c = cell_of[a] - v.base;
+    const int n0 = v.ncell[0], n1 = v.ncell[1];
+    const int q0 = c % n0;
+    const int q1 = (c / n0) % n1;
+    const int q2 = c / (n0 * n1);
+    const int x0 = (q0 > 0) ? q0 - 1 : 0, x1 = (q0 < n0 - 1) ? q0 + 1 : n0 - 1;
+    int xw = -1;   // a periodic x axis: the wrapped neighbour cell outside [x0, x1]
+    if (v.periodic[0] && n0 >= 3) {
+        if (q0 == 0) xw = n0 - 1;
+        else if (q0 == n0 - 1) xw = 0;
+    }
+    Runs<DIM> R;
+    constexpr int ZN = (DIM == 3) ? 3 : 1;
+#pragma unroll
+    for (int iz = 0; iz < ZN; ++iz) {
+#pragma unroll
+        for (int iy = 0; iy < 3; ++iy) {
+            const int r = 2 * (iz * 3 + iy);
+            R.lo[r] = R.hi[r] = 0;
+            R.lo[r + 1] = R.hi[r + 1] = 0;
+            int t2 = (DIM == 3) ? q2 + iz - 1 : 0;
+            if (DIM == 3 && (t2 < 0 || t2 >= v.ncell[2])) {
                 if (!v.periodic[2]) continue;
                 t2 = (t2 + v.ncell[2]) % v.ncell[2];
             }
-        }
-        for (int dy = -1; dy <= 1; ++dy) {
-            int t1 = q1 + dy;
-            if (t1 < 0 || t1 >= v.ncell[1]) {
+            int t1 = q1 + iy - 1;
+            if (t1 < 0 || t1 >= n1) {
                 if (!v.periodic[1]) continue;
-                t1 = (t1 + v.ncell[1]) % v.ncell[1];
+                t1 = (t1 + n1) % n1;
             }
-            for (int dx = -1; dx <= 1; ++dx) {
-                int t0 = q0 + dx;
-                if (t0 < 0 || t0 >= v.ncell[0]) {
-                    if (!v.periodic[0]) continue;
-                    t0 = (t0 + v.ncell[0]) % v.ncell[0];
-                }
-                const int cc = v.base + (t2 * v.ncell[1] + t1) * v.ncell[0] + t0;
-                const int l = cell_start[cc], h = cell_start[cc + 1];
-                // ids ascend within a cell: a cell whose last id is <= a has no partner b > a
-                if (h > l && cell_pid[h - 1] > a) {
-                    lo[m] = l;
-                    hi[m] = h;
-                    ++m;
-                }
+            const int row = v.base + (t2 * n1 + t1) * n0;
+            // the run's cells x0 .. x1 (one to three): their bounds, then their last
+            // ids (independent loads); the run starts at its first cell with an id above a
+            const int nx = x1 - x0 + 1;
+            const int cs0 = cell_start[row + x0];
+            const int cs1 = (nx > 1) ? cell_start[row + x0 + 1] : 0;
+            const int cs2 = (nx > 2) ? cell_start[row + x0 + 2] : 0;
+            const int cs3 = cell_start[row + x1 + 1];
+            const int e0 = (nx > 1) ? cs1 : cs3, e1 = (nx > 2) ? cs2 : cs3;
+            const int L0 = (e0 > cs0) ? cell_pid[e0 - 1] : -1;
+            const int L1 = (nx > 1 && e1 > cs1) ? cell_pid[e1 - 1] : -1;
+            const int L2 = (nx > 2 && cs3 > cs2) ? cell_pid[cs3 - 1] : -1;
+            const int start = (L0 > a) ? cs0 : (L1 > a) ? cs1 : (L2 > a) ? cs2 : -1;
+            if (start >= 0) {
+                R.lo[r] = start;
+                R.hi[r] = cs3;
+            }
+            if (xw >= 0 && last_id(cell_start, cell_pid, row + xw) > a) {
+                R.lo[r + 1] = cell_start[row + xw];
+                R.hi[r + 1] = cell_start[row + xw + 1];
             }
         }
     }
-    int j = 0;
-    int s = (m > 0) ? lo[0] : 0;
+    // the pre-filter's data (pf null: the exact test only)
+    float4 pa = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+    float Lf[3] = {(float)v.L[0], (float)v.L[1], (float)v.L[2]};
+    const float delta_f = (float)g.delta;
+    if (pf) pa = pf[a];
+    // flat walk over the runs
+    int j = 0, s = R.lo[0], e = R.hi[0];
     for (;;) {
-        while (j < m && s >= hi[j]) {
-            ++j;
-            if (j < m) s = lo[j];
+        while (s >= e) {
+            if (++j >= Runs<DIM>::N) break;
+#pragma unroll
+            for (int k = 1; k < Runs<DIM>::N; ++k)
+                if (k == j) { s = R.lo[k]; e = R.hi[k]; }
         }
-        if (j >= m) break;
+        if (j >= Runs<DIM>::N) break;
         const int b = cell_pid[s++];
-        if (b > a && pair_touches<DIM>(v, g.delta, xa, ra, pos, radius, b)) f(b);
+        if (b > a && !(pf && pair_far_f32<DIM>(v, Lf, delta_f, pa, pf[b])) &&
+            pair_touches<DIM>(v, g.delta, xa, ra, pos, radius, b))
+            f(b);
     }
 }
 
@@ -328,7 +416,7 @@ __global__ void k_pair_count(CdGeom g, CdWork w, const double* __restrict__ pos,
         double ra = radius[a];
         int cnt = 0;
         int* keep = w.cand ? w.cand + (size_t)a * CD_CAND : nullptr;
-        for_each_partner<DIM>(g, v, a, xa, ra, pos, radius, cell_of, cell_start, cell_pid, [&](int b) {
+        for_each_partner<DIM>(g, v, a, xa, ra, pos, radius, cell_of, cell_start, cell_pid, w.pf, [&](int b) {
             if (keep && cnt < CD_CAND) keep[cnt] = b;   // the emitting pass reuses them instead of walking again
             ++cnt;
         });
@@ -431,31 +519,44 @@ __global__ void k_pair_emit(CdGeom g, CdWork w, const double* __restrict__ pos, 
 #pragma unroll
         for (int k = 0; k < DIM; ++k) xa[k] = pos[a * DIM + k];
         double ra = radius[a];
-        int found[CD_MAXLOC];
-        int nf = 0;
-        auto insert = [&](int b) {
-            if (nf < CD_MAXLOC) {
-                // insertion into the sorted prefix
-                int j = nf++;
-                while (j > 0 && found[j - 1] > b) { found[j] = found[j - 1]; --j; }
-                found[j] = b;
-            }
-        };
         int nw = 0;
         for (int k = 0; k < 2 * DIM; ++k)
             if (wall_on(v, DIM, k) && wall_gap(xa, ra, wp, k) < g.delta) ++nw;
         const int npart = w.pcnt[a] - nw;   // partners the counting pass found
-        if (w.cand && npart <= CD_CAND) {
-            const int* keep = w.cand + (size_t)a * CD_CAND;
-            for (int f = 0; f < npart; ++f) insert(keep[f]);
-        } else {
-            for_each_partner<DIM>(g, v, a, xa, ra, pos, radius, w.cell_of, w.cell_start, w.cell_pid, insert);
-        }
         int o = w.poff[a];
-        for (int f = 0; f < nf; ++f) {
-            double nv[3], gap, mn, mt;
-            contact_geometry<DIM>(g, w, a, found[f], pos, radius, inv_m, inv_I, nv, &gap, &mn, &mt);
-            store_geometry<DIM>(w, o++, a, found[f], nv, gap, mn, mt);
+        if (w.cand && npart <= CD_CAND) {
+            // the counting pass kept them (in walk order): emit in ascending id by
+            // repeated selection of the smallest one above the last emitted
+            const int* keep = w.cand + (size_t)a * CD_CAND;
+            int last = a;
+            for (int f = 0; f < npart; ++f) {
+                int bmin = INT_MAX;
+                for (int q = 0; q < npart; ++q) {
+                    const int bq = keep[q];
+                    if (bq > last && bq < bmin) bmin = bq;
+                }
+                double nv[3], gap, mn, mt;
+                contact_geometry<DIM>(g, w, a, bmin, pos, radius, inv_m, inv_I, nv, &gap, &mn, &mt);
+                store_geometry<DIM>(w, o++, a, bmin, nv, gap, mn, mt);
+                last = bmin;
+            }
+        } else {
+            int found[CD_MAXLOC];
+            int nf = 0;
+            auto insert = [&](int b) {
+                if (nf < CD_MAXLOC) {
+                    // insertion into the sorted prefix
+                    int j = nf++;
+                    while (j > 0 && found[j - 1] > b) { found[j] = found[j - 1]; --j; }
+                    found[j] = b;
+                }
+            };
+            for_each_partner<DIM>(g, v, a, xa, ra, pos, radius, w.cell_of, w.cell_start, w.cell_pid, w.pf, insert);
+            for (int f = 0; f < nf; ++f) {
+                double nv[3], gap, mn, mt;
+                contact_geometry<DIM>(g, w, a, found[f], pos, radius, inv_m, inv_I, nv, &gap, &mn, &mt);
+                store_geometry<DIM>(w, o++, a, found[f], nv, gap, mn, mt);
+            }
         }
         for (int k = 0; k < 2 * DIM; ++k) {
             if (wall_on(v, DIM, k) && wall_gap(xa, ra, wp, k) < g.delta) {
@@ -570,8 +671,8 @@ cudaError_t cd_launch_detect(const CdGeom& g, const CdWork& w, const double* pos
     if ((e = cudaMemsetAsync(w.cell_cnt, 0, sizeof(int) * (size_t)(ncell + 1), s)) != cudaSuccess) return e;
     if ((e = cudaMemsetAsync(w.cell_fill, 0, sizeof(int) * (size_t)ncell, s)) != cudaSuccess) return e;
     int gb = grid_for(g.n);
-    if (g.dim == 2) k_cell_count<2><<<gb, CD_BLOCK, 0, s>>>(g, w, pos, w.cell_of, w.cell_cnt, w.ctrl);
-    else k_cell_count<3><<<gb, CD_BLOCK, 0, s>>>(g, w, pos, w.cell_of, w.cell_cnt, w.ctrl);
+    if (g.dim == 2) k_cell_count<2><<<gb, CD_BLOCK, 0, s>>>(g, w, pos, radius, w.cell_of, w.cell_cnt, w.ctrl);
+    else k_cell_count<3><<<gb, CD_BLOCK, 0, s>>>(g, w, pos, radius, w.cell_of, w.cell_cnt, w.ctrl);
     ++*nl;
     if ((e = cd_scan_exclusive(w.cell_cnt, w.cell_start, ncell + 1, w.scan_tmp, nullptr, s, nl)) != cudaSuccess) return e;
     k_cell_fill<<<gb, CD_BLOCK, 0, s>>>(g.n, w.cell_of, w.cell_start, w.cell_fill, w.cell_pid, w.ctrl); ++*nl;

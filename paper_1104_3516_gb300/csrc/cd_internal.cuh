@@ -94,6 +94,7 @@ struct CdWork {
     int* cell_pid;      // n
     int* pcnt;          // n + 1
     int* cand;          // n * CD_CAND: partners b > a found by the counting pass (first CD_CAND, found order)
+    float4* pf;         // n: (x, y, z, r) in single precision for the pair pre-filter (null: exact test only)
     int* poff;          // n + 1
     int* scan_tmp;      // block sums of the scans
     // contacts, key order
