@@ -339,8 +339,10 @@ cd_status cd_download_state(cd_system* sys, double* pos_host, double* vel_host, 
  * Inputs (device): pos, radius, inv_mass, inv_inertia as in
  * cd_create_system; params as there (wall planes from params->wall_pos).
  * Outputs (device, caller-owned): pairs max_contacts*2 int32, normal
- * max_contacts*3 doubles, gap max_contacts doubles; *n_contacts (host) the
- * number found.  Work is enqueued on cuda_stream and the call synchronises it.
+ * max_contacts*3 doubles, gap max_contacts doubles (may be NULL when
+ * max_contacts is 0: a size query); *n_contacts (host) the number found.
+ * Work is enqueued on cuda_stream, and every call synchronises that stream
+ * (it reads the largest radius and the contact count back to the host).
  *
  * Scratch lives in a fixed device array of about 4.1 MB inside the library,
  * held by every GPU that loads it until the process exits; limits: n <= 16384
@@ -350,7 +352,9 @@ cd_status cd_download_state(cd_system* sys, double* pos_host, double* vel_host, 
  * CD_ERR_CAPACITY with the number needed in *n_contacts and nothing written
  * past max_contacts.  The first call on each device looks up the array's
  * device address (cudaGetSymbolAddress) with that device current, so make
- * that first call before any stream capture.  All calls share the array:
+ * that first call before any stream capture; the address is then kept for
+ * the life of the process, so the entry point must not be used on a device
+ * after a cudaDeviceReset of it.  All calls share the array:
  * each call clears what must start at zero, and calls that overlap on the
  * GPU (different streams or threads) race with each other. */
 cd_status cd_detect_contacts_noalloc(const cd_params* params, int64_t n, const double* pos, const double* radius,

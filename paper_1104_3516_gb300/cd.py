@@ -309,13 +309,35 @@ def cd_download_state(sysptr, pos_host, vel_host, omega_host):
 
 def cd_detect_contacts_noalloc(params: cd_params, n, pos, radius, inv_mass, inv_inertia, max_contacts, pairs,
                                normal, gap, stream) -> int:
-    """Detection without a system or workspace (library-held scratch; see cd_api.h)."""
+    """Detection without a system or workspace (library-held scratch; see
+    cd_api.h).  Checks the tensors first (dtype, contiguity, device, room for
+    max_contacts rows: the kernels write through the raw pointers).  On
+    CD_ERR_CAPACITY the raised CDError carries the number of contacts needed
+    in its `needed` attribute, so a caller can resize and call again."""
+    dim = int(params.dim)
+    need = [(pos, torch.float64, n * dim, "pos"), (radius, torch.float64, n, "radius"),
+            (inv_mass, torch.float64, n, "inv_mass"), (inv_inertia, torch.float64, n, "inv_inertia")]
+    if max_contacts > 0 or pairs is not None:
+        need += [(pairs, torch.int32, 2 * max_contacts, "pairs"), (normal, torch.float64, 3 * max_contacts, "normal"),
+                 (gap, torch.float64, max_contacts, "gap")]
+    for t, dt, cnt, name in need:
+        if t is None:
+            raise ValueError(f"{name} is required")
+        if t.dtype != dt or not t.is_contiguous() or t.device != pos.device or t.device.type != "cuda":
+            raise ValueError(f"{name} must be a contiguous {dt} tensor on {pos.device}")
+        if t.numel() < cnt:
+            raise ValueError(f"{name} holds {t.numel()} elements, {cnt} needed")
     nc = C.c_int64()
     ptr = lambda t: None if t is None else t.data_ptr()
     st = lib().cd_detect_contacts_noalloc(C.byref(params), int(n), ptr(pos), ptr(radius), ptr(inv_mass),
                                           ptr(inv_inertia), int(max_contacts), ptr(pairs), ptr(normal), ptr(gap),
                                           C.byref(nc), stream)
-    _check(None, st)
+    try:
+        _check(None, st)
+    except CDError as e:
+        if e.status == CD_ERR_CAPACITY:
+            e.needed = int(nc.value)
+        raise
     return int(nc.value)
 
 

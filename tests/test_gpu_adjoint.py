@@ -292,7 +292,7 @@ def test_gpu_adjoint_settling_10k_against_finite_differences():
     L.backward()
     gv, gmu = v0.grad.cpu().numpy(), float(mu.grad)
     L0 = loss_of(wl.v, wl.mu)
-    assert abs(L0 - float(L)) <= 1e-12 * abs(L0)
+    assert abs(L0 - float(L.detach())) <= 1e-12 * abs(L0)
     rng = np.random.default_rng(2024)
     smooth, kinked = 0, 0
     for _ in range(32):

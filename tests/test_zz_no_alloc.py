@@ -16,7 +16,9 @@ from paper_1104_3516_gb300 import workloads as W
 pytestmark = [pytest.mark.gpu, needs_gpu]
 
 
-def _noalloc(wl, max_contacts):
+def _noalloc(wl, max_contacts, buffers=None, outputs=True):
+    """One call on the workload; `buffers` (pairs, normal, gap) lets a test
+    keep the output tensors, `outputs=False` passes none (size query)."""
     import torch
     from paper_1104_3516_gb300 import cd
     dev = torch.device("cuda:0")
@@ -25,17 +27,28 @@ def _noalloc(wl, max_contacts):
     rad = torch.as_tensor(wl.r, **dd)
     im = torch.as_tensor(wl.inv_m, **dd)
     iI = torch.as_tensor(wl.inv_I, **dd)
-    pairs = torch.full((max_contacts, 2), -1, dtype=torch.int32, device=dev)
-    normal = torch.zeros((max_contacts, 3), **dd)
-    gap = torch.zeros(max_contacts, **dd)
+    if buffers is None:
+        buffers = (torch.full((max_contacts, 2), -1, dtype=torch.int32, device=dev),
+                   torch.zeros((max_contacts, 3), **dd), torch.zeros(max_contacts, **dd))
+    pairs, normal, gap = buffers if outputs else (None, None, None)
     p = cd.make_params(wl)
     nc = cd.cd_detect_contacts_noalloc(p, wl.n, pos, rad, im, iI, max_contacts, pairs, normal, gap,
                                        torch.cuda.current_stream(dev).cuda_stream)
+    if not outputs:
+        return nc
     return pairs[:nc].cpu().numpy(), normal[:nc].cpu().numpy(), gap[:nc].cpu().numpy()
 
 
+def _periodic_gas_3d():
+    """A 3D gas periodic along x and y, with the floor only."""
+    wl = W.sphere_gas(n=3000, floor=20.0, vsig=0.5)
+    wl.periodic = (1, 1, 0)
+    wl.wall_mask = 0b010000
+    return wl
+
+
 def test_noalloc_detection_equals_workspace_detection_on_two_calls_in_a_row():
-    cases = [W.dense_biaxial_discs(n=5000), W.sphere_gas(n=3000, floor=20.0, vsig=0.5)]
+    cases = [W.dense_biaxial_discs(n=5000), W.sphere_gas(n=3000, floor=20.0, vsig=0.5), _periodic_gas_3d()]
     for wl in cases:
         g = gpu_system(wl)
         g.detect_contacts()
@@ -53,9 +66,28 @@ def test_noalloc_limits_are_reported():
     with pytest.raises(cd.CDError) as e:
         _noalloc(wl, 65537)
     assert e.value.status == cd.CD_ERR_INVALID_ARG and "65536" in str(e.value)
+    g = gpu_system(wl)
+    needed = g.detect_contacts()
+    import torch
+    dev = torch.device("cuda:0")
+    bufs = (torch.full((10, 2), -1, dtype=torch.int32, device=dev),
+            torch.zeros((10, 3), dtype=torch.float64, device=dev), torch.zeros(10, dtype=torch.float64, device=dev))
+    big_pairs = torch.full((20, 2), -1, dtype=torch.int32, device=dev)
+    bufs_in_big = (big_pairs[:10], bufs[1], bufs[2])
     with pytest.raises(cd.CDError) as e:
-        _noalloc(wl, 10)
+        _noalloc(wl, 10, buffers=bufs_in_big)
     assert e.value.status == cd.CD_ERR_CAPACITY
+    assert e.value.needed == needed
+    assert torch.all(big_pairs[10:] == -1)        # nothing written past max_contacts
+    # a size query: no outputs, max_contacts 0
+    with pytest.raises(cd.CDError) as e:
+        _noalloc(wl, 0, outputs=False)
+    assert e.value.status == cd.CD_ERR_CAPACITY and e.value.needed == needed
+    # undersized or mistyped outputs are refused before the call
+    with pytest.raises(ValueError):
+        _noalloc(wl, 10, buffers=(bufs[0][:5], bufs[1], bufs[2]))
+    with pytest.raises(ValueError):
+        _noalloc(wl, 10, buffers=(bufs[0].to(torch.int64), bufs[1], bufs[2]))
     big = W.settling_discs(n=16385)
     with pytest.raises(cd.CDError) as e:
         _noalloc(big, 1000)
