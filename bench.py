@@ -98,6 +98,9 @@ def parse():
                     help="timed steps of the 1,000-disc dilute leg (0: skip)")
     ap.add_argument("--converge-cap", type=int, default=100000,
                     help="sweep cap of the untimed steps that measure the sweeps to residual 1e-6 (0: skip)")
+    ap.add_argument("--mixed-scan", type=int, nargs="*", default=None, metavar="N",
+                    help="instead of the benchmark: the iterations N_I the mixed update of Sec. 2.3 needs against "
+                         "its parallel fraction p, both readings of the parallel subset, on loaded piles of N discs")
     ap.add_argument("--cpu-sweeps", type=int, default=30,
                     help="sweep cap of the oracle's bounded sample step")
     return ap.parse_args()
@@ -904,8 +907,42 @@ def run_e2e(args, sysg, wl, device, ws):
             "steps": args.steps, "api": "cd_upload_state + cd_step + cd_download_state"}
 
 
+def run_mixed_scan(args):
+    """Sec. 2.3's protocol on the GPU: a static loaded packing (a
+    gravity-deposited pile of N discs at rest, floor and a fixed lid, mu 0.3)
+    has its forces set to zero and is solved within one time step until the
+    global test passes at 1e-6 (cap 20,000 sweeps), for parallel fractions
+    p from 0 to 1, with the parallel subset fixed per contact key and drawn
+    afresh in every iteration step.  Prints one JSON line: N_I per p (null:
+    not converged, with the largest impulse it reached)."""
+    import torch
+    from paper_1104_3516_gb300 import cd, workloads as W
+    device = torch.device("cuda", 0)
+    ps = [0.0, 0.05, 0.1, 0.2, 0.3, 0.4, 0.5, 0.6, 0.7, 0.8, 1.0]
+    out = {"protocol": "static gravity-loaded pile, forces from zero, one solve, global test 1e-6, cap 20000",
+           "p": ps, "piles": {}}
+    for n in args.mixed_scan or [2000]:
+        wl = W.dense_biaxial_discs(n=n, wall_speed=0.0)
+        res = {}
+        for redraw in (0, 1):
+            row = []
+            for p in ps:
+                g = cd.CDSystem(wl, device=device, criterion=cd.CD_CONV_GLOBAL_REL, alpha=1e-6, max_sweeps=20000,
+                                warm_start=0, parallel_p=p, parallel_redraw=redraw, max_contacts=4 * n)
+                st = g.step(1)["last"]
+                pmax = float(np.nanmax(np.abs(g.contacts()["impulse"])))
+                row.append({"sweeps": st["sweeps"] if st["converged"] else None, "max_impulse": pmax})
+                del g
+            res["redrawn_every_step" if redraw else "fixed_per_contact"] = row
+        out["piles"][str(n)] = res
+    print(json.dumps(out), flush=True)
+
+
 def main():
     args = parse()
+    if args.mixed_scan is not None:
+        run_mixed_scan(args)
+        return
     if args.impl == "reference":
         run_reference(args)
     else:

@@ -159,6 +159,12 @@ typedef struct {
                                contact of capacity.  Plain systems with the
                                colour-barrier schedule, kinematic walls, no
                                mixed update, no tape.  All 1: Gauss-Seidel. */
+    int64_t parallel_redraw; /* mixed update (parallel_p): 0 the parallel subset
+                               is fixed per contact key; 1 it is drawn afresh
+                               in every iteration step (the step's number
+                               mixed into the hash of the key), the way the
+                               paper draws its random sequential order anew
+                               each step (Sec. 2.1) */
     int64_t merge_last_colour; /* colour-barrier schedule of a plain system:
                                1 lets a step run its two last colours in one
                                phase when the last class is small (at most a

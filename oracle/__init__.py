@@ -62,6 +62,7 @@ class Params(C.Structure):
         ("wall_push", C.c_double * 6),
         ("wall_mass", C.c_double * 6),
         ("domains", C.c_int64 * 3),
+        ("parallel_redraw", C.c_int64),
     ]
 
 
@@ -147,7 +148,8 @@ def _f64(a):
 def make_params(dim=2, dt=1e-3, mu=0.3, gravity=(0.0, -1.0, 0.0), box_lo=(0, 0, 0), box_hi=(1, 1, 1),
                 periodic=(0, 0, 0), wall_mask=0, wall_vel=None, delta=0.24, alpha=1e-6,
                 criterion=CRIT_GLOBAL_REL, max_sweeps=1000, order=ORDER_COLOUR, warm_start=1, seed=0,
-                parallel_p=0.0, rotations=1, wall_push=None, wall_mass=None, domains=(1, 1, 1)) -> Params:
+                parallel_p=0.0, rotations=1, wall_push=None, wall_mass=None, domains=(1, 1, 1),
+                parallel_redraw=0) -> Params:
     p = Params()
     p.dim = dim
     p.dt = dt
@@ -169,6 +171,7 @@ def make_params(dim=2, dt=1e-3, mu=0.3, gravity=(0.0, -1.0, 0.0), box_lo=(0, 0, 
     p.warm_start = int(warm_start)
     p.seed = int(seed) & (2**64 - 1)
     p.parallel_p = parallel_p
+    p.parallel_redraw = int(parallel_redraw)
     p.rotations = int(rotations)
     wp = np.zeros(6) if wall_push is None else np.asarray(wall_push, dtype=np.float64).reshape(6)
     wm = np.zeros(6) if wall_mass is None else np.asarray(wall_mass, dtype=np.float64).reshape(6)

@@ -41,7 +41,9 @@
  *   - R_avg is the mean of the impulse magnitudes |P|.
  *   - criterion ORA_CRIT_GLOBAL_REL (default) tests the non-squared relative
  *     change of R_avg against alpha; ORA_CRIT_GLOBAL_SQ is the paper's
- *     squared form (II); ORA_CRIT_LOCAL is test (I).
+ *     squared form (II); ORA_CRIT_LOCAL is test (I).  Both averages zero
+ *     (0/0) counts as converged; a NaN average (a diverged iteration) gives
+ *     a NaN ratio, which never passes.
  *   - warm start: impulses are carried over by contact key from the previous
  *     time step (off: the iteration starts from zero forces).
  *   - domain-wise update: domains are a grid of equal slabs of the box (the
@@ -86,6 +88,9 @@ typedef struct {
     int64_t domains[3];     /* domain-wise update of Sec. 3.1: the box is cut
                                into domains[k] equal slabs along axis k (<= 1:
                                one); 1 x 1 x 1 is plain Gauss-Seidel */
+    int64_t parallel_redraw;/* mixed update: 0 the parallel subset is fixed per
+                               contact key; 1 it is drawn afresh in every
+                               iteration step (see is_parallel) */
 } ora_params;
 
 /* A force-controlled wall: present, with a positive mass. */
@@ -801,13 +806,19 @@ int64_t ora_contact_domains(const ora_params* p, long long n, const double* x, c
     return total;
 }
 
-/* A contact is in the parallel-update set of Sec. 2.3 when a hash of its key
- * falls below p (a fixed subset per contact key). */
-static int is_parallel(const ora_params* p, uint64_t key)
+/* A contact is in the parallel-update set of Sec. 2.3 when a uniform number
+ * drawn for it falls below p.  The draw is splitmix64 of the contact key
+ * mixed with the seed: one fixed subset per contact key (parallel_redraw 0),
+ * or, with the iteration step's number mixed in as well, a fresh subset in
+ * every iteration step (parallel_redraw 1), the way the paper draws its
+ * random sequential order anew each step (Sec. 2.1). */
+static int is_parallel(const ora_params* p, uint64_t key, long long sweep)
 {
     if (p->parallel_p <= 0.0) return 0;
     if (p->parallel_p >= 1.0) return 1;
-    uint64_t h = ora_splitmix64(key ^ (p->seed * 0xD1B54A32D192ED03ULL));
+    uint64_t x = key ^ (p->seed * 0xD1B54A32D192ED03ULL);
+    if (p->parallel_redraw) x ^= (uint64_t)(sweep + 1) * 0x9E3779B97F4A7C15ULL;
+    uint64_t h = ora_splitmix64(x);
     double u = (double)(h >> 11) * (1.0 / 9007199254740992.0);
     return u < p->parallel_p;
 }
@@ -875,7 +886,7 @@ int ora_solve(ora_params* p, long long n, double* v, double* w,
     long long npar = 0;
     for (long long c = 0; c < nc; ++c) {
         /* the domain-wise update replaces the mixed update of Sec. 2.3 */
-        par[c] = domain ? 0 : (char)is_parallel(p, key_of(pairs[2 * c], pairs[2 * c + 1]));
+        par[c] = domain ? 0 : (char)is_parallel(p, key_of(pairs[2 * c], pairs[2 * c + 1]), 0);
         npar += par[c];
     }
     double* Pprev = (double*)malloc(sizeof(double) * (size_t)(nc > 0 ? nc : 1) * (size_t)pw);
@@ -908,6 +919,14 @@ int ora_solve(ora_params* p, long long n, double* v, double* w,
             for (long long i = nc - 1; i > 0; --i) {
                 long long j = (long long)(rng_next(&st_rng) % (uint64_t)(i + 1));
                 long long t = order[i]; order[i] = order[j]; order[j] = t;
+            }
+        }
+        if (p->parallel_redraw && !domain && p->parallel_p > 0.0 && p->parallel_p < 1.0) {
+            /* a fresh parallel subset for this iteration step */
+            npar = 0;
+            for (long long c = 0; c < nc; ++c) {
+                par[c] = (char)is_parallel(p, key_of(pairs[2 * c], pairs[2 * c + 1]), sweep);
+                npar += par[c];
             }
         }
         if (npar > 0) {
@@ -964,10 +983,10 @@ int ora_solve(ora_params* p, long long n, double* v, double* w,
         if (ravg_hist) ravg_hist[sweep] = ravg;
         double den = ravg + ravg_prev;
         if (p->criterion == ORA_CRIT_GLOBAL_REL) {
-            resid = (den > 0.0) ? fabs(ravg - ravg_prev) / den : 0.0;
+            resid = (den > 0.0) ? fabs(ravg - ravg_prev) / den : (den == 0.0 ? 0.0 : den);
             converged = resid < p->alpha;
         } else if (p->criterion == ORA_CRIT_GLOBAL_SQ) {
-            double q = (den > 0.0) ? (ravg - ravg_prev) / den : 0.0;
+            double q = (den > 0.0) ? (ravg - ravg_prev) / den : (den == 0.0 ? 0.0 : den);
             resid = q * q;
             converged = resid < p->alpha;
         } else if (p->criterion == ORA_CRIT_LOCAL) {
@@ -986,7 +1005,7 @@ int ora_solve(ora_params* p, long long n, double* v, double* w,
             resid = (nc > 0) ? (double)(nc - n_rel) / (double)nc : 0.0;
             converged = (10 * n_rel >= 9 * nc) && n_bad == 0;
         } else {
-            resid = (den > 0.0) ? fabs(ravg - ravg_prev) / den : 0.0;
+            resid = (den > 0.0) ? fabs(ravg - ravg_prev) / den : (den == 0.0 ? 0.0 : den);
             converged = 0;
         }
         st->r_avg_prev = ravg_prev;

@@ -506,6 +506,11 @@ static cd_status create_impl(const cd_params* params, int64_t npk, const int64_t
         return fail(nullptr, CD_ERR_INVALID_ARG, "parallel_p needs a plain system with the colour-barrier schedule");
     }
     g.par_p = p.parallel_p;
+    if (p.parallel_redraw != 0 && p.parallel_redraw != 1) {
+        delete s;
+        return fail(nullptr, CD_ERR_INVALID_ARG, "parallel_redraw must be 0 or 1");
+    }
+    g.par_redraw = (int)p.parallel_redraw;
     {
         // force-controlled walls
         int dyn = 0;

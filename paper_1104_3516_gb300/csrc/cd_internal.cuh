@@ -258,6 +258,7 @@ struct CdGeom {
     int npk;            // packings (1 for a plain system)
     int ncell_total;    // cells of all packings' grids
     double par_p;       // parallel fraction of the mixed update (0: Gauss-Seidel)
+    int par_redraw;     // 1: the parallel subset is drawn afresh in every iteration step
     int dyn_walls;      // bit k: wall k is force-controlled (a body n + k in V, S, p2c)
     int pad2;
     double wall_im[6];  // inverse mass of a force-controlled wall, else 0
@@ -296,13 +297,19 @@ __host__ __device__ __forceinline__ unsigned long long cd_key(int a, int b)
     return ((unsigned long long)(unsigned)a << 32) | (unsigned long long)(unsigned)b;
 }
 
-// Mixed update (Sec. 2.3): a contact is in the parallel subset when the hash
-// of its key falls below p.
-__device__ __forceinline__ bool cd_is_parallel(double p, unsigned long long seed, unsigned long long key)
+// Mixed update (Sec. 2.3): a contact is in the parallel subset when a
+// uniform number drawn for it (splitmix64 of its key mixed with the seed)
+// falls below p.  sweep < 0: one fixed subset per contact key; sweep >= 0
+// (params.parallel_redraw): the iteration step's number is mixed in as well,
+// a fresh subset in every step.
+__device__ __forceinline__ bool cd_is_parallel(double p, unsigned long long seed, unsigned long long key,
+                                               long long sweep = -1)
 {
     if (p <= 0.0) return false;
     if (p >= 1.0) return true;
-    unsigned long long h = cd_splitmix64(key ^ (seed * 0xD1B54A32D192ED03ULL));
+    unsigned long long x = key ^ (seed * 0xD1B54A32D192ED03ULL);
+    if (sweep >= 0) x ^= (unsigned long long)(sweep + 1) * 0x9E3779B97F4A7C15ULL;
+    unsigned long long h = cd_splitmix64(x);
     double u = (double)(h >> 11) * (1.0 / 9007199254740992.0);
     return u < p;
 }

@@ -38,6 +38,7 @@ struct MgInfo {
     int klast;
     int M;
     const int* lst;
+    long long draw;   // mixed update: the iteration step whose parallel subset applies (-1: fixed subset)
 };
 
 template <typename T> struct Vec;
@@ -309,17 +310,17 @@ __device__ __forceinline__ void sweep_test(const double* part, int nb, int nc, i
             double rs;
             int cv;
             if (crit == CD_CONV_GLOBAL_REL) {
-                rs = (den > 0.0) ? fabs(ra - ravg_prev) / den : 0.0;
+                rs = (den > 0.0) ? fabs(ra - ravg_prev) / den : (den == 0.0 ? 0.0 : den);
                 cv = rs < alpha;
             } else if (crit == CD_CONV_GLOBAL_SQ) {
-                double q = (den > 0.0) ? (ra - ravg_prev) / den : 0.0;
+                double q = (den > 0.0) ? (ra - ravg_prev) / den : (den == 0.0 ? 0.0 : den);
                 rs = q * q;
                 cv = rs < alpha;
             } else if (local) {
                 rs = (double)(nc - (long long)xr) / (double)nc;
                 cv = (10.0 * xr >= 9.0 * (double)nc) && xb == 0.0;
             } else {
-                rs = (den > 0.0) ? fabs(ra - ravg_prev) / den : 0.0;
+                rs = (den > 0.0) ? fabs(ra - ravg_prev) / den : (den == 0.0 ? 0.0 : den);
                 cv = 0;
             }
             s_b3[0] = ra;
@@ -434,13 +435,17 @@ __device__ __forceinline__ float clamp_sym(float x, float lim) { return x < -lim
 // wide FP32 pipe); then one Newton step of Heron's iteration for sqrt(m)
 // from y = m z, with z / 2 for 1 / (2 y): y + (m - y^2) z / 2; scale by 2^k.
 // With |z sqrt(m) - 1| = e of order 2^-24 the result is sqrt(s) (1 - 1.5 e^2
-// + O(e^3)), within 1e-14 relative.  Zero, subnormal, infinite, negative and
-// NaN s take s * rsqrt(s) (zero for s <= 0 and NaN, as s > 0.0 would decide).
+// + O(e^3)), within 1e-14 relative.  Subnormal and infinite s take
+// s * rsqrt(s); zero and negative s give 0; NaN gives NaN (as sqrt would: a
+// diverged iteration must not look converged to the residual test).
 __device__ __forceinline__ double norm_of_sq(double s)
 {
     const long long b = __double_as_longlong(s);
     const int be = (int)(b >> 52);   // biased exponent (sign clear for s >= 0)
-    if (be <= 0 || be >= 0x7FF) return (b > 0 && b <= 0x7FF0000000000000LL) ? s * rsqrt(s) : 0.0;
+    if (be <= 0 || be >= 0x7FF) {
+        if (s != s) return s;   // NaN
+        return (b > 0 && b <= 0x7FF0000000000000LL) ? s * rsqrt(s) : 0.0;
+    }
     const int e = be - 1023;
     const int k = e >> 1;   // floor(e / 2)
     const long long mb = (b & 0x000FFFFFFFFFFFFFLL) | ((long long)(1023 + e - 2 * k) << 52);
@@ -791,7 +796,7 @@ __device__ __forceinline__ void colour_phase(const CdGeom& g, const CdWork& w, c
     int p = sp.p;
     const bool mixed = MIXED && !apply_only;   // parallel contacts were done in their own phase
     if (p < end) {
-        if (!(mixed && cd_is_parallel(g.par_p, g.seed, cd_key(nxt.ab.x, nxt.ab.y)))) {
+        if (!(mixed && cd_is_parallel(g.par_p, g.seed, cd_key(nxt.ab.x, nxt.ab.y), mg.draw))) {
             UpdOut o = apply_rec<DIM, T, VIEWS, DEFER>(g, w, p, nxt, apply_only, crit, alpha, ravg_prev, pend);
             acc[0] += o.pabs;
             if (DEFER) pend = make_double2(o.pn, o.pt);
@@ -800,7 +805,7 @@ __device__ __forceinline__ void colour_phase(const CdGeom& g, const CdWork& w, c
         for (p += blockDim.x; p < end; p += blockDim.x) {
             Rec<DIM, T> r;
             load_rec<DIM, T, VIEWS>(g, w, p, r);
-            if (mixed && cd_is_parallel(g.par_p, g.seed, cd_key(r.ab.x, r.ab.y))) continue;
+            if (mixed && cd_is_parallel(g.par_p, g.seed, cd_key(r.ab.x, r.ab.y), mg.draw)) continue;
             UpdOut o = apply_rec<DIM, T, VIEWS, DEFER>(g, w, p, r, apply_only, crit, alpha, ravg_prev, pend);
             acc[0] += o.pabs;
             if (DEFER) pend = make_double2(o.pn, o.pt);
@@ -915,7 +920,7 @@ __device__ __forceinline__ UpdOut par_compute(const CdGeom& g, const CdWork& w, 
 }
 
 template <int DIM, typename T>
-__device__ __forceinline__ void par_apply(const CdGeom& g, const CdWork& w, int tid, int stride)
+__device__ __forceinline__ void par_apply(const CdGeom& g, const CdWork& w, int tid, int stride, long long draw)
 {
     typedef typename Vec<T>::V4 T4;
     T4* V = (T4*)w.V;
@@ -928,7 +933,7 @@ __device__ __forceinline__ void par_apply(const CdGeom& g, const CdWork& w, int 
         for (int q = w.p2c_off[i]; q < e; ++q) {
             const int c = w.p2c[q];
             const int2 ab = w.pairs[c];
-            if (!cd_is_parallel(g.par_p, g.seed, cd_key(ab.x, ab.y))) continue;
+            if (!cd_is_parallel(g.par_p, g.seed, cd_key(ab.x, ab.y), draw)) continue;
             if (!any) {
                 any = true;
                 if (DIM == 2) v = V[i];
@@ -1043,7 +1048,7 @@ k_sweep(CdGeom g, CdWork w, int crit, double alpha, int max_sweeps)
     unsigned long long epoch = 0;
     for (int k = threadIdx.x; k <= CD_KMAX; k += blockDim.x) s_off[k] = w.colour_off[k];
     MgInfo mg;
-    mg.on = 0; mg.klast = -1; mg.M = 0; mg.lst = nullptr;
+    mg.on = 0; mg.klast = -1; mg.M = 0; mg.lst = nullptr; mg.draw = -1;
     __shared__ int s_mgl[2 * CD_MG_MAXC];
     if constexpr (MODE == CD_SWEEP_MERGE) {
         const int M = ctrl->merge;
@@ -1098,11 +1103,12 @@ k_sweep(CdGeom g, CdWork w, int crit, double alpha, int max_sweeps)
             double* part = w.partials + (size_t)buf * 3 * nb;
             double a3[3] = {0.0, 0.0, 0.0};
             const bool mixed = MIXED;
+            if (MIXED && g.par_redraw) mg.draw = sweeps;   // this iteration step's parallel subset
             if (mixed) {
                 for (int p = tid; p < nc; p += stride) {
                     Rec<DIM, T> r;
                     load_rec<DIM, T>(g, w, p, r);
-                    if (!cd_is_parallel(g.par_p, g.seed, cd_key(r.ab.x, r.ab.y))) continue;
+                    if (!cd_is_parallel(g.par_p, g.seed, cd_key(r.ab.x, r.ab.y), mg.draw)) continue;
                     UpdOut o = par_compute<DIM, T>(g, w, p, r, crit, alpha, ravg_prev);
                     a3[0] += o.pabs;
                     if (crit == CD_CONV_LOCAL) { a3[1] += (double)o.rel_ok; a3[2] += (double)o.bad; }
@@ -1126,7 +1132,7 @@ k_sweep(CdGeom g, CdWork w, int crit, double alpha, int max_sweeps)
                 }
                 if (mixed && k == K - 1) {
                     if (!cd_grid_sync(ctrl, nb, epoch)) return;
-                    par_apply<DIM, T>(g, w, tid, stride);
+                    par_apply<DIM, T>(g, w, tid, stride, mg.draw);
                 }
                 if (k == K - 1) {
                     block_sum<3>(a3, s_red, test_values(crit));
@@ -1194,17 +1200,17 @@ __device__ __forceinline__ void pk_reduce(const CdGeom& g, const CdWork& w, int 
                 double resid;
                 int conv;
                 if (crit == CD_CONV_GLOBAL_REL) {
-                    resid = (den > 0.0) ? fabs(R - Rp) / den : 0.0;
+                    resid = (den > 0.0) ? fabs(R - Rp) / den : (den == 0.0 ? 0.0 : den);
                     conv = resid < alpha;
                 } else if (crit == CD_CONV_GLOBAL_SQ) {
-                    double q = (den > 0.0) ? (R - Rp) / den : 0.0;
+                    double q = (den > 0.0) ? (R - Rp) / den : (den == 0.0 ? 0.0 : den);
                     resid = q * q;
                     conv = resid < alpha;
                 } else if (crit == CD_CONV_LOCAL) {
                     resid = (ncb > 0) ? (double)(ncb - (long long)a3[1]) / (double)ncb : 0.0;
                     conv = (10.0 * a3[1] >= 9.0 * (double)ncb) && a3[2] == 0.0;
                 } else {
-                    resid = (den > 0.0) ? fabs(R - Rp) / den : 0.0;
+                    resid = (den > 0.0) ? fabs(R - Rp) / den : (den == 0.0 ? 0.0 : den);
                     conv = 0;
                 }
                 st[PKS_SWEEPS] = (double)(sweep + 1);

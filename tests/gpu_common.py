@@ -98,7 +98,8 @@ def run_pair(wl, steps=1, criterion=None, max_sweeps=None, alpha=None, precision
     o = oracle_system(wl, f_ext=f_ext, use_cells=use_cells, criterion=oracle_crit(criterion), max_sweeps=ms,
                       alpha=al, warm_start=warm_start, order=O.ORDER_COLOUR,
                       cap=max_contacts or max(64, 8 * wl.n),
-                      parallel_p=gpu_kw.get("parallel_p", 0.0), domains=gpu_kw.get("domains", (1, 1, 1)))
+                      parallel_p=gpu_kw.get("parallel_p", 0.0), parallel_redraw=gpu_kw.get("parallel_redraw", 0),
+                      domains=gpu_kw.get("domains", (1, 1, 1)))
     gst, ost = [], []
     for _ in range(steps):
         gst.append(g.step(1))

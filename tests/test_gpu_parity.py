@@ -317,10 +317,13 @@ def test_given_contact_list_and_warm_impulses():
 
 @pytest.mark.parametrize("p", [0.3, 1.0])
 @pytest.mark.parametrize("k", [1, 5, 20])
-def test_mixed_update_sweep_by_sweep(p, k):
+@pytest.mark.parametrize("redraw", [0, 1])
+def test_mixed_update_sweep_by_sweep(p, k, redraw):
+    """Both readings of the parallel subset: fixed per contact key, and
+    drawn afresh in every iteration step."""
     from paper_1104_3516_gb300 import cd
     wl = CASES["dense_deposit"]
-    g, o, gst, ost = run_pair(wl, criterion=cd.CD_CONV_NONE, max_sweeps=k, parallel_p=p)
+    g, o, gst, ost = run_pair(wl, criterion=cd.CD_CONV_NONE, max_sweeps=k, parallel_p=p, parallel_redraw=redraw)
     assert impulse_err(g.contacts()["impulse"], o.impulses) <= FP64_TOL
     s = g.state()
     vs = max(float(np.abs(o.v).max()), 1e-300)
@@ -342,6 +345,26 @@ def test_parallel_fraction_destabilises_a_dense_packing():
         assert pg == pytest.approx(po, rel=1e-9)
         peak[p] = pg
     assert peak[0.5] > 1e6 * peak[0.0]
+
+
+@pytest.mark.parametrize("redraw,p,stable", [(1, 0.2, True), (1, 0.6, False), (0, 0.1, False)])
+def test_mixed_update_stability_matches_the_oracle(redraw, p, stable):
+    """Sec. 2.3's protocol on a loaded 500-disc pile at rest, forces from
+    zero: with the subset drawn afresh every step, p = 0.2 converges and
+    p = 0.6 diverges; with a fixed subset even p = 0.1 diverges.  GPU and
+    oracle (colour order) agree on the outcome and, where it converges, on
+    the sweeps needed."""
+    from paper_1104_3516_gb300 import cd
+    wl = W.dense_biaxial_discs(n=500, wall_speed=0.0)
+    g, o, gst, ost = run_pair(wl, criterion=cd.CD_CONV_GLOBAL_REL, alpha=1e-6, max_sweeps=20000, warm_start=0,
+                              parallel_p=p, parallel_redraw=redraw)
+    assert gst[0]["last"]["converged"] == ost[0]["converged"] == stable
+    if stable:
+        # ~4,500 sweeps: the stopping sweep may differ by rounding; the floor force agrees
+        assert abs(gst[0]["last"]["sweeps"] - ost[0]["sweeps"]) <= 0.01 * ost[0]["sweeps"]
+        assert gst[0]["last"]["wall_force"][2] == pytest.approx(ost[0]["wall_force"][2], rel=1e-5)
+    else:
+        assert not np.isfinite(g.contacts()["impulse"]).all() or np.abs(g.contacts()["impulse"]).max() > 1e6
 
 
 # --- observables (Sec. 4.4, Figs. 14-15) -------------------------------------------

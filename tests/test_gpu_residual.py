@@ -98,3 +98,23 @@ def test_gpu_local_test_ninety_percent_rule():
     assert c["converged"] and c["sweeps"] == 2
     d = _row_gpu([1.0] * 20, [True] * 19 + [False])
     assert not d["converged"] and d["sweeps"] == 1
+
+
+def test_gpu_nan_impulses_never_pass_the_global_tests():
+    """A NaN starting impulse (given through cd_set_contacts) spreads through
+    the velocities: every R_avg is NaN and must not pass tests (II), which
+    count only 0/0 (both averages zero) as converged; the solve runs to the
+    cap with a NaN residual."""
+    from paper_1104_3516_gb300 import cd
+    wl = cases.floor_row([1.0] * 4)
+    wl.v = wl.v.copy()
+    wl.v[:, 1] -= G * DT
+    pairs = np.array([[i, wl.n + 2] for i in range(wl.n)], dtype=np.int32)
+    P0 = np.zeros((wl.n, 2))
+    P0[1, 0] = np.nan
+    for crit in (cd.CD_CONV_GLOBAL_REL, cd.CD_CONV_GLOBAL_SQ):
+        g = gpu_system(wl, criterion=crit, alpha=1e-6, max_sweeps=50)
+        g.set_contacts(pairs, P0)
+        st = g.solve_contacts()
+        assert not st["converged"] and st["sweeps"] == 50
+        assert math.isnan(st["residual"])

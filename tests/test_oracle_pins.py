@@ -569,6 +569,70 @@ def test_jacobi_update_needs_more_sweeps_than_gauss_seidel():
     assert out[1.0] > 1.2 * out[0.0]
 
 
+def _splitmix64(x):
+    """splitmix64 (Steele, Lea and Flood, OOPSLA 2014), the generator the
+    parallel subset is drawn with: restated here to predict the draws."""
+    M = (1 << 64) - 1
+    z = (x + 0x9E3779B97F4A7C15) & M
+    z = ((z ^ (z >> 30)) * 0xBF58476D1CE4E5B9) & M
+    z = ((z ^ (z >> 27)) * 0x94D049BB133111EB) & M
+    return z ^ (z >> 31)
+
+
+def _drawn_parallel(a, b, seed, p, sweep):
+    """Whether contact (a, b) is in the re-drawn parallel subset of iteration
+    step `sweep` (0-based): a uniform number from splitmix64 of the key mixed
+    with the seed and the step number, below p."""
+    M = (1 << 64) - 1
+    x = ((a << 32) | b) ^ ((seed * 0xD1B54A32D192ED03) & M) ^ (((sweep + 1) * 0x9E3779B97F4A7C15) & M)
+    return (_splitmix64(x) >> 11) * (1.0 / 9007199254740992.0) < p
+
+
+@pytest.mark.parametrize("seed", [3, 11, 12345])
+def test_redrawn_parallel_subset_follows_the_stack_recursion(seed):
+    """Sec. 2.3 with the parallel subset drawn afresh in every iteration
+    step.  Two discs stacked on the floor, forces from zero, in units of
+    m g dt: the disc-disc contact B is updated before the floor contact A,
+    and always sees the old A (B_k = A_(k-1) / 2: it comes first, and a
+    parallel A's change lands at the end of the sweep).  A sees the new B of
+    its sweep (A_k = 1 + B_k) only if neither contact is parallel; a parallel
+    A works from the sweep's start and a parallel B's change lands at the
+    end, so otherwise A_k = 1 + B_(k-1).  The draws, predicted from the
+    generator's definition, must reproduce the oracle's impulses sweep by
+    sweep, and differ from sweep to sweep."""
+    wl = cases.stack2()
+    wl.seed = seed
+    unit = G * DT / wl.inv_m[0]
+    p = 0.5
+    A, B = 0.0, 0.0
+    draws = []
+    for k in range(1, 9):
+        parA = _drawn_parallel(0, 4, seed, p, k - 1)
+        parB = _drawn_parallel(0, 1, seed, p, k - 1)
+        draws.append((parA, parB))
+        Bk = A / 2.0
+        A = 1.0 + (B if (parA or parB) else Bk)
+        B = Bk
+        s, _ = _one_step(wl, order=O.ORDER_COLOUR, criterion=O.CRIT_NONE, max_sweeps=k, warm_start=0,
+                         parallel_p=p, parallel_redraw=1)
+        assert s.contacts.tolist() == [[0, 1], [0, 4]]
+        assert s.impulses[1, 0] == pytest.approx(A * unit, rel=1e-12)
+        assert s.impulses[0, 0] == pytest.approx(B * unit, rel=1e-12, abs=1e-18)
+    assert len(set(draws)) > 1              # the subset changes between steps
+
+
+def test_redrawn_subset_limits_are_the_fixed_schemes():
+    """p = 0 and p = 1 draw the same subsets in every step, so both
+    readings give the sequential and the Jacobi scheme, bit for bit."""
+    F = 1.0
+    for p in (0.0, 1.0):
+        wl, f = cases.chain(n=12, force=F)
+        a, st_a = _one_step(wl, f_ext=f, order=O.ORDER_COLOUR, criterion=O.CRIT_NONE, max_sweeps=60, parallel_p=p)
+        b, st_b = _one_step(wl, f_ext=f, order=O.ORDER_COLOUR, criterion=O.CRIT_NONE, max_sweeps=60, parallel_p=p,
+                            parallel_redraw=1)
+        assert np.array_equal(a.impulses, b.impulses)
+
+
 # --- observables of Sec. 4.4 ---------------------------------------------------
 
 def test_column_observables_closed_form():

@@ -182,3 +182,22 @@ def test_local_test_needs_the_rest_below_the_absolute_bound(radius):
     P, v, w, st = _row_solve([1.0] * 19 + [radius], [True] * 19 + [False])
     assert not st["converged"] and st["sweeps"] == 1
     assert st["residual"] == pytest.approx(0.05, rel=1e-15)
+
+
+def test_nan_impulses_never_pass_the_global_tests():
+    """A NaN starting impulse spreads through the velocities: every R_avg is
+    NaN and must not pass tests (II), which count only 0/0 (both averages
+    zero) as converged; the solve runs to the cap with a NaN residual."""
+    for crit in (O.CRIT_GLOBAL_REL, O.CRIT_GLOBAL_SQ):
+        wl = cases.floor_row([1.0] * 4)
+        p = params(wl, criterion=crit, alpha=1e-6, max_sweeps=50, order=O.ORDER_RANDOM)
+        wp = np.asarray(wl.wall_pos, dtype=np.float64)
+        pairs = O.detect_brute(p, wl.x, wl.r, wp)
+        normal, gap, mn, mt = O.contact_geometry(p, wl.x, wl.r, wl.inv_m, wl.inv_I, wp, pairs)
+        P0 = np.zeros((wl.n, 2))
+        P0[1, 0] = np.nan
+        vfree = wl.v.copy()
+        vfree[:, 1] -= G * DT
+        P, v, w, st = O.solve(p, vfree, wl.w, wl.r, wl.inv_m, wl.inv_I, pairs, normal, gap, mn, mt, P0=P0)
+        assert not st["converged"] and st["sweeps"] == 50
+        assert math.isnan(st["residual"])
