@@ -436,16 +436,16 @@ __device__ __forceinline__ float clamp_sym(float x, float lim) { return x < -lim
 // from y = m z, with z / 2 for 1 / (2 y): y + (m - y^2) z / 2; scale by 2^k.
 // With |z sqrt(m) - 1| = e of order 2^-24 the result is sqrt(s) (1 - 1.5 e^2
 // + O(e^3)), within 1e-14 relative.  Subnormal and infinite s take
-// s * rsqrt(s); zero and negative s give 0; NaN gives NaN (as sqrt would: a
-// diverged iteration must not look converged to the residual test).
+// s * rsqrt(s); zero and negative s give 0; a NaN with the sign bit clear
+// (what arithmetic on NaN produces here) gives NaN, as sqrt would, so that a
+// diverged iteration does not look converged to the residual test; the
+// decision is on the bit pattern, with no FP64 compare.
 __device__ __forceinline__ double norm_of_sq(double s)
 {
     const long long b = __double_as_longlong(s);
     const int be = (int)(b >> 52);   // biased exponent (sign clear for s >= 0)
-    if (be <= 0 || be >= 0x7FF) {
-        if (s != s) return s;   // NaN
-        return (b > 0 && b <= 0x7FF0000000000000LL) ? s * rsqrt(s) : 0.0;
-    }
+    if (be <= 0 || be >= 0x7FF)
+        return (b > 0 && b <= 0x7FF0000000000000LL) ? s * rsqrt(s) : (b > 0x7FF0000000000000LL ? s : 0.0);
     const int e = be - 1023;
     const int k = e >> 1;   // floor(e / 2)
     const long long mb = (b & 0x000FFFFFFFFFFFFFLL) | ((long long)(1023 + e - 2 * k) << 52);
