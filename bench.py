@@ -57,6 +57,17 @@ FLOPS_PER_UPDATE_2D = 42
 # n x dP 9, both bodies' v and w 24, |P| 7 (+ square root; the cone scaling
 # of sliding contacts is not counted)
 FLOPS_PER_UPDATE_3D = 101
+# algorithmic bytes of one detection (cell list, pair test, geometry and warm
+# start; the library's "detect" phase): per particle the position and radius
+# read (8 D + 8); per contact the key-order record written (key 8, normal 24,
+# gap 8, m_n 8, m_t 8, impulse 8 x (D + 1)) and the previous set's key and
+# impulse read by the warm start (8 + 8 x (D + 1), counted at the new set's
+# size)
+def detect_bytes_model(dim):
+    pw = 2 if dim == 2 else 4
+    return 64 + 16 * pw, 8 * dim + 8
+
+
 # FP64 peak of GB300 from unit counts and clock: 152 SMs x 2 FP64 FMA/clk x 2
 # flops x 2.07 GHz (nominal 1.25 TFLOP/s)
 FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12
@@ -324,6 +335,20 @@ def sweep_bytes_model(dim, precision):
     return BYTES_PER_CONTACT[precision], BYTES_PER_PARTICLE[precision]
 
 
+def detect_roofline(dim, detect_ms, n, contacts):
+    """HBM view of the detection phase: its algorithmic bytes over its
+    CUDA-event time (`detect_ms` summed over the steps whose contact counts
+    are `contacts`)."""
+    bpc, bpp = detect_bytes_model(dim)
+    peak, peak_kind = peaks()
+    byt = sum(bpc * c + bpp * n for c in contacts)
+    gbs = byt / (detect_ms / 1e3) / 1e9 if detect_ms > 0 else 0.0
+    return {"bound": "hbm", "achieved": gbs, "peak": peak, "unit": "GB/s", "frac": gbs / peak,
+            "kernels": "k_cell_count .. k_pair_count, k_pair_emit .. k_commit (the detect phase)",
+            "avg_phase_ms": detect_ms / max(len(contacts), 1), "peak_source": f"{peak_kind} HBM copy bandwidth",
+            "bytes_model": f"{bpc} B x contacts + {bpp} B x particles per detection"}
+
+
 def timed_steps(sysg, wl, steps, flush, precision):
     """`steps` CD time steps of a system created with timing=1, the L2 flushed
     (512 MiB written) before each; device times from the library's CUDA events
@@ -448,6 +473,7 @@ def run_ours(args):
                     "avg_launch_ms": ph["sweep"] / max(args.steps, 1), "hbm_view": hbm_view}
     else:
         roofline = dict(hbm_view, traffic=traffic, kernel=kname, avg_launch_ms=ph["sweep"] / max(args.steps, 1))
+    roofline["detect_view"] = detect_roofline(wl.dim, ph["detect"], wl.n, t["ncs"])
 
     batched = None
     if args.batched_steps > 0 and wl.dim == 2:
@@ -703,7 +729,8 @@ def run_sphere_gas(args, device, flush):
                 "avg_launch_ms": ph["sweep"] / args.sphere_steps,
                 "hbm_view": {"bound": "hbm", "achieved": gbs, "peak": peak, "unit": "GB/s", "frac": gbs / peak,
                              "peak_source": f"{peak_kind} HBM copy bandwidth",
-                             "bytes_model": f"per sweep {bpc} B x contacts + {bpp} B x particles"}}
+                             "bytes_model": f"per sweep {bpc} B x contacts + {bpp} B x particles"},
+                "detect_view": detect_roofline(3, ph["detect"], wl.n, ncs)}
     out = {"value": upd / (ms / 1e3), "unit": UNIT, "spheres": wl.n, "steps": args.sphere_steps, "roofline": roofline,
            "ms_per_step": ms / args.sphere_steps, "steps_per_s": args.sphere_steps / (ms / 1e3),
            "phase_ms_per_step": {k: v / args.sphere_steps for k, v in ph.items()},

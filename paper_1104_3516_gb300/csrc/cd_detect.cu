@@ -3,10 +3,10 @@
 //
 // Pipeline (all on one stream, sizes read from the control block so nothing
 // is synchronised with the host):
-//   cell_count -> scan -> cell_fill          counting sort of particles by cell
+//   cell_count -> scan -> cell_fill, sort    counting sort of particles by cell
 //   pair_count -> scan -> capacity check     contacts per particle a (b > a)
-//   pair_emit                                keys (a, b) sorted per a, geometry
-//   warm_match -> commit                     impulses carried over by key
+//   pair_emit                                keys (a, b) sorted per a
+//   geometry_warm -> commit                  geometry per contact, impulses carried over by key
 // The pair test uses the same FP64 operation sequence as the CPU oracle
 // (explicit round-to-nearest intrinsics, no FMA contraction) so the contact
 // set is bit-identical to brute force.
@@ -315,6 +315,26 @@ template <int DIM>
 struct Runs {
     static constexpr int N = (DIM == 3) ? 18 : 6;   // 3^(DIM-1) rows, each with a possible wrapped cell
     int lo[N], hi[N];
+    // r is a compile-time index at every call (unrolled loops)
+    __device__ __forceinline__ void set(int r, int l, int h) { lo[r] = l; hi[r] = h; }
+    __device__ __forceinline__ void get(int j, int& l, int& h) const
+    {
+#pragma unroll
+        for (int k = 0; k < N; ++k)
+            if (k == j) { l = lo[k]; h = hi[k]; }
+    }
+};
+
+// The same runs in shared memory, [run][thread] (a warp's accesses fall in
+// distinct banks): the counting pass keeps its registers for the walk
+// itself, and a run is fetched by its run-time index.
+template <int DIM>
+struct RunsShared {
+    static constexpr int N = Runs<DIM>::N;
+    int* lo;   // &s_lo[0][threadIdx.x], stride CD_BLOCK
+    int* hi;
+    __device__ __forceinline__ void set(int r, int l, int h) { lo[r * CD_BLOCK] = l; hi[r * CD_BLOCK] = h; }
+    __device__ __forceinline__ void get(int j, int& l, int& h) const { l = lo[j * CD_BLOCK]; h = hi[j * CD_BLOCK]; }
 };
 
 __device__ __forceinline__ int last_id(const int* __restrict__ cell_start, const int* __restrict__ cell_pid, int cc)
@@ -323,11 +343,12 @@ __device__ __forceinline__ int last_id(const int* __restrict__ cell_start, const
     return (h > l) ? cell_pid[h - 1] : -1;
 }
 
-template <int DIM, typename F>
-__device__ __forceinline__ void for_each_partner(const CdGeom& g, const GridV& v, int a, const double* xa, double ra,
-                                                 const double* __restrict__ pos, const double* __restrict__ radius,
-                                                 const int* __restrict__ cell_of, const int* __restrict__ cell_start,
-                                                 const int* __restrict__ cell_pid, const float4* __restrict__ pf, F f)
+// Builds the runs of particle a in R (Runs or RunsShared); the walk starts
+// at run 0.
+template <int DIM, typename RS>
+__device__ __forceinline__ void walk_init(const GridV& v, int a, const int* __restrict__ cell_of,
+                                          const int* __restrict__ cell_start, const int* __restrict__ cell_pid,
+                                          RS& R)
 {
     const int c = cell_of[a] - v.base;
     const int n0 = v.ncell[0], n1 = v.ncell[1];
@@ -340,23 +361,21 @@ __device__ __forceinline__ void for_each_partner(const CdGeom& g, const GridV& v
         if (q0 == 0) xw = n0 - 1;
         else if (q0 == n0 - 1) xw = 0;
     }
-    Runs<DIM> R;
     constexpr int ZN = (DIM == 3) ? 3 : 1;
 #pragma unroll
     for (int iz = 0; iz < ZN; ++iz) {
 #pragma unroll
         for (int iy = 0; iy < 3; ++iy) {
             const int r = 2 * (iz * 3 + iy);
-            R.lo[r] = R.hi[r] = 0;
-            R.lo[r + 1] = R.hi[r + 1] = 0;
+            int l0 = 0, h0 = 0, l1 = 0, h1 = 0;
             int t2 = (DIM == 3) ? q2 + iz - 1 : 0;
             if (DIM == 3 && (t2 < 0 || t2 >= v.ncell[2])) {
-                if (!v.periodic[2]) continue;
+                if (!v.periodic[2]) { R.set(r, 0, 0); R.set(r + 1, 0, 0); continue; }
                 t2 = (t2 + v.ncell[2]) % v.ncell[2];
             }
             int t1 = q1 + iy - 1;
             if (t1 < 0 || t1 >= n1) {
-                if (!v.periodic[1]) continue;
+                if (!v.periodic[1]) { R.set(r, 0, 0); R.set(r + 1, 0, 0); continue; }
                 t1 = (t1 + n1) % n1;
             }
             const int row = v.base + (t2 * n1 + t1) * n0;
@@ -373,65 +392,179 @@ __device__ __forceinline__ void for_each_partner(const CdGeom& g, const GridV& v
             const int L2 = (nx > 2 && cs3 > cs2) ? cell_pid[cs3 - 1] : -1;
             const int start = (L0 > a) ? cs0 : (L1 > a) ? cs1 : (L2 > a) ? cs2 : -1;
             if (start >= 0) {
-                R.lo[r] = start;
-                R.hi[r] = cs3;
+                l0 = start;
+                h0 = cs3;
             }
             if (xw >= 0 && last_id(cell_start, cell_pid, row + xw) > a) {
-                R.lo[r + 1] = cell_start[row + xw];
-                R.hi[r + 1] = cell_start[row + xw + 1];
+                l1 = cell_start[row + xw];
+                h1 = cell_start[row + xw + 1];
             }
+            R.set(r, l0, h0);
+            R.set(r + 1, l1, h1);
         }
     }
+}
+
+// The next candidate of the flat walk over the runs (j the run, [s, e) what
+// is left of it), or -1 once they are exhausted (and on every later call).
+template <int DIM, typename RS>
+__device__ __forceinline__ int walk_next(const RS& R, int& j, int& s, int& e, const int* __restrict__ cell_pid)
+{
+    while (s >= e) {
+        if (++j >= Runs<DIM>::N) return -1;
+        R.get(j, s, e);
+    }
+    return cell_pid[s++];
+}
+
+template <int DIM, typename F>
+__device__ __forceinline__ void for_each_partner(const CdGeom& g, const GridV& v, int a, const double* xa, double ra,
+                                                 const double* __restrict__ pos, const double* __restrict__ radius,
+                                                 const int* __restrict__ cell_of, const int* __restrict__ cell_start,
+                                                 const int* __restrict__ cell_pid, const float4* __restrict__ pf, F f)
+{
+    Runs<DIM> R;
+    walk_init<DIM>(v, a, cell_of, cell_start, cell_pid, R);
+    int j = 0, s = R.lo[0], e = R.hi[0];
     // the pre-filter's data (pf null: the exact test only)
     float4 pa = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
-    float Lf[3] = {(float)v.L[0], (float)v.L[1], (float)v.L[2]};
+    const float Lf[3] = {(float)v.L[0], (float)v.L[1], (float)v.L[2]};
     const float delta_f = (float)g.delta;
     if (pf) pa = pf[a];
-    // flat walk over the runs
-    int j = 0, s = R.lo[0], e = R.hi[0];
     for (;;) {
-        while (s >= e) {
-            if (++j >= Runs<DIM>::N) break;
-#pragma unroll
-            for (int k = 1; k < Runs<DIM>::N; ++k)
-                if (k == j) { s = R.lo[k]; e = R.hi[k]; }
-        }
-        if (j >= Runs<DIM>::N) break;
-        const int b = cell_pid[s++];
+        const int b = walk_next<DIM>(R, j, s, e, cell_pid);
+        if (b < 0) break;
         if (b > a && !(pf && pair_far_f32<DIM>(v, Lf, delta_f, pa, pf[b])) &&
             pair_touches<DIM>(v, g.delta, xa, ra, pos, radius, b))
             f(b);
     }
 }
 
-// Three blocks per SM (<= 80 registers): the walk is latency-bound, and the
-// occupancy pays for a few spilled bytes (3D: 2.6 -> 2.5 ms of a 1e6-sphere step).
+// Exact tests of the first `take` queued pairs of a warp, lane q on pair q:
+// the owner lane's particle (its id, position and radius by shuffles), the
+// partner's from memory.  A pair that touches counts for its owner and is
+// kept among the owner's first CD_CAND partners.
 template <int DIM>
-__global__ void __launch_bounds__(CD_BLOCK, 3) k_pair_count(CdGeom g, CdWork w, const double* __restrict__ pos, const double* __restrict__ radius,
+__device__ __forceinline__ void exact_batch(const CdGeom& g, const CdWork& w, const double* __restrict__ pos,
+                                            const double* __restrict__ radius, int a, double x0, double x1,
+                                            double x2, double ra, int take, const int* qb, const int* qo, int* cnt)
+{
+    const int lane = threadIdx.x & 31;
+    const int o = (lane < take) ? qo[lane] : 0;
+    const int b = (lane < take) ? qb[lane] : 0;
+    const int ao = __shfl_sync(0xffffffffu, a, o);
+    double xo[3];
+    xo[0] = __shfl_sync(0xffffffffu, x0, o);
+    xo[1] = __shfl_sync(0xffffffffu, x1, o);
+    xo[2] = (DIM == 3) ? __shfl_sync(0xffffffffu, x2, o) : 0.0;
+    const double ro = __shfl_sync(0xffffffffu, ra, o);
+    if (lane < take) {
+        GridV vo;
+        grid_of(g, w, ao, vo);
+        if (pair_touches<DIM>(vo, g.delta, xo, ro, pos, radius, b)) {
+            const int slot = atomicAdd(&cnt[o], 1);
+            if (w.cand && slot < CD_CAND) w.cand[(size_t)ao * CD_CAND + slot] = b;
+        }
+    }
+}
+
+// Counting pass: partners b > a of every particle, and its walls.  A lane
+// walks its particle's candidates through the single-precision pre-filter;
+// the candidates that pass are queued per warp (ballot and prefix count) and
+// the warp runs the exact FP64 test on 32 queued pairs at a time, whoever
+// owns them.  With the test inside the walk the warp issued it in nearly
+// every step, since some lane's candidate nearly always passes the
+// pre-filter (~220 FP64 warp instructions per particle warp on the
+// 1e6-sphere gas).  The partners found and their count are those of the
+// walk; only the order in which a particle's first CD_CAND partners are kept
+// depends on timing, and the emitting pass sorts them.  The runs live in
+// shared memory, the walk's state in registers.
+template <int DIM>
+__global__ void __launch_bounds__(CD_BLOCK, 4) k_pair_count(CdGeom g, CdWork w, const double* __restrict__ pos, const double* __restrict__ radius,
                              const int* __restrict__ cell_of, const int* __restrict__ cell_start,
                              const int* __restrict__ cell_pid, int* __restrict__ pcnt, CdCtrl* ctrl)
 {
+    __shared__ int s_qb[CD_BLOCK / 32][64];   // queued partners (at most 31 left over + 32 new)
+    __shared__ int s_qo[CD_BLOCK / 32][64];   // their owner lanes
+    __shared__ int s_cnt[CD_BLOCK];
+    __shared__ int s_lo[Runs<DIM>::N][CD_BLOCK], s_hi[Runs<DIM>::N][CD_BLOCK];
     if (ctrl->skip) return;
-    for (int a = blockIdx.x * blockDim.x + threadIdx.x; a < g.n; a += gridDim.x * blockDim.x) {
+    const int lane = threadIdx.x & 31, wq = threadIdx.x >> 5;
+    int* const qb = s_qb[wq];
+    int* const qo = s_qo[wq];
+    int* const cnt_w = s_cnt + 32 * wq;
+    // warps step through the particles together (the loop bound is warp-uniform)
+    for (int base = blockIdx.x * blockDim.x + (threadIdx.x & ~31); base < g.n; base += gridDim.x * blockDim.x) {
+        const int a = base + lane;
+        const bool act = a < g.n;
         GridV v;
-        grid_of(g, w, a, v);
-        const double* wp = w.pk_wall_pos + 6 * v.pkid;
         double xa[3] = {0.0, 0.0, 0.0};
+        double ra = 0.0;
+        RunsShared<DIM> R;
+        R.lo = &s_lo[0][threadIdx.x];
+        R.hi = &s_hi[0][threadIdx.x];
+        int j = 0, s = 0, e = 0;
+        float4 pa = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+        float Lf[3] = {0.0f, 0.0f, 0.0f};
+        bool more = act;
+        if (act) {
+            grid_of(g, w, a, v);
 #pragma unroll
-        for (int k = 0; k < DIM; ++k) xa[k] = pos[a * DIM + k];
-        double ra = radius[a];
-        int cnt = 0;
-        int* keep = w.cand ? w.cand + (size_t)a * CD_CAND : nullptr;
-        for_each_partner<DIM>(g, v, a, xa, ra, pos, radius, cell_of, cell_start, cell_pid, w.pf, [&](int b) {
-            if (keep && cnt < CD_CAND) keep[cnt] = b;   // the emitting pass reuses them instead of walking again
-            ++cnt;
-        });
-        int nw = 0;
+            for (int k = 0; k < DIM; ++k) xa[k] = pos[a * DIM + k];
+            ra = radius[a];
+            walk_init<DIM>(v, a, cell_of, cell_start, cell_pid, R);
+            R.get(0, s, e);
+            if (w.pf) pa = w.pf[a];
 #pragma unroll
-        for (int k = 0; k < 2 * DIM; ++k)
-            if (wall_on(v, DIM, k) && wall_gap(xa, ra, wp, k) < g.delta) ++nw;
-        if (cnt > CD_MAXLOC) atomicCAS(&ctrl->error, CDE_NONE, CDE_PER_PARTICLE);
-        pcnt[a] = cnt + nw;
+            for (int k = 0; k < 3; ++k) Lf[k] = (float)v.L[k];
+        }
+        const float delta_f = (float)g.delta;
+        s_cnt[threadIdx.x] = 0;
+        __syncwarp();
+        int qn = 0;   // queued pairs (the same in every lane)
+        for (;;) {
+            int b = -1;
+            bool q = false;
+            if (more) {
+                b = walk_next<DIM>(R, j, s, e, cell_pid);
+                if (b < 0) more = false;
+                else q = b > a && !(w.pf && pair_far_f32<DIM>(v, Lf, delta_f, pa, w.pf[b]));
+            }
+            const unsigned m = __ballot_sync(0xffffffffu, q);
+            if (q) {
+                const int at = qn + __popc(m & ((1u << lane) - 1u));
+                qb[at] = b;
+                qo[at] = lane;
+            }
+            qn += __popc(m);
+            const bool done = !__any_sync(0xffffffffu, more);
+            while (qn >= 32 || (done && qn > 0)) {
+                __syncwarp();
+                const int take = qn < 32 ? qn : 32;
+                exact_batch<DIM>(g, w, pos, radius, a, xa[0], xa[1], xa[2], ra, take, qb, qo, cnt_w);
+                // the rest (fewer than 32) to the front of the queue
+                const int rest = qn - take;
+                int rb = 0, ro = 0;
+                if (lane < rest) { rb = qb[32 + lane]; ro = qo[32 + lane]; }
+                __syncwarp();
+                if (lane < rest) { qb[lane] = rb; qo[lane] = ro; }
+                __syncwarp();
+                qn = rest;
+            }
+            if (done) break;
+        }
+        __syncwarp();
+        if (act) {
+            const int cnt = s_cnt[threadIdx.x];
+            const double* wp = w.pk_wall_pos + 6 * v.pkid;
+            int nw = 0;
+#pragma unroll
+            for (int k = 0; k < 2 * DIM; ++k)
+                if (wall_on(v, DIM, k) && wall_gap(xa, ra, wp, k) < g.delta) ++nw;
+            if (cnt > CD_MAXLOC) atomicCAS(&ctrl->error, CDE_NONE, CDE_PER_PARTICLE);
+            pcnt[a] = cnt + nw;
+        }
+        __syncwarp();
     }
 }
 
@@ -516,9 +649,12 @@ __device__ __forceinline__ void store_geometry(const CdWork& w, int c, int a, in
     w.mt[c] = mt;
 }
 
+// Emitting pass: the keys (a, b) of every particle's contacts, partners in
+// ascending id, then its walls, at the particle's offset from the scan of
+// the counts.  Integer work only; the geometry follows one thread per
+// contact (k_geometry_warm).
 template <int DIM>
-__global__ void k_pair_emit(CdGeom g, CdWork w, const double* __restrict__ pos, const double* __restrict__ radius,
-                            const double* __restrict__ inv_m, const double* __restrict__ inv_I)
+__global__ void k_pair_emit(CdGeom g, CdWork w, const double* __restrict__ pos, const double* __restrict__ radius)
 {
     CdCtrl* ctrl = w.ctrl;
     if (ctrl->skip) return;
@@ -537,8 +673,9 @@ __global__ void k_pair_emit(CdGeom g, CdWork w, const double* __restrict__ pos, 
         const int npart = w.pcnt[a] - nw;   // partners the counting pass found
         int o = w.poff[a];
         if (w.cand && npart <= CD_CAND) {
-            // the counting pass kept them (in walk order): emit in ascending id by
-            // repeated selection of the smallest one above the last emitted
+            // the counting pass kept them (in the order its exact tests ran):
+            // emit in ascending id by repeated selection of the smallest one
+            // above the last emitted
             const int* keep = w.cand + (size_t)a * CD_CAND;
             int last = a;
             for (int f = 0; f < npart; ++f) {
@@ -547,9 +684,7 @@ __global__ void k_pair_emit(CdGeom g, CdWork w, const double* __restrict__ pos, 
                     const int bq = keep[q];
                     if (bq > last && bq < bmin) bmin = bq;
                 }
-                double nv[3], gap, mn, mt;
-                contact_geometry<DIM>(g, w, a, bmin, pos, radius, inv_m, inv_I, nv, &gap, &mn, &mt);
-                store_geometry<DIM>(w, o++, a, bmin, nv, gap, mn, mt);
+                w.pairs_nx[o++] = make_int2(a, bmin);
                 last = bmin;
             }
         } else {
@@ -564,21 +699,66 @@ __global__ void k_pair_emit(CdGeom g, CdWork w, const double* __restrict__ pos, 
                 }
             };
             for_each_partner<DIM>(g, v, a, xa, ra, pos, radius, w.cell_of, w.cell_start, w.cell_pid, w.pf, insert);
-            for (int f = 0; f < nf; ++f) {
-                double nv[3], gap, mn, mt;
-                contact_geometry<DIM>(g, w, a, found[f], pos, radius, inv_m, inv_I, nv, &gap, &mn, &mt);
-                store_geometry<DIM>(w, o++, a, found[f], nv, gap, mn, mt);
+            for (int f = 0; f < nf; ++f) w.pairs_nx[o++] = make_int2(a, found[f]);
+        }
+#pragma unroll
+        for (int k = 0; k < 2 * DIM; ++k)
+            if (wall_on(v, DIM, k) && wall_gap(xa, ra, wp, k) < g.delta)
+                w.pairs_nx[o++] = make_int2(a, g.n + 6 * v.pkid + k);
+    }
+}
+
+// Geometry of every detected contact, one thread per contact (so that the
+// FP64 square root and divisions run on full warps), and its starting
+// impulse: matched by key in the current (previous) set; in 3D the old
+// tangential impulse is projected onto the new tangent plane.
+template <int DIM>
+__global__ void k_geometry_warm(CdGeom g, CdWork w, const double* __restrict__ pos, const double* __restrict__ radius,
+                                const double* __restrict__ inv_m, const double* __restrict__ inv_I, int warm, int pw)
+{
+    CdCtrl* ctrl = w.ctrl;
+    if (ctrl->skip) return;
+    const int nnew = ctrl->nc_needed;
+    const int nold = ctrl->nc;
+    for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < nnew; c += gridDim.x * blockDim.x) {
+        const int2 ab = w.pairs_nx[c];
+        double nv[3], gap, mn, mt;
+        contact_geometry<DIM>(g, w, ab.x, ab.y, pos, radius, inv_m, inv_I, nv, &gap, &mn, &mt);
+        w.nrm[3 * c + 0] = nv[0];
+        w.nrm[3 * c + 1] = nv[1];
+        w.nrm[3 * c + 2] = nv[2];
+        w.gap[c] = gap;
+        w.mn[c] = mn;
+        w.mt[c] = mt;
+        double out[4] = {0.0, 0.0, 0.0, 0.0};
+        if (warm && nold > 0) {
+            const unsigned long long key = cd_key(ab.x, ab.y);
+            int lo = 0, hi = nold - 1, o = -1;
+            while (lo <= hi) {
+                int mid = lo + ((hi - lo) >> 1);
+                int2 m = w.pairs[mid];
+                unsigned long long km = cd_key(m.x, m.y);
+                if (km == key) { o = mid; break; }
+                if (km < key) lo = mid + 1; else hi = mid - 1;
+            }
+            if (o >= 0) {
+                if (DIM == 2) {
+                    out[0] = w.Pk[2 * o];
+                    out[1] = w.Pk[2 * o + 1];
+                } else {
+                    const double* q = w.Pk + 4 * o;
+                    double tn = __dadd_rn(__dadd_rn(__dmul_rn(q[1], nv[0]), __dmul_rn(q[2], nv[1])),
+                                          __dmul_rn(q[3], nv[2]));
+                    out[0] = q[0];
+                    out[1] = __dsub_rn(q[1], __dmul_rn(tn, nv[0]));
+                    out[2] = __dsub_rn(q[2], __dmul_rn(tn, nv[1]));
+                    out[3] = __dsub_rn(q[3], __dmul_rn(tn, nv[2]));
+                }
             }
         }
 #pragma unroll
-        for (int k = 0; k < 2 * DIM; ++k) {
-            if (wall_on(v, DIM, k) && wall_gap(xa, ra, wp, k) < g.delta) {
-                const int wid = g.n + 6 * v.pkid + k;
-                double nv[3], gap, mn, mt;
-                contact_geometry<DIM>(g, w, a, wid, pos, radius, inv_m, inv_I, nv, &gap, &mn, &mt);
-                store_geometry<DIM>(w, o++, a, wid, nv, gap, mn, mt);
-            }
-        }
+        for (int k = 0; k < 4; ++k)
+            if (k < pw) w.Pk_nx[pw * c + k] = out[k];   // compile-time indices keep out[] in registers
     }
 }
 
@@ -601,47 +781,6 @@ __global__ void k_copy_pairs(int nc, const int32_t* __restrict__ src, int2* __re
     for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < nc; c += gridDim.x * blockDim.x)
         dst[c] = make_int2(src[2 * c], src[2 * c + 1]);
     if (blockIdx.x == 0 && threadIdx.x == 0) ctrl->nc_needed = nc;
-}
-
-// Impulses of the new set: matched by key in the current (previous) set; in
-// 3D the old tangential impulse is projected onto the new tangent plane.
-template <int DIM>
-__global__ void k_warm_match(CdWork w, int warm, int pw)
-{
-    CdCtrl* ctrl = w.ctrl;
-    if (ctrl->skip) return;
-    int nnew = ctrl->nc_needed;
-    int nold = ctrl->nc;
-    for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < nnew; c += gridDim.x * blockDim.x) {
-        double out[4] = {0.0, 0.0, 0.0, 0.0};
-        if (warm && nold > 0) {
-            int2 ab = w.pairs_nx[c];
-            unsigned long long key = cd_key(ab.x, ab.y);
-            int lo = 0, hi = nold - 1, o = -1;
-            while (lo <= hi) {
-                int mid = lo + ((hi - lo) >> 1);
-                int2 m = w.pairs[mid];
-                unsigned long long km = cd_key(m.x, m.y);
-                if (km == key) { o = mid; break; }
-                if (km < key) lo = mid + 1; else hi = mid - 1;
-            }
-            if (o >= 0) {
-                if (DIM == 2) {
-                    out[0] = w.Pk[2 * o];
-                    out[1] = w.Pk[2 * o + 1];
-                } else {
-                    const double* q = w.Pk + 4 * o;
-                    double n0 = w.nrm[3 * c], n1 = w.nrm[3 * c + 1], n2 = w.nrm[3 * c + 2];
-                    double tn = __dadd_rn(__dadd_rn(__dmul_rn(q[1], n0), __dmul_rn(q[2], n1)), __dmul_rn(q[3], n2));
-                    out[0] = q[0];
-                    out[1] = __dsub_rn(q[1], __dmul_rn(tn, n0));
-                    out[2] = __dsub_rn(q[2], __dmul_rn(tn, n1));
-                    out[3] = __dsub_rn(q[3], __dmul_rn(tn, n2));
-                }
-            }
-        }
-        for (int k = 0; k < pw; ++k) w.Pk_nx[pw * c + k] = out[k];
-    }
 }
 
 // Caller-given starting impulses (or zeros) for a caller-given list.
@@ -700,12 +839,12 @@ cudaError_t cd_launch_detect(const CdGeom& g, const CdWork& w, const double* pos
     if ((e = cudaMemsetAsync(w.pcnt + g.n, 0, sizeof(int), s)) != cudaSuccess) return e;
     if ((e = cd_scan_exclusive(w.pcnt, w.poff, g.n + 1, w.scan_tmp, &w.ctrl->nc_needed, s, nl)) != cudaSuccess) return e;
     k_cap_check<<<1, 1, 0, s>>>(w.ctrl, g.cap); ++*nl;
-    if (g.dim == 2) k_pair_emit<2><<<gb, CD_BLOCK, 0, s>>>(g, w, pos, radius, inv_m, inv_I);
-    else k_pair_emit<3><<<gb, CD_BLOCK, 0, s>>>(g, w, pos, radius, inv_m, inv_I);
+    if (g.dim == 2) k_pair_emit<2><<<gb, CD_BLOCK, 0, s>>>(g, w, pos, radius);
+    else k_pair_emit<3><<<gb, CD_BLOCK, 0, s>>>(g, w, pos, radius);
     ++*nl;
     int gc = grid_for(g.cap);
-    if (g.dim == 2) k_warm_match<2><<<gc, CD_BLOCK, 0, s>>>(w, warm, pw);
-    else k_warm_match<3><<<gc, CD_BLOCK, 0, s>>>(w, warm, pw);
+    if (g.dim == 2) k_geometry_warm<2><<<gc, CD_BLOCK, 0, s>>>(g, w, pos, radius, inv_m, inv_I, warm, pw);
+    else k_geometry_warm<3><<<gc, CD_BLOCK, 0, s>>>(g, w, pos, radius, inv_m, inv_I, warm, pw);
     ++*nl;
     k_commit<<<gc, CD_BLOCK, 0, s>>>(w, pw); ++*nl;
     k_set_nc<<<1, 1, 0, s>>>(w.ctrl); ++*nl;
