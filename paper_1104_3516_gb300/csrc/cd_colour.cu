@@ -106,6 +106,30 @@ __device__ __forceinline__ void jp_append(int* list, int* len, int c, bool take)
     if (take) list[base + __popc(m & ((1u << lane) - 1u))] = c;
 }
 
+// Appends each lane's up to four entries c[u] (take[u]) with one atomic per
+// warp: the lane's offset is the exclusive prefix sum of the lanes' counts.
+__device__ __forceinline__ void jp_append4(int* list, int* len, const int (&c)[4], const bool (&take)[4])
+{
+    const int lane = threadIdx.x & 31;
+    int k = 0;
+#pragma unroll
+    for (int u = 0; u < 4; ++u) k += take[u] ? 1 : 0;
+    int incl = k;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const int y = __shfl_up_sync(0xffffffffu, incl, o);
+        if (lane >= o) incl += y;
+    }
+    const int total = __shfl_sync(0xffffffffu, incl, 31);
+    if (total == 0) return;
+    int base = 0;
+    if (lane == 31) base = atomicAdd(len, total);
+    base = __shfl_sync(0xffffffffu, base, 31) + incl - k;
+#pragma unroll
+    for (int u = 0; u < 4; ++u)
+        if (take[u]) list[base++] = c[u];
+}
+
 __global__ void __launch_bounds__(CD_SWEEP_THREADS) k_jp(CdGeom g, CdWork w, unsigned long long* prio,
                                                           int* round_cnt)
 {
@@ -117,7 +141,6 @@ __global__ void __launch_bounds__(CD_SWEEP_THREADS) k_jp(CdGeom g, CdWork w, uns
     const int tid = blockIdx.x * blockDim.x + threadIdx.x;
     const int stride = gridDim.x * blockDim.x;
     int* cnt = w.rep_flag;
-    int* lists[2] = {w.rep_list, w.rep_path};
     for (int c = tid; c < nc; c += stride) {
         int2 ab = w.pairs[c];
         unsigned long long h;
@@ -165,17 +188,20 @@ __global__ void __launch_bounds__(CD_SWEEP_THREADS) k_jp(CdGeom g, CdWork w, uns
             }
             cnt[c] = k;
         }
-        jp_append(lists[0], &round_cnt[0], c, c < nc && k == 0);   // round 0's list
+        jp_append(w.rep_list, &round_cnt[0], c, c < nc && k == 0);   // round 0's list
     }
     if (!cd_grid_sync(ctrl, nb, epoch)) return;
     for (int round = 0; round < (1 << 20); ++round) {
-        const int cur = round & 1, nxt = cur ^ 1;
+        // even rounds read rep_list and fill rep_path, odd rounds the reverse
+        // (selected, not indexed: an indexed pair of pointers lives in local memory)
+        int* const list_cur = (round & 1) ? w.rep_path : w.rep_list;
+        int* const list_nxt = (round & 1) ? w.rep_list : w.rep_path;
         const int len = cd_ld_volatile_int(&round_cnt[round % 3]);
         if (len == 0) break;
         if (tid == 0) round_cnt[(round + 2) % 3] = 0;
         for (int i0 = blockIdx.x * blockDim.x + (threadIdx.x & ~31); i0 < len; i0 += stride) {
             const int i = i0 + (threadIdx.x & 31);
-            const int c = (i < len) ? lists[cur][i] : -1;
+            const int c = (i < len) ? list_cur[i] : -1;
             int2 ab = make_int2(0, 0);
             unsigned long long pc = 0ULL, kc = 0ULL;
             if (c >= 0) {
@@ -210,11 +236,13 @@ __global__ void __launch_bounds__(CD_SWEEP_THREADS) k_jp(CdGeom g, CdWork w, uns
 #pragma unroll
                     for (int u = 0; u < 4; ++u)
                         v[u] = hi[u] ? cd_ld_volatile_int(&w.colour[d[u]]) : (lo[u] ? atomicSub(&cnt[d[u]], 1) : 0);
+                    bool rel[4];
 #pragma unroll
                     for (int u = 0; u < 4; ++u) {
                         if (hi[u] && v[u] >= 0) used |= 1ULL << v[u];
-                        jp_append(lists[nxt], &round_cnt[(round + 1) % 3], d[u], lo[u] && v[u] == 1);
+                        rel[u] = lo[u] && v[u] == 1;   // its last higher-priority neighbour: next round
                     }
+                    jp_append4(list_nxt, &round_cnt[(round + 1) % 3], d, rel);
                 }
             }
             int top = 0;
