@@ -288,23 +288,27 @@ __device__ __forceinline__ double grid_total(const double* part, int nblocks, do
 __device__ __forceinline__ int test_values(int crit) { return crit == CD_CONV_LOCAL ? 3 : 1; }
 
 // The convergence test after a sweep (tests I and II) from the block
-// partials part[0 .. 3 nb): warp 0 sums them (the order of grid_total) and
-// thread 0 decides; the result reaches the block through shared memory
-// (s_b3, three doubles), so the FP64 divisions run once per block.
+// partials part[0 .. 3 nb): the block's last warp sums them (the order of
+// grid_total) and its lane 0 decides; the result reaches the block through
+// shared memory (s_b3, three doubles), so the FP64 divisions run once per
+// block.  The last warp holds the fewest contacts of a colour phase (they
+// are dealt from thread 0 up), so the other warps' work before the block
+// barrier below (the next sweep's first updates, staged) overlaps the test.
 __device__ __forceinline__ void sweep_test(const double* part, int nb, int nc, int crit, double alpha,
                                            double ravg_prev, double& ravg, double& resid, int& converged,
                                            double* s_b3)
 {
-    if (threadIdx.x < 32) {
+    if ((threadIdx.x >> 5) == (blockDim.x >> 5) - 1) {
+        const int lane = threadIdx.x & 31;
         const bool local = (crit == CD_CONV_LOCAL);
         double x = 0.0, xr = 0.0, xb = 0.0;
-        for (int b = threadIdx.x; b < nb; b += 32) {
+        for (int b = lane; b < nb; b += 32) {
             x += part[b];
             if (local) { xr += part[nb + b]; xb += part[2 * nb + b]; }
         }
         x = warp_sum(x);
         if (local) { xr = warp_sum(xr); xb = warp_sum(xb); }
-        if (threadIdx.x == 0) {
+        if (lane == 0) {
             const double ra = x / (double)nc;
             const double den = ra + ravg_prev;
             double rs;
@@ -557,34 +561,61 @@ __device__ __forceinline__ void wall_vel2(const CdGeom& g, const CdWork& w, int 
 // DEFER (FP64): the result's pabs is |P| of the thread's previous update,
 // taken from its (P_n, P_t) `pend` after this update's velocity loads are
 // issued; pn, pt hold this update's impulse.
+// A 2D update computed but not yet stored: the two velocity records and the
+// impulse, where they go.
+template <typename T>
+struct Staged2 {
+    typename Vec<T>::V4 va, vb;
+    typename Vec<T>::V2 P;
+    int ia, ib, pos;
+    bool wall, store_p;
+};
+
+template <typename T, bool VIEWS = false, bool DEFER = false>
+__device__ __forceinline__ UpdOut stage2d(const CdGeom& g, const CdWork& w, int pos, const Rec<2, T>& r,
+                                          bool apply_only, int crit, double alpha, double ravg_prev, double2 pend,
+                                          Staged2<T>& st)
+{
+    typedef typename Vec<T>::V4 T4;
+    const T4* V = (const T4*)w.V;
+    st.ia = VIEWS ? r.vab.x : r.ab.x;
+    st.ib = VIEWS ? r.vab.y : r.ab.y;
+    st.pos = pos;
+    st.store_p = !apply_only;
+    st.wall = !cd_is_body(g, r.ab.y);   // kinematic wall
+    st.va = V[st.ia];
+    if (!st.wall) st.vb = V[st.ib];
+    else wall_vel2<T>(g, w, r.ab.y, st.vb);
+    const double prev = DEFER ? abs_of_pair(pend.x, pend.y) : 0.0;
+    UpdOut o = core2d<T, DEFER>(g, r, st.va, st.vb, st.wall, apply_only, crit, alpha, ravg_prev, st.P);
+    if constexpr (DEFER) o.pabs = prev;
+    if (!st.wall && r.ab.y >= g.n) {
+        // a force-controlled wall moves along its normal only
+        if (((r.ab.y - g.n) >> 1) == 0) st.vb.y = (T)0; else st.vb.x = (T)0;
+        st.vb.z = (T)0;
+    }
+    return o;
+}
+
+template <typename T>
+__device__ __forceinline__ void commit2d(const CdWork& w, const Staged2<T>& st)
+{
+    typedef typename Vec<T>::V4 T4;
+    typedef typename Vec<T>::V2 T2;
+    T4* V = (T4*)w.V;
+    V[st.ia] = st.va;
+    if (!st.wall) V[st.ib] = st.vb;
+    if (st.store_p) ((T2*)w.c_P)[st.pos] = st.P;
+}
+
 template <typename T, bool VIEWS = false, bool DEFER = false>
 __device__ __forceinline__ UpdOut apply2d(const CdGeom& g, const CdWork& w, int pos, const Rec<2, T>& r,
                                           bool apply_only, int crit, double alpha, double ravg_prev,
                                           double2 pend = make_double2(0.0, 0.0))
 {
-    typedef typename Vec<T>::V4 T4;
-    typedef typename Vec<T>::V2 T2;
-    T4* V = (T4*)w.V;
-    const int ia = VIEWS ? r.vab.x : r.ab.x, ib = VIEWS ? r.vab.y : r.ab.y;
-    const bool wall = !cd_is_body(g, r.ab.y);   // kinematic wall
-    T4 va = V[ia];
-    T4 vb;
-    if (!wall) vb = V[ib];
-    else wall_vel2<T>(g, w, r.ab.y, vb);
-    const double prev = DEFER ? abs_of_pair(pend.x, pend.y) : 0.0;
-    T2 Pnew;
-    UpdOut o = core2d<T, DEFER>(g, r, va, vb, wall, apply_only, crit, alpha, ravg_prev, Pnew);
-    if constexpr (DEFER) o.pabs = prev;
-    V[ia] = va;
-    if (!wall) {
-        if (r.ab.y >= g.n) {
-            // a force-controlled wall moves along its normal only
-            if (((r.ab.y - g.n) >> 1) == 0) vb.y = (T)0; else vb.x = (T)0;
-            vb.z = (T)0;
-        }
-        V[ib] = vb;
-    }
-    if (!apply_only) ((T2*)w.c_P)[pos] = Pnew;
+    Staged2<T> st;
+    const UpdOut o = stage2d<T, VIEWS, DEFER>(g, w, pos, r, apply_only, crit, alpha, ravg_prev, pend, st);
+    commit2d<T>(w, st);
     return o;
 }
 
@@ -754,7 +785,7 @@ template <int DIM, typename T, int MODE>
 __device__ __forceinline__ void colour_phase(const CdGeom& g, const CdWork& w, const int* s_off, int k, int knext,
                                              int tid, int stride, Rec<DIM, T>& nxt, bool apply_only, int crit,
                                              double alpha, double ravg_prev, double (&acc)[3], double2& pend,
-                                             const MgInfo& mg)
+                                             const MgInfo& mg, bool skip_first = false)
 {
     constexpr bool MIXED = (MODE == CD_SWEEP_MIXED);
     constexpr bool VIEWS = (MODE == CD_SWEEP_DOMAINS);
@@ -796,7 +827,9 @@ __device__ __forceinline__ void colour_phase(const CdGeom& g, const CdWork& w, c
     int p = sp.p;
     const bool mixed = MIXED && !apply_only;   // parallel contacts were done in their own phase
     if (p < end) {
-        if (!(mixed && cd_is_parallel(g.par_p, g.seed, cd_key(nxt.ab.x, nxt.ab.y), mg.draw))) {
+        // skip_first: this thread's first update of the phase was staged and
+        // stored before the phase (the first colour of a sweep, see k_sweep)
+        if (!skip_first && !(mixed && cd_is_parallel(g.par_p, g.seed, cd_key(nxt.ab.x, nxt.ab.y), mg.draw))) {
             UpdOut o = apply_rec<DIM, T, VIEWS, DEFER>(g, w, p, nxt, apply_only, crit, alpha, ravg_prev, pend);
             acc[0] += o.pabs;
             if (DEFER) pend = make_double2(o.pn, o.pt);
@@ -1098,10 +1131,20 @@ k_sweep(CdGeom g, CdWork w, int crit, double alpha, int max_sweeps)
         ravg_prev = grid_total(w.partials, nb, &s_bc) / (double)nc;
         ravg = ravg_prev;
 
+        // 2D plain and merged schedules under the global tests: while the last
+        // warp of each block runs the convergence test of sweep j, the other
+        // threads compute their first update of sweep j + 1 (colour 0, its
+        // record prefetched) into registers and store it only if the test
+        // says continue.  The same updates in the same order: bits unchanged.
+        constexpr bool SPEC_OK = (DIM == 2) && !MIXED && !VIEWS;
+        const bool spec_on = SPEC_OK && crit != CD_CONV_LOCAL && !(mg.on && mg.klast == 0);
+        bool spec_done = false;   // this thread's first colour-0 update of the coming sweep is stored
+        double carry = 0.0;       // its residual term (the first term of the sweep's sum)
         while (!converged && sweeps < max_sweeps) {
             const int buf = (sweeps & 1) ? 0 : 1;   // alternate with the buffer of the previous sweep
             double* part = w.partials + (size_t)buf * 3 * nb;
-            double a3[3] = {0.0, 0.0, 0.0};
+            double a3[3] = {carry, 0.0, 0.0};
+            carry = 0.0;
             const bool mixed = MIXED;
             if (MIXED && g.par_redraw) mg.draw = sweeps;   // this iteration step's parallel subset
             if (mixed) {
@@ -1123,7 +1166,7 @@ k_sweep(CdGeom g, CdWork w, int crit, double alpha, int max_sweeps)
                 // no prefetch inside the phase: it is issued after the barrier arrival
                 // below, so that the arriving thread's fence does not wait for it
                 colour_phase<DIM, T, MODE>(g, w, s_off, k, -1, tid, stride, nxt, false, crit, alpha, ravg_prev, a3,
-                                           pend, mg);
+                                           pend, mg, k == 0 && spec_done);
                 if (k == K - 1) {
                     // (a thread without a pending impulse adds nothing: skip the FP64 work)
                     if ((__double_as_longlong(pend.x) | __double_as_longlong(pend.y)) != 0)
@@ -1151,7 +1194,34 @@ k_sweep(CdGeom g, CdWork w, int crit, double alpha, int max_sweeps)
                 if (!cd_grid_sync(ctrl, nb, epoch)) return;
             }
             ++sweeps;
-            sweep_test(part, nb, nc, crit, alpha, ravg_prev, ravg, resid, converged, s_red[0]);
+            spec_done = false;
+            if constexpr (SPEC_OK) {
+                constexpr bool DEFER = std::is_same<T, double>::value;
+                Staged2<T> st;
+                bool staged = false;
+                if (spec_on && sweeps < max_sweeps) {
+                    const CdSpan s0 = cd_colour_span(s_off[0], s_off[1]);
+                    if (s0.p < s0.end) {
+                        // pend is (0, 0) here (the last phase added it to the sum), so
+                        // the staged update's own residual term is 0 under DEFER
+                        (void)stage2d<T, false, DEFER>(g, w, s0.p, nxt, false, crit, alpha, ravg_prev, pend, st);
+                        staged = true;
+                    }
+                }
+                sweep_test(part, nb, nc, crit, alpha, ravg_prev, ravg, resid, converged, s_red[0]);
+                if (staged && !converged) {
+                    commit2d<T>(w, st);
+                    spec_done = true;
+                    if constexpr (DEFER) {
+                        pend = make_double2((double)st.P.x, (double)st.P.y);   // its |P| joins the sum later
+                    } else {
+                        // |P| of the update, as core2d takes it in this precision
+                        carry = abs_of_sq<T>((double)fma_of<T>(st.P.y, st.P.y, mul_of<T>(st.P.x, st.P.x)));
+                    }
+                }
+            } else {
+                sweep_test(part, nb, nc, crit, alpha, ravg_prev, ravg, resid, converged, s_red[0]);
+            }
             ravg_prev = ravg;
         }
     }
