@@ -116,6 +116,7 @@ static size_t layout(cd_system* s, char* base, CdWork* w)
     t.cell_pid = L.take<int>(base, n);
     t.pcnt = L.take<int>(base, n + 1);
     t.poff = L.take<int>(base, n + 1);
+    t.poff_prev = L.take<int>(base, n + 1);
     t.cand = L.take<int>(base, n * CD_CAND);
     t.pf = L.take<float4>(base, n);
     t.scan_tmp = L.take<int>(base, cd_scan_tmp_ints((int)scan_max) + 32);
@@ -441,7 +442,12 @@ static cd_status create_impl(const cd_params* params, int64_t npk, const int64_t
     g.seed = p.seed;
     g.npk = (int)npk;
     for (int k = 0; k < 18; ++k) g.wall_vel[k] = p.wall_vel[k];
-    const double ell = 2.0 * rmax + p.delta;   // Sec. 3.1: cell side l = 2 r_max + delta
+    // Sec. 3.1: cell side l = 2 r_max + delta, here longer by a relative 1e-9:
+    // rounding may file a particle within a few ulps of a cell face in the
+    // neighbouring cell, and a side longer than any contact distance by more
+    // than that keeps every contact within the cells next to its particles'
+    // (for grids of up to 1e6 cells per axis)
+    const double ell = (2.0 * rmax + p.delta) * (1.0 + 1e-9);
     double ncell_total = 0.0;
     s->pk_host.resize((size_t)npk);
     s->pk_wall0.resize((size_t)(6 * npk));
@@ -462,12 +468,13 @@ static cd_status create_impl(const cd_params* params, int64_t npk, const int64_t
                 if (m > 1.0e6) m = 1.0e6;
                 pk.ncell[k] = (int)m;
                 pk.cs[k] = pk.L[k] / m;
+                pk.inv_cs[k] = 1.0 / pk.cs[k];
                 if (pk.periodic[k] && pk.ncell[k] < 3) {
                     delete s;
                     return fail(nullptr, CD_ERR_INVALID_ARG, "a periodic axis needs at least 3 cells (box >= 3 l)");
                 }
             } else {
-                pk.lo[k] = 0.0; pk.hi[k] = 1.0; pk.L[k] = 1.0; pk.ncell[k] = 1; pk.cs[k] = 1.0;
+                pk.lo[k] = 0.0; pk.hi[k] = 1.0; pk.L[k] = 1.0; pk.ncell[k] = 1; pk.cs[k] = 1.0; pk.inv_cs[k] = 1.0;
             }
             cells *= pk.ncell[k];
         }
@@ -489,7 +496,7 @@ static cd_status create_impl(const cd_params* params, int64_t npk, const int64_t
             g.gravity[k] = p.gravity[k];
             g.periodic[k] = p0.periodic[k];
             g.lo[k] = p0.lo[k]; g.hi[k] = p0.hi[k]; g.L[k] = p0.L[k];
-            g.ncell[k] = p0.ncell[k]; g.cs[k] = p0.cs[k];
+            g.ncell[k] = p0.ncell[k]; g.cs[k] = p0.cs[k]; g.inv_cs[k] = p0.inv_cs[k];
         }
     }
     if (npk > 1) {
@@ -1071,6 +1078,9 @@ static cd_status ckpt_copy(cd_system* s, void* buf, size_t bytes, bool save)
         else CD_CUDA(s, cudaMemcpyAsync(q.dev, b + q.off, q.len, cudaMemcpyDeviceToDevice, s->stream));
     }
     if (!save) {
+        // the loaded set's per-particle offsets are not kept: the next warm
+        // start searches the whole set
+        CD_CUDA(s, cudaMemsetAsync(&s->w.ctrl->prev_offsets, 0, sizeof(int), s->stream));
         s->has_contacts = 1;
         s->tape_head = 0;
         s->tape_count = 0;

@@ -131,7 +131,7 @@ cudaError_t cd_scan_exclusive(const int* in, int* out, int n, int* tmp, int* tot
 // so particles of different packings are never in neighbouring cells.
 // ---------------------------------------------------------------------------
 struct GridV {
-    double lo[3], cs[3], L[3];
+    double lo[3], cs[3], inv_cs[3], L[3];
     int ncell[3], periodic[3];
     int base, wall_mask, pkid;
 };
@@ -143,25 +143,33 @@ __device__ __forceinline__ void grid_of(const CdGeom& g, const CdWork& w, int i,
         const CdPack& p = w.pk[b];
 #pragma unroll
         for (int k = 0; k < 3; ++k) {
-            v.lo[k] = p.lo[k]; v.cs[k] = p.cs[k]; v.L[k] = p.L[k];
+            v.lo[k] = p.lo[k]; v.cs[k] = p.cs[k]; v.inv_cs[k] = p.inv_cs[k]; v.L[k] = p.L[k];
             v.ncell[k] = p.ncell[k]; v.periodic[k] = p.periodic[k];
         }
         v.base = p.cell_base; v.wall_mask = p.wall_mask; v.pkid = b;
     } else {
 #pragma unroll
         for (int k = 0; k < 3; ++k) {
-            v.lo[k] = g.lo[k]; v.cs[k] = g.cs[k]; v.L[k] = g.L[k];
+            v.lo[k] = g.lo[k]; v.cs[k] = g.cs[k]; v.inv_cs[k] = g.inv_cs[k]; v.L[k] = g.L[k];
             v.ncell[k] = g.ncell[k]; v.periodic[k] = g.periodic[k];
         }
         v.base = 0; v.wall_mask = g.wall_mask; v.pkid = 0;
     }
 }
 
+// Cell index along axis k: floor((x - lo) / cs) clamped to the grid, with
+// the quotient taken as a product by 1 / cs and rounded down to an integer
+// in one conversion (a correctly rounded FP64 division is ~10 FP64
+// instructions).  Either rounding may put a particle within a few ulps of a
+// cell face into the neighbouring cell; no contact is lost: a contact is
+// closer than r_a + r_b + delta <= 2 r_max + delta, the cell side is longer
+// than that by a relative 1e-9 (far more than the misplacement, on grids of
+// up to 1e6 cells per axis), and the pair walk visits every cell next to the
+// one a particle is filed in.  (A NaN coordinate converts to 0: cell 0.)
 __device__ __forceinline__ int cell_axis(const GridV& v, int k, double x)
 {
-    double q = floor(__ddiv_rn(__dsub_rn(x, v.lo[k]), v.cs[k]));
-    int c = (q < 0.0) ? 0 : (q > (double)(v.ncell[k] - 1) ? v.ncell[k] - 1 : (int)q);
-    return c;
+    const int q = __double2int_rd(__dmul_rn(__dsub_rn(x, v.lo[k]), v.inv_cs[k]));
+    return q < 0 ? 0 : (q > v.ncell[k] - 1 ? v.ncell[k] - 1 : q);
 }
 
 template <int DIM>
@@ -733,7 +741,13 @@ __global__ void k_geometry_warm(CdGeom g, CdWork w, const double* __restrict__ p
         double out[4] = {0.0, 0.0, 0.0, 0.0};
         if (warm && nold > 0) {
             const unsigned long long key = cd_key(ab.x, ab.y);
+            // the old set is in key order, so particle a's old contacts are the
+            // range its offsets give (when kept), else somewhere in the whole set
             int lo = 0, hi = nold - 1, o = -1;
+            if (ctrl->prev_offsets) {
+                lo = w.poff_prev[ab.x];
+                hi = w.poff_prev[ab.x + 1] - 1;
+            }
             while (lo <= hi) {
                 int mid = lo + ((hi - lo) >> 1);
                 int2 m = w.pairs[mid];
@@ -790,7 +804,9 @@ __global__ void k_given_impulses(CdWork w, int nc, const double* __restrict__ im
         w.Pk_nx[i] = imp ? imp[i] : 0.0;
 }
 
-__global__ void k_commit(CdWork w, int pw)
+// The new set becomes the current one; with `n` > 0 (a detected set) the
+// per-particle offsets of the detection are kept for the next warm start.
+__global__ void k_commit(CdWork w, int pw, int n)
 {
     CdCtrl* ctrl = w.ctrl;
     if (ctrl->skip) return;
@@ -799,12 +815,17 @@ __global__ void k_commit(CdWork w, int pw)
         w.pairs[c] = w.pairs_nx[c];
         for (int k = 0; k < pw; ++k) w.Pk[pw * c + k] = w.Pk_nx[pw * c + k];
     }
+    if (w.poff_prev && n > 0)
+        for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n + 1; i += gridDim.x * blockDim.x)
+            w.poff_prev[i] = w.poff[i];
 }
 
-__global__ void k_set_nc(CdCtrl* ctrl)
+// by_particle: the new set's per-particle offsets are in poff_prev.
+__global__ void k_set_nc(CdCtrl* ctrl, int by_particle)
 {
     if (ctrl->skip) return;
     ctrl->nc = ctrl->nc_needed;
+    ctrl->prev_offsets = by_particle;
 }
 
 static int grid_for(int n, int per_block = CD_BLOCK)
@@ -846,8 +867,8 @@ cudaError_t cd_launch_detect(const CdGeom& g, const CdWork& w, const double* pos
     if (g.dim == 2) k_geometry_warm<2><<<gc, CD_BLOCK, 0, s>>>(g, w, pos, radius, inv_m, inv_I, warm, pw);
     else k_geometry_warm<3><<<gc, CD_BLOCK, 0, s>>>(g, w, pos, radius, inv_m, inv_I, warm, pw);
     ++*nl;
-    k_commit<<<gc, CD_BLOCK, 0, s>>>(w, pw); ++*nl;
-    k_set_nc<<<1, 1, 0, s>>>(w.ctrl); ++*nl;
+    k_commit<<<gc, CD_BLOCK, 0, s>>>(w, pw, g.n); ++*nl;
+    k_set_nc<<<1, 1, 0, s>>>(w.ctrl, w.poff_prev != nullptr); ++*nl;
     return cudaGetLastError();
 }
 
@@ -863,7 +884,7 @@ cudaError_t cd_launch_set_contacts(const CdGeom& g, const CdWork& w, const doubl
         ++*nl;
     }
     k_given_impulses<<<grid_for(nc * pw > 0 ? nc * pw : 1), CD_BLOCK, 0, s>>>(w, nc, impulses, pw); ++*nl;
-    k_commit<<<gc, CD_BLOCK, 0, s>>>(w, pw); ++*nl;
-    k_set_nc<<<1, 1, 0, s>>>(w.ctrl); ++*nl;
+    k_commit<<<gc, CD_BLOCK, 0, s>>>(w, pw, 0); ++*nl;   // a caller-given list: no offsets
+    k_set_nc<<<1, 1, 0, s>>>(w.ctrl, 0); ++*nl;
     return cudaGetLastError();
 }

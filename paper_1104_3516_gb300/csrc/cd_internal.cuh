@@ -30,7 +30,7 @@ struct CdCtrl {
     int error;                      // CDE_* (timeouts, colour overflow)
     int skip;                       // 1: skip all remaining work of this call
     int uncoloured;
-    int pad0;
+    int prev_offsets;               // 1: poff_prev holds the per-particle offsets of the current set
     long long sweeps;               // last solve
     long long converged;
     double residual;
@@ -69,6 +69,7 @@ struct CdPack {
     double hi[3];
     double L[3];
     double cs[3];
+    double inv_cs[3];               // 1 / cs (cell assignment)
     int ncell[3];
     int cell_base;      // first global cell id of this packing
     int periodic[3];
@@ -96,6 +97,7 @@ struct CdWork {
     int* cand;          // n * CD_CAND: partners b > a found by the counting pass (first CD_CAND, found order)
     float4* pf;         // n: (x, y, z, r) in single precision for the pair pre-filter (null: exact test only)
     int* poff;          // n + 1
+    int* poff_prev;     // n + 1: poff of the current set (null: not kept)
     int* scan_tmp;      // block sums of the scans
     // contacts, key order
     int2* pairs;        // current set
@@ -247,6 +249,7 @@ struct CdGeom {
     double hi[3];
     double L[3];
     double cs[3];       // cell side per axis
+    double inv_cs[3];   // 1 / cs (cell assignment)
     double delta;
     double dt;
     double mu;

@@ -159,7 +159,7 @@ extern "C" cd_status cd_detect_contacts_noalloc(const cd_params* params, int64_t
     g.rotations = (int)p.rotations;
     g.seed = p.seed;
     g.npk = 1;
-    const double ell = 2.0 * rmax + p.delta;
+    const double ell = (2.0 * rmax + p.delta) * (1.0 + 1e-9);   // as in cd_create_system
     long long ncell = 1;
     for (int k = 0; k < 3; ++k) {
         g.periodic[k] = (k < p.dim) ? (int)p.periodic[k] : 0;
@@ -172,10 +172,11 @@ extern "C" cd_status cd_detect_contacts_noalloc(const cd_params* params, int64_t
             if (m > (double)CD_NOALLOC_MAX_CELLS) m = (double)CD_NOALLOC_MAX_CELLS;
             g.ncell[k] = (int)m;
             g.cs[k] = g.L[k] / m;
+            g.inv_cs[k] = 1.0 / g.cs[k];
             if (g.periodic[k] && g.ncell[k] < 3)
                 return na_error(CD_ERR_INVALID_ARG, "a periodic axis needs at least 3 cells (box >= 3 l)");
         } else {
-            g.lo[k] = 0.0; g.hi[k] = 1.0; g.L[k] = 1.0; g.ncell[k] = 1; g.cs[k] = 1.0;
+            g.lo[k] = 0.0; g.hi[k] = 1.0; g.L[k] = 1.0; g.ncell[k] = 1; g.cs[k] = 1.0; g.inv_cs[k] = 1.0;
         }
         ncell *= g.ncell[k];
     }
