@@ -313,6 +313,29 @@ def test_given_contact_list_and_warm_impulses():
     assert float(np.abs(s["v"].reshape(-1) - v).max()) <= FP64_TOL * float(np.abs(v).max())
 
 
+@pytest.mark.parametrize("name", ["settling_discs", "sphere_gas"])
+def test_warm_start_by_particle_equals_the_whole_set_search(name):
+    """The warm start looks each new contact up among its first particle's
+    contacts of the previous set (the detection's offsets, kept at commit);
+    after a checkpoint load it searches the whole set instead.  A system that
+    reloads its own checkpoint before every step (so that every warm start
+    takes the whole-set search) steps bit for bit like one that does not."""
+    from paper_1104_3516_gb300 import cd
+    wl = CASES[name]
+    a = gpu_system(wl, criterion=cd.CD_CONV_GLOBAL_REL, max_sweeps=200)
+    b = gpu_system(wl, criterion=cd.CD_CONV_GLOBAL_REL, max_sweeps=200)
+    for _ in range(4):
+        a.step(1)
+        b.load_checkpoint(b.save_checkpoint())
+        b.step(1)
+    ca, cb = a.contacts(), b.contacts()
+    assert len(ca["pairs"]) > 0
+    assert np.array_equal(ca["pairs"], cb["pairs"])
+    assert np.array_equal(ca["impulse"], cb["impulse"])
+    sa, sb = a.state(), b.state()
+    assert np.array_equal(sa["x"], sb["x"]) and np.array_equal(sa["v"], sb["v"])
+
+
 # --- mixed parallel / sequential update (Sec. 2.3) -------------------------------
 
 @pytest.mark.parametrize("p", [0.3, 1.0])
