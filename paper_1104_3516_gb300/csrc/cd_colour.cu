@@ -472,7 +472,9 @@ static cudaError_t launch_repair(const CdGeom& g, const CdWork& w, int gc, cudaS
     k_rep_scan_colours<<<gm, CD_BLOCK, 0, s>>>(g, w);
     k_rep_flag<<<gc, CD_BLOCK, 0, s>>>(g, w);
     *nl += 3;
-    if ((e = cd_scan_exclusive(w.rep_flag, w.rep_pos, g.cap + 1, w.scan_tmp, nullptr, s, nl)) != cudaSuccess)
+    // the live contacts only (their count read on the device)
+    if ((e = cd_scan_exclusive(w.rep_flag, w.rep_pos, g.cap + 1, w.scan_tmp, nullptr, s, nl, &w.ctrl->nc)) !=
+        cudaSuccess)
         return e;
     k_rep_fill<<<gc, CD_BLOCK, 0, s>>>(w);
     // one warp per packing: a plain system's repair is one sequential walk
@@ -597,11 +599,17 @@ cudaError_t cd_launch_pk_ranges(const CdGeom& g, const CdWork& w, cudaStream_t s
     return cudaGetLastError();
 }
 
+// Blocks per SM of the cooperative colouring grid (k_jp, and the merge's
+// chain labelling, which runs on the same grid).
+#define CD_COLOUR_PER_SM 1
+
 int cd_colour_max_blocks(int num_sms)
 {
     int per_sm = 0;
     if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_jp, CD_SWEEP_THREADS, 0) != cudaSuccess) return 0;
-    if (per_sm > 1) per_sm = 1;   // one block per SM keeps the barrier cheap
+    const int mg = cd_merge_label_blocks_per_sm();
+    if (mg > 0 && mg < per_sm) per_sm = mg;
+    if (per_sm > CD_COLOUR_PER_SM) per_sm = CD_COLOUR_PER_SM;
     return per_sm * num_sms;
 }
 

@@ -15,12 +15,29 @@
 #include "cd_internal.cuh"
 
 // ---------------------------------------------------------------------------
-// Exclusive scan of int32 (three passes: block sums, scan of the sums, block
-// scans).  `total_dst` (device) receives the sum of all inputs if non-null.
+// Exclusive scan of int32: the block sums of the tiles, then every block
+// scans its tile and adds the prefix of the tiles before it.  Up to
+// SCAN_FUSE tiles each block sums that prefix itself from the block sums
+// (read by all blocks from L2; integer sums, so the order is immaterial);
+// beyond, a single block scans the block sums in between (three passes).
+// `n_dev` (device, optional) clips the scan at run time to its first
+// min(*n_dev + 1, n) entries (the rest of `out` is left untouched), for
+// arrays sized by capacity of which only the live contacts count.
+// `total_dst` (device) receives the sum of the scanned inputs if non-null.
+// In place (in == out) is allowed: a tile is read and written by the same
+// threads.
 // ---------------------------------------------------------------------------
 #define SCAN_T 256
 #define SCAN_PER 4
 #define SCAN_TILE (SCAN_T * SCAN_PER)
+#define SCAN_FUSE 2048
+
+__device__ __forceinline__ int scan_extent(int n, const int* n_dev)
+{
+    if (!n_dev) return n;
+    const int c = *n_dev + 1;
+    return (c < n) ? c : n;
+}
 
 __device__ __forceinline__ int warp_incl_scan(int v)
 {
@@ -54,9 +71,11 @@ __device__ __forceinline__ int block_excl_scan(int v, int* total)
     return r;
 }
 
-__global__ void k_scan_sums(const int* __restrict__ in, int n, int* __restrict__ sums)
+__global__ void k_scan_sums(const int* __restrict__ in, int n, const int* n_dev, int* __restrict__ sums)
 {
+    n = scan_extent(n, n_dev);
     int base = blockIdx.x * SCAN_TILE;
+    if (base >= n) return;
     int s = 0;
 #pragma unroll
     for (int k = 0; k < SCAN_PER; ++k) {
@@ -68,8 +87,12 @@ __global__ void k_scan_sums(const int* __restrict__ in, int n, int* __restrict__
     if (threadIdx.x == 0) sums[blockIdx.x] = tot;
 }
 
-__global__ void k_scan_top(int* sums, int nb, int* total_dst)
+// Three-pass form only: one block turns the block sums into their exclusive
+// prefixes.
+__global__ void k_scan_top(int* sums, int n, const int* n_dev, int* total_dst)
 {
+    n = scan_extent(n, n_dev);
+    const int nb = (n + SCAN_TILE - 1) / SCAN_TILE;
     __shared__ int carry_s;
     if (threadIdx.x == 0) carry_s = 0;
     __syncthreads();
@@ -87,8 +110,23 @@ __global__ void k_scan_top(int* sums, int nb, int* total_dst)
     if (threadIdx.x == 0 && total_dst) *total_dst = carry_s;
 }
 
-__global__ void k_scan_apply(const int* in, int n, const int* __restrict__ sums, int* out)
+// fused: the prefix of this tile from the raw block sums (else sums already
+// holds the prefixes)
+__global__ void k_scan_apply(const int* in, int n, const int* n_dev, const int* __restrict__ sums, int fused,
+                             int* out, int* total_dst)
 {
+    n = scan_extent(n, n_dev);
+    const int nb = (n + SCAN_TILE - 1) / SCAN_TILE;
+    if ((int)blockIdx.x >= nb) return;
+    __shared__ int prefix;
+    if (fused) {
+        int p = 0;
+        for (int j = threadIdx.x; j < (int)blockIdx.x; j += SCAN_T) p += sums[j];
+        block_excl_scan(p, &prefix);
+    } else {
+        if (threadIdx.x == 0) prefix = sums[blockIdx.x];
+        __syncthreads();
+    }
     int base = blockIdx.x * SCAN_TILE + threadIdx.x * SCAN_PER;
     int v[SCAN_PER];
     int s = 0;
@@ -99,13 +137,14 @@ __global__ void k_scan_apply(const int* in, int n, const int* __restrict__ sums,
         s += v[k];
     }
     __shared__ int tot;
-    int ex = block_excl_scan(s, &tot) + sums[blockIdx.x];
+    int ex = block_excl_scan(s, &tot) + prefix;
 #pragma unroll
     for (int k = 0; k < SCAN_PER; ++k) {
         int i = base + k;
         if (i < n) out[i] = ex;
         ex += v[k];
     }
+    if (fused && total_dst && (int)blockIdx.x == nb - 1 && threadIdx.x == 0) *total_dst = prefix + tot;
 }
 
 size_t cd_scan_tmp_ints(int n)
@@ -114,14 +153,18 @@ size_t cd_scan_tmp_ints(int n)
 }
 
 cudaError_t cd_scan_exclusive(const int* in, int* out, int n, int* tmp, int* total_dst, cudaStream_t stream,
-                              int* nl)
+                              int* nl, const int* n_dev)
 {
     if (n <= 0) return cudaSuccess;
     int nb = (n + SCAN_TILE - 1) / SCAN_TILE;
-    k_scan_sums<<<nb, SCAN_T, 0, stream>>>(in, n, tmp);
-    k_scan_top<<<1, SCAN_T, 0, stream>>>(tmp, nb, total_dst);
-    k_scan_apply<<<nb, SCAN_T, 0, stream>>>(in, n, tmp, out);
-    *nl += 3;
+    const int fused = (nb <= SCAN_FUSE || n_dev) ? 1 : 0;
+    k_scan_sums<<<nb, SCAN_T, 0, stream>>>(in, n, n_dev, tmp);
+    if (!fused) {
+        k_scan_top<<<1, SCAN_T, 0, stream>>>(tmp, n, n_dev, total_dst);
+        ++*nl;
+    }
+    k_scan_apply<<<nb, SCAN_T, 0, stream>>>(in, n, n_dev, tmp, fused, out, total_dst);
+    *nl += 2;
     return cudaGetLastError();
 }
 

@@ -426,7 +426,7 @@ __device__ __forceinline__ CdSpan cd_colour_span(int lo, int hi)
 // Host-side launchers (defined in the .cu files), all on `stream`.
 // ---------------------------------------------------------------------------
 cudaError_t cd_scan_exclusive(const int* in, int* out, int n, int* tmp, int* total_dst, cudaStream_t stream,
-                              int* nl);
+                              int* nl, const int* n_dev = nullptr);
 size_t cd_scan_tmp_ints(int n);
 
 cudaError_t cd_launch_detect(const CdGeom& g, const CdWork& w, const double* pos, const double* radius,

@@ -240,7 +240,9 @@ static cudaError_t merge_pass(const CdGeom& g, const CdWork& w, int coop_blocks,
     }
     k_mg_size<<<gc, CD_BLOCK, 0, s>>>(g, w, M);
     ++*nl;
-    if ((e = cd_scan_exclusive(w.mg_w, w.mg_start, g.cap + 1, w.scan_tmp, nullptr, s, nl)) != cudaSuccess) return e;
+    // the live contacts only (their count read on the device)
+    if ((e = cd_scan_exclusive(w.mg_w, w.mg_start, g.cap + 1, w.scan_tmp, nullptr, s, nl, &w.ctrl->nc)) != cudaSuccess)
+        return e;
     k_mg_bucket<<<gc, CD_BLOCK, 0, s>>>(g, w, M);
     k_mg_decide<<<1, 1, 0, s>>>(w, M);
     *nl += 2;
