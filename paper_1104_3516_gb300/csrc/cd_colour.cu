@@ -600,7 +600,9 @@ cudaError_t cd_launch_pk_ranges(const CdGeom& g, const CdWork& w, cudaStream_t s
 }
 
 // Blocks per SM of the cooperative colouring grid (k_jp, and the merge's
-// chain labelling, which runs on the same grid).
+// chain labelling, which runs on the same grid).  One keeps the grid barrier
+// cheap: two made the 1e5-disc pile's colouring (29 rounds) 0.08 ms slower a
+// step and the 1e6-sphere gas's (17 rounds) 0.02 ms faster.
 #define CD_COLOUR_PER_SM 1
 
 int cd_colour_max_blocks(int num_sms)
