@@ -102,12 +102,12 @@ __device__ __forceinline__ void adj_update(const CdGeom& g, const CdWork& w, con
     if (!(P.x > thr)) return;                         // open
     const int2 ab = t.ab[p];
     const bool wall = ab.y >= g.n;
-    const double4 geo = t.geo[p];
+    const double4_16a geo = t.geo[p];
     const double nx = geo.x, ny = geo.y, mn = geo.w, mt = t.mt[p];
-    const double4* S = (const double4*)w.S;
-    const double4 sa = S[ab.x];
-    double4 Ga = w.adj_B[2 * ab.x], La = w.adj_B[2 * ab.x + 1];
-    double4 Gb = make_double4(0.0, 0.0, 0.0, 0.0), Lb = Gb, sb = Gb;
+    const double4_16a* S = (const double4_16a*)w.S;
+    const double4_16a sa = S[ab.x];
+    double4_16a Ga = w.adj_B[2 * ab.x], La = w.adj_B[2 * ab.x + 1];
+    double4_16a Gb = make_double4_16a(0.0, 0.0, 0.0, 0.0), Lb = Gb, sb = Gb;
     if (!wall) {
         sb = S[ab.y];
         Gb = w.adj_B[2 * ab.y];
@@ -156,13 +156,13 @@ __device__ __forceinline__ void adj_geometry(const CdGeom& g, const CdWork& w, c
     if (!(P.x > thr)) return;
     const int2 ab = t.ab[p];
     const bool wall = ab.y >= g.n;
-    const double4 geo = t.geo[p];
+    const double4_16a geo = t.geo[p];
     const double nx = geo.x, ny = geo.y;
-    const double4* S = (const double4*)w.S;
-    const double4 sa = S[ab.x];
-    const double4 Ga = w.adj_B[2 * ab.x];
-    const double4 va = t.V[ab.x];
-    double4 Gb = make_double4(0.0, 0.0, 0.0, 0.0), vb = Gb, sb = Gb;
+    const double4_16a* S = (const double4_16a*)w.S;
+    const double4_16a sa = S[ab.x];
+    const double4_16a Ga = w.adj_B[2 * ab.x];
+    const double4_16a va = t.V[ab.x];
+    double4_16a Gb = make_double4_16a(0.0, 0.0, 0.0, 0.0), vb = Gb, sb = Gb;
     if (!wall) {
         sb = S[ab.y];
         Gb = w.adj_B[2 * ab.y];
@@ -221,11 +221,11 @@ __global__ void k_tape_record(CdWork w, int n, int64_t cap)
     for (int k = tid; k <= CD_KMAX; k += stride) t.hdr->colour_off[k] = w.colour_off[k];
     for (int c = tid; c < nc; c += stride) {
         t.ab[c] = w.c_ab[c];
-        t.geo[c] = ((const double4*)w.c_geo)[c];
+        t.geo[c] = ((const double4_16a*)w.c_geo)[c];
         t.mt[c] = ((const double*)w.c_m)[c];
         t.P[c] = ((const double2*)w.c_P)[c];
     }
-    for (int i = tid; i < n; i += stride) t.V[i] = ((const double4*)w.V)[i];
+    for (int i = tid; i < n; i += stride) t.V[i] = ((const double4_16a*)w.V)[i];
 }
 
 __global__ void k_tape_advance(CdCtrl* ctrl, int T)
@@ -262,16 +262,16 @@ k_adjoint(CdGeom g, CdWork w, CdTape t, CdAdjIO io, double alpha, int max_sweeps
     for (int k = threadIdx.x; k <= CD_KMAX; k += blockDim.x) s_off[k] = t.hdr->colour_off[k];
 
     // incoming gradient: lambda = dL/dv' + dt dL/dx' (Eq. 2), Gamma = W lambda
-    const double4* S = (const double4*)w.S;
+    const double4_16a* S = (const double4_16a*)w.S;
     for (int i = tid; i < n; i += stride) {
         const double lx = io.dLv[2 * i] + g.dt * io.dLx[2 * i];
         const double ly = io.dLv[2 * i + 1] + g.dt * io.dLx[2 * i + 1];
         const double lw = io.dLw[i];
         const double im = S[i].x;
         const double iI = g.rotations ? io.inv_I[i] : 0.0;
-        w.adj_B[2 * i] = make_double4(im * lx, im * ly, iI * lw, 0.0);
-        w.adj_B[2 * i + 1] = make_double4(0.0, 0.0, 0.0, 0.0);
-        w.adj_lam[i] = make_double4(lx, ly, lw, 0.0);
+        w.adj_B[2 * i] = make_double4_16a(im * lx, im * ly, iI * lw, 0.0);
+        w.adj_B[2 * i + 1] = make_double4_16a(0.0, 0.0, 0.0, 0.0);
+        w.adj_lam[i] = make_double4_16a(lx, ly, lw, 0.0);
         w.adj_gx[i] = make_double2(io.dLx[2 * i], io.dLx[2 * i + 1]);
         w.adj_mark[i] = 0;
     }
@@ -285,10 +285,10 @@ k_adjoint(CdGeom g, CdWork w, CdTape t, CdAdjIO io, double alpha, int max_sweeps
             w.adj_Y[c] = make_double2(0.0, 0.0);
             pmax = fmax(pmax, t.P[c].x);
             const int2 ab = t.ab[c];
-            const double4 Ga = w.adj_B[2 * ab.x];
+            const double4_16a Ga = w.adj_B[2 * ab.x];
             double sc = sqrt(Ga.x * Ga.x + Ga.y * Ga.y) + S[ab.x].y * fabs(Ga.z);
             if (ab.y < n) {
-                const double4 Gb = w.adj_B[2 * ab.y];
+                const double4_16a Gb = w.adj_B[2 * ab.y];
                 sc += sqrt(Gb.x * Gb.x + Gb.y * Gb.y) + S[ab.y].y * fabs(Gb.z);
             } else {
                 sc += fabs(io.wq[ab.y - n]);
@@ -361,8 +361,8 @@ k_adjoint(CdGeom g, CdWork w, CdTape t, CdAdjIO io, double alpha, int max_sweeps
         w.partials[(size_t)((sweeps & 1) ? 1 : 0) * 3 * nb + 2 * nb + blockIdx.x] = acc4[3];
     }
     for (int i = tid; i < n; i += stride) {
-        const double4 lam = w.adj_lam[i];
-        const double4 L = w.adj_B[2 * i + 1];
+        const double4_16a lam = w.adj_lam[i];
+        const double4_16a L = w.adj_B[2 * i + 1];
         const double2 gx = w.adj_gx[i];
         io.ox[2 * i] = gx.x;
         io.ox[2 * i + 1] = gx.y;

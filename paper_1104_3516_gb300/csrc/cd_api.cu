@@ -201,8 +201,8 @@ static size_t layout(cd_system* s, char* base, CdWork* w)
     const size_t T = (size_t)s->p.tape_steps;
     t.tape = L.take<char>(base, T ? T * cd_tape_slot_bytes((int64_t)n, (int64_t)cap) : 1);
     t.adj_Y = L.take<double2>(base, T ? cap : 1);
-    t.adj_B = L.take<double4>(base, T ? 2 * n : 1);
-    t.adj_lam = L.take<double4>(base, T ? n : 1);
+    t.adj_B = L.take<double4_16a>(base, T ? 2 * n : 1);
+    t.adj_lam = L.take<double4_16a>(base, T ? n : 1);
     t.adj_gx = L.take<double2>(base, T ? n : 1);
     t.adj_mark = L.take<int>(base, T ? n : 1);
     if (w) *w = t;

@@ -527,7 +527,7 @@ __global__ void k_colour_scatter(CdGeom g, CdWork w, int nchunk, int pw)
     w.c_ab[pos] = ab;
     double b = __ddiv_rn(w.gap[c], g.dt);
     if (DIM == 2) {
-        typedef typename std::conditional<sizeof(T) == 8, double4, float4>::type T4;
+        typedef typename std::conditional<sizeof(T) == 8, double4_32a, float4>::type T4;
         typedef typename std::conditional<sizeof(T) == 8, double2, float2>::type T2;
         T4 geo;
         geo.x = (T)w.nrm[3 * c];
@@ -541,7 +541,7 @@ __global__ void k_colour_scatter(CdGeom g, CdWork w, int nchunk, int pw)
         P.y = (T)w.Pk[2 * c + 1];
         ((T2*)w.c_P)[pos] = P;
     } else {
-        typedef typename std::conditional<sizeof(T) == 8, double4, float4>::type T4;
+        typedef typename std::conditional<sizeof(T) == 8, double4_32a, float4>::type T4;
         typedef typename std::conditional<sizeof(T) == 8, double2, float2>::type T2;
         T4 geo;
         geo.x = (T)w.nrm[3 * c];

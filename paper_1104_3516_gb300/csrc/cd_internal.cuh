@@ -182,8 +182,8 @@ struct CdWork {
     // adjoint (params.tape_steps > 0)
     char* tape;         // tape_steps slots of CdTapeHdr + one step's records
     double2* adj_Y;     // cap: adjoint multipliers (Y_n, Y_t) of the contacts
-    double4* adj_B;     // 2 n: per particle Gamma (x, y, w, 0) then Lambda (x, y, w, 0)
-    double4* adj_lam;   // n: dL/dv of the step's velocities (x, y, w, 0)
+    double4_16a* adj_B; // 2 n: per particle Gamma (x, y, w, 0) then Lambda (x, y, w, 0)
+    double4_16a* adj_lam; // n: dL/dv of the step's velocities (x, y, w, 0)
     double2* adj_gx;    // n: dL/dx being accumulated
     int* adj_mark;      // n: 1 if the particle has a non-open contact
 };
@@ -201,17 +201,17 @@ struct CdTapeHdr {
 struct CdTape {
     CdTapeHdr* hdr;
     int2* ab;
-    double4* geo;       // nx, ny, b = g/dt, m_n
+    double4_16a* geo;   // nx, ny, b = g/dt, m_n
     double* mt;
     double2* P;         // converged (P_n, P_t)
-    double4* V;         // n: velocities after the step (vx, vy, w, 0)
+    double4_16a* V;     // n: velocities after the step (vx, vy, w, 0)
 };
 __host__ __device__ inline size_t cd_align256(size_t x) { return (x + 255) & ~(size_t)255; }
 __host__ __device__ inline size_t cd_tape_slot_bytes(int64_t n, int64_t cap)
 {
     const size_t c = (size_t)(cap > 0 ? cap : 1), m = (size_t)(n > 0 ? n : 1);
-    return cd_align256(sizeof(CdTapeHdr)) + cd_align256(c * sizeof(int2)) + cd_align256(c * sizeof(double4)) +
-           cd_align256(c * sizeof(double)) + cd_align256(c * sizeof(double2)) + cd_align256(m * sizeof(double4));
+    return cd_align256(sizeof(CdTapeHdr)) + cd_align256(c * sizeof(int2)) + cd_align256(c * sizeof(double4_16a)) +
+           cd_align256(c * sizeof(double)) + cd_align256(c * sizeof(double2)) + cd_align256(m * sizeof(double4_16a));
 }
 __host__ __device__ inline CdTape cd_tape_slot(char* tape, int64_t n, int64_t cap, int slot)
 {
@@ -222,13 +222,13 @@ __host__ __device__ inline CdTape cd_tape_slot(char* tape, int64_t n, int64_t ca
     p += cd_align256(sizeof(CdTapeHdr));
     t.ab = (int2*)p;
     p += cd_align256(c * sizeof(int2));
-    t.geo = (double4*)p;
-    p += cd_align256(c * sizeof(double4));
+    t.geo = (double4_16a*)p;
+    p += cd_align256(c * sizeof(double4_16a));
     t.mt = (double*)p;
     p += cd_align256(c * sizeof(double));
     t.P = (double2*)p;
     p += cd_align256(c * sizeof(double2));
-    t.V = (double4*)p;
+    t.V = (double4_16a*)p;
     return t;
 }
 #define CD_OBS_MAX 65536

@@ -42,7 +42,9 @@ struct MgInfo {
 };
 
 template <typename T> struct Vec;
-template <> struct Vec<double> { typedef double4 V4; typedef double2 V2; };
+// FP64 records are 32 bytes at 32-byte aligned addresses (every workspace array
+// is 256-byte aligned): one 256-bit access per record
+template <> struct Vec<double> { typedef double4_32a V4; typedef double2 V2; };
 template <> struct Vec<float> { typedef float4 V4; typedef float2 V2; };
 
 // Arithmetic of the sweep's real type with the rounding written out (no
@@ -1564,7 +1566,7 @@ cudaError_t cd_launch_static(const CdGeom& g, const CdWork& w, const double* rad
                              const double* inv_I, int precision, cudaStream_t s, int* nl)
 {
     if (precision == CD_FP64)
-        k_static<double><<<grid_n(g.n), CD_BLOCK, 0, s>>>(g, g.n, g.rotations, radius, inv_m, inv_I, (double4*)w.S);
+        k_static<double><<<grid_n(g.n), CD_BLOCK, 0, s>>>(g, g.n, g.rotations, radius, inv_m, inv_I, (Vec<double>::V4*)w.S);
     else
         k_static<float><<<grid_n(g.n), CD_BLOCK, 0, s>>>(g, g.n, g.rotations, radius, inv_m, inv_I, (float4*)w.S);
     ++*nl;
