@@ -373,7 +373,7 @@ def test_gpu_adjoint_sliding_pyramids_10k_against_finite_differences(record_prop
     gmu_F, = torch.autograd.grad(F, [mu])
     gv_H, gmu_H, gmu_F = gv_H.cpu().numpy(), float(gmu_H), float(gmu_F)
     F0, H0, s0, top0 = run(wl.v, wl.mu)
-    assert abs(F0 - float(F)) <= 1e-12 * abs(F0) and abs(H0 - float(H)) <= 1e-12 * abs(H0)
+    assert abs(F0 - float(F.detach())) <= 1e-12 * abs(F0) and abs(H0 - float(H.detach())) <= 1e-12 * abs(H0)
     assert abs(gmu_H) > 1e-3 and abs(gmu_F) > 0.1       # friction matters for both losses
     rng = np.random.default_rng(2025)
     dirs = [(np.zeros_like(wl.v), 1.0)] + [(rng.standard_normal(wl.v.shape), float(rng.standard_normal()))
