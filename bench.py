@@ -92,8 +92,9 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--domains", type=int, nargs=3, default=[1, 1, 1], metavar=("NX", "NY", "NZ"),
                     help="domain-wise update of Sec. 3.1: slabs per axis (1 1 1: Gauss-Seidel)")
-    ap.add_argument("--merge-last-colour", type=int, default=1,
-                    help="1: run the three (else two) last colours as one phase when the last class is small; 2: two at most; 0: off")
+    ap.add_argument("--merge-last-colour", type=int, default=4,
+                    help="1: run the three (else two) last colours as one phase when the last class is small; 2: two at most; "
+                         "4: as 1 after a solve of at least 64 sweeps (the default); 0: off")
     ap.add_argument("--sphere-steps", type=int, default=5,
                     help="timed steps of the 1e6-sphere 3D gas leg (rank 0 at N=1 only; 0: skip)")
     ap.add_argument("--batched-steps", type=int, default=3,

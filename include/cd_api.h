@@ -166,18 +166,23 @@ typedef struct {
                                paper draws its random sequential order anew
                                each step (Sec. 2.1) */
     int64_t merge_last_colour; /* colour-barrier schedule of a plain system:
-                               1 lets a step run its two last colours in one
+                               a step may run its M last colours in one
                                phase when the last class is small (at most a
-                               quarter of the one before): the contacts of
-                               the two colours are grouped into the chains
+                               quarter of the first merged one): the contacts
+                               of the M colours are grouped into the chains
                                that share particles (each at most 64
                                contacts), every chain goes whole to one block,
-                               which updates the chains' contacts of the
-                               earlier colour, synchronises its threads and
-                               then updates those of the last colour.  The
-                               order is the colour order, so results equal
-                               those without merging; one grid barrier per
-                               sweep fewer.  0: every colour its own phase. */
+                               which updates the chains' contacts of colour
+                               K-M, synchronises its threads, then those of
+                               colour K-M+1, and so on.  The order is the
+                               colour order, so results equal those without
+                               merging; M - 1 grid barriers per sweep fewer.
+                               1 or 3: M = 3 if that is taken, else M = 2;
+                               2: M = 2 only; 4: as 1, but a step merges only
+                               if the system's previous solve took at least
+                               64 sweeps (or there was none): the grouping
+                               costs about as much as ~60 sweeps' saving;
+                               0: every colour its own phase. */
 } cd_params;
 
 typedef struct cd_system cd_system;
@@ -191,7 +196,7 @@ typedef struct {
     int64_t n_colours;
     double wall_force[6];     /* sum of normal impulses on each wall / dt */
     int64_t n_phases;         /* grid-barrier phases per sweep: n_colours, or
-                                 one fewer when the two last colours ran as
+                                 M - 1 fewer when the M last colours ran as
                                  one phase (params.merge_last_colour) */
 } cd_solve_stats;
 

@@ -392,7 +392,7 @@ def cd_last_error(sysptr=None) -> str:
 def make_params(wl, precision=CD_FP64, criterion=CD_CONV_GLOBAL_REL, max_contacts=None, warm_start=1, rotations=1,
                 seed=None, max_sweeps=None, alpha=None, timing=0,
                 parallel_p=0.0, tape_steps=0, adjoint_compliance=0.0, use_graph=0, sweep_threads=0,
-                sweep_blocks_per_sm=0, domains=(1, 1, 1), merge_last_colour=1, parallel_redraw=0) -> cd_params:
+                sweep_blocks_per_sm=0, domains=(1, 1, 1), merge_last_colour=4, parallel_redraw=0) -> cd_params:
     p = cd_params()
     p.dim = wl.dim
     p.precision = precision

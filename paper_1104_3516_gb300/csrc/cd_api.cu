@@ -42,6 +42,12 @@ struct cd_system {
     int tape_head;                     // next tape slot a step records into
     int tape_count;                    // recorded steps not yet consumed by cd_adjoint_step
     int adj_blocks;                    // cooperative grid of the adjoint kernel
+    // params.merge_last_colour 4: sweeps + 1 of the last solve as last read
+    // back (0: none yet), valid while no solve has been launched since; lets
+    // a direct launch skip the merge passes the device would skip anyway
+    int mg_hint = 0;
+    bool mg_hint_valid = false;
+    bool capturing = false;            // inside capture_step: every launch goes into the graph
     std::vector<cudaEvent_t> events;   // phase events (params.timing)
     size_t ev_used;
     std::string err;
@@ -118,6 +124,7 @@ static size_t layout(cd_system* s, char* base, CdWork* w)
     t.poff = L.take<int>(base, n + 1);
     t.poff_prev = L.take<int>(base, n + 1);
     t.cand = L.take<int>(base, n * CD_CAND);
+    t.wmask = L.take<unsigned char>(base, n);
     t.pf = L.take<float4>(base, n);
     t.scan_tmp = L.take<int>(base, cd_scan_tmp_ints((int)scan_max) + 32);
     t.pairs = L.take<int2>(base, cap);
@@ -266,6 +273,8 @@ static cd_status read_ctrl(cd_system* s, CdCtrl* h)
 {
     CD_CUDA(s, cudaMemcpyAsync(h, s->w.ctrl, sizeof(CdCtrl), cudaMemcpyDeviceToHost, s->stream));
     CD_CUDA(s, cudaStreamSynchronize(s->stream));
+    s->mg_hint = h->mg_prev;
+    s->mg_hint_valid = true;
     return CD_OK;
 }
 
@@ -318,13 +327,23 @@ static cd_status launch_detect_chain(cd_system* s, int timed)
     CD_CUDA(s, cudaGetLastError());
     if (s->g.ndom_total > 1)
         CD_CUDA(s, cd_launch_domains(s->g, s->w, s->pos, s->radius, s->stream, &s->launches));
-    if (s->g.merge_last) CD_CUDA(s, cd_launch_merge(s->g, s->w, s->colour_blocks, s->stream, &s->launches));
+    if (s->g.merge_last) {
+        if (s->g.merge_auto && !s->capturing && s->mg_hint_valid && s->mg_hint > 0 &&
+            s->mg_hint - 1 < CD_MG_MIN_SWEEPS) {
+            // the previous solve was short (known on the host): no merge passes;
+            // merge = -1 tells the sweep that this step is not merged
+            CD_CUDA(s, cudaMemsetAsync(&s->w.ctrl->merge, 0xFF, sizeof(int), s->stream));
+        } else {
+            CD_CUDA(s, cd_launch_merge(s->g, s->w, s->colour_blocks, s->stream, &s->launches));
+        }
+    }
     return CD_OK;
 }
 
 static cd_status launch_solve(cd_system* s, int free_flight, int timed)
 {
     cd_status st;
+    s->mg_hint_valid = false;   // this solve's sweeps are unknown to the host until read back
     CD_CUDA(s, cd_launch_pack(s->g, s->w, s->vel, s->omega, s->radius, s->inv_m, s->inv_I, s->f_ext, free_flight,
                               (int)s->p.precision, s->stream, &s->launches));
     if (timed && (st = mark(s)) != CD_OK) return st;
@@ -617,12 +636,13 @@ static cd_status create_impl(const cd_params* params, int64_t npk, const int64_t
         s->sweep_threads = th;
         s->sweep_blocks = s->num_sms * per;
     }
-    // merging of the two last colours: plain systems with the colour-barrier
+    // merging of the last colours: plain systems with the colour-barrier
     // schedule (ignored otherwise)
-    if (p.merge_last_colour < 0 || p.merge_last_colour > 3) {
+    if (p.merge_last_colour < 0 || p.merge_last_colour > 4) {
         delete s;
-        return fail(nullptr, CD_ERR_INVALID_ARG, "merge_last_colour must be 0, 1, 2 or 3");
+        return fail(nullptr, CD_ERR_INVALID_ARG, "merge_last_colour must be 0, 1, 2, 3 or 4");
     }
+    g.merge_auto = (p.merge_last_colour == 4) ? 1 : 0;
     g.merge_last = (p.merge_last_colour && npk == 1 && g.par_p == 0.0 &&
                     g.ndom_total == 1 && !g.dyn_walls && p.tape_steps == 0 && cd_merge_label_blocks_per_sm() >= 1)
                        ? (p.merge_last_colour == 2 ? 2 : 3) : 0;
@@ -775,7 +795,9 @@ static cd_status capture_step(cd_system* s)
     cudaError_t e = cudaStreamBeginCapture(s->stream, cudaStreamCaptureModeThreadLocal);
     if (e != cudaSuccess) return cuda_fail(s, e, "cudaStreamBeginCapture (use_graph needs a non-default stream)");
     const int l0 = s->launches;
+    s->capturing = true;
     cd_status st = launch_step(s, 0);
+    s->capturing = false;
     cudaGraph_t graph = nullptr;
     e = cudaStreamEndCapture(s->stream, &graph);
     if (st != CD_OK) {

@@ -346,6 +346,18 @@ __device__ __forceinline__ bool wall_on(const GridV& v, int dim, int k)
     return ((v.wall_mask >> k) & 1) && (k >> 1) < dim;
 }
 
+// Walls in contact with the particle at xa (bit k: wall k has gap < delta).
+template <int DIM>
+__device__ __forceinline__ unsigned wall_mask_of(const CdGeom& g, const GridV& v, const double* wp, const double* xa,
+                                                 double ra)
+{
+    unsigned m = 0u;
+#pragma unroll
+    for (int k = 0; k < 2 * DIM; ++k)
+        if (wall_on(v, DIM, k) && wall_gap(xa, ra, wp, k) < g.delta) m |= 1u << k;
+    return m;
+}
+
 // Visits the candidate partners b > a of particle a in the 3^DIM cells around
 // it (in a's packing grid); calls f(b) for each b that passes the pair test.
 // Needs each cell's list sorted by id (k_cell_sort).
@@ -607,13 +619,10 @@ __global__ void __launch_bounds__(CD_BLOCK, 4) k_pair_count(CdGeom g, CdWork w, 
         __syncwarp();
         if (act) {
             const int cnt = s_cnt[threadIdx.x];
-            const double* wp = w.pk_wall_pos + 6 * v.pkid;
-            int nw = 0;
-#pragma unroll
-            for (int k = 0; k < 2 * DIM; ++k)
-                if (wall_on(v, DIM, k) && wall_gap(xa, ra, wp, k) < g.delta) ++nw;
+            const unsigned wm = wall_mask_of<DIM>(g, v, w.pk_wall_pos + 6 * v.pkid, xa, ra);
+            if (w.wmask) w.wmask[a] = (unsigned char)wm;   // the emitting pass reuses it
             if (cnt > CD_MAXLOC) atomicCAS(&ctrl->error, CDE_NONE, CDE_PER_PARTICLE);
-            pcnt[a] = cnt + nw;
+            pcnt[a] = cnt + __popc(wm);
         }
         __syncwarp();
     }
@@ -712,16 +721,14 @@ __global__ void k_pair_emit(CdGeom g, CdWork w, const double* __restrict__ pos, 
     for (int a = blockIdx.x * blockDim.x + threadIdx.x; a < g.n; a += gridDim.x * blockDim.x) {
         GridV v;
         grid_of(g, w, a, v);
-        const double* wp = w.pk_wall_pos + 6 * v.pkid;
         double xa[3] = {0.0, 0.0, 0.0};
 #pragma unroll
         for (int k = 0; k < DIM; ++k) xa[k] = pos[a * DIM + k];
         double ra = radius[a];
-        int nw = 0;
-#pragma unroll
-        for (int k = 0; k < 2 * DIM; ++k)
-            if (wall_on(v, DIM, k) && wall_gap(xa, ra, wp, k) < g.delta) ++nw;
-        const int npart = w.pcnt[a] - nw;   // partners the counting pass found
+        // the counting pass's walls (the same test, so not repeated in FP64)
+        const unsigned wm = w.wmask ? (unsigned)w.wmask[a]
+                                    : wall_mask_of<DIM>(g, v, w.pk_wall_pos + 6 * v.pkid, xa, ra);
+        const int npart = w.pcnt[a] - __popc(wm);   // partners the counting pass found
         int o = w.poff[a];
         if (w.cand && npart <= CD_CAND) {
             // the counting pass kept them (in the order its exact tests ran):
@@ -754,8 +761,7 @@ __global__ void k_pair_emit(CdGeom g, CdWork w, const double* __restrict__ pos, 
         }
 #pragma unroll
         for (int k = 0; k < 2 * DIM; ++k)
-            if (wall_on(v, DIM, k) && wall_gap(xa, ra, wp, k) < g.delta)
-                w.pairs_nx[o++] = make_int2(a, g.n + 6 * v.pkid + k);
+            if ((wm >> k) & 1u) w.pairs_nx[o++] = make_int2(a, g.n + 6 * v.pkid + k);
     }
 }
 

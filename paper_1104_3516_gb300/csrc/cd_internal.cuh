@@ -15,6 +15,7 @@
 #define CD_CHUNK 256          // contacts per chunk of the stable colour partition
 #define CD_WAIT_NS 2000000000ULL  // bound on any device-side wait (2 s)
 #define CD_MG_MAXC 3          // most colours one merged sweep phase takes
+#define CD_MG_MIN_SWEEPS 64   // params.merge_last_colour 4: merge after solves of at least this many sweeps
 
 // Device error codes written into CdCtrl::error.
 enum { CDE_NONE = 0, CDE_TIMEOUT = 1, CDE_COLOURS = 2, CDE_PER_PARTICLE = 3, CDE_TAPE = 4 };
@@ -56,10 +57,10 @@ struct CdCtrl {
     int tape_slot;                  // slot the next recorded step goes to
     int tape_pad;
     // merging of the last colours (params.merge_last_colour)
-    int merge;                      // M > 0: this step's sweeps run the M last colours as one phase
+    int merge;                      // M > 0: this step's sweeps run the M last colours as one phase (-1: not this step)
     int mg_changed;                 // chain labelling: a label moved in the current round
     int mg_maxsize;                 // largest chain
-    int mg_pad;
+    int mg_prev;                    // sweeps + 1 of the last solve (0: none yet), for params.merge_last_colour 4
 };
 
 // Parameters of one packing of a batched system (a plain system is a batch of
@@ -95,6 +96,7 @@ struct CdWork {
     int* cell_pid;      // n
     int* pcnt;          // n + 1
     int* cand;          // n * CD_CAND: partners b > a found by the counting pass (first CD_CAND, found order)
+    unsigned char* wmask; // n: walls in contact with each particle (bit k: wall k), from the counting pass (null: recomputed)
     float4* pf;         // n: (x, y, z, r) in single precision for the pair pre-filter (null: exact test only)
     int* poff;          // n + 1
     int* poff_prev;     // n + 1: poff of the current set (null: not kept)
@@ -269,6 +271,7 @@ struct CdGeom {
     int ndom[3];        // domain-wise update (Sec. 3.1): slabs per axis (1: not cut)
     int ndom_total;     // product; > 1 selects the domain-wise sweep
     int merge_last;     // params.merge_last_colour (0 off, 2: at most two colours, 3: three, else two)
+    int merge_auto;     // merge only after a solve of at least CD_MG_MIN_SWEEPS sweeps (or none yet)
     int merge_blocks;   // blocks of the sweep grid the chains are assigned to
 };
 

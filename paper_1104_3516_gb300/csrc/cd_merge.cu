@@ -62,8 +62,15 @@ __global__ void k_mg_init(CdGeom g, CdWork w, int M, int first)
     CdCtrl* ctrl = w.ctrl;
     if (!first && !mg_pass_live(ctrl)) return;
     const int i0 = blockIdx.x * blockDim.x + threadIdx.x, st = gridDim.x * blockDim.x;
+    if (first && g.merge_auto && ctrl->mg_prev > 0 && ctrl->mg_prev - 1 < CD_MG_MIN_SWEEPS) {
+        // the previous solve was short: grouping the chains would cost more
+        // than the barriers it saves; -1 stops this step's passes
+        if (i0 == 0) ctrl->merge = -1;
+        return;
+    }
     for (int i = i0; i < M * g.n; i += st) w.mg_slot[i] = -1;
-    for (int i = i0; i <= g.cap; i += st) { w.mg_size[i] = 0; w.mg_w[i] = 0; }
+    const int nc = ctrl->nc;   // labels, sizes and weights are indexed by live positions only
+    for (int i = i0; i <= nc; i += st) { w.mg_size[i] = 0; w.mg_w[i] = 0; }
     const int nbk = M * g.merge_blocks;
     for (int i = i0; i <= nbk; i += st) w.mg_bcnt[i] = 0;
     for (int i = i0; i < nbk; i += st) { w.mg_bmin[i] = INT_MAX; w.mg_bmax[i] = -1; }

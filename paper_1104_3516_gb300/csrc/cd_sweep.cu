@@ -902,6 +902,7 @@ __device__ __forceinline__ void finish_solve(const CdGeom& g, const CdWork& w, i
         if (threadIdx.x == 0) {
             for (int q = 0; q < 6; ++q) ctrl->wall_force[q] = wf[q] / g.dt;
             ctrl->sweeps = sweeps;
+            ctrl->mg_prev = sweeps + 1;
             ctrl->converged = converged;
             ctrl->residual = resid;
             ctrl->r_avg = ravg;

@@ -102,8 +102,23 @@ def test_merged_phase_full_size_pile():
 
 def test_merge_parameter_is_checked():
     from paper_1104_3516_gb300 import cd
-    with pytest.raises(cd.CDError):
-        gpu_system(CASES["dense_deposit"], merge_last_colour=4)
+    for bad in (-1, 5):
+        with pytest.raises(cd.CDError):
+            gpu_system(CASES["dense_deposit"], merge_last_colour=bad)
+
+
+@pytest.mark.parametrize("cap, merged_later", [(5, False), (80, True)])
+def test_automatic_merge_follows_the_previous_solve(cap, merged_later):
+    """merge_last_colour 4 merges on a system's first step (no solve yet)
+    and afterwards only if the previous solve took at least 64 sweeps; the
+    bits equal the unmerged run's either way."""
+    from paper_1104_3516_gb300 import cd
+    a, b, sa, sb = pair(CASES["dense_deposit"], steps=3, merge=4, criterion=cd.CD_CONV_NONE, max_sweeps=cap)
+    identical(a, b)
+    k = [s["last"]["n_colours"] for s in sb]
+    assert sb[0]["last"]["n_phases"] == k[0] - 2
+    for s, kk in zip(sb[1:], k[1:]):
+        assert s["last"]["n_phases"] == (kk - 2 if merged_later else kk)
 
 
 @pytest.mark.parametrize("kw", [dict(parallel_p=0.3), dict(domains=(2, 2, 1))])
