@@ -324,7 +324,8 @@ __global__ void k_rep_flag(CdGeom g, CdWork w)
 {
     if (w.ctrl->skip) return;
     const int nc = w.ctrl->nc;
-    for (int c = blockIdx.x * blockDim.x + threadIdx.x; c <= g.cap; c += gridDim.x * blockDim.x) {
+    // up to nc: the scan of the flags reads the live contacts only
+    for (int c = blockIdx.x * blockDim.x + threadIdx.x; c <= nc; c += gridDim.x * blockDim.x) {
         int f = 0;
         if (c < nc) {
             const int t = w.rep_top[rep_pack_of(g, w, w.pairs[c].x)];
@@ -457,8 +458,12 @@ __global__ void k_rep_ncolours(CdWork w)
 {
     if (w.ctrl->skip) return;
     const int nc = w.ctrl->nc;
-    for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < nc; c += gridDim.x * blockDim.x)
-        atomicMax(&w.ctrl->ncolours, w.colour[c] + 1);
+    // warps step together (uniform bound); one atomic per warp
+    for (int c0 = blockIdx.x * blockDim.x + (threadIdx.x & ~31); c0 < nc; c0 += gridDim.x * blockDim.x) {
+        const int c = c0 + (threadIdx.x & 31);
+        const int top = __reduce_max_sync(0xffffffffu, c < nc ? w.colour[c] + 1 : 0);
+        if ((threadIdx.x & 31) == 0) atomicMax(&w.ctrl->ncolours, top);
+    }
 }
 
 static cudaError_t launch_repair(const CdGeom& g, const CdWork& w, int gc, cudaStream_t s, int* nl)
