@@ -491,12 +491,19 @@ static cudaError_t launch_repair(const CdGeom& g, const CdWork& w, int gc, cudaS
 }
 
 // Per-chunk colour histogram, layout [colour][chunk].
-__global__ void k_chunk_hist(CdWork w, int nchunk)
+// Chunks of CD_CHUNK colour-order positions: only the live ones (those
+// holding contacts) are counted, laid out [colour][live chunk], and scanned.
+__device__ __forceinline__ int live_chunks(int nc) { return (nc + CD_CHUNK - 1) / CD_CHUNK; }
+
+__global__ void k_chunk_hist(CdWork w)
 {
     __shared__ int s_cnt[CD_KMAX];
     CdCtrl* ctrl = w.ctrl;
     if (ctrl->skip) return;
     int nc = ctrl->nc;
+    const int ncl = live_chunks(nc);
+    if (blockIdx.x == 0 && threadIdx.x == 0) ctrl->chunk_last = CD_KMAX * ncl - 1;
+    if ((int)blockIdx.x >= ncl) return;
     for (int k = threadIdx.x; k < CD_KMAX; k += blockDim.x) s_cnt[k] = 0;
     __syncthreads();
     int c = blockIdx.x * CD_CHUNK + threadIdx.x;
@@ -505,16 +512,18 @@ __global__ void k_chunk_hist(CdWork w, int nchunk)
         if (k >= 0 && k < CD_KMAX) atomicAdd(&s_cnt[k], 1);
     }
     __syncthreads();
-    for (int k = threadIdx.x; k < CD_KMAX; k += blockDim.x) w.chunk_cnt[k * nchunk + blockIdx.x] = s_cnt[k];
+    for (int k = threadIdx.x; k < CD_KMAX; k += blockDim.x) w.chunk_cnt[k * ncl + blockIdx.x] = s_cnt[k];
 }
 
 template <int DIM, typename T>
-__global__ void k_colour_scatter(CdGeom g, CdWork w, int nchunk, int pw)
+__global__ void k_colour_scatter(CdGeom g, CdWork w, int pw)
 {
     __shared__ int s_wcnt[CD_CHUNK / 32][CD_KMAX];
     CdCtrl* ctrl = w.ctrl;
     if (ctrl->skip) return;
     int nc = ctrl->nc;
+    const int ncl = live_chunks(nc);
+    if ((int)blockIdx.x >= ncl) return;
     int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     for (int i = threadIdx.x; i < (CD_CHUNK / 32) * CD_KMAX; i += blockDim.x) (&s_wcnt[0][0])[i] = 0;
     __syncthreads();
@@ -526,7 +535,7 @@ __global__ void k_colour_scatter(CdGeom g, CdWork w, int nchunk, int pw)
     __syncthreads();
     if (c >= nc || k < 0) return;
     for (int v = 0; v < wid; ++v) rank += s_wcnt[v][k];
-    int pos = w.chunk_cnt[k * nchunk + blockIdx.x] + rank;
+    int pos = w.chunk_cnt[k * ncl + blockIdx.x] + rank;
     w.perm[pos] = c;
     int2 ab = w.pairs[c];
     w.c_ab[pos] = ab;
@@ -567,12 +576,13 @@ __global__ void k_colour_scatter(CdGeom g, CdWork w, int nchunk, int pw)
     }
 }
 
-__global__ void k_colour_offsets(CdWork w, int nchunk)
+__global__ void k_colour_offsets(CdWork w)
 {
     CdCtrl* ctrl = w.ctrl;
     if (ctrl->skip) return;
     int k = threadIdx.x;
-    if (k < CD_KMAX) w.colour_off[k] = w.chunk_cnt[k * nchunk];
+    const int ncl = live_chunks(ctrl->nc);
+    if (k < CD_KMAX) w.colour_off[k] = (ncl > 0) ? w.chunk_cnt[k * ncl] : 0;
     if (k == 0) w.colour_off[CD_KMAX] = ctrl->nc;
 }
 
@@ -653,18 +663,19 @@ cudaError_t cd_launch_colour(const CdGeom& g, const CdWork& w, int coop_blocks, 
         ++*nl;
     }
     if ((e = launch_repair(g, w, gc, s, nl)) != cudaSuccess) return e;
-    k_chunk_hist<<<nchunk, CD_CHUNK, 0, s>>>(w, nchunk); ++*nl;
-    if ((e = cd_scan_exclusive(w.chunk_cnt, w.chunk_cnt, CD_KMAX * nchunk, w.scan_tmp, nullptr, s, nl)) != cudaSuccess)
+    k_chunk_hist<<<nchunk, CD_CHUNK, 0, s>>>(w); ++*nl;
+    if ((e = cd_scan_exclusive(w.chunk_cnt, w.chunk_cnt, CD_KMAX * nchunk, w.scan_tmp, nullptr, s, nl,
+                               &w.ctrl->chunk_last)) != cudaSuccess)
         return e;
     if (g.dim == 2) {
-        if (precision == CD_FP64) k_colour_scatter<2, double><<<nchunk, CD_CHUNK, 0, s>>>(g, w, nchunk, pw);
-        else k_colour_scatter<2, float><<<nchunk, CD_CHUNK, 0, s>>>(g, w, nchunk, pw);
+        if (precision == CD_FP64) k_colour_scatter<2, double><<<nchunk, CD_CHUNK, 0, s>>>(g, w, pw);
+        else k_colour_scatter<2, float><<<nchunk, CD_CHUNK, 0, s>>>(g, w, pw);
         ++*nl;
     } else {
-        if (precision == CD_FP64) k_colour_scatter<3, double><<<nchunk, CD_CHUNK, 0, s>>>(g, w, nchunk, pw);
-        else k_colour_scatter<3, float><<<nchunk, CD_CHUNK, 0, s>>>(g, w, nchunk, pw);
+        if (precision == CD_FP64) k_colour_scatter<3, double><<<nchunk, CD_CHUNK, 0, s>>>(g, w, pw);
+        else k_colour_scatter<3, float><<<nchunk, CD_CHUNK, 0, s>>>(g, w, pw);
         ++*nl;
     }
-    k_colour_offsets<<<1, CD_KMAX, 0, s>>>(w, nchunk); ++*nl;
+    k_colour_offsets<<<1, CD_KMAX, 0, s>>>(w); ++*nl;
     return cudaGetLastError();
 }

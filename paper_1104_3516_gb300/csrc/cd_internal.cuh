@@ -61,6 +61,8 @@ struct CdCtrl {
     int mg_changed;                 // chain labelling: a label moved in the current round
     int mg_maxsize;                 // largest chain
     int mg_prev;                    // sweeps + 1 of the last solve (0: none yet), for params.merge_last_colour 4
+    int chunk_last;                 // colour partition: CD_KMAX x live chunks - 1 (the scan's extent)
+    int chunk_pad;
 };
 
 // Parameters of one packing of a batched system (a plain system is a batch of
@@ -118,7 +120,7 @@ struct CdWork {
     int* p2c;           // 2 * cap
     unsigned long long* prio;  // cap colouring priorities
     int* round_cnt;     // 3 counters of the colouring rounds
-    int* chunk_cnt;     // CD_KMAX * nchunk_cap + 1
+    int* chunk_cnt;     // CD_KMAX * nchunk_cap + 1; used as [colour][live chunk]
     int* colour_off;    // CD_KMAX + 1
     int* perm;          // colour position -> key index
     // contacts, colour order (real type)
