@@ -161,9 +161,10 @@ struct CdWork {
     int* view_owner;    // 2 cap: particle of each view record
     void* V0;           // 2 cap velocity records: the sweep-start velocity of the view's particle
     int2* c_vab;        // cap (colour order): velocity records of bodies a and b
-    // merging of the two last colours: the colour-order positions of the two
-    // last colours form chains (contacts linked through a shared particle);
-    // chains are assigned whole to the blocks of the sweep grid
+    // merging of the M last colours: their colour-order positions form chains
+    // (contacts linked through a shared particle); chains are assigned whole
+    // to the blocks of the sweep grid (arrays sized by capacity, used up to
+    // the live contacts)
     int* mg_slot;       // CD_MG_MAXC x n: [m n + i] position of particle i's contact of colour K-M+m, or -1
     int* mg_label;      // cap: chain label (smallest position of the chain)
     int* mg_size;       // cap + 1: contacts of the chain labelled by the index
