@@ -449,14 +449,16 @@ __device__ __forceinline__ double clamp_sym(double x, double lim)
 }
 __device__ __forceinline__ float clamp_sym(float x, float lim) { return x < -lim ? -lim : (x > lim ? lim : x); }
 
-// |P| = sqrt(s) from |P|^2 for the residual only, in three FP64
-// instructions (the FP64 pipe is the narrow one).  Write s = m 4^k with m in
-// [1, 4) by exponent arithmetic on the bit pattern; take the FP32 reciprocal
-// square root z of m rounded to FP32 (correctly rounded, __frsqrt_rn, on the
-// wide FP32 pipe); then one Newton step of Heron's iteration for sqrt(m)
-// from y = m z, with z / 2 for 1 / (2 y): y + (m - y^2) z / 2; scale by 2^k.
-// With |z sqrt(m) - 1| = e of order 2^-24 the result is sqrt(s) (1 - 1.5 e^2
-// + O(e^3)), within 1e-14 relative.  Subnormal and infinite s take
+// |P| = sqrt(s) from |P|^2 for the residual only, in two FP64 instructions
+// (the FP64 pipe is the narrow one).  Write s = m 4^k with m in [1, 4) by
+// exponent arithmetic on the bit pattern; take the FP32 reciprocal square
+// root z of m rounded to FP32 (correctly rounded, __frsqrt_rn) and the FP32
+// product y = m z, both on the wide FP32 pipe and widened exactly; then one
+// Newton step of Heron's iteration for sqrt(m) from y, with z / 2 for
+// 1 / (2 y): y + (m - y^2) z / 2; scale by 2^k.  With y = sqrt(m) (1 + d),
+// |d| <= 2.5 2^-24 (three FP32 roundings), and z sqrt(m) = 1 + e, |e| <=
+// 1.5 2^-24, the result is sqrt(m) (1 - d^2 / 2 - d e + O(d^3)): within
+// 2.5e-14 relative.  Subnormal and infinite s take
 // s * rsqrt(s); zero and negative s give 0; a NaN with the sign bit clear
 // (what arithmetic on NaN produces here) gives NaN, as sqrt would, so that a
 // diverged iteration does not look converged to the residual test; the
@@ -475,9 +477,9 @@ __device__ __forceinline__ double norm_of_sq(double s)
     const float mf = __int_as_float((int)(((mb + (1LL << 28)) >> 29) - (896LL << 23)));
     const float zf = __frsqrt_rn(mf);   // in [0.5, 1]
     const long long zb = ((long long)__float_as_int(zf) << 29) + (896LL << 52);   // exact widening
-    const double z = __longlong_as_double(zb);
     const double h = __longlong_as_double(zb - (1LL << 52));                      // z / 2
-    const double y = __dmul_rn(m, z);
+    const float yf = __fmul_rn(mf, zf);                                            // ~sqrt(m), in (0.9, 2.1)
+    const double y = __longlong_as_double(((long long)__float_as_int(yf) << 29) + (896LL << 52));   // exact
     const double r = __fma_rn(-y, y, m);
     const double y1 = __fma_rn(r, h, y);
     return __longlong_as_double(__double_as_longlong(y1) + ((long long)k << 52));
