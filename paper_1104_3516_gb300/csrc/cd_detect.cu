@@ -541,9 +541,12 @@ __device__ __forceinline__ void exact_batch(const CdGeom& g, const CdWork& w, co
 // 1e6-sphere gas).  The partners found and their count are those of the
 // walk; only the order in which a particle's first CD_CAND partners are kept
 // depends on timing, and the emitting pass sorts them.  The runs live in
-// shared memory, the walk's state in registers.
+// shared memory and the walk's state in registers: 64 registers, four
+// blocks per SM without spills.  The particle's wall contacts are kept as a
+// bit mask for the emitting pass.
 template <int DIM>
-__global__ void __launch_bounds__(CD_BLOCK, 4) k_pair_count(CdGeom g, CdWork w, const double* __restrict__ pos, const double* __restrict__ radius,
+__global__ void __launch_bounds__(CD_BLOCK, 4)
+k_pair_count(CdGeom g, CdWork w, const double* __restrict__ pos, const double* __restrict__ radius,
                              const int* __restrict__ cell_of, const int* __restrict__ cell_start,
                              const int* __restrict__ cell_pid, int* __restrict__ pcnt, CdCtrl* ctrl)
 {
