@@ -50,7 +50,8 @@ BYTES_PER_CONTACT_3D = {"f64": 120, "f32": 64}
 BYTES_PER_PARTICLE_3D = {"f64": 160, "f32": 80}
 # algorithmic FP64 flops of one 2D contact update as the sweep kernel writes
 # it: relative velocity 2 + 2 (u_n) + 7 (u_t), P_n 3, mu P_n 1, P_t 2,
-# impulse change 2, its vector 6, both bodies' velocities 12, |P| 4 (3 + sqrt)
+# impulse change 2, its vector 6, both bodies' velocities 12, |P| 4 + 1 (the
+# square root counted as one)
 FLOPS_PER_UPDATE_2D = 42
 # 3D (FMA = 2): lever sums 9, relative velocity 15, u_n 5, tangential part 6,
 # P_n 3, trial P_t 6, mu P_n 1, cone test 6, impulse change 4, its vector 6,
